@@ -1,0 +1,325 @@
+"""Pins for the CPU oracle: each check comes from somewhere other than the
+oracle's own code (brute force, closed-form counts, homomorphism projections,
+the thesis's worked example, planted mistakes)."""
+from math import comb, perm
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1807_08804_gb300.inputs import ANY, UNBOUND
+from tests.helpers import (connected_random_query, graph_from_triples, homomorphism_projections,
+                           parse_worked_example, query, random_tiny)
+
+
+def og(g):
+    return O.OracleGraph.from_graph(g)
+
+
+# ----------------------------------------------------------- brute force
+def test_backtracking_equals_brute_force_2000_cases():
+    """Definition 3.2 (injective, edges and labels kept) read for directed,
+    relation-labelled graphs: backtracking == every injective map tried."""
+    rng = np.random.default_rng(12345)
+    nonzero = 0
+    for case in range(2000):
+        g, q = random_tiny(rng)
+        o = og(g)
+        a = O.match(o, q, cap=1 << 16)
+        b = O.brute(o, q, cap=1 << 16)
+        assert a.status == 0 and b.status == 0
+        assert a.count == b.count, case
+        assert a.fingerprint == b.fingerprint, case
+        np.testing.assert_array_equal(a.rows, b.rows)
+        nonzero += a.count > 0
+    assert nonzero > 300  # the cases are not all trivially empty
+
+
+def test_cap_keeps_lexicographically_smallest_rows():
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        g, q = random_tiny(rng)
+        o = og(g)
+        full = O.brute(o, q, cap=1 << 16)
+        for cap in (1, 2, 5):
+            t = O.match(o, q, cap=cap)
+            assert t.count == full.count and t.fingerprint == full.fingerprint
+            np.testing.assert_array_equal(t.rows, full.rows[:cap])
+
+
+# ----------------------------------------------------------- closed forms
+def complete_digraph(n, T=1, types=None):
+    return graph_from_triples(n, [(s, 0, d) for s in range(n) for d in range(n) if s != d], types, T, 1)
+
+
+@pytest.mark.parametrize("n,k", [(6, 1), (6, 3), (7, 4), (8, 5), (9, 4)])
+def test_complete_digraph_counts(n, k):
+    """K_n (every ordered pair, one relation): any connected k-vertex query
+    has n!/(n-k)! embeddings; with one bound vertex (n-1)!/(n-k)!."""
+    rng = np.random.default_rng(n * 100 + k)
+    o = og(complete_digraph(n))
+    for extra in (0, 2):
+        edges = connected_random_query(rng, k, 1, extra if k > 1 else 0)
+        assert O.match(o, query(k, edges), cap=0).count == perm(n, k)
+        vb = [UNBOUND] * k
+        vb[int(rng.integers(k))] = int(rng.integers(n))
+        assert O.match(o, query(k, edges, vbind=vb), cap=0).count == perm(n - 1, k - 1)
+
+
+def test_typed_complete_digraph_counts():
+    """Typed K_n: types of sizes n_t, query with c_t vertices of type t:
+    prod_t n_t!/(n_t-c_t)!."""
+    sizes = [3, 4, 2]
+    types = sum([[t] * s for t, s in enumerate(sizes)], [])
+    o = og(complete_digraph(sum(sizes), T=3, types=types))
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        k = int(rng.integers(2, 6))
+        qt = [int(x) for x in rng.integers(0, 3, k)]
+        want = 1
+        for t, s in enumerate(sizes):
+            want *= perm(s, qt.count(t)) if qt.count(t) <= s else 0
+        edges = connected_random_query(rng, k, 1, 1)
+        assert O.match(o, query(k, edges, vtype=qt), cap=0).count == want
+
+
+def transitive_tournament(n):
+    return graph_from_triples(n, [(i, 0, j) for i in range(n) for j in range(n) if i < j])
+
+
+@pytest.mark.parametrize("n,k", [(7, 3), (9, 4), (10, 5)])
+def test_transitive_tournament_direction(n, k):
+    """Edges i->j iff i<j: a directed k-path and a transitive k-clique both
+    give C(n,k); a directed k-cycle gives 0 (ignoring direction would give
+    n!/(n-k)! for each)."""
+    o = og(transitive_tournament(n))
+    path = [(i, i + 1, 0) for i in range(k - 1)]
+    clique = [(i, j, 0) for i in range(k) for j in range(i + 1, k)]
+    cycle = [(i, (i + 1) % k, 0) for i in range(k)]
+    assert O.match(o, query(k, path), cap=0).count == comb(n, k)
+    assert O.match(o, query(k, clique), cap=0).count == comb(n, k)
+    assert O.match(o, query(k, cycle), cap=0).count == 0
+    reversed_path = [(i + 1, i, 0) for i in range(k - 1)]
+    assert O.match(o, query(k, reversed_path), cap=0).count == comb(n, k)
+
+
+@pytest.mark.parametrize("c,m", [(3, 4), (2, 5), (4, 3)])
+def test_disjoint_cycles(c, m):
+    """c disjoint directed m-cycles: a directed k-path (k<=m) gives c*m
+    embeddings; a directed m-cycle c*m; a k-cycle with k != m gives 0."""
+    tr = [(b * m + i, 0, b * m + (i + 1) % m) for b in range(c) for i in range(m)]
+    o = og(graph_from_triples(c * m, tr))
+    for k in range(1, m + 1):
+        assert O.match(o, query(k, [(i, i + 1, 0) for i in range(k - 1)]), cap=0).count == c * m
+    assert O.match(o, query(m, [(i, (i + 1) % m, 0) for i in range(m)]), cap=0).count == c * m
+    for k in range(2, m + 3):
+        if k != m:
+            assert O.match(o, query(k, [(i, (i + 1) % k, 0) for i in range(k)]), cap=0).count == 0
+
+
+@pytest.mark.parametrize("d,s", [(5, 2), (6, 4), (7, 7), (4, 5)])
+def test_out_star(d, s):
+    """Hub with d out-leaves: an out-star query with s leaves gives
+    d!/(d-s)! (0 when s > d); its in-star mirror gives 0."""
+    o = og(graph_from_triples(d + 1, [(0, 0, i) for i in range(1, d + 1)]))
+    want = perm(d, s) if s <= d else 0
+    assert O.match(o, query(s + 1, [(0, i, 0) for i in range(1, s + 1)]), cap=0).count == want
+    assert O.match(o, query(s + 1, [(i, 0, 0) for i in range(1, s + 1)]), cap=0).count == 0
+
+
+def test_relation_labels_matter():
+    """Two relations on the same pairs: a query on relation 1 only sees
+    relation-1 edges."""
+    tr = [(0, 0, 1), (1, 1, 2), (2, 0, 0), (0, 1, 2)]
+    o = og(graph_from_triples(3, tr, R=2))
+    assert O.match(o, query(2, [(0, 1, 1)]), cap=0).count == 2   # (1,2), (0,2)
+    assert O.match(o, query(2, [(0, 1, 0)]), cap=0).count == 2   # (0,1), (2,0)
+    assert O.match(o, query(3, [(0, 1, 0), (1, 2, 1)]), cap=0).count == 1  # 0->1->2
+
+
+# --------------------------------------------------------- worked example
+def test_worked_example():
+    """Facts printed for the thesis's sample query/data graph (Section 3.3):
+    Definition 3.3 candidates C(u3), C(u1) and the stated match."""
+    d = parse_worked_example()
+    qn = sorted(d["query_labels"], key=lambda s: int(s[1:]))
+    dn = sorted(d["data_labels"], key=lambda s: int(s[1:]))
+    qi = {u: i for i, u in enumerate(qn)}
+    di = {v: i for i, v in enumerate(dn)}
+    tr = []
+    for a, b in d["data_edges"]:
+        tr += [(di[a], 0, di[b]), (di[b], 0, di[a])]
+    g = graph_from_triples(len(dn), tr, [d["data_labels"][v] for v in dn], 5, 1)
+    qe = []
+    for a, b in d["query_edges"]:
+        qe += [(qi[a], qi[b], 0), (qi[b], qi[a], 0)]
+    q = query(len(qn), qe, vtype=[d["query_labels"][u] for u in qn])
+    o = og(g)
+    c0 = O.candidates(o, q, signature=True)
+    for u, vs in d["expect_candidates"].items():
+        got = sorted(dn[v] for v in np.flatnonzero(c0[qi[u]]))
+        assert got == sorted(vs, key=lambda s: int(s[1:])), u
+    r = O.match(o, q, cap=16)
+    assert r.count == d["expect_count"]
+    want = [di[d["expect_match"][u]] for u in qn]
+    assert [list(x) for x in r.rows] == [want]
+
+
+# ------------------------------------------------ filter and refinement
+def test_refinement_on_trees_equals_homomorphism_projection():
+    """Arc consistency is exact on tree-shaped queries: starting from the
+    binding/type sets, the refinement fixpoint equals {f(u)} over all
+    (not necessarily injective) edge-preserving maps."""
+    rng = np.random.default_rng(99)
+    checked = 0
+    for _ in range(150):
+        g, _ = random_tiny(rng, n_max=5, k_max=4)
+        k = int(rng.integers(1, 5))
+        edges = connected_random_query(rng, k, g.num_rels, 0)  # a tree
+        qt = [int(rng.integers(g.num_types)) if rng.random() < 0.5 else ANY for _ in range(k)]
+        qb = [int(rng.integers(g.num_vertices)) if rng.random() < 0.15 else UNBOUND for _ in range(k)]
+        q = query(k, edges, qt, qb)
+        o = og(g)
+        start = O.candidates(o, q, signature=False)
+        fix, _ = O.refine(o, q, start)
+        want = homomorphism_projections(g, q)
+        if not want.any():
+            # with no homomorphism at all, every set empties (tree case)
+            assert not fix.any()
+        else:
+            np.testing.assert_array_equal(fix, want)
+        checked += 1
+    assert checked == 150
+
+
+def test_filter_and_fixpoint_are_sound():
+    """Every vertex used by an embedding survives C0 (with the degree test)
+    and the refinement fixpoint, on cyclic queries too."""
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        g, q = random_tiny(rng)
+        o = og(g)
+        emb = O.brute(o, q, cap=1 << 16)
+        c0 = O.candidates(o, q, True)
+        fix, _ = O.refine(o, q, c0)
+        assert not (fix & ~c0).any()
+        for row in emb.rows:
+            for u, v in enumerate(row):
+                assert c0[u, v] and fix[u, v]
+
+
+def test_degree_test_is_per_direction_and_relation():
+    """Definition 3.3 read per (direction, relation): a query vertex with s
+    out-neighbours over relation r admits exactly the data vertices with at
+    least s distinct r-out-neighbours (counted here from the triple list)."""
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        g, _ = random_tiny(rng, n_max=7)
+        R = g.num_rels
+        s = int(rng.integers(1, 4))
+        r = int(rng.integers(R))
+        q = query(s + 1, [(0, i, r) for i in range(1, s + 1)])
+        c0 = O.candidates(og(g), q, True)
+        outs = {}
+        for v in range(g.num_vertices):
+            a, b = int(g.row_offsets[v]), int(g.row_offsets[v + 1])
+            outs[v] = len({int(g.col_targets[e]) for e in range(a, b) if g.edge_rel[e] == r})
+        assert [bool(x) for x in c0[0]] == [outs[v] >= s for v in range(g.num_vertices)]
+        ins = {v: 0 for v in range(g.num_vertices)}
+        seen = set()
+        for v in range(g.num_vertices):
+            for e in range(int(g.row_offsets[v]), int(g.row_offsets[v + 1])):
+                t = (v, int(g.col_targets[e]))
+                if g.edge_rel[e] == r and t not in seen:
+                    seen.add(t)
+                    ins[t[1]] += 1
+        assert [bool(x) for x in c0[1]] == [ins[v] >= 1 for v in range(g.num_vertices)]
+
+
+def test_edge_tables_against_single_edge_matches():
+    """Section 3.3.4's candidate edges: for a one-edge query the total table
+    size equals the number of embeddings, in both orientations, and every
+    embedding's (f(a), f(b)) pair is in the table of any query edge."""
+    rng = np.random.default_rng(21)
+    for _ in range(200):
+        g, q = random_tiny(rng)
+        o = og(g)
+        if q.m == 0:
+            continue
+        fix = O.fixpoint(o, q)
+        emb = O.brute(o, q, cap=1 << 16)
+        for e in range(q.m):
+            a, b = int(q.esrc[e]), int(q.edst[e])
+            for from_src in (True, False):
+                keys, off, vals = O.edge_table(o, q, fix, e, from_src)
+                pairs = set()
+                for i, key in enumerate(keys):
+                    for v in vals[int(off[i]):int(off[i + 1])]:
+                        pairs.add((int(key), int(v)) if from_src else (int(v), int(key)))
+                    assert list(vals[int(off[i]):int(off[i + 1])]) == sorted(vals[int(off[i]):int(off[i + 1])])
+                for row in emb.rows:
+                    assert (int(row[a]), int(row[b])) in pairs
+        # one-edge query: table size == embeddings
+        e = 0
+        q1 = query(2, [(0, 1, int(q.erel[e]))],
+                   vtype=[q.vtype[q.esrc[e]], q.vtype[q.edst[e]]], vbind=[q.vbind[q.esrc[e]], q.vbind[q.edst[e]]])
+        f1 = O.fixpoint(o, q1)
+        n1 = O.brute(o, q1, cap=0).count
+        for from_src in (True, False):
+            _, off, _ = O.edge_table(o, q1, f1, 0, from_src)
+            assert int(off[-1]) == n1
+
+
+# ----------------------------------------------------- verifier, fingerprint
+def test_verifier_catches_planted_mistakes():
+    rng = np.random.default_rng(31)
+    caught = 0
+    for _ in range(300):
+        g, q = random_tiny(rng)
+        o = og(g)
+        emb = O.brute(o, q, cap=1 << 16)
+        assert O.verify(o, q, emb.rows) == -1
+        if emb.count == 0:
+            continue
+        valid = {tuple(r) for r in emb.rows}
+        bad = emb.rows[0].copy()
+        i = int(rng.integers(q.k))
+        bad[i] = (bad[i] + 1 + int(rng.integers(g.num_vertices - 1))) % g.num_vertices
+        rows = np.vstack([emb.rows, bad[None]])
+        if tuple(bad) in valid:
+            assert O.verify(o, q, rows) == -1
+        else:
+            assert O.verify(o, q, rows) == len(emb.rows)
+            caught += 1
+    assert caught > 50
+
+
+def test_fingerprint_is_order_free_sum():
+    rng = np.random.default_rng(41)
+    for _ in range(100):
+        g, q = random_tiny(rng)
+        o = og(g)
+        r = O.match(o, q, cap=1 << 16)
+        perm_rows = r.rows[rng.permutation(len(r.rows))] if len(r.rows) else r.rows
+        assert O.fingerprint(perm_rows) == r.fingerprint
+        if len(r.rows) >= 2:
+            # a changed row changes the fingerprint
+            alt = r.rows.copy()
+            alt[0, 0] ^= 1
+            assert O.fingerprint(alt) != r.fingerprint
+
+
+def test_invalid_queries_rejected():
+    o = og(complete_digraph(4))
+    assert O.match(o, query(2, [(0, 0, 0)]), cap=0).status == 1      # self-loop
+    assert O.match(o, query(2, [(0, 2, 0)]), cap=0).status == 1      # endpoint out of range
+    assert O.match(o, query(2, [(0, 1, 3)]), cap=0).status == 1      # relation out of range
+    assert O.match(o, query(2, [(0, 1, 0)], vbind=[9, UNBOUND]), cap=0).status == 1
+
+
+def test_duplicate_query_edges_and_shared_binding():
+    o = og(complete_digraph(5))
+    a = O.match(o, query(3, [(0, 1, 0), (1, 2, 0)]), cap=0).count
+    b = O.match(o, query(3, [(0, 1, 0), (1, 2, 0), (0, 1, 0)]), cap=0).count
+    assert a == b == perm(5, 3)
+    assert O.match(o, query(2, [(0, 1, 0)], vbind=[2, 2]), cap=0).count == 0  # injectivity
