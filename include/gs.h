@@ -1,0 +1,218 @@
+/*
+ * gs.h — C ABI of the GB300 engine for exact labeled subgraph matching
+ * (the filtering-and-joining method of thesis arXiv:1807.08804, Ch. 3,
+ * Algorithm "FilteringAndJoining").
+ *
+ * What a match is (Definition 3.2, read for directed graphs whose edges carry
+ * relation labels, Section 3.2 "Commonsense Graph Transformation"): given a
+ * data graph G = (V, E subset of V x R x V, type: V -> [0,T)) and a query with
+ * k vertices and m directed labeled edges, an embedding is an injective map
+ * f: [0,k) -> V such that
+ *   - a bound query vertex i (a "concept node", Section 3.2) has f(i) = vbind[i];
+ *   - a typed query vertex i has type(f(i)) = vtype[i] (GS_ANY: no constraint);
+ *   - every query edge (i -> j, r) has (f(i), r, f(j)) in E.
+ * The engine returns every embedding: the exact count always, plus the
+ * lexicographically smallest `cap` embeddings written in query-vertex order.
+ *
+ * Conventions for every call:
+ *   - Return value: a gs_status.  On failure nothing is returned through the
+ *     output arguments and gs_last_error() holds a message for this thread.
+ *   - Pointers are host pointers unless a flag says they are device pointers.
+ *   - The library copies every input; the caller keeps ownership of its arrays.
+ *   - Memory the library returns (gs_result.rows) is freed with gs_result_free.
+ *   - All ids are uint32.  Limits: V < 2^24, num_rels <= 255, num_types <= 255,
+ *     1 <= k <= 16, m <= 120 edges per query.
+ *   - Work runs on the CUDA device that is current when gs_graph_load is
+ *     called; later calls on that graph must run with the same device current.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID = 1,      /* bad argument or query; nothing was done */
+  GS_ERR_OOM = 2,          /* device or host allocation failed */
+  GS_ERR_CUDA = 3,         /* a CUDA call failed; see gs_last_error() */
+  GS_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+  GS_ERR_UNSUPPORTED = 5,  /* valid but outside this build (e.g. disconnected query) */
+  GS_ERR_BUSY = 6,         /* serving queue full; retry later */
+  GS_ERR_NOT_READY = 7     /* serving result not finished yet */
+} gs_status;
+
+#define GS_UNBOUND 0xFFFFFFFFu  /* vbind[i]: variable vertex (no binding) */
+#define GS_ANY 0xFFFFFFFFu      /* vtype[i]: no type constraint */
+
+/* gs_graph_desc.flags */
+#define GS_DEVICE_PTRS 1u       /* the arrays are device pointers (read on cuda_stream) */
+
+/*
+ * A data graph as an out-CSR (Section 3.3.1: "nodes array" of start offsets
+ * and "edges array" of neighbours, plus label arrays of length |V| and |E|).
+ * Rows may be in any order and may repeat a (src, rel, dst) triple; the
+ * library sorts each row by (relation, neighbour), drops repeats and builds
+ * the incoming CSR as well (Section 3.5, "incoming and outgoing graph
+ * representations").
+ */
+typedef struct {
+  uint32_t num_vertices;        /* V */
+  uint64_t num_edges;           /* E = row_offsets[V] */
+  const uint64_t *row_offsets;  /* [V+1], non-decreasing, row_offsets[0] = 0 */
+  const uint32_t *col_targets;  /* [E], each < V, no self-loops required (they never match) */
+  const uint32_t *edge_rel;     /* [E], each < num_rels */
+  const uint32_t *vertex_type;  /* [V], each < num_types */
+  uint32_t num_types, num_rels;
+  uint32_t flags;               /* GS_DEVICE_PTRS or 0 */
+  void *cuda_stream;            /* cudaStream_t for device inputs; NULL = default stream */
+} gs_graph_desc;
+
+typedef struct gs_graph gs_graph;
+
+/* Canonicalise and upload a graph (untimed setup; a few device sorts).
+ * Errors: GS_ERR_INVALID (sizes, ids, labels out of range), GS_ERR_OOM,
+ * GS_ERR_CUDA.  *out is owned by the caller; free it with gs_graph_free. */
+gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out);
+void gs_graph_free(gs_graph *g);
+/* Distinct (src, rel, dst) triples after canonicalisation. */
+uint64_t gs_graph_num_edges(const gs_graph *g);
+
+/*
+ * A query graph (Section 3.2: concept nodes, variable nodes, labeled edges).
+ * Edges are directed esrc[j] -> edst[j] with relation erel[j].  Repeated
+ * edges are dropped.  Errors: k = 0 or k > 16, m > 120, an endpoint >= k, a
+ * self-loop, a type/relation/binding out of range -> GS_ERR_INVALID; a
+ * disconnected query -> GS_ERR_UNSUPPORTED.  Host pointers.
+ */
+typedef struct {
+  uint32_t k, m;
+  const uint32_t *vtype;  /* [k], < num_types or GS_ANY */
+  const uint32_t *vbind;  /* [k], < V or GS_UNBOUND */
+  const uint32_t *esrc;   /* [m] */
+  const uint32_t *edst;   /* [m] */
+  const uint32_t *erel;   /* [m], < num_rels */
+} gs_query;
+
+/* gs_match_opts.mode */
+#define GS_ENUMERATE 0u    /* count + fingerprint + smallest `cap` rows */
+#define GS_COUNT_ONLY 1u   /* count + fingerprint, no rows */
+
+typedef struct {
+  uint64_t cap;               /* rows to return (0 = none); the count is always exact */
+  uint32_t mode;              /* GS_ENUMERATE or GS_COUNT_ONLY */
+  uint32_t max_refine_rounds; /* 0 = refine until nothing changes (Section 3.3.3) */
+  uint64_t chunk_bytes;       /* partial-embedding budget per join level before the
+                                 join switches to chunked depth-first expansion;
+                                 0 = library default (1 GiB) */
+  void *cuda_stream;          /* cudaStream_t; NULL = the library's own stream */
+} gs_match_opts;
+
+typedef struct {
+  uint64_t count;        /* exact number of embeddings */
+  uint64_t num_rows;     /* rows returned = min(count, cap) */
+  uint64_t fingerprint;  /* sum over ALL embeddings of an order-free 64-bit row hash */
+  uint32_t k;            /* row width */
+  uint32_t truncated;    /* 1 if count > cap */
+  uint32_t *rows;        /* [num_rows * k] row-major, query-vertex order, ascending; owned */
+  uint32_t status;       /* gs_status of this query (batch calls) */
+  uint32_t reserved;
+} gs_result;
+
+/* Match one query (a batch of one).  Blocks until the result is on the host. */
+gs_status gs_match(gs_graph *g, const gs_query *q, const gs_match_opts *opts, gs_result *out);
+
+/* Match n queries as one batch: every phase runs once for all of them.
+ * outs[n] receive per-query results (outs[i].status says whether query i was
+ * valid).  Returns GS_OK unless the call itself failed. */
+gs_status gs_match_batch(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
+                         gs_result *outs);
+
+void gs_result_free(gs_result *r);
+const char *gs_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Prepared batches: the queries are validated, packed and uploaded once; each
+ * gs_batch_run then executes the whole device pipeline (plan, filter,
+ * refinement, edge tables, join, sort) from device-resident inputs, replaying
+ * a captured CUDA graph.  Results stay in device memory until gs_batch_fetch.
+ * ------------------------------------------------------------------------ */
+typedef struct gs_batch gs_batch;
+gs_status gs_batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
+                          gs_batch **out);
+/* Enqueue one run on the batch's stream (asynchronous). */
+gs_status gs_batch_run(gs_batch *b);
+/* Wait for the last run, finish queries that overflowed the device budgets
+ * (chunked join on the host-driven path), and make results fetchable. */
+gs_status gs_batch_finish(gs_batch *b);
+/* Copy results of the last finished run to the host (outs[n]). */
+gs_status gs_batch_fetch(gs_batch *b, gs_result *outs);
+void gs_batch_destroy(gs_batch *b);
+
+/* Per-kernel statistics accumulated by runs since the last reset:
+ * launches, device time (CUDA events) and algorithmic bytes.  Timing is
+ * recorded only while enabled (adds events around each launch). */
+#define GS_NUM_KERNEL_KINDS 16
+typedef struct {
+  const char *name[GS_NUM_KERNEL_KINDS];
+  uint64_t launches[GS_NUM_KERNEL_KINDS];
+  double ms[GS_NUM_KERNEL_KINDS];
+  uint64_t bytes[GS_NUM_KERNEL_KINDS];
+} gs_kernel_stats;
+gs_status gs_stats_enable(gs_batch *b, int on);
+gs_status gs_stats_get(gs_batch *b, gs_kernel_stats *out);
+gs_status gs_stats_reset(gs_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Inspection of the filtering phase and the candidate-edge tables of one
+ * query, for per-kernel parity checks.
+ * ------------------------------------------------------------------------ */
+#define GS_STAGE_FILTER 0u    /* C0(u): binding, type, per-(direction, relation) degree */
+#define GS_STAGE_FIXPOINT 1u  /* after exploration and refinement to a fixpoint */
+
+/* Candidate sets of query q at `stage` as sorted lists: for query vertex u,
+ * ids[off[u] .. off[u+1]) ascending.  off has k+1 entries; ids has room for
+ * `cap_ids`; *n_ids receives the total (GS_ERR_INVALID if cap_ids is too
+ * small; ids may be NULL to ask for the size).  Host pointers. */
+gs_status gs_inspect_candidates(gs_graph *g, const gs_query *q, uint32_t stage, uint64_t *off,
+                                uint32_t *ids, uint64_t cap_ids, uint64_t *n_ids);
+
+/* Candidate-edge table of query edge e after the fixpoint (Section 3.3.4),
+ * oriented from esrc[e] (from_src = 1: keys = C(esrc), lists of out-neighbours
+ * in C(edst)) or from edst[e] (from_src = 0: keys = C(edst), lists of
+ * in-neighbours in C(esrc)).  keys[nkeys], off[nkeys+1], vals[off[nkeys]].
+ * With keys == NULL only *nkeys and *nvals are written. */
+gs_status gs_inspect_edge_table(gs_graph *g, const gs_query *q, uint32_t e, uint32_t from_src, uint32_t *keys,
+                                uint64_t *off, uint32_t *vals, uint64_t cap_keys, uint64_t cap_vals,
+                                uint64_t *nkeys, uint64_t *nvals);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop that keeps the graph device-resident and admits
+ * queries while slots and the working-set budget allow (continuous batching:
+ * requests that arrive while others run are admitted as slots free up).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint64_t budget_bytes;  /* working-set budget for admitted queries (0 = 40 GB) */
+  uint32_t slots;         /* concurrent micro-batches in flight (0 = 4) */
+  uint32_t max_batch;     /* queries per micro-batch (0 = 256) */
+  uint32_t queue_depth;   /* pending requests before submit says GS_ERR_BUSY (0 = 65536) */
+  uint32_t reserved;
+} gs_serve_opts;
+
+typedef struct gs_server gs_server;
+gs_status gs_serve_create(gs_graph *g, const gs_serve_opts *opts, gs_server **out);
+/* Queue one query; *ticket identifies it.  The query is copied. */
+gs_status gs_serve_submit(gs_server *s, const gs_query *q, const gs_match_opts *opts, uint64_t *ticket);
+/* Non-blocking: GS_ERR_NOT_READY until the result is done; then fills *out
+ * (free with gs_result_free) and forgets the ticket.  *latency_s (may be NULL)
+ * receives submit-to-completion time in seconds. */
+gs_status gs_serve_poll(gs_server *s, uint64_t ticket, gs_result *out, double *latency_s);
+gs_status gs_serve_destroy(gs_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H_ */

@@ -1,0 +1,308 @@
+"""GB300 engine for exact labeled subgraph matching (thesis arXiv:1807.08804,
+Ch. 3, the filtering-and-joining method).
+
+This module is a thin ctypes binding over the C ABI in `include/gs.h`
+(`libgs.so`, built by `build.py`).  It only marshals arguments: every step of
+the matching runs in the library's CUDA kernels.  There is no CPU fallback: if
+the library or a CUDA device is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (seeded input generators)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgs.so")
+
+GS_OK, GS_ERR_INVALID, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED, GS_ERR_BUSY, GS_ERR_NOT_READY = range(8)
+STATUS_NAMES = ["OK", "INVALID", "OOM", "CUDA", "TIMEOUT", "UNSUPPORTED", "BUSY", "NOT_READY"]
+UNBOUND = 0xFFFFFFFF
+ANY = 0xFFFFFFFF
+GS_DEVICE_PTRS = 1
+GS_ENUMERATE, GS_COUNT_ONLY = 0, 1
+GS_STAGE_FILTER, GS_STAGE_FIXPOINT = 0, 1
+NUM_KERNEL_KINDS = 16
+
+
+class GSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+P = ctypes.c_void_p
+U32, U64 = ctypes.c_uint32, ctypes.c_uint64
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("num_vertices", U32), ("num_edges", U64), ("row_offsets", P), ("col_targets", P),
+                ("edge_rel", P), ("vertex_type", P), ("num_types", U32), ("num_rels", U32), ("flags", U32),
+                ("cuda_stream", P)]
+
+
+class QueryDesc(ctypes.Structure):
+    _fields_ = [("k", U32), ("m", U32), ("vtype", P), ("vbind", P), ("esrc", P), ("edst", P), ("erel", P)]
+
+
+class MatchOpts(ctypes.Structure):
+    _fields_ = [("cap", U64), ("mode", U32), ("max_refine_rounds", U32), ("chunk_bytes", U64), ("cuda_stream", P)]
+
+
+class ResultDesc(ctypes.Structure):
+    _fields_ = [("count", U64), ("num_rows", U64), ("fingerprint", U64), ("k", U32), ("truncated", U32),
+                ("rows", ctypes.POINTER(U32)), ("status", U32), ("reserved", U32)]
+
+
+class KernelStats(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p * NUM_KERNEL_KINDS), ("launches", U64 * NUM_KERNEL_KINDS),
+                ("ms", ctypes.c_double * NUM_KERNEL_KINDS), ("bytes", U64 * NUM_KERNEL_KINDS)]
+
+
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("budget_bytes", U64), ("slots", U32), ("max_batch", U32), ("queue_depth", U32), ("reserved", U32)]
+
+
+# Every entry point of include/gs.h with its argument types.
+SIGNATURES = {
+    "gs_graph_load": (ctypes.c_int, [ctypes.POINTER(GraphDesc), ctypes.POINTER(P)]),
+    "gs_graph_free": (None, [P]),
+    "gs_graph_num_edges": (U64, [P]),
+    "gs_match": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), ctypes.POINTER(MatchOpts), ctypes.POINTER(ResultDesc)]),
+    "gs_match_batch": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts),
+                                      ctypes.POINTER(ResultDesc)]),
+    "gs_result_free": (None, [ctypes.POINTER(ResultDesc)]),
+    "gs_last_error": (ctypes.c_char_p, []),
+    "gs_batch_create": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts), ctypes.POINTER(P)]),
+    "gs_batch_run": (ctypes.c_int, [P]),
+    "gs_batch_finish": (ctypes.c_int, [P]),
+    "gs_batch_fetch": (ctypes.c_int, [P, ctypes.POINTER(ResultDesc)]),
+    "gs_batch_destroy": (None, [P]),
+    "gs_stats_enable": (ctypes.c_int, [P, ctypes.c_int]),
+    "gs_stats_get": (ctypes.c_int, [P, ctypes.POINTER(KernelStats)]),
+    "gs_stats_reset": (ctypes.c_int, [P]),
+    "gs_inspect_candidates": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, P, P, U64, ctypes.POINTER(U64)]),
+    "gs_inspect_edge_table": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, U32, P, P, P, U64, U64,
+                                             ctypes.POINTER(U64), ctypes.POINTER(U64)]),
+    "gs_serve_create": (ctypes.c_int, [P, ctypes.POINTER(ServeOpts), ctypes.POINTER(P)]),
+    "gs_serve_submit": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), ctypes.POINTER(MatchOpts), ctypes.POINTER(U64)]),
+    "gs_serve_poll": (ctypes.c_int, [P, U64, ctypes.POINTER(ResultDesc), ctypes.POINTER(ctypes.c_double)]),
+    "gs_serve_destroy": (ctypes.c_int, [P]),
+}
+# Entry points beyond include/gs.h's core list, used by tests and the benchmark.
+EXTRA_SIGNATURES = {
+    "gs_batch_create_waves": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts), U32,
+                                             ctypes.POINTER(P)]),
+    "gs_batch_set": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, U32]),
+}
+
+_lib = None
+
+
+def build(verbose: bool = False) -> str:
+    from .buildlib import build as _build
+    return _build(verbose=verbose)
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded engine library.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise GSError(GS_ERR_UNSUPPORTED, f"{LIB_PATH} is missing; run paper_1807_08804_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in {**SIGNATURES, **EXTRA_SIGNATURES}.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != GS_OK:
+        raise GSError(st, lib().gs_last_error().decode(errors="replace"))
+
+
+def _u32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(P)
+
+
+class _QueryPack:
+    """Queries as a ctypes array; keeps the numpy buffers alive."""
+
+    def __init__(self, queries):
+        self.keep = []
+        self.arr = (QueryDesc * max(len(queries), 1))()
+        for i, q in enumerate(queries):
+            a = [_u32(q.vtype), _u32(q.vbind), _u32(q.esrc), _u32(q.edst), _u32(q.erel)]
+            self.keep.append(a)
+            self.arr[i] = QueryDesc(a[0].shape[0], a[2].shape[0], *[_ptr(x) for x in a])
+
+
+def _opts(cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0, stream=None) -> MatchOpts:
+    return MatchOpts(cap, mode, max_refine_rounds, chunk_bytes, stream)
+
+
+@dataclass
+class MatchResult:
+    count: int
+    fingerprint: int
+    rows: np.ndarray      # uint32 [num_rows, k], query-vertex order, ascending
+    truncated: bool
+    status: int
+
+
+def _take(r: ResultDesc) -> MatchResult:
+    n, k = int(r.num_rows), int(r.k)
+    rows = np.zeros((n, k), np.uint32)
+    if n:
+        rows[:] = np.ctypeslib.as_array(r.rows, shape=(n * k,)).reshape(n, k)
+    out = MatchResult(int(r.count), int(r.fingerprint), rows, bool(r.truncated), int(r.status))
+    lib().gs_result_free(ctypes.byref(r))
+    return out
+
+
+class DeviceGraph:
+    """A data graph canonicalised and resident on the current CUDA device."""
+
+    def __init__(self, g=None, *, num_vertices=None, num_edges=None, row_offsets=None, col_targets=None, edge_rel=None,
+                 vertex_type=None, num_types=None, num_rels=None, device_ptrs=False, stream=None):
+        if g is not None:
+            num_vertices, row_offsets, col_targets = g.num_vertices, g.row_offsets, g.col_targets
+            edge_rel, vertex_type, num_types, num_rels = g.edge_rel, g.vertex_type, g.num_types, g.num_rels
+        self._h = P()
+        if device_ptrs:  # device addresses (e.g. tensor.data_ptr()) and an explicit edge count
+            d = GraphDesc(int(num_vertices), int(num_edges), row_offsets, col_targets, edge_rel, vertex_type,
+                          int(num_types), int(num_rels), GS_DEVICE_PTRS, stream)
+            keep = ()
+        else:
+            ro = np.ascontiguousarray(np.asarray(row_offsets, dtype=np.uint64))
+            keep = (ro, _u32(col_targets), _u32(edge_rel), _u32(vertex_type))
+            d = GraphDesc(int(num_vertices), int(ro[-1]), *[_ptr(x) for x in keep], int(num_types), int(num_rels),
+                          0, stream)
+        _check(lib().gs_graph_load(ctypes.byref(d), ctypes.byref(self._h)))
+        del keep
+        self.num_vertices = int(num_vertices)
+
+    @property
+    def num_edges(self) -> int:
+        return int(lib().gs_graph_num_edges(self._h))
+
+    def free(self):
+        if self._h:
+            lib().gs_graph_free(self._h)
+            self._h = P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def match(dg: DeviceGraph, q, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0) -> MatchResult:
+    pack = _QueryPack([q])
+    o = _opts(cap, mode, max_refine_rounds, chunk_bytes)
+    r = ResultDesc()
+    _check(lib().gs_match(dg._h, pack.arr, ctypes.byref(o), ctypes.byref(r)))
+    return _take(r)
+
+
+def match_batch(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0,
+                chunk_bytes=0) -> list[MatchResult]:
+    pack = _QueryPack(queries)
+    o = _opts(cap, mode, max_refine_rounds, chunk_bytes)
+    res = (ResultDesc * max(len(queries), 1))()
+    _check(lib().gs_match_batch(dg._h, pack.arr, len(queries), ctypes.byref(o), res))
+    return [_take(res[i]) for i in range(len(queries))]
+
+
+class Batch:
+    """A prepared batch (device-resident queries, captured pipeline graph)."""
+
+    def __init__(self, dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0,
+                 wave_queries=0, stream=None):
+        self.dg = dg
+        self.n = len(queries)
+        self._pack = _QueryPack(queries)
+        o = _opts(cap, mode, max_refine_rounds, chunk_bytes, stream)
+        self._h = P()
+        if wave_queries:
+            _check(lib().gs_batch_create_waves(dg._h, self._pack.arr, self.n, ctypes.byref(o), wave_queries,
+                                               ctypes.byref(self._h)))
+        else:
+            _check(lib().gs_batch_create(dg._h, self._pack.arr, self.n, ctypes.byref(o), ctypes.byref(self._h)))
+
+    def configure(self, use_graph=True, group=32, refine_rounds=0):
+        _check(lib().gs_batch_set(self._h, 1 if use_graph else 0, group, refine_rounds))
+
+    def run(self):
+        _check(lib().gs_batch_run(self._h))
+
+    def finish(self):
+        _check(lib().gs_batch_finish(self._h))
+
+    def fetch(self) -> list[MatchResult]:
+        res = (ResultDesc * max(self.n, 1))()
+        _check(lib().gs_batch_fetch(self._h, res))
+        return [_take(res[i]) for i in range(self.n)]
+
+    def stats_enable(self, on=True):
+        _check(lib().gs_stats_enable(self._h, 1 if on else 0))
+
+    def stats_reset(self):
+        _check(lib().gs_stats_reset(self._h))
+
+    def stats(self) -> dict:
+        s = KernelStats()
+        _check(lib().gs_stats_get(self._h, ctypes.byref(s)))
+        out = {}
+        for i in range(NUM_KERNEL_KINDS):
+            name = s.name[i].decode() if s.name[i] else ""
+            if name:
+                out[name] = {"launches": int(s.launches[i]), "ms": float(s.ms[i]), "bytes": int(s.bytes[i])}
+        return out
+
+    def close(self):
+        if self._h:
+            lib().gs_batch_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def inspect_candidates(dg: DeviceGraph, q, stage=GS_STAGE_FIXPOINT) -> list[np.ndarray]:
+    pack = _QueryPack([q])
+    k = len(q.vtype)
+    off = np.zeros(k + 1, np.uint64)
+    n = U64()
+    _check(lib().gs_inspect_candidates(dg._h, pack.arr, stage, _ptr(off), None, 0, ctypes.byref(n)))
+    ids = np.zeros(max(n.value, 1), np.uint32)
+    _check(lib().gs_inspect_candidates(dg._h, pack.arr, stage, _ptr(off), _ptr(ids), ids.shape[0], ctypes.byref(n)))
+    return [ids[int(off[u]):int(off[u + 1])].copy() for u in range(k)]
+
+
+def inspect_edge_table(dg: DeviceGraph, q, e: int, from_src: bool):
+    pack = _QueryPack([q])
+    nk, nv = U64(), U64()
+    _check(lib().gs_inspect_edge_table(dg._h, pack.arr, e, 1 if from_src else 0, None, None, None, 0, 0,
+                                       ctypes.byref(nk), ctypes.byref(nv)))
+    keys = np.zeros(max(nk.value, 1), np.uint32)
+    off = np.zeros(nk.value + 1, np.uint64)
+    vals = np.zeros(max(nv.value, 1), np.uint32)
+    _check(lib().gs_inspect_edge_table(dg._h, pack.arr, e, 1 if from_src else 0, _ptr(keys), _ptr(off), _ptr(vals),
+                                       keys.shape[0], vals.shape[0], ctypes.byref(nk), ctypes.byref(nv)))
+    return keys[: nk.value], off, vals[: nv.value]

@@ -1,0 +1,175 @@
+// Engine-internal device structures shared by the kernels and the host
+// orchestration.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace cg = cooperative_groups;
+
+constexpr uint32_t kUnbound = 0xFFFFFFFFu;
+constexpr uint32_t kAny = 0xFFFFFFFFu;
+constexpr uint32_t kMaxRounds = 64;
+
+// Per-query status.
+enum : uint32_t {
+  QS_OK = 0,        // running / finished normally
+  QS_EMPTY = 1,     // some candidate set is empty: no embedding
+  QS_OVERFLOW = 2,  // a device pool was too small: finish on the fallback path
+  QS_INVALID = 3,   // empty slot (padding) or rejected by the host checks
+  QS_TOPCAP = 4,    // more embeddings than cap: smallest rows via the fallback path
+};
+
+// Kernel kinds for statistics.
+enum : int {
+  KK_PLAN = 0, KK_FILTER, KK_COMPACT, KK_EXPLORE, KK_REFINE, KK_EC_COUNT, KK_EC_WRITE, KK_CLEAR,
+  KK_JOIN_COUNT, KK_JOIN_WRITE, KK_SCAN, KK_SORT, KK_GATHER, KK_OTHER, KK_N
+};
+
+// One query as the device sees it.  The host fills the query part (edges
+// without repeats, incidence lists, degree needs); the device fills the plan.
+struct DQuery {
+  uint32_t k, m;
+  uint32_t qv_base;                 // slot index of query vertex 0
+  uint32_t qe_base;                 // slot index of query edge 0
+  uint32_t vtype[kMaxK];            // type or kAny
+  uint32_t vbind[kMaxK];            // data id or kUnbound
+  uint8_t esrc[kMaxM], edst[kMaxM], erel[kMaxM];
+  uint8_t inc_begin[kMaxK + 1];     // incident edges of u: inc_edge[inc_begin[u] .. inc_begin[u+1])
+  uint8_t inc_edge[2 * kMaxM];
+  uint8_t need_begin[kMaxK + 1];    // degree needs of u: (plane, count) pairs
+  uint16_t need_plane[2 * kMaxM];   // dir * R + rel
+  uint8_t need_cnt[2 * kMaxM];
+  uint32_t mode;
+  uint64_t cap;
+  uint8_t force_root;               // 0xFF, or the first visited vertex (inspection runs)
+  uint8_t force_from_src;           // 0xFF, or a fixed edge-table orientation (inspection runs)
+  // plan (device)
+  uint32_t nvisit;
+  uint8_t visit[kMaxK];
+  uint8_t parent[kMaxK];            // spanning-tree parent (0xFF at the root)
+  uint8_t pedge[kMaxK];             // tree edge to the parent
+  uint8_t init_step[kMaxK];         // exploration step after which u has a candidate set
+  uint8_t join[kMaxK];              // join order
+  uint8_t pos[kMaxK];               // position of u in the join order
+  uint8_t from_src[kMaxM];          // edge-table orientation (1: keyed by esrc)
+  uint32_t status;
+};
+
+// Per-query join bookkeeping and results (slot arrays).
+struct QState {
+  uint64_t count, fp;
+  uint64_t cur_row_base, cur_rows, cur_word_base;   // rows of the current level
+  uint64_t nxt_rows;                                 // rows produced for the next level
+  uint64_t out_row_base, out_rows, out_word_base;   // final rows in the output pool
+  uint64_t fin_row_base, fin_word_base;             // sorted rows in query order
+};
+
+// Rows of level s kept aside while the allocator lays out level s+1.
+struct SrcRows {
+  uint64_t row_base, rows, word_base;
+};
+
+// One wave of a batch, as listed in the batch's wave table.
+struct WaveDesc {
+  uint32_t q0, nq;        // batch query range
+  uint32_t qv0, nqv;      // batch query-vertex range
+  uint32_t qe0, nqe;      // batch query-edge range
+};
+
+// Batch-level results written by the epilogue of each wave.
+struct BatchOut {
+  uint64_t *count, *fp, *nrows, *word_off;  // [n]
+  uint32_t *status;                          // [n]
+  uint32_t *store;                           // rows of every query, query-vertex order
+  uint64_t store_cap;                        // words
+};
+
+struct Ctrl {
+  uint64_t len[8];                  // device-side lengths read by persistent kernels
+  uint32_t changed[kMaxRounds];     // refinement: did round t clear any bit
+  uint64_t lvl_top, out_top;        // output pool top (words)
+  uint64_t out_rows_total;
+  uint64_t store_top;               // batch row store top (words)
+  uint32_t wave;                    // index of the wave being run
+  uint32_t err;
+  uint64_t bytes[KK_N];             // algorithmic bytes per kernel kind
+};
+
+// Everything a kernel needs, passed by value.  Capacities are fixed when the
+// batch is created; the number of live queries of the wave is implicit
+// (padding slots are QS_INVALID).
+struct Wave {
+  DevGraph G;
+  DQuery *dq;                       // slot queries [nq + 1]; dq[nq] is a permanent empty slot
+  QState *qs;                       // [nq]
+  Ctrl *ctrl;
+  uint32_t nq, nqv, nqe;            // slot capacities
+  uint32_t *qv_q;                   // slot query of each slot query vertex [nqv]
+  uint32_t *qe_q;                   // slot query of each slot query edge [nqe]
+  // source of the wave descriptors
+  const DQuery *all_dq;             // batch queries [n]
+  const WaveDesc *waves;
+  BatchOut bo;
+  // candidate bitmaps
+  uint32_t *bm;                     // [nqv][slot_words]
+  uint64_t slot_words;
+  // compaction
+  uint32_t *ccount;                 // [nqv * ipg]
+  uint64_t *cscan;                  // [nqv * ipg + 1]
+  uint64_t *ascan;                  // [nqv * ipg + 1] (refinement items)
+  // candidate lists
+  uint32_t *tlist; uint64_t tlist_cap;   // exploration work list
+  uint32_t *alist; uint64_t alist_cap;   // every set before refinement
+  uint32_t *flist; uint64_t flist_cap;   // final sets
+  uint64_t *flist_off;              // [nqv]
+  uint32_t *flist_len;              // [nqv]
+  // edge tables
+  uint32_t *ec_nkeys;               // [nqe]
+  uint64_t *ec_key_base;            // [nqe + 1]
+  uint32_t *ec_cnt; uint64_t ec_items_cap;
+  uint64_t *ec_off;                 // [ec_items_cap + 1]
+  uint32_t *ec_vals; uint64_t ec_vals_cap;
+  // join levels
+  uint32_t *lvl[2]; uint64_t lvl_words;
+  uint32_t *row_cnt; uint64_t row_cap;
+  uint64_t *row_scan;               // [row_cap + 1]
+  SrcRows *src;                     // [nq]
+  uint32_t *out; uint64_t out_words;  // final rows, join-order columns
+  uint32_t *out_q;                  // slot query of each output row
+  uint64_t out_rows_cap;
+  uint32_t *out_final;              // sorted rows, query-vertex order
+  // sort
+  uint32_t *skey[2], *sval[2];
+  int stats;
+};
+
+// ------------------------------------------------------------ launchers
+void launch_prologue(const Wave &W, cudaStream_t s, int sms);
+void launch_plan(const Wave &W, const uint32_t *type_count, cudaStream_t s, int sms);
+void launch_filter(const Wave &W, cudaStream_t s, int sms);
+void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms);
+void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint64_t cap,
+                          cudaStream_t s, int sms);
+void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms);
+void launch_refine(const Wave &W, uint32_t round, int group, cudaStream_t s, int sms);
+void launch_list_table(const Wave &W, cudaStream_t s, int sms);
+void launch_join_plan(const Wave &W, cudaStream_t s, int sms);
+void launch_ec_limit(const Wave &W, cudaStream_t s, int sms);
+void launch_ec(const Wave &W, bool write, int group, cudaStream_t s, int sms);
+void launch_clear(const Wave &W, cudaStream_t s, int sms);
+void launch_join0(const Wave &W, cudaStream_t s, int sms);
+void launch_join_count(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms);
+void launch_join_totals(const Wave &W, cudaStream_t s, int sms);
+void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s);
+void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms);
+void launch_final_bases(const Wave &W, cudaStream_t s);
+void launch_iota(const Wave &W, uint32_t *perm, cudaStream_t s, int sms);
+void launch_sort_keys(const Wave &W, const uint32_t *perm, uint32_t *key, uint32_t col, cudaStream_t s, int sms);
+void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms);
+void launch_epilogue(const Wave &W, cudaStream_t s, int sms);
+
+}  // namespace gs

@@ -1,0 +1,331 @@
+// Data-graph storage (Section 3.3.1: a "nodes array" of row offsets and an
+// "edges array" of neighbours, plus node- and edge-label arrays) built in
+// both directions (Section 3.5: "incoming and outgoing graph
+// representations"), canonicalised on the device:
+//   - each row sorted by (relation, neighbour) and packed rel << 24 | nbr, so
+//     a relation's neighbours form one ascending run found by binary search;
+//   - repeated (src, rel, dst) triples dropped;
+//   - per-vertex, per-(direction, relation) distinct-neighbour counts kept
+//     as 4-bit signatures for the candidate test (Definition 3.3's degree
+//     condition, read per direction and relation).
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+static thread_local std::string t_last_error;
+
+void set_error(const std::string &msg) { t_last_error = msg; }
+gs_status fail(gs_status st, const std::string &msg) {
+  set_error(msg);
+  return st;
+}
+gs_status cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
+}
+
+namespace {
+
+constexpr int kT = 256;
+
+inline unsigned blocks_for(uint64_t n, int per = kT, unsigned cap = 1u << 20) {
+  uint64_t b = (n + per - 1) / per;
+  if (b == 0) b = 1;
+  return (unsigned)(b < cap ? b : cap);
+}
+
+// Validation: bit 0 offsets, bit 1 target, bit 2 relation, bit 3 type.
+__global__ void k_validate(uint32_t V, uint64_t E, const uint64_t *ro, const uint32_t *col, const uint32_t *rel,
+                           const uint32_t *vt, uint32_t T, uint32_t R, uint32_t *err) {
+  uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = tid; v < V; v += stride) {
+    if (ro[v] > ro[v + 1]) atomicOr(err, 1u);
+    if (vt[v] >= T) atomicOr(err, 8u);
+  }
+  if (tid == 0 && (ro[0] != 0 || ro[V] != E)) atomicOr(err, 1u);
+  for (uint64_t e = tid; e < E; e += stride) {
+    if (col[e] >= V) atomicOr(err, 2u);
+    if (rel[e] >= R) atomicOr(err, 4u);
+  }
+}
+
+// Expand rows to triples: key = rel << 24 | dst, val = src.
+__global__ void k_expand(uint32_t V, const uint64_t *ro, const uint32_t *col, const uint32_t *rel, uint32_t *key,
+                         uint32_t *val) {
+  uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = tid; v < V; v += stride)
+    for (uint64_t e = ro[v]; e < ro[v + 1]; ++e) {
+      key[e] = (rel[e] << kNbrBits) | col[e];
+      val[e] = (uint32_t)v;
+    }
+}
+
+// After sorting by (row, packed): keep[i] = first occurrence.
+__global__ void k_mark_first(uint64_t n, const uint32_t *row, const uint32_t *packed, uint32_t *keep) {
+  uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < n; i += stride)
+    keep[i] = (i == 0 || row[i] != row[i - 1] || packed[i] != packed[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_compact_triples(uint64_t n, const uint32_t *row, const uint32_t *packed, const uint32_t *keep,
+                                  const uint64_t *pos, uint32_t *out_row, uint32_t *out_packed) {
+  uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < n; i += stride)
+    if (keep[i]) {
+      out_row[pos[i]] = row[i];
+      out_packed[pos[i]] = packed[i];
+    }
+}
+
+// Row lengths by counting; rows are contiguous after the sort.
+__global__ void k_row_count(uint64_t n, const uint32_t *row, uint32_t *cnt) {
+  uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < n; i += stride) atomicAdd(&cnt[row[i]], 1u);
+}
+
+// Re-key kept triples for the incoming direction: key = rel << 24 | src, val = dst.
+__global__ void k_rekey_in(uint64_t n, const uint32_t *src, const uint32_t *packed, uint32_t *key, uint32_t *val) {
+  uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < n; i += stride) {
+    key[i] = (packed[i] & ~kNbrMask) | src[i];
+    val[i] = packed[i] & kNbrMask;
+  }
+}
+
+// Signatures: one thread per (direction, vertex) walks its sorted row and
+// ORs each relation's saturated count into its plane.
+__global__ void k_signatures(uint32_t V, uint32_t R, const uint64_t *off, const uint32_t *adj, int dir, uint32_t *sig,
+                             uint64_t sig_words) {
+  uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = tid; v < V; v += stride) {
+    uint64_t b = off[v], e = off[v + 1];
+    uint64_t i = b;
+    while (i < e) {
+      uint32_t r = adj[i] >> kNbrBits;
+      uint64_t j = i;
+      while (j < e && (adj[j] >> kNbrBits) == r) ++j;
+      uint32_t c = (uint32_t)((j - i) > 15 ? 15 : (j - i));
+      atomicOr(&sig[(uint64_t)(dir * R + r) * sig_words + (v >> 3)], c << ((v & 7) * 4));
+      i = j;
+    }
+  }
+}
+
+__global__ void k_types(uint32_t V, const uint32_t *vt, uint8_t *out, uint32_t *hist) {
+  uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = tid; v < V; v += stride) {
+    out[v] = (uint8_t)vt[v];
+    atomicAdd(&hist[vt[v]], 1u);
+  }
+}
+
+int bits_for(uint64_t maxval) {
+  int b = 1;
+  while (b < 32 && (maxval >> b)) ++b;
+  return b;
+}
+
+struct DevBuf {
+  void *p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  template <typename T>
+  T *as() const { return static_cast<T *>(p); }
+};
+
+}  // namespace
+
+// Build one direction: given (row, packed) pairs, sort by (row, packed),
+// drop repeats, and produce off[V+1], adj[n'].  Returns kept count.
+static gs_status build_direction(uint32_t V, uint32_t R, uint64_t n, uint32_t *key, uint32_t *val, uint32_t *k1,
+                                 uint32_t *v1, uint64_t *scan_buf, uint64_t *tmp, uint64_t *d_n, cudaStream_t s,
+                                 int sms, uint64_t **off_out, uint32_t **adj_out, uint32_t **row_out, uint64_t *kept) {
+  // (1) by packed key (carry row), (2) stably by row (carry packed)
+  int cur = radix_sort_pairs(key, val, k1, v1, d_n, n, 0, kNbrBits + bits_for(R ? R - 1 : 0), tmp, s, sms);
+  uint32_t *pk = cur ? k1 : key, *rw = cur ? v1 : val;
+  uint32_t *pk_alt = cur ? key : k1, *rw_alt = cur ? val : v1;
+  cur = radix_sort_pairs(rw, pk, rw_alt, pk_alt, d_n, n, 0, bits_for(V ? V - 1 : 0), tmp, s, sms);
+  uint32_t *row = cur ? rw_alt : rw, *packed = cur ? pk_alt : pk;
+  uint32_t *frow = cur ? rw : rw_alt, *fpacked = cur ? pk : pk_alt;  // free buffers
+  // de-duplicate
+  uint32_t *keep = frow;  // reuse as flags
+  k_mark_first<<<blocks_for(n), kT, 0, s>>>(n, row, packed, keep);
+  scan_u32(keep, scan_buf, d_n, n, tmp, s, sms);
+  uint64_t total = 0;
+  GS_CUDA(cudaMemcpyAsync(&total, scan_buf + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  uint32_t *adj = nullptr, *crow = nullptr;
+  GS_CUDA(cudaMalloc(&adj, sizeof(uint32_t) * (total ? total : 1)));
+  GS_CUDA(cudaMalloc(&crow, sizeof(uint32_t) * (total ? total : 1)));
+  k_compact_triples<<<blocks_for(n), kT, 0, s>>>(n, row, packed, keep, scan_buf, crow, adj);
+  (void)fpacked;
+  // offsets
+  uint32_t *cnt = frow;  // keep flags no longer needed after compaction
+  GS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (V + 1), s));
+  k_row_count<<<blocks_for(total), kT, 0, s>>>(total, crow, cnt);
+  uint64_t *off = nullptr;
+  GS_CUDA(cudaMalloc(&off, sizeof(uint64_t) * (V + 1)));
+  uint64_t nv = V;
+  GS_CUDA(cudaMemcpyAsync(d_n, &nv, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  scan_u32(cnt, off, d_n, V, tmp, s, sms);
+  GS_CUDA(cudaStreamSynchronize(s));
+  GS_CUDA(cudaMemcpyAsync(d_n, &n, sizeof(uint64_t), cudaMemcpyHostToDevice, s));  // restore
+  *off_out = off;
+  *adj_out = adj;
+  *row_out = crow;
+  *kept = total;
+  return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
+  if (!desc || !out) return fail(GS_ERR_INVALID, "gs_graph_load: null argument");
+  *out = nullptr;
+  const uint32_t V = desc->num_vertices;
+  const uint64_t E = desc->num_edges;
+  if (V == 0 || V > (1u << kNbrBits)) return fail(GS_ERR_INVALID, "num_vertices must be in [1, 2^24]");
+  if (desc->num_types == 0 || desc->num_types > 256) return fail(GS_ERR_INVALID, "num_types must be in [1, 256]");
+  if (desc->num_rels == 0 || desc->num_rels > 255) return fail(GS_ERR_INVALID, "num_rels must be in [1, 255]");
+  if (E >= (1ull << 32)) return fail(GS_ERR_UNSUPPORTED, "num_edges must be < 2^32");
+  if (!desc->row_offsets || !desc->vertex_type || (E && (!desc->col_targets || !desc->edge_rel)))
+    return fail(GS_ERR_INVALID, "gs_graph_load: null array");
+  cudaStream_t s = static_cast<cudaStream_t>(desc->cuda_stream);
+  int dev = 0, sms = 0;
+  GS_CUDA(cudaGetDevice(&dev));
+  GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool on_dev = desc->flags & GS_DEVICE_PTRS;
+  const uint32_t T = desc->num_types, R = desc->num_rels;
+  const uint64_t En = E ? E : 1;
+
+  DevBuf ro, col, rel, vt, k0, v0, k1, v1, scanb, tmpb, dn, err;
+  GS_CUDA(cudaMalloc(&ro.p, sizeof(uint64_t) * (V + 1)));
+  GS_CUDA(cudaMalloc(&col.p, sizeof(uint32_t) * En));
+  GS_CUDA(cudaMalloc(&rel.p, sizeof(uint32_t) * En));
+  GS_CUDA(cudaMalloc(&vt.p, sizeof(uint32_t) * V));
+  cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  GS_CUDA(cudaMemcpyAsync(ro.p, desc->row_offsets, sizeof(uint64_t) * (V + 1), kind, s));
+  if (E) {
+    GS_CUDA(cudaMemcpyAsync(col.p, desc->col_targets, sizeof(uint32_t) * E, kind, s));
+    GS_CUDA(cudaMemcpyAsync(rel.p, desc->edge_rel, sizeof(uint32_t) * E, kind, s));
+  }
+  GS_CUDA(cudaMemcpyAsync(vt.p, desc->vertex_type, sizeof(uint32_t) * V, kind, s));
+  GS_CUDA(cudaMalloc(&err.p, sizeof(uint32_t)));
+  GS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(uint32_t), s));
+  k_validate<<<blocks_for(V > E ? V : E), kT, 0, s>>>(V, E, ro.as<uint64_t>(), col.as<uint32_t>(), rel.as<uint32_t>(),
+                                                       vt.as<uint32_t>(), T, R, err.as<uint32_t>());
+  uint32_t herr = 0;
+  GS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  if (herr & 1) return fail(GS_ERR_INVALID, "row_offsets must start at 0, be non-decreasing and end at num_edges");
+  if (herr & 2) return fail(GS_ERR_INVALID, "col_targets holds an id >= num_vertices");
+  if (herr & 4) return fail(GS_ERR_INVALID, "edge_rel holds a relation >= num_rels");
+  if (herr & 8) return fail(GS_ERR_INVALID, "vertex_type holds a type >= num_types");
+
+  const uint64_t nmax = En > V + 1 ? En : V + 1;
+  GS_CUDA(cudaMalloc(&k0.p, sizeof(uint32_t) * nmax));
+  GS_CUDA(cudaMalloc(&v0.p, sizeof(uint32_t) * nmax));
+  GS_CUDA(cudaMalloc(&k1.p, sizeof(uint32_t) * nmax));
+  GS_CUDA(cudaMalloc(&v1.p, sizeof(uint32_t) * nmax));
+  GS_CUDA(cudaMalloc(&scanb.p, sizeof(uint64_t) * (nmax + 1)));
+  uint64_t tw = radix_tmp_words(nmax);
+  uint64_t sw = scan_tmp_words(nmax);
+  GS_CUDA(cudaMalloc(&tmpb.p, sizeof(uint64_t) * (tw > sw ? tw : sw)));
+  GS_CUDA(cudaMalloc(&dn.p, sizeof(uint64_t)));
+  GS_CUDA(cudaMemcpyAsync(dn.p, &E, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+
+  gs_graph *g = new gs_graph();
+  memset(g, 0, sizeof(*g));
+  g->device = dev;
+  g->num_sms = sms;
+  auto cleanup = [&](gs_status st) {
+    gs_graph_free(g);
+    return st;
+  };
+
+  k_expand<<<blocks_for(V), kT, 0, s>>>(V, ro.as<uint64_t>(), col.as<uint32_t>(), rel.as<uint32_t>(), k0.as<uint32_t>(),
+                                        v0.as<uint32_t>());
+  uint32_t *src_rows = nullptr;
+  uint64_t kept = 0;
+  gs_status st = build_direction(V, R, E, k0.as<uint32_t>(), v0.as<uint32_t>(), k1.as<uint32_t>(), v1.as<uint32_t>(),
+                                 scanb.as<uint64_t>(), tmpb.as<uint64_t>(), dn.as<uint64_t>(), s, sms, &g->off_out,
+                                 &g->adj_out, &src_rows, &kept);
+  if (st != GS_OK) return cleanup(st);
+  // incoming direction from the kept triples
+  GS_CUDA(cudaMemcpyAsync(dn.p, &kept, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  k_rekey_in<<<blocks_for(kept), kT, 0, s>>>(kept, src_rows, g->adj_out, k0.as<uint32_t>(), v0.as<uint32_t>());
+  uint32_t *dst_rows = nullptr;
+  uint64_t kept_in = 0;
+  st = build_direction(V, R, kept, k0.as<uint32_t>(), v0.as<uint32_t>(), k1.as<uint32_t>(), v1.as<uint32_t>(),
+                       scanb.as<uint64_t>(), tmpb.as<uint64_t>(), dn.as<uint64_t>(), s, sms, &g->off_in, &g->adj_in,
+                       &dst_rows, &kept_in);
+  cudaFree(src_rows);
+  cudaFree(dst_rows);
+  if (st != GS_OK) return cleanup(st);
+
+  // Planes hold whole 16-byte groups (32 vertices) so the filter can read
+  // them as aligned uint4 vectors up to the last partial group.
+  const uint64_t sig_words = ((V + 7) / 8 + 3) / 4 * 4;
+  if (cudaMalloc(&g->sig, sizeof(uint32_t) * sig_words * 2 * R) != cudaSuccess)
+    return cleanup(fail(GS_ERR_OOM, "signature planes"));
+  GS_CUDA(cudaMemsetAsync(g->sig, 0, sizeof(uint32_t) * sig_words * 2 * R, s));
+  k_signatures<<<blocks_for(V), kT, 0, s>>>(V, R, g->off_out, g->adj_out, 0, g->sig, sig_words);
+  k_signatures<<<blocks_for(V), kT, 0, s>>>(V, R, g->off_in, g->adj_in, 1, g->sig, sig_words);
+  const uint64_t vt_bytes = ((uint64_t)V + 127) / 128 * 128;  // whole 32-vertex groups, zero padded
+  if (cudaMalloc(&g->vtype, vt_bytes) != cudaSuccess) return cleanup(fail(GS_ERR_OOM, "types"));
+  GS_CUDA(cudaMemsetAsync(g->vtype, 0, vt_bytes, s));
+  uint32_t *hist = nullptr;
+  GS_CUDA(cudaMalloc(&hist, sizeof(uint32_t) * T));
+  GS_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * T, s));
+  k_types<<<blocks_for(V), kT, 0, s>>>(V, vt.as<uint32_t>(), g->vtype, hist);
+  g->type_count = new uint32_t[T];
+  GS_CUDA(cudaMemcpyAsync(g->type_count, hist, sizeof(uint32_t) * T, cudaMemcpyDeviceToHost, s));
+  // content hash for the tuning cache: sizes plus a sample of rows
+  std::vector<uint32_t> sample(1024, 0);
+  uint64_t ns = kept < 1024 ? kept : 1024;
+  if (ns) GS_CUDA(cudaMemcpyAsync(sample.data(), g->adj_out + (kept - ns), ns * 4, cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  cudaFree(hist);
+  uint64_t h = 1469598103934665603ull;
+  auto mixin = [&](uint64_t x) { h = (h ^ x) * 1099511628211ull; };
+  mixin(V); mixin(kept); mixin(T); mixin(R);
+  for (uint64_t i = 0; i < ns; ++i) mixin(sample[i]);
+  g->hash = h;
+
+  DevGraph &d = g->d;
+  d.V = V; d.T = T; d.R = R; d.E = kept;
+  d.off[0] = g->off_out; d.off[1] = g->off_in;
+  d.adj[0] = g->adj_out; d.adj[1] = g->adj_in;
+  d.vtype = g->vtype;
+  d.sig = g->sig;
+  d.sig_words = sig_words;
+  d.W0 = (V + 31) / 32;
+  d.W1 = (d.W0 + 31) / 32;
+  d.ipg = (d.W1 + 31) / 32;
+  *out = g;
+  return GS_OK;
+}
+
+extern "C" void gs_graph_free(gs_graph *g) {
+  if (!g) return;
+  cudaFree(g->off_out);
+  cudaFree(g->off_in);
+  cudaFree(g->adj_out);
+  cudaFree(g->adj_in);
+  cudaFree(g->vtype);
+  cudaFree(g->sig);
+  delete[] g->type_count;
+  delete g;
+}
+
+extern "C" uint64_t gs_graph_num_edges(const gs_graph *g) { return g ? g->d.E : 0; }
+
+extern "C" const char *gs_last_error(void) { return gs::t_last_error.c_str(); }

@@ -1,0 +1,84 @@
+// Internal declarations shared by the engine's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr uint32_t kMaxK = 16;        // query vertices
+constexpr uint32_t kMaxM = 120;       // query edges (after dropping repeats)
+constexpr uint32_t kNbrBits = 24;     // packed adjacency entry: rel << 24 | neighbour
+constexpr uint32_t kNbrMask = (1u << kNbrBits) - 1;
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+gs_status fail(gs_status st, const std::string &msg);
+gs_status cuda_fail(cudaError_t e, const char *what);
+#define GS_CUDA(call)                                         \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return ::gs::cuda_fail(e_, #call); \
+  } while (0)
+
+// ------------------------------------------------------------ device graph
+// Both directions as CSR over packed (relation << 24 | neighbour) entries,
+// each row ascending, i.e. sorted by (relation, neighbour).  Signatures:
+// for direction d and relation r, plane (d * R + r) holds one 4-bit count per
+// vertex (8 vertices per 32-bit word): the number of distinct r-neighbours in
+// that direction, saturated at 15.
+struct DevGraph {
+  uint32_t V, T, R;
+  uint64_t E;
+  const uint64_t *off[2];   // [dir][V+1]; dir 0 = out, 1 = in
+  const uint32_t *adj[2];   // [dir][E]
+  const uint8_t *vtype;     // [V]
+  const uint32_t *sig;      // [2R][sig_words]
+  uint64_t sig_words;       // ceil(V / 8)
+  uint32_t W0;              // bitmap words per candidate set: ceil(V/32)
+  uint32_t W1;              // summary words: ceil(W0/32)
+  uint32_t ipg;             // compaction items per set: ceil(W1/32)
+};
+
+}  // namespace gs
+
+struct gs_graph {
+  gs::DevGraph d;
+  int device;
+  int num_sms;
+  uint64_t *off_out, *off_in;
+  uint32_t *adj_out, *adj_in;
+  uint8_t *vtype;
+  uint32_t *sig;
+  uint32_t *type_count;     // host copy [T]
+  uint64_t hash;            // content hash (tuning cache key)
+};
+
+namespace gs {
+
+// ------------------------------------------------------------ primitives
+// Exclusive prefix sum of n uint32 counts into out[0..n] (out[n] = total),
+// where n is read from device memory (*d_n).  max_n bounds n and sizes the
+// launch; tmp must hold scan_tmp_words(max_n) uint64 values.
+uint64_t scan_tmp_words(uint64_t max_n);
+void scan_u32(const uint32_t *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp,
+              cudaStream_t s, int num_sms);
+// Same for uint64 inputs.
+void scan_u64(const uint64_t *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp,
+              cudaStream_t s, int num_sms);
+
+// Stable LSD radix sort of (key, val) pairs by key bits [0, nbits).  n is read
+// from device memory.  Data ping-pongs between (k0, v0) and (k1, v1); the
+// return value is 0 if the result ends in (k0, v0), 1 if in (k1, v1).
+// tmp must hold radix_tmp_words(max_n) uint64 values.
+uint64_t radix_tmp_words(uint64_t max_n);
+int radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const uint64_t *d_n, uint64_t max_n,
+                     int bit_lo, int nbits, uint64_t *tmp, cudaStream_t s, int num_sms);
+int radix_passes(int nbits);
+
+}  // namespace gs

@@ -1,0 +1,1144 @@
+// The filtering-and-joining kernels (thesis Ch. 3, Algorithm
+// "FilteringAndJoining"), each persistent over a device-sized work list so a
+// whole batch can be captured once in a CUDA graph:
+//   plan        query plan on the device (Section 3.3.2 / 3.5)
+//   filter      kernel_check: C0 bitmaps of the first visited vertex
+//   compact     kernel_collect: bitmap -> sorted candidate list
+//   explore     kernel_explore: prune + expand along the spanning tree
+//   refine      refine_node_candidates: prune over every query edge, to a fixpoint
+//   ec_*        collect_edge_candidates: count / scan / write
+//   join_*      combine_edge_candidates: count / scan / write per level
+//   sort/gather lexicographic order of the embeddings, query-vertex columns
+#include "gs_engine.cuh"
+
+namespace gs {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint64_t gtid() { return blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; }
+__device__ __forceinline__ uint64_t gthreads() { return (uint64_t)gridDim.x * blockDim.x; }
+
+// ------------------------------------------------------------ bitmaps
+// A candidate set over V is a two-level bitmap: W0 words of one bit per
+// vertex, then W1 summary words with one bit per non-zero level-0 word.
+__device__ __forceinline__ uint32_t *slot_of(const Wave &W, uint32_t gqv) { return W.bm + (uint64_t)gqv * W.slot_words; }
+__device__ __forceinline__ bool bit_test(const uint32_t *slot, uint32_t v) { return (slot[v >> 5] >> (v & 31)) & 1u; }
+__device__ __forceinline__ void bit_set(const Wave &W, uint32_t *slot, uint32_t v) {
+  uint32_t old = atomicOr(&slot[v >> 5], 1u << (v & 31));
+  if (old == 0) atomicOr(&slot[W.G.W0 + (v >> 10)], 1u << ((v >> 5) & 31));
+}
+__device__ __forceinline__ void bit_clear(uint32_t *slot, uint32_t v) { atomicAnd(&slot[v >> 5], ~(1u << (v & 31))); }
+
+// Candidate test of Definition 3.3 read per direction and relation: binding,
+// type, and for every (direction, relation) at least as many distinct data
+// neighbours as the query vertex has query neighbours.
+__device__ __forceinline__ bool cand_ok(const DevGraph &G, const DQuery &Q, uint32_t u, uint32_t v) {
+  uint32_t b = Q.vbind[u];
+  if (b != kUnbound && b != v) return false;
+  uint32_t t = Q.vtype[u];
+  if (t != kAny && G.vtype[v] != t) return false;
+  for (uint32_t i = Q.need_begin[u]; i < Q.need_begin[u + 1]; ++i) {
+    uint32_t w = G.sig[(uint64_t)Q.need_plane[i] * G.sig_words + (v >> 3)];
+    if (((w >> ((v & 7) * 4)) & 15u) < Q.need_cnt[i]) return false;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------ group search
+// First index in [lo, hi) with a[i] >= key, searched by a tile of G lanes
+// (G-ary search, then one probe per lane).
+template <int G>
+__device__ __forceinline__ uint64_t tile_lower_bound(const cg::thread_block_tile<G> &t, const uint32_t *a, uint64_t lo,
+                                                     uint64_t hi, uint32_t key) {
+  const uint32_t r = t.thread_rank();
+  while (hi - lo > G) {
+    uint64_t step = (hi - lo + G - 1) / G;
+    uint64_t p = lo + (uint64_t)(r + 1) * step - 1;
+    bool less = p < hi && a[p] < key;
+    uint32_t c = __popc(t.ballot(less));
+    uint64_t nlo = lo + (uint64_t)c * step;
+    uint64_t nhi = c < G ? lo + (uint64_t)(c + 1) * step - 1 : hi;
+    lo = nlo < hi ? nlo : hi;
+    hi = nhi < hi ? nhi : hi;
+    if (lo > hi) lo = hi;
+  }
+  uint64_t i = lo + r;
+  bool less = i < hi && a[i] < key;
+  return lo + __popc(t.ballot(less));
+}
+
+// Relation run of a sorted packed row: entries with (x >> 24) == rel.
+template <int G>
+__device__ __forceinline__ void rel_range(const cg::thread_block_tile<G> &t, const DevGraph &Gr, int dir, uint32_t v,
+                                          uint32_t rel, uint64_t &lo, uint64_t &hi) {
+  const uint32_t *a = Gr.adj[dir];
+  uint64_t b = Gr.off[dir][v], e = Gr.off[dir][v + 1];
+  lo = tile_lower_bound<G>(t, a, b, e, rel << kNbrBits);
+  hi = tile_lower_bound<G>(t, a, lo, e, (rel + 1) << kNbrBits);
+}
+
+// Binary search of a sorted uint32 list (all lanes do the same search).
+__device__ __forceinline__ int64_t list_find(const uint32_t *a, uint64_t n, uint32_t key) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint64_t mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return (lo < n && a[lo] == key) ? (int64_t)lo : -1;
+}
+__device__ __forceinline__ bool list_has(const uint32_t *a, uint64_t n, uint32_t key) { return list_find(a, n, key) >= 0; }
+
+// Segment of an item: largest s in [0, ns) with base(s) <= item, where
+// base(s) = bases[s * stride].
+__device__ __forceinline__ uint32_t seg_of(const uint64_t *bases, uint64_t stride, uint32_t ns, uint64_t item) {
+  uint32_t lo = 0, hi = ns;  // invariant: answer in [lo, hi)
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (bases[(uint64_t)mid * stride] <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ uint32_t seg_of_rows(const QState *qs, uint32_t nq, uint64_t item) {
+  uint32_t lo = 0, hi = nq;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (qs[mid].cur_row_base <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void add_bytes(const Wave &W, int kind, uint64_t b) {
+  if (W.stats && b) atomicAdd((unsigned long long *)&W.ctrl->bytes[kind], (unsigned long long)b);
+}
+
+__device__ __forceinline__ void mark(DQuery &Q, uint32_t st) { atomicCAS(&Q.status, QS_OK, st); }
+
+// splitmix64 finaliser (Steele, Lea & Flood 2014); row hash for fingerprints.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// Hash of an embedding in query-vertex order; row holds join-order columns
+// 0..s, with column s+1 (query vertex w) = c.
+__device__ __forceinline__ uint64_t row_hash(const DQuery &Q, const uint32_t *row, uint32_t w, uint32_t c) {
+  uint64_t h = Q.k;
+  for (uint32_t u = 0; u < Q.k; ++u) {
+    uint32_t x = u == w ? c : row[Q.pos[u]];
+    h = mix64(h ^ ((uint64_t)x + (uint64_t)(u + 1) * 0x9E3779B97F4A7C15ull));
+  }
+  return h;
+}
+
+// ============================================================ plan
+// Section 3.5 ("Modify the query plan"): start at the bound vertex of largest
+// degree, else at the vertex of largest deg(u)/freq(type(u)) (Section 3.3.2's
+// ranking); then repeatedly explore the already-covered vertex with the most
+// uncovered neighbours until every vertex is covered.  The explored vertices
+// form the visit order; each newly covered vertex hangs below the vertex that
+// covered it (the spanning tree T).
+__global__ void k_plan(Wave W, const uint32_t *type_count) {
+  const WaveDesc D = W.waves[W.ctrl->wave];
+  for (uint64_t qi = gtid(); qi <= W.nq; qi += gthreads()) {
+    DQuery &Q = W.dq[qi];
+    if (qi >= D.nq) {  // padding and the permanent empty slot
+      Q.k = 0; Q.m = 0; Q.status = QS_INVALID; Q.nvisit = 0;
+      if (qi < W.nq) {
+        QState &S = W.qs[qi];
+        S = QState{};
+      }
+      continue;
+    }
+    QState &S = W.qs[qi];
+    S = QState{};
+    Q.qv_base -= D.qv0;
+    Q.qe_base -= D.qe0;
+    if (Q.status == QS_INVALID) continue;
+    Q.status = QS_OK;
+    const uint32_t k = Q.k;
+    uint32_t nbr[kMaxK];  // neighbour masks
+    for (uint32_t u = 0; u < k; ++u) {
+      nbr[u] = 0;
+      for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1]; ++i) {
+        uint32_t e = Q.inc_edge[i];
+        nbr[u] |= 1u << (Q.esrc[e] == u ? Q.edst[e] : Q.esrc[e]);
+      }
+    }
+    int root = Q.force_root != 0xFF ? (int)Q.force_root : -1;
+    if (root < 0)
+      for (uint32_t u = 0; u < k; ++u)
+        if (Q.vbind[u] != kUnbound && (root < 0 || __popc(nbr[u]) > __popc(nbr[root]))) root = (int)u;
+    if (root < 0) {
+      uint64_t bn = 0, bf = 1;
+      for (uint32_t u = 0; u < k; ++u) {
+        uint64_t d = __popc(nbr[u]);
+        uint64_t f = Q.vtype[u] == kAny ? W.G.V : type_count[Q.vtype[u]];
+        if (f == 0) f = 1;
+        if (root < 0 || d * bf > bn * f) { root = (int)u; bn = d; bf = f; }
+      }
+    }
+    for (uint32_t u = 0; u < kMaxK; ++u) { Q.parent[u] = 0xFF; Q.pedge[u] = 0xFF; Q.init_step[u] = 0xFF; }
+    uint32_t covered = 1u << root, inO = 0, all = (k == 32) ? 0xFFFFFFFFu : ((1u << k) - 1);
+    Q.init_step[root] = 0;
+    uint32_t nv = 0, cur = (uint32_t)root;
+    for (;;) {
+      Q.visit[nv] = (uint8_t)cur;
+      inO |= 1u << cur;
+      uint32_t fresh = nbr[cur] & ~covered;
+      for (uint32_t i = Q.inc_begin[cur]; i < Q.inc_begin[cur + 1]; ++i) {
+        uint32_t e = Q.inc_edge[i];
+        uint32_t w = Q.esrc[e] == cur ? Q.edst[e] : Q.esrc[e];
+        if ((fresh >> w) & 1u) {
+          if (Q.parent[w] == 0xFF) { Q.parent[w] = (uint8_t)cur; Q.pedge[w] = (uint8_t)e; Q.init_step[w] = (uint8_t)(nv + 1); }
+        }
+      }
+      covered |= fresh;
+      nv++;
+      if (covered == all) break;
+      int best = -1, bestc = -1;
+      for (uint32_t u = 0; u < k; ++u) {
+        if (!((covered >> u) & 1u) || ((inO >> u) & 1u)) continue;
+        int c = __popc(nbr[u] & ~covered);
+        if (c > bestc) { bestc = c; best = (int)u; }
+      }
+      if (best < 0 || bestc <= 0) { Q.status = QS_INVALID; break; }  // disconnected (host rejects these)
+      cur = (uint32_t)best;
+    }
+    Q.nvisit = nv;
+  }
+}
+
+// ============================================================ filter
+// kernel_check for the first visited vertex of each query: a bound vertex has
+// the single candidate bind (if it passes the test); otherwise every data
+// vertex is tested.  One warp writes 32 level-0 words and one summary word.
+__global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
+  const DevGraph &G = W.G;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = gthreads() / 32;
+  const uint64_t items = (uint64_t)W.nq * G.W1;
+  for (uint64_t it = gtid() / 32; it < items; it += warps) {
+    const uint32_t qi = (uint32_t)(it / G.W1), w1 = (uint32_t)(it % G.W1);
+    const DQuery &Q = W.dq[qi];
+    if (Q.status != QS_OK) continue;
+    const uint32_t u = Q.visit[0];
+    uint32_t *slot = slot_of(W, Q.qv_base + u);
+    if (Q.vbind[u] != kUnbound) {
+      if (w1 == 0 && lane == 0 && cand_ok(G, Q, u, Q.vbind[u])) bit_set(W, slot, Q.vbind[u]);
+      continue;
+    }
+    const uint32_t w0 = w1 * 32 + lane;
+    uint32_t word = 0;
+    if (w0 < G.W0) {
+      const uint32_t v0 = w0 * 32;
+      const uint32_t t = Q.vtype[u];
+      uint32_t ok = 0xFFFFFFFFu;
+      if (t != kAny) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(G.vtype + v0);
+        uint4 a = p[0], b = p[1];
+        uint32_t wd[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        ok = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) ok |= (((wd[j >> 2] >> ((j & 3) * 8)) & 0xFFu) == t ? 1u : 0u) << j;
+      }
+      for (uint32_t i = Q.need_begin[u]; i < Q.need_begin[u + 1] && ok; ++i) {
+        const uint4 s = *reinterpret_cast<const uint4 *>(G.sig + (uint64_t)Q.need_plane[i] * G.sig_words + (uint64_t)w0 * 4);
+        uint32_t sw[4] = {s.x, s.y, s.z, s.w};
+        uint32_t c = Q.need_cnt[i], m = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) m |= (((sw[j >> 3] >> ((j & 7) * 4)) & 15u) >= c ? 1u : 0u) << j;
+        ok &= m;
+      }
+      if (v0 + 32 > G.V) ok &= (G.V - v0 >= 32) ? 0xFFFFFFFFu : ((1u << (G.V - v0)) - 1);
+      word = ok;
+      slot[w0] = word;
+    }
+    uint32_t nz = __ballot_sync(kFull, word != 0);
+    if (lane == 0) slot[G.W0 + w1] = nz;
+    if (lane == 0 && W.stats) {
+      uint64_t nb = 32ull * 32 * (Q.vtype[u] != kAny ? 1 : 0) + 32ull * 16 * (Q.need_begin[u + 1] - Q.need_begin[u]) + 32 * 4 + 4;
+      add_bytes(W, KK_FILTER, nb);
+    }
+  }
+}
+
+// ============================================================ compaction
+// kernel_collect: the candidate set as a sorted list.  Items are chunks of 32
+// summary words (32K vertices) of a selected set; selection mode 0 picks the
+// step-th visited vertex of each query, mode 1 every query vertex.
+__device__ __forceinline__ bool sel_slot(const Wave &W, int mode, uint32_t step, uint32_t s, uint32_t &gqv) {
+  if (mode == 0) {
+    const DQuery &Q = W.dq[s];
+    if (Q.status != QS_OK || Q.nvisit <= step) return false;
+    gqv = Q.qv_base + Q.visit[step];
+    return true;
+  }
+  gqv = s;
+  return W.dq[W.qv_q[s]].status == QS_OK;
+}
+
+__global__ void __launch_bounds__(kThreads) k_compact_count(Wave W, int mode, uint32_t step) {
+  const DevGraph &G = W.G;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = gthreads() / 32;
+  const uint32_t nsel = mode == 0 ? W.nq : W.nqv;
+  const uint64_t items = (uint64_t)nsel * G.ipg;
+  for (uint64_t it = gtid() / 32; it < items; it += warps) {
+    const uint32_t s = (uint32_t)(it / G.ipg), c = (uint32_t)(it % G.ipg);
+    uint32_t gqv = 0;
+    uint32_t cnt = 0;
+    if (sel_slot(W, mode, step, s, gqv)) {
+      const uint32_t *slot = slot_of(W, gqv);
+      const uint32_t w1 = c * 32 + lane;
+      uint32_t sw = w1 < G.W1 ? slot[G.W0 + w1] : 0;
+      uint32_t m = __ballot_sync(kFull, sw != 0);
+      while (m) {
+        int j = __ffs(m) - 1;
+        m &= m - 1;
+        uint32_t swj = __shfl_sync(kFull, sw, j);
+        uint32_t w0 = (c * 32 + j) * 32 + lane;
+        if ((swj >> lane) & 1u) cnt += __popc(slot[w0]);
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
+    }
+    if (lane == 0) W.ccount[it] = cnt;
+  }
+}
+
+// Writes ids in ascending order at dst[cscan[item] ...]; marks a query that
+// does not fit dst_cap as overflowed.
+__global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, uint32_t step, const uint64_t *scan,
+                                                             uint32_t *dst, uint64_t dst_cap) {
+  const DevGraph &G = W.G;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = gthreads() / 32;
+  const uint32_t nsel = mode == 0 ? W.nq : W.nqv;
+  const uint64_t items = (uint64_t)nsel * G.ipg;
+  for (uint64_t it = gtid() / 32; it < items; it += warps) {
+    const uint32_t s = (uint32_t)(it / G.ipg), c = (uint32_t)(it % G.ipg);
+    uint32_t gqv = 0;
+    if (!sel_slot(W, mode, step, s, gqv)) continue;
+    const uint64_t base = scan[it];
+    if (scan[it + 1] > dst_cap) {
+      if (lane == 0) mark(W.dq[mode == 0 ? s : W.qv_q[s]], QS_OVERFLOW);
+      continue;
+    }
+    const uint32_t *slot = slot_of(W, gqv);
+    const uint32_t w1 = c * 32 + lane;
+    uint32_t sw = w1 < G.W1 ? slot[G.W0 + w1] : 0;
+    uint32_t m = __ballot_sync(kFull, sw != 0);
+    uint64_t run = base;
+    while (m) {
+      int j = __ffs(m) - 1;
+      m &= m - 1;
+      uint32_t swj = __shfl_sync(kFull, sw, j);
+      uint32_t w0 = (c * 32 + j) * 32 + lane;
+      uint32_t x = ((swj >> lane) & 1u) ? slot[w0] : 0;
+      uint32_t n = __popc(x), incl = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      uint64_t p = run + incl - n;
+      while (x) {
+        int b = __ffs(x) - 1;
+        x &= x - 1;
+        dst[p++] = w0 * 32 + b;
+      }
+      run += __shfl_sync(kFull, incl, 31);
+    }
+  }
+}
+
+// ============================================================ explore
+// kernel_explore (Algorithm "Candidate nodes initialization"): one tile of G
+// lanes per candidate v of the visited vertex u.  v is dropped when some
+// query neighbour w of u has no candidate among v's data neighbours over the
+// edge's relation and direction (a neighbour whose set is not built yet is
+// tested with the candidate test); otherwise v's neighbours that pass the
+// candidate test are added to the sets of u's spanning-tree children.
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
+  auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+  const DevGraph &Gr = W.G;
+  const uint32_t r = tile.thread_rank();
+  const uint64_t ntile = gthreads() / G;
+  const uint64_t items = W.cscan[(uint64_t)W.nq * Gr.ipg];
+  for (uint64_t it = gtid() / G; it < items; it += ntile) {
+    const uint32_t qi = seg_of(W.cscan, Gr.ipg, W.nq, it);
+    DQuery &Q = W.dq[qi];
+    if (Q.status != QS_OK) continue;
+    const uint32_t u = Q.visit[step];
+    const uint32_t v = W.tlist[it];
+    uint64_t bytes = 0;
+    bool keep = true;
+    for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1] && keep; ++i) {
+      const uint32_t e = Q.inc_edge[i];
+      const int dir = Q.esrc[e] == u ? 0 : 1;
+      const uint32_t w = dir == 0 ? Q.edst[e] : Q.esrc[e];
+      uint64_t lo, hi;
+      rel_range<G>(tile, Gr, dir, v, Q.erel[e], lo, hi);
+      const bool built = Q.init_step[w] <= step;
+      const uint32_t *ws = slot_of(W, Q.qv_base + w);
+      bool found = false;
+      for (uint64_t b = lo; b < hi && !found; b += G) {
+        uint64_t j = b + r;
+        bool ok = false;
+        if (j < hi) {
+          uint32_t x = Gr.adj[dir][j] & kNbrMask;
+          ok = built ? bit_test(ws, x) : cand_ok(Gr, Q, w, x);
+        }
+        found = tile.any(ok);
+      }
+      bytes += 16 + 4 * (hi - lo);
+      if (!found) keep = false;
+    }
+    if (!keep) {
+      if (r == 0) bit_clear(slot_of(W, Q.qv_base + u), v);
+    } else {
+      for (uint32_t w = 0; w < Q.k; ++w) {
+        if (Q.parent[w] != u || Q.init_step[w] != step + 1) continue;
+        const uint32_t e = Q.pedge[w];
+        const int dir = Q.esrc[e] == u ? 0 : 1;
+        uint64_t lo, hi;
+        rel_range<G>(tile, Gr, dir, v, Q.erel[e], lo, hi);
+        uint32_t *ws = slot_of(W, Q.qv_base + w);
+        for (uint64_t j = lo + r; j < hi; j += G) {
+          uint32_t x = Gr.adj[dir][j] & kNbrMask;
+          if (cand_ok(Gr, Q, w, x)) bit_set(W, ws, x);
+        }
+        bytes += 16 + 4 * (hi - lo);
+      }
+    }
+    if (r == 0) add_bytes(W, KK_EXPLORE, bytes + 4);
+  }
+}
+
+// ============================================================ refine
+// refine_node_candidates, one round: every live candidate v of every query
+// vertex u keeps its place only if, for every query edge at u, some data
+// neighbour of v over that relation and direction is a live candidate of the
+// other endpoint.  Rounds repeat until one clears nothing (the fixpoint).
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_refine(Wave W, uint32_t round) {
+  if (round > 0 && W.ctrl->changed[round - 1] == 0) return;
+  auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+  const DevGraph &Gr = W.G;
+  const uint32_t r = tile.thread_rank();
+  const uint64_t ntile = gthreads() / G;
+  const uint64_t items = W.ascan[(uint64_t)W.nqv * Gr.ipg];
+  bool changed = false;
+  for (uint64_t it = gtid() / G; it < items; it += ntile) {
+    const uint32_t gqv = seg_of(W.ascan, Gr.ipg, W.nqv, it);
+    DQuery &Q = W.dq[W.qv_q[gqv]];
+    if (Q.status != QS_OK) continue;
+    const uint32_t u = gqv - Q.qv_base;
+    const uint32_t v = W.alist[it];
+    uint32_t *us = slot_of(W, gqv);
+    if (!bit_test(us, v)) continue;
+    uint64_t bytes = 0;
+    for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1]; ++i) {
+      const uint32_t e = Q.inc_edge[i];
+      const int dir = Q.esrc[e] == u ? 0 : 1;
+      const uint32_t w = dir == 0 ? Q.edst[e] : Q.esrc[e];
+      uint64_t lo, hi;
+      rel_range<G>(tile, Gr, dir, v, Q.erel[e], lo, hi);
+      const uint32_t *ws = slot_of(W, Q.qv_base + w);
+      bool found = false;
+      for (uint64_t b = lo; b < hi && !found; b += G) {
+        uint64_t j = b + r;
+        found = tile.any(j < hi && bit_test(ws, Gr.adj[dir][j] & kNbrMask));
+      }
+      bytes += 16 + 4 * (hi - lo);
+      if (!found) {
+        if (r == 0) bit_clear(us, v);
+        changed = true;
+        break;
+      }
+    }
+    if (r == 0) add_bytes(W, KK_REFINE, bytes + 4);
+  }
+  if (changed && tile.thread_rank() == 0) W.ctrl->changed[round] = 1;
+}
+
+// Final candidate lists: offsets and lengths per query vertex; a query with
+// an empty set has no embedding.
+__global__ void k_list_table(Wave W) {
+  const uint32_t ipg = W.G.ipg;
+  for (uint64_t g = gtid(); g < W.nqv; g += gthreads()) {
+    uint64_t b = W.cscan[g * ipg], e = W.cscan[(g + 1) * ipg];
+    W.flist_off[g] = b;
+    W.flist_len[g] = (uint32_t)(e - b);
+    DQuery &Q = W.dq[W.qv_q[g]];
+    if (e == b) mark(Q, QS_EMPTY);
+  }
+}
+
+// ============================================================ join plan
+// Join order (Section 3.3.4, combine_edge_candidates): begin with the vertex
+// of fewest candidates, then repeatedly take the vertex with the most edges
+// into the joined part (ties: fewer candidates, then lower index).  Each
+// query edge is oriented from its earlier-joined endpoint, whose candidates
+// key its candidate-edge table.
+__global__ void k_join_plan(Wave W) {
+  for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
+    DQuery &Q = W.dq[qi];
+    const bool ok = Q.status == QS_OK;
+    const uint32_t k = Q.k;
+    if (ok) {
+      uint32_t size[kMaxK];
+      for (uint32_t u = 0; u < k; ++u) size[u] = W.flist_len[Q.qv_base + u];
+      uint32_t joined = 0;
+      for (uint32_t s = 0; s < k; ++s) {
+        int best = -1, bl = -1;
+        for (uint32_t u = 0; u < k; ++u) {
+          if ((joined >> u) & 1u) continue;
+          int links = 0;
+          for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1]; ++i) {
+            uint32_t e = Q.inc_edge[i];
+            uint32_t w = Q.esrc[e] == u ? Q.edst[e] : Q.esrc[e];
+            links += (joined >> w) & 1u;
+          }
+          if (s > 0 && links == 0) continue;
+          if (best < 0 || links > bl || (links == bl && size[u] < size[best])) { best = (int)u; bl = links; }
+        }
+        Q.join[s] = (uint8_t)best;
+        Q.pos[best] = (uint8_t)s;
+        joined |= 1u << best;
+      }
+    }
+    for (uint32_t e = 0; e < Q.m; ++e) {
+      uint32_t n = 0;
+      if (ok) {
+        Q.from_src[e] = Q.force_from_src != 0xFF ? Q.force_from_src : (Q.pos[Q.esrc[e]] < Q.pos[Q.edst[e]] ? 1 : 0);
+        n = W.flist_len[Q.qv_base + (Q.from_src[e] ? Q.esrc[e] : Q.edst[e])];
+      }
+      W.ec_nkeys[Q.qe_base + e] = n;
+    }
+  }
+}
+
+// ============================================================ edge tables
+// collect_edge_candidates with the two-step output scheme: for query edge e
+// keyed by endpoint x (candidates in ascending order), the list of key c
+// holds c's data neighbours over e's relation and direction that are
+// candidates of the other endpoint y, ascending.
+template <int G, bool WRITE>
+__global__ void __launch_bounds__(kThreads) k_ec(Wave W) {
+  auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+  const DevGraph &Gr = W.G;
+  const uint32_t r = tile.thread_rank();
+  const uint64_t ntile = gthreads() / G;
+  const uint64_t items = W.ctrl->len[5];  // clamped to the table capacity by k_ec_limit
+  for (uint64_t it = gtid() / G; it < items; it += ntile) {
+    const uint32_t ge = seg_of(W.ec_key_base, 1, W.nqe, it);
+    DQuery &Q = W.dq[W.qe_q[ge]];
+    if (Q.status != QS_OK) {
+      if (!WRITE && r == 0) W.ec_cnt[it] = 0;
+      continue;
+    }
+    const uint32_t e = ge - Q.qe_base;
+    const uint32_t x = Q.from_src[e] ? Q.esrc[e] : Q.edst[e];
+    const uint32_t y = Q.from_src[e] ? Q.edst[e] : Q.esrc[e];
+    const int dir = Q.from_src[e] ? 0 : 1;
+    const uint32_t key = W.flist[W.flist_off[Q.qv_base + x] + (it - W.ec_key_base[ge])];
+    uint64_t lo, hi;
+    rel_range<G>(tile, Gr, dir, key, Q.erel[e], lo, hi);
+    const uint32_t *ys = slot_of(W, Q.qv_base + y);
+    if (!WRITE) {
+      uint32_t cnt = 0;
+      for (uint64_t b = lo; b < hi; b += G) {
+        uint64_t j = b + r;
+        cnt += __popc(tile.ballot(j < hi && bit_test(ys, Gr.adj[dir][j] & kNbrMask)));
+      }
+      if (r == 0) {
+        W.ec_cnt[it] = cnt;
+        add_bytes(W, KK_EC_COUNT, 16 + 4 * (hi - lo) + 4 * (uint64_t)((hi - lo + 31) / 32) + 4);
+      }
+    } else {
+      uint64_t p = W.ec_off[it];
+      if (W.ec_off[it + 1] > W.ec_vals_cap) {
+        if (r == 0) mark(Q, QS_OVERFLOW);
+        continue;
+      }
+      for (uint64_t b = lo; b < hi; b += G) {
+        uint64_t j = b + r;
+        uint32_t xv = j < hi ? (Gr.adj[dir][j] & kNbrMask) : 0;
+        bool ok = j < hi && bit_test(ys, xv);
+        uint32_t m = tile.ballot(ok);
+        if (ok) W.ec_vals[p + __popc(m & ((1u << r) - 1))] = xv;
+        p += __popc(m);
+      }
+      if (r == 0) add_bytes(W, KK_EC_WRITE, 16 + 4 * (hi - lo) + 4 * (W.ec_off[it + 1] - W.ec_off[it]) + 8);
+    }
+  }
+}
+
+// Restore every touched bitmap word to zero (only words flagged in the
+// summary are visited), so the slots are clean for the next run.
+__global__ void __launch_bounds__(kThreads) k_clear(Wave W) {
+  const DevGraph &G = W.G;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = gthreads() / 32;
+  const uint64_t items = (uint64_t)W.nqv * G.ipg;
+  for (uint64_t it = gtid() / 32; it < items; it += warps) {
+    const uint32_t gqv = (uint32_t)(it / G.ipg), c = (uint32_t)(it % G.ipg);
+    uint32_t *slot = slot_of(W, gqv);
+    const uint32_t w1 = c * 32 + lane;
+    uint32_t sw = w1 < G.W1 ? slot[G.W0 + w1] : 0;
+    uint32_t m = __ballot_sync(kFull, sw != 0);
+    while (m) {
+      int j = __ffs(m) - 1;
+      m &= m - 1;
+      uint32_t swj = __shfl_sync(kFull, sw, j);
+      if ((swj >> lane) & 1u) slot[(c * 32 + j) * 32 + lane] = 0;
+    }
+    if (sw) slot[G.W0 + w1] = 0;
+  }
+}
+
+// Queries whose edge-table keys would pass the capacity are sent to the
+// fallback path; the item count is clamped so no kernel reads past it.
+__global__ void k_ec_limit(Wave W) {
+  const uint64_t total = W.ec_key_base[W.nqe];
+  for (uint64_t ge = gtid(); ge < W.nqe; ge += gthreads())
+    if (W.ec_key_base[ge + 1] > W.ec_items_cap && W.ec_key_base[ge + 1] > W.ec_key_base[ge])
+      mark(W.dq[W.qe_q[ge]], QS_OVERFLOW);
+  if (gtid() == 0) W.ctrl->len[5] = total < W.ec_items_cap ? total : W.ec_items_cap;
+}
+
+// ============================================================ wave I/O
+// Prologue: copy the wave's queries into the slots and reset the control
+// block.  The wave index advances in the epilogue, so replaying the same
+// captured graph runs the waves in order.
+__global__ void k_prologue(Wave W) {
+  const WaveDesc D = W.waves[W.ctrl->wave];
+  const uint64_t words = sizeof(DQuery) / 4;
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(W.all_dq + D.q0);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(W.dq);
+  for (uint64_t i = gtid(); i < (uint64_t)D.nq * words; i += gthreads()) dst[i] = src[i];
+  for (uint64_t g = gtid(); g < W.nqv; g += gthreads()) W.qv_q[g] = W.nq;  // owners come from k_owners
+  for (uint64_t g = gtid(); g < W.nqe; g += gthreads()) {
+    W.qe_q[g] = W.nq;
+    W.ec_nkeys[g] = 0;
+  }
+  if (gtid() == 0) {
+    for (int i = 0; i < 8; ++i)
+      if (i >= 3) W.ctrl->len[i] = 0;
+    for (uint32_t i = 0; i < kMaxRounds; ++i) W.ctrl->changed[i] = 0;
+    W.ctrl->lvl_top = 0;
+    W.ctrl->out_top = 0;
+    W.ctrl->out_rows_total = 0;
+  }
+}
+
+// Owner tables of the wave's query vertices and edges (after the plan has
+// rebased each slot's vertex and edge ranges).
+__global__ void k_owners(Wave W) {
+  for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
+    const DQuery &Q = W.dq[qi];
+    if (Q.status == QS_INVALID && Q.k == 0) continue;
+    for (uint32_t u = 0; u < Q.k; ++u) W.qv_q[Q.qv_base + u] = (uint32_t)qi;
+    for (uint32_t e = 0; e < Q.m; ++e) W.qe_q[Q.qe_base + e] = (uint32_t)qi;
+  }
+}
+
+// ============================================================ join
+// Level 0: the candidates of join[0] are the first partial embeddings.
+__global__ void k_join0_rows(Wave W) {
+  for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
+    const DQuery &Q = W.dq[qi];
+    QState &S = W.qs[qi];
+    S.nxt_rows = Q.status == QS_OK ? W.flist_len[Q.qv_base + Q.join[0]] : 0;
+    if (Q.status == QS_OK && Q.k == 1) S.count = S.nxt_rows;
+  }
+}
+
+// Layout of level `lvl` (rows of width lvl+1), one block over the queries in
+// order.  A non-final level goes to level buffer (lvl & 1); a final level
+// goes to the output pool when rows are wanted and count <= cap.  Pass 0
+// marks queries that do not fit; pass 1 lays out the rest (which then fit).
+__device__ __forceinline__ void level_sizes(const Wave &W, uint32_t qi, uint32_t lvl, bool pass0, uint64_t v[4],
+                                            bool &to_out, bool &mid) {
+  v[0] = v[1] = v[2] = v[3] = 0;
+  to_out = mid = false;
+  if (qi >= W.nq) return;
+  DQuery &Q = W.dq[qi];
+  const QState &S = W.qs[qi];
+  if (Q.status != QS_OK || Q.k <= lvl) return;
+  if (Q.k == lvl + 1) {
+    if (Q.mode == GS_COUNT_ONLY || Q.cap == 0) return;
+    if (S.count > Q.cap) {
+      if (pass0) mark(Q, QS_TOPCAP);
+      return;
+    }
+    to_out = true;
+    v[2] = S.nxt_rows;
+    v[3] = S.nxt_rows * Q.k;
+  } else {
+    mid = true;
+    v[0] = S.nxt_rows;
+    v[1] = S.nxt_rows * (lvl + 1);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
+  __shared__ uint64_t sm[4][32];
+  __shared__ uint64_t carry[4];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (threadIdx.x == 0) {
+      carry[0] = 0; carry[1] = 0;
+      carry[2] = W.ctrl->out_rows_total; carry[3] = W.ctrl->out_top;
+    }
+    __syncthreads();
+    for (uint32_t base = 0; base < W.nq; base += blockDim.x) {
+      const uint32_t qi = base + threadIdx.x;
+      uint64_t v[4], ex[4];
+      bool to_out, mid;
+      level_sizes(W, qi, lvl, pass == 0, v, to_out, mid);
+      for (int a = 0; a < 4; ++a) {
+        uint64_t x = v[a];
+        for (int o = 1; o < 32; o <<= 1) {
+          uint64_t y = __shfl_up_sync(kFull, x, o);
+          if (lane >= o) x += y;
+        }
+        if (lane == 31) sm[a][warp] = x;
+        ex[a] = x - v[a];
+      }
+      __syncthreads();
+      if (warp < 4) {
+        uint64_t x = sm[warp][lane];
+        for (int o = 1; o < 32; o <<= 1) {
+          uint64_t y = __shfl_up_sync(kFull, x, o);
+          if (lane >= o) x += y;
+        }
+        sm[warp][lane] = x;
+      }
+      __syncthreads();
+      uint64_t pos[4];
+      for (int a = 0; a < 4; ++a) pos[a] = carry[a] + ex[a] + (warp ? sm[a][warp - 1] : 0);
+      if (qi < W.nq) {
+        DQuery &Q = W.dq[qi];
+        QState &S = W.qs[qi];
+        if (pass == 0) {
+          if (mid && (pos[0] + v[0] > W.row_cap || pos[1] + v[1] > W.lvl_words)) mark(Q, QS_OVERFLOW);
+          if (to_out && (pos[2] + v[2] > W.out_rows_cap || pos[3] + v[3] > W.out_words)) mark(Q, QS_OVERFLOW);
+        } else {
+          S.cur_row_base = pos[0];
+          S.cur_word_base = pos[1];
+          S.cur_rows = v[0];
+          if (to_out) {
+            S.out_row_base = pos[2];
+            S.out_word_base = pos[3];
+            S.out_rows = v[2];
+          }
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int a = 0; a < 4; ++a) carry[a] += sm[a][31];
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    W.ctrl->len[3] = carry[0];
+    W.ctrl->out_rows_total = carry[2];
+    W.ctrl->out_top = carry[3];
+  }
+}
+
+// Level-0 rows (final rows when k == 1), one block per query.
+__global__ void k_join0_write(Wave W) {
+  for (uint64_t qi = blockIdx.x; qi < W.nq; qi += gridDim.x) {
+    const DQuery &Q = W.dq[qi];
+    QState &S = W.qs[qi];
+    if (Q.status != QS_OK) continue;
+    const uint32_t j0 = Q.join[0];
+    const uint64_t n = W.flist_len[Q.qv_base + j0];
+    const uint32_t *lst = W.flist + W.flist_off[Q.qv_base + j0];
+    const bool final = Q.k == 1;
+    uint64_t fp = 0;
+    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t v = lst[i];
+      if (final) {
+        fp += mix64((uint64_t)1 ^ ((uint64_t)v + 0x9E3779B97F4A7C15ull));
+        if (S.out_rows) {
+          W.out[S.out_word_base + i] = v;
+          W.out_q[S.out_row_base + i] = (uint32_t)qi;
+        }
+      } else {
+        W.lvl[0][S.cur_word_base + i] = v;
+      }
+    }
+    if (final) {
+      for (int o = 16; o; o >>= 1) fp += __shfl_down_sync(kFull, fp, o);
+      if ((threadIdx.x & 31) == 0 && fp) atomicAdd((unsigned long long *)&S.fp, (unsigned long long)fp);
+    }
+  }
+}
+
+// Candidates for the next vertex w = join[s+1] of one partial row: the
+// candidate-edge table of every query edge between w and the joined part is
+// looked up by the joined endpoint's id; the shortest list drives and the
+// others are probed (sorted-list intersection); ids already in the row are
+// skipped (injectivity).
+struct JoinCtx {
+  uint32_t w, nedge, drive;
+  const uint32_t *lst[kMaxK];
+  uint32_t len[kMaxK];
+};
+
+__device__ __forceinline__ bool join_setup(const Wave &W, const DQuery &Q, uint32_t s, const uint32_t *row, JoinCtx &c) {
+  c.w = Q.join[s + 1];
+  c.nedge = 0;
+  c.drive = 0;
+  uint64_t best = ~0ull;
+  for (uint32_t i = Q.inc_begin[c.w]; i < Q.inc_begin[c.w + 1]; ++i) {
+    const uint32_t e = Q.inc_edge[i];
+    const uint32_t x = Q.esrc[e] == c.w ? Q.edst[e] : Q.esrc[e];
+    if (Q.pos[x] > s) continue;
+    const uint32_t gx = Q.qv_base + x;
+    const int64_t t = list_find(W.flist + W.flist_off[gx], W.flist_len[gx], row[Q.pos[x]]);
+    if (t < 0) return false;
+    const uint64_t item = W.ec_key_base[Q.qe_base + e] + (uint64_t)t;
+    const uint64_t b = W.ec_off[item], en = W.ec_off[item + 1];
+    c.lst[c.nedge] = W.ec_vals + b;
+    c.len[c.nedge] = (uint32_t)(en - b);
+    if (en - b < best) { best = en - b; c.drive = c.nedge; }
+    c.nedge++;
+  }
+  return c.nedge > 0;
+}
+
+__device__ __forceinline__ bool join_ok(const JoinCtx &c, const uint32_t *row, uint32_t s, uint32_t cand) {
+  for (uint32_t i = 0; i <= s; ++i)
+    if (row[i] == cand) return false;
+  for (uint32_t j = 0; j < c.nedge; ++j)
+    if (j != c.drive && !list_has(c.lst[j], c.len[j], cand)) return false;
+  return true;
+}
+
+__device__ __forceinline__ uint32_t seg_of_src(const SrcRows *src, uint32_t nq, uint64_t item) {
+  uint32_t lo = 0, hi = nq;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (src[mid].row_base <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Count pass of level s -> s+1; a query whose last vertex is w also adds its
+// embeddings and their hashes to its count and fingerprint here.
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_join_count(Wave W, uint32_t s) {
+  auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+  const uint32_t r = tile.thread_rank();
+  const uint64_t ntile = gthreads() / G;
+  const uint64_t items = W.ctrl->len[3];
+  const uint32_t *lvl = W.lvl[s & 1];
+  for (uint64_t it = gtid() / G; it < items; it += ntile) {
+    const uint32_t qi = seg_of_rows(W.qs, W.nq, it);
+    const DQuery &Q = W.dq[qi];
+    QState &S = W.qs[qi];
+    uint32_t cnt = 0;
+    uint64_t fp = 0, bytes = 0;
+    const bool live = Q.status == QS_OK && it < S.cur_row_base + S.cur_rows;
+    if (live) {
+      const uint32_t *row = lvl + S.cur_word_base + (it - S.cur_row_base) * (s + 1);
+      JoinCtx c;
+      if (join_setup(W, Q, s, row, c)) {
+        const bool final = Q.k == s + 2;
+        const uint32_t *d = c.lst[c.drive];
+        for (uint32_t j = r; j < c.len[c.drive]; j += G) {
+          const uint32_t cand = d[j];
+          if (join_ok(c, row, s, cand)) {
+            cnt++;
+            if (final) fp += row_hash(Q, row, c.w, cand);
+          }
+        }
+        bytes = 4ull * (s + 1) + 4ull * c.len[c.drive] + 24ull * c.nedge;
+      }
+    }
+    for (int o = G / 2; o; o >>= 1) {
+      cnt += tile.shfl_down(cnt, o);
+      fp += tile.shfl_down(fp, o);
+    }
+    if (r == 0) {
+      W.row_cnt[it] = cnt;
+      if (live && Q.k == s + 2) {
+        if (cnt) atomicAdd((unsigned long long *)&S.count, (unsigned long long)cnt);
+        if (fp) atomicAdd((unsigned long long *)&S.fp, (unsigned long long)fp);
+      }
+      add_bytes(W, KK_JOIN_COUNT, bytes);
+    }
+  }
+}
+
+// Rows produced per query (scan of the per-row counts), and the current
+// level kept aside as the source of the write pass.
+__global__ void k_join_totals(Wave W) {
+  for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
+    QState &S = W.qs[qi];
+    S.nxt_rows = S.cur_rows ? W.row_scan[S.cur_row_base + S.cur_rows] - W.row_scan[S.cur_row_base] : 0;
+    W.src[qi] = SrcRows{S.cur_row_base, S.cur_rows, S.cur_word_base};
+  }
+  if (gtid() == 0) W.ctrl->len[4] = W.ctrl->len[3];
+}
+
+// Write pass of level s -> s+1 into the layout made by k_level_alloc.
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_join_write(Wave W, uint32_t s) {
+  auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+  const uint32_t r = tile.thread_rank();
+  const uint64_t ntile = gthreads() / G;
+  const uint64_t items = W.ctrl->len[4];
+  const uint32_t *lvl = W.lvl[s & 1];
+  uint32_t *nxt = W.lvl[(s + 1) & 1];
+  for (uint64_t it = gtid() / G; it < items; it += ntile) {
+    const uint32_t qi = seg_of_src(W.src, W.nq, it);
+    const DQuery &Q = W.dq[qi];
+    const QState &S = W.qs[qi];
+    const SrcRows R = W.src[qi];
+    if (Q.status != QS_OK || it >= R.row_base + R.rows) continue;
+    const bool final = Q.k == s + 2;
+    const uint32_t width = s + 2;
+    uint32_t *dst;
+    uint64_t rbase;
+    if (final) {
+      if (S.out_rows == 0) continue;
+      dst = W.out + S.out_word_base;
+      rbase = S.out_row_base;
+    } else {
+      dst = nxt + S.cur_word_base;
+      rbase = 0;
+    }
+    const uint32_t *row = lvl + R.word_base + (it - R.row_base) * (s + 1);
+    uint64_t p = W.row_scan[it] - W.row_scan[R.row_base];
+    JoinCtx c;
+    if (!join_setup(W, Q, s, row, c)) continue;
+    const uint32_t *d = c.lst[c.drive];
+    uint64_t written = 0;
+    for (uint32_t b = 0; b < c.len[c.drive]; b += G) {
+      const uint32_t j = b + r;
+      const uint32_t cand = j < c.len[c.drive] ? d[j] : 0;
+      const bool ok = j < c.len[c.drive] && join_ok(c, row, s, cand);
+      const uint32_t m = tile.ballot(ok);
+      if (ok) {
+        const uint64_t at = p + __popc(m & ((1u << r) - 1));
+        uint32_t *o = dst + at * width;
+        for (uint32_t i = 0; i <= s; ++i) o[i] = row[i];
+        o[s + 1] = cand;
+        if (final) W.out_q[rbase + at] = qi;
+      }
+      p += __popc(m);
+      written += __popc(m);
+    }
+    if (r == 0)
+      add_bytes(W, KK_JOIN_WRITE, 4ull * written * width + 4ull * (s + 1) + 4ull * c.len[c.drive] + 24ull * c.nedge);
+  }
+}
+
+// Query-order layout of the sorted rows.
+__global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
+  __shared__ uint64_t sm[2][32];
+  __shared__ uint64_t carry[2];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) { carry[0] = 0; carry[1] = 0; }
+  __syncthreads();
+  for (uint32_t base = 0; base < W.nq; base += blockDim.x) {
+    const uint32_t qi = base + threadIdx.x;
+    uint64_t v[2] = {0, 0}, ex[2];
+    if (qi < W.nq && W.dq[qi].status == QS_OK) {
+      v[0] = W.qs[qi].out_rows;
+      v[1] = W.qs[qi].out_rows * W.dq[qi].k;
+    }
+    for (int a = 0; a < 2; ++a) {
+      uint64_t x = v[a];
+      for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) sm[a][warp] = x;
+      ex[a] = x - v[a];
+    }
+    __syncthreads();
+    if (warp < 2) {
+      uint64_t x = sm[warp][lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+      }
+      sm[warp][lane] = x;
+    }
+    __syncthreads();
+    if (qi < W.nq) {
+      W.qs[qi].fin_row_base = carry[0] + ex[0] + (warp ? sm[0][warp - 1] : 0);
+      W.qs[qi].fin_word_base = carry[1] + ex[1] + (warp ? sm[1][warp - 1] : 0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { carry[0] += sm[0][31]; carry[1] += sm[1][31]; }
+    __syncthreads();
+  }
+}
+
+// ============================================================ sort + gather
+__global__ void k_iota(Wave W, uint32_t *perm) {
+  const uint64_t n = W.ctrl->out_rows_total;
+  for (uint64_t i = gtid(); i < n; i += gthreads()) perm[i] = (uint32_t)i;
+}
+
+// key[i] = id of query vertex `col` in output row perm[i] (0 past the row's
+// width), or the slot query when col == kMaxK (the most significant pass).
+__global__ void k_sort_keys(Wave W, const uint32_t *perm, uint32_t *key, uint32_t col) {
+  const uint64_t n = W.ctrl->out_rows_total;
+  for (uint64_t i = gtid(); i < n; i += gthreads()) {
+    const uint32_t row = perm[i];
+    const uint32_t qi = W.out_q[row];
+    if (col == kMaxK) { key[i] = qi; continue; }
+    const DQuery &Q = W.dq[qi];
+    const QState &S = W.qs[qi];
+    key[i] = col < Q.k ? W.out[S.out_word_base + (uint64_t)(row - S.out_row_base) * Q.k + Q.pos[col]] : 0;
+  }
+}
+
+// Sorted rows in query-vertex column order, laid out query by query.
+__global__ void k_gather(Wave W, const uint32_t *perm) {
+  const uint64_t n = W.ctrl->out_rows_total;
+  for (uint64_t i = gtid(); i < n; i += gthreads()) {
+    const uint32_t row = perm[i];
+    const uint32_t qi = W.out_q[row];
+    const DQuery &Q = W.dq[qi];
+    const QState &S = W.qs[qi];
+    const uint32_t *src = W.out + S.out_word_base + (uint64_t)(row - S.out_row_base) * Q.k;
+    uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.fin_row_base) * Q.k;
+    for (uint32_t u = 0; u < Q.k; ++u) dst[u] = src[Q.pos[u]];
+  }
+}
+
+// Epilogue: per-query results and rows of this wave into the batch store.
+__global__ void k_epilogue_copy(Wave W) {
+  const WaveDesc D = W.waves[W.ctrl->wave];
+  const uint64_t top = W.ctrl->store_top, words = W.ctrl->out_top;
+  const bool fits = top + words <= W.bo.store_cap;
+  for (uint64_t qi = gtid(); qi < D.nq; qi += gthreads()) {
+    const uint64_t b = D.q0 + qi;
+    const DQuery &Q = W.dq[qi];
+    const QState &S = W.qs[qi];
+    uint32_t st = Q.status;
+    if (st == QS_OK && S.out_rows && !fits) st = QS_OVERFLOW;
+    W.bo.count[b] = S.count;
+    W.bo.fp[b] = S.fp;
+    W.bo.status[b] = st;
+    W.bo.nrows[b] = st == QS_OK ? S.out_rows : 0;
+    W.bo.word_off[b] = top + S.fin_word_base;
+  }
+  if (fits)
+    for (uint64_t i = gtid(); i < words; i += gthreads()) W.bo.store[top + i] = W.out_final[i];
+}
+
+__global__ void k_epilogue_advance(Wave W) {
+  const uint64_t top = W.ctrl->store_top, words = W.ctrl->out_top;
+  if (top + words <= W.bo.store_cap) W.ctrl->store_top = top + words;
+  W.ctrl->wave += 1;
+}
+
+inline unsigned grid_for(int sms, int per_sm) { return (unsigned)(sms * per_sm); }
+inline unsigned blocks_for(uint64_t n, unsigned per) {
+  uint64_t b = (n + per - 1) / per;
+  return (unsigned)(b ? b : 1);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+void launch_prologue(const Wave &W, cudaStream_t s, int sms) {
+  k_prologue<<<grid_for(sms, 2), kThreads, 0, s>>>(W);
+}
+void launch_plan(const Wave &W, const uint32_t *type_count, cudaStream_t s, int sms) {
+  k_plan<<<blocks_for(W.nq + 1, 128), 128, 0, s>>>(W, type_count);
+  k_owners<<<blocks_for(W.nq, 128), 128, 0, s>>>(W);
+}
+void launch_filter(const Wave &W, cudaStream_t s, int sms) { k_filter<<<grid_for(sms, 8), kThreads, 0, s>>>(W); }
+void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms) {
+  k_compact_count<<<grid_for(sms, 8), kThreads, 0, s>>>(W, mode, step);
+}
+void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint64_t cap,
+                          cudaStream_t s, int sms) {
+  k_compact_write<<<grid_for(sms, 8), kThreads, 0, s>>>(W, mode, step, scan, dst, cap);
+}
+void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms) {
+  const unsigned g = grid_for(sms, 8);
+  switch (group) {
+    case 8: k_explore<8><<<g, kThreads, 0, s>>>(W, step); break;
+    case 16: k_explore<16><<<g, kThreads, 0, s>>>(W, step); break;
+    default: k_explore<32><<<g, kThreads, 0, s>>>(W, step); break;
+  }
+}
+void launch_refine(const Wave &W, uint32_t round, int group, cudaStream_t s, int sms) {
+  const unsigned g = grid_for(sms, 8);
+  switch (group) {
+    case 8: k_refine<8><<<g, kThreads, 0, s>>>(W, round); break;
+    case 16: k_refine<16><<<g, kThreads, 0, s>>>(W, round); break;
+    default: k_refine<32><<<g, kThreads, 0, s>>>(W, round); break;
+  }
+}
+void launch_list_table(const Wave &W, cudaStream_t s, int sms) {
+  k_list_table<<<blocks_for(W.nqv, kThreads), kThreads, 0, s>>>(W);
+}
+void launch_join_plan(const Wave &W, cudaStream_t s, int sms) { k_join_plan<<<blocks_for(W.nq, 64), 64, 0, s>>>(W); }
+void launch_ec_limit(const Wave &W, cudaStream_t s, int sms) {
+  k_ec_limit<<<blocks_for(W.nqe, kThreads), kThreads, 0, s>>>(W);
+}
+void launch_ec(const Wave &W, bool write, int group, cudaStream_t s, int sms) {
+  const unsigned g = grid_for(sms, 8);
+  switch (group) {
+    case 8: if (write) k_ec<8, true><<<g, kThreads, 0, s>>>(W); else k_ec<8, false><<<g, kThreads, 0, s>>>(W); break;
+    case 16: if (write) k_ec<16, true><<<g, kThreads, 0, s>>>(W); else k_ec<16, false><<<g, kThreads, 0, s>>>(W); break;
+    default: if (write) k_ec<32, true><<<g, kThreads, 0, s>>>(W); else k_ec<32, false><<<g, kThreads, 0, s>>>(W); break;
+  }
+}
+void launch_clear(const Wave &W, cudaStream_t s, int sms) { k_clear<<<grid_for(sms, 8), kThreads, 0, s>>>(W); }
+void launch_join0(const Wave &W, cudaStream_t s, int sms) {
+  k_join0_rows<<<blocks_for(W.nq, 256), 256, 0, s>>>(W);
+  k_level_alloc<<<1, 1024, 0, s>>>(W, 0);
+  k_join0_write<<<grid_for(sms, 4), kThreads, 0, s>>>(W);
+}
+void launch_join_count(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms) {
+  const unsigned g = grid_for(sms, 8);
+  switch (group) {
+    case 8: k_join_count<8><<<g, kThreads, 0, s>>>(W, lvl); break;
+    case 16: k_join_count<16><<<g, kThreads, 0, s>>>(W, lvl); break;
+    default: k_join_count<32><<<g, kThreads, 0, s>>>(W, lvl); break;
+  }
+}
+void launch_join_totals(const Wave &W, cudaStream_t s, int sms) {
+  k_join_totals<<<blocks_for(W.nq, 256), 256, 0, s>>>(W);
+}
+void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s) { k_level_alloc<<<1, 1024, 0, s>>>(W, lvl); }
+void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms) {
+  const unsigned g = grid_for(sms, 8);
+  switch (group) {
+    case 8: k_join_write<8><<<g, kThreads, 0, s>>>(W, lvl); break;
+    case 16: k_join_write<16><<<g, kThreads, 0, s>>>(W, lvl); break;
+    default: k_join_write<32><<<g, kThreads, 0, s>>>(W, lvl); break;
+  }
+}
+void launch_final_bases(const Wave &W, cudaStream_t s) { k_final_bases<<<1, 1024, 0, s>>>(W); }
+void launch_iota(const Wave &W, uint32_t *perm, cudaStream_t s, int sms) { k_iota<<<grid_for(sms, 4), kThreads, 0, s>>>(W, perm); }
+void launch_sort_keys(const Wave &W, const uint32_t *perm, uint32_t *key, uint32_t col, cudaStream_t s, int sms) {
+  k_sort_keys<<<grid_for(sms, 4), kThreads, 0, s>>>(W, perm, key, col);
+}
+void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms) {
+  k_gather<<<grid_for(sms, 4), kThreads, 0, s>>>(W, perm);
+}
+void launch_epilogue(const Wave &W, cudaStream_t s, int sms) {
+  k_epilogue_copy<<<grid_for(sms, 4), kThreads, 0, s>>>(W);
+  k_epilogue_advance<<<1, 1, 0, s>>>(W);
+}
+
+}  // namespace gs

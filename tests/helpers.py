@@ -112,3 +112,7 @@ def parse_worked_example(path=None):
         elif key == "expect_count":
             d[key] = int(toks[0])
     return d
+
+
+def complete_digraph_triples(n, rel=0):
+    return [(s, rel, d) for s in range(n) for d in range(n) if s != d]

@@ -1,0 +1,201 @@
+"""Parity of the CUDA engine with the CPU oracle, through the C ABI.
+
+Integer work: every comparison is exact (counts, fingerprints, the sorted
+embedding rows, candidate sets, candidate-edge tables)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1807_08804_gb300 as gs
+from paper_1807_08804_gb300 import inputs as I
+from tests.helpers import complete_digraph_triples, graph_from_triples, query, random_tiny
+
+pytestmark = pytest.mark.gpu
+
+
+def assert_same(r, o, ctx=""):
+    assert r.status == 0, (ctx, r.status)
+    assert r.count == o.count, (ctx, r.count, o.count)
+    assert r.fingerprint == o.fingerprint, (ctx, r.fingerprint, o.fingerprint)
+    np.testing.assert_array_equal(r.rows, o.rows, err_msg=str(ctx))
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = I.WORKLOADS["single-10k"]
+    g = w.graph()
+    qs = w.queries(g)
+    return g, qs, O.OracleGraph.from_graph(g), gs.DeviceGraph(g)
+
+
+def test_graph_canonicalisation_counts_distinct_triples(small):
+    g, _, og, dg = small
+    assert dg.num_edges == og.E
+
+
+def test_small_workload_batch_bit_exact(small):
+    g, qs, og, dg = small
+    res = gs.match_batch(dg, qs, cap=1 << 20)
+    for i, (q, r) in enumerate(zip(qs, res)):
+        assert_same(r, O.match(og, q, cap=1 << 20), i)
+
+
+def test_small_workload_one_at_a_time(small):
+    g, qs, og, dg = small
+    for i, q in enumerate(qs[:25]):
+        assert_same(gs.match(dg, q, cap=1 << 20), O.match(og, q, cap=1 << 20), i)
+
+
+def test_filter_kernel_candidates(small):
+    g, qs, og, dg = small
+    for q in qs[:30]:
+        got = gs.inspect_candidates(dg, q, gs.GS_STAGE_FILTER)
+        want = O.candidates(og, q, signature=True)
+        for u in range(q.k):
+            np.testing.assert_array_equal(got[u], np.flatnonzero(want[u]).astype(np.uint32))
+
+
+def test_refinement_fixpoint(small):
+    g, qs, og, dg = small
+    for q in qs[:30]:
+        got = gs.inspect_candidates(dg, q, gs.GS_STAGE_FIXPOINT)
+        want = O.fixpoint(og, q)
+        for u in range(q.k):
+            np.testing.assert_array_equal(got[u], np.flatnonzero(want[u]).astype(np.uint32))
+
+
+def test_edge_tables(small):
+    g, qs, og, dg = small
+    for q in qs[:20]:
+        fix = O.fixpoint(og, q)
+        for e in range(q.m):
+            for from_src in (True, False):
+                k1, o1, v1 = gs.inspect_edge_table(dg, q, e, from_src)
+                k2, o2, v2 = O.edge_table(og, q, fix, e, from_src)
+                np.testing.assert_array_equal(k1, k2)
+                np.testing.assert_array_equal(o1, o2)
+                np.testing.assert_array_equal(v1, v2)
+
+
+def test_tiny_random_instances_against_brute_force():
+    rng = np.random.default_rng(2024)
+    for case in range(120):
+        g, q = random_tiny(rng)
+        o = O.OracleGraph.from_graph(g)
+        dg = gs.DeviceGraph(g)
+        want = O.brute(o, q, cap=1 << 16)
+        got = gs.match_batch(dg, [q, q], cap=1 << 16)
+        for r in got:
+            assert_same(r, want, case)
+        dg.free()
+
+
+def test_closed_forms():
+    from math import comb, perm
+    n = 9
+    dg = gs.DeviceGraph(graph_from_triples(n, complete_digraph_triples(n)))
+    for k in (2, 3, 4, 5):
+        path = query(k, [(i, i + 1, 0) for i in range(k - 1)])
+        cyc = query(k, [(i, (i + 1) % k, 0) for i in range(k)]) if k > 2 else path
+        for r in gs.match_batch(dg, [path, cyc], cap=0, mode=gs.GS_COUNT_ONLY):
+            assert r.count == perm(n, k)
+    tt = gs.DeviceGraph(graph_from_triples(10, [(i, 0, j) for i in range(10) for j in range(10) if i < j]))
+    for k in (3, 4, 5):
+        path = query(k, [(i, i + 1, 0) for i in range(k - 1)])
+        cyc = query(k, [(i, (i + 1) % k, 0) for i in range(k)])
+        clique = query(k, [(i, j, 0) for i in range(k) for j in range(i + 1, k)])
+        r = gs.match_batch(tt, [path, cyc, clique], cap=0, mode=gs.GS_COUNT_ONLY)
+        assert [x.count for x in r] == [comb(10, k), 0, comb(10, k)]
+    star = gs.DeviceGraph(graph_from_triples(8, [(0, 0, i) for i in range(1, 8)]))
+    for s in (1, 3, 5, 7, 8):
+        r = gs.match(star, query(s + 1, [(0, i, 0) for i in range(1, s + 1)]), cap=0, mode=gs.GS_COUNT_ONLY)
+        assert r.count == (perm(7, s) if s <= 7 else 0)
+
+
+def test_results_invariant_to_schedule(small):
+    g, qs, og, dg = small
+    sub = qs[:40]
+    base = gs.match_batch(dg, sub, cap=1 << 20)
+    for group in (8, 16, 32):
+        for use_graph in (True, False):
+            for rounds in (0, 1, 3):
+                b = gs.Batch(dg, sub, cap=1 << 20)
+                b.configure(use_graph=use_graph, group=group, refine_rounds=rounds)
+                b.run()
+                b.finish()
+                for i, (x, y) in enumerate(zip(b.fetch(), base)):
+                    assert (x.count, x.fingerprint) == (y.count, y.fingerprint), (group, use_graph, rounds, i)
+                    np.testing.assert_array_equal(x.rows, y.rows)
+                b.close()
+    b = gs.Batch(dg, sub, cap=1 << 20, wave_queries=1)
+    for rep in range(2):  # a replayed batch gives the same results
+        b.run()
+        b.finish()
+        for x, y in zip(b.fetch(), base):
+            assert (x.count, x.fingerprint) == (y.count, y.fingerprint)
+            np.testing.assert_array_equal(x.rows, y.rows)
+    b.close()
+
+
+def test_count_only_mode(small):
+    g, qs, og, dg = small
+    a = gs.match_batch(dg, qs[:50], cap=1 << 20)
+    b = gs.match_batch(dg, qs[:50], cap=0, mode=gs.GS_COUNT_ONLY)
+    for x, y in zip(a, b):
+        assert (x.count, x.fingerprint) == (y.count, y.fingerprint)
+        assert y.rows.shape[0] == 0
+
+
+def test_edge_cases(small):
+    g, qs, og, dg = small
+    V = g.num_vertices
+    single = query(1, [], vtype=[3])
+    bound_wrong = query(2, [(0, 1, 0)], vtype=[I.ANY, I.ANY], vbind=[0, 0])  # same id twice: 0 embeddings
+    self_loop = query(2, [(0, 0, 0)])
+    disconnected = query(3, [(0, 1, 0)])
+    out_of_range = query(2, [(0, 1, 0)], vbind=[V, I.UNBOUND])
+    res = gs.match_batch(dg, [single, bound_wrong, self_loop, disconnected, out_of_range, qs[0]], cap=1 << 20)
+    assert_same(res[0], O.match(og, single, cap=1 << 20))
+    assert res[1].status == 0 and res[1].count == 0 and res[1].rows.shape[0] == 0
+    assert res[2].status == gs.GS_ERR_INVALID
+    assert res[3].status == gs.GS_ERR_UNSUPPORTED
+    assert res[4].status == gs.GS_ERR_INVALID
+    assert_same(res[5], O.match(og, qs[0], cap=1 << 20))
+    with pytest.raises(gs.GSError):
+        gs.match(dg, self_loop)
+    assert gs.match_batch(dg, [], cap=1) == []
+
+
+@pytest.fixture(scope="module")
+def scale_1m():
+    w = I.WORKLOADS["single-1m"]
+    g = w.graph()
+    qs = w.queries(g)
+    return g, qs, O.OracleGraph.from_graph(g), gs.DeviceGraph(g)
+
+
+def test_scale_1m_batch_against_oracle(scale_1m):
+    """The 1M-vertex / 8M-edge workload at full size, in the batched launch
+    configuration the benchmark times: all 1,000 queries' counts and
+    fingerprints, rows for a sample."""
+    g, qs, og, dg = scale_1m
+    res = gs.match_batch(dg, qs, cap=1 << 22)
+    cnt, fp, st, _ = O.match_many(og, qs, threads=0, time_limit_s=60.0)
+    assert (st == 0).all()
+    for i, r in enumerate(res):
+        assert r.status == 0
+        assert (r.count, r.fingerprint) == (int(cnt[i]), int(fp[i])), i
+    rng = np.random.default_rng(1)
+    for i in rng.choice(len(qs), 60, replace=False):
+        assert_same(res[i], O.match(og, qs[i], cap=1 << 22), i)
+
+
+def test_scale_1m_one_at_a_time_waves(scale_1m):
+    g, qs, og, dg = scale_1m
+    sub = qs[:100]
+    b = gs.Batch(dg, sub, cap=1 << 22, wave_queries=1)
+    b.run()
+    b.finish()
+    for i, r in enumerate(b.fetch()):
+        assert_same(r, O.match(og, sub[i], cap=1 << 22), i)
+    b.close()
