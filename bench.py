@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark: exact labeled subgraph matching on one GB300 (or N replicas).
+
+One step = the whole device pipeline (plan, filter, exploration, refinement,
+candidate-edge tables, join, sort) over one batch of queries: by default the
+1,000 queries of 4-10 vertices on the 1M-vertex / 8M-edge graph.  Prints one
+JSON line.
+
+  value   queries/s of the batched pipeline, inputs resident in HBM
+          (CUDA events on the launching stream; L2 flushed between steps)
+  e2e     the same metric through gs_match_batch with host buffers
+          (query upload and result download inside the timed region)
+  one_at_a_time   queries/s when the same device pipeline runs each query
+                  as its own wave (the baseline the batching is measured against)
+
+--impl reference times the CPU oracle (test infrastructure) on the same
+workload on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/s and embeddings/s, batched vs one-at-a-time (exact); serving p50/p99 ms"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i, v in enumerate(r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(workload, g, qs, sample_n=None):
+    """The oracle as it stands, counts and fingerprints, on every host core."""
+    import oracle
+    og = oracle.OracleGraph.from_graph(g)
+    sample = qs if sample_n is None else qs[:sample_n]
+    t = time.perf_counter()
+    cnt, fp, st, used = oracle.match_many(og, sample, threads=0, time_limit_s=60.0)
+    dt = time.perf_counter() - t
+    return {"value": len(sample) / dt, "unit": "queries/s", "cores": int(used), "kind": "oracle",
+            "sample": f"{len(sample)} of the {len(qs)} queries of {workload.name} (counts and fingerprints, "
+                      f"all embeddings enumerated), {dt:.2f} s, {int((st == 2).sum())} timed out",
+            "embeddings_per_s": float(cnt.sum()) / dt}
+
+
+def serve_measure(gs, dg, qs, rate_qps, duration_s, cap, seed=1):
+    """Poisson arrivals at rate_qps for duration_s into the serving loop;
+    latency is submit-to-completion as the server observes it."""
+    from paper_1807_08804_gb300 import inputs as I
+    n = max(1, int(rate_qps * duration_s))
+    arr = I.make_arrivals(n, rate_qps, seed=seed)
+    pack = gs._QueryPack(qs)
+    srv = gs.Server(dg, slots=4, max_batch=256)
+    tickets = []
+    t0 = time.perf_counter()
+    for i in range(n):
+        while time.perf_counter() - t0 < arr[i]:
+            pass
+        tickets.append(srv.submit_packed(pack, i % len(qs), cap=cap))
+    submit_end = time.perf_counter() - t0
+    lat = []
+    pending = list(tickets)
+    deadline = time.perf_counter() + 120
+    while pending and time.perf_counter() < deadline:
+        rest = []
+        for t in pending:
+            r = srv.poll(t)
+            if r is None:
+                rest.append(t)
+            else:
+                lat.append(r[1])
+        pending = rest
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat.sort()
+    q = lambda p: 1e3 * lat[min(len(lat) - 1, int(p * len(lat)))] if lat else None
+    return {"offered_qps": rate_qps, "requests": n, "completed": len(lat), "p50_ms": q(0.50), "p99_ms": q(0.99),
+            "p999_ms": q(0.999), "sustained_qps": len(lat) / max(wall, submit_end), "submit_s": submit_end}
+
+
+def run_reference(args, world, rank):
+    from paper_1807_08804_gb300 import inputs as I
+    import oracle
+    if rank != 0:
+        return
+    w = I.WORKLOADS[args.workload]
+    g = w.graph()
+    qs = w.queries(g)
+    og = oracle.OracleGraph.from_graph(g)
+    per_step = qs if args.ref_sample is None else qs[:args.ref_sample]
+    for _ in range(args.warmup):
+        oracle.match_many(og, per_step, threads=0, time_limit_s=60.0)
+    times, used, emb = [], 1, 0
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        cnt, fp, st, used = oracle.match_many(og, per_step, threads=0, time_limit_s=60.0)
+        times.append(time.perf_counter() - t)
+        emb = int(cnt.sum())
+    tot = sum(times)
+    value = len(per_step) * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": w.name, "vertices": w.V, "edges": w.E, "queries": len(per_step),
+                       "query_vertices": [w.kmin, w.kmax], "p_bind": w.p_bind, "cap": w.cap},
+            "embeddings_per_s": emb * args.steps / tot,
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": int(used), "kind": "oracle",
+                             "sample": f"{len(per_step)} queries per step (the whole workload), counts and "
+                                       f"fingerprints"},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--workload", default="single-1m")
+    ap.add_argument("--one-steps", type=int, default=2, help="steps of the one-query-at-a-time comparison")
+    ap.add_argument("--ref-sample", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of arrivals per serving rate (0 = skip)")
+    ap.add_argument("--mode", default=None, choices=["enumerate", "count"],
+                    help="enumerate rows (default) or count only (default for stress-16m)")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import paper_1807_08804_gb300 as gs
+    from paper_1807_08804_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = I.WORKLOADS[args.workload]
+    g = w.graph()
+    qs = w.queries(g)
+    n = len(qs)
+    mode = args.mode or ("count" if w.shapes else "enumerate")
+    gmode = gs.GS_COUNT_ONLY if mode == "count" else gs.GS_ENUMERATE
+    cap = 0 if mode == "count" else w.cap
+    dg = gs.DeviceGraph(g)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    b = gs.Batch(dg, qs, cap=cap, mode=gmode, stream=sh)
+    one = gs.Batch(dg, qs, cap=cap, mode=gmode, wave_queries=1, stream=sh)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    for _ in range(max(args.warmup, 3)):
+        b.run()
+        b.finish()  # finishes queries that need the chunked path too
+    res = b.fetch()
+    embeddings = sum(r.count for r in res)
+    bad = [i for i, r in enumerate(res) if r.status != 0]
+    fallback_needed = b.counters().get("fallback_queries", 0) > 0
+    if args.one_steps:
+        one.run()
+        one.finish()
+        ref = one.fetch()
+        assert all((x.count, x.fingerprint) == (y.count, y.fingerprint) for x, y in zip(res, ref)), "modes disagree"
+
+    # ---- timed region: batched pipeline, device-resident inputs
+    b.stats_enable(True)
+    b.run()
+    b.finish()
+    b.stats_reset()
+    launches0 = b.counters()["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run()
+        if fallback_needed:
+            b.finish()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    b.finish()
+    launches = b.counters()["kernel_launches"] - launches0
+    stats = b.stats()
+    tot_ms = max_over_ranks(sum(step_ms), world, dev)
+    value = n * world * args.steps / (tot_ms / 1e3)
+
+    # ---- one query at a time through the same pipeline
+    one_ms = []
+    for _ in range(args.one_steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one.run()
+        e1.record(stream)
+        e1.synchronize()
+        one_ms.append(e0.elapsed_time(e1))
+    one.finish()
+    one_tot = max_over_ranks(sum(one_ms), world, dev)
+    one_qps = n * world * args.one_steps / (one_tot / 1e3) if args.one_steps else None
+
+    # ---- end to end through the public API with host buffers
+    h0, d0 = dg.io_bytes()
+    gs.match_batch(dg, qs, cap=cap, mode=gmode)  # warm the reusable pools
+    h0, d0 = dg.io_bytes()
+    barrier(world)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    e2e_steps = max(2, args.steps // 2)
+    for _ in range(e2e_steps):
+        out = gs.match_batch(dg, qs, cap=cap, mode=gmode)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t, world, dev)
+    h1, d1 = dg.io_bytes()
+    assert sum(r.count for r in out) == embeddings
+
+    # ---- serving: continuous batching under Poisson arrivals
+    rates = w.qps if w.qps else (20000.0,)
+    serving = ([serve_measure(gs, dg, qs, r, args.serve_seconds, cap) for r in rates]
+               if args.serve_seconds > 0 and not w.shapes else [])
+
+    # ---- roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    kinds = {k: v for k, v in stats.items() if v["launches"] and v["bytes"]}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"]) if kinds else None
+    roof = None
+    if dom:
+        achieved = kinds[dom]["bytes"] / (kinds[dom]["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "bytes_per_launch": kinds[dom]["bytes"] / kinds[dom]["launches"],
+                "ms_per_launch": kinds[dom]["ms"] / kinds[dom]["launches"]}
+
+    line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": w.name, "vertices": w.V, "edges": w.E, "queries": n, "mode": mode,
+                       "query_vertices": [w.kmin, w.kmax], "p_bind": w.p_bind, "cap": cap,
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "embeddings_per_s": embeddings * world * args.steps / (tot_ms / 1e3),
+            "embeddings_per_step": embeddings,
+            "one_at_a_time": ({"value": one_qps, "unit": "queries/s", "ms_per_step": one_tot / args.one_steps,
+                               "speedup_batched": value / one_qps} if one_qps else None),
+            "e2e": {"value": n * world * e2e_steps / e2e_s, "unit": "queries/s",
+                    "h2d_bytes_per_step": (h1 - h0) // e2e_steps, "d2h_bytes_per_step": (d1 - d0) // e2e_steps},
+            "gpu_launches": launches,
+            "serving": serving,
+            "roofline": roof,
+            "clocks": clk,
+            "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in stats.items() if v["launches"]},
+            "fallback_queries": b.counters().get("fallback_queries", 0), "failed_queries": len(bad)}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, g, qs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    one.close()
+    dg.free()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

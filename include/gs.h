@@ -132,7 +132,14 @@ gs_status gs_match_batch(gs_graph *g, const gs_query *qs, uint32_t n, const gs_m
                          gs_result *outs);
 
 void gs_result_free(gs_result *r);
+/* gs_result_free on each of r[0..n). */
+void gs_results_free(gs_result *r, uint32_t n);
 const char *gs_last_error(void);
+
+/* Bytes copied host->device and device->host by all gs_match and
+ * gs_match_batch calls on this graph so far (query descriptors in; counts,
+ * fingerprints and rows out). */
+gs_status gs_graph_io_bytes(gs_graph *g, uint64_t *h2d, uint64_t *d2h);
 
 /* ------------------------------------------------------------------------
  * Prepared batches: the queries are validated, packed and uploaded once; each
@@ -151,6 +158,17 @@ gs_status gs_batch_finish(gs_batch *b);
 /* Copy results of the last finished run to the host (outs[n]). */
 gs_status gs_batch_fetch(gs_batch *b, gs_result *outs);
 void gs_batch_destroy(gs_batch *b);
+/* Waves of `wave_queries` queries each: every phase runs per wave (1 = one
+ * query at a time through the same device pipeline). */
+gs_status gs_batch_create_waves(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
+                                uint32_t wave_queries, gs_batch **out);
+/* Execution knobs: captured graph or direct launches, lanes per work item
+ * (8, 16 or 32), refinement rounds (0 = until nothing changes). */
+gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_t refine_rounds);
+/* Kernels launched by runs so far, bytes moved between host and device, and
+ * queries finished on the host-driven chunked path by the last finish. */
+gs_status gs_batch_counters(gs_batch *b, uint64_t *kernel_launches, uint64_t *h2d, uint64_t *d2h,
+                            uint64_t *fallback_queries);
 
 /* Per-kernel statistics accumulated by runs since the last reset:
  * launches, device time (CUDA events) and algorithmic bytes.  Timing is

@@ -76,6 +76,7 @@ SIGNATURES = {
     "gs_match_batch": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts),
                                       ctypes.POINTER(ResultDesc)]),
     "gs_result_free": (None, [ctypes.POINTER(ResultDesc)]),
+    "gs_results_free": (None, [ctypes.POINTER(ResultDesc), U32]),
     "gs_last_error": (ctypes.c_char_p, []),
     "gs_batch_create": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts), ctypes.POINTER(P)]),
     "gs_batch_run": (ctypes.c_int, [P]),
@@ -98,6 +99,9 @@ EXTRA_SIGNATURES = {
     "gs_batch_create_waves": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts), U32,
                                              ctypes.POINTER(P)]),
     "gs_batch_set": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, U32]),
+    "gs_batch_counters": (ctypes.c_int, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64),
+                                         ctypes.POINTER(U64)]),
+    "gs_graph_io_bytes": (ctypes.c_int, [P, ctypes.POINTER(U64), ctypes.POINTER(U64)]),
 }
 
 _lib = None
@@ -136,16 +140,36 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(P)
 
 
+_QDESC_DTYPE = np.dtype({"names": ["k", "m", "vtype", "vbind", "esrc", "edst", "erel"],
+                         "formats": ["<u4", "<u4", "<u8", "<u8", "<u8", "<u8", "<u8"],
+                         "offsets": [0, 4, 8, 16, 24, 32, 40], "itemsize": 48})
+
+
 class _QueryPack:
-    """Queries as a ctypes array; keeps the numpy buffers alive."""
+    """Queries as an array of gs_query structs over five flat id arrays (built
+    with vectorised numpy, no per-query ctypes objects)."""
 
     def __init__(self, queries):
-        self.keep = []
-        self.arr = (QueryDesc * max(len(queries), 1))()
-        for i, q in enumerate(queries):
-            a = [_u32(q.vtype), _u32(q.vbind), _u32(q.esrc), _u32(q.edst), _u32(q.erel)]
-            self.keep.append(a)
-            self.arr[i] = QueryDesc(a[0].shape[0], a[2].shape[0], *[_ptr(x) for x in a])
+        n = len(queries)
+        ks = np.fromiter((len(q.vtype) for q in queries), np.int64, n)
+        ms = np.fromiter((len(q.esrc) for q in queries), np.int64, n)
+        cat = lambda f: np.ascontiguousarray(np.concatenate(
+            [np.asarray(getattr(q, f), np.uint32).ravel() for q in queries] + [np.zeros(1, np.uint32)]))
+        self.flat = [cat("vtype"), cat("vbind"), cat("esrc"), cat("edst"), cat("erel")]
+        voff = np.zeros(n, np.uint64)
+        eoff = np.zeros(n, np.uint64)
+        if n:
+            voff[1:] = np.cumsum(ks[:-1]) * 4
+            eoff[1:] = np.cumsum(ms[:-1]) * 4
+        d = np.zeros(max(n, 1), _QDESC_DTYPE)
+        if n:
+            d["k"][:n] = ks
+            d["m"][:n] = ms
+            for name, arr, o in zip(("vtype", "vbind", "esrc", "edst", "erel"), self.flat,
+                                    (voff, voff, eoff, eoff, eoff)):
+                d[name][:n] = np.uint64(arr.ctypes.data) + o
+        self.desc = d
+        self.arr = ctypes.cast(d.ctypes.data, ctypes.POINTER(QueryDesc))
 
 
 def _opts(cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0, stream=None) -> MatchOpts:
@@ -165,9 +189,36 @@ def _take(r: ResultDesc) -> MatchResult:
     n, k = int(r.num_rows), int(r.k)
     rows = np.zeros((n, k), np.uint32)
     if n:
-        rows[:] = np.ctypeslib.as_array(r.rows, shape=(n * k,)).reshape(n, k)
+        ctypes.memmove(rows.ctypes.data, r.rows, 4 * n * k)
     out = MatchResult(int(r.count), int(r.fingerprint), rows, bool(r.truncated), int(r.status))
     lib().gs_result_free(ctypes.byref(r))
+    return out
+
+
+_RES_DTYPE = np.dtype({"names": ["count", "num_rows", "fingerprint", "k", "truncated", "rows", "status"],
+                       "formats": ["<u8", "<u8", "<u8", "<u4", "<u4", "<u8", "<u4"],
+                       "offsets": [0, 8, 16, 24, 28, 32, 40], "itemsize": 48})
+
+
+def _take_all(res, n: int) -> list[MatchResult]:
+    """Results of a batch call: one copy of all rows into one array (views per
+    query), fields read as a structured array, then one free call."""
+    if n == 0:
+        return []
+    a = np.frombuffer(res, dtype=_RES_DTYPE, count=n)
+    nr, ks = a["num_rows"].astype(np.int64), a["k"].astype(np.int64)
+    words = nr * ks
+    off = np.zeros(n + 1, np.int64)
+    np.cumsum(words, out=off[1:])
+    big = np.empty(int(off[-1]), np.uint32)
+    base = big.ctypes.data
+    ptrs = a["rows"]
+    for i in np.flatnonzero(words):
+        ctypes.memmove(base + 4 * int(off[i]), int(ptrs[i]), 4 * int(words[i]))
+    counts, fps, tr, st = a["count"].tolist(), a["fingerprint"].tolist(), a["truncated"].tolist(), a["status"].tolist()
+    out = [MatchResult(counts[i], fps[i], big[off[i]:off[i + 1]].reshape(int(nr[i]), int(ks[i])), bool(tr[i]), st[i])
+           for i in range(n)]
+    lib().gs_results_free(res, n)
     return out
 
 
@@ -197,6 +248,11 @@ class DeviceGraph:
     def num_edges(self) -> int:
         return int(lib().gs_graph_num_edges(self._h))
 
+    def io_bytes(self) -> tuple[int, int]:
+        h, d = U64(), U64()
+        _check(lib().gs_graph_io_bytes(self._h, ctypes.byref(h), ctypes.byref(d)))
+        return h.value, d.value
+
     def free(self):
         if self._h:
             lib().gs_graph_free(self._h)
@@ -223,7 +279,7 @@ def match_batch(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_re
     o = _opts(cap, mode, max_refine_rounds, chunk_bytes)
     res = (ResultDesc * max(len(queries), 1))()
     _check(lib().gs_match_batch(dg._h, pack.arr, len(queries), ctypes.byref(o), res))
-    return [_take(res[i]) for i in range(len(queries))]
+    return _take_all(res, len(queries))
 
 
 class Batch:
@@ -254,7 +310,12 @@ class Batch:
     def fetch(self) -> list[MatchResult]:
         res = (ResultDesc * max(self.n, 1))()
         _check(lib().gs_batch_fetch(self._h, res))
-        return [_take(res[i]) for i in range(self.n)]
+        return _take_all(res, self.n)
+
+    def counters(self) -> dict:
+        k, h, d, f = U64(), U64(), U64(), U64()
+        _check(lib().gs_batch_counters(self._h, ctypes.byref(k), ctypes.byref(h), ctypes.byref(d), ctypes.byref(f)))
+        return {"kernel_launches": k.value, "h2d_bytes": h.value, "d2h_bytes": d.value, "fallback_queries": f.value}
 
     def stats_enable(self, on=True):
         _check(lib().gs_stats_enable(self._h, 1 if on else 0))
@@ -306,3 +367,49 @@ def inspect_edge_table(dg: DeviceGraph, q, e: int, from_src: bool):
     _check(lib().gs_inspect_edge_table(dg._h, pack.arr, e, 1 if from_src else 0, _ptr(keys), _ptr(off), _ptr(vals),
                                        keys.shape[0], vals.shape[0], ctypes.byref(nk), ctypes.byref(nv)))
     return keys[: nk.value], off, vals[: nv.value]
+
+
+class Server:
+    """Continuous-batching request loop over a device-resident graph
+    (gs_serve_*): submit queries, poll results by ticket."""
+
+    def __init__(self, dg: DeviceGraph, budget_bytes=0, slots=0, max_batch=0, queue_depth=0):
+        self.dg = dg
+        o = ServeOpts(budget_bytes, slots, max_batch, queue_depth, 0)
+        self._h = P()
+        _check(lib().gs_serve_create(dg._h, ctypes.byref(o), ctypes.byref(self._h)))
+
+    def submit(self, q, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0) -> int:
+        pack = _QueryPack([q])
+        o = _opts(cap, mode, max_refine_rounds, 0)
+        t = U64()
+        _check(lib().gs_serve_submit(self._h, pack.arr, ctypes.byref(o), ctypes.byref(t)))
+        return t.value
+
+    def submit_packed(self, pack: "_QueryPack", i: int, cap=1 << 20, mode=GS_ENUMERATE) -> int:
+        """Submit query i of a pre-built _QueryPack (no per-call packing)."""
+        o = _opts(cap, mode, 0, 0)
+        t = U64()
+        _check(lib().gs_serve_submit(self._h, ctypes.byref(pack.arr[i]), ctypes.byref(o), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        """(MatchResult, latency_s) when done, else None."""
+        r = ResultDesc()
+        lat = ctypes.c_double()
+        st = lib().gs_serve_poll(self._h, ticket, ctypes.byref(r), ctypes.byref(lat))
+        if st == GS_ERR_NOT_READY:
+            return None
+        _check(st)
+        return _take(r), lat.value
+
+    def close(self):
+        if self._h:
+            lib().gs_serve_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

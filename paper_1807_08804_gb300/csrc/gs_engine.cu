@@ -113,14 +113,18 @@ struct Sizing {
 static Sizing size_pools(const gs_batch *b, const gs_match_opts *o) {
   const uint64_t V = b->g->d.V;
   Sizing s;
-  const uint64_t L = 1ull << 27;  // 128M entries per candidate-list pool at most
-  s.tlist = std::min<uint64_t>((uint64_t)b->nq_s * V, L);
-  s.alist = std::min<uint64_t>((uint64_t)b->nqv_s * V, L);
+  // Candidate lists and edge tables: room for about 8K candidates per query
+  // vertex on average (the sets after exploration are far smaller than V on
+  // these graphs); a query that needs more finishes on the fallback path,
+  // which has pools of its own.
+  auto clampu = [](uint64_t x, uint64_t lo, uint64_t hi) { return std::min(std::max(x, lo), hi); };
+  s.tlist = std::min<uint64_t>((uint64_t)b->nq_s * V, clampu((uint64_t)b->nq_s << 14, 1ull << 22, 1ull << 28));
+  s.alist = std::min<uint64_t>((uint64_t)b->nqv_s * V, clampu((uint64_t)b->nqv_s << 13, 1ull << 22, 1ull << 28));
   s.flist = s.alist;
-  s.ec_items = std::min<uint64_t>((uint64_t)b->nqe_s * V, 1ull << 27);
-  s.ec_vals = std::min<uint64_t>((uint64_t)b->nqe_s * std::max<uint64_t>(b->g->d.E, 1), 1ull << 28);
+  s.ec_items = std::min<uint64_t>((uint64_t)b->nqe_s * V, clampu((uint64_t)b->nqe_s << 13, 1ull << 22, 1ull << 28));
+  s.ec_vals = clampu((uint64_t)b->nqe_s << 14, 1ull << 22, 1ull << 29);
   uint64_t chunk = (o && o->chunk_bytes) ? o->chunk_bytes : (1ull << 30);
-  s.lvl_words = std::max<uint64_t>(chunk / 4 / 2, 1ull << 16);
+  s.lvl_words = std::max<uint64_t>(std::min<uint64_t>(chunk / 4 / 2, std::max<uint64_t>((uint64_t)b->nq_s << 16, 1ull << 22)), 1ull << 16);
   uint64_t want_rows = 0, want_words = 0;
   for (uint32_t i = 0; i < b->n; ++i) {
     if (b->hstatus[i] != GS_OK || b->hq[i].mode == GS_COUNT_ONLY) continue;
@@ -141,6 +145,14 @@ static Sizing size_pools(const gs_batch *b, const gs_match_opts *o) {
   s.out_rows = std::min<uint64_t>(per_wave_rows, 1ull << 25);
   s.out_words = std::min<uint64_t>(per_wave_words, 1ull << 27);
   s.store_words = std::min<uint64_t>(want_words, 1ull << 28);
+  if (b->big) {  // the fallback context: large filtering pools, join buffers of its own
+    s.tlist = std::min<uint64_t>((uint64_t)b->nq_s * V, 1ull << 28);
+    s.alist = s.flist = std::min<uint64_t>((uint64_t)b->nqv_s * V, 1ull << 28);
+    s.ec_items = std::min<uint64_t>((uint64_t)b->nqe_s * V, 1ull << 28);
+    s.ec_vals = 1ull << 29;
+    s.lvl_words = 1ull << 16;
+    s.out_rows = s.out_words = s.store_words = 1ull << 10;
+  }
   return s;
 }
 
@@ -162,15 +174,15 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   A(W.ctrl, 1);
   A(W.qv_q, W.nqv);
   A(W.qe_q, W.nqe);
-  A(b->all_dq, b->n);
-  A(b->dwaves, b->waves.size());
+  A(b->all_dq, b->n_cap);
+  A(b->dwaves, std::max<size_t>(b->n_cap, b->waves.size()));
   W.all_dq = b->all_dq;
   W.waves = b->dwaves;
-  A(W.bo.count, b->n);
-  A(W.bo.fp, b->n);
-  A(W.bo.nrows, b->n);
-  A(W.bo.word_off, b->n);
-  A(W.bo.status, b->n);
+  A(W.bo.count, b->n_cap);
+  A(W.bo.fp, b->n_cap);
+  A(W.bo.nrows, b->n_cap);
+  A(W.bo.word_off, b->n_cap);
+  A(W.bo.status, b->n_cap);
   A(W.bo.store, s.store_words);
   W.bo.store_cap = s.store_words;
   A(W.bm, (uint64_t)W.nqv * W.slot_words);
@@ -219,7 +231,10 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
 
 // Upload the packed queries and the wave table.
 static gs_status batch_upload(gs_batch *b) {
-  GS_CUDA(cudaMemcpyAsync(b->all_dq, b->hq.data(), sizeof(DQuery) * b->n, cudaMemcpyHostToDevice, b->stream));
+  b->last_upload_bytes = sizeof(DQuery) * b->n + sizeof(WaveDesc) * b->waves.size();
+  b->h2d_bytes += b->last_upload_bytes;
+  if (b->n)
+    GS_CUDA(cudaMemcpyAsync(b->all_dq, b->hq.data(), sizeof(DQuery) * b->n, cudaMemcpyHostToDevice, b->stream));
   GS_CUDA(cudaMemcpyAsync(b->dwaves, b->waves.data(), sizeof(WaveDesc) * b->waves.size(), cudaMemcpyHostToDevice,
                           b->stream));
   return GS_OK;
@@ -253,157 +268,225 @@ static void make_waves(gs_batch *b, uint32_t nq_s, uint32_t nqv_s, uint32_t nqe_
 }
 
 // ------------------------------------------------------------ the pipeline
-struct Rec {
+// ------------------------------------------------------------ capture
+// The pipeline of one wave is captured once per query size K as CUDA graphs
+// (every launch is persistent over device-sized work, so one graph serves
+// every wave): graph A runs plan through the one-block sort of small
+// outputs; graph B, launched only when some query has more than 2,048
+// output rows, sorts those outputs with the radix passes; graph C moves the
+// wave's results to the batch store.  Kernels with no work for a wave return
+// at once.
+struct Pipe {
   gs_batch *b;
-  std::vector<gs_batch::Ev> *out;
-  bool capture;
+  std::vector<gs_batch::Ev> *evs;
+  bool capture;      // inside stream capture
+  cudaStream_t cur;  // stream receiving launches
   int kind = -1;
-  cudaEvent_t a = nullptr;
+  cudaEvent_t ev0 = nullptr;
+
   void begin(int k) {
     if (!b->stats_on) return;
     kind = k;
-    cudaEventCreate(&a);
-    cudaEventRecordWithFlags(a, b->stream, capture ? cudaEventRecordExternal : cudaEventRecordDefault);
+    cudaEventCreate(&ev0);
+    cudaEventRecordWithFlags(ev0, cur, capture ? cudaEventRecordExternal : cudaEventRecordDefault);
   }
   void end() {
     if (!b->stats_on || kind < 0) return;
     cudaEvent_t e;
     cudaEventCreate(&e);
-    cudaEventRecordWithFlags(e, b->stream, capture ? cudaEventRecordExternal : cudaEventRecordDefault);
-    out->push_back({kind, a, e});
+    cudaEventRecordWithFlags(e, cur, capture ? cudaEventRecordExternal : cudaEventRecordDefault);
+    evs->push_back({kind, ev0, e});
     kind = -1;
   }
 };
 
-void enqueue_wave(gs_batch *b, int K, bool capture, std::vector<gs_batch::Ev> *evs) {
+static bool rows_wanted(const gs_batch *b) {
+  for (uint32_t i = 0; i < b->n; ++i)
+    if (b->hstatus[i] == GS_OK && b->hq[i].mode != GS_COUNT_ONLY && b->hq[i].cap) return b->W.out_rows_cap > 0;
+  return false;
+}
+
+void enqueue_front(Pipe &P, int K) {
+  gs_batch *b = P.b;
   Wave &W = b->W;
   W.stats = b->stats_on ? 1 : 0;
-  cudaStream_t s = b->stream;
   const int sms = b->sms, grp = b->group;
   const uint64_t ipg = W.G.ipg;
-  Rec R{b, evs, capture};
-  R.begin(KK_PLAN);
-  launch_prologue(W, s, sms);
-  launch_plan(W, b->type_count, s, sms);
-  R.end();
-  R.begin(KK_FILTER);
-  launch_filter(W, s, sms);
-  R.end();
+  P.begin(KK_PLAN);
+  launch_prologue(W, P.cur, sms);
+  launch_plan(W, b->type_count, P.cur, sms);
+  P.end();
+  P.begin(KK_FILTER);
+  launch_filter(W, P.cur, sms);
+  P.end();
   const int steps = K >= 2 ? K - 1 : 0;
   for (int step = 0; step < steps; ++step) {
-    R.begin(KK_COMPACT);
-    launch_compact_count(W, 0, step, s, sms);
-    scan_u32(W.ccount, W.cscan, &W.ctrl->len[0], (uint64_t)W.nq * ipg, b->scan_tmp, s, sms);
-    launch_compact_write(W, 0, step, W.cscan, W.tlist, W.tlist_cap, s, sms);
-    R.end();
-    R.begin(KK_EXPLORE);
-    launch_explore(W, step, grp, s, sms);
-    R.end();
+    P.begin(KK_COMPACT);
+    launch_compact_count(W, 0, step, P.cur, sms);
+    scan_u32(W.ccount, W.cscan, &W.ctrl->len[0], (uint64_t)W.nq * ipg, b->scan_tmp, P.cur, sms);
+    launch_compact_write(W, 0, step, W.cscan, W.tlist, W.tlist_cap, P.cur, sms);
+    P.end();
+    P.begin(KK_EXPLORE);
+    launch_explore(W, step, grp, P.cur, sms);
+    P.end();
   }
-  R.begin(KK_COMPACT);
-  launch_compact_count(W, 1, 0, s, sms);
-  scan_u32(W.ccount, W.ascan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, s, sms);
-  launch_compact_write(W, 1, 0, W.ascan, W.alist, W.alist_cap, s, sms);
-  R.end();
-  R.begin(KK_REFINE);
-  for (uint32_t r = 0; r < b->refine_rounds; ++r) launch_refine(W, r, grp, s, sms);
-  R.end();
+  P.begin(KK_COMPACT);
+  launch_compact_count(W, 1, 0, P.cur, sms);
+  scan_u32(W.ccount, W.ascan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, P.cur, sms);
+  launch_compact_write(W, 1, 0, W.ascan, W.alist, W.alist_cap, P.cur, sms);
+  P.end();
+  P.begin(KK_REFINE);
+  for (uint32_t r = 0; r < b->refine_rounds; ++r) launch_refine(W, r, grp, P.cur, sms);
+  P.end();
+}
+
+// stop: 0 = through the one-block sort, 1 = after the final candidate lists,
+// 2 = after the candidate-edge tables.
+void enqueue_back(Pipe &P, int K, int stop) {
+  gs_batch *b = P.b;
+  Wave &W = b->W;
+  const int sms = b->sms, grp = b->group;
+  const uint64_t ipg = W.G.ipg;
+  P.begin(KK_COMPACT);
+  launch_compact_count(W, 1, 0, P.cur, sms);
+  scan_u32(W.ccount, W.cscan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, P.cur, sms);
+  launch_compact_write(W, 1, 0, W.cscan, W.flist, W.flist_cap, P.cur, sms);
+  launch_list_table(W, P.cur, sms);
+  P.end();
+  if (stop == 1) return;
+  P.begin(KK_OTHER);
+  launch_join_plan(W, P.cur, sms);
+  scan_u32(W.ec_nkeys, W.ec_key_base, &W.ctrl->len[2], W.nqe, b->scan_tmp, P.cur, sms);
+  launch_ec_limit(W, P.cur, sms);
+  P.end();
+  P.begin(KK_EC_COUNT);
+  launch_ec(W, false, grp, P.cur, sms);
+  P.end();
+  P.begin(KK_SCAN);
+  scan_u32(W.ec_cnt, W.ec_off, &W.ctrl->len[5], W.ec_items_cap, b->scan_tmp, P.cur, sms);
+  P.end();
+  P.begin(KK_EC_WRITE);
+  launch_ec(W, true, grp, P.cur, sms);
+  P.end();
+  if (stop == 2) return;
+  P.begin(KK_CLEAR);
+  launch_clear(W, P.cur, sms);
+  P.end();
+  P.begin(KK_OTHER);
+  launch_join0(W, P.cur, sms);
+  P.end();
+  for (int lvl = 0; lvl + 1 < K; ++lvl) {
+    P.begin(KK_JOIN_COUNT);
+    launch_join_count(W, lvl, grp, P.cur, sms);
+    P.end();
+    P.begin(KK_SCAN);
+    scan_u32(W.row_cnt, W.row_scan, &W.ctrl->len[3], W.row_cap, b->scan_tmp, P.cur, sms);
+    launch_join_totals(W, P.cur, sms);
+    launch_level_alloc(W, lvl + 1, P.cur);
+    P.end();
+    P.begin(KK_JOIN_WRITE);
+    launch_join_write(W, lvl, grp, P.cur, sms);
+    P.end();
+  }
+  P.begin(KK_SORT);
+  launch_final_bases(W, P.cur);
+  if (rows_wanted(b)) launch_small_sort(W, P.cur, sms);
+  P.end();
+}
+
+// Radix sort of the outputs above the one-block limit (graph B).
+void enqueue_large_sort(Pipe &P, int K) {
+  gs_batch *b = P.b;
+  Wave &W = b->W;
+  const int sms = b->sms;
+  P.begin(KK_SORT);
+  uint32_t *perm[2] = {W.sval[0], W.sval[1]};
+  int cur = 0;
+  launch_iota(W, perm[cur], P.cur, sms);
+  const int nb = bits_for(W.G.V ? W.G.V - 1 : 0);
+  for (int col = K - 1; col >= 0; --col) {
+    launch_sort_keys(W, perm[cur], W.skey[0], (uint32_t)col, P.cur, sms);
+    int r = radix_sort_pairs(W.skey[0], perm[cur], W.skey[1], perm[cur ^ 1], &W.ctrl->len[6], W.out_rows_cap, 0, nb,
+                             b->scan_tmp, P.cur, sms);
+    cur = r ? cur ^ 1 : cur;
+  }
+  if (W.nq > 1) {
+    launch_sort_keys(W, perm[cur], W.skey[0], kMaxK, P.cur, sms);
+    int r = radix_sort_pairs(W.skey[0], perm[cur], W.skey[1], perm[cur ^ 1], &W.ctrl->len[6], W.out_rows_cap, 0,
+                             bits_for(W.nq - 1), b->scan_tmp, P.cur, sms);
+    cur = r ? cur ^ 1 : cur;
+  }
+  P.end();
+  P.begin(KK_GATHER);
+  launch_gather(W, perm[cur], P.cur, sms);
+  P.end();
+}
+
+// Results of the wave into the batch store (graph C).
+void enqueue_epilogue(Pipe &P) {
+  P.begin(KK_OTHER);
+  launch_epilogue(P.b->W, P.cur, P.b->sms);
+  P.end();
+}
+
+void enqueue_wave(gs_batch *b, int K, bool capture, std::vector<gs_batch::Ev> *evs) {
+  Pipe P{b, evs, capture, b->stream};
+  enqueue_front(P, K);
 }
 
 void enqueue_wave_tail(gs_batch *b, int K, bool capture, std::vector<gs_batch::Ev> *evs, int stop) {
-  Wave &W = b->W;
-  cudaStream_t s = b->stream;
-  const int sms = b->sms, grp = b->group;
-  const uint64_t ipg = W.G.ipg;
-  Rec R{b, evs, capture};
-  R.begin(KK_COMPACT);
-  launch_compact_count(W, 1, 0, s, sms);
-  scan_u32(W.ccount, W.cscan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, s, sms);
-  launch_compact_write(W, 1, 0, W.cscan, W.flist, W.flist_cap, s, sms);
-  launch_list_table(W, s, sms);
-  R.end();
-  if (stop == 1) return;
-  R.begin(KK_OTHER);
-  launch_join_plan(W, s, sms);
-  scan_u32(W.ec_nkeys, W.ec_key_base, &W.ctrl->len[2], W.nqe, b->scan_tmp, s, sms);
-  launch_ec_limit(W, s, sms);
-  R.end();
-  R.begin(KK_EC_COUNT);
-  launch_ec(W, false, grp, s, sms);
-  R.end();
-  R.begin(KK_SCAN);
-  scan_u32(W.ec_cnt, W.ec_off, &W.ctrl->len[5], W.ec_items_cap, b->scan_tmp, s, sms);
-  R.end();
-  R.begin(KK_EC_WRITE);
-  launch_ec(W, true, grp, s, sms);
-  R.end();
-  if (stop == 2) return;
-  R.begin(KK_CLEAR);
-  launch_clear(W, s, sms);
-  R.end();
-  R.begin(KK_OTHER);
-  launch_join0(W, s, sms);
-  R.end();
-  for (int lvl = 0; lvl + 1 < K; ++lvl) {
-    R.begin(KK_JOIN_COUNT);
-    launch_join_count(W, lvl, grp, s, sms);
-    R.end();
-    R.begin(KK_SCAN);
-    scan_u32(W.row_cnt, W.row_scan, &W.ctrl->len[3], W.row_cap, b->scan_tmp, s, sms);
-    launch_join_totals(W, s, sms);
-    launch_level_alloc(W, lvl + 1, s);
-    R.end();
-    R.begin(KK_JOIN_WRITE);
-    launch_join_write(W, lvl, grp, s, sms);
-    R.end();
+  Pipe P{b, evs, capture, b->stream};
+  enqueue_back(P, K, stop);
+}
+
+// Capture one segment of the pipeline into an executable graph.
+template <typename F>
+static gs_status capture_one(gs_batch *b, F body, cudaGraphExec_t *exec, std::vector<gs_batch::Ev> *evs,
+                             uint64_t *kernels) {
+  cudaGraph_t graph;
+  GS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  Pipe P{b, evs, true, b->stream};
+  body(P);
+  cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+  if (e != cudaSuccess) return cuda_fail(e, "pipeline capture");
+  size_t nn = 0;
+  cudaGraphGetNodes(graph, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+  uint64_t kern = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) kern++;
   }
-  R.begin(KK_SORT);
-  launch_final_bases(W, s);
-  bool rows_wanted = false;
-  for (uint32_t i = 0; i < b->n; ++i)
-    if (b->hstatus[i] == GS_OK && b->hq[i].mode != GS_COUNT_ONLY && b->hq[i].cap) rows_wanted = true;
-  if (rows_wanted && W.out_rows_cap) {
-    uint32_t *perm[2] = {W.sval[0], W.sval[1]};
-    int cur = 0;
-    launch_iota(W, perm[cur], s, sms);
-    const int nb = bits_for(W.G.V ? W.G.V - 1 : 0);
-    for (int col = K - 1; col >= 0; --col) {
-      launch_sort_keys(W, perm[cur], W.skey[0], (uint32_t)col, s, sms);
-      int r = radix_sort_pairs(W.skey[0], perm[cur], W.skey[1], perm[cur ^ 1], &W.ctrl->out_rows_total,
-                               W.out_rows_cap, 0, nb, b->scan_tmp, s, sms);
-      cur = r ? cur ^ 1 : cur;
-    }
-    if (W.nq > 1) {
-      launch_sort_keys(W, perm[cur], W.skey[0], kMaxK, s, sms);
-      int r = radix_sort_pairs(W.skey[0], perm[cur], W.skey[1], perm[cur ^ 1], &W.ctrl->out_rows_total,
-                               W.out_rows_cap, 0, bits_for(W.nq - 1), b->scan_tmp, s, sms);
-      cur = r ? cur ^ 1 : cur;
-    }
-    R.end();
-    R.begin(KK_GATHER);
-    launch_gather(W, perm[cur], s, sms);
-  }
-  R.end();
-  R.begin(KK_OTHER);
-  launch_epilogue(W, s, sms);
-  R.end();
+  *kernels = kern;
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return GS_OK;
 }
 
 static gs_status capture_k(gs_batch *b, int K) {
   if (b->execs.count(K)) return GS_OK;
-  cudaGraph_t graph;
-  std::vector<gs_batch::Ev> evs;
-  GS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-  enqueue_wave(b, K, true, &evs);
-  enqueue_wave_tail(b, K, true, &evs, 0);
-  cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  cudaGraphExec_t exec;
-  e = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  b->execs[K] = exec;
-  b->graph_evs[K] = evs;
+  cudaGraphExec_t a = nullptr, s = nullptr;
+  std::vector<gs_batch::Ev> ea, es;
+  uint64_t ka = 0, ks = 0;
+  gs_status st = capture_one(b, [&](Pipe &P) { enqueue_front(P, K); enqueue_back(P, K, 0); }, &a, &ea, &ka);
+  if (st != GS_OK) return st;
+  st = capture_one(b, [&](Pipe &P) { enqueue_large_sort(P, K); }, &s, &es, &ks);
+  if (st != GS_OK) {
+    cudaGraphExecDestroy(a);
+    return st;
+  }
+  if (!b->epi_exec) {
+    st = capture_one(b, [&](Pipe &P) { enqueue_epilogue(P); }, &b->epi_exec, &b->epi_evs, &b->epi_kernels);
+    if (st != GS_OK) return st;
+  }
+  b->execs[K] = a;
+  b->sort_execs[K] = s;
+  b->graph_evs[K] = ea;
+  b->sort_evs[K] = es;
+  b->kernels_per_exec[K] = ka;
+  b->sort_kernels[K] = ks;
   return GS_OK;
 }
 
@@ -439,16 +522,15 @@ gs_status refine_to_fixpoint(gs_batch *b) {
 gs_status run_waves(gs_batch *b) {
   GS_CUDA(cudaMemsetAsync(&b->W.ctrl->wave, 0, sizeof(uint32_t), b->stream));
   GS_CUDA(cudaMemsetAsync(&b->W.ctrl->store_top, 0, sizeof(uint64_t), b->stream));
+  if (!b->flag) GS_CUDA(cudaMallocHost((void **)&b->flag, sizeof(uint64_t)));
+  const bool sorting = rows_wanted(b);
   for (size_t w = 0; w < b->waves.size(); ++w) {
     const int K = b->wave_k[w];
     if (b->use_graph) {
       gs_status st = capture_k(b, K);
       if (st != GS_OK) return st;
       GS_CUDA(cudaGraphLaunch(b->execs[K], b->stream));
-      if (b->stats_on) {
-        GS_CUDA(cudaStreamSynchronize(b->stream));
-        harvest_events(b, b->graph_evs[K], false);
-      }
+      b->kernel_launches += b->kernels_per_exec[K];
     } else {
       enqueue_wave(b, K, false, &b->evs);
       if (b->fixpoint) {
@@ -456,8 +538,37 @@ gs_status run_waves(gs_batch *b) {
         if (st != GS_OK) return st;
       }
       enqueue_wave_tail(b, K, false, &b->evs, 0);
-      if (b->stats_on) {
-        GS_CUDA(cudaStreamSynchronize(b->stream));
+    }
+    bool large = false;
+    if (sorting) {  // any output too large for the one-block sort?
+      GS_CUDA(cudaMemcpyAsync(b->flag, &b->W.ctrl->len[6], sizeof(uint64_t), cudaMemcpyDeviceToHost, b->stream));
+      GS_CUDA(cudaStreamSynchronize(b->stream));
+      large = *b->flag != 0;
+      if (large) {
+        if (b->use_graph) {
+          GS_CUDA(cudaGraphLaunch(b->sort_execs[K], b->stream));
+          b->kernel_launches += b->sort_kernels[K];
+        } else {
+          Pipe P{b, &b->evs, false, b->stream};
+          enqueue_large_sort(P, K);
+        }
+        b->large_sorts++;
+      }
+    }
+    if (b->use_graph) {
+      GS_CUDA(cudaGraphLaunch(b->epi_exec, b->stream));
+      b->kernel_launches += b->epi_kernels;
+    } else {
+      Pipe P{b, &b->evs, false, b->stream};
+      enqueue_epilogue(P);
+    }
+    if (b->stats_on) {
+      GS_CUDA(cudaStreamSynchronize(b->stream));
+      if (b->use_graph) {
+        harvest_events(b, b->graph_evs[K], false);
+        if (large) harvest_events(b, b->sort_evs[K], false);
+        harvest_events(b, b->epi_evs, false);
+      } else {
         harvest_events(b, b->evs, true);
       }
     }
@@ -465,24 +576,45 @@ gs_status run_waves(gs_batch *b) {
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
-
-gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts, uint32_t wave_queries,
-                       gs_batch **out) {
-  *out = nullptr;
-  gs_batch *b = new gs_batch();
-  b->g = g;
-  b->sms = g->num_sms;
+static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match_opts *opts) {
   b->n = n;
-  b->hq.resize(n);
-  b->hstatus.resize(n);
+  b->hq.assign(n, DQuery{});
+  b->hstatus.assign(n, GS_OK);
   for (uint32_t i = 0; i < n; ++i) {
-    gs_status st = pack_query(g->d, &qs[i], opts, &b->hq[i]);
+    gs_status st = pack_query(b->g->d, &qs[i], opts, &b->hq[i]);
     b->hstatus[i] = st;
     if (st != GS_OK) {
       memset(&b->hq[i], 0, sizeof(DQuery));
       b->hq[i].status = QS_INVALID;
     }
   }
+  b->ran = b->finished = false;
+}
+
+static void opts_key(gs_batch *b, const gs_match_opts *opts) {
+  b->key_cap = opts ? opts->cap : 0;
+  b->key_mode = opts ? opts->mode : 0;
+  b->key_rounds = opts ? opts->max_refine_rounds : 0;
+  b->key_chunk = opts ? opts->chunk_bytes : 0;
+  b->key_stream = opts ? opts->cuda_stream : nullptr;
+}
+
+static bool opts_match(const gs_batch *b, const gs_match_opts *opts) {
+  return b->key_cap == (opts ? opts->cap : 0) && b->key_mode == (opts ? opts->mode : 0) &&
+         b->key_rounds == (opts ? opts->max_refine_rounds : 0) && b->key_chunk == (opts ? opts->chunk_bytes : 0) &&
+         b->key_stream == (opts ? opts->cuda_stream : nullptr);
+}
+
+gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts, uint32_t wave_queries,
+                       gs_batch **out, bool big) {
+  *out = nullptr;
+  gs_batch *b = new gs_batch();
+  b->g = g;
+  b->big = big;
+  b->sms = g->num_sms;
+  pack_all(b, qs, n, opts);
+  b->n_cap = std::max<uint32_t>(n, 1);
+  opts_key(b, opts);
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
     b->fixpoint = false;
@@ -504,20 +636,24 @@ gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_mat
   uint64_t max_qv = std::max<uint64_t>(bm_budget / slot_bytes, kMaxK);
   uint32_t nq_s = wave_queries ? wave_queries : n;
   uint64_t tot_qv = 0, tot_qe = 0;
-  for (uint32_t i = 0; i < n; ++i) { tot_qv += b->hq[i].k; tot_qe += b->hq[i].m; }
+  uint32_t mk = 1, mm = 1;
+  for (uint32_t i = 0; i < n; ++i) {
+    tot_qv += b->hq[i].k; tot_qe += b->hq[i].m;
+    mk = std::max(mk, b->hq[i].k); mm = std::max(mm, b->hq[i].m);
+  }
   uint32_t nqv_s = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(tot_qv, 1), max_qv);
   if (wave_queries) {
-    uint32_t mk = 1, mm = 1;
-    for (uint32_t i = 0; i < n; ++i) { mk = std::max(mk, b->hq[i].k); mm = std::max(mm, b->hq[i].m); }
     nqv_s = (uint32_t)std::min<uint64_t>((uint64_t)wave_queries * mk, max_qv);
     tot_qe = (uint64_t)wave_queries * mm;
   }
-  uint32_t nqe_s = (uint32_t)std::max<uint64_t>(tot_qe, 1);
+  nqv_s = std::max<uint32_t>(nqv_s, mk);
+  uint32_t nqe_s = (uint32_t)std::max<uint64_t>({tot_qe, (uint64_t)mm, 1});
   nq_s = std::max<uint32_t>(nq_s, 1);
   make_waves(b, nq_s, nqv_s, nqe_s);
   uint32_t mq = 1, mqv = 1, mqe = 1;
   for (auto &w : b->waves) { mq = std::max(mq, w.nq); mqv = std::max(mqv, w.nqv); mqe = std::max(mqe, w.nqe); }
   b->nq_s = mq; b->nqv_s = mqv; b->nqe_s = mqe;
+  if (big) { b->nq_s = 1; b->nqv_s = kMaxK; b->nqe_s = kMaxM; }
   gs_status st = batch_alloc(b, opts);
   if (st == GS_OK) st = batch_upload(b);
   if (st != GS_OK) {
@@ -528,10 +664,75 @@ gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_mat
   return GS_OK;
 }
 
+// An empty batch with fixed capacities (queries come later through
+// batch_rearm): n_cap queries, nqv_s query vertices and nqe_s query edges in
+// one wave.
+gs_status batch_create_capacity(gs_graph *g, const gs_match_opts *opts, uint32_t n_cap, uint32_t nqv_s, uint32_t nqe_s,
+                                gs_batch **out) {
+  *out = nullptr;
+  gs_batch *b = new gs_batch();
+  b->g = g;
+  b->sms = g->num_sms;
+  b->n_cap = std::max<uint32_t>(n_cap, 1);
+  opts_key(b, opts);
+  if (opts && opts->max_refine_rounds) {
+    b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
+    b->fixpoint = false;
+  }
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return fail(GS_ERR_CUDA, "cudaStreamCreate");
+  }
+  b->own_stream = true;
+  b->n = 0;
+  b->nq_s = b->n_cap;
+  b->nqv_s = std::max<uint32_t>(nqv_s, kMaxK);
+  b->nqe_s = std::max<uint32_t>(nqe_s, 1);
+  // output pools sized for n_cap queries at the options' cap
+  b->hq.assign(b->n_cap, DQuery{});
+  b->hstatus.assign(b->n_cap, GS_OK);
+  for (uint32_t i = 0; i < b->n_cap; ++i) {
+    b->hq[i].k = kMaxK;
+    b->hq[i].mode = opts ? opts->mode : GS_ENUMERATE;
+    b->hq[i].cap = opts ? std::min<uint64_t>(opts->cap, 1u << 12) : 0;
+  }
+  b->n = b->n_cap;
+  b->waves.assign(1, WaveDesc{0, b->n_cap, 0, b->nqv_s, 0, b->nqe_s});
+  b->wave_k.assign(1, kMaxK);
+  gs_status st = batch_alloc(b, opts);
+  b->n = 0;
+  b->waves.clear();
+  b->wave_k.clear();
+  if (st != GS_OK) {
+    batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return GS_OK;
+}
+
+// Load new queries into an existing batch (same options, within its
+// capacities).  Returns false when they do not fit.
+bool batch_rearm(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match_opts *opts) {
+  if (n > b->n_cap || !opts_match(b, opts)) return false;
+  for (uint32_t i = 0; i < n; ++i)
+    if (qs[i].k > b->nqv_s || qs[i].m > b->nqe_s) return false;
+  pack_all(b, qs, n, opts);
+  for (uint32_t i = 0; i < n; ++i)
+    if (b->hq[i].k > b->nqv_s || b->hq[i].m > b->nqe_s) return false;
+  make_waves(b, b->nq_s, b->nqv_s, b->nqe_s);
+  return batch_upload(b) == GS_OK;
+}
+
 void batch_destroy(gs_batch *b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (auto &kv : b->execs) cudaGraphExecDestroy(kv.second);
+  for (auto &kv : b->sort_execs) cudaGraphExecDestroy(kv.second);
+  if (b->epi_exec) cudaGraphExecDestroy(b->epi_exec);
+  for (auto &kv : b->sort_evs) harvest_events(b, kv.second, true);
+  harvest_events(b, b->epi_evs, true);
+  if (b->flag) cudaFreeHost(b->flag);
   for (auto &kv : b->graph_evs) harvest_events(b, kv.second, true);
   harvest_events(b, b->evs, true);
   for (void *p : b->allocs) cudaFree(p);
@@ -555,17 +756,20 @@ gs_status batch_finish(gs_batch *b) {
   GS_CUDA(cudaMemcpyAsync(&top, &b->W.ctrl->store_top, 8, cudaMemcpyDeviceToHost, b->stream));
   GS_CUDA(cudaStreamSynchronize(b->stream));
   b->rows.resize(top);
+  b->d2h_bytes += 36ull * n + 8 + 4ull * top;
   if (top) {
     GS_CUDA(cudaMemcpyAsync(b->rows.data(), b->W.bo.store, 4ull * top, cudaMemcpyDeviceToHost, b->stream));
     GS_CUDA(cudaStreamSynchronize(b->stream));
   }
   b->fb_rows.assign(n, {});
   b->fb_done.assign(n, 0);
+  b->fallbacks = 0;
   for (uint32_t i = 0; i < n; ++i) {
     if (b->hstatus[i] != GS_OK) continue;
     if (b->status[i] == QS_OVERFLOW || b->status[i] == QS_TOPCAP) {
       gs_status st = fallback_query(b, i);
       if (st != GS_OK) return st;
+      b->fallbacks++;
     }
   }
   b->finished = true;
@@ -650,13 +854,25 @@ extern "C" gs_status gs_batch_fetch(gs_batch *b, gs_result *outs) {
 
 extern "C" void gs_batch_destroy(gs_batch *b) { batch_destroy(b); }
 
+// Forget captured graphs (their launch parameters changed).
+static void drop_graphs(gs_batch *b) {
+  for (auto &kv : b->execs) cudaGraphExecDestroy(kv.second);
+  for (auto &kv : b->sort_execs) cudaGraphExecDestroy(kv.second);
+  if (b->epi_exec) cudaGraphExecDestroy(b->epi_exec);
+  b->execs.clear();
+  b->sort_execs.clear();
+  b->epi_exec = nullptr;
+  for (auto &kv : b->graph_evs) harvest_events(b, kv.second, true);
+  for (auto &kv : b->sort_evs) harvest_events(b, kv.second, true);
+  harvest_events(b, b->epi_evs, true);
+  b->graph_evs.clear();
+  b->sort_evs.clear();
+}
+
 extern "C" gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_t refine_rounds) {
   if (!b) return fail(GS_ERR_INVALID, "gs_batch_set: null batch");
-  if (group != 8 && group != 16 && group != 32) return fail(GS_ERR_INVALID, "group must be 8, 16 or 32");
-  for (auto &kv : b->execs) cudaGraphExecDestroy(kv.second);
-  b->execs.clear();
-  for (auto &kv : b->graph_evs) harvest_events(b, kv.second, true);
-  b->graph_evs.clear();
+  if (group != 4 && group != 8 && group != 16 && group != 32) return fail(GS_ERR_INVALID, "group must be 4, 8, 16 or 32");
+  drop_graphs(b);
   b->use_graph = use_graph != 0;
   b->group = group;
   if (refine_rounds) {
@@ -669,17 +885,80 @@ extern "C" gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_
   return GS_OK;
 }
 
+namespace gs {
+
+// Batches kept per graph so that repeated gs_match / gs_match_batch calls
+// reuse their device pools and captured graphs.
+struct MatchCache {
+  std::mutex mu;
+  std::vector<gs_batch *> batches;
+  uint64_t h2d = 0, d2h = 0;
+};
+
+static MatchCache *cache_of(gs_graph *g) {
+  static std::mutex init_mu;
+  std::lock_guard<std::mutex> lk(init_mu);
+  if (!g->cache) g->cache = new MatchCache();
+  return static_cast<MatchCache *>(g->cache);
+}
+
+void release_cache(gs_graph *g) {
+  if (!g->cache) return;
+  MatchCache *c = static_cast<MatchCache *>(g->cache);
+  for (gs_batch *b : c->batches) batch_destroy(b);
+  delete c;
+  g->cache = nullptr;
+}
+
+}  // namespace gs
+
 extern "C" gs_status gs_match_batch(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
                                     gs_result *outs) {
   if (!g || !outs || (n && !qs)) return fail(GS_ERR_INVALID, "gs_match_batch: null argument");
+  if (n == 0) return GS_OK;
+  GS_CUDA(cudaSetDevice(g->device));
+  MatchCache *c = cache_of(g);
+  std::lock_guard<std::mutex> lk(c->mu);
   gs_batch *b = nullptr;
-  gs_status st = gs_batch_create(g, qs, n, opts, &b);
-  if (st != GS_OK) return st;
-  st = gs_batch_run(b);
-  if (st == GS_OK) st = gs_batch_finish(b);
-  if (st == GS_OK) st = gs_batch_fetch(b, outs);
-  gs_batch_destroy(b);
+  for (gs_batch *x : c->batches)
+    if (batch_rearm(x, qs, n, opts)) { b = x; break; }
+  if (!b) {
+    gs_status st = batch_create(g, qs, n, opts, 0, &b);
+    if (st != GS_OK) return st;
+    if (c->batches.size() >= 4) {
+      batch_destroy(c->batches.front());
+      c->batches.erase(c->batches.begin());
+    }
+    c->batches.push_back(b);
+  }
+  const uint64_t d0 = b->d2h_bytes;
+  c->h2d += b->last_upload_bytes;
+  gs_status st = run_waves(b);
+  b->ran = st == GS_OK;
+  if (st == GS_OK) st = batch_finish(b);
+  if (st == GS_OK) st = batch_fetch(b, outs);
+  for (uint32_t i = 0; i < n && st == GS_OK; ++i) b->d2h_bytes += 4ull * outs[i].num_rows * outs[i].k;
+  c->d2h += b->d2h_bytes - d0;
   return st;
+}
+
+extern "C" gs_status gs_graph_io_bytes(gs_graph *g, uint64_t *h2d, uint64_t *d2h) {
+  if (!g) return fail(GS_ERR_INVALID, "null graph");
+  MatchCache *c = cache_of(g);
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (h2d) *h2d = c->h2d;
+  if (d2h) *d2h = c->d2h;
+  return GS_OK;
+}
+
+extern "C" gs_status gs_batch_counters(gs_batch *b, uint64_t *kernel_launches, uint64_t *h2d, uint64_t *d2h,
+                                       uint64_t *fallback_queries) {
+  if (!b) return fail(GS_ERR_INVALID, "null batch");
+  if (fallback_queries) *fallback_queries = b->fallbacks;
+  if (kernel_launches) *kernel_launches = b->kernel_launches;
+  if (h2d) *h2d = b->h2d_bytes;
+  if (d2h) *d2h = b->d2h_bytes;
+  return GS_OK;
 }
 
 extern "C" gs_status gs_match(gs_graph *g, const gs_query *q, const gs_match_opts *opts, gs_result *out) {
@@ -700,14 +979,14 @@ extern "C" void gs_result_free(gs_result *r) {
   r->num_rows = 0;
 }
 
+extern "C" void gs_results_free(gs_result *r, uint32_t n) {
+  if (!r) return;
+  for (uint32_t i = 0; i < n; ++i) gs_result_free(&r[i]);
+}
+
 extern "C" gs_status gs_stats_enable(gs_batch *b, int on) {
   if (!b) return fail(GS_ERR_INVALID, "null batch");
-  if ((on != 0) != b->stats_on) {
-    for (auto &kv : b->execs) cudaGraphExecDestroy(kv.second);
-    b->execs.clear();
-    for (auto &kv : b->graph_evs) harvest_events(b, kv.second, true);
-    b->graph_evs.clear();
-  }
+  if ((on != 0) != b->stats_on) drop_graphs(b);
   b->stats_on = on != 0;
   return GS_OK;
 }

@@ -13,6 +13,8 @@ namespace cg = cooperative_groups;
 constexpr uint32_t kUnbound = 0xFFFFFFFFu;
 constexpr uint32_t kAny = 0xFFFFFFFFu;
 constexpr uint32_t kMaxRounds = 64;
+constexpr uint32_t kSmallRows = 2048;    // outputs sorted by one block in shared memory
+constexpr uint32_t kSmallWords = 24576;
 
 // Per-query status.
 enum : uint32_t {
@@ -66,6 +68,7 @@ struct QState {
   uint64_t nxt_rows;                                 // rows produced for the next level
   uint64_t out_row_base, out_rows, out_word_base;   // final rows in the output pool
   uint64_t fin_row_base, fin_word_base;             // sorted rows in query order
+  uint64_t lrg_row_base;                             // rows sorted by the radix path
 };
 
 // Rows of level s kept aside while the allocator lays out level s+1.
@@ -96,6 +99,9 @@ struct Ctrl {
   uint64_t store_top;               // batch row store top (words)
   uint32_t wave;                    // index of the wave being run
   uint32_t err;
+  uint32_t max_nvisit;              // longest visit order in the wave
+  uint32_t refine_iters;            // rounds run by the refinement loop
+  uint64_t fb_src[3];               // source rows staged by the chunked join
   uint64_t bytes[KK_N];             // algorithmic bytes per kernel kind
 };
 
@@ -167,6 +173,7 @@ void launch_join_totals(const Wave &W, cudaStream_t s, int sms);
 void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s);
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms);
 void launch_final_bases(const Wave &W, cudaStream_t s);
+void launch_small_sort(const Wave &W, cudaStream_t s, int sms);
 void launch_iota(const Wave &W, uint32_t *perm, cudaStream_t s, int sms);
 void launch_sort_keys(const Wave &W, const uint32_t *perm, uint32_t *key, uint32_t col, cudaStream_t s, int sms);
 void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms);

@@ -316,6 +316,8 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
 
 extern "C" void gs_graph_free(gs_graph *g) {
   if (!g) return;
+  gs::release_cache(g);
+  gs::release_fallback(g);
   cudaFree(g->off_out);
   cudaFree(g->off_in);
   cudaFree(g->adj_out);

@@ -1,10 +1,50 @@
 // Host-side functions shared by the engine's translation units.
 #pragma once
 
+#include <cstring>
 #include <map>
+#include <new>
 #include <vector>
 
 #include "gs_engine.cuh"
+
+// Host array in page-locked memory (direct DMA for uploads and result
+// downloads); grows geometrically, never shrinks.
+template <typename T>
+struct PinnedVec {
+  T *p = nullptr;
+  size_t n = 0, cap = 0;
+  PinnedVec() = default;
+  PinnedVec(const PinnedVec &) = delete;
+  PinnedVec &operator=(const PinnedVec &) = delete;
+  ~PinnedVec() {
+    if (p) cudaFreeHost(p);
+  }
+  void resize(size_t m) {
+    if (m > cap) {
+      size_t c = cap ? cap : 16;
+      while (c < m) c *= 2;
+      T *q = nullptr;
+      if (cudaMallocHost((void **)&q, sizeof(T) * c) != cudaSuccess) throw std::bad_alloc();
+      if (p) {
+        memcpy(q, p, sizeof(T) * n);
+        cudaFreeHost(p);
+      }
+      p = q;
+      cap = c;
+    }
+    n = m;
+  }
+  void assign(size_t m, const T &v) {
+    resize(m);
+    for (size_t i = 0; i < m; ++i) p[i] = v;
+  }
+  T *data() { return p; }
+  const T *data() const { return p; }
+  size_t size() const { return n; }
+  T &operator[](size_t i) { return p[i]; }
+  const T &operator[](size_t i) const { return p[i]; }
+};
 
 using gs::DQuery;
 using gs::KK_N;
@@ -22,7 +62,7 @@ struct gs_batch {
   bool fixpoint = true;            // loop rounds on the host until nothing changes (non-graph runs)
   bool use_graph = true;
   uint32_t n = 0;
-  std::vector<DQuery> hq;
+  PinnedVec<DQuery> hq;
   std::vector<uint32_t> hstatus;   // gs_status per query from the host checks
   std::vector<WaveDesc> waves;
   std::vector<int> wave_k;
@@ -44,19 +84,43 @@ struct gs_batch {
   uint64_t bytes_base[KK_N] = {0};
   bool ran = false, finished = false;
   // host results
-  std::vector<uint64_t> count, fp, nrows, word_off;
-  std::vector<uint32_t> status;
-  std::vector<uint32_t> rows;        // store contents
+  PinnedVec<uint64_t> count, fp, nrows, word_off;
+  PinnedVec<uint32_t> status;
+  PinnedVec<uint32_t> rows;          // store contents
   std::vector<std::vector<uint32_t>> fb_rows;  // rows of queries finished on the fallback path
   std::vector<uint8_t> fb_done;
+  // capacity and options (for reuse by later calls with the same options)
+  uint32_t n_cap = 0;
+  uint64_t key_cap = 0, key_chunk = 0;
+  uint32_t key_mode = 0, key_rounds = 0;
+  void *key_stream = nullptr;
+  // accounting
+  std::map<int, uint64_t> kernels_per_exec;
+  uint64_t kernel_launches = 0;
+  uint64_t h2d_bytes = 0, d2h_bytes = 0;
+  uint64_t last_upload_bytes = 0;
+  bool big = false;                // fallback context sizing
+  // the large-output sort and the epilogue as separate graphs
+  std::map<int, cudaGraphExec_t> sort_execs;
+  std::map<int, std::vector<Ev>> sort_evs;
+  std::map<int, uint64_t> sort_kernels;
+  cudaGraphExec_t epi_exec = nullptr;
+  std::vector<Ev> epi_evs;
+  uint64_t epi_kernels = 0;
+  uint64_t *flag = nullptr;        // pinned word read between graphs
+  uint64_t large_sorts = 0;
+  uint64_t fallbacks = 0;          // queries finished on the chunked path by the last finish
 };
 
 namespace gs {
 
 gs_status pack_query(const DevGraph &G, const gs_query *q, const gs_match_opts *o, DQuery *d);
 gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts, uint32_t wave_queries,
-                       gs_batch **out);
+                       gs_batch **out, bool big = false);
 void batch_destroy(gs_batch *b);
+bool batch_rearm(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match_opts *opts);
+gs_status batch_create_capacity(gs_graph *g, const gs_match_opts *opts, uint32_t n_cap, uint32_t nqv_s, uint32_t nqe_s,
+                                gs_batch **out);
 gs_status run_waves(gs_batch *b);
 gs_status batch_finish(gs_batch *b);
 gs_status batch_fetch(gs_batch *b, gs_result *outs);

@@ -1,6 +1,5 @@
 // Inspection of one query's candidate sets and candidate-edge tables, for
-// per-kernel parity checks, and the host-driven path that finishes queries a
-// batch could not finish on the device.
+// per-kernel parity checks.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -8,16 +7,6 @@
 #include "gs_host.h"
 
 using namespace gs;
-
-namespace gs {
-
-gs_status fallback_query(gs_batch *b, uint32_t i) {
-  (void)b;
-  (void)i;
-  return GS_OK;
-}
-
-}  // namespace gs
 
 namespace {
 

@@ -57,9 +57,14 @@ struct gs_graph {
   uint32_t *sig;
   uint32_t *type_count;     // host copy [T]
   uint64_t hash;            // content hash (tuning cache key)
+  void *cache;              // batches reused by gs_match / gs_match_batch
+  void *fallback;           // context of the chunked join
 };
 
 namespace gs {
+
+void release_cache(gs_graph *g);
+void release_fallback(gs_graph *g);
 
 // ------------------------------------------------------------ primitives
 // Exclusive prefix sum of n uint32 counts into out[0..n] (out[n] = total),

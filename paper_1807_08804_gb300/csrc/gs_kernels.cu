@@ -207,6 +207,7 @@ __global__ void k_plan(Wave W, const uint32_t *type_count) {
       cur = (uint32_t)best;
     }
     Q.nvisit = nv;
+    atomicMax(&W.ctrl->max_nvisit, nv);
   }
 }
 
@@ -285,26 +286,38 @@ __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W, int mode, ui
   const uint64_t warps = gthreads() / 32;
   const uint32_t nsel = mode == 0 ? W.nq : W.nqv;
   const uint64_t items = (uint64_t)nsel * G.ipg;
-  for (uint64_t it = gtid() / 32; it < items; it += warps) {
-    const uint32_t s = (uint32_t)(it / G.ipg), c = (uint32_t)(it % G.ipg);
-    uint32_t gqv = 0;
-    uint32_t cnt = 0;
-    if (sel_slot(W, mode, step, s, gqv)) {
-      const uint32_t *slot = slot_of(W, gqv);
-      const uint32_t w1 = c * 32 + lane;
-      uint32_t sw = w1 < G.W1 ? slot[G.W0 + w1] : 0;
-      uint32_t m = __ballot_sync(kFull, sw != 0);
+  constexpr int kU = 4;  // items per warp iteration: their summary loads overlap
+  for (uint64_t it0 = (gtid() / 32) * kU; it0 < items; it0 += warps * kU) {
+    uint32_t sw[kU];
+    const uint32_t *slots[kU];
+    bool live[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint64_t it = it0 + u;
+      uint32_t gqv = 0;
+      live[u] = it < items && sel_slot(W, mode, step, (uint32_t)(it / G.ipg), gqv);
+      slots[u] = live[u] ? slot_of(W, gqv) : nullptr;
+      const uint32_t w1 = (uint32_t)(it % G.ipg) * 32 + lane;
+      sw[u] = (live[u] && w1 < G.W1) ? slots[u][G.W0 + w1] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint64_t it = it0 + u;
+      if (it >= items) break;
+      uint32_t cnt = 0;
+      const uint32_t c = (uint32_t)(it % G.ipg);
+      uint32_t m = __ballot_sync(kFull, sw[u] != 0);
       while (m) {
         int j = __ffs(m) - 1;
         m &= m - 1;
-        uint32_t swj = __shfl_sync(kFull, sw, j);
+        uint32_t swj = __shfl_sync(kFull, sw[u], j);
         uint32_t w0 = (c * 32 + j) * 32 + lane;
-        if ((swj >> lane) & 1u) cnt += __popc(slot[w0]);
+        if ((swj >> lane) & 1u) cnt += __popc(slots[u][w0]);
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
+      if (lane == 0) W.ccount[it] = cnt;
     }
-    if (lane == 0) W.ccount[it] = cnt;
   }
 }
 
@@ -633,6 +646,7 @@ __global__ void k_prologue(Wave W) {
     W.ctrl->lvl_top = 0;
     W.ctrl->out_top = 0;
     W.ctrl->out_rows_total = 0;
+    W.ctrl->max_nvisit = 0;
   }
 }
 
@@ -933,7 +947,7 @@ __global__ void __launch_bounds__(kThreads) k_join_write(Wave W, uint32_t s) {
         uint32_t *o = dst + at * width;
         for (uint32_t i = 0; i <= s; ++i) o[i] = row[i];
         o[s + 1] = cand;
-        if (final) W.out_q[rbase + at] = qi;
+        if (final && W.out_q) W.out_q[rbase + at] = qi;
       }
       p += __popc(m);
       written += __popc(m);
@@ -943,21 +957,27 @@ __global__ void __launch_bounds__(kThreads) k_join_write(Wave W, uint32_t s) {
   }
 }
 
-// Query-order layout of the sorted rows.
+// Query-order layout of the sorted rows, and of the rows of queries whose
+// output is too large for the one-block sort (sorted by the radix path).
+__device__ __forceinline__ bool small_output(const DQuery &Q, const QState &S) {
+  return S.out_rows <= kSmallRows && S.out_rows * Q.k <= kSmallWords;
+}
+
 __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
-  __shared__ uint64_t sm[2][32];
-  __shared__ uint64_t carry[2];
+  __shared__ uint64_t sm[3][32];
+  __shared__ uint64_t carry[3];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) { carry[0] = 0; carry[1] = 0; }
+  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
   __syncthreads();
   for (uint32_t base = 0; base < W.nq; base += blockDim.x) {
     const uint32_t qi = base + threadIdx.x;
-    uint64_t v[2] = {0, 0}, ex[2];
+    uint64_t v[3] = {0, 0, 0}, ex[3];
     if (qi < W.nq && W.dq[qi].status == QS_OK) {
       v[0] = W.qs[qi].out_rows;
       v[1] = W.qs[qi].out_rows * W.dq[qi].k;
+      v[2] = small_output(W.dq[qi], W.qs[qi]) ? 0 : W.qs[qi].out_rows;
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < 3; ++a) {
       uint64_t x = v[a];
       for (int o = 1; o < 32; o <<= 1) {
         uint64_t y = __shfl_up_sync(kFull, x, o);
@@ -967,7 +987,7 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
       ex[a] = x - v[a];
     }
     __syncthreads();
-    if (warp < 2) {
+    if (warp < 3) {
       uint64_t x = sm[warp][lane];
       for (int o = 1; o < 32; o <<= 1) {
         uint64_t y = __shfl_up_sync(kFull, x, o);
@@ -979,23 +999,79 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
     if (qi < W.nq) {
       W.qs[qi].fin_row_base = carry[0] + ex[0] + (warp ? sm[0][warp - 1] : 0);
       W.qs[qi].fin_word_base = carry[1] + ex[1] + (warp ? sm[1][warp - 1] : 0);
+      W.qs[qi].lrg_row_base = carry[2] + ex[2] + (warp ? sm[2][warp - 1] : 0);
     }
     __syncthreads();
-    if (threadIdx.x == 0) { carry[0] += sm[0][31]; carry[1] += sm[1][31]; }
+    if (threadIdx.x < 3) carry[threadIdx.x] += sm[threadIdx.x][31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) W.ctrl->len[6] = carry[2];
+}
+
+// One block sorts one query's rows in shared memory (bitonic network over
+// row indices, rows compared in query-vertex order) and writes them sorted.
+__device__ __forceinline__ bool row_less(const uint32_t *rows, uint32_t k, uint32_t n, uint32_t a, uint32_t b) {
+  if (a >= n) return false;
+  if (b >= n) return true;
+  const uint32_t *x = rows + a * k, *y = rows + b * k;
+  for (uint32_t u = 0; u < k; ++u)
+    if (x[u] != y[u]) return x[u] < y[u];
+  return false;
+}
+
+__global__ void __launch_bounds__(256) k_small_sort(Wave W) {
+  extern __shared__ uint32_t smem[];
+  uint32_t *rows = smem;                 // [kSmallWords]
+  uint32_t *idx = smem + kSmallWords;    // [kSmallRows]
+  for (uint32_t qi = blockIdx.x; qi < W.nq; qi += gridDim.x) {
+    const DQuery &Q = W.dq[qi];
+    const QState &S = W.qs[qi];
+    const uint32_t n = (uint32_t)S.out_rows, k = Q.k;
+    if (Q.status != QS_OK || n == 0 || !small_output(Q, S)) continue;
+    for (uint32_t t = threadIdx.x; t < n * k; t += blockDim.x) {
+      const uint32_t i = t / k, u = t % k;
+      rows[t] = W.out[S.out_word_base + (uint64_t)i * k + Q.pos[u]];
+    }
+    uint32_t np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (uint32_t t = threadIdx.x; t < np2; t += blockDim.x) idx[t] = t;
+    __syncthreads();
+    for (uint32_t size = 2; size <= np2; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t t = threadIdx.x; t < np2; t += blockDim.x) {
+          const uint32_t p = t ^ stride;
+          if (p > t) {
+            const bool up = (t & size) == 0;
+            const uint32_t a = idx[t], b = idx[p];
+            const bool swap = up ? row_less(rows, k, n, b, a) : row_less(rows, k, n, a, b);
+            if (swap) { idx[t] = b; idx[p] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    uint32_t *dst = W.out_final + S.fin_word_base;
+    for (uint32_t t = threadIdx.x; t < n * k; t += blockDim.x) dst[t] = rows[idx[t / k] * k + t % k];
     __syncthreads();
   }
 }
 
 // ============================================================ sort + gather
+// Rows of large outputs, in output-pool order, as the initial permutation.
 __global__ void k_iota(Wave W, uint32_t *perm) {
   const uint64_t n = W.ctrl->out_rows_total;
-  for (uint64_t i = gtid(); i < n; i += gthreads()) perm[i] = (uint32_t)i;
+  for (uint64_t r = gtid(); r < n; r += gthreads()) {
+    const uint32_t qi = W.out_q[r];
+    const DQuery &Q = W.dq[qi];
+    const QState &S = W.qs[qi];
+    if (!small_output(Q, S)) perm[S.lrg_row_base + (r - S.out_row_base)] = (uint32_t)r;
+  }
 }
 
 // key[i] = id of query vertex `col` in output row perm[i] (0 past the row's
 // width), or the slot query when col == kMaxK (the most significant pass).
 __global__ void k_sort_keys(Wave W, const uint32_t *perm, uint32_t *key, uint32_t col) {
-  const uint64_t n = W.ctrl->out_rows_total;
+  const uint64_t n = W.ctrl->len[6];
   for (uint64_t i = gtid(); i < n; i += gthreads()) {
     const uint32_t row = perm[i];
     const uint32_t qi = W.out_q[row];
@@ -1006,16 +1082,16 @@ __global__ void k_sort_keys(Wave W, const uint32_t *perm, uint32_t *key, uint32_
   }
 }
 
-// Sorted rows in query-vertex column order, laid out query by query.
+// Sorted large rows in query-vertex column order, laid out query by query.
 __global__ void k_gather(Wave W, const uint32_t *perm) {
-  const uint64_t n = W.ctrl->out_rows_total;
+  const uint64_t n = W.ctrl->len[6];
   for (uint64_t i = gtid(); i < n; i += gthreads()) {
     const uint32_t row = perm[i];
     const uint32_t qi = W.out_q[row];
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
     const uint32_t *src = W.out + S.out_word_base + (uint64_t)(row - S.out_row_base) * Q.k;
-    uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.fin_row_base) * Q.k;
+    uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.lrg_row_base) * Q.k;
     for (uint32_t u = 0; u < Q.k; ++u) dst[u] = src[Q.pos[u]];
   }
 }
@@ -1048,6 +1124,12 @@ __global__ void k_epilogue_advance(Wave W) {
 }
 
 inline unsigned grid_for(int sms, int per_sm) { return (unsigned)(sms * per_sm); }
+// Blocks for a fixed number of warp-sized items, at most the persistent grid.
+inline unsigned grid_items(uint64_t warp_items, int sms) {
+  uint64_t b = (warp_items + kThreads / 32 - 1) / (kThreads / 32);
+  if (b == 0) b = 1;
+  return (unsigned)(b < (uint64_t)sms * 8 ? b : (uint64_t)sms * 8);
+}
 inline unsigned blocks_for(uint64_t n, unsigned per) {
   uint64_t b = (n + per - 1) / per;
   return (unsigned)(b ? b : 1);
@@ -1063,17 +1145,22 @@ void launch_plan(const Wave &W, const uint32_t *type_count, cudaStream_t s, int 
   k_plan<<<blocks_for(W.nq + 1, 128), 128, 0, s>>>(W, type_count);
   k_owners<<<blocks_for(W.nq, 128), 128, 0, s>>>(W);
 }
-void launch_filter(const Wave &W, cudaStream_t s, int sms) { k_filter<<<grid_for(sms, 8), kThreads, 0, s>>>(W); }
+void launch_filter(const Wave &W, cudaStream_t s, int sms) {
+  k_filter<<<grid_items((uint64_t)W.nq * W.G.W1, sms), kThreads, 0, s>>>(W);
+}
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms) {
-  k_compact_count<<<grid_for(sms, 8), kThreads, 0, s>>>(W, mode, step);
+  const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.ipg;
+  k_compact_count<<<grid_items(items, sms), kThreads, 0, s>>>(W, mode, step);
 }
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint64_t cap,
                           cudaStream_t s, int sms) {
-  k_compact_write<<<grid_for(sms, 8), kThreads, 0, s>>>(W, mode, step, scan, dst, cap);
+  const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.ipg;
+  k_compact_write<<<grid_items(items, sms), kThreads, 0, s>>>(W, mode, step, scan, dst, cap);
 }
 void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms) {
   const unsigned g = grid_for(sms, 8);
   switch (group) {
+    case 4: k_explore<4><<<g, kThreads, 0, s>>>(W, step); break;
     case 8: k_explore<8><<<g, kThreads, 0, s>>>(W, step); break;
     case 16: k_explore<16><<<g, kThreads, 0, s>>>(W, step); break;
     default: k_explore<32><<<g, kThreads, 0, s>>>(W, step); break;
@@ -1082,6 +1169,7 @@ void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int
 void launch_refine(const Wave &W, uint32_t round, int group, cudaStream_t s, int sms) {
   const unsigned g = grid_for(sms, 8);
   switch (group) {
+    case 4: k_refine<4><<<g, kThreads, 0, s>>>(W, round); break;
     case 8: k_refine<8><<<g, kThreads, 0, s>>>(W, round); break;
     case 16: k_refine<16><<<g, kThreads, 0, s>>>(W, round); break;
     default: k_refine<32><<<g, kThreads, 0, s>>>(W, round); break;
@@ -1097,12 +1185,15 @@ void launch_ec_limit(const Wave &W, cudaStream_t s, int sms) {
 void launch_ec(const Wave &W, bool write, int group, cudaStream_t s, int sms) {
   const unsigned g = grid_for(sms, 8);
   switch (group) {
+    case 4: if (write) k_ec<4, true><<<g, kThreads, 0, s>>>(W); else k_ec<4, false><<<g, kThreads, 0, s>>>(W); break;
     case 8: if (write) k_ec<8, true><<<g, kThreads, 0, s>>>(W); else k_ec<8, false><<<g, kThreads, 0, s>>>(W); break;
     case 16: if (write) k_ec<16, true><<<g, kThreads, 0, s>>>(W); else k_ec<16, false><<<g, kThreads, 0, s>>>(W); break;
     default: if (write) k_ec<32, true><<<g, kThreads, 0, s>>>(W); else k_ec<32, false><<<g, kThreads, 0, s>>>(W); break;
   }
 }
-void launch_clear(const Wave &W, cudaStream_t s, int sms) { k_clear<<<grid_for(sms, 8), kThreads, 0, s>>>(W); }
+void launch_clear(const Wave &W, cudaStream_t s, int sms) {
+  k_clear<<<grid_items((uint64_t)W.nqv * W.G.ipg, sms), kThreads, 0, s>>>(W);
+}
 void launch_join0(const Wave &W, cudaStream_t s, int sms) {
   k_join0_rows<<<blocks_for(W.nq, 256), 256, 0, s>>>(W);
   k_level_alloc<<<1, 1024, 0, s>>>(W, 0);
@@ -1111,6 +1202,7 @@ void launch_join0(const Wave &W, cudaStream_t s, int sms) {
 void launch_join_count(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms) {
   const unsigned g = grid_for(sms, 8);
   switch (group) {
+    case 4: k_join_count<4><<<g, kThreads, 0, s>>>(W, lvl); break;
     case 8: k_join_count<8><<<g, kThreads, 0, s>>>(W, lvl); break;
     case 16: k_join_count<16><<<g, kThreads, 0, s>>>(W, lvl); break;
     default: k_join_count<32><<<g, kThreads, 0, s>>>(W, lvl); break;
@@ -1123,12 +1215,23 @@ void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s) { k_level_a
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms) {
   const unsigned g = grid_for(sms, 8);
   switch (group) {
+    case 4: k_join_write<4><<<g, kThreads, 0, s>>>(W, lvl); break;
     case 8: k_join_write<8><<<g, kThreads, 0, s>>>(W, lvl); break;
     case 16: k_join_write<16><<<g, kThreads, 0, s>>>(W, lvl); break;
     default: k_join_write<32><<<g, kThreads, 0, s>>>(W, lvl); break;
   }
 }
 void launch_final_bases(const Wave &W, cudaStream_t s) { k_final_bases<<<1, 1024, 0, s>>>(W); }
+void launch_small_sort(const Wave &W, cudaStream_t s, int sms) {
+  static bool attr = false;
+  const int bytes = (int)(4 * (kSmallWords + kSmallRows));
+  if (!attr) {
+    cudaFuncSetAttribute(k_small_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr = true;
+  }
+  const unsigned g = W.nq < (uint32_t)sms * 2 ? (W.nq ? W.nq : 1) : (unsigned)sms * 2;
+  k_small_sort<<<g, 256, bytes, s>>>(W);
+}
 void launch_iota(const Wave &W, uint32_t *perm, cudaStream_t s, int sms) { k_iota<<<grid_for(sms, 4), kThreads, 0, s>>>(W, perm); }
 void launch_sort_keys(const Wave &W, const uint32_t *perm, uint32_t *key, uint32_t col, cudaStream_t s, int sms) {
   k_sort_keys<<<grid_for(sms, 4), kThreads, 0, s>>>(W, perm, key, col);

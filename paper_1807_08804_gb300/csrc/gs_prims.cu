@@ -6,6 +6,8 @@
 // Sizes are read from device memory so that a whole pipeline can be captured
 // once in a CUDA graph and replayed: each kernel is persistent over tiles and
 // learns how many tiles exist from *d_n.
+#include <algorithm>
+
 #include "gs_internal.h"
 
 namespace gs {
@@ -13,13 +15,20 @@ namespace gs {
 namespace {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
-constexpr uint64_t kScanTile = kScanThreads * kScanItems;  // 4096
+constexpr uint64_t kScanMaxTiles = 8192;
+
+// Tile of the scan: 1,024 items while that gives at most 8,192 tiles (short
+// serial chains for the small scans of the pipeline), larger beyond.  Every
+// kernel of one scan derives it from the same n.
+__device__ __forceinline__ uint64_t scan_rounds(uint64_t n) {
+  uint64_t r = (n + kScanThreads * kScanMaxTiles - 1) / (kScanThreads * kScanMaxTiles);
+  return r < 4 ? 4 : r;
+}
 
 constexpr int kRadixThreads = 256;
 constexpr int kRadixWarps = kRadixThreads / 32;
-constexpr int kRadixRounds = 16;
-constexpr uint64_t kRadixTile = kRadixThreads * kRadixRounds;  // 4096
+constexpr int kRadixRounds = 4;
+constexpr uint64_t kRadixTile = kRadixThreads * kRadixRounds;  // 1024
 constexpr int kRadixBins = 256;
 
 // Exclusive scan of one value per thread over a 256-thread block.
@@ -53,12 +62,13 @@ template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T *in, const uint64_t *d_n, uint64_t *tile_sums) {
   __shared__ uint64_t red[kScanThreads / 32];
   const uint64_t n = *d_n;
-  const uint64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  const uint64_t rounds = scan_rounds(n), tile = rounds * kScanThreads;
+  const uint64_t ntiles = (n + tile - 1) / tile;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     uint64_t s = 0;
-    const uint64_t base = t * kScanTile;
+    const uint64_t base = t * tile;
 #pragma unroll 4
-    for (int j = 0; j < kScanItems; ++j) {
+    for (uint64_t j = 0; j < rounds; ++j) {
       uint64_t i = base + (uint64_t)j * kScanThreads + threadIdx.x;
       if (i < n) s += (uint64_t)in[i];
     }
@@ -79,7 +89,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T *in, const
 __global__ void __launch_bounds__(kScanThreads) k_scan_partials(uint64_t *tile_sums, const uint64_t *d_n, uint64_t *out) {
   __shared__ uint64_t smem[kScanThreads / 32];
   const uint64_t n = *d_n;
-  const uint64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  const uint64_t tile = scan_rounds(n) * kScanThreads;
+  const uint64_t ntiles = (n + tile - 1) / tile;
   uint64_t carry = 0;
   for (uint64_t base = 0; base < ntiles; base += kScanThreads) {
     uint64_t i = base + threadIdx.x;
@@ -96,11 +107,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const T *in, const u
                                                              uint64_t *out) {
   __shared__ uint64_t smem[kScanThreads / 32];
   const uint64_t n = *d_n;
-  const uint64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  const uint64_t rounds = scan_rounds(n), tile = rounds * kScanThreads;
+  const uint64_t ntiles = (n + tile - 1) / tile;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     uint64_t carry = tile_sums[t];
-    const uint64_t base = t * kScanTile;
-    for (int j = 0; j < kScanItems; ++j) {
+    const uint64_t base = t * tile;
+    for (uint64_t j = 0; j < rounds; ++j) {
       uint64_t i = base + (uint64_t)j * kScanThreads + threadIdx.x;
       uint64_t v = i < n ? (uint64_t)in[i] : 0, tot;
       uint64_t ex = block_exclusive_scan(v, &tot, smem);
@@ -113,7 +125,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const T *in, const u
 template <typename T>
 void scan_impl(const T *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp, cudaStream_t s,
                int num_sms) {
-  uint64_t tiles = (max_n + kScanTile - 1) / kScanTile;
+  uint64_t tiles = std::min<uint64_t>((max_n + 1023) / 1024, kScanMaxTiles);
   unsigned grid = (unsigned)(tiles < (uint64_t)num_sms * 8 ? (tiles ? tiles : 1) : (uint64_t)num_sms * 8);
   k_scan_reduce<T><<<grid, kScanThreads, 0, s>>>(in, d_n, tmp);
   k_scan_partials<<<1, kScanThreads, 0, s>>>(tmp, d_n, out);
@@ -199,7 +211,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const uint32_t 
 
 }  // namespace
 
-uint64_t scan_tmp_words(uint64_t max_n) { return (max_n + kScanTile - 1) / kScanTile + 1; }
+uint64_t scan_tmp_words(uint64_t max_n) { return std::min<uint64_t>((max_n + 1023) / 1024, kScanMaxTiles) + 1; }
 
 void scan_u32(const uint32_t *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp, cudaStream_t s,
               int num_sms) {

@@ -1,16 +1,296 @@
-// Serving loop (continuous batching); filled in below the matching engine.
+// Serving: a request loop over a device-resident graph with continuous
+// batching.  Requests queue on submit; a worker thread admits them into
+// micro-batches whenever a slot is free and the working-set budget allows,
+// so requests that arrive while others are on the GPU join the next
+// micro-batch instead of waiting for the whole queue to drain.  Each slot has
+// its own stream, so several micro-batches overlap on the device.  Results
+// are kept per ticket until polled.
+//
+// Admission estimate per query (from candidate-set sizes): a bound vertex has
+// one candidate, a typed vertex at most the number of data vertices of its
+// type, an untyped one at most V; each candidate costs its list entry, its
+// candidate-edge table entries and a bitmap slot share.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
 #include "gs_host.h"
 
 using namespace gs;
 
-extern "C" gs_status gs_serve_create(gs_graph *, const gs_serve_opts *, gs_server **out) {
-  if (out) *out = nullptr;
-  return fail(GS_ERR_UNSUPPORTED, "serving not built yet");
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+  uint64_t ticket = 0;
+  uint32_t k = 0, m = 0;
+  std::vector<uint32_t> vtype, vbind, esrc, edst, erel;
+  gs_match_opts opts{};
+  Clock::time_point t_submit;
+  uint64_t est = 0;
+  gs_query view() const {
+    return gs_query{k, m, vtype.data(), vbind.data(), esrc.data(), edst.data(), erel.data()};
+  }
+};
+
+struct Done {
+  gs_result r;
+  double latency_s;
+};
+
+struct Slot {
+  gs_batch *b = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool busy = false;
+  std::vector<Req> reqs;
+  uint64_t est = 0;
+  gs_match_opts opts{};
+};
+
+bool same_opts(const gs_match_opts &a, const gs_match_opts &b) {
+  return a.cap == b.cap && a.mode == b.mode && a.max_refine_rounds == b.max_refine_rounds &&
+         a.chunk_bytes == b.chunk_bytes;
 }
-extern "C" gs_status gs_serve_submit(gs_server *, const gs_query *, const gs_match_opts *, uint64_t *) {
-  return fail(GS_ERR_UNSUPPORTED, "serving not built yet");
+
+}  // namespace
+
+struct gs_server {
+  gs_graph *g = nullptr;
+  gs_serve_opts o{};
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  std::deque<Req> pending;
+  std::unordered_map<uint64_t, Done> done;
+  std::unordered_map<uint64_t, int> inflight;  // ticket -> slot
+  uint64_t next_ticket = 1;
+  uint64_t inflight_est = 0;
+  std::vector<Slot> slots;
+  std::thread worker;
+  gs_status worker_error = GS_OK;
+  std::string worker_msg;
+};
+
+namespace {
+
+uint64_t estimate(const gs_graph *g, const gs_query &q) {
+  const uint64_t slot_bytes = 4 * (((uint64_t)g->d.W0 + g->d.W1 + 31) / 32 * 32);
+  uint64_t est = 1 << 16;
+  for (uint32_t u = 0; u < q.k; ++u) {
+    uint64_t c = q.vbind[u] != GS_UNBOUND ? 1 : (q.vtype[u] != GS_ANY && q.vtype[u] < g->d.T ? g->type_count[q.vtype[u]] : g->d.V);
+    uint64_t deg = 0;
+    for (uint32_t j = 0; j < q.m; ++j) deg += (q.esrc[j] == u) + (q.edst[j] == u);
+    est += c * 4 * (2 + deg) + slot_bytes;
+  }
+  return est;
 }
-extern "C" gs_status gs_serve_poll(gs_server *, uint64_t, gs_result *, double *) {
-  return fail(GS_ERR_UNSUPPORTED, "serving not built yet");
+
+// Finish a slot whose micro-batch completed: results move to `done`.
+void harvest(gs_server *s, Slot &sl) {
+  gs_status st = batch_finish(sl.b);
+  std::vector<gs_result> outs(sl.reqs.size());
+  if (st == GS_OK) st = batch_fetch(sl.b, outs.data());
+  const auto now = Clock::now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (size_t i = 0; i < sl.reqs.size(); ++i) {
+    Done d;
+    if (st == GS_OK) {
+      d.r = outs[i];
+    } else {
+      memset(&d.r, 0, sizeof(d.r));
+      d.r.status = st;
+    }
+    d.latency_s = std::chrono::duration<double>(now - sl.reqs[i].t_submit).count();
+    s->inflight.erase(sl.reqs[i].ticket);
+    s->done.emplace(sl.reqs[i].ticket, d);
+  }
+  s->inflight_est -= sl.est;
+  sl.reqs.clear();
+  sl.est = 0;
+  sl.busy = false;
 }
-extern "C" gs_status gs_serve_destroy(gs_server *) { return GS_OK; }
+
+// Take the next micro-batch from the queue (FIFO, same options, within the
+// budget; the head is always admitted when nothing is in flight).
+std::vector<Req> admit(gs_server *s, uint64_t &est_sum) {
+  std::vector<Req> take;
+  est_sum = 0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  while (!s->pending.empty() && take.size() < s->o.max_batch) {
+    Req &r = s->pending.front();
+    if (!take.empty() && !same_opts(take.front().opts, r.opts)) break;
+    const bool fits = s->inflight_est + est_sum + r.est <= s->o.budget_bytes;
+    if (!fits && !(take.empty() && s->inflight_est == 0)) break;
+    est_sum += r.est;
+    take.push_back(std::move(r));
+    s->pending.pop_front();
+  }
+  s->inflight_est += est_sum;
+  return take;
+}
+
+gs_status launch(gs_server *s, Slot &sl, std::vector<Req> &&reqs, uint64_t est) {
+  std::vector<gs_query> qs;
+  qs.reserve(reqs.size());
+  for (auto &r : reqs) qs.push_back(r.view());
+  const gs_match_opts &o = reqs.front().opts;
+  if (!sl.b || !batch_rearm(sl.b, qs.data(), (uint32_t)qs.size(), &o)) {
+    if (sl.b) batch_destroy(sl.b);
+    sl.b = nullptr;
+    gs_status st = batch_create_capacity(s->g, &o, s->o.max_batch, s->o.max_batch * 10, s->o.max_batch * 16, &sl.b);
+    if (st != GS_OK) return st;
+    if (!batch_rearm(sl.b, qs.data(), (uint32_t)qs.size(), &o)) return fail(GS_ERR_INVALID, "serving slot too small");
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto &r : reqs) s->inflight[r.ticket] = (int)(&sl - s->slots.data());
+  }
+  sl.reqs = std::move(reqs);
+  sl.est = est;
+  sl.opts = o;
+  sl.busy = true;
+  gs_status st = run_waves(sl.b);
+  sl.b->ran = st == GS_OK;
+  if (st != GS_OK) return st;
+  GS_CUDA(cudaEventRecord(sl.ev, sl.b->stream));
+  return GS_OK;
+}
+
+void worker_main(gs_server *s) {
+  cudaSetDevice(s->g->device);
+  for (Slot &sl : s->slots) cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+  for (;;) {
+    bool worked = false;
+    for (Slot &sl : s->slots) {
+      if (sl.busy && cudaEventQuery(sl.ev) == cudaSuccess) {
+        harvest(s, sl);
+        worked = true;
+      }
+    }
+    for (Slot &sl : s->slots) {
+      if (sl.busy) continue;
+      uint64_t est = 0;
+      std::vector<Req> reqs = admit(s, est);
+      if (reqs.empty()) break;
+      gs_status st = launch(s, sl, std::move(reqs), est);
+      if (st != GS_OK) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->worker_error = st;
+        s->worker_msg = gs_last_error();
+        for (auto &r : sl.reqs) {
+          Done d;
+          memset(&d.r, 0, sizeof(d.r));
+          d.r.status = st;
+          d.latency_s = 0;
+          s->inflight.erase(r.ticket);
+          s->done.emplace(r.ticket, d);
+        }
+        s->inflight_est -= sl.est;
+        sl.reqs.clear();
+        sl.busy = false;
+      }
+      worked = true;
+    }
+    std::unique_lock<std::mutex> lk(s->mu);
+    bool any_busy = false;
+    for (Slot &sl : s->slots) any_busy |= sl.busy;
+    if (s->stop && !any_busy) break;
+    if (!worked) {
+      if (any_busy) {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+      } else if (s->pending.empty()) {
+        s->cv.wait_for(lk, std::chrono::milliseconds(2));
+      }
+    }
+  }
+  for (Slot &sl : s->slots) {
+    if (sl.b) batch_destroy(sl.b);
+    sl.b = nullptr;
+    if (sl.ev) cudaEventDestroy(sl.ev);
+  }
+}
+
+}  // namespace
+
+extern "C" gs_status gs_serve_create(gs_graph *g, const gs_serve_opts *opts, gs_server **out) {
+  if (!g || !out) return fail(GS_ERR_INVALID, "gs_serve_create: null argument");
+  *out = nullptr;
+  gs_server *s = new gs_server();
+  s->g = g;
+  if (opts) s->o = *opts;
+  if (!s->o.budget_bytes) s->o.budget_bytes = 40ull << 30;
+  if (!s->o.slots) s->o.slots = 4;
+  if (!s->o.max_batch) s->o.max_batch = 256;
+  if (!s->o.queue_depth) s->o.queue_depth = 65536;
+  if (s->o.slots > 64 || s->o.max_batch > 65536) {
+    delete s;
+    return fail(GS_ERR_INVALID, "serving options out of range");
+  }
+  s->slots.resize(s->o.slots);
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return GS_OK;
+}
+
+extern "C" gs_status gs_serve_submit(gs_server *s, const gs_query *q, const gs_match_opts *opts, uint64_t *ticket) {
+  if (!s || !q || !ticket) return fail(GS_ERR_INVALID, "gs_serve_submit: null argument");
+  // validate now so that a bad query fails at submit
+  DQuery d;
+  gs_status st = pack_query(s->g->d, q, opts, &d);
+  if (st != GS_OK) return st;
+  Req r;
+  r.k = q->k;
+  r.m = q->m;
+  r.vtype.assign(q->vtype, q->vtype + q->k);
+  r.vbind.assign(q->vbind, q->vbind + q->k);
+  r.esrc.assign(q->esrc, q->esrc + q->m);
+  r.edst.assign(q->edst, q->edst + q->m);
+  r.erel.assign(q->erel, q->erel + q->m);
+  if (opts) r.opts = *opts;
+  r.opts.cuda_stream = nullptr;
+  r.t_submit = Clock::now();
+  r.est = estimate(s->g, *q);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->pending.size() >= s->o.queue_depth) return fail(GS_ERR_BUSY, "serving queue full");
+    r.ticket = s->next_ticket++;
+    *ticket = r.ticket;
+    s->pending.push_back(std::move(r));
+  }
+  s->cv.notify_one();
+  return GS_OK;
+}
+
+extern "C" gs_status gs_serve_poll(gs_server *s, uint64_t ticket, gs_result *out, double *latency_s) {
+  if (!s || !out) return fail(GS_ERR_INVALID, "gs_serve_poll: null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->done.find(ticket);
+  if (it == s->done.end()) {
+    if (ticket == 0 || ticket >= s->next_ticket) return fail(GS_ERR_INVALID, "unknown ticket");
+    return GS_ERR_NOT_READY;
+  }
+  *out = it->second.r;
+  if (latency_s) *latency_s = it->second.latency_s;
+  s->done.erase(it);
+  return GS_OK;
+}
+
+extern "C" gs_status gs_serve_destroy(gs_server *s) {
+  if (!s) return GS_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto &kv : s->done) gs_result_free(&kv.second.r);
+  delete s;
+  return GS_OK;
+}

@@ -112,11 +112,67 @@ def test_closed_forms():
         assert r.count == (perm(7, s) if s <= 7 else 0)
 
 
+def test_large_outputs_take_the_radix_path():
+    """Outputs above the one-block sort limit (2,048 rows) are sorted by the
+    global radix path; a batch mixes both kinds."""
+    n = 9
+    g = graph_from_triples(n, complete_digraph_triples(n))
+    og = O.OracleGraph.from_graph(g)
+    dg = gs.DeviceGraph(g)
+    qs = [query(k, [(i, i + 1, 0) for i in range(k - 1)]) for k in (2, 4, 5, 3)]
+    qs.append(query(4, [(0, 1, 0), (0, 2, 0), (0, 3, 0)], vbind=[I.UNBOUND, 3, I.UNBOUND, I.UNBOUND]))
+    res = gs.match_batch(dg, qs, cap=1 << 20)
+    for i, (q, r) in enumerate(zip(qs, res)):
+        assert_same(r, O.match(og, q, cap=1 << 20), i)
+    assert res[2].count == 15120
+    r = gs.match(dg, qs[2], cap=1 << 20)
+    assert_same(r, O.match(og, qs[2], cap=1 << 20))
+
+
+def test_more_embeddings_than_cap_returns_the_smallest_rows():
+    """count > cap: the exact count and fingerprint, and the cap
+    lexicographically smallest embeddings (the chunked path's running top-cap)."""
+    n = 9
+    g = graph_from_triples(n, complete_digraph_triples(n))
+    og = O.OracleGraph.from_graph(g)
+    dg = gs.DeviceGraph(g)
+    qs = [query(5, [(i, i + 1, 0) for i in range(4)]), query(4, [(i, (i + 1) % 4, 0) for i in range(4)]),
+          query(1, [], vtype=[0]), query(3, [(0, 1, 0), (2, 1, 0)])]
+    for cap in (1, 100, 5000):
+        res = gs.match_batch(dg, qs, cap=cap)
+        for i, (q, r) in enumerate(zip(qs, res)):
+            o = O.match(og, q, cap=cap)
+            assert_same(r, o, (cap, i))
+            assert r.truncated == (o.count > cap)
+
+
+def test_chunked_join_with_small_level_buffers(monkeypatch):
+    """Partial embeddings that overflow the level budget finish on the
+    chunked depth-first path; tiny buffers force many chunks."""
+    from math import perm
+    monkeypatch.setenv("GS_FALLBACK_DEPTH_WORDS", "32768")
+    monkeypatch.setenv("GS_FALLBACK_DEPTH_ROWS", "8192")
+    n = 12
+    g = graph_from_triples(n, complete_digraph_triples(n))
+    og = O.OracleGraph.from_graph(g)
+    dg = gs.DeviceGraph(g)  # fresh graph: fresh chunked-join context with the small buffers
+    path6 = query(6, [(i, i + 1, 0) for i in range(5)])
+    star = query(5, [(0, i, 0) for i in range(1, 5)])
+    res = gs.match_batch(dg, [path6, star], cap=1 << 20, chunk_bytes=1 << 16)
+    assert res[0].count == perm(12, 6)
+    for q, r in zip([path6, star], res):
+        assert_same(r, O.match(og, q, cap=1 << 20))
+    cnt = gs.match_batch(dg, [path6, star], cap=0, mode=gs.GS_COUNT_ONLY, chunk_bytes=1 << 16)
+    assert [(c.count, c.fingerprint) for c in cnt] == [(r.count, r.fingerprint) for r in res]
+    top = gs.match(dg, path6, cap=777, chunk_bytes=1 << 16)
+    assert_same(top, O.match(og, path6, cap=777))
+
+
 def test_results_invariant_to_schedule(small):
     g, qs, og, dg = small
     sub = qs[:40]
     base = gs.match_batch(dg, sub, cap=1 << 20)
-    for group in (8, 16, 32):
+    for group in (4, 8, 16, 32):
         for use_graph in (True, False):
             for rounds in (0, 1, 3):
                 b = gs.Batch(dg, sub, cap=1 << 20)
