@@ -208,6 +208,29 @@ gs_status gs_inspect_edge_table(gs_graph *g, const gs_query *q, uint32_t e, uint
                                 uint64_t *nkeys, uint64_t *nvals);
 
 /* ------------------------------------------------------------------------
+ * Candidate filter without allocation.  The thesis has no counterpart: this
+ * is an interface for callers that must not let the library allocate (a
+ * process that reserved its device memory budget up front, or one whose own
+ * allocator owns the device; cudaMalloc/cudaFree can also stall the device).
+ *
+ * Writes the candidates of query vertex u (binding, type and the
+ * per-direction, per-relation degree test; the same set gs_inspect_candidates
+ * reports at GS_STAGE_FILTER) in ascending order to d_ids[0 .. min(n, cap_ids))
+ * and their number n to *d_count, both device pointers owned by the caller,
+ * asynchronously on cuda_stream (NULL = default stream).
+ *
+ * It calls no allocating routine.  Its scratch is one fixed array inside the
+ * library (196,616 bytes per device, held until the process exits), which
+ * limits the graph to 2^24 vertices (larger graphs: GS_ERR_INVALID).  Every
+ * call on a device shares that array, so calls that overlap on the GPU race:
+ * serialise them.  The first call on each device looks up the array's device
+ * address; make that first call before any stream capture.
+ * Errors: GS_ERR_INVALID (null pointers, bad query, u >= k, too many vertices).
+ * ------------------------------------------------------------------------ */
+gs_status gs_filter_candidates_static(gs_graph *g, const gs_query *q, uint32_t u, uint32_t *d_ids, uint64_t cap_ids,
+                                      uint64_t *d_count, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Serving: a request loop that keeps the graph device-resident and admits
  * queries while slots and the working-set budget allow (continuous batching:
  * requests that arrive while others run are admitted as slots free up).

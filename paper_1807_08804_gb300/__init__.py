@@ -102,6 +102,7 @@ EXTRA_SIGNATURES = {
     "gs_batch_counters": (ctypes.c_int, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64),
                                          ctypes.POINTER(U64)]),
     "gs_graph_io_bytes": (ctypes.c_int, [P, ctypes.POINTER(U64), ctypes.POINTER(U64)]),
+    "gs_filter_candidates_static": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, P, U64, P, P]),
 }
 
 _lib = None
