@@ -213,6 +213,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of arrivals per serving rate (0 = skip)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--mode", default=None, choices=["enumerate", "count"],
                     help="enumerate rows (default) or count only (default for stress-16m)")
     args = ap.parse_args()
@@ -235,8 +236,13 @@ def main():
     gmode = gs.GS_COUNT_ONLY if mode == "count" else gs.GS_ENUMERATE
     cap = 0 if mode == "count" else w.cap
     dg = gs.DeviceGraph(g)
-    stream = torch.cuda.current_stream()
+    tuned = gs.tune(dg, qs, cap=cap, mode=gmode) if not args.no_tune else None  # untimed
+    # A dedicated stream: the library launches on it and the CUDA events are
+    # recorded on it (the legacy default stream would not order with it).
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     sh = stream.cuda_stream
+    assert sh != 0
     b = gs.Batch(dg, qs, cap=cap, mode=gmode, stream=sh)
     one = gs.Batch(dg, qs, cap=cap, mode=gmode, wave_queries=1, stream=sh)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -287,7 +293,7 @@ def main():
 
     # ---- one query at a time through the same pipeline
     one_ms = []
-    for _ in range(args.one_steps):
+    for _ in range(args.one_steps if args.one_steps else 0):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -296,7 +302,8 @@ def main():
         e1.record(stream)
         e1.synchronize()
         one_ms.append(e0.elapsed_time(e1))
-    one.finish()
+    if args.one_steps:
+        one.finish()
     one_tot = max_over_ranks(sum(one_ms), world, dev)
     one_qps = n * world * args.one_steps / (one_tot / 1e3) if args.one_steps else None
 
@@ -338,7 +345,7 @@ def main():
             "config": {"workload": w.name, "vertices": w.V, "edges": w.E, "queries": n, "mode": mode,
                        "query_vertices": [w.kmin, w.kmax], "p_bind": w.p_bind, "cap": cap,
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "tuned": tuned},
             "embeddings_per_s": embeddings * world * args.steps / (tot_ms / 1e3),
             "embeddings_per_step": embeddings,
             "one_at_a_time": ({"value": one_qps, "unit": "queries/s", "ms_per_step": one_tot / args.one_steps,

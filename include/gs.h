@@ -185,6 +185,28 @@ gs_status gs_stats_get(gs_batch *b, gs_kernel_stats *out);
 gs_status gs_stats_reset(gs_batch *b);
 
 /* ------------------------------------------------------------------------
+ * Autotuning.  Times the captured pipeline on the given queries for each
+ * lanes-per-work-item setting (4, 8, 16, 32: the lanes that share one
+ * candidate vertex, edge-table key or partial embedding) and each number of
+ * refinement rounds (2, 4, 8), and keeps the fastest for batches created on
+ * this graph afterwards.  Results never depend on these settings.  With
+ * cache_path != NULL the choice is read from / appended to that text file,
+ * keyed by graph content hash, GPU name and a signature of the query load
+ * (batch size class, mean k and m, bound fraction, mode).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint32_t group;          /* lanes per work item */
+  uint32_t refine_rounds;  /* refinement rounds in captured runs */
+  double ms;               /* best time of one run of the given queries */
+  uint32_t from_cache;     /* 1 if read from cache_path */
+  uint32_t configs_tried;
+} gs_tuning;
+gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts, const char *cache_path,
+                  gs_tuning *out);
+/* Set the tuned values by hand (0 = library default). */
+gs_status gs_tune_set(gs_graph *g, uint32_t group, uint32_t refine_rounds);
+
+/* ------------------------------------------------------------------------
  * Inspection of the filtering phase and the candidate-edge tables of one
  * query, for per-kernel parity checks.
  * ------------------------------------------------------------------------ */

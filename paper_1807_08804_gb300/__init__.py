@@ -63,6 +63,11 @@ class KernelStats(ctypes.Structure):
                 ("ms", ctypes.c_double * NUM_KERNEL_KINDS), ("bytes", U64 * NUM_KERNEL_KINDS)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("group", U32), ("refine_rounds", U32), ("ms", ctypes.c_double), ("from_cache", U32),
+                ("configs_tried", U32)]
+
+
 class ServeOpts(ctypes.Structure):
     _fields_ = [("budget_bytes", U64), ("slots", U32), ("max_batch", U32), ("queue_depth", U32), ("reserved", U32)]
 
@@ -103,6 +108,9 @@ EXTRA_SIGNATURES = {
                                          ctypes.POINTER(U64)]),
     "gs_graph_io_bytes": (ctypes.c_int, [P, ctypes.POINTER(U64), ctypes.POINTER(U64)]),
     "gs_filter_candidates_static": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, P, U64, P, P]),
+    "gs_tune": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts), ctypes.c_char_p,
+                               ctypes.POINTER(Tuning)]),
+    "gs_tune_set": (ctypes.c_int, [P, U32, U32]),
 }
 
 _lib = None
@@ -344,6 +352,18 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def tune(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, cache_path: str | None = None) -> dict:
+    """Pick lanes per work item and refinement rounds for this graph and
+    query load (gs_tune); later batches on the graph use them."""
+    pack = _QueryPack(queries)
+    o = _opts(cap, mode)
+    t = Tuning()
+    _check(lib().gs_tune(dg._h, pack.arr, len(queries), ctypes.byref(o),
+                         cache_path.encode() if cache_path else None, ctypes.byref(t)))
+    return {"group": t.group, "refine_rounds": t.refine_rounds, "ms": t.ms, "from_cache": bool(t.from_cache),
+            "configs_tried": t.configs_tried}
 
 
 def inspect_candidates(dg: DeviceGraph, q, stage=GS_STAGE_FIXPOINT) -> list[np.ndarray]:

@@ -14,6 +14,8 @@
 
 using namespace gs;
 
+static void drop_graphs(gs_batch *b);
+
 namespace gs {
 
 // ------------------------------------------------------------ query packing
@@ -113,16 +115,37 @@ struct Sizing {
 static Sizing size_pools(const gs_batch *b, const gs_match_opts *o) {
   const uint64_t V = b->g->d.V;
   Sizing s;
-  // Candidate lists and edge tables: room for about 8K candidates per query
-  // vertex on average (the sets after exploration are far smaller than V on
-  // these graphs); a query that needs more finishes on the fallback path,
-  // which has pools of its own.
+  // Candidate lists and edge tables sized from upper bounds of the initial
+  // candidate sets (a bound vertex: 1; a typed one: the vertices of its type;
+  // an untyped one: V), per wave, capped; a query that needs more than the
+  // caps finishes on the fallback path, which has pools of its own.
   auto clampu = [](uint64_t x, uint64_t lo, uint64_t hi) { return std::min(std::max(x, lo), hi); };
-  s.tlist = std::min<uint64_t>((uint64_t)b->nq_s * V, clampu((uint64_t)b->nq_s << 14, 1ull << 22, 1ull << 28));
-  s.alist = std::min<uint64_t>((uint64_t)b->nqv_s * V, clampu((uint64_t)b->nqv_s << 13, 1ull << 22, 1ull << 28));
+  auto est = [&](const DQuery &d, uint32_t u) -> uint64_t {
+    if (d.vbind[u] != kUnbound) return 1;
+    if (d.vtype[u] != kAny && d.vtype[u] < b->g->d.T) return b->g->type_count[d.vtype[u]];
+    return V;
+  };
+  uint64_t w_t = 0, w_a = 0, w_e = 0;
+  for (const auto &w : b->waves) {
+    uint64_t t = 0, a = 0, e = 0;
+    for (uint32_t i = w.q0; i < w.q0 + w.nq && i < b->n; ++i) {
+      const DQuery &d = b->hq[i];
+      uint64_t mx = 0;
+      for (uint32_t u = 0; u < d.k; ++u) { a += est(d, u); mx = std::max(mx, est(d, u)); }
+      t += mx;
+      for (uint32_t j = 0; j < d.m; ++j) e += std::max(est(d, d.esrc[j]), est(d, d.edst[j]));
+    }
+    w_t = std::max(w_t, t); w_a = std::max(w_a, a); w_e = std::max(w_e, e);
+  }
+  s.tlist = clampu(w_t, 1ull << 20, 1ull << 28);
+  s.alist = clampu(w_a, 1ull << 20, 1ull << 28);
   s.flist = s.alist;
-  s.ec_items = std::min<uint64_t>((uint64_t)b->nqe_s * V, clampu((uint64_t)b->nqe_s << 13, 1ull << 22, 1ull << 28));
-  s.ec_vals = clampu((uint64_t)b->nqe_s << 14, 1ull << 22, 1ull << 29);
+  s.ec_items = clampu(w_e, 1ull << 20, 1ull << 28);
+  s.ec_vals = clampu(4 * w_e, 1ull << 20, 1ull << 29);
+  if (b->pool_hint) {  // capacity-created batches (serving slots): fixed pools
+    s.tlist = s.alist = s.flist = s.ec_items = b->pool_hint;
+    s.ec_vals = 4 * b->pool_hint;
+  }
   uint64_t chunk = (o && o->chunk_bytes) ? o->chunk_bytes : (1ull << 30);
   s.lvl_words = std::max<uint64_t>(std::min<uint64_t>(chunk / 4 / 2, std::max<uint64_t>((uint64_t)b->nq_s << 16, 1ull << 22)), 1ull << 16);
   uint64_t want_rows = 0, want_words = 0;
@@ -324,7 +347,7 @@ void enqueue_front(Pipe &P, int K) {
     P.begin(KK_COMPACT);
     launch_compact_count(W, 0, step, P.cur, sms);
     scan_u32(W.ccount, W.cscan, &W.ctrl->len[0], (uint64_t)W.nq * ipg, b->scan_tmp, P.cur, sms);
-    launch_compact_write(W, 0, step, W.cscan, W.tlist, W.tlist_cap, P.cur, sms);
+    launch_compact_write(W, 0, step, W.cscan, W.tlist, W.tlist_cap, HW_TLIST, P.cur, sms);
     P.end();
     P.begin(KK_EXPLORE);
     launch_explore(W, step, grp, P.cur, sms);
@@ -333,7 +356,7 @@ void enqueue_front(Pipe &P, int K) {
   P.begin(KK_COMPACT);
   launch_compact_count(W, 1, 0, P.cur, sms);
   scan_u32(W.ccount, W.ascan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, P.cur, sms);
-  launch_compact_write(W, 1, 0, W.ascan, W.alist, W.alist_cap, P.cur, sms);
+  launch_compact_write(W, 1, 0, W.ascan, W.alist, W.alist_cap, HW_ALIST, P.cur, sms);
   P.end();
   P.begin(KK_REFINE);
   for (uint32_t r = 0; r < b->refine_rounds; ++r) launch_refine(W, r, grp, P.cur, sms);
@@ -350,7 +373,7 @@ void enqueue_back(Pipe &P, int K, int stop) {
   P.begin(KK_COMPACT);
   launch_compact_count(W, 1, 0, P.cur, sms);
   scan_u32(W.ccount, W.cscan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, P.cur, sms);
-  launch_compact_write(W, 1, 0, W.cscan, W.flist, W.flist_cap, P.cur, sms);
+  launch_compact_write(W, 1, 0, W.cscan, W.flist, W.flist_cap, HW_FLIST, P.cur, sms);
   launch_list_table(W, P.cur, sms);
   P.end();
   if (stop == 1) return;
@@ -394,27 +417,20 @@ void enqueue_back(Pipe &P, int K, int stop) {
   P.end();
 }
 
-// Radix sort of the outputs above the one-block limit (graph B).
-void enqueue_large_sort(Pipe &P, int K) {
+// Merge sort of the outputs above the one-block limit: tiles sorted in
+// shared memory, then ceil(log2(largest / tile)) merge passes (launched
+// directly: the host reads the largest output first).
+void enqueue_large_sort(Pipe &P, uint64_t max_rows) {
   gs_batch *b = P.b;
   Wave &W = b->W;
   const int sms = b->sms;
   P.begin(KK_SORT);
   uint32_t *perm[2] = {W.sval[0], W.sval[1]};
   int cur = 0;
-  launch_iota(W, perm[cur], P.cur, sms);
-  const int nb = bits_for(W.G.V ? W.G.V - 1 : 0);
-  for (int col = K - 1; col >= 0; --col) {
-    launch_sort_keys(W, perm[cur], W.skey[0], (uint32_t)col, P.cur, sms);
-    int r = radix_sort_pairs(W.skey[0], perm[cur], W.skey[1], perm[cur ^ 1], &W.ctrl->len[6], W.out_rows_cap, 0, nb,
-                             b->scan_tmp, P.cur, sms);
-    cur = r ? cur ^ 1 : cur;
-  }
-  if (W.nq > 1) {
-    launch_sort_keys(W, perm[cur], W.skey[0], kMaxK, P.cur, sms);
-    int r = radix_sort_pairs(W.skey[0], perm[cur], W.skey[1], perm[cur ^ 1], &W.ctrl->len[6], W.out_rows_cap, 0,
-                             bits_for(W.nq - 1), b->scan_tmp, P.cur, sms);
-    cur = r ? cur ^ 1 : cur;
+  launch_tile_sort(W, perm[cur], P.cur, sms);
+  for (uint64_t run = kTileRows; run < max_rows; run *= 2) {
+    launch_merge_pass(W, perm[cur], perm[cur ^ 1], run, P.cur, sms);
+    cur ^= 1;
   }
   P.end();
   P.begin(KK_GATHER);
@@ -467,26 +483,18 @@ static gs_status capture_one(gs_batch *b, F body, cudaGraphExec_t *exec, std::ve
 
 static gs_status capture_k(gs_batch *b, int K) {
   if (b->execs.count(K)) return GS_OK;
-  cudaGraphExec_t a = nullptr, s = nullptr;
-  std::vector<gs_batch::Ev> ea, es;
-  uint64_t ka = 0, ks = 0;
+  cudaGraphExec_t a = nullptr;
+  std::vector<gs_batch::Ev> ea;
+  uint64_t ka = 0;
   gs_status st = capture_one(b, [&](Pipe &P) { enqueue_front(P, K); enqueue_back(P, K, 0); }, &a, &ea, &ka);
   if (st != GS_OK) return st;
-  st = capture_one(b, [&](Pipe &P) { enqueue_large_sort(P, K); }, &s, &es, &ks);
-  if (st != GS_OK) {
-    cudaGraphExecDestroy(a);
-    return st;
-  }
   if (!b->epi_exec) {
     st = capture_one(b, [&](Pipe &P) { enqueue_epilogue(P); }, &b->epi_exec, &b->epi_evs, &b->epi_kernels);
     if (st != GS_OK) return st;
   }
   b->execs[K] = a;
-  b->sort_execs[K] = s;
   b->graph_evs[K] = ea;
-  b->sort_evs[K] = es;
   b->kernels_per_exec[K] = ka;
-  b->sort_kernels[K] = ks;
   return GS_OK;
 }
 
@@ -520,9 +528,10 @@ gs_status refine_to_fixpoint(gs_batch *b) {
 }
 
 gs_status run_waves(gs_batch *b) {
+  GS_CUDA(cudaMemsetAsync(b->W.ctrl->hw, 0, sizeof(b->W.ctrl->hw), b->stream));
   GS_CUDA(cudaMemsetAsync(&b->W.ctrl->wave, 0, sizeof(uint32_t), b->stream));
   GS_CUDA(cudaMemsetAsync(&b->W.ctrl->store_top, 0, sizeof(uint64_t), b->stream));
-  if (!b->flag) GS_CUDA(cudaMallocHost((void **)&b->flag, sizeof(uint64_t)));
+  if (!b->flag) GS_CUDA(cudaMallocHost((void **)&b->flag, 2 * sizeof(uint64_t)));
   const bool sorting = rows_wanted(b);
   for (size_t w = 0; w < b->waves.size(); ++w) {
     const int K = b->wave_k[w];
@@ -542,16 +551,16 @@ gs_status run_waves(gs_batch *b) {
     bool large = false;
     if (sorting) {  // any output too large for the one-block sort?
       GS_CUDA(cudaMemcpyAsync(b->flag, &b->W.ctrl->len[6], sizeof(uint64_t), cudaMemcpyDeviceToHost, b->stream));
+      GS_CUDA(cudaMemcpyAsync(b->flag + 1, &b->W.ctrl->max_large_rows, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                              b->stream));
       GS_CUDA(cudaStreamSynchronize(b->stream));
-      large = *b->flag != 0;
+      large = b->flag[0] != 0;
       if (large) {
-        if (b->use_graph) {
-          GS_CUDA(cudaGraphLaunch(b->sort_execs[K], b->stream));
-          b->kernel_launches += b->sort_kernels[K];
-        } else {
-          Pipe P{b, &b->evs, false, b->stream};
-          enqueue_large_sort(P, K);
-        }
+        Pipe P{b, &b->sort_evs_direct, false, b->stream};
+        enqueue_large_sort(P, b->flag[1]);
+        uint64_t passes = 0;
+        for (uint64_t run = kTileRows; run < b->flag[1]; run *= 2) ++passes;
+        b->kernel_launches += 2 + passes;
         b->large_sorts++;
       }
     }
@@ -566,7 +575,7 @@ gs_status run_waves(gs_batch *b) {
       GS_CUDA(cudaStreamSynchronize(b->stream));
       if (b->use_graph) {
         harvest_events(b, b->graph_evs[K], false);
-        if (large) harvest_events(b, b->sort_evs[K], false);
+        harvest_events(b, b->sort_evs_direct, true);
         harvest_events(b, b->epi_evs, false);
       } else {
         harvest_events(b, b->evs, true);
@@ -615,6 +624,8 @@ gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_mat
   pack_all(b, qs, n, opts);
   b->n_cap = std::max<uint32_t>(n, 1);
   opts_key(b, opts);
+  if (g->tuned_group) b->group = g->tuned_group;
+  if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds;
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
     b->fixpoint = false;
@@ -675,6 +686,8 @@ gs_status batch_create_capacity(gs_graph *g, const gs_match_opts *opts, uint32_t
   b->sms = g->num_sms;
   b->n_cap = std::max<uint32_t>(n_cap, 1);
   opts_key(b, opts);
+  if (g->tuned_group) b->group = g->tuned_group;
+  if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds;
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
     b->fixpoint = false;
@@ -697,6 +710,7 @@ gs_status batch_create_capacity(gs_graph *g, const gs_match_opts *opts, uint32_t
     b->hq[i].cap = opts ? std::min<uint64_t>(opts->cap, 1u << 12) : 0;
   }
   b->n = b->n_cap;
+  b->pool_hint = 1ull << 25;
   b->waves.assign(1, WaveDesc{0, b->n_cap, 0, b->nqv_s, 0, b->nqe_s});
   b->wave_k.assign(1, kMaxK);
   gs_status st = batch_alloc(b, opts);
@@ -728,16 +742,91 @@ void batch_destroy(gs_batch *b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (auto &kv : b->execs) cudaGraphExecDestroy(kv.second);
-  for (auto &kv : b->sort_execs) cudaGraphExecDestroy(kv.second);
   if (b->epi_exec) cudaGraphExecDestroy(b->epi_exec);
-  for (auto &kv : b->sort_evs) harvest_events(b, kv.second, true);
   harvest_events(b, b->epi_evs, true);
+  harvest_events(b, b->sort_evs_direct, true);
   if (b->flag) cudaFreeHost(b->flag);
   for (auto &kv : b->graph_evs) harvest_events(b, kv.second, true);
   harvest_events(b, b->evs, true);
   for (void *p : b->allocs) cudaFree(p);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
+}
+
+// Replace one device pool by a larger one (contents are not kept).
+template <typename T>
+static gs_status regrow(gs_batch *b, T **p, uint64_t count) {
+  void *old = *p;
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ERR_OOM;  // keep the old pool; overflowing queries keep taking the fallback path
+  }
+  cudaFree(old);
+  for (auto &a : b->allocs)
+    if (a == old) a = q;
+  *p = static_cast<T *>(q);
+  return GS_OK;
+}
+
+// After a run: enlarge every pool the run asked more of than it had, so the
+// next run of a similar load stays on the device (this run's overflowing
+// queries are finished on the fallback path as usual).  Graphs are captured
+// again because pool pointers are kernel parameters.
+gs_status grow_pools(gs_batch *b) {
+  if (b->big) return GS_OK;
+  uint64_t hw[HW_N];
+  GS_CUDA(cudaMemcpy(hw, b->W.ctrl->hw, sizeof(hw), cudaMemcpyDeviceToHost));
+  Wave &W = b->W;
+  auto want = [](uint64_t need) { return need + need / 4 + 1024; };
+  const uint64_t kMaxEntries = 1ull << 31;
+  bool changed = false;
+  auto grow32 = [&](uint32_t **p, uint64_t *cap, uint64_t need) {
+    if (need <= *cap || need > kMaxEntries) return;
+    const uint64_t n = want(need);
+    if (regrow(b, p, n) == GS_OK) { *cap = n; changed = true; }
+  };
+  grow32(&W.tlist, &W.tlist_cap, hw[HW_TLIST]);
+  grow32(&W.alist, &W.alist_cap, hw[HW_ALIST]);
+  grow32(&W.flist, &W.flist_cap, hw[HW_FLIST]);
+  grow32(&W.ec_vals, &W.ec_vals_cap, hw[HW_EC_VALS]);
+  if (hw[HW_EC_ITEMS] > W.ec_items_cap && hw[HW_EC_ITEMS] <= kMaxEntries) {
+    const uint64_t n = want(hw[HW_EC_ITEMS]);
+    if (regrow(b, &W.ec_cnt, n) == GS_OK && regrow(b, &W.ec_off, n + 1) == GS_OK) { W.ec_items_cap = n; changed = true; }
+  }
+  const uint64_t need_words = std::max(hw[HW_LVL_WORDS], W.lvl_words), need_rows = std::max(hw[HW_ROWS], W.row_cap);
+  if ((need_words > W.lvl_words || need_rows > W.row_cap) && need_words <= kMaxEntries && need_rows <= kMaxEntries) {
+    const uint64_t nw = std::max(want(need_words), want(need_rows));  // rows of width 1 can fill a buffer
+    if (regrow(b, &W.lvl[0], nw) == GS_OK && regrow(b, &W.lvl[1], nw) == GS_OK && regrow(b, &W.row_cnt, nw) == GS_OK &&
+        regrow(b, &W.row_scan, nw + 1) == GS_OK) {
+      W.lvl_words = W.row_cap = nw;
+      changed = true;
+    }
+  }
+  if (hw[HW_OUT_ROWS] > W.out_rows_cap && hw[HW_OUT_ROWS] <= kMaxEntries) {
+    const uint64_t n = want(hw[HW_OUT_ROWS]);
+    bool ok = regrow(b, &W.out_q, n) == GS_OK;
+    for (int i = 0; i < 2 && ok; ++i) ok = regrow(b, &W.skey[i], n) == GS_OK && regrow(b, &W.sval[i], n) == GS_OK;
+    if (ok) { W.out_rows_cap = n; changed = true; }
+  }
+  if (hw[HW_OUT_WORDS] > W.out_words && hw[HW_OUT_WORDS] <= kMaxEntries) {
+    const uint64_t n = want(hw[HW_OUT_WORDS]);
+    if (regrow(b, &W.out, n) == GS_OK && regrow(b, &W.out_final, n) == GS_OK) { W.out_words = n; changed = true; }
+  }
+  if (hw[HW_STORE] > W.bo.store_cap && hw[HW_STORE] <= kMaxEntries) {
+    const uint64_t n = want(hw[HW_STORE]);
+    if (regrow(b, &W.bo.store, n) == GS_OK) { W.bo.store_cap = n; changed = true; }
+  }
+  if (changed) {
+    const uint64_t ipg = W.G.ipg;
+    uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * ipg, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap}));
+    tmpw = std::max(tmpw, radix_tmp_words(W.out_rows_cap));
+    regrow(b, &b->scan_tmp, tmpw);
+    ::drop_graphs(b);
+    b->regrows++;
+  }
+  return GS_OK;
 }
 
 gs_status batch_finish(gs_batch *b) {
@@ -761,6 +850,8 @@ gs_status batch_finish(gs_batch *b) {
     GS_CUDA(cudaMemcpyAsync(b->rows.data(), b->W.bo.store, 4ull * top, cudaMemcpyDeviceToHost, b->stream));
     GS_CUDA(cudaStreamSynchronize(b->stream));
   }
+  gs_status gst = grow_pools(b);
+  if (gst != GS_OK) return gst;
   b->fb_rows.assign(n, {});
   b->fb_done.assign(n, 0);
   b->fallbacks = 0;
@@ -857,16 +948,12 @@ extern "C" void gs_batch_destroy(gs_batch *b) { batch_destroy(b); }
 // Forget captured graphs (their launch parameters changed).
 static void drop_graphs(gs_batch *b) {
   for (auto &kv : b->execs) cudaGraphExecDestroy(kv.second);
-  for (auto &kv : b->sort_execs) cudaGraphExecDestroy(kv.second);
   if (b->epi_exec) cudaGraphExecDestroy(b->epi_exec);
   b->execs.clear();
-  b->sort_execs.clear();
   b->epi_exec = nullptr;
   for (auto &kv : b->graph_evs) harvest_events(b, kv.second, true);
-  for (auto &kv : b->sort_evs) harvest_events(b, kv.second, true);
   harvest_events(b, b->epi_evs, true);
   b->graph_evs.clear();
-  b->sort_evs.clear();
 }
 
 extern "C" gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_t refine_rounds) {

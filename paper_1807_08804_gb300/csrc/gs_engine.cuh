@@ -15,6 +15,7 @@ constexpr uint32_t kAny = 0xFFFFFFFFu;
 constexpr uint32_t kMaxRounds = 64;
 constexpr uint32_t kSmallRows = 2048;    // outputs sorted by one block in shared memory
 constexpr uint32_t kSmallWords = 24576;
+constexpr uint32_t kTileRows = 1024;     // rows per tile of the large-output merge sort
 
 // Per-query status.
 enum : uint32_t {
@@ -23,6 +24,13 @@ enum : uint32_t {
   QS_OVERFLOW = 2,  // a device pool was too small: finish on the fallback path
   QS_INVALID = 3,   // empty slot (padding) or rejected by the host checks
   QS_TOPCAP = 4,    // more embeddings than cap: smallest rows via the fallback path
+};
+
+// Pools whose requested sizes the device records (Ctrl::hw), so that the
+// host can enlarge a pool that was too small for the next run.
+enum : int {
+  HW_TLIST = 0, HW_ALIST, HW_FLIST, HW_EC_ITEMS, HW_EC_VALS, HW_LVL_WORDS, HW_ROWS, HW_OUT_ROWS, HW_OUT_WORDS,
+  HW_STORE, HW_N
 };
 
 // Kernel kinds for statistics.
@@ -68,7 +76,8 @@ struct QState {
   uint64_t nxt_rows;                                 // rows produced for the next level
   uint64_t out_row_base, out_rows, out_word_base;   // final rows in the output pool
   uint64_t fin_row_base, fin_word_base;             // sorted rows in query order
-  uint64_t lrg_row_base;                             // rows sorted by the radix path
+  uint64_t lrg_row_base;                             // rows sorted by the merge path
+  uint64_t lrg_tile_base;                            // their first tile
 };
 
 // Rows of level s kept aside while the allocator lays out level s+1.
@@ -102,6 +111,8 @@ struct Ctrl {
   uint32_t max_nvisit;              // longest visit order in the wave
   uint32_t refine_iters;            // rounds run by the refinement loop
   uint64_t fb_src[3];               // source rows staged by the chunked join
+  uint64_t hw[10];                  // sizes the run asked of each pool (see HW_*)
+  uint64_t max_large_rows;          // largest output above the one-block sort limit
   uint64_t bytes[KK_N];             // algorithmic bytes per kernel kind
 };
 
@@ -159,7 +170,7 @@ void launch_plan(const Wave &W, const uint32_t *type_count, cudaStream_t s, int 
 void launch_filter(const Wave &W, cudaStream_t s, int sms);
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms);
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint64_t cap,
-                          cudaStream_t s, int sms);
+                          int hw_slot, cudaStream_t s, int sms);
 void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms);
 void launch_refine(const Wave &W, uint32_t round, int group, cudaStream_t s, int sms);
 void launch_list_table(const Wave &W, cudaStream_t s, int sms);
@@ -174,8 +185,8 @@ void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s);
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms);
 void launch_final_bases(const Wave &W, cudaStream_t s);
 void launch_small_sort(const Wave &W, cudaStream_t s, int sms);
-void launch_iota(const Wave &W, uint32_t *perm, cudaStream_t s, int sms);
-void launch_sort_keys(const Wave &W, const uint32_t *perm, uint32_t *key, uint32_t col, cudaStream_t s, int sms);
+void launch_tile_sort(const Wave &W, uint32_t *perm, cudaStream_t s, int sms);
+void launch_merge_pass(const Wave &W, const uint32_t *in, uint32_t *out, uint64_t run, cudaStream_t s, int sms);
 void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms);
 void launch_epilogue(const Wave &W, cudaStream_t s, int sms);
 

@@ -100,16 +100,16 @@ struct gs_batch {
   uint64_t h2d_bytes = 0, d2h_bytes = 0;
   uint64_t last_upload_bytes = 0;
   bool big = false;                // fallback context sizing
-  // the large-output sort and the epilogue as separate graphs
-  std::map<int, cudaGraphExec_t> sort_execs;
-  std::map<int, std::vector<Ev>> sort_evs;
-  std::map<int, uint64_t> sort_kernels;
+  uint64_t pool_hint = 0;          // fixed candidate-pool entries (serving slots)
+  // the epilogue as a separate graph; the large-output sort launched directly
+  std::vector<Ev> sort_evs_direct;
   cudaGraphExec_t epi_exec = nullptr;
   std::vector<Ev> epi_evs;
   uint64_t epi_kernels = 0;
-  uint64_t *flag = nullptr;        // pinned word read between graphs
+  uint64_t *flag = nullptr;        // pinned words read between graphs
   uint64_t large_sorts = 0;
   uint64_t fallbacks = 0;          // queries finished on the chunked path by the last finish
+  uint64_t regrows = 0;            // times pools were enlarged after a run
 };
 
 namespace gs {

@@ -59,6 +59,8 @@ struct gs_graph {
   uint64_t hash;            // content hash (tuning cache key)
   void *cache;              // batches reused by gs_match / gs_match_batch
   void *fallback;           // context of the chunked join
+  uint32_t tuned_group;     // lanes per work item chosen by gs_tune (0 = default)
+  uint32_t tuned_rounds;    // refinement rounds chosen by gs_tune (0 = default)
 };
 
 namespace gs {

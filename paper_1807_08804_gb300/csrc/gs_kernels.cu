@@ -109,8 +109,13 @@ __device__ __forceinline__ uint32_t seg_of_rows(const QState *qs, uint32_t nq, u
   return lo;
 }
 
-__device__ __forceinline__ void add_bytes(const Wave &W, int kind, uint64_t b) {
-  if (W.stats && b) atomicAdd((unsigned long long *)&W.ctrl->bytes[kind], (unsigned long long)b);
+// Algorithmic bytes: each thread accumulates in a register; at the end of
+// the kernel one warp-reduced atomic per warp adds them up (statistics runs
+// only).  Every lane of the warp must reach flush_bytes.
+__device__ __forceinline__ void flush_bytes(const Wave &W, int kind, uint64_t b) {
+  if (!W.stats) return;
+  for (int o = 16; o; o >>= 1) b += __shfl_down_sync(kFull, b, o);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd((unsigned long long *)&W.ctrl->bytes[kind], (unsigned long long)b);
 }
 
 __device__ __forceinline__ void mark(DQuery &Q, uint32_t st) { atomicCAS(&Q.status, QS_OK, st); }
@@ -220,6 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
   const uint64_t items = (uint64_t)W.nq * G.W1;
+  uint64_t acc = 0;
   for (uint64_t it = gtid() / 32; it < items; it += warps) {
     const uint32_t qi = (uint32_t)(it / G.W1), w1 = (uint32_t)(it % G.W1);
     const DQuery &Q = W.dq[qi];
@@ -237,19 +243,32 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
       const uint32_t t = Q.vtype[u];
       uint32_t ok = 0xFFFFFFFFu;
       if (t != kAny) {
+        // four type bytes per word compared at once; the 0xFF/0x00 byte
+        // flags are then gathered into four bits by one multiply
         const uint4 *p = reinterpret_cast<const uint4 *>(G.vtype + v0);
         uint4 a = p[0], b = p[1];
         uint32_t wd[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        const uint32_t tt = t * 0x01010101u;
         ok = 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) ok |= (((wd[j >> 2] >> ((j & 3) * 8)) & 0xFFu) == t ? 1u : 0u) << j;
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t y = (__vcmpeq4(wd[q], tt) >> 7) & 0x01010101u;
+          ok |= ((y * 0x01020408u) >> 24) << (4 * q);
+        }
       }
       for (uint32_t i = Q.need_begin[u]; i < Q.need_begin[u + 1] && ok; ++i) {
+        // eight 4-bit counts per word: even and odd nibbles compared as
+        // bytes, then interleaved back into vertex order
         const uint4 s = *reinterpret_cast<const uint4 *>(G.sig + (uint64_t)Q.need_plane[i] * G.sig_words + (uint64_t)w0 * 4);
         uint32_t sw[4] = {s.x, s.y, s.z, s.w};
-        uint32_t c = Q.need_cnt[i], m = 0;
+        const uint32_t cc = Q.need_cnt[i] * 0x01010101u;
+        uint32_t m = 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) m |= (((sw[j >> 3] >> ((j & 7) * 4)) & 15u) >= c ? 1u : 0u) << j;
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t z = __vsetgeu4(sw[q] & 0x0F0F0F0Fu, cc) | (__vsetgeu4((sw[q] >> 4) & 0x0F0F0F0Fu, cc) << 1);
+          const uint32_t r = (z & 3u) | ((z >> 6) & 0xCu) | ((z >> 12) & 0x30u) | ((z >> 18) & 0xC0u);
+          m |= r << (8 * q);
+        }
         ok &= m;
       }
       if (v0 + 32 > G.V) ok &= (G.V - v0 >= 32) ? 0xFFFFFFFFu : ((1u << (G.V - v0)) - 1);
@@ -258,11 +277,10 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
     }
     uint32_t nz = __ballot_sync(kFull, word != 0);
     if (lane == 0) slot[G.W0 + w1] = nz;
-    if (lane == 0 && W.stats) {
-      uint64_t nb = 32ull * 32 * (Q.vtype[u] != kAny ? 1 : 0) + 32ull * 16 * (Q.need_begin[u + 1] - Q.need_begin[u]) + 32 * 4 + 4;
-      add_bytes(W, KK_FILTER, nb);
-    }
+    if (lane == 0)
+      acc += 32ull * 32 * (Q.vtype[u] != kAny ? 1 : 0) + 32ull * 16 * (Q.need_begin[u + 1] - Q.need_begin[u]) + 32 * 4 + 4;
   }
+  flush_bytes(W, KK_FILTER, acc);
 }
 
 // ============================================================ compaction
@@ -324,12 +342,13 @@ __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W, int mode, ui
 // Writes ids in ascending order at dst[cscan[item] ...]; marks a query that
 // does not fit dst_cap as overflowed.
 __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, uint32_t step, const uint64_t *scan,
-                                                             uint32_t *dst, uint64_t dst_cap) {
+                                                             uint32_t *dst, uint64_t dst_cap, int hw_slot) {
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
   const uint32_t nsel = mode == 0 ? W.nq : W.nqv;
   const uint64_t items = (uint64_t)nsel * G.ipg;
+  if (gtid() == 0) atomicMax((unsigned long long *)&W.ctrl->hw[hw_slot], (unsigned long long)scan[items]);
   for (uint64_t it = gtid() / 32; it < items; it += warps) {
     const uint32_t s = (uint32_t)(it / G.ipg), c = (uint32_t)(it % G.ipg);
     uint32_t gqv = 0;
@@ -373,7 +392,13 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, ui
 // query neighbour w of u has no candidate among v's data neighbours over the
 // edge's relation and direction (a neighbour whose set is not built yet is
 // tested with the candidate test); otherwise v's neighbours that pass the
-// candidate test are added to the sets of u's spanning-tree children.
+// candidate test join the sets of u's spanning-tree children.
+// The edges to children are scanned once: the candidate test of each
+// neighbour both feeds the existence check and sets the child's bit.  They
+// are scanned after the other edges, so most dropped candidates expand
+// nothing; a candidate dropped by a later child edge may leave extra bits in
+// an earlier child's set, which keeps the sets supersets of the exact ones
+// (refinement removes them).
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
@@ -381,6 +406,7 @@ __global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
   const uint32_t r = tile.thread_rank();
   const uint64_t ntile = gthreads() / G;
   const uint64_t items = W.cscan[(uint64_t)W.nq * Gr.ipg];
+  uint64_t acc = 0;
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
     const uint32_t qi = seg_of(W.cscan, Gr.ipg, W.nq, it);
     DQuery &Q = W.dq[qi];
@@ -389,10 +415,12 @@ __global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
     const uint32_t v = W.tlist[it];
     uint64_t bytes = 0;
     bool keep = true;
+    // edges to vertices other than the children initialised by this step
     for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1] && keep; ++i) {
       const uint32_t e = Q.inc_edge[i];
       const int dir = Q.esrc[e] == u ? 0 : 1;
       const uint32_t w = dir == 0 ? Q.edst[e] : Q.esrc[e];
+      if (Q.parent[w] == u && Q.init_step[w] == step + 1 && Q.pedge[w] == e) continue;
       uint64_t lo, hi;
       rel_range<G>(tile, Gr, dir, v, Q.erel[e], lo, hi);
       const bool built = Q.init_step[w] <= step;
@@ -410,25 +438,33 @@ __global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
       bytes += 16 + 4 * (hi - lo);
       if (!found) keep = false;
     }
-    if (!keep) {
-      if (r == 0) bit_clear(slot_of(W, Q.qv_base + u), v);
-    } else {
-      for (uint32_t w = 0; w < Q.k; ++w) {
-        if (Q.parent[w] != u || Q.init_step[w] != step + 1) continue;
-        const uint32_t e = Q.pedge[w];
-        const int dir = Q.esrc[e] == u ? 0 : 1;
-        uint64_t lo, hi;
-        rel_range<G>(tile, Gr, dir, v, Q.erel[e], lo, hi);
-        uint32_t *ws = slot_of(W, Q.qv_base + w);
-        for (uint64_t j = lo + r; j < hi; j += G) {
+    // tree edges to the children: test, expand and check existence in one scan
+    for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1] && keep; ++i) {
+      const uint32_t e = Q.inc_edge[i];
+      const int dir = Q.esrc[e] == u ? 0 : 1;
+      const uint32_t w = dir == 0 ? Q.edst[e] : Q.esrc[e];
+      if (!(Q.parent[w] == u && Q.init_step[w] == step + 1 && Q.pedge[w] == e)) continue;
+      uint64_t lo, hi;
+      rel_range<G>(tile, Gr, dir, v, Q.erel[e], lo, hi);
+      uint32_t *ws = slot_of(W, Q.qv_base + w);
+      bool found = false;
+      for (uint64_t b = lo; b < hi; b += G) {
+        uint64_t j = b + r;
+        bool ok = false;
+        if (j < hi) {
           uint32_t x = Gr.adj[dir][j] & kNbrMask;
-          if (cand_ok(Gr, Q, w, x)) bit_set(W, ws, x);
+          ok = cand_ok(Gr, Q, w, x);
+          if (ok) bit_set(W, ws, x);
         }
-        bytes += 16 + 4 * (hi - lo);
+        found = found || tile.any(ok);
       }
+      bytes += 16 + 4 * (hi - lo);
+      if (!found) keep = false;
     }
-    if (r == 0) add_bytes(W, KK_EXPLORE, bytes + 4);
+    if (!keep && r == 0) bit_clear(slot_of(W, Q.qv_base + u), v);
+    if (r == 0) acc += bytes + 4;
   }
+  flush_bytes(W, KK_EXPLORE, acc);
 }
 
 // ============================================================ refine
@@ -445,6 +481,7 @@ __global__ void __launch_bounds__(kThreads) k_refine(Wave W, uint32_t round) {
   const uint64_t ntile = gthreads() / G;
   const uint64_t items = W.ascan[(uint64_t)W.nqv * Gr.ipg];
   bool changed = false;
+  uint64_t acc = 0;
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
     const uint32_t gqv = seg_of(W.ascan, Gr.ipg, W.nqv, it);
     DQuery &Q = W.dq[W.qv_q[gqv]];
@@ -473,9 +510,10 @@ __global__ void __launch_bounds__(kThreads) k_refine(Wave W, uint32_t round) {
         break;
       }
     }
-    if (r == 0) add_bytes(W, KK_REFINE, bytes + 4);
+    if (r == 0) acc += bytes + 4;
   }
   if (changed && tile.thread_rank() == 0) W.ctrl->changed[round] = 1;
+  flush_bytes(W, KK_REFINE, acc);
 }
 
 // Final candidate lists: offsets and lengths per query vertex; a query with
@@ -547,6 +585,8 @@ __global__ void __launch_bounds__(kThreads) k_ec(Wave W) {
   const uint32_t r = tile.thread_rank();
   const uint64_t ntile = gthreads() / G;
   const uint64_t items = W.ctrl->len[5];  // clamped to the table capacity by k_ec_limit
+  uint64_t acc = 0;
+  if (WRITE && gtid() == 0) atomicMax((unsigned long long *)&W.ctrl->hw[HW_EC_VALS], (unsigned long long)W.ec_off[items]);
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
     const uint32_t ge = seg_of(W.ec_key_base, 1, W.nqe, it);
     DQuery &Q = W.dq[W.qe_q[ge]];
@@ -570,7 +610,7 @@ __global__ void __launch_bounds__(kThreads) k_ec(Wave W) {
       }
       if (r == 0) {
         W.ec_cnt[it] = cnt;
-        add_bytes(W, KK_EC_COUNT, 16 + 4 * (hi - lo) + 4 * (uint64_t)((hi - lo + 31) / 32) + 4);
+        acc += 16 + 4 * (hi - lo) + 4 * (uint64_t)((hi - lo + 31) / 32) + 4;
       }
     } else {
       uint64_t p = W.ec_off[it];
@@ -586,9 +626,10 @@ __global__ void __launch_bounds__(kThreads) k_ec(Wave W) {
         if (ok) W.ec_vals[p + __popc(m & ((1u << r) - 1))] = xv;
         p += __popc(m);
       }
-      if (r == 0) add_bytes(W, KK_EC_WRITE, 16 + 4 * (hi - lo) + 4 * (W.ec_off[it + 1] - W.ec_off[it]) + 8);
+      if (r == 0) acc += 16 + 4 * (hi - lo) + 4 * (W.ec_off[it + 1] - W.ec_off[it]) + 8;
     }
   }
+  flush_bytes(W, WRITE ? KK_EC_WRITE : KK_EC_COUNT, acc);
 }
 
 // Restore every touched bitmap word to zero (only words flagged in the
@@ -621,7 +662,10 @@ __global__ void k_ec_limit(Wave W) {
   for (uint64_t ge = gtid(); ge < W.nqe; ge += gthreads())
     if (W.ec_key_base[ge + 1] > W.ec_items_cap && W.ec_key_base[ge + 1] > W.ec_key_base[ge])
       mark(W.dq[W.qe_q[ge]], QS_OVERFLOW);
-  if (gtid() == 0) W.ctrl->len[5] = total < W.ec_items_cap ? total : W.ec_items_cap;
+  if (gtid() == 0) {
+    W.ctrl->len[5] = total < W.ec_items_cap ? total : W.ec_items_cap;
+    atomicMax((unsigned long long *)&W.ctrl->hw[HW_EC_ITEMS], (unsigned long long)total);
+  }
 }
 
 // ============================================================ wave I/O
@@ -758,6 +802,12 @@ __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
         for (int a = 0; a < 4; ++a) carry[a] += sm[a][31];
       __syncthreads();
     }
+    if (pass == 0 && threadIdx.x == 0) {  // what this level asked for before any query was sent away
+      atomicMax((unsigned long long *)&W.ctrl->hw[HW_ROWS], (unsigned long long)carry[0]);
+      atomicMax((unsigned long long *)&W.ctrl->hw[HW_LVL_WORDS], (unsigned long long)carry[1]);
+      atomicMax((unsigned long long *)&W.ctrl->hw[HW_OUT_ROWS], (unsigned long long)carry[2]);
+      atomicMax((unsigned long long *)&W.ctrl->hw[HW_OUT_WORDS], (unsigned long long)carry[3]);
+    }
   }
   if (threadIdx.x == 0) {
     W.ctrl->len[3] = carry[0];
@@ -855,6 +905,7 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Wave W, uint32_t s) {
   const uint64_t ntile = gthreads() / G;
   const uint64_t items = W.ctrl->len[3];
   const uint32_t *lvl = W.lvl[s & 1];
+  uint64_t acc = 0;
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
     const uint32_t qi = seg_of_rows(W.qs, W.nq, it);
     const DQuery &Q = W.dq[qi];
@@ -888,9 +939,10 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Wave W, uint32_t s) {
         if (cnt) atomicAdd((unsigned long long *)&S.count, (unsigned long long)cnt);
         if (fp) atomicAdd((unsigned long long *)&S.fp, (unsigned long long)fp);
       }
-      add_bytes(W, KK_JOIN_COUNT, bytes);
+      acc += bytes;
     }
   }
+  flush_bytes(W, KK_JOIN_COUNT, acc);
 }
 
 // Rows produced per query (scan of the per-row counts), and the current
@@ -913,6 +965,7 @@ __global__ void __launch_bounds__(kThreads) k_join_write(Wave W, uint32_t s) {
   const uint64_t items = W.ctrl->len[4];
   const uint32_t *lvl = W.lvl[s & 1];
   uint32_t *nxt = W.lvl[(s + 1) & 1];
+  uint64_t acc = 0;
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
     const uint32_t qi = seg_of_src(W.src, W.nq, it);
     const DQuery &Q = W.dq[qi];
@@ -952,9 +1005,9 @@ __global__ void __launch_bounds__(kThreads) k_join_write(Wave W, uint32_t s) {
       p += __popc(m);
       written += __popc(m);
     }
-    if (r == 0)
-      add_bytes(W, KK_JOIN_WRITE, 4ull * written * width + 4ull * (s + 1) + 4ull * c.len[c.drive] + 24ull * c.nedge);
+    if (r == 0) acc += 4ull * written * width + 4ull * (s + 1) + 4ull * c.len[c.drive] + 24ull * c.nedge;
   }
+  flush_bytes(W, KK_JOIN_WRITE, acc);
 }
 
 // Query-order layout of the sorted rows, and of the rows of queries whose
@@ -964,20 +1017,23 @@ __device__ __forceinline__ bool small_output(const DQuery &Q, const QState &S) {
 }
 
 __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
-  __shared__ uint64_t sm[3][32];
-  __shared__ uint64_t carry[3];
+  __shared__ uint64_t sm[4][32];
+  __shared__ uint64_t carry[4];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+  if (threadIdx.x < 4) carry[threadIdx.x] = 0;
+  if (threadIdx.x == 0) W.ctrl->max_large_rows = 0;
   __syncthreads();
   for (uint32_t base = 0; base < W.nq; base += blockDim.x) {
     const uint32_t qi = base + threadIdx.x;
-    uint64_t v[3] = {0, 0, 0}, ex[3];
+    uint64_t v[4] = {0, 0, 0, 0}, ex[4];
     if (qi < W.nq && W.dq[qi].status == QS_OK) {
       v[0] = W.qs[qi].out_rows;
       v[1] = W.qs[qi].out_rows * W.dq[qi].k;
       v[2] = small_output(W.dq[qi], W.qs[qi]) ? 0 : W.qs[qi].out_rows;
+      v[3] = (v[2] + kTileRows - 1) / kTileRows;
+      if (v[2]) atomicMax((unsigned long long *)&W.ctrl->max_large_rows, (unsigned long long)v[2]);
     }
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 4; ++a) {
       uint64_t x = v[a];
       for (int o = 1; o < 32; o <<= 1) {
         uint64_t y = __shfl_up_sync(kFull, x, o);
@@ -987,7 +1043,7 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
       ex[a] = x - v[a];
     }
     __syncthreads();
-    if (warp < 3) {
+    if (warp < 4) {
       uint64_t x = sm[warp][lane];
       for (int o = 1; o < 32; o <<= 1) {
         uint64_t y = __shfl_up_sync(kFull, x, o);
@@ -1000,12 +1056,16 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
       W.qs[qi].fin_row_base = carry[0] + ex[0] + (warp ? sm[0][warp - 1] : 0);
       W.qs[qi].fin_word_base = carry[1] + ex[1] + (warp ? sm[1][warp - 1] : 0);
       W.qs[qi].lrg_row_base = carry[2] + ex[2] + (warp ? sm[2][warp - 1] : 0);
+      W.qs[qi].lrg_tile_base = carry[3] + ex[3] + (warp ? sm[3][warp - 1] : 0);
     }
     __syncthreads();
-    if (threadIdx.x < 3) carry[threadIdx.x] += sm[threadIdx.x][31];
+    if (threadIdx.x < 4) carry[threadIdx.x] += sm[threadIdx.x][31];
     __syncthreads();
   }
-  if (threadIdx.x == 0) W.ctrl->len[6] = carry[2];
+  if (threadIdx.x == 0) {
+    W.ctrl->len[6] = carry[2];
+    W.ctrl->len[7] = carry[3];
+  }
 }
 
 // One block sorts one query's rows in shared memory (bitonic network over
@@ -1057,28 +1117,92 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
 }
 
 // ============================================================ sort + gather
-// Rows of large outputs, in output-pool order, as the initial permutation.
-__global__ void k_iota(Wave W, uint32_t *perm) {
-  const uint64_t n = W.ctrl->out_rows_total;
-  for (uint64_t r = gtid(); r < n; r += gthreads()) {
-    const uint32_t qi = W.out_q[r];
+// Large outputs (more than the one-block limit) are sorted as a merge sort
+// of row indices: each block sorts one tile of kTileRows rows of one query in
+// shared memory (rows in query-vertex column order, bitonic network), then
+// merge passes double the sorted runs within each query's rows.
+__device__ __forceinline__ uint32_t seg_of_large(const QState *qs, uint32_t nq, uint64_t item, bool tiles) {
+  uint32_t lo = 0, hi = nq;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if ((tiles ? qs[mid].lrg_tile_base : qs[mid].lrg_row_base) <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_tile_sort(Wave W, uint32_t *perm) {
+  extern __shared__ uint32_t smem[];
+  uint32_t *rows = smem;                           // [kTileRows * kMaxK]
+  uint32_t *idx = smem + kTileRows * kMaxK;        // [kTileRows]
+  const uint64_t ntiles = W.ctrl->len[7];
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint32_t qi = seg_of_large(W.qs, W.nq, t, true);
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
-    if (!small_output(Q, S)) perm[S.lrg_row_base + (r - S.out_row_base)] = (uint32_t)r;
+    const uint64_t first = (t - S.lrg_tile_base) * kTileRows;
+    const uint32_t n = (uint32_t)min((uint64_t)kTileRows, S.out_rows - first), k = Q.k;
+    for (uint32_t x = threadIdx.x; x < n * k; x += blockDim.x) {
+      const uint32_t i = x / k, u = x % k;
+      rows[x] = W.out[S.out_word_base + (first + i) * k + Q.pos[u]];
+    }
+    uint32_t np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (uint32_t x = threadIdx.x; x < np2; x += blockDim.x) idx[x] = x;
+    __syncthreads();
+    for (uint32_t size = 2; size <= np2; size <<= 1)
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t x = threadIdx.x; x < np2; x += blockDim.x) {
+          const uint32_t p = x ^ stride;
+          if (p > x) {
+            const bool up = (x & size) == 0;
+            const uint32_t a = idx[x], b = idx[p];
+            if (up ? row_less(rows, k, n, b, a) : row_less(rows, k, n, a, b)) { idx[x] = b; idx[p] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+      perm[S.lrg_row_base + first + i] = (uint32_t)(S.out_row_base + first + idx[i]);
+    __syncthreads();
   }
 }
 
-// key[i] = id of query vertex `col` in output row perm[i] (0 past the row's
-// width), or the slot query when col == kMaxK (the most significant pass).
-__global__ void k_sort_keys(Wave W, const uint32_t *perm, uint32_t *key, uint32_t col) {
+// Row r of the output pool (query qi) compared in query-vertex order.
+__device__ __forceinline__ bool out_row_le(const Wave &W, const DQuery &Q, const QState &S, uint32_t a, uint32_t b) {
+  const uint32_t *x = W.out + S.out_word_base + (uint64_t)(a - S.out_row_base) * Q.k;
+  const uint32_t *y = W.out + S.out_word_base + (uint64_t)(b - S.out_row_base) * Q.k;
+  for (uint32_t u = 0; u < Q.k; ++u) {
+    const uint32_t xa = x[Q.pos[u]], yb = y[Q.pos[u]];
+    if (xa != yb) return xa < yb;
+  }
+  return true;
+}
+
+// One merge pass: runs of `run` rows become runs of 2*run within each query.
+// Each output position finds its source by a merge-path search (stable: the
+// left run wins ties).
+__global__ void k_merge_pass(Wave W, const uint32_t *in, uint32_t *out, uint64_t run) {
   const uint64_t n = W.ctrl->len[6];
-  for (uint64_t i = gtid(); i < n; i += gthreads()) {
-    const uint32_t row = perm[i];
-    const uint32_t qi = W.out_q[row];
-    if (col == kMaxK) { key[i] = qi; continue; }
+  for (uint64_t g = gtid(); g < n; g += gthreads()) {
+    const uint32_t qi = seg_of_large(W.qs, W.nq, g, false);
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
-    key[i] = col < Q.k ? W.out[S.out_word_base + (uint64_t)(row - S.out_row_base) * Q.k + Q.pos[col]] : 0;
+    const uint64_t base = S.lrg_row_base, nq = S.out_rows, i = g - base;
+    const uint64_t a0 = (i / (2 * run)) * 2 * run, o = i - a0;
+    const uint64_t na = min(run, nq - a0), nb = nq - a0 > run ? min(run, nq - a0 - run) : 0;
+    if (nb == 0) {
+      out[g] = in[g];
+      continue;
+    }
+    const uint32_t *A = in + base + a0, *B = A + na;
+    uint64_t lo = o > nb ? o - nb : 0, hi = min(o, na);
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (out_row_le(W, Q, S, A[mid], B[o - 1 - mid])) lo = mid + 1; else hi = mid;
+    }
+    const uint64_t ia = lo, ib = o - lo;
+    const bool take_a = ib >= nb || (ia < na && out_row_le(W, Q, S, A[ia], B[ib]));
+    out[g] = take_a ? A[ia] : B[ib];
   }
 }
 
@@ -1091,7 +1215,7 @@ __global__ void k_gather(Wave W, const uint32_t *perm) {
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
     const uint32_t *src = W.out + S.out_word_base + (uint64_t)(row - S.out_row_base) * Q.k;
-    uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.lrg_row_base) * Q.k;
+    uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.lrg_row_base) * Q.k;  // perm is query-grouped
     for (uint32_t u = 0; u < Q.k; ++u) dst[u] = src[Q.pos[u]];
   }
 }
@@ -1119,6 +1243,7 @@ __global__ void k_epilogue_copy(Wave W) {
 
 __global__ void k_epilogue_advance(Wave W) {
   const uint64_t top = W.ctrl->store_top, words = W.ctrl->out_top;
+  if (top + words > W.ctrl->hw[HW_STORE]) W.ctrl->hw[HW_STORE] = top + words;
   if (top + words <= W.bo.store_cap) W.ctrl->store_top = top + words;
   W.ctrl->wave += 1;
 }
@@ -1153,9 +1278,9 @@ void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s
   k_compact_count<<<grid_items(items, sms), kThreads, 0, s>>>(W, mode, step);
 }
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint64_t cap,
-                          cudaStream_t s, int sms) {
+                          int hw_slot, cudaStream_t s, int sms) {
   const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.ipg;
-  k_compact_write<<<grid_items(items, sms), kThreads, 0, s>>>(W, mode, step, scan, dst, cap);
+  k_compact_write<<<grid_items(items, sms), kThreads, 0, s>>>(W, mode, step, scan, dst, cap, hw_slot);
 }
 void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms) {
   const unsigned g = grid_for(sms, 8);
@@ -1232,9 +1357,17 @@ void launch_small_sort(const Wave &W, cudaStream_t s, int sms) {
   const unsigned g = W.nq < (uint32_t)sms * 2 ? (W.nq ? W.nq : 1) : (unsigned)sms * 2;
   k_small_sort<<<g, 256, bytes, s>>>(W);
 }
-void launch_iota(const Wave &W, uint32_t *perm, cudaStream_t s, int sms) { k_iota<<<grid_for(sms, 4), kThreads, 0, s>>>(W, perm); }
-void launch_sort_keys(const Wave &W, const uint32_t *perm, uint32_t *key, uint32_t col, cudaStream_t s, int sms) {
-  k_sort_keys<<<grid_for(sms, 4), kThreads, 0, s>>>(W, perm, key, col);
+void launch_tile_sort(const Wave &W, uint32_t *perm, cudaStream_t s, int sms) {
+  static bool attr = false;
+  const int bytes = (int)(4 * (kTileRows * kMaxK + kTileRows));
+  if (!attr) {
+    cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr = true;
+  }
+  k_tile_sort<<<grid_for(sms, 2), 256, bytes, s>>>(W, perm);
+}
+void launch_merge_pass(const Wave &W, const uint32_t *in, uint32_t *out, uint64_t run, cudaStream_t s, int sms) {
+  k_merge_pass<<<grid_for(sms, 4), kThreads, 0, s>>>(W, in, out, run);
 }
 void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms) {
   k_gather<<<grid_for(sms, 4), kThreads, 0, s>>>(W, perm);

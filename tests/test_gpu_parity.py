@@ -255,3 +255,23 @@ def test_scale_1m_one_at_a_time_waves(scale_1m):
     for i, r in enumerate(b.fetch()):
         assert_same(r, O.match(og, sub[i], cap=1 << 22), i)
     b.close()
+
+
+def test_autotuner_choice_is_cached_and_results_unchanged(small, tmp_path):
+    g, qs, og, dg = small
+    sub = qs[:60]
+    base = gs.match_batch(dg, sub, cap=1 << 20)
+    cache = str(tmp_path / "tune.txt")
+    t1 = gs.tune(dg, sub, cap=1 << 20, cache_path=cache)
+    assert t1["group"] in (4, 8, 16, 32) and t1["refine_rounds"] in (2, 4, 8) and not t1["from_cache"]
+    assert t1["configs_tried"] == 12
+    t2 = gs.tune(dg, sub, cap=1 << 20, cache_path=cache)
+    assert t2["from_cache"] and (t2["group"], t2["refine_rounds"]) == (t1["group"], t1["refine_rounds"])
+    b = gs.Batch(dg, sub, cap=1 << 20)  # built with the tuned settings
+    b.run()
+    b.finish()
+    for x, y in zip(b.fetch(), base):
+        assert (x.count, x.fingerprint) == (y.count, y.fingerprint)
+        np.testing.assert_array_equal(x.rows, y.rows)
+    b.close()
+    gs.lib().gs_tune_set(dg._h, 0, 0)
