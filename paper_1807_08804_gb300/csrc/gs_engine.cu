@@ -186,8 +186,8 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   W.nq = b->nq_s;
   W.nqv = b->nqv_s;
   W.nqe = b->nqe_s;
-  const uint64_t ipg = G.ipg;
-  W.slot_words = ((uint64_t)G.W0 + G.W1 + 31) / 32 * 32;
+  const uint64_t ipg = G.nchunks;  // compaction items per set
+  W.slot_words = ((uint64_t)G.W0 + G.W1 + G.ipg + 31) / 32 * 32;
   Sizing s = size_pools(b, o);
   gs_status st;
 #define A(ptr, n) \
@@ -334,7 +334,7 @@ void enqueue_front(Pipe &P, int K) {
   Wave &W = b->W;
   W.stats = b->stats_on ? 1 : 0;
   const int sms = b->sms, grp = b->group;
-  const uint64_t ipg = W.G.ipg;
+  const uint64_t ipg = W.G.nchunks;  // compaction items per set
   P.begin(KK_PLAN);
   launch_prologue(W, P.cur, sms);
   launch_plan(W, b->type_count, P.cur, sms);
@@ -353,7 +353,7 @@ void enqueue_front(Pipe &P, int K) {
     launch_explore(W, step, grp, P.cur, sms);
     P.end();
   }
-  P.begin(KK_COMPACT);
+  P.begin(KK_COMPACT_ALL);
   launch_compact_count(W, 1, 0, P.cur, sms);
   scan_u32(W.ccount, W.ascan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, P.cur, sms);
   launch_compact_write(W, 1, 0, W.ascan, W.alist, W.alist_cap, HW_ALIST, P.cur, sms);
@@ -369,8 +369,8 @@ void enqueue_back(Pipe &P, int K, int stop) {
   gs_batch *b = P.b;
   Wave &W = b->W;
   const int sms = b->sms, grp = b->group;
-  const uint64_t ipg = W.G.ipg;
-  P.begin(KK_COMPACT);
+  const uint64_t ipg = W.G.nchunks;  // compaction items per set
+  P.begin(KK_COMPACT_ALL);
   launch_compact_count(W, 1, 0, P.cur, sms);
   scan_u32(W.ccount, W.cscan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, P.cur, sms);
   launch_compact_write(W, 1, 0, W.cscan, W.flist, W.flist_cap, HW_FLIST, P.cur, sms);
@@ -427,6 +427,8 @@ void enqueue_large_sort(Pipe &P, uint64_t max_rows) {
   P.begin(KK_SORT);
   uint32_t *perm[2] = {W.sval[0], W.sval[1]};
   int cur = 0;
+  P.end();
+  P.begin(KK_SORT_LARGE);
   launch_tile_sort(W, perm[cur], P.cur, sms);
   for (uint64_t run = kTileRows; run < max_rows; run *= 2) {
     launch_merge_pass(W, perm[cur], perm[cur ^ 1], run, P.cur, sms);
@@ -642,7 +644,7 @@ gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_mat
     b->own_stream = true;
   }
   // waves: bounded by the candidate-bitmap budget
-  const uint64_t slot_bytes = 4 * (((uint64_t)g->d.W0 + g->d.W1 + 31) / 32 * 32);
+  const uint64_t slot_bytes = 4 * (((uint64_t)g->d.W0 + g->d.W1 + g->d.ipg + 31) / 32 * 32);
   const uint64_t bm_budget = 24ull << 30;
   uint64_t max_qv = std::max<uint64_t>(bm_budget / slot_bytes, kMaxK);
   uint32_t nq_s = wave_queries ? wave_queries : n;
@@ -819,7 +821,7 @@ gs_status grow_pools(gs_batch *b) {
     if (regrow(b, &W.bo.store, n) == GS_OK) { W.bo.store_cap = n; changed = true; }
   }
   if (changed) {
-    const uint64_t ipg = W.G.ipg;
+    const uint64_t ipg = W.G.nchunks;  // compaction items per set
     uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * ipg, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap}));
     tmpw = std::max(tmpw, radix_tmp_words(W.out_rows_cap));
     regrow(b, &b->scan_tmp, tmpw);
@@ -1080,7 +1082,7 @@ extern "C" gs_status gs_stats_enable(gs_batch *b, int on) {
 
 static const char *kKindNames[GS_NUM_KERNEL_KINDS] = {
     "plan", "filter", "compact", "explore", "refine", "ec_count", "ec_write", "clear",
-    "join_count", "join_write", "scan", "sort", "gather", "other", "", ""};
+    "join_count", "join_write", "scan", "sort", "gather", "other", "compact_all", "sort_large"};
 
 extern "C" gs_status gs_stats_get(gs_batch *b, gs_kernel_stats *out) {
   if (!b || !out) return fail(GS_ERR_INVALID, "null argument");

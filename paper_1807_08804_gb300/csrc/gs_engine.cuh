@@ -36,7 +36,7 @@ enum : int {
 // Kernel kinds for statistics.
 enum : int {
   KK_PLAN = 0, KK_FILTER, KK_COMPACT, KK_EXPLORE, KK_REFINE, KK_EC_COUNT, KK_EC_WRITE, KK_CLEAR,
-  KK_JOIN_COUNT, KK_JOIN_WRITE, KK_SCAN, KK_SORT, KK_GATHER, KK_OTHER, KK_N
+  KK_JOIN_COUNT, KK_JOIN_WRITE, KK_SCAN, KK_SORT, KK_GATHER, KK_OTHER, KK_COMPACT_ALL, KK_SORT_LARGE, KK_N
 };
 
 // One query as the device sees it.  The host fills the query part (edges
@@ -113,6 +113,7 @@ struct Ctrl {
   uint64_t fb_src[3];               // source rows staged by the chunked join
   uint64_t hw[10];                  // sizes the run asked of each pool (see HW_*)
   uint64_t max_large_rows;          // largest output above the one-block sort limit
+  uint64_t fin_words;               // words of the rows returned by this wave
   uint64_t bytes[KK_N];             // algorithmic bytes per kernel kind
 };
 

@@ -309,7 +309,8 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   d.sig_words = sig_words;
   d.W0 = (V + 31) / 32;
   d.W1 = (d.W0 + 31) / 32;
-  d.ipg = (d.W1 + 31) / 32;
+  d.nchunks = (d.W1 + 31) / 32;
+  d.ipg = (d.nchunks + 31) / 32;
   *out = g;
   return GS_OK;
 }

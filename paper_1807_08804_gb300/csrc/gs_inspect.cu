@@ -48,7 +48,7 @@ extern "C" gs_status gs_inspect_candidates(gs_graph *g, const gs_query *q, uint3
   if (st != GS_OK) return st;
   const uint32_t k = b->hq[0].k;
   const cudaStream_t s = b->stream;
-  const uint64_t ipg = g->d.ipg;
+  const uint64_t ipg = g->d.nchunks;
   std::vector<std::vector<uint32_t>> sets(k);
   if (stage == GS_STAGE_FILTER) {
     for (uint32_t u = 0; u < k && st == GS_OK; ++u) {

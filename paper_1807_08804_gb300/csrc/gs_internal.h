@@ -42,7 +42,8 @@ struct DevGraph {
   uint64_t sig_words;       // ceil(V / 8)
   uint32_t W0;              // bitmap words per candidate set: ceil(V/32)
   uint32_t W1;              // summary words: ceil(W0/32)
-  uint32_t ipg;             // compaction items per set: ceil(W1/32)
+  uint32_t nchunks;         // level-2 bits per set: one per 32 summary words, ceil(W1/32)
+  uint32_t ipg;             // level-2 words per set = compaction items per set: ceil(nchunks/32)
 };
 
 }  // namespace gs

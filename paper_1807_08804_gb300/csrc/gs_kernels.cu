@@ -21,13 +21,18 @@ __device__ __forceinline__ uint64_t gtid() { return blockIdx.x * (uint64_t)block
 __device__ __forceinline__ uint64_t gthreads() { return (uint64_t)gridDim.x * blockDim.x; }
 
 // ------------------------------------------------------------ bitmaps
-// A candidate set over V is a two-level bitmap: W0 words of one bit per
-// vertex, then W1 summary words with one bit per non-zero level-0 word.
+// A candidate set over V is a three-level bitmap: W0 words of one bit per
+// vertex, W1 summary words with one bit per non-zero level-0 word, and ipg
+// words with one bit per non-zero group of 32 summary words (a "chunk" of
+// 32,768 vertices).  Compaction and clearing visit only non-zero chunks.
 __device__ __forceinline__ uint32_t *slot_of(const Wave &W, uint32_t gqv) { return W.bm + (uint64_t)gqv * W.slot_words; }
 __device__ __forceinline__ bool bit_test(const uint32_t *slot, uint32_t v) { return (slot[v >> 5] >> (v & 31)) & 1u; }
 __device__ __forceinline__ void bit_set(const Wave &W, uint32_t *slot, uint32_t v) {
   uint32_t old = atomicOr(&slot[v >> 5], 1u << (v & 31));
-  if (old == 0) atomicOr(&slot[W.G.W0 + (v >> 10)], 1u << ((v >> 5) & 31));
+  if (old == 0) {
+    uint32_t old1 = atomicOr(&slot[W.G.W0 + (v >> 10)], 1u << ((v >> 5) & 31));
+    if (old1 == 0) atomicOr(&slot[W.G.W0 + W.G.W1 + (v >> 20)], 1u << ((v >> 15) & 31));
+  }
 }
 __device__ __forceinline__ void bit_clear(uint32_t *slot, uint32_t v) { atomicAnd(&slot[v >> 5], ~(1u << (v & 31))); }
 
@@ -276,7 +281,10 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
       slot[w0] = word;
     }
     uint32_t nz = __ballot_sync(kFull, word != 0);
-    if (lane == 0) slot[G.W0 + w1] = nz;
+    if (lane == 0) {
+      slot[G.W0 + w1] = nz;
+      if (nz) atomicOr(&slot[G.W0 + G.W1 + (w1 >> 10)], 1u << ((w1 >> 5) & 31));
+    }
     if (lane == 0)
       acc += 32ull * 32 * (Q.vtype[u] != kAny ? 1 : 0) + 32ull * 16 * (Q.need_begin[u + 1] - Q.need_begin[u]) + 32 * 4 + 4;
   }
@@ -298,39 +306,54 @@ __device__ __forceinline__ bool sel_slot(const Wave &W, int mode, uint32_t step,
   return W.dq[W.qv_q[s]].status == QS_OK;
 }
 
+// Items are chunks of 32 summary words (32,768 vertices) of a selected set.
+// A chunk whose level-2 bit is clear is skipped after one (cached) word
+// load; otherwise the warp loads the chunk's 32 summary words (lane j word
+// j) and walks the non-zero ones, lane j taking level-0 word j.  Four items
+// per warp iteration keep several summary loads in flight.
+constexpr int kCU = 4;
+
+__device__ __forceinline__ uint64_t chunk_items(const Wave &W, int mode) {
+  return (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.nchunks;
+}
+
+// Summary word of lane `lane` for chunk item `it` (0 when the chunk is empty
+// or the set is not selected).
+__device__ __forceinline__ uint32_t chunk_summary(const Wave &W, int mode, uint32_t step, uint64_t it, uint32_t lane,
+                                                  const uint32_t *&slot) {
+  const DevGraph &G = W.G;
+  uint32_t gqv = 0;
+  slot = nullptr;
+  if (!sel_slot(W, mode, step, (uint32_t)(it / G.nchunks), gqv)) return 0;
+  slot = slot_of(W, gqv);
+  const uint32_t c = (uint32_t)(it % G.nchunks);
+  if (!((slot[G.W0 + G.W1 + (c >> 5)] >> (c & 31)) & 1u)) return 0;
+  const uint32_t w1 = c * 32 + lane;
+  return w1 < G.W1 ? slot[G.W0 + w1] : 0;
+}
+
 __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W, int mode, uint32_t step) {
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
-  const uint32_t nsel = mode == 0 ? W.nq : W.nqv;
-  const uint64_t items = (uint64_t)nsel * G.ipg;
-  constexpr int kU = 4;  // items per warp iteration: their summary loads overlap
-  for (uint64_t it0 = (gtid() / 32) * kU; it0 < items; it0 += warps * kU) {
-    uint32_t sw[kU];
-    const uint32_t *slots[kU];
-    bool live[kU];
+  const uint64_t items = chunk_items(W, mode);
+  for (uint64_t it0 = (gtid() / 32) * kCU; it0 < items; it0 += warps * kCU) {
+    uint32_t sw[kCU];
+    const uint32_t *slots[kCU];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const uint64_t it = it0 + u;
-      uint32_t gqv = 0;
-      live[u] = it < items && sel_slot(W, mode, step, (uint32_t)(it / G.ipg), gqv);
-      slots[u] = live[u] ? slot_of(W, gqv) : nullptr;
-      const uint32_t w1 = (uint32_t)(it % G.ipg) * 32 + lane;
-      sw[u] = (live[u] && w1 < G.W1) ? slots[u][G.W0 + w1] : 0;
-    }
+    for (int u = 0; u < kCU; ++u) sw[u] = it0 + u < items ? chunk_summary(W, mode, step, it0 + u, lane, slots[u]) : 0;
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
+    for (int u = 0; u < kCU; ++u) {
       const uint64_t it = it0 + u;
       if (it >= items) break;
+      const uint32_t c = (uint32_t)(it % G.nchunks);
       uint32_t cnt = 0;
-      const uint32_t c = (uint32_t)(it % G.ipg);
       uint32_t m = __ballot_sync(kFull, sw[u] != 0);
       while (m) {
-        int j = __ffs(m) - 1;
+        const int j = __ffs(m) - 1;
         m &= m - 1;
-        uint32_t swj = __shfl_sync(kFull, sw[u], j);
-        uint32_t w0 = (c * 32 + j) * 32 + lane;
-        if ((swj >> lane) & 1u) cnt += __popc(slots[u][w0]);
+        const uint32_t swj = __shfl_sync(kFull, sw[u], j);
+        if ((swj >> lane) & 1u) cnt += __popc(slots[u][(c * 32 + j) * 32 + lane]);
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
@@ -339,47 +362,45 @@ __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W, int mode, ui
   }
 }
 
-// Writes ids in ascending order at dst[cscan[item] ...]; marks a query that
+// Writes ids in ascending order at dst[scan[item] ...]; marks a query that
 // does not fit dst_cap as overflowed.
 __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, uint32_t step, const uint64_t *scan,
                                                              uint32_t *dst, uint64_t dst_cap, int hw_slot) {
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
-  const uint32_t nsel = mode == 0 ? W.nq : W.nqv;
-  const uint64_t items = (uint64_t)nsel * G.ipg;
+  const uint64_t items = chunk_items(W, mode);
   if (gtid() == 0) atomicMax((unsigned long long *)&W.ctrl->hw[hw_slot], (unsigned long long)scan[items]);
   for (uint64_t it = gtid() / 32; it < items; it += warps) {
-    const uint32_t s = (uint32_t)(it / G.ipg), c = (uint32_t)(it % G.ipg);
-    uint32_t gqv = 0;
-    if (!sel_slot(W, mode, step, s, gqv)) continue;
-    const uint64_t base = scan[it];
+    const uint32_t *slot;
+    const uint32_t sw = chunk_summary(W, mode, step, it, lane, slot);
+    uint32_t m = __ballot_sync(kFull, sw != 0);
+    if (!m) continue;
     if (scan[it + 1] > dst_cap) {
+      const uint32_t s = (uint32_t)(it / G.nchunks);
       if (lane == 0) mark(W.dq[mode == 0 ? s : W.qv_q[s]], QS_OVERFLOW);
       continue;
     }
-    const uint32_t *slot = slot_of(W, gqv);
-    const uint32_t w1 = c * 32 + lane;
-    uint32_t sw = w1 < G.W1 ? slot[G.W0 + w1] : 0;
-    uint32_t m = __ballot_sync(kFull, sw != 0);
-    uint64_t run = base;
+    const uint32_t c = (uint32_t)(it % G.nchunks);
+    uint64_t run = scan[it];
     while (m) {
-      int j = __ffs(m) - 1;
+      const int j = __ffs(m) - 1;
       m &= m - 1;
-      uint32_t swj = __shfl_sync(kFull, sw, j);
-      uint32_t w0 = (c * 32 + j) * 32 + lane;
+      const uint32_t swj = __shfl_sync(kFull, sw, j);
+      const uint32_t w0 = (c * 32 + j) * 32 + lane;
       uint32_t x = ((swj >> lane) & 1u) ? slot[w0] : 0;
-      uint32_t n = __popc(x), incl = n;
+      const uint32_t n = __popc(x);
+      uint32_t incl = n;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, incl, o);
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += y;
       }
       uint64_t p = run + incl - n;
       while (x) {
-        int b = __ffs(x) - 1;
+        const int bpos = __ffs(x) - 1;
         x &= x - 1;
-        dst[p++] = w0 * 32 + b;
+        dst[p++] = w0 * 32 + bpos;
       }
       run += __shfl_sync(kFull, incl, 31);
     }
@@ -405,10 +426,10 @@ __global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
   const DevGraph &Gr = W.G;
   const uint32_t r = tile.thread_rank();
   const uint64_t ntile = gthreads() / G;
-  const uint64_t items = W.cscan[(uint64_t)W.nq * Gr.ipg];
+  const uint64_t items = W.cscan[(uint64_t)W.nq * Gr.nchunks];
   uint64_t acc = 0;
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
-    const uint32_t qi = seg_of(W.cscan, Gr.ipg, W.nq, it);
+    const uint32_t qi = seg_of(W.cscan, Gr.nchunks, W.nq, it);
     DQuery &Q = W.dq[qi];
     if (Q.status != QS_OK) continue;
     const uint32_t u = Q.visit[step];
@@ -479,11 +500,11 @@ __global__ void __launch_bounds__(kThreads) k_refine(Wave W, uint32_t round) {
   const DevGraph &Gr = W.G;
   const uint32_t r = tile.thread_rank();
   const uint64_t ntile = gthreads() / G;
-  const uint64_t items = W.ascan[(uint64_t)W.nqv * Gr.ipg];
+  const uint64_t items = W.ascan[(uint64_t)W.nqv * Gr.nchunks];
   bool changed = false;
   uint64_t acc = 0;
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
-    const uint32_t gqv = seg_of(W.ascan, Gr.ipg, W.nqv, it);
+    const uint32_t gqv = seg_of(W.ascan, Gr.nchunks, W.nqv, it);
     DQuery &Q = W.dq[W.qv_q[gqv]];
     if (Q.status != QS_OK) continue;
     const uint32_t u = gqv - Q.qv_base;
@@ -519,7 +540,7 @@ __global__ void __launch_bounds__(kThreads) k_refine(Wave W, uint32_t round) {
 // Final candidate lists: offsets and lengths per query vertex; a query with
 // an empty set has no embedding.
 __global__ void k_list_table(Wave W) {
-  const uint32_t ipg = W.G.ipg;
+  const uint32_t ipg = W.G.nchunks;
   for (uint64_t g = gtid(); g < W.nqv; g += gthreads()) {
     uint64_t b = W.cscan[g * ipg], e = W.cscan[(g + 1) * ipg];
     W.flist_off[g] = b;
@@ -632,26 +653,34 @@ __global__ void __launch_bounds__(kThreads) k_ec(Wave W) {
   flush_bytes(W, WRITE ? KK_EC_WRITE : KK_EC_COUNT, acc);
 }
 
-// Restore every touched bitmap word to zero (only words flagged in the
-// summary are visited), so the slots are clean for the next run.
+// Restore every touched bitmap word to zero (only chunks flagged at level 2
+// and words flagged at level 1 are visited), so the slots are clean for the
+// next run.
 __global__ void __launch_bounds__(kThreads) k_clear(Wave W) {
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
   const uint64_t items = (uint64_t)W.nqv * G.ipg;
   for (uint64_t it = gtid() / 32; it < items; it += warps) {
-    const uint32_t gqv = (uint32_t)(it / G.ipg), c = (uint32_t)(it % G.ipg);
+    const uint32_t gqv = (uint32_t)(it / G.ipg), grp = (uint32_t)(it % G.ipg);
     uint32_t *slot = slot_of(W, gqv);
-    const uint32_t w1 = c * 32 + lane;
-    uint32_t sw = w1 < G.W1 ? slot[G.W0 + w1] : 0;
-    uint32_t m = __ballot_sync(kFull, sw != 0);
-    while (m) {
-      int j = __ffs(m) - 1;
-      m &= m - 1;
-      uint32_t swj = __shfl_sync(kFull, sw, j);
-      if ((swj >> lane) & 1u) slot[(c * 32 + j) * 32 + lane] = 0;
+    uint32_t m2 = slot[G.W0 + G.W1 + grp];
+    while (m2) {
+      const uint32_t c = grp * 32 + (__ffs(m2) - 1);
+      m2 &= m2 - 1;
+      const uint32_t w1 = c * 32 + lane;
+      const uint32_t sw = w1 < G.W1 ? slot[G.W0 + w1] : 0;
+      uint32_t m = __ballot_sync(kFull, sw != 0);
+      while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t swj = __shfl_sync(kFull, sw, j);
+        if ((swj >> lane) & 1u) slot[(c * 32 + j) * 32 + lane] = 0;
+      }
+      if (sw) slot[G.W0 + w1] = 0;
     }
-    if (sw) slot[G.W0 + w1] = 0;
+    __syncwarp();
+    if (lane == 0) slot[G.W0 + G.W1 + grp] = 0;
   }
 }
 
@@ -730,7 +759,10 @@ __device__ __forceinline__ void level_sizes(const Wave &W, uint32_t qi, uint32_t
   if (Q.status != QS_OK || Q.k <= lvl) return;
   if (Q.k == lvl + 1) {
     if (Q.mode == GS_COUNT_ONLY || Q.cap == 0) return;
-    if (S.count > Q.cap) {
+    // More rows than cap are still written (and the smallest cap kept after
+    // the sort) while they stay within 8 * cap; beyond, the chunked path
+    // keeps a running top-cap instead.
+    if (S.count > Q.cap && S.count > 8 * Q.cap) {
       if (pass0) mark(Q, QS_TOPCAP);
       return;
     }
@@ -1027,8 +1059,9 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
     const uint32_t qi = base + threadIdx.x;
     uint64_t v[4] = {0, 0, 0, 0}, ex[4];
     if (qi < W.nq && W.dq[qi].status == QS_OK) {
-      v[0] = W.qs[qi].out_rows;
-      v[1] = W.qs[qi].out_rows * W.dq[qi].k;
+      const uint64_t keep = min(W.qs[qi].out_rows, W.dq[qi].cap);  // rows returned
+      v[0] = keep;
+      v[1] = keep * W.dq[qi].k;
       v[2] = small_output(W.dq[qi], W.qs[qi]) ? 0 : W.qs[qi].out_rows;
       v[3] = (v[2] + kTileRows - 1) / kTileRows;
       if (v[2]) atomicMax((unsigned long long *)&W.ctrl->max_large_rows, (unsigned long long)v[2]);
@@ -1065,6 +1098,7 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
   if (threadIdx.x == 0) {
     W.ctrl->len[6] = carry[2];
     W.ctrl->len[7] = carry[3];
+    W.ctrl->fin_words = carry[1];
   }
 }
 
@@ -1111,7 +1145,8 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
       }
     }
     uint32_t *dst = W.out_final + S.fin_word_base;
-    for (uint32_t t = threadIdx.x; t < n * k; t += blockDim.x) dst[t] = rows[idx[t / k] * k + t % k];
+    const uint32_t keep = (uint32_t)min((uint64_t)n, Q.cap);
+    for (uint32_t t = threadIdx.x; t < keep * k; t += blockDim.x) dst[t] = rows[idx[t / k] * k + t % k];
     __syncthreads();
   }
 }
@@ -1178,31 +1213,83 @@ __device__ __forceinline__ bool out_row_le(const Wave &W, const DQuery &Q, const
   return true;
 }
 
-// One merge pass: runs of `run` rows become runs of 2*run within each query.
-// Each output position finds its source by a merge-path search (stable: the
-// left run wins ties).
-__global__ void k_merge_pass(Wave W, const uint32_t *in, uint32_t *out, uint64_t run) {
-  const uint64_t n = W.ctrl->len[6];
-  for (uint64_t g = gtid(); g < n; g += gthreads()) {
-    const uint32_t qi = seg_of_large(W.qs, W.nq, g, false);
+// One merge pass: runs of `run` (>= kTileRows) rows become runs of 2*run
+// within each query.  One block per output tile of kTileRows rows: two
+// merge-path searches (stable: the left run wins ties) bound the tile's
+// slices of both runs; the slices are staged in shared memory with a 64-bit
+// key of the row's first two query-vertex columns, and each thread merges
+// four outputs after a short search inside the slices.  Full rows are read
+// only when the keys tie.
+__device__ __forceinline__ uint64_t row_key2(const Wave &W, const DQuery &Q, const QState &S, uint32_t r) {
+  const uint32_t *x = W.out + S.out_word_base + (uint64_t)(r - S.out_row_base) * Q.k;
+  return ((uint64_t)x[Q.pos[0]] << 32) | (Q.k > 1 ? x[Q.pos[1]] : 0u);
+}
+
+// a <= b for (key, row) pairs: keys first, then the remaining columns.
+__device__ __forceinline__ bool kr_le(const Wave &W, const DQuery &Q, const QState &S, uint64_t ka, uint32_t ra,
+                                      uint64_t kb, uint32_t rb) {
+  if (ka != kb) return ka < kb;
+  return out_row_le(W, Q, S, ra, rb);
+}
+
+__global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *in, uint32_t *out, uint64_t run) {
+  __shared__ uint32_t sidx[2 * kTileRows];
+  __shared__ uint64_t skey[2 * kTileRows];
+  __shared__ uint64_t bounds[4];
+  const uint64_t ntiles = W.ctrl->len[7];
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint32_t qi = seg_of_large(W.qs, W.nq, t, true);
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
-    const uint64_t base = S.lrg_row_base, nq = S.out_rows, i = g - base;
-    const uint64_t a0 = (i / (2 * run)) * 2 * run, o = i - a0;
-    const uint64_t na = min(run, nq - a0), nb = nq - a0 > run ? min(run, nq - a0 - run) : 0;
+    const uint64_t base = S.lrg_row_base, n = S.out_rows;
+    const uint64_t first = (t - S.lrg_tile_base) * kTileRows;           // local output index of the tile
+    const uint64_t a0 = (first / (2 * run)) * 2 * run;                   // pair start
+    const uint64_t na = min(run, n - a0), nb = n - a0 > run ? min(run, n - a0 - run) : 0;
+    const uint64_t o0 = first - a0, o1 = min(o0 + kTileRows, na + nb);
     if (nb == 0) {
-      out[g] = in[g];
-      continue;
+      for (uint64_t i = first + threadIdx.x; i < min(first + kTileRows, n); i += blockDim.x) out[base + i] = in[base + i];
+      continue;  // block-uniform
     }
     const uint32_t *A = in + base + a0, *B = A + na;
-    uint64_t lo = o > nb ? o - nb : 0, hi = min(o, na);
-    while (lo < hi) {
-      const uint64_t mid = (lo + hi) >> 1;
-      if (out_row_le(W, Q, S, A[mid], B[o - 1 - mid])) lo = mid + 1; else hi = mid;
+    if (threadIdx.x < 2) {  // diagonal searches for the tile's two ends
+      const uint64_t o = threadIdx.x == 0 ? o0 : o1;
+      uint64_t lo = o > nb ? o - nb : 0, hi = min(o, na);
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        const uint32_t ra = A[mid], rb = B[o - 1 - mid];
+        if (kr_le(W, Q, S, row_key2(W, Q, S, ra), ra, row_key2(W, Q, S, rb), rb)) lo = mid + 1; else hi = mid;
+      }
+      bounds[threadIdx.x * 2] = lo;
+      bounds[threadIdx.x * 2 + 1] = o - lo;
     }
-    const uint64_t ia = lo, ib = o - lo;
-    const bool take_a = ib >= nb || (ia < na && out_row_le(W, Q, S, A[ia], B[ib]));
-    out[g] = take_a ? A[ia] : B[ib];
+    __syncthreads();
+    const uint64_t ab = bounds[0], bb = bounds[1], ae = bounds[2], be = bounds[3];
+    const uint32_t la = (uint32_t)(ae - ab), lb = (uint32_t)(be - bb);
+    for (uint32_t i = threadIdx.x; i < la + lb; i += blockDim.x) {
+      const uint32_t r = i < la ? A[ab + i] : B[bb + i - la];
+      sidx[i] = r;
+      skey[i] = row_key2(W, Q, S, r);
+    }
+    __syncthreads();
+    const uint32_t total = la + lb;  // == o1 - o0
+    for (uint32_t p0 = threadIdx.x * 4; p0 < total; p0 += blockDim.x * 4) {
+      // merge-path search inside the staged slices for output p0
+      uint32_t lo = p0 > lb ? p0 - lb : 0, hi = min(p0, la);
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (kr_le(W, Q, S, skey[mid], sidx[mid], skey[la + p0 - 1 - mid], sidx[la + p0 - 1 - mid])) lo = mid + 1;
+        else hi = mid;
+      }
+      uint32_t ia = lo, ib = p0 - lo;
+      for (uint32_t p = p0; p < min(p0 + 4, total); ++p) {
+        bool take_a;
+        if (ib >= lb) take_a = true;
+        else if (ia >= la) take_a = false;
+        else take_a = kr_le(W, Q, S, skey[ia], sidx[ia], skey[la + ib], sidx[la + ib]);
+        out[base + first + p] = take_a ? sidx[ia++] : sidx[la + ib++];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -1214,6 +1301,7 @@ __global__ void k_gather(Wave W, const uint32_t *perm) {
     const uint32_t qi = W.out_q[row];
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
+    if (i - S.lrg_row_base >= Q.cap) continue;  // past the rows returned
     const uint32_t *src = W.out + S.out_word_base + (uint64_t)(row - S.out_row_base) * Q.k;
     uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.lrg_row_base) * Q.k;  // perm is query-grouped
     for (uint32_t u = 0; u < Q.k; ++u) dst[u] = src[Q.pos[u]];
@@ -1223,7 +1311,7 @@ __global__ void k_gather(Wave W, const uint32_t *perm) {
 // Epilogue: per-query results and rows of this wave into the batch store.
 __global__ void k_epilogue_copy(Wave W) {
   const WaveDesc D = W.waves[W.ctrl->wave];
-  const uint64_t top = W.ctrl->store_top, words = W.ctrl->out_top;
+  const uint64_t top = W.ctrl->store_top, words = W.ctrl->fin_words;
   const bool fits = top + words <= W.bo.store_cap;
   for (uint64_t qi = gtid(); qi < D.nq; qi += gthreads()) {
     const uint64_t b = D.q0 + qi;
@@ -1234,7 +1322,7 @@ __global__ void k_epilogue_copy(Wave W) {
     W.bo.count[b] = S.count;
     W.bo.fp[b] = S.fp;
     W.bo.status[b] = st;
-    W.bo.nrows[b] = st == QS_OK ? S.out_rows : 0;
+    W.bo.nrows[b] = st == QS_OK ? min(S.out_rows, Q.cap) : 0;
     W.bo.word_off[b] = top + S.fin_word_base;
   }
   if (fits)
@@ -1242,7 +1330,7 @@ __global__ void k_epilogue_copy(Wave W) {
 }
 
 __global__ void k_epilogue_advance(Wave W) {
-  const uint64_t top = W.ctrl->store_top, words = W.ctrl->out_top;
+  const uint64_t top = W.ctrl->store_top, words = W.ctrl->fin_words;
   if (top + words > W.ctrl->hw[HW_STORE]) W.ctrl->hw[HW_STORE] = top + words;
   if (top + words <= W.bo.store_cap) W.ctrl->store_top = top + words;
   W.ctrl->wave += 1;
@@ -1274,12 +1362,12 @@ void launch_filter(const Wave &W, cudaStream_t s, int sms) {
   k_filter<<<grid_items((uint64_t)W.nq * W.G.W1, sms), kThreads, 0, s>>>(W);
 }
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms) {
-  const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.ipg;
-  k_compact_count<<<grid_items(items, sms), kThreads, 0, s>>>(W, mode, step);
+  const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.nchunks;
+  k_compact_count<<<grid_items((items + kCU - 1) / kCU, sms), kThreads, 0, s>>>(W, mode, step);
 }
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint64_t cap,
                           int hw_slot, cudaStream_t s, int sms) {
-  const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.ipg;
+  const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.nchunks;
   k_compact_write<<<grid_items(items, sms), kThreads, 0, s>>>(W, mode, step, scan, dst, cap, hw_slot);
 }
 void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms) {
@@ -1367,7 +1455,7 @@ void launch_tile_sort(const Wave &W, uint32_t *perm, cudaStream_t s, int sms) {
   k_tile_sort<<<grid_for(sms, 2), 256, bytes, s>>>(W, perm);
 }
 void launch_merge_pass(const Wave &W, const uint32_t *in, uint32_t *out, uint64_t run, cudaStream_t s, int sms) {
-  k_merge_pass<<<grid_for(sms, 4), kThreads, 0, s>>>(W, in, out, run);
+  k_merge_tiles<<<grid_for(sms, 4), 256, 0, s>>>(W, in, out, run);
 }
 void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms) {
   k_gather<<<grid_for(sms, 4), kThreads, 0, s>>>(W, perm);

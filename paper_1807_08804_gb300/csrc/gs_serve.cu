@@ -80,7 +80,7 @@ struct gs_server {
 namespace {
 
 uint64_t estimate(const gs_graph *g, const gs_query &q) {
-  const uint64_t slot_bytes = 4 * (((uint64_t)g->d.W0 + g->d.W1 + 31) / 32 * 32);
+  const uint64_t slot_bytes = 4 * (((uint64_t)g->d.W0 + g->d.W1 + g->d.ipg + 31) / 32 * 32);
   uint64_t est = 1 << 16;
   for (uint32_t u = 0; u < q.k; ++u) {
     uint64_t c = q.vbind[u] != GS_UNBOUND ? 1 : (q.vtype[u] != GS_ANY && q.vtype[u] < g->d.T ? g->type_count[q.vtype[u]] : g->d.V);
