@@ -214,6 +214,8 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   A(W.ascan, (uint64_t)W.nqv * ipg + 1);
   A(W.tlist, s.tlist); W.tlist_cap = s.tlist;
   A(W.alist, s.alist); W.alist_cap = s.alist;
+  A(W.tlist_q, s.tlist);
+  A(W.alist_q, s.alist);
   A(W.flist, s.flist); W.flist_cap = s.flist;
   A(W.flist_off, W.nqv);
   A(W.flist_len, W.nqv);
@@ -347,7 +349,7 @@ void enqueue_front(Pipe &P, int K) {
     P.begin(KK_COMPACT);
     launch_compact_count(W, 0, step, P.cur, sms);
     scan_u32(W.ccount, W.cscan, &W.ctrl->len[0], (uint64_t)W.nq * ipg, b->scan_tmp, P.cur, sms);
-    launch_compact_write(W, 0, step, W.cscan, W.tlist, W.tlist_cap, HW_TLIST, P.cur, sms);
+    launch_compact_write(W, 0, step, W.cscan, W.tlist, W.tlist_q, W.tlist_cap, HW_TLIST, P.cur, sms);
     P.end();
     P.begin(KK_EXPLORE);
     launch_explore(W, step, grp, P.cur, sms);
@@ -356,7 +358,7 @@ void enqueue_front(Pipe &P, int K) {
   P.begin(KK_COMPACT_ALL);
   launch_compact_count(W, 1, 0, P.cur, sms);
   scan_u32(W.ccount, W.ascan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, P.cur, sms);
-  launch_compact_write(W, 1, 0, W.ascan, W.alist, W.alist_cap, HW_ALIST, P.cur, sms);
+  launch_compact_write(W, 1, 0, W.ascan, W.alist, W.alist_q, W.alist_cap, HW_ALIST, P.cur, sms);
   P.end();
   P.begin(KK_REFINE);
   for (uint32_t r = 0; r < b->refine_rounds; ++r) launch_refine(W, r, grp, P.cur, sms);
@@ -373,7 +375,7 @@ void enqueue_back(Pipe &P, int K, int stop) {
   P.begin(KK_COMPACT_ALL);
   launch_compact_count(W, 1, 0, P.cur, sms);
   scan_u32(W.ccount, W.cscan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, P.cur, sms);
-  launch_compact_write(W, 1, 0, W.cscan, W.flist, W.flist_cap, HW_FLIST, P.cur, sms);
+  launch_compact_write(W, 1, 0, W.cscan, W.flist, nullptr, W.flist_cap, HW_FLIST, P.cur, sms);
   launch_list_table(W, P.cur, sms);
   P.end();
   if (stop == 1) return;
@@ -789,8 +791,13 @@ gs_status grow_pools(gs_batch *b) {
     const uint64_t n = want(need);
     if (regrow(b, p, n) == GS_OK) { *cap = n; changed = true; }
   };
-  grow32(&W.tlist, &W.tlist_cap, hw[HW_TLIST]);
-  grow32(&W.alist, &W.alist_cap, hw[HW_ALIST]);
+  auto grow_owned = [&](uint32_t **p, uint32_t **owner, uint64_t *cap, uint64_t need) {
+    if (need <= *cap || need > kMaxEntries) return;
+    const uint64_t n = want(need);
+    if (regrow(b, p, n) == GS_OK && regrow(b, owner, n) == GS_OK) { *cap = n; changed = true; }
+  };
+  grow_owned(&W.tlist, &W.tlist_q, &W.tlist_cap, hw[HW_TLIST]);
+  grow_owned(&W.alist, &W.alist_q, &W.alist_cap, hw[HW_ALIST]);
   grow32(&W.flist, &W.flist_cap, hw[HW_FLIST]);
   grow32(&W.ec_vals, &W.ec_vals_cap, hw[HW_EC_VALS]);
   if (hw[HW_EC_ITEMS] > W.ec_items_cap && hw[HW_EC_ITEMS] <= kMaxEntries) {

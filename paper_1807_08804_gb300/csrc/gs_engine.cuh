@@ -142,6 +142,7 @@ struct Wave {
   // candidate lists
   uint32_t *tlist; uint64_t tlist_cap;   // exploration work list
   uint32_t *alist; uint64_t alist_cap;   // every set before refinement
+  uint32_t *tlist_q, *alist_q;           // owner of each entry: query / global query vertex
   uint32_t *flist; uint64_t flist_cap;   // final sets
   uint64_t *flist_off;              // [nqv]
   uint32_t *flist_len;              // [nqv]
@@ -170,8 +171,8 @@ void launch_prologue(const Wave &W, cudaStream_t s, int sms);
 void launch_plan(const Wave &W, const uint32_t *type_count, cudaStream_t s, int sms);
 void launch_filter(const Wave &W, cudaStream_t s, int sms);
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms);
-void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint64_t cap,
-                          int hw_slot, cudaStream_t s, int sms);
+void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint32_t *owner,
+                          uint64_t cap, int hw_slot, cudaStream_t s, int sms);
 void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms);
 void launch_refine(const Wave &W, uint32_t round, int group, cudaStream_t s, int sms);
 void launch_list_table(const Wave &W, cudaStream_t s, int sms);

@@ -60,7 +60,7 @@ extern "C" gs_status gs_inspect_candidates(gs_graph *g, const gs_query *q, uint3
       launch_filter(b->W, s, b->sms);
       launch_compact_count(b->W, 0, 0, s, b->sms);
       scan_u32(b->W.ccount, b->W.cscan, &b->W.ctrl->len[0], (uint64_t)b->W.nq * ipg, b->scan_tmp, s, b->sms);
-      launch_compact_write(b->W, 0, 0, b->W.cscan, b->W.tlist, b->W.tlist_cap, HW_TLIST, s, b->sms);
+      launch_compact_write(b->W, 0, 0, b->W.cscan, b->W.tlist, b->W.tlist_q, b->W.tlist_cap, HW_TLIST, s, b->sms);
       uint64_t total = 0;
       GS_CUDA(cudaMemcpyAsync(&total, b->W.cscan + (uint64_t)b->W.nq * ipg, 8, cudaMemcpyDeviceToHost, s));
       GS_CUDA(cudaStreamSynchronize(s));

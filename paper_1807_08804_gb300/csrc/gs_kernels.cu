@@ -9,6 +9,9 @@
 //   ec_*        collect_edge_candidates: count / scan / write
 //   join_*      combine_edge_candidates: count / scan / write per level
 //   sort/gather lexicographic order of the embeddings, query-vertex columns
+#include <mutex>
+#include <unordered_map>
+
 #include "gs_engine.cuh"
 
 namespace gs {
@@ -110,6 +113,26 @@ __device__ __forceinline__ uint32_t seg_of_rows(const QState *qs, uint32_t nq, u
   while (hi - lo > 1) {
     uint32_t mid = (lo + hi) >> 1;
     if (qs[mid].cur_row_base <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Tile-cooperative form of the same search: each round the G lanes probe G
+// evenly spaced points of [lo, hi) and keep the gap between the last probe
+// at or below the item and the first above it, so a search over n segments
+// takes log_{G+1}(n) dependent loads instead of log_2(n).  Every lane of the
+// tile calls it with the same item and gets the same answer.
+template <int G, class Tile, class Base>
+__device__ __forceinline__ uint32_t tile_seg(const Tile &tile, uint32_t ns, uint64_t item, Base base) {
+  uint32_t lo = 0, hi = ns;  // invariant: answer in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t step = (hi - lo + G) / (G + 1);
+    const uint32_t p = lo + (tile.thread_rank() + 1) * step;
+    const bool le = p < hi && base(p) <= item;
+    const uint32_t cnt = __popc(tile.ballot(le));  // the probes at or below the item are a prefix
+    const uint32_t nlo = lo + cnt * step;
+    hi = min(hi, nlo + step);
+    lo = nlo;
   }
   return lo;
 }
@@ -332,6 +355,28 @@ __device__ __forceinline__ uint32_t chunk_summary(const Wave &W, int mode, uint3
   return w1 < G.W1 ? slot[G.W0 + w1] : 0;
 }
 
+// Level-0 words of lane `lane`'s level-1 word `sw` in chunk c: eight 16-byte
+// loads, issued together, of the quads that hold a set level-1 bit (the
+// others read as zero).  Words whose level-1 bit is clear are zeroed, so a
+// quad that runs past the last level-0 word counts nothing.
+__device__ __forceinline__ void load_l0(const uint32_t *slot, uint32_t c, uint32_t lane, uint32_t sw, uint32_t (&x)[32]) {
+  const uint4 *p = reinterpret_cast<const uint4 *>(slot + (uint64_t)(c * 32 + lane) * 32);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if ((sw >> (4 * q)) & 0xFu) v = __ldg(p + q);
+    x[4 * q] = v.x;
+    x[4 * q + 1] = v.y;
+    x[4 * q + 2] = v.z;
+    x[4 * q + 3] = v.w;
+  }
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    if (!((sw >> i) & 1u)) x[i] = 0;
+}
+
+// Candidates per chunk item.  One warp per item; lane j owns level-1 word j
+// of the chunk and counts its level-0 words.
 __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W, int mode, uint32_t step) {
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
@@ -346,14 +391,12 @@ __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W, int mode, ui
     for (int u = 0; u < kCU; ++u) {
       const uint64_t it = it0 + u;
       if (it >= items) break;
-      const uint32_t c = (uint32_t)(it % G.nchunks);
       uint32_t cnt = 0;
-      uint32_t m = __ballot_sync(kFull, sw[u] != 0);
-      while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t swj = __shfl_sync(kFull, sw[u], j);
-        if ((swj >> lane) & 1u) cnt += __popc(slots[u][(c * 32 + j) * 32 + lane]);
+      if (sw[u]) {
+        uint32_t x[32];
+        load_l0(slots[u], (uint32_t)(it % G.nchunks), lane, sw[u], x);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) cnt += __popc(x[i]);
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
@@ -362,10 +405,13 @@ __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W, int mode, ui
   }
 }
 
-// Writes ids in ascending order at dst[scan[item] ...]; marks a query that
-// does not fit dst_cap as overflowed.
+// Writes ids in ascending order at dst[scan[item] ...] and, when `owner` is
+// given, the set's owner (query for mode 0, global query vertex for mode 1)
+// beside each id; marks a query that does not fit dst_cap as overflowed.
+// Lane j writes the ids of level-1 word j after the ids of the lanes before it.
 __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, uint32_t step, const uint64_t *scan,
-                                                             uint32_t *dst, uint64_t dst_cap, int hw_slot) {
+                                                             uint32_t *dst, uint32_t *owner, uint64_t dst_cap,
+                                                             int hw_slot) {
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
@@ -374,35 +420,42 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, ui
   for (uint64_t it = gtid() / 32; it < items; it += warps) {
     const uint32_t *slot;
     const uint32_t sw = chunk_summary(W, mode, step, it, lane, slot);
-    uint32_t m = __ballot_sync(kFull, sw != 0);
-    if (!m) continue;
+    if (!__any_sync(kFull, sw != 0)) continue;
     if (scan[it + 1] > dst_cap) {
       const uint32_t s = (uint32_t)(it / G.nchunks);
       if (lane == 0) mark(W.dq[mode == 0 ? s : W.qv_q[s]], QS_OVERFLOW);
+      // positions of this chunk below the capacity still name their owner,
+      // so that every entry a consumer reads below the capacity is defined
+      if (owner)
+        for (uint64_t p = scan[it] + lane; p < dst_cap; p += 32) owner[p] = s;
       continue;
     }
     const uint32_t c = (uint32_t)(it % G.nchunks);
-    uint64_t run = scan[it];
-    while (m) {
-      const int j = __ffs(m) - 1;
-      m &= m - 1;
-      const uint32_t swj = __shfl_sync(kFull, sw, j);
-      const uint32_t w0 = (c * 32 + j) * 32 + lane;
-      uint32_t x = ((swj >> lane) & 1u) ? slot[w0] : 0;
-      const uint32_t n = __popc(x);
-      uint32_t incl = n;
+    uint32_t x[32];
+    uint32_t n = 0;
+    if (sw) {
+      load_l0(slot, c, lane, sw, x);
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
+      for (int i = 0; i < 32; ++i) n += __popc(x[i]);
+    }
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (!sw) continue;
+    uint64_t p = scan[it] + incl - n;
+    const uint32_t id0 = (c * 32 + lane) * 1024, s = (uint32_t)(it / G.nchunks);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      uint32_t w = x[i];
+      while (w) {
+        const int bpos = __ffs(w) - 1;
+        w &= w - 1;
+        if (owner) owner[p] = s;
+        dst[p++] = id0 + i * 32 + bpos;
       }
-      uint64_t p = run + incl - n;
-      while (x) {
-        const int bpos = __ffs(x) - 1;
-        x &= x - 1;
-        dst[p++] = w0 * 32 + bpos;
-      }
-      run += __shfl_sync(kFull, incl, 31);
     }
   }
 }
@@ -429,8 +482,8 @@ __global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
   const uint64_t items = W.cscan[(uint64_t)W.nq * Gr.nchunks];
   uint64_t acc = 0;
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
-    const uint32_t qi = seg_of(W.cscan, Gr.nchunks, W.nq, it);
-    DQuery &Q = W.dq[qi];
+    if (it >= W.tlist_cap) break;  // entries past the list belong to overflowed queries
+    DQuery &Q = W.dq[W.tlist_q[it]];
     if (Q.status != QS_OK) continue;
     const uint32_t u = Q.visit[step];
     const uint32_t v = W.tlist[it];
@@ -504,7 +557,8 @@ __global__ void __launch_bounds__(kThreads) k_refine(Wave W, uint32_t round) {
   bool changed = false;
   uint64_t acc = 0;
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
-    const uint32_t gqv = seg_of(W.ascan, Gr.nchunks, W.nqv, it);
+    if (it >= W.alist_cap) break;  // entries past the list belong to overflowed queries
+    const uint32_t gqv = W.alist_q[it];
     DQuery &Q = W.dq[W.qv_q[gqv]];
     if (Q.status != QS_OK) continue;
     const uint32_t u = gqv - Q.qv_base;
@@ -609,7 +663,7 @@ __global__ void __launch_bounds__(kThreads) k_ec(Wave W) {
   uint64_t acc = 0;
   if (WRITE && gtid() == 0) atomicMax((unsigned long long *)&W.ctrl->hw[HW_EC_VALS], (unsigned long long)W.ec_off[items]);
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
-    const uint32_t ge = seg_of(W.ec_key_base, 1, W.nqe, it);
+    const uint32_t ge = tile_seg<G>(tile, W.nqe, it, [&](uint32_t s) { return W.ec_key_base[s]; });
     DQuery &Q = W.dq[W.qe_q[ge]];
     if (Q.status != QS_OK) {
       if (!WRITE && r == 0) W.ec_cnt[it] = 0;
@@ -939,7 +993,7 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Wave W, uint32_t s) {
   const uint32_t *lvl = W.lvl[s & 1];
   uint64_t acc = 0;
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
-    const uint32_t qi = seg_of_rows(W.qs, W.nq, it);
+    const uint32_t qi = tile_seg<G>(tile, W.nq, it, [&](uint32_t s) { return W.qs[s].cur_row_base; });
     const DQuery &Q = W.dq[qi];
     QState &S = W.qs[qi];
     uint32_t cnt = 0;
@@ -999,7 +1053,7 @@ __global__ void __launch_bounds__(kThreads) k_join_write(Wave W, uint32_t s) {
   uint32_t *nxt = W.lvl[(s + 1) & 1];
   uint64_t acc = 0;
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
-    const uint32_t qi = seg_of_src(W.src, W.nq, it);
+    const uint32_t qi = tile_seg<G>(tile, W.nq, it, [&](uint32_t s) { return W.src[s].row_base; });
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
     const SrcRows R = W.src[qi];
@@ -1337,11 +1391,37 @@ __global__ void k_epilogue_advance(Wave W) {
 }
 
 inline unsigned grid_for(int sms, int per_sm) { return (unsigned)(sms * per_sm); }
+
+// Resident blocks per SM of a kernel (from its registers and shared memory),
+// capped at 8; queried once per kernel.  Persistent grid-stride kernels are
+// launched with exactly this many blocks per SM, so that no block waits for a
+// second wave behind the others.
+int resident_per_sm(const void *fn, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(fn);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  n = n > 8 ? 8 : n;
+  cache.emplace(fn, n);
+  return n;
+}
+template <class... P>
+unsigned persistent_grid(void (*fn)(P...), int sms, int threads = kThreads, size_t smem = 0) {
+  return (unsigned)(sms * resident_per_sm((const void *)fn, threads, smem));
+}
 // Blocks for a fixed number of warp-sized items, at most the persistent grid.
-inline unsigned grid_items(uint64_t warp_items, int sms) {
+template <class... P>
+unsigned grid_items(void (*fn)(P...), uint64_t warp_items, int sms) {
   uint64_t b = (warp_items + kThreads / 32 - 1) / (kThreads / 32);
   if (b == 0) b = 1;
-  return (unsigned)(b < (uint64_t)sms * 8 ? b : (uint64_t)sms * 8);
+  const uint64_t cap = persistent_grid(fn, sms);
+  return (unsigned)(b < cap ? b : cap);
 }
 inline unsigned blocks_for(uint64_t n, unsigned per) {
   uint64_t b = (n + per - 1) / per;
@@ -1359,33 +1439,31 @@ void launch_plan(const Wave &W, const uint32_t *type_count, cudaStream_t s, int 
   k_owners<<<blocks_for(W.nq, 128), 128, 0, s>>>(W);
 }
 void launch_filter(const Wave &W, cudaStream_t s, int sms) {
-  k_filter<<<grid_items((uint64_t)W.nq * W.G.W1, sms), kThreads, 0, s>>>(W);
+  k_filter<<<grid_items(k_filter, (uint64_t)W.nq * W.G.W1, sms), kThreads, 0, s>>>(W);
 }
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms) {
   const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.nchunks;
-  k_compact_count<<<grid_items((items + kCU - 1) / kCU, sms), kThreads, 0, s>>>(W, mode, step);
+  k_compact_count<<<grid_items(k_compact_count, (items + kCU - 1) / kCU, sms), kThreads, 0, s>>>(W, mode, step);
 }
-void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint64_t cap,
-                          int hw_slot, cudaStream_t s, int sms) {
+void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint32_t *owner,
+                          uint64_t cap, int hw_slot, cudaStream_t s, int sms) {
   const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.nchunks;
-  k_compact_write<<<grid_items(items, sms), kThreads, 0, s>>>(W, mode, step, scan, dst, cap, hw_slot);
+  k_compact_write<<<grid_items(k_compact_write, items, sms), kThreads, 0, s>>>(W, mode, step, scan, dst, owner, cap, hw_slot);
 }
 void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms) {
-  const unsigned g = grid_for(sms, 8);
   switch (group) {
-    case 4: k_explore<4><<<g, kThreads, 0, s>>>(W, step); break;
-    case 8: k_explore<8><<<g, kThreads, 0, s>>>(W, step); break;
-    case 16: k_explore<16><<<g, kThreads, 0, s>>>(W, step); break;
-    default: k_explore<32><<<g, kThreads, 0, s>>>(W, step); break;
+    case 4: k_explore<4><<<persistent_grid(k_explore<4>, sms), kThreads, 0, s>>>(W, step); break;
+    case 8: k_explore<8><<<persistent_grid(k_explore<8>, sms), kThreads, 0, s>>>(W, step); break;
+    case 16: k_explore<16><<<persistent_grid(k_explore<16>, sms), kThreads, 0, s>>>(W, step); break;
+    default: k_explore<32><<<persistent_grid(k_explore<32>, sms), kThreads, 0, s>>>(W, step); break;
   }
 }
 void launch_refine(const Wave &W, uint32_t round, int group, cudaStream_t s, int sms) {
-  const unsigned g = grid_for(sms, 8);
   switch (group) {
-    case 4: k_refine<4><<<g, kThreads, 0, s>>>(W, round); break;
-    case 8: k_refine<8><<<g, kThreads, 0, s>>>(W, round); break;
-    case 16: k_refine<16><<<g, kThreads, 0, s>>>(W, round); break;
-    default: k_refine<32><<<g, kThreads, 0, s>>>(W, round); break;
+    case 4: k_refine<4><<<persistent_grid(k_refine<4>, sms), kThreads, 0, s>>>(W, round); break;
+    case 8: k_refine<8><<<persistent_grid(k_refine<8>, sms), kThreads, 0, s>>>(W, round); break;
+    case 16: k_refine<16><<<persistent_grid(k_refine<16>, sms), kThreads, 0, s>>>(W, round); break;
+    default: k_refine<32><<<persistent_grid(k_refine<32>, sms), kThreads, 0, s>>>(W, round); break;
   }
 }
 void launch_list_table(const Wave &W, cudaStream_t s, int sms) {
@@ -1396,29 +1474,27 @@ void launch_ec_limit(const Wave &W, cudaStream_t s, int sms) {
   k_ec_limit<<<blocks_for(W.nqe, kThreads), kThreads, 0, s>>>(W);
 }
 void launch_ec(const Wave &W, bool write, int group, cudaStream_t s, int sms) {
-  const unsigned g = grid_for(sms, 8);
   switch (group) {
-    case 4: if (write) k_ec<4, true><<<g, kThreads, 0, s>>>(W); else k_ec<4, false><<<g, kThreads, 0, s>>>(W); break;
-    case 8: if (write) k_ec<8, true><<<g, kThreads, 0, s>>>(W); else k_ec<8, false><<<g, kThreads, 0, s>>>(W); break;
-    case 16: if (write) k_ec<16, true><<<g, kThreads, 0, s>>>(W); else k_ec<16, false><<<g, kThreads, 0, s>>>(W); break;
-    default: if (write) k_ec<32, true><<<g, kThreads, 0, s>>>(W); else k_ec<32, false><<<g, kThreads, 0, s>>>(W); break;
+    case 4: if (write) k_ec<4, true><<<persistent_grid(k_ec<4, true>, sms), kThreads, 0, s>>>(W); else k_ec<4, false><<<persistent_grid(k_ec<4, false>, sms), kThreads, 0, s>>>(W); break;
+    case 8: if (write) k_ec<8, true><<<persistent_grid(k_ec<8, true>, sms), kThreads, 0, s>>>(W); else k_ec<8, false><<<persistent_grid(k_ec<8, false>, sms), kThreads, 0, s>>>(W); break;
+    case 16: if (write) k_ec<16, true><<<persistent_grid(k_ec<16, true>, sms), kThreads, 0, s>>>(W); else k_ec<16, false><<<persistent_grid(k_ec<16, false>, sms), kThreads, 0, s>>>(W); break;
+    default: if (write) k_ec<32, true><<<persistent_grid(k_ec<32, true>, sms), kThreads, 0, s>>>(W); else k_ec<32, false><<<persistent_grid(k_ec<32, false>, sms), kThreads, 0, s>>>(W); break;
   }
 }
 void launch_clear(const Wave &W, cudaStream_t s, int sms) {
-  k_clear<<<grid_items((uint64_t)W.nqv * W.G.ipg, sms), kThreads, 0, s>>>(W);
+  k_clear<<<grid_items(k_clear, (uint64_t)W.nqv * W.G.ipg, sms), kThreads, 0, s>>>(W);
 }
 void launch_join0(const Wave &W, cudaStream_t s, int sms) {
   k_join0_rows<<<blocks_for(W.nq, 256), 256, 0, s>>>(W);
   k_level_alloc<<<1, 1024, 0, s>>>(W, 0);
-  k_join0_write<<<grid_for(sms, 4), kThreads, 0, s>>>(W);
+  k_join0_write<<<persistent_grid(k_join0_write, sms), kThreads, 0, s>>>(W);
 }
 void launch_join_count(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms) {
-  const unsigned g = grid_for(sms, 8);
   switch (group) {
-    case 4: k_join_count<4><<<g, kThreads, 0, s>>>(W, lvl); break;
-    case 8: k_join_count<8><<<g, kThreads, 0, s>>>(W, lvl); break;
-    case 16: k_join_count<16><<<g, kThreads, 0, s>>>(W, lvl); break;
-    default: k_join_count<32><<<g, kThreads, 0, s>>>(W, lvl); break;
+    case 4: k_join_count<4><<<persistent_grid(k_join_count<4>, sms), kThreads, 0, s>>>(W, lvl); break;
+    case 8: k_join_count<8><<<persistent_grid(k_join_count<8>, sms), kThreads, 0, s>>>(W, lvl); break;
+    case 16: k_join_count<16><<<persistent_grid(k_join_count<16>, sms), kThreads, 0, s>>>(W, lvl); break;
+    default: k_join_count<32><<<persistent_grid(k_join_count<32>, sms), kThreads, 0, s>>>(W, lvl); break;
   }
 }
 void launch_join_totals(const Wave &W, cudaStream_t s, int sms) {
@@ -1426,12 +1502,11 @@ void launch_join_totals(const Wave &W, cudaStream_t s, int sms) {
 }
 void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s) { k_level_alloc<<<1, 1024, 0, s>>>(W, lvl); }
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms) {
-  const unsigned g = grid_for(sms, 8);
   switch (group) {
-    case 4: k_join_write<4><<<g, kThreads, 0, s>>>(W, lvl); break;
-    case 8: k_join_write<8><<<g, kThreads, 0, s>>>(W, lvl); break;
-    case 16: k_join_write<16><<<g, kThreads, 0, s>>>(W, lvl); break;
-    default: k_join_write<32><<<g, kThreads, 0, s>>>(W, lvl); break;
+    case 4: k_join_write<4><<<persistent_grid(k_join_write<4>, sms), kThreads, 0, s>>>(W, lvl); break;
+    case 8: k_join_write<8><<<persistent_grid(k_join_write<8>, sms), kThreads, 0, s>>>(W, lvl); break;
+    case 16: k_join_write<16><<<persistent_grid(k_join_write<16>, sms), kThreads, 0, s>>>(W, lvl); break;
+    default: k_join_write<32><<<persistent_grid(k_join_write<32>, sms), kThreads, 0, s>>>(W, lvl); break;
   }
 }
 void launch_final_bases(const Wave &W, cudaStream_t s) { k_final_bases<<<1, 1024, 0, s>>>(W); }
@@ -1452,16 +1527,16 @@ void launch_tile_sort(const Wave &W, uint32_t *perm, cudaStream_t s, int sms) {
     cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr = true;
   }
-  k_tile_sort<<<grid_for(sms, 2), 256, bytes, s>>>(W, perm);
+  k_tile_sort<<<persistent_grid(k_tile_sort, sms, 256, bytes), 256, bytes, s>>>(W, perm);
 }
 void launch_merge_pass(const Wave &W, const uint32_t *in, uint32_t *out, uint64_t run, cudaStream_t s, int sms) {
-  k_merge_tiles<<<grid_for(sms, 4), 256, 0, s>>>(W, in, out, run);
+  k_merge_tiles<<<persistent_grid(k_merge_tiles, sms, 256), 256, 0, s>>>(W, in, out, run);
 }
 void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms) {
-  k_gather<<<grid_for(sms, 4), kThreads, 0, s>>>(W, perm);
+  k_gather<<<persistent_grid(k_gather, sms), kThreads, 0, s>>>(W, perm);
 }
 void launch_epilogue(const Wave &W, cudaStream_t s, int sms) {
-  k_epilogue_copy<<<grid_for(sms, 4), kThreads, 0, s>>>(W);
+  k_epilogue_copy<<<persistent_grid(k_epilogue_copy, sms), kThreads, 0, s>>>(W);
   k_epilogue_advance<<<1, 1, 0, s>>>(W);
 }
 
