@@ -216,6 +216,8 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   A(W.alist, s.alist); W.alist_cap = s.alist;
   A(W.tlist_q, s.tlist);
   A(W.alist_q, s.alist);
+  A(W.fcnt, W.nq);
+  A(W.fscan, (uint64_t)W.nq + 1);
   A(W.flist, s.flist); W.flist_cap = s.flist;
   A(W.flist_off, W.nqv);
   A(W.flist_len, W.nqv);
@@ -247,8 +249,10 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   GS_CUDA(cudaMemsetAsync(W.bm, 0, sizeof(uint32_t) * (uint64_t)W.nqv * W.slot_words, b->stream));
   GS_CUDA(cudaMemsetAsync(W.ctrl, 0, sizeof(Ctrl), b->stream));
   GS_CUDA(cudaMemsetAsync(W.dq, 0, sizeof(DQuery) * (W.nq + 1), b->stream));
-  uint64_t lens[3] = {(uint64_t)W.nq * ipg, (uint64_t)W.nqv * ipg, (uint64_t)W.nqe};
+  const uint64_t lens[3] = {(uint64_t)W.nq * ipg, (uint64_t)W.nqv * ipg, (uint64_t)W.nqe};
   GS_CUDA(cudaMemcpyAsync(W.ctrl->len, lens, sizeof(lens), cudaMemcpyHostToDevice, b->stream));
+  const uint64_t nq = W.nq;
+  GS_CUDA(cudaMemcpyAsync(&W.ctrl->len[8], &nq, sizeof(nq), cudaMemcpyHostToDevice, b->stream));
   GS_CUDA(cudaMemcpyAsync(b->type_count, b->g->type_count, sizeof(uint32_t) * G.T, cudaMemcpyHostToDevice, b->stream));
   GS_CUDA(cudaStreamSynchronize(b->stream));
   return GS_OK;
@@ -342,6 +346,7 @@ void enqueue_front(Pipe &P, int K) {
   launch_plan(W, b->type_count, P.cur, sms);
   P.end();
   P.begin(KK_FILTER);
+  scan_u32(W.fcnt, W.fscan, &W.ctrl->len[8], W.nq, b->scan_tmp, P.cur, sms);
   launch_filter(W, P.cur, sms);
   P.end();
   const int steps = K >= 2 ? K - 1 : 0;

@@ -101,7 +101,7 @@ struct BatchOut {
 };
 
 struct Ctrl {
-  uint64_t len[8];                  // device-side lengths read by persistent kernels
+  uint64_t len[10];                 // device-side lengths read by persistent kernels
   uint32_t changed[kMaxRounds];     // refinement: did round t clear any bit
   uint64_t lvl_top, out_top;        // output pool top (words)
   uint64_t out_rows_total;
@@ -143,6 +143,7 @@ struct Wave {
   uint32_t *tlist; uint64_t tlist_cap;   // exploration work list
   uint32_t *alist; uint64_t alist_cap;   // every set before refinement
   uint32_t *tlist_q, *alist_q;           // owner of each entry: query / global query vertex
+  uint32_t *fcnt; uint64_t *fscan;       // filter work items per query [nq] and their scan [nq + 1]
   uint32_t *flist; uint64_t flist_cap;   // final sets
   uint64_t *flist_off;              // [nqv]
   uint32_t *flist_len;              // [nqv]

@@ -116,6 +116,11 @@ __global__ void k_signatures(uint32_t V, uint32_t R, const uint64_t *off, const 
   }
 }
 
+__global__ void k_iota(uint32_t n, uint32_t *out) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)i;
+}
+
 __global__ void k_types(uint32_t V, const uint32_t *vt, uint8_t *out, uint32_t *hist) {
   uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = tid; v < V; v += stride) {
@@ -294,6 +299,26 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   if (ns) GS_CUDA(cudaMemcpyAsync(sample.data(), g->adj_out + (kept - ns), ns * 4, cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaStreamSynchronize(s));
   cudaFree(hist);
+  // Vertices grouped by type (stable radix sort of (type, id) pairs keeps
+  // the ids ascending within a type); run starts from the type counts.
+  {
+    std::vector<uint32_t> toff(T + 1, 0);
+    for (uint32_t t = 0; t < T; ++t) toff[t + 1] = toff[t] + g->type_count[t];
+    if (cudaMalloc(&g->toff, sizeof(uint32_t) * (T + 1)) != cudaSuccess ||
+        cudaMalloc(&g->tvid, sizeof(uint32_t) * V) != cudaSuccess)
+      return cleanup(fail(GS_ERR_OOM, "type lists"));
+    GS_CUDA(cudaMemcpyAsync(g->toff, toff.data(), sizeof(uint32_t) * (T + 1), cudaMemcpyHostToDevice, s));
+    uint64_t nv = V;
+    GS_CUDA(cudaMemcpyAsync(dn.p, &nv, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    GS_CUDA(cudaMemcpyAsync(k0.p, vt.p, sizeof(uint32_t) * V, cudaMemcpyDeviceToDevice, s));
+    k_iota<<<blocks_for(V), kT, 0, s>>>(V, v0.as<uint32_t>());
+    int tb = 1;
+    while (tb < 8 && ((T - 1) >> tb)) ++tb;
+    const int res = radix_sort_pairs(k0.as<uint32_t>(), v0.as<uint32_t>(), k1.as<uint32_t>(), v1.as<uint32_t>(),
+                                     dn.as<uint64_t>(), nmax, 0, tb, tmpb.as<uint64_t>(), s, sms);
+    GS_CUDA(cudaMemcpyAsync(g->tvid, res ? v1.p : v0.p, sizeof(uint32_t) * V, cudaMemcpyDeviceToDevice, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+  }
   uint64_t h = 1469598103934665603ull;
   auto mixin = [&](uint64_t x) { h = (h ^ x) * 1099511628211ull; };
   mixin(V); mixin(kept); mixin(T); mixin(R);
@@ -305,6 +330,8 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   d.off[0] = g->off_out; d.off[1] = g->off_in;
   d.adj[0] = g->adj_out; d.adj[1] = g->adj_in;
   d.vtype = g->vtype;
+  d.tvid = g->tvid;
+  d.toff = g->toff;
   d.sig = g->sig;
   d.sig_words = sig_words;
   d.W0 = (V + 31) / 32;
@@ -324,6 +351,8 @@ extern "C" void gs_graph_free(gs_graph *g) {
   cudaFree(g->adj_out);
   cudaFree(g->adj_in);
   cudaFree(g->vtype);
+  cudaFree(g->tvid);
+  cudaFree(g->toff);
   cudaFree(g->sig);
   delete[] g->type_count;
   delete g;

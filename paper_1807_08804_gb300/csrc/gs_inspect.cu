@@ -57,6 +57,7 @@ extern "C" gs_status gs_inspect_candidates(gs_graph *g, const gs_query *q, uint3
       GS_CUDA(cudaMemsetAsync(&b->W.ctrl->wave, 0, sizeof(uint32_t), s));
       launch_prologue(b->W, s, b->sms);
       launch_plan(b->W, b->type_count, s, b->sms);
+      scan_u32(b->W.fcnt, b->W.fscan, &b->W.ctrl->len[8], b->W.nq, b->scan_tmp, s, b->sms);
       launch_filter(b->W, s, b->sms);
       launch_compact_count(b->W, 0, 0, s, b->sms);
       scan_u32(b->W.ccount, b->W.cscan, &b->W.ctrl->len[0], (uint64_t)b->W.nq * ipg, b->scan_tmp, s, b->sms);

@@ -245,45 +245,90 @@ __global__ void k_plan(Wave W, const uint32_t *type_count) {
 }
 
 // ============================================================ filter
-// kernel_check for the first visited vertex of each query: a bound vertex has
-// the single candidate bind (if it passes the test); otherwise every data
-// vertex is tested.  One warp writes 32 level-0 words and one summary word.
+// kernel_check for the first visited vertex u of each query.  Work items
+// (one warp each) per query: a bound u has one (its binding, if it passes the
+// test); a typed u has one per 1024 vertices of its type, taken from the
+// per-type vertex lists, so the filter reads only vertices that can pass the
+// type test; an untyped u has one per summary word (1024 vertices), which
+// writes 32 level-0 words and the summary word outright.
+__device__ __forceinline__ uint32_t filter_items(const DevGraph &G, const DQuery &Q) {
+  if (Q.status != QS_OK || Q.nvisit == 0) return 0;
+  const uint32_t u = Q.visit[0];
+  if (Q.vbind[u] != kUnbound) return 1;
+  if (Q.vtype[u] != kAny) return (G.toff[Q.vtype[u] + 1] - G.toff[Q.vtype[u]] + 1023) / 1024;
+  return G.W1;
+}
+
+// Degree-signature part of the candidate test (type and binding known to pass).
+__device__ __forceinline__ bool sig_ok(const DevGraph &G, const DQuery &Q, uint32_t u, uint32_t v) {
+  for (uint32_t i = Q.need_begin[u]; i < Q.need_begin[u + 1]; ++i) {
+    uint32_t w = G.sig[(uint64_t)Q.need_plane[i] * G.sig_words + (v >> 3)];
+    if (((w >> ((v & 7) * 4)) & 15u) < Q.need_cnt[i]) return false;
+  }
+  return true;
+}
+
+// OR `bits` into level-0 word w0, raising the summary bits when the word was empty.
+__device__ __forceinline__ void word_or(const Wave &W, uint32_t *slot, uint32_t w0, uint32_t bits) {
+  const uint32_t old = atomicOr(&slot[w0], bits);
+  if (old == 0) {
+    const uint32_t old1 = atomicOr(&slot[W.G.W0 + (w0 >> 5)], 1u << (w0 & 31));
+    if (old1 == 0) atomicOr(&slot[W.G.W0 + W.G.W1 + (w0 >> 15)], 1u << ((w0 >> 10) & 31));
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
   const DevGraph &G = W.G;
+  auto warp = cg::tiled_partition<32>(cg::this_thread_block());
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
-  const uint64_t items = (uint64_t)W.nq * G.W1;
+  const uint64_t items = W.fscan[W.nq];
   uint64_t acc = 0;
   for (uint64_t it = gtid() / 32; it < items; it += warps) {
-    const uint32_t qi = (uint32_t)(it / G.W1), w1 = (uint32_t)(it % G.W1);
+    const uint32_t qi = tile_seg<32>(warp, W.nq, it, [&](uint32_t s) { return W.fscan[s]; });
     const DQuery &Q = W.dq[qi];
     if (Q.status != QS_OK) continue;
     const uint32_t u = Q.visit[0];
+    const uint32_t j = (uint32_t)(it - W.fscan[qi]);
     uint32_t *slot = slot_of(W, Q.qv_base + u);
+    const uint32_t nneed = Q.need_begin[u + 1] - Q.need_begin[u];
     if (Q.vbind[u] != kUnbound) {
-      if (w1 == 0 && lane == 0 && cand_ok(G, Q, u, Q.vbind[u])) bit_set(W, slot, Q.vbind[u]);
+      if (lane == 0 && cand_ok(G, Q, u, Q.vbind[u])) bit_set(W, slot, Q.vbind[u]);
+      if (lane == 0) acc += 4 + nneed;
       continue;
     }
+    if (Q.vtype[u] != kAny) {
+      // 32 rounds of 32 consecutive type-list entries; the ids ascend, so the
+      // lanes that share a level-0 word are contiguous: a segmented OR over
+      // them leaves one atomic per touched word
+      const uint32_t t = Q.vtype[u];
+      const uint32_t b0 = G.toff[t] + j * 1024, e0 = min(b0 + 1024, G.toff[t + 1]);
+      for (uint32_t x0 = b0; x0 < e0; x0 += 32) {
+        const uint32_t x = x0 + lane;
+        uint32_t w = 0xFFFFFFFFu, bits = 0;
+        if (x < e0) {
+          const uint32_t v = G.tvid[x];
+          w = v >> 5;
+          if (sig_ok(G, Q, u, v)) bits = 1u << (v & 31);
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_down_sync(kFull, bits, o);
+          const uint32_t w2 = __shfl_down_sync(kFull, w, o);
+          if (lane + o < 32 && w2 == w) bits |= y;
+        }
+        const uint32_t wp = __shfl_up_sync(kFull, w, 1);
+        if ((lane == 0 || wp != w) && w != 0xFFFFFFFFu && bits) word_or(W, slot, w, bits);
+      }
+      if (lane == 0) acc += (uint64_t)(e0 - b0) * (4 + nneed);
+      continue;
+    }
+    const uint32_t w1 = j;
     const uint32_t w0 = w1 * 32 + lane;
     uint32_t word = 0;
     if (w0 < G.W0) {
       const uint32_t v0 = w0 * 32;
-      const uint32_t t = Q.vtype[u];
       uint32_t ok = 0xFFFFFFFFu;
-      if (t != kAny) {
-        // four type bytes per word compared at once; the 0xFF/0x00 byte
-        // flags are then gathered into four bits by one multiply
-        const uint4 *p = reinterpret_cast<const uint4 *>(G.vtype + v0);
-        uint4 a = p[0], b = p[1];
-        uint32_t wd[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        const uint32_t tt = t * 0x01010101u;
-        ok = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint32_t y = (__vcmpeq4(wd[q], tt) >> 7) & 0x01010101u;
-          ok |= ((y * 0x01020408u) >> 24) << (4 * q);
-        }
-      }
       for (uint32_t i = Q.need_begin[u]; i < Q.need_begin[u + 1] && ok; ++i) {
         // eight 4-bit counts per word: even and odd nibbles compared as
         // bytes, then interleaved back into vertex order
@@ -308,8 +353,7 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
       slot[G.W0 + w1] = nz;
       if (nz) atomicOr(&slot[G.W0 + G.W1 + (w1 >> 10)], 1u << ((w1 >> 5) & 31));
     }
-    if (lane == 0)
-      acc += 32ull * 32 * (Q.vtype[u] != kAny ? 1 : 0) + 32ull * 16 * (Q.need_begin[u + 1] - Q.need_begin[u]) + 32 * 4 + 4;
+    if (lane == 0) acc += 32ull * 16 * nneed + 32 * 4 + 4;
   }
   flush_bytes(W, KK_FILTER, acc);
 }
@@ -782,6 +826,7 @@ __global__ void k_prologue(Wave W) {
 __global__ void k_owners(Wave W) {
   for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
     const DQuery &Q = W.dq[qi];
+    W.fcnt[qi] = filter_items(W.G, Q);
     if (Q.status == QS_INVALID && Q.k == 0) continue;
     for (uint32_t u = 0; u < Q.k; ++u) W.qv_q[Q.qv_base + u] = (uint32_t)qi;
     for (uint32_t e = 0; e < Q.m; ++e) W.qe_q[Q.qe_base + e] = (uint32_t)qi;
