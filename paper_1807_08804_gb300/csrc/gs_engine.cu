@@ -186,7 +186,7 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   W.nq = b->nq_s;
   W.nqv = b->nqv_s;
   W.nqe = b->nqe_s;
-  const uint64_t ipg = G.nchunks;  // compaction items per set
+  const uint64_t cps = G.nchunks;  // chunks per set: one candidate count per chunk
   W.slot_words = ((uint64_t)G.W0 + G.W1 + G.ipg + 31) / 32 * 32;
   Sizing s = size_pools(b, o);
   gs_status st;
@@ -209,14 +209,16 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   A(W.bo.store, s.store_words);
   W.bo.store_cap = s.store_words;
   A(W.bm, (uint64_t)W.nqv * W.slot_words);
-  A(W.ccount, (uint64_t)W.nqv * ipg);
-  A(W.cscan, (uint64_t)W.nqv * ipg + 1);
-  A(W.ascan, (uint64_t)W.nqv * ipg + 1);
+  A(W.ccount, (uint64_t)W.nqv * cps);
+  A(W.cscan, (uint64_t)W.nqv * cps + 1);
+  A(W.ascan, (uint64_t)W.nqv * cps + 1);
   A(W.tlist, s.tlist); W.tlist_cap = s.tlist;
   A(W.alist, s.alist); W.alist_cap = s.alist;
   A(W.tlist_q, s.tlist);
   A(W.alist_q, s.alist);
   A(W.fcnt, W.nq);
+  if ((uint64_t)W.nqv * cps >= (1ull << 32)) return fail(GS_ERR_UNSUPPORTED, "batch too large for the chunk index");
+  A(W.clist, (uint64_t)W.nqv * cps);
   A(W.fscan, (uint64_t)W.nq + 1);
   A(W.flist, s.flist); W.flist_cap = s.flist;
   A(W.flist_off, W.nqv);
@@ -241,7 +243,7 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
     A(W.skey[i], s.out_rows);
     A(W.sval[i], s.out_rows);
   }
-  uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * ipg, (uint64_t)W.nqe, s.ec_items, W.row_cap}));
+  uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * cps, (uint64_t)W.nqe, s.ec_items, W.row_cap}));
   tmpw = std::max(tmpw, radix_tmp_words(s.out_rows));
   A(b->scan_tmp, tmpw);
   A(b->type_count, G.T);
@@ -249,7 +251,7 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   GS_CUDA(cudaMemsetAsync(W.bm, 0, sizeof(uint32_t) * (uint64_t)W.nqv * W.slot_words, b->stream));
   GS_CUDA(cudaMemsetAsync(W.ctrl, 0, sizeof(Ctrl), b->stream));
   GS_CUDA(cudaMemsetAsync(W.dq, 0, sizeof(DQuery) * (W.nq + 1), b->stream));
-  const uint64_t lens[3] = {(uint64_t)W.nq * ipg, (uint64_t)W.nqv * ipg, (uint64_t)W.nqe};
+  const uint64_t lens[3] = {(uint64_t)W.nq * cps, (uint64_t)W.nqv * cps, (uint64_t)W.nqe};
   GS_CUDA(cudaMemcpyAsync(W.ctrl->len, lens, sizeof(lens), cudaMemcpyHostToDevice, b->stream));
   const uint64_t nq = W.nq;
   GS_CUDA(cudaMemcpyAsync(&W.ctrl->len[8], &nq, sizeof(nq), cudaMemcpyHostToDevice, b->stream));
@@ -340,7 +342,7 @@ void enqueue_front(Pipe &P, int K) {
   Wave &W = b->W;
   W.stats = b->stats_on ? 1 : 0;
   const int sms = b->sms, grp = b->group;
-  const uint64_t ipg = W.G.nchunks;  // compaction items per set
+  const uint64_t cps = W.G.nchunks;  // chunks per set: one candidate count per chunk
   P.begin(KK_PLAN);
   launch_prologue(W, P.cur, sms);
   launch_plan(W, b->type_count, P.cur, sms);
@@ -353,7 +355,7 @@ void enqueue_front(Pipe &P, int K) {
   for (int step = 0; step < steps; ++step) {
     P.begin(KK_COMPACT);
     launch_compact_count(W, 0, step, P.cur, sms);
-    scan_u32(W.ccount, W.cscan, &W.ctrl->len[0], (uint64_t)W.nq * ipg, b->scan_tmp, P.cur, sms);
+    scan_u32(W.ccount, W.cscan, &W.ctrl->len[0], (uint64_t)W.nq * cps, b->scan_tmp, P.cur, sms);
     launch_compact_write(W, 0, step, W.cscan, W.tlist, W.tlist_q, W.tlist_cap, HW_TLIST, P.cur, sms);
     P.end();
     P.begin(KK_EXPLORE);
@@ -362,7 +364,7 @@ void enqueue_front(Pipe &P, int K) {
   }
   P.begin(KK_COMPACT_ALL);
   launch_compact_count(W, 1, 0, P.cur, sms);
-  scan_u32(W.ccount, W.ascan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, P.cur, sms);
+  scan_u32(W.ccount, W.ascan, &W.ctrl->len[1], (uint64_t)W.nqv * cps, b->scan_tmp, P.cur, sms);
   launch_compact_write(W, 1, 0, W.ascan, W.alist, W.alist_q, W.alist_cap, HW_ALIST, P.cur, sms);
   P.end();
   P.begin(KK_REFINE);
@@ -376,10 +378,10 @@ void enqueue_back(Pipe &P, int K, int stop) {
   gs_batch *b = P.b;
   Wave &W = b->W;
   const int sms = b->sms, grp = b->group;
-  const uint64_t ipg = W.G.nchunks;  // compaction items per set
+  const uint64_t cps = W.G.nchunks;  // chunks per set: one candidate count per chunk
   P.begin(KK_COMPACT_ALL);
   launch_compact_count(W, 1, 0, P.cur, sms);
-  scan_u32(W.ccount, W.cscan, &W.ctrl->len[1], (uint64_t)W.nqv * ipg, b->scan_tmp, P.cur, sms);
+  scan_u32(W.ccount, W.cscan, &W.ctrl->len[1], (uint64_t)W.nqv * cps, b->scan_tmp, P.cur, sms);
   launch_compact_write(W, 1, 0, W.cscan, W.flist, nullptr, W.flist_cap, HW_FLIST, P.cur, sms);
   launch_list_table(W, P.cur, sms);
   P.end();
@@ -833,8 +835,8 @@ gs_status grow_pools(gs_batch *b) {
     if (regrow(b, &W.bo.store, n) == GS_OK) { W.bo.store_cap = n; changed = true; }
   }
   if (changed) {
-    const uint64_t ipg = W.G.nchunks;  // compaction items per set
-    uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * ipg, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap}));
+    const uint64_t cps = W.G.nchunks;  // chunks per set: one candidate count per chunk
+    uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * cps, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap}));
     tmpw = std::max(tmpw, radix_tmp_words(W.out_rows_cap));
     regrow(b, &b->scan_tmp, tmpw);
     ::drop_graphs(b);

@@ -144,6 +144,7 @@ struct Wave {
   uint32_t *alist; uint64_t alist_cap;   // every set before refinement
   uint32_t *tlist_q, *alist_q;           // owner of each entry: query / global query vertex
   uint32_t *fcnt; uint64_t *fscan;       // filter work items per query [nq] and their scan [nq + 1]
+  uint64_t *clist;                       // non-empty chunks of a compaction: (gqv << 32) | count index
   uint32_t *flist; uint64_t flist_cap;   // final sets
   uint64_t *flist_off;              // [nqv]
   uint32_t *flist_len;              // [nqv]

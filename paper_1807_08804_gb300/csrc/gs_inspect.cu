@@ -48,7 +48,7 @@ extern "C" gs_status gs_inspect_candidates(gs_graph *g, const gs_query *q, uint3
   if (st != GS_OK) return st;
   const uint32_t k = b->hq[0].k;
   const cudaStream_t s = b->stream;
-  const uint64_t ipg = g->d.nchunks;
+  const uint64_t cps = g->d.nchunks;
   std::vector<std::vector<uint32_t>> sets(k);
   if (stage == GS_STAGE_FILTER) {
     for (uint32_t u = 0; u < k && st == GS_OK; ++u) {
@@ -60,10 +60,10 @@ extern "C" gs_status gs_inspect_candidates(gs_graph *g, const gs_query *q, uint3
       scan_u32(b->W.fcnt, b->W.fscan, &b->W.ctrl->len[8], b->W.nq, b->scan_tmp, s, b->sms);
       launch_filter(b->W, s, b->sms);
       launch_compact_count(b->W, 0, 0, s, b->sms);
-      scan_u32(b->W.ccount, b->W.cscan, &b->W.ctrl->len[0], (uint64_t)b->W.nq * ipg, b->scan_tmp, s, b->sms);
+      scan_u32(b->W.ccount, b->W.cscan, &b->W.ctrl->len[0], (uint64_t)b->W.nq * cps, b->scan_tmp, s, b->sms);
       launch_compact_write(b->W, 0, 0, b->W.cscan, b->W.tlist, b->W.tlist_q, b->W.tlist_cap, HW_TLIST, s, b->sms);
       uint64_t total = 0;
-      GS_CUDA(cudaMemcpyAsync(&total, b->W.cscan + (uint64_t)b->W.nq * ipg, 8, cudaMemcpyDeviceToHost, s));
+      GS_CUDA(cudaMemcpyAsync(&total, b->W.cscan + (uint64_t)b->W.nq * cps, 8, cudaMemcpyDeviceToHost, s));
       GS_CUDA(cudaStreamSynchronize(s));
       sets[u].resize(total);
       st = d2h(sets[u].data(), b->W.tlist, total, s);

@@ -380,23 +380,23 @@ __device__ __forceinline__ bool sel_slot(const Wave &W, int mode, uint32_t step,
 // per warp iteration keep several summary loads in flight.
 constexpr int kCU = 4;
 
-__device__ __forceinline__ uint64_t chunk_items(const Wave &W, int mode) {
-  return (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.nchunks;
+// Compaction items are groups of 32 chunks (one level-2 word) of a set:
+// ipg items per set.  A warp reads the group's level-2 word once and visits
+// only its non-empty chunks.
+__device__ __forceinline__ uint64_t group_items(const Wave &W, int mode) {
+  return (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.ipg;
 }
 
-// Summary word of lane `lane` for chunk item `it` (0 when the chunk is empty
-// or the set is not selected).
-__device__ __forceinline__ uint32_t chunk_summary(const Wave &W, int mode, uint32_t step, uint64_t it, uint32_t lane,
-                                                  const uint32_t *&slot) {
+// Selected set of item `it` and its level-2 word (0 when not selected).
+__device__ __forceinline__ uint32_t group_word(const Wave &W, int mode, uint32_t step, uint64_t it, uint32_t &s,
+                                               const uint32_t *&slot) {
   const DevGraph &G = W.G;
+  s = (uint32_t)(it / G.ipg);
   uint32_t gqv = 0;
   slot = nullptr;
-  if (!sel_slot(W, mode, step, (uint32_t)(it / G.nchunks), gqv)) return 0;
+  if (!sel_slot(W, mode, step, s, gqv)) return 0;
   slot = slot_of(W, gqv);
-  const uint32_t c = (uint32_t)(it % G.nchunks);
-  if (!((slot[G.W0 + G.W1 + (c >> 5)] >> (c & 31)) & 1u)) return 0;
-  const uint32_t w1 = c * 32 + lane;
-  return w1 < G.W1 ? slot[G.W0 + w1] : 0;
+  return slot[G.W0 + G.W1 + (uint32_t)(it % G.ipg)];
 }
 
 // Level-0 words of lane `lane`'s level-1 word `sw` in chunk c: eight 16-byte
@@ -419,62 +419,98 @@ __device__ __forceinline__ void load_l0(const uint32_t *slot, uint32_t c, uint32
     if (!((sw >> i) & 1u)) x[i] = 0;
 }
 
-// Candidates per chunk item.  One warp per item; lane j owns level-1 word j
-// of the chunk and counts its level-0 words.
-__global__ void __launch_bounds__(kThreads) k_compact_count(Wave W, int mode, uint32_t step) {
+// Level-1 word of lane `lane` in chunk c.
+__device__ __forceinline__ uint32_t l1_word(const DevGraph &G, const uint32_t *slot, uint32_t c, uint32_t lane) {
+  const uint32_t w1 = c * 32 + lane;
+  return w1 < G.W1 ? slot[G.W0 + w1] : 0;
+}
+
+// Non-empty chunks of the selected sets as a work list: entry
+// (gqv << 32) | (s * nchunks + c) for chunk c of set s (slot gqv).  One warp
+// per level-2 word appends its set bits with one atomic; the order of the
+// list does not matter (positions come from the scan of the counts).
+__global__ void __launch_bounds__(kThreads) k_chunk_list(Wave W, int mode, uint32_t step) {
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
-  const uint64_t items = chunk_items(W, mode);
+  const uint64_t items = group_items(W, mode);
+  for (uint64_t it = gtid() / 32; it < items; it += warps) {
+    uint32_t s, gqv = 0;
+    const uint32_t *slot;
+    const uint32_t m = group_word(W, mode, step, it, s, slot);
+    if (!m) continue;
+    sel_slot(W, mode, step, s, gqv);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd((unsigned long long *)&W.ctrl->len[9], (unsigned long long)__popc(m));
+    base = __shfl_sync(kFull, base, 0);
+    if ((m >> lane) & 1u) {
+      const uint32_t c = (uint32_t)(it % G.ipg) * 32 + lane;
+      W.clist[base + __popc(m & ((1u << lane) - 1))] = ((uint64_t)gqv << 32) | ((uint64_t)s * G.nchunks + c);
+    }
+  }
+}
+
+// Candidates per listed chunk (the others were zeroed before the list was
+// built).  Lane j owns level-1 word j and counts its level-0 words; the
+// level-1 words of kCU chunks are loaded together.
+__global__ void __launch_bounds__(kThreads) k_compact_count(Wave W) {
+  const DevGraph &G = W.G;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = gthreads() / 32;
+  const uint64_t items = W.ctrl->len[9];
   for (uint64_t it0 = (gtid() / 32) * kCU; it0 < items; it0 += warps * kCU) {
+    uint64_t e[kCU];
     uint32_t sw[kCU];
-    const uint32_t *slots[kCU];
-#pragma unroll
-    for (int u = 0; u < kCU; ++u) sw[u] = it0 + u < items ? chunk_summary(W, mode, step, it0 + u, lane, slots[u]) : 0;
 #pragma unroll
     for (int u = 0; u < kCU; ++u) {
-      const uint64_t it = it0 + u;
-      if (it >= items) break;
+      e[u] = it0 + u < items ? W.clist[it0 + u] : 0;
+      sw[u] = it0 + u < items ? l1_word(G, slot_of(W, (uint32_t)(e[u] >> 32)), (uint32_t)e[u] % G.nchunks, lane) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kCU; ++u) {
+      if (it0 + u >= items) break;
+      const uint32_t ci = (uint32_t)e[u], c = ci % G.nchunks;
       uint32_t cnt = 0;
       if (sw[u]) {
         uint32_t x[32];
-        load_l0(slots[u], (uint32_t)(it % G.nchunks), lane, sw[u], x);
+        load_l0(slot_of(W, (uint32_t)(e[u] >> 32)), c, lane, sw[u], x);
 #pragma unroll
         for (int i = 0; i < 32; ++i) cnt += __popc(x[i]);
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
-      if (lane == 0) W.ccount[it] = cnt;
+      if (lane == 0) W.ccount[ci] = cnt;
     }
   }
 }
 
-// Writes ids in ascending order at dst[scan[item] ...] and, when `owner` is
+// Writes ids in ascending order at dst[scan[chunk] ...] and, when `owner` is
 // given, the set's owner (query for mode 0, global query vertex for mode 1)
 // beside each id; marks a query that does not fit dst_cap as overflowed.
-// Lane j writes the ids of level-1 word j after the ids of the lanes before it.
-__global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, uint32_t step, const uint64_t *scan,
-                                                             uint32_t *dst, uint32_t *owner, uint64_t dst_cap,
-                                                             int hw_slot) {
+// Per listed chunk, lane j writes the ids of level-1 word j after the ids of
+// the lanes before it.
+__global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, const uint64_t *scan, uint32_t *dst,
+                                                             uint32_t *owner, uint64_t dst_cap, int hw_slot) {
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
-  const uint64_t items = chunk_items(W, mode);
-  if (gtid() == 0) atomicMax((unsigned long long *)&W.ctrl->hw[hw_slot], (unsigned long long)scan[items]);
+  const uint64_t items = W.ctrl->len[9];
+  if (gtid() == 0)
+    atomicMax((unsigned long long *)&W.ctrl->hw[hw_slot],
+              (unsigned long long)scan[(uint64_t)(mode == 0 ? W.nq : W.nqv) * G.nchunks]);
   for (uint64_t it = gtid() / 32; it < items; it += warps) {
-    const uint32_t *slot;
-    const uint32_t sw = chunk_summary(W, mode, step, it, lane, slot);
-    if (!__any_sync(kFull, sw != 0)) continue;
-    if (scan[it + 1] > dst_cap) {
-      const uint32_t s = (uint32_t)(it / G.nchunks);
+    const uint64_t e = W.clist[it];
+    const uint32_t ci = (uint32_t)e, s = ci / G.nchunks, c = ci % G.nchunks;
+    const uint32_t *slot = slot_of(W, (uint32_t)(e >> 32));
+    if (scan[ci + 1] > dst_cap) {
       if (lane == 0) mark(W.dq[mode == 0 ? s : W.qv_q[s]], QS_OVERFLOW);
       // positions of this chunk below the capacity still name their owner,
       // so that every entry a consumer reads below the capacity is defined
       if (owner)
-        for (uint64_t p = scan[it] + lane; p < dst_cap; p += 32) owner[p] = s;
+        for (uint64_t p = scan[ci] + lane; p < dst_cap; p += 32) owner[p] = s;
       continue;
     }
-    const uint32_t c = (uint32_t)(it % G.nchunks);
+    const uint32_t sw = l1_word(G, slot, c, lane);
     uint32_t x[32];
     uint32_t n = 0;
     if (sw) {
@@ -489,8 +525,8 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, ui
       if (lane >= o) incl += y;
     }
     if (!sw) continue;
-    uint64_t p = scan[it] + incl - n;
-    const uint32_t id0 = (c * 32 + lane) * 1024, s = (uint32_t)(it / G.nchunks);
+    uint64_t p = scan[ci] + incl - n;
+    const uint32_t id0 = (c * 32 + lane) * 1024;
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       uint32_t w = x[i];
@@ -1487,13 +1523,15 @@ void launch_filter(const Wave &W, cudaStream_t s, int sms) {
   k_filter<<<grid_items(k_filter, (uint64_t)W.nq * W.G.W1, sms), kThreads, 0, s>>>(W);
 }
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms) {
-  const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.nchunks;
-  k_compact_count<<<grid_items(k_compact_count, (items + kCU - 1) / kCU, sms), kThreads, 0, s>>>(W, mode, step);
+  const uint64_t sets = mode == 0 ? W.nq : W.nqv;
+  cudaMemsetAsync(W.ccount, 0, sizeof(uint32_t) * sets * W.G.nchunks, s);
+  cudaMemsetAsync(&W.ctrl->len[9], 0, sizeof(uint64_t), s);
+  k_chunk_list<<<grid_items(k_chunk_list, sets * W.G.ipg, sms), kThreads, 0, s>>>(W, mode, step);
+  k_compact_count<<<persistent_grid(k_compact_count, sms), kThreads, 0, s>>>(W);
 }
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint32_t *owner,
                           uint64_t cap, int hw_slot, cudaStream_t s, int sms) {
-  const uint64_t items = (uint64_t)(mode == 0 ? W.nq : W.nqv) * W.G.nchunks;
-  k_compact_write<<<grid_items(k_compact_write, items, sms), kThreads, 0, s>>>(W, mode, step, scan, dst, owner, cap, hw_slot);
+  k_compact_write<<<persistent_grid(k_compact_write, sms), kThreads, 0, s>>>(W, mode, scan, dst, owner, cap, hw_slot);
 }
 void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms) {
   switch (group) {
