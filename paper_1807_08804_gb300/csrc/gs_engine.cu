@@ -243,6 +243,7 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
     A(W.skey[i], s.out_rows);
     A(W.sval[i], s.out_rows);
   }
+  A(W.msplit, s.out_rows / kTileRows + W.nq + 1);
   uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * cps, (uint64_t)W.nqe, s.ec_items, W.row_cap}));
   tmpw = std::max(tmpw, radix_tmp_words(s.out_rows));
   A(b->scan_tmp, tmpw);
@@ -435,12 +436,13 @@ void enqueue_large_sort(Pipe &P, uint64_t max_rows) {
   const int sms = b->sms;
   P.begin(KK_SORT);
   uint32_t *perm[2] = {W.sval[0], W.sval[1]};
+  uint64_t *keys[2] = {W.skey[0], W.skey[1]};
   int cur = 0;
   P.end();
   P.begin(KK_SORT_LARGE);
-  launch_tile_sort(W, perm[cur], P.cur, sms);
+  launch_tile_sort(W, perm[cur], keys[cur], P.cur, sms);
   for (uint64_t run = kTileRows; run < max_rows; run *= 2) {
-    launch_merge_pass(W, perm[cur], perm[cur ^ 1], run, P.cur, sms);
+    launch_merge_pass(W, perm[cur], keys[cur], perm[cur ^ 1], keys[cur ^ 1], run, P.cur, sms);
     cur ^= 1;
   }
   P.end();
@@ -571,7 +573,7 @@ gs_status run_waves(gs_batch *b) {
         enqueue_large_sort(P, b->flag[1]);
         uint64_t passes = 0;
         for (uint64_t run = kTileRows; run < b->flag[1]; run *= 2) ++passes;
-        b->kernel_launches += 2 + passes;
+        b->kernel_launches += 2 + 2 * passes;
         b->large_sorts++;
       }
     }
@@ -824,6 +826,7 @@ gs_status grow_pools(gs_batch *b) {
     const uint64_t n = want(hw[HW_OUT_ROWS]);
     bool ok = regrow(b, &W.out_q, n) == GS_OK;
     for (int i = 0; i < 2 && ok; ++i) ok = regrow(b, &W.skey[i], n) == GS_OK && regrow(b, &W.sval[i], n) == GS_OK;
+    ok = ok && regrow(b, &W.msplit, n / kTileRows + W.nq + 1) == GS_OK;
     if (ok) { W.out_rows_cap = n; changed = true; }
   }
   if (hw[HW_OUT_WORDS] > W.out_words && hw[HW_OUT_WORDS] <= kMaxEntries) {

@@ -164,7 +164,9 @@ struct Wave {
   uint64_t out_rows_cap;
   uint32_t *out_final;              // sorted rows, query-vertex order
   // sort
-  uint32_t *skey[2], *sval[2];
+  uint64_t *skey[2];                    // sort keys of the large-output merge sort
+  uint32_t *sval[2];                    // row indices of the large-output merge sort
+  uint64_t *msplit;                     // merge-path split of each output tile
   int stats;
 };
 
@@ -189,8 +191,9 @@ void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s);
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms);
 void launch_final_bases(const Wave &W, cudaStream_t s);
 void launch_small_sort(const Wave &W, cudaStream_t s, int sms);
-void launch_tile_sort(const Wave &W, uint32_t *perm, cudaStream_t s, int sms);
-void launch_merge_pass(const Wave &W, const uint32_t *in, uint32_t *out, uint64_t run, cudaStream_t s, int sms);
+void launch_tile_sort(const Wave &W, uint32_t *perm, uint64_t *keys, cudaStream_t s, int sms);
+void launch_merge_pass(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+                       uint64_t run, cudaStream_t s, int sms);
 void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms);
 void launch_epilogue(const Wave &W, cudaStream_t s, int sms);
 

@@ -338,6 +338,8 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   d.W1 = (d.W0 + 31) / 32;
   d.nchunks = (d.W1 + 31) / 32;
   d.ipg = (d.nchunks + 31) / 32;
+  d.idbits = 1;
+  while (d.idbits < 32 && ((V - 1) >> d.idbits)) ++d.idbits;
   *out = g;
   return GS_OK;
 }

@@ -46,6 +46,7 @@ struct DevGraph {
   uint32_t W1;              // summary words: ceil(W0/32)
   uint32_t nchunks;         // level-2 bits per set: one per 32 summary words, ceil(W1/32)
   uint32_t ipg;             // level-2 words per set = compaction items per set: ceil(nchunks/32)
+  uint32_t idbits;          // bits of the largest vertex id (at least 1)
 };
 
 }  // namespace gs

@@ -1288,9 +1288,14 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
 
 // ============================================================ sort + gather
 // Large outputs (more than the one-block limit) are sorted as a merge sort
-// of row indices: each block sorts one tile of kTileRows rows of one query in
-// shared memory (rows in query-vertex column order, bitonic network), then
-// merge passes double the sorted runs within each query's rows.
+// of (key, row index) pairs.  The key packs the row's leading columns in
+// query-vertex order at the graph's id width (the first column in the top
+// bits; the column that does not fit whole contributes its top bits), so key
+// order is row order on those bits and only equal keys compare full rows.
+// Each block first sorts one tile of kTileRows rows of one query in shared
+// memory (bitonic network); merge passes then double the sorted runs within
+// each query, one partition kernel placing every output tile's split and one
+// merge kernel per pass moving contiguous slices.
 __device__ __forceinline__ uint32_t seg_of_large(const QState *qs, uint32_t nq, uint64_t item, bool tiles) {
   uint32_t lo = 0, hi = nq;
   while (hi - lo > 1) {
@@ -1300,41 +1305,22 @@ __device__ __forceinline__ uint32_t seg_of_large(const QState *qs, uint32_t nq, 
   return lo;
 }
 
-__global__ void __launch_bounds__(256) k_tile_sort(Wave W, uint32_t *perm) {
-  extern __shared__ uint32_t smem[];
-  uint32_t *rows = smem;                           // [kTileRows * kMaxK]
-  uint32_t *idx = smem + kTileRows * kMaxK;        // [kTileRows]
-  const uint64_t ntiles = W.ctrl->len[7];
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint32_t qi = seg_of_large(W.qs, W.nq, t, true);
-    const DQuery &Q = W.dq[qi];
-    const QState &S = W.qs[qi];
-    const uint64_t first = (t - S.lrg_tile_base) * kTileRows;
-    const uint32_t n = (uint32_t)min((uint64_t)kTileRows, S.out_rows - first), k = Q.k;
-    for (uint32_t x = threadIdx.x; x < n * k; x += blockDim.x) {
-      const uint32_t i = x / k, u = x % k;
-      rows[x] = W.out[S.out_word_base + (first + i) * k + Q.pos[u]];
+// Key of a row whose column of query vertex u is x[pos(u)].
+template <class Col>
+__device__ __forceinline__ uint64_t pack_key(uint32_t k, uint32_t b, Col col) {
+  uint64_t key = 0;
+  uint32_t used = 0;
+  for (uint32_t u = 0; u < k && used < 64; ++u) {
+    const uint64_t c = col(u);
+    if (used + b <= 64) {
+      key |= c << (64 - used - b);
+      used += b;
+    } else {
+      key |= c >> (b - (64 - used));
+      used = 64;
     }
-    uint32_t np2 = 1;
-    while (np2 < n) np2 <<= 1;
-    for (uint32_t x = threadIdx.x; x < np2; x += blockDim.x) idx[x] = x;
-    __syncthreads();
-    for (uint32_t size = 2; size <= np2; size <<= 1)
-      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-        for (uint32_t x = threadIdx.x; x < np2; x += blockDim.x) {
-          const uint32_t p = x ^ stride;
-          if (p > x) {
-            const bool up = (x & size) == 0;
-            const uint32_t a = idx[x], b = idx[p];
-            if (up ? row_less(rows, k, n, b, a) : row_less(rows, k, n, a, b)) { idx[x] = b; idx[p] = a; }
-          }
-        }
-        __syncthreads();
-      }
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-      perm[S.lrg_row_base + first + i] = (uint32_t)(S.out_row_base + first + idx[i]);
-    __syncthreads();
   }
+  return key;
 }
 
 // Row r of the output pool (query qi) compared in query-vertex order.
@@ -1348,80 +1334,153 @@ __device__ __forceinline__ bool out_row_le(const Wave &W, const DQuery &Q, const
   return true;
 }
 
-// One merge pass: runs of `run` (>= kTileRows) rows become runs of 2*run
-// within each query.  One block per output tile of kTileRows rows: two
-// merge-path searches (stable: the left run wins ties) bound the tile's
-// slices of both runs; the slices are staged in shared memory with a 64-bit
-// key of the row's first two query-vertex columns, and each thread merges
-// four outputs after a short search inside the slices.  Full rows are read
-// only when the keys tie.
-__device__ __forceinline__ uint64_t row_key2(const Wave &W, const DQuery &Q, const QState &S, uint32_t r) {
-  const uint32_t *x = W.out + S.out_word_base + (uint64_t)(r - S.out_row_base) * Q.k;
-  return ((uint64_t)x[Q.pos[0]] << 32) | (Q.k > 1 ? x[Q.pos[1]] : 0u);
-}
-
-// a <= b for (key, row) pairs: keys first, then the remaining columns.
+// (ka, a) <= (kb, b): keys first, the rows on equal keys.
 __device__ __forceinline__ bool kr_le(const Wave &W, const DQuery &Q, const QState &S, uint64_t ka, uint32_t ra,
                                       uint64_t kb, uint32_t rb) {
   if (ka != kb) return ka < kb;
   return out_row_le(W, Q, S, ra, rb);
 }
 
-__global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *in, uint32_t *out, uint64_t run) {
-  __shared__ uint32_t sidx[2 * kTileRows];
-  __shared__ uint64_t skey[2 * kTileRows];
-  __shared__ uint64_t bounds[4];
+// Tile sort: keys (and row indices) in shared memory, bitonic network;
+// rows are read from the output pool only to build the keys and to order
+// equal keys.
+__global__ void __launch_bounds__(256) k_tile_sort(Wave W, uint32_t *perm, uint64_t *keys) {
+  __shared__ uint64_t key[kTileRows];
+  __shared__ uint32_t idx[kTileRows];
   const uint64_t ntiles = W.ctrl->len[7];
+  const uint32_t b = W.G.idbits;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint32_t qi = seg_of_large(W.qs, W.nq, t, true);
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
-    const uint64_t base = S.lrg_row_base, n = S.out_rows;
-    const uint64_t first = (t - S.lrg_tile_base) * kTileRows;           // local output index of the tile
-    const uint64_t a0 = (first / (2 * run)) * 2 * run;                   // pair start
-    const uint64_t na = min(run, n - a0), nb = n - a0 > run ? min(run, n - a0 - run) : 0;
-    const uint64_t o0 = first - a0, o1 = min(o0 + kTileRows, na + nb);
-    if (nb == 0) {
-      for (uint64_t i = first + threadIdx.x; i < min(first + kTileRows, n); i += blockDim.x) out[base + i] = in[base + i];
+    const uint64_t first = (t - S.lrg_tile_base) * kTileRows;
+    const uint32_t n = (uint32_t)min((uint64_t)kTileRows, S.out_rows - first), k = Q.k;
+    const uint32_t r0 = (uint32_t)(S.out_row_base + first);  // pool index of the tile's first row
+    uint32_t np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
+      idx[i] = i;
+      if (i < n) {
+        const uint32_t *x = W.out + S.out_word_base + (first + i) * k;
+        key[i] = pack_key(k, b, [&](uint32_t u) { return x[Q.pos[u]]; });
+      }
+    }
+    __syncthreads();
+    // a < c in (key, row) order; positions past n sort last
+    auto less = [&](uint32_t a, uint32_t c) {
+      if (a >= n) return false;
+      if (c >= n) return true;
+      if (key[a] != key[c]) return key[a] < key[c];
+      return !out_row_le(W, Q, S, r0 + c, r0 + a);
+    };
+    for (uint32_t size = 2; size <= np2; size <<= 1)
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t x = threadIdx.x; x < np2 / 2; x += blockDim.x) {
+          // x-th compare-exchange pair of this stage: (i, i + stride)
+          const uint32_t i = 2 * x - (x & (stride - 1));
+          const uint32_t p = i + stride;
+          const bool up = (i & size) == 0;
+          const uint32_t a = idx[i], c = idx[p];
+          if (up ? less(c, a) : less(a, c)) { idx[i] = c; idx[p] = a; }
+        }
+        __syncthreads();
+      }
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      perm[S.lrg_row_base + first + i] = r0 + idx[i];
+      keys[S.lrg_row_base + first + i] = key[idx[i]];
+    }
+    __syncthreads();
+  }
+}
+
+// Where output tile t of a merge pass with runs of `run` rows sits: its
+// query, the start of its pair of runs and their lengths (nb = 0: a lone run).
+struct MergeTile {
+  uint32_t qi;
+  uint64_t base, first, a0, na, nb;
+};
+__device__ __forceinline__ MergeTile merge_tile(const Wave &W, uint64_t t, uint64_t run) {
+  MergeTile m;
+  m.qi = seg_of_large(W.qs, W.nq, t, true);
+  const QState &S = W.qs[m.qi];
+  const uint64_t n = S.out_rows;
+  m.base = S.lrg_row_base;
+  m.first = (t - S.lrg_tile_base) * kTileRows;
+  m.a0 = (m.first / (2 * run)) * 2 * run;
+  m.na = min(run, n - m.a0);
+  m.nb = n - m.a0 > run ? min(run, n - m.a0 - run) : 0;
+  return m;
+}
+
+// Merge-path split of every output tile: how many of its first outputs come
+// from the left run (stable: the left run wins ties).  One thread per tile.
+__global__ void k_merge_split(Wave W, const uint32_t *perm, const uint64_t *key, uint64_t run) {
+  const uint64_t ntiles = W.ctrl->len[7];
+  for (uint64_t t = gtid(); t < ntiles; t += gthreads()) {
+    const MergeTile m = merge_tile(W, t, run);
+    const uint64_t o = m.first - m.a0;
+    if (m.nb == 0) {
+      W.msplit[t] = o;
+      continue;
+    }
+    const DQuery &Q = W.dq[m.qi];
+    const QState &S = W.qs[m.qi];
+    const uint64_t A = m.base + m.a0, B = A + m.na;
+    uint64_t lo = o > m.nb ? o - m.nb : 0, hi = min(o, m.na);
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1, j = o - 1 - mid;
+      if (kr_le(W, Q, S, key[A + mid], perm[A + mid], key[B + j], perm[B + j])) lo = mid + 1; else hi = mid;
+    }
+    W.msplit[t] = lo;
+  }
+}
+
+// One merge pass: runs of `run` (>= kTileRows) rows become runs of 2*run.
+// One block per output tile: the tile's slices of both runs (bounded by the
+// splits of this tile and the next) are staged in shared memory with their
+// keys; each thread places four outputs after a short search in the slices.
+__global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout,
+                                                     uint64_t *kout, uint64_t run) {
+  __shared__ uint64_t sk[kTileRows];
+  __shared__ uint32_t si[kTileRows];
+  const uint64_t ntiles = W.ctrl->len[7];
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const MergeTile m = merge_tile(W, t, run);
+    const uint64_t n = m.na + m.nb, o0 = m.first - m.a0, o1 = min(o0 + kTileRows, n);
+    if (m.nb == 0) {
+      for (uint64_t i = m.base + m.first + threadIdx.x; i < m.base + m.a0 + o1; i += blockDim.x) {
+        pout[i] = pin[i];
+        kout[i] = kin[i];
+      }
       continue;  // block-uniform
     }
-    const uint32_t *A = in + base + a0, *B = A + na;
-    if (threadIdx.x < 2) {  // diagonal searches for the tile's two ends
-      const uint64_t o = threadIdx.x == 0 ? o0 : o1;
-      uint64_t lo = o > nb ? o - nb : 0, hi = min(o, na);
-      while (lo < hi) {
-        const uint64_t mid = (lo + hi) >> 1;
-        const uint32_t ra = A[mid], rb = B[o - 1 - mid];
-        if (kr_le(W, Q, S, row_key2(W, Q, S, ra), ra, row_key2(W, Q, S, rb), rb)) lo = mid + 1; else hi = mid;
-      }
-      bounds[threadIdx.x * 2] = lo;
-      bounds[threadIdx.x * 2 + 1] = o - lo;
+    const DQuery &Q = W.dq[m.qi];
+    const QState &S = W.qs[m.qi];
+    const uint64_t ab = W.msplit[t], bb = o0 - ab;
+    const uint64_t ae = o1 == n ? m.na : W.msplit[t + 1], be = o1 - ae;
+    const uint32_t la = (uint32_t)(ae - ab), lb = (uint32_t)(be - bb), total = la + lb;
+    const uint64_t A = m.base + m.a0 + ab, B = m.base + m.a0 + m.na + bb;
+    for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+      const uint64_t src = i < la ? A + i : B + (i - la);
+      sk[i] = kin[src];
+      si[i] = pin[src];
     }
     __syncthreads();
-    const uint64_t ab = bounds[0], bb = bounds[1], ae = bounds[2], be = bounds[3];
-    const uint32_t la = (uint32_t)(ae - ab), lb = (uint32_t)(be - bb);
-    for (uint32_t i = threadIdx.x; i < la + lb; i += blockDim.x) {
-      const uint32_t r = i < la ? A[ab + i] : B[bb + i - la];
-      sidx[i] = r;
-      skey[i] = row_key2(W, Q, S, r);
-    }
-    __syncthreads();
-    const uint32_t total = la + lb;  // == o1 - o0
     for (uint32_t p0 = threadIdx.x * 4; p0 < total; p0 += blockDim.x * 4) {
-      // merge-path search inside the staged slices for output p0
       uint32_t lo = p0 > lb ? p0 - lb : 0, hi = min(p0, la);
       while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (kr_le(W, Q, S, skey[mid], sidx[mid], skey[la + p0 - 1 - mid], sidx[la + p0 - 1 - mid])) lo = mid + 1;
-        else hi = mid;
+        const uint32_t mid = (lo + hi) >> 1, j = la + p0 - 1 - mid;
+        if (kr_le(W, Q, S, sk[mid], si[mid], sk[j], si[j])) lo = mid + 1; else hi = mid;
       }
       uint32_t ia = lo, ib = p0 - lo;
       for (uint32_t p = p0; p < min(p0 + 4, total); ++p) {
         bool take_a;
         if (ib >= lb) take_a = true;
         else if (ia >= la) take_a = false;
-        else take_a = kr_le(W, Q, S, skey[ia], sidx[ia], skey[la + ib], sidx[la + ib]);
-        out[base + first + p] = take_a ? sidx[ia++] : sidx[la + ib++];
+        else take_a = kr_le(W, Q, S, sk[ia], si[ia], sk[la + ib], si[la + ib]);
+        const uint32_t src = take_a ? ia++ : la + ib++;
+        pout[m.base + m.first + p] = si[src];
+        kout[m.base + m.first + p] = sk[src];
       }
     }
     __syncthreads();
@@ -1603,17 +1662,13 @@ void launch_small_sort(const Wave &W, cudaStream_t s, int sms) {
   const unsigned g = W.nq < (uint32_t)sms * 2 ? (W.nq ? W.nq : 1) : (unsigned)sms * 2;
   k_small_sort<<<g, 256, bytes, s>>>(W);
 }
-void launch_tile_sort(const Wave &W, uint32_t *perm, cudaStream_t s, int sms) {
-  static bool attr = false;
-  const int bytes = (int)(4 * (kTileRows * kMaxK + kTileRows));
-  if (!attr) {
-    cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    attr = true;
-  }
-  k_tile_sort<<<persistent_grid(k_tile_sort, sms, 256, bytes), 256, bytes, s>>>(W, perm);
+void launch_tile_sort(const Wave &W, uint32_t *perm, uint64_t *keys, cudaStream_t s, int sms) {
+  k_tile_sort<<<persistent_grid(k_tile_sort, sms, 256), 256, 0, s>>>(W, perm, keys);
 }
-void launch_merge_pass(const Wave &W, const uint32_t *in, uint32_t *out, uint64_t run, cudaStream_t s, int sms) {
-  k_merge_tiles<<<persistent_grid(k_merge_tiles, sms, 256), 256, 0, s>>>(W, in, out, run);
+void launch_merge_pass(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+                       uint64_t run, cudaStream_t s, int sms) {
+  k_merge_split<<<persistent_grid(k_merge_split, sms), kThreads, 0, s>>>(W, pin, kin, run);
+  k_merge_tiles<<<persistent_grid(k_merge_tiles, sms, 256), 256, 0, s>>>(W, pin, kin, pout, kout, run);
 }
 void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms) {
   k_gather<<<persistent_grid(k_gather, sms), kThreads, 0, s>>>(W, perm);
