@@ -110,6 +110,37 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def kernel_section_sha(kind):
+    """Hash of the source of one kernel kind: the shared device helpers at the
+    top of gs_kernels.cu (before the first banner) plus the text between its
+    '// ====... <kind>' banner and the next one.  A stored DRAM-traffic figure
+    is used only while this still matches."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1807_08804_gb300", "csrc", "gs_kernels.cu")).read()
+    banner = "// " + "=" * 60 + " "
+    i = src.find(banner + kind + "\n")
+    if i < 0:
+        return None
+    j = src.find(banner, i + len(banner))
+    head = src[:src.find(banner)]
+    return hashlib.sha256((head + src[i:j if j > 0 else len(src)]).encode()).hexdigest()[:16]
+
+
+def stored_traffic(kind, workload):
+    """DRAM bytes per launch of `kind` on `workload` from a committed ncu
+    summary (a 'traffic-record:' line under profiles/), or None when there
+    is none or the kernel's source changed since the capture."""
+    import glob
+    import re
+    sha = kernel_section_sha(kind)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = re.match(r"traffic-record: kind=(\S+) workload=(\S+) bytes_per_launch=(\d+) section_sha=(\S+)", line)
+            if m and m.group(1) == kind and m.group(2) == workload and m.group(4) == sha:
+                return int(m.group(3))
+    return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -214,6 +245,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of arrivals per serving rate (0 = skip)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--tune-cache", default=os.path.join(ROOT, "paper_1807_08804_gb300", "_build", "tune_cache.txt"),
+                    help="autotuner cache file: a choice made once for this graph, GPU and load is reused")
     ap.add_argument("--mode", default=None, choices=["enumerate", "count"],
                     help="enumerate rows (default) or count only (default for stress-16m)")
     args = ap.parse_args()
@@ -236,7 +269,10 @@ def main():
     gmode = gs.GS_COUNT_ONLY if mode == "count" else gs.GS_ENUMERATE
     cap = 0 if mode == "count" else w.cap
     dg = gs.DeviceGraph(g)
-    tuned = gs.tune(dg, qs, cap=cap, mode=gmode) if not args.no_tune else None  # untimed
+    tuned = None
+    if not args.no_tune:  # untimed
+        os.makedirs(os.path.dirname(os.path.abspath(args.tune_cache)), exist_ok=True)
+        tuned = gs.tune(dg, qs, cap=cap, mode=gmode, cache_path=args.tune_cache)
     # A dedicated stream: the library launches on it and the CUDA events are
     # recorded on it (the legacy default stream would not order with it).
     stream = torch.cuda.Stream(device=dev)
@@ -335,7 +371,7 @@ def main():
     if dom:
         achieved = kinds[dom]["bytes"] / (kinds[dom]["ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": stored_traffic(dom, w.name),
                 "bytes_per_launch": kinds[dom]["bytes"] / kinds[dom]["launches"],
                 "ms_per_launch": kinds[dom]["ms"] / kinds[dom]["launches"]}
 

@@ -366,6 +366,12 @@ def tune(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, cache_path: s
             "configs_tried": t.configs_tried}
 
 
+def tune_set(dg: DeviceGraph, group: int = 0, refine_rounds: int = 0) -> None:
+    """Set lanes per work item (4, 8, 16 or 32; 0 = default) and refinement
+    rounds (0 = default) for batches created on the graph afterwards."""
+    _check(lib().gs_tune_set(dg._h, group, refine_rounds))
+
+
 def inspect_candidates(dg: DeviceGraph, q, stage=GS_STAGE_FIXPOINT) -> list[np.ndarray]:
     pack = _QueryPack([q])
     k = len(q.vtype)

@@ -245,11 +245,12 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   }
   A(W.msplit, s.out_rows / kTileRows + W.nq + 1);
   uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * cps, (uint64_t)W.nqe, s.ec_items, W.row_cap}));
-  tmpw = std::max(tmpw, radix_tmp_words(s.out_rows));
   A(b->scan_tmp, tmpw);
+  b->scan_tmp_words = tmpw;
   A(b->type_count, G.T);
 #undef A
   GS_CUDA(cudaMemsetAsync(W.bm, 0, sizeof(uint32_t) * (uint64_t)W.nqv * W.slot_words, b->stream));
+  GS_CUDA(cudaMemsetAsync(b->scan_tmp, 0, sizeof(uint64_t) * b->scan_tmp_words, b->stream));
   GS_CUDA(cudaMemsetAsync(W.ctrl, 0, sizeof(Ctrl), b->stream));
   GS_CUDA(cudaMemsetAsync(W.dq, 0, sizeof(DQuery) * (W.nq + 1), b->stream));
   const uint64_t lens[3] = {(uint64_t)W.nq * cps, (uint64_t)W.nqv * cps, (uint64_t)W.nqe};
@@ -840,8 +841,10 @@ gs_status grow_pools(gs_batch *b) {
   if (changed) {
     const uint64_t cps = W.G.nchunks;  // chunks per set: one candidate count per chunk
     uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * cps, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap}));
-    tmpw = std::max(tmpw, radix_tmp_words(W.out_rows_cap));
-    regrow(b, &b->scan_tmp, tmpw);
+    if (regrow(b, &b->scan_tmp, tmpw) == GS_OK) {
+      b->scan_tmp_words = tmpw;
+      GS_CUDA(cudaMemsetAsync(b->scan_tmp, 0, sizeof(uint64_t) * tmpw, b->stream));
+    }
     ::drop_graphs(b);
     b->regrows++;
   }
@@ -861,8 +864,11 @@ gs_status batch_finish(gs_batch *b) {
     GS_CUDA(cudaMemcpyAsync(b->status.data(), b->W.bo.status, 4ull * n, cudaMemcpyDeviceToHost, b->stream));
   }
   uint64_t top = 0;
+  uint32_t scan_err = 0;
   GS_CUDA(cudaMemcpyAsync(&top, &b->W.ctrl->store_top, 8, cudaMemcpyDeviceToHost, b->stream));
+  GS_CUDA(cudaMemcpyAsync(&scan_err, scan_error_word(b->scan_tmp), 4, cudaMemcpyDeviceToHost, b->stream));
   GS_CUDA(cudaStreamSynchronize(b->stream));
+  if (scan_err) return fail(GS_ERR_CUDA, "a prefix scan gave up waiting on a predecessor tile; results are invalid");
   b->rows.resize(top);
   b->d2h_bytes += 36ull * n + 8 + 4ull * top;
   if (top) {

@@ -118,7 +118,8 @@ struct Fallback {
   uint64_t *bounds = nullptr;
   uint64_t bounds_cap = 1 << 20;
   uint64_t *d_n = nullptr;
-  uint64_t *tmp = nullptr;
+  uint64_t *tmp = nullptr;   // radix sort scratch (zeroed when allocated)
+  uint64_t *stmp = nullptr;  // scan scratch (zeroed when allocated)
   // rows of queries with more than cap embeddings
   uint32_t *top = nullptr, *top2 = nullptr, *perm[2] = {}, *key[2] = {};
   uint64_t top_rows = 0;  // capacity in rows
@@ -175,7 +176,11 @@ static gs_status fallback_ctx(gs_graph *g, Fallback **out) {
   if (st == GS_OK) st = falloc(f, &f->cnt, f->depth_rows);
   if (st == GS_OK) st = falloc(f, &f->bounds, f->bounds_cap + 1);
   if (st == GS_OK) st = falloc(f, &f->d_n, 1);
-  if (st == GS_OK) st = falloc(f, &f->tmp, std::max(scan_tmp_words(f->depth_rows), radix_tmp_words(1)));
+  if (st == GS_OK) st = falloc(f, &f->tmp, radix_tmp_words(1));
+  if (st == GS_OK) st = falloc(f, &f->stmp, scan_tmp_words(f->depth_rows));
+  if (st == GS_OK && (cudaMemset(f->tmp, 0, sizeof(uint64_t) * radix_tmp_words(1)) != cudaSuccess ||
+                      cudaMemset(f->stmp, 0, sizeof(uint64_t) * scan_tmp_words(f->depth_rows)) != cudaSuccess))
+    st = fail(GS_ERR_CUDA, "cudaMemset (fallback scratch)");
   if (st != GS_OK) {
     delete f;
     return st;
@@ -203,8 +208,10 @@ static gs_status ensure_top(Fallback *f, uint64_t rows, uint32_t k) {
   if (st != GS_OK) return st;
   // radix scratch for `rows` items
   void *t = nullptr;
-  cudaError_t e = cudaMalloc(&t, sizeof(uint64_t) * std::max(radix_tmp_words(rows), scan_tmp_words(f->depth_rows)));
+  cudaError_t e = cudaMalloc(&t, sizeof(uint64_t) * radix_tmp_words(rows));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (fallback sort scratch)");
+  e = cudaMemset(t, 0, sizeof(uint64_t) * radix_tmp_words(rows));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset (fallback sort scratch)");
   f->allocs.erase(std::remove(f->allocs.begin(), f->allocs.end(), (void *)f->tmp), f->allocs.end());
   cudaFree(f->tmp);
   f->tmp = static_cast<uint64_t *>(t);
@@ -281,7 +288,7 @@ gs_status expand(FbRun &R, uint32_t s, uint64_t n) {
   W.row_scan = f->rscan[s];
   set_state(R, n, 0, 0, SrcRows{0, 0, 0}, n, 0);
   launch_join_count(W, s, R.grp, R.s, R.sms);
-  scan_u32(f->cnt, f->rscan[s], &W.ctrl->len[3], f->depth_rows, f->tmp, R.s, R.sms);
+  scan_u32(f->cnt, f->rscan[s], &W.ctrl->len[3], f->depth_rows, f->stmp, R.s, R.sms);
   uint64_t T = 0;
   gs_status st = d2h1(&T, f->rscan[s] + n, R.s);
   if (st != GS_OK) return st;

@@ -149,7 +149,8 @@ struct DevBuf {
 // Build one direction: given (row, packed) pairs, sort by (row, packed),
 // drop repeats, and produce off[V+1], adj[n'].  Returns kept count.
 static gs_status build_direction(uint32_t V, uint32_t R, uint64_t n, uint32_t *key, uint32_t *val, uint32_t *k1,
-                                 uint32_t *v1, uint64_t *scan_buf, uint64_t *tmp, uint64_t *d_n, cudaStream_t s,
+                                 uint32_t *v1, uint64_t *scan_buf, uint64_t *tmp, uint64_t *stmp, uint64_t *d_n,
+                                 cudaStream_t s,
                                  int sms, uint64_t **off_out, uint32_t **adj_out, uint32_t **row_out, uint64_t *kept) {
   // (1) by packed key (carry row), (2) stably by row (carry packed)
   int cur = radix_sort_pairs(key, val, k1, v1, d_n, n, 0, kNbrBits + bits_for(R ? R - 1 : 0), tmp, s, sms);
@@ -161,7 +162,7 @@ static gs_status build_direction(uint32_t V, uint32_t R, uint64_t n, uint32_t *k
   // de-duplicate
   uint32_t *keep = frow;  // reuse as flags
   k_mark_first<<<blocks_for(n), kT, 0, s>>>(n, row, packed, keep);
-  scan_u32(keep, scan_buf, d_n, n, tmp, s, sms);
+  scan_u32(keep, scan_buf, d_n, n, stmp, s, sms);
   uint64_t total = 0;
   GS_CUDA(cudaMemcpyAsync(&total, scan_buf + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaStreamSynchronize(s));
@@ -178,7 +179,7 @@ static gs_status build_direction(uint32_t V, uint32_t R, uint64_t n, uint32_t *k
   GS_CUDA(cudaMalloc(&off, sizeof(uint64_t) * (V + 1)));
   uint64_t nv = V;
   GS_CUDA(cudaMemcpyAsync(d_n, &nv, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
-  scan_u32(cnt, off, d_n, V, tmp, s, sms);
+  scan_u32(cnt, off, d_n, V, stmp, s, sms);
   GS_CUDA(cudaStreamSynchronize(s));
   GS_CUDA(cudaMemcpyAsync(d_n, &n, sizeof(uint64_t), cudaMemcpyHostToDevice, s));  // restore
   *off_out = off;
@@ -211,7 +212,7 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   const uint32_t T = desc->num_types, R = desc->num_rels;
   const uint64_t En = E ? E : 1;
 
-  DevBuf ro, col, rel, vt, k0, v0, k1, v1, scanb, tmpb, dn, err;
+  DevBuf ro, col, rel, vt, k0, v0, k1, v1, scanb, tmpb, stmpb, dn, err;
   GS_CUDA(cudaMalloc(&ro.p, sizeof(uint64_t) * (V + 1)));
   GS_CUDA(cudaMalloc(&col.p, sizeof(uint32_t) * En));
   GS_CUDA(cudaMalloc(&rel.p, sizeof(uint32_t) * En));
@@ -243,7 +244,10 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   GS_CUDA(cudaMalloc(&scanb.p, sizeof(uint64_t) * (nmax + 1)));
   uint64_t tw = radix_tmp_words(nmax);
   uint64_t sw = scan_tmp_words(nmax);
-  GS_CUDA(cudaMalloc(&tmpb.p, sizeof(uint64_t) * (tw > sw ? tw : sw)));
+  GS_CUDA(cudaMalloc(&tmpb.p, sizeof(uint64_t) * tw));   // radix sort scratch
+  GS_CUDA(cudaMalloc(&stmpb.p, sizeof(uint64_t) * sw));  // scan scratch
+  GS_CUDA(cudaMemsetAsync(tmpb.p, 0, sizeof(uint64_t) * tw, s));
+  GS_CUDA(cudaMemsetAsync(stmpb.p, 0, sizeof(uint64_t) * sw, s));
   GS_CUDA(cudaMalloc(&dn.p, sizeof(uint64_t)));
   GS_CUDA(cudaMemcpyAsync(dn.p, &E, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
 
@@ -261,7 +265,7 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   uint32_t *src_rows = nullptr;
   uint64_t kept = 0;
   gs_status st = build_direction(V, R, E, k0.as<uint32_t>(), v0.as<uint32_t>(), k1.as<uint32_t>(), v1.as<uint32_t>(),
-                                 scanb.as<uint64_t>(), tmpb.as<uint64_t>(), dn.as<uint64_t>(), s, sms, &g->off_out,
+                                 scanb.as<uint64_t>(), tmpb.as<uint64_t>(), stmpb.as<uint64_t>(), dn.as<uint64_t>(), s, sms, &g->off_out,
                                  &g->adj_out, &src_rows, &kept);
   if (st != GS_OK) return cleanup(st);
   // incoming direction from the kept triples
@@ -270,7 +274,7 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   uint32_t *dst_rows = nullptr;
   uint64_t kept_in = 0;
   st = build_direction(V, R, kept, k0.as<uint32_t>(), v0.as<uint32_t>(), k1.as<uint32_t>(), v1.as<uint32_t>(),
-                       scanb.as<uint64_t>(), tmpb.as<uint64_t>(), dn.as<uint64_t>(), s, sms, &g->off_in, &g->adj_in,
+                       scanb.as<uint64_t>(), tmpb.as<uint64_t>(), stmpb.as<uint64_t>(), dn.as<uint64_t>(), s, sms, &g->off_in, &g->adj_in,
                        &dst_rows, &kept_in);
   cudaFree(src_rows);
   cudaFree(dst_rows);

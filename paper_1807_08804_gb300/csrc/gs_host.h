@@ -71,7 +71,8 @@ struct gs_batch {
   Wave W{};
   DQuery *all_dq = nullptr;
   WaveDesc *dwaves = nullptr;
-  uint64_t *scan_tmp = nullptr;
+  uint64_t *scan_tmp = nullptr;  // scan scratch: zeroed when allocated, used by scans only
+  uint64_t scan_tmp_words = 0;
   uint32_t *type_count = nullptr;
   std::map<int, cudaGraphExec_t> execs;
   // stats

@@ -14,30 +14,50 @@ namespace gs {
 
 namespace {
 
-constexpr int kScanThreads = 256;
-constexpr uint64_t kScanMaxTiles = 8192;
-
-// Tile of the scan: 1,024 items while that gives at most 8,192 tiles (short
-// serial chains for the small scans of the pipeline), larger beyond.  Every
-// kernel of one scan derives it from the same n.
-__device__ __forceinline__ uint64_t scan_rounds(uint64_t n) {
-  uint64_t r = (n + kScanThreads * kScanMaxTiles - 1) / (kScanThreads * kScanMaxTiles);
-  return r < 4 ? 4 : r;
-}
-
 constexpr int kRadixThreads = 256;
 constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kRadixRounds = 4;
 constexpr uint64_t kRadixTile = kRadixThreads * kRadixRounds;  // 1024
 constexpr int kRadixBins = 256;
 
-// Exclusive scan of one value per thread over a 256-thread block.
-__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *total, uint64_t *smem) {
+// ------------------------------------------------------------ scan
+// Single-pass exclusive scan with decoupled look-back (Merrill and Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016).
+// Blocks claim tiles in order from an atomic counter; each publishes its
+// tile's aggregate, then sums the aggregates of the tiles before it (a warp
+// reads 32 predecessors at a time) until it meets one that has published
+// its inclusive prefix, and publishes its own.  A block only waits on tiles
+// claimed before its own, by blocks that are already running, so the waits
+// end; each is bounded all the same and records an error when the bound is
+// hit.  Descriptors carry the scan's epoch, so the scratch needs zeroing
+// only once, when it is allocated; the last block to finish resets the tile
+// counter and advances the epoch for the next scan on the same scratch.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr uint64_t kScanTile = (uint64_t)kScanThreads * kScanItems;  // 2048
+constexpr uint32_t kLookbackLimit = 1u << 22;
+constexpr uint32_t kEpochMask = (1u << 30) - 1;  // epochs wrap after 2^30 scans
+
+struct ScanState {  // the first 16 bytes of the scratch (the error word is read by scan_error_word)
+  uint32_t tiles;  // next tile to claim
+  uint32_t done;   // blocks finished
+  uint32_t epoch;  // scans completed on this scratch
+  uint32_t err;    // a look-back wait hit its bound
+};
+struct __align__(32) ScanDesc {
+  uint64_t agg;   // the tile's total
+  uint64_t incl;  // prefix through the tile
+  uint32_t flag;  // (epoch << 2) | 1 (aggregate) or 2 (inclusive)
+  uint32_t pad[3];
+};
+static_assert(sizeof(ScanState) == 16 && sizeof(ScanDesc) == 32, "scan scratch layout");
+
+__device__ __forceinline__ uint64_t block_scan_excl(uint64_t v, uint64_t *total, uint64_t *smem) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    uint64_t y = __shfl_up_sync(kFull, x, o);
+    const uint64_t y = __shfl_up_sync(kFull, x, o);
     if (lane >= o) x += y;
   }
   if (lane == 31) smem[warp] = x;
@@ -46,90 +66,152 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *t
     uint64_t w = lane < kScanThreads / 32 ? smem[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint64_t y = __shfl_up_sync(kFull, w, o);
+      const uint64_t y = __shfl_up_sync(kFull, w, o);
       if (lane >= o) w += y;
     }
-    if (lane < kScanThreads / 32) smem[lane] = w;  // inclusive warp totals
+    if (lane < kScanThreads / 32) smem[lane] = w;
   }
   __syncthreads();
-  uint64_t before = warp ? smem[warp - 1] : 0;
+  const uint64_t before = warp ? smem[warp - 1] : 0;
   *total = smem[kScanThreads / 32 - 1];
   __syncthreads();
   return before + x - v;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T *in, const uint64_t *d_n, uint64_t *tile_sums) {
+__global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64_t *d_n, uint64_t *out, ScanState *st,
+                                                        ScanDesc *desc) {
+  __shared__ uint64_t vals[kScanTile];
   __shared__ uint64_t red[kScanThreads / 32];
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_prefix;
   const uint64_t n = *d_n;
-  const uint64_t rounds = scan_rounds(n), tile = rounds * kScanThreads;
-  const uint64_t ntiles = (n + tile - 1) / tile;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    uint64_t s = 0;
-    const uint64_t base = t * tile;
-#pragma unroll 4
-    for (uint64_t j = 0; j < rounds; ++j) {
-      uint64_t i = base + (uint64_t)j * kScanThreads + threadIdx.x;
-      if (i < n) s += (uint64_t)in[i];
-    }
+  const uint64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  const uint32_t epoch = *reinterpret_cast<volatile uint32_t *>(&st->epoch);
+  const int lane = threadIdx.x & 31;
+  if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&st->tiles, 1u);
+    __syncthreads();
+    const uint64_t t = s_tile;
+    if (t >= ntiles) break;  // block-uniform
+    const uint64_t base = t * kScanTile;
+    // striped loads (coalesced), then each thread owns 8 consecutive items
 #pragma unroll
-    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(kFull, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    for (int j = 0; j < kScanItems; ++j) {
+      const uint64_t i = base + (uint64_t)j * kScanThreads + threadIdx.x;
+      vals[j * kScanThreads + threadIdx.x] = i < n ? (uint64_t)in[i] : 0;
+    }
     __syncthreads();
+    uint64_t loc[kScanItems], sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+      loc[j] = sum;
+      sum += vals[threadIdx.x * kScanItems + j];
+    }
+    uint64_t agg;
+    const uint64_t ex = block_scan_excl(sum, &agg, red);
+    const uint32_t tag = (epoch & kEpochMask) << 2;
     if (threadIdx.x == 0) {
-      uint64_t tot = 0;
-      for (int w = 0; w < kScanThreads / 32; ++w) tot += red[w];
-      tile_sums[t] = tot;
+      ScanDesc &d = desc[t];
+      if (t == 0) {
+        __stcg(&d.incl, agg);
+        __threadfence();
+        __stcg(&d.flag, tag | 2u);
+      } else {
+        __stcg(&d.agg, agg);
+        __threadfence();
+        __stcg(&d.flag, tag | 1u);
+      }
+    }
+    if (threadIdx.x < 32) {  // look-back
+      uint64_t prefix = 0;
+      if (t > 0) {
+        int64_t pos = (int64_t)t - 1;
+        uint32_t spins = 0;
+        for (;;) {
+          const int64_t p = pos - lane;
+          uint32_t status = 2;  // before tile 0: an inclusive prefix of 0
+          if (p >= 0) {
+            const uint32_t f = __ldcg(&desc[p].flag);
+            status = (f & ~3u) == tag ? (f & 3u) : 0u;
+          }
+          const uint32_t incl_mask = __ballot_sync(kFull, status == 2);
+          const uint32_t zero_mask = __ballot_sync(kFull, status == 0);
+          const int first = incl_mask ? __ffs(incl_mask) - 1 : 32;
+          const uint32_t need = first >= 31 ? kFull : ((2u << first) - 1);
+          if ((zero_mask & need) && ++spins < kLookbackLimit) continue;
+          if (zero_mask & need) {  // bound hit: record it and stop waiting
+            if (lane == 0) atomicExch(&st->err, 1u);
+          }
+          __threadfence();
+          uint64_t v = 0;
+          if (p >= 0 && status != 0 && lane <= first) v = lane < first ? __ldcg(&desc[p].agg) : __ldcg(&desc[p].incl);
+#pragma unroll
+          for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+          prefix += v;
+          if (first < 32 || (zero_mask & need)) break;
+          pos -= 32;
+        }
+        if (lane == 0) {
+          ScanDesc &d = desc[t];
+          __stcg(&d.incl, prefix + agg);
+          __threadfence();
+          __stcg(&d.flag, tag | 2u);
+        }
+      }
+      if (lane == 0) s_prefix = prefix;
     }
     __syncthreads();
+    const uint64_t pre = s_prefix + ex;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) vals[threadIdx.x * kScanItems + j] = pre + loc[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+      const uint64_t i = base + (uint64_t)j * kScanThreads + threadIdx.x;
+      if (i < n) out[i] = vals[j * kScanThreads + threadIdx.x];
+    }
+    if (t == ntiles - 1 && threadIdx.x == 0) out[n] = s_prefix + agg;
+    __syncthreads();
   }
-}
-
-// One block: exclusive scan of the tile sums in place; out[n] = grand total.
-__global__ void __launch_bounds__(kScanThreads) k_scan_partials(uint64_t *tile_sums, const uint64_t *d_n, uint64_t *out) {
-  __shared__ uint64_t smem[kScanThreads / 32];
-  const uint64_t n = *d_n;
-  const uint64_t tile = scan_rounds(n) * kScanThreads;
-  const uint64_t ntiles = (n + tile - 1) / tile;
-  uint64_t carry = 0;
-  for (uint64_t base = 0; base < ntiles; base += kScanThreads) {
-    uint64_t i = base + threadIdx.x;
-    uint64_t v = i < ntiles ? tile_sums[i] : 0, tot;
-    uint64_t ex = block_exclusive_scan(v, &tot, smem);
-    if (i < ntiles) tile_sums[i] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) out[n] = carry;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const T *in, const uint64_t *d_n, const uint64_t *tile_sums,
-                                                             uint64_t *out) {
-  __shared__ uint64_t smem[kScanThreads / 32];
-  const uint64_t n = *d_n;
-  const uint64_t rounds = scan_rounds(n), tile = rounds * kScanThreads;
-  const uint64_t ntiles = (n + tile - 1) / tile;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    uint64_t carry = tile_sums[t];
-    const uint64_t base = t * tile;
-    for (uint64_t j = 0; j < rounds; ++j) {
-      uint64_t i = base + (uint64_t)j * kScanThreads + threadIdx.x;
-      uint64_t v = i < n ? (uint64_t)in[i] : 0, tot;
-      uint64_t ex = block_exclusive_scan(v, &tot, smem);
-      if (i < n) out[i] = carry + ex;
-      carry += tot;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&st->done, 1u) == gridDim.x - 1) {  // every block has stopped claiming tiles
+      st->tiles = 0;
+      st->done = 0;
+      st->epoch = (epoch + 1) & kEpochMask;
+      __threadfence();
     }
   }
+}
+
+int scan_resident(const void *fn) {
+  static int cached[2] = {0, 0};
+  const int slot = fn == (const void *)k_scan<uint32_t> ? 0 : 1;
+  if (!cached[slot]) {
+    int r = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, kScanThreads, 0) != cudaSuccess || r < 1) {
+      cudaGetLastError();
+      r = 1;
+    }
+    cached[slot] = r;
+  }
+  return cached[slot];
 }
 
 template <typename T>
 void scan_impl(const T *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp, cudaStream_t s,
                int num_sms) {
-  uint64_t tiles = std::min<uint64_t>((max_n + 1023) / 1024, kScanMaxTiles);
-  unsigned grid = (unsigned)(tiles < (uint64_t)num_sms * 8 ? (tiles ? tiles : 1) : (uint64_t)num_sms * 8);
-  k_scan_reduce<T><<<grid, kScanThreads, 0, s>>>(in, d_n, tmp);
-  k_scan_partials<<<1, kScanThreads, 0, s>>>(tmp, d_n, out);
-  k_scan_down<T><<<grid, kScanThreads, 0, s>>>(in, d_n, tmp, out);
+  const uint64_t tiles = std::max<uint64_t>((max_n + kScanTile - 1) / kScanTile, 1);
+  // at most two blocks per SM: every block claims one tile past the end and
+  // counts itself done with an atomic, so a small scan sized for a large
+  // max_n stays cheap; large scans loop over tiles
+  const uint64_t cap = (uint64_t)num_sms * std::min(2, scan_resident((const void *)k_scan<T>));
+  const unsigned grid = (unsigned)std::min(tiles, cap);
+  ScanState *st = reinterpret_cast<ScanState *>(tmp);
+  ScanDesc *desc = reinterpret_cast<ScanDesc *>(tmp + 4);
+  k_scan<T><<<grid, kScanThreads, 0, s>>>(in, d_n, out, st, desc);
 }
 
 // ------------------------------------------------------------ radix sort
@@ -211,7 +293,10 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const uint32_t 
 
 }  // namespace
 
-uint64_t scan_tmp_words(uint64_t max_n) { return std::min<uint64_t>((max_n + 1023) / 1024, kScanMaxTiles) + 1; }
+uint64_t scan_tmp_words(uint64_t max_n) {
+  const uint64_t tiles = std::max<uint64_t>((max_n + kScanTile - 1) / kScanTile, 1);
+  return 4 + 4 * tiles;  // state (padded to 32 bytes) + one 32-byte descriptor per tile
+}
 
 void scan_u32(const uint32_t *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp, cudaStream_t s,
               int num_sms) {

@@ -18,6 +18,8 @@ def main():
     ap.add_argument("--queries", type=int, default=0)
     ap.add_argument("--runs", type=int, default=1)
     ap.add_argument("--wave", type=int, default=0)
+    ap.add_argument("--group", type=int, default=0, help="lanes per work item (0 = library default)")
+    ap.add_argument("--rounds", type=int, default=0, help="refinement rounds (0 = library default)")
     a = ap.parse_args()
     import paper_1807_08804_gb300 as gs
     from paper_1807_08804_gb300 import inputs as I
@@ -25,6 +27,8 @@ def main():
     g = w.graph()
     qs = w.queries(g, a.queries or None)
     dg = gs.DeviceGraph(g)
+    if a.group or a.rounds:
+        gs.tune_set(dg, a.group, a.rounds)
     b = gs.Batch(dg, qs, cap=w.cap, wave_queries=a.wave)
     for _ in range(a.runs):
         b.run()
