@@ -655,9 +655,16 @@ gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_mat
     }
     b->own_stream = true;
   }
-  // waves: bounded by the candidate-bitmap budget
+  // waves: bounded by the candidate-bitmap budget, a quarter of the free
+  // device memory (at least 4 GB, at most 64 GB), so that on a large GPU a
+  // batch of thousands of queries runs as one wave
   const uint64_t slot_bytes = 4 * (((uint64_t)g->d.W0 + g->d.W1 + g->d.ipg + 31) / 32 * 32);
-  const uint64_t bm_budget = 24ull << 30;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = 0;
+  }
+  const uint64_t bm_budget = std::min<uint64_t>(std::max<uint64_t>(free_b / 4, 4ull << 30), 64ull << 30);
   uint64_t max_qv = std::max<uint64_t>(bm_budget / slot_bytes, kMaxK);
   uint32_t nq_s = wave_queries ? wave_queries : n;
   uint64_t tot_qv = 0, tot_qe = 0;

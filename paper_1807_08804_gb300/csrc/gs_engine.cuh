@@ -14,7 +14,6 @@ constexpr uint32_t kUnbound = 0xFFFFFFFFu;
 constexpr uint32_t kAny = 0xFFFFFFFFu;
 constexpr uint32_t kMaxRounds = 64;
 constexpr uint32_t kSmallRows = 2048;    // outputs sorted by one block in shared memory
-constexpr uint32_t kSmallWords = 24576;
 constexpr uint32_t kTileRows = 1024;     // rows per tile of the large-output merge sort
 
 // Per-query status.
@@ -136,9 +135,9 @@ struct Wave {
   uint32_t *bm;                     // [nqv][slot_words]
   uint64_t slot_words;
   // compaction
-  uint32_t *ccount;                 // [nqv * ipg]
-  uint64_t *cscan;                  // [nqv * ipg + 1]
-  uint64_t *ascan;                  // [nqv * ipg + 1] (refinement items)
+  uint32_t *ccount;                 // candidates per chunk [nqv * nchunks]
+  uint64_t *cscan;                  // [nqv * nchunks + 1]
+  uint64_t *ascan;                  // [nqv * nchunks + 1] (refinement items)
   // candidate lists
   uint32_t *tlist; uint64_t tlist_cap;   // exploration work list
   uint32_t *alist; uint64_t alist_cap;   // every set before refinement

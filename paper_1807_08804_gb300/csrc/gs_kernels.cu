@@ -1178,10 +1178,8 @@ __global__ void __launch_bounds__(kThreads) k_join_write(Wave W, uint32_t s) {
 }
 
 // Query-order layout of the sorted rows, and of the rows of queries whose
-// output is too large for the one-block sort (sorted by the radix path).
-__device__ __forceinline__ bool small_output(const DQuery &Q, const QState &S) {
-  return S.out_rows <= kSmallRows && S.out_rows * Q.k <= kSmallWords;
-}
+// output is too large for the one-block sort (sorted by the merge path).
+__device__ __forceinline__ bool small_output(const DQuery &, const QState &S) { return S.out_rows <= kSmallRows; }
 
 __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
   __shared__ uint64_t sm[4][32];
@@ -1234,55 +1232,6 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
     W.ctrl->len[6] = carry[2];
     W.ctrl->len[7] = carry[3];
     W.ctrl->fin_words = carry[1];
-  }
-}
-
-// One block sorts one query's rows in shared memory (bitonic network over
-// row indices, rows compared in query-vertex order) and writes them sorted.
-__device__ __forceinline__ bool row_less(const uint32_t *rows, uint32_t k, uint32_t n, uint32_t a, uint32_t b) {
-  if (a >= n) return false;
-  if (b >= n) return true;
-  const uint32_t *x = rows + a * k, *y = rows + b * k;
-  for (uint32_t u = 0; u < k; ++u)
-    if (x[u] != y[u]) return x[u] < y[u];
-  return false;
-}
-
-__global__ void __launch_bounds__(256) k_small_sort(Wave W) {
-  extern __shared__ uint32_t smem[];
-  uint32_t *rows = smem;                 // [kSmallWords]
-  uint32_t *idx = smem + kSmallWords;    // [kSmallRows]
-  for (uint32_t qi = blockIdx.x; qi < W.nq; qi += gridDim.x) {
-    const DQuery &Q = W.dq[qi];
-    const QState &S = W.qs[qi];
-    const uint32_t n = (uint32_t)S.out_rows, k = Q.k;
-    if (Q.status != QS_OK || n == 0 || !small_output(Q, S)) continue;
-    for (uint32_t t = threadIdx.x; t < n * k; t += blockDim.x) {
-      const uint32_t i = t / k, u = t % k;
-      rows[t] = W.out[S.out_word_base + (uint64_t)i * k + Q.pos[u]];
-    }
-    uint32_t np2 = 1;
-    while (np2 < n) np2 <<= 1;
-    for (uint32_t t = threadIdx.x; t < np2; t += blockDim.x) idx[t] = t;
-    __syncthreads();
-    for (uint32_t size = 2; size <= np2; size <<= 1) {
-      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-        for (uint32_t t = threadIdx.x; t < np2; t += blockDim.x) {
-          const uint32_t p = t ^ stride;
-          if (p > t) {
-            const bool up = (t & size) == 0;
-            const uint32_t a = idx[t], b = idx[p];
-            const bool swap = up ? row_less(rows, k, n, b, a) : row_less(rows, k, n, a, b);
-            if (swap) { idx[t] = b; idx[p] = a; }
-          }
-        }
-        __syncthreads();
-      }
-    }
-    uint32_t *dst = W.out_final + S.fin_word_base;
-    const uint32_t keep = (uint32_t)min((uint64_t)n, Q.cap);
-    for (uint32_t t = threadIdx.x; t < keep * k; t += blockDim.x) dst[t] = rows[idx[t / k] * k + t % k];
-    __syncthreads();
   }
 }
 
@@ -1339,6 +1288,57 @@ __device__ __forceinline__ bool kr_le(const Wave &W, const DQuery &Q, const QSta
                                       uint64_t kb, uint32_t rb) {
   if (ka != kb) return ka < kb;
   return out_row_le(W, Q, S, ra, rb);
+}
+
+// One block sorts one query's rows: packed 64-bit keys of the rows (see the
+// large-output sort below) and row indices in shared memory, bitonic
+// network, full rows compared on equal keys only; then the first `cap` rows
+// are written in query-vertex column order.
+__global__ void __launch_bounds__(256) k_small_sort(Wave W) {
+  __shared__ uint64_t key[kSmallRows];
+  __shared__ uint32_t idx[kSmallRows];
+  const uint32_t b = W.G.idbits;
+  for (uint32_t qi = blockIdx.x; qi < W.nq; qi += gridDim.x) {
+    const DQuery &Q = W.dq[qi];
+    const QState &S = W.qs[qi];
+    const uint32_t n = (uint32_t)S.out_rows, k = Q.k;
+    if (Q.status != QS_OK || n == 0 || !small_output(Q, S)) continue;
+    const uint32_t *rows = W.out + S.out_word_base;
+    const uint32_t r0 = (uint32_t)S.out_row_base;
+    uint32_t np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
+      idx[i] = i;
+      if (i < n) {
+        const uint32_t *x = rows + (uint64_t)i * k;
+        key[i] = pack_key(k, b, [&](uint32_t u) { return x[Q.pos[u]]; });
+      }
+    }
+    __syncthreads();
+    auto less = [&](uint32_t a, uint32_t c) {
+      if (a >= n) return false;
+      if (c >= n) return true;
+      if (key[a] != key[c]) return key[a] < key[c];
+      return !out_row_le(W, Q, S, r0 + c, r0 + a);
+    };
+    for (uint32_t size = 2; size <= np2; size <<= 1)
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t x = threadIdx.x; x < np2 / 2; x += blockDim.x) {
+          const uint32_t i = 2 * x - (x & (stride - 1)), p = i + stride;
+          const bool up = (i & size) == 0;
+          const uint32_t a = idx[i], c = idx[p];
+          if (up ? less(c, a) : less(a, c)) { idx[i] = c; idx[p] = a; }
+        }
+        __syncthreads();
+      }
+    uint32_t *dst = W.out_final + S.fin_word_base;
+    const uint32_t keep = (uint32_t)min((uint64_t)n, Q.cap);
+    for (uint32_t t = threadIdx.x; t < keep * k; t += blockDim.x) {
+      const uint32_t i = t / k, u = t % k;
+      dst[t] = rows[(uint64_t)idx[i] * k + Q.pos[u]];
+    }
+    __syncthreads();
+  }
 }
 
 // Tile sort: keys (and row indices) in shared memory, bitonic network;
@@ -1653,14 +1653,8 @@ void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, i
 }
 void launch_final_bases(const Wave &W, cudaStream_t s) { k_final_bases<<<1, 1024, 0, s>>>(W); }
 void launch_small_sort(const Wave &W, cudaStream_t s, int sms) {
-  static bool attr = false;
-  const int bytes = (int)(4 * (kSmallWords + kSmallRows));
-  if (!attr) {
-    cudaFuncSetAttribute(k_small_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    attr = true;
-  }
-  const unsigned g = W.nq < (uint32_t)sms * 2 ? (W.nq ? W.nq : 1) : (unsigned)sms * 2;
-  k_small_sort<<<g, 256, bytes, s>>>(W);
+  const unsigned cap = persistent_grid(k_small_sort, sms, 256);
+  k_small_sort<<<W.nq < cap ? (W.nq ? W.nq : 1) : cap, 256, 0, s>>>(W);
 }
 void launch_tile_sort(const Wave &W, uint32_t *perm, uint64_t *keys, cudaStream_t s, int sms) {
   k_tile_sort<<<persistent_grid(k_tile_sort, sms, 256), 256, 0, s>>>(W, perm, keys);
