@@ -65,8 +65,19 @@ struct DQuery {
   uint8_t join[kMaxK];              // join order
   uint8_t pos[kMaxK];               // position of u in the join order
   uint8_t from_src[kMaxM];          // edge-table orientation (1: keyed by esrc)
+  uint32_t xinc[2 * kMaxM];         // incident edges packed by the plan (xinc_pack), same order as inc_edge
   uint32_t status;
 };
+
+// Packed incident edge: bit 0 direction (0: u is the source), bits 1-8
+// relation, 9-12 the other endpoint, 13-14 its role when u is explored.
+__host__ __device__ __forceinline__ uint32_t xinc_pack(uint32_t dir, uint32_t rel, uint32_t w, uint32_t role) {
+  return dir | (rel << 1) | (w << 9) | (role << 13);
+}
+__host__ __device__ __forceinline__ int xinc_dir(uint32_t x) { return (int)(x & 1u); }
+__host__ __device__ __forceinline__ uint32_t xinc_rel(uint32_t x) { return (x >> 1) & 0xFFu; }
+__host__ __device__ __forceinline__ uint32_t xinc_w(uint32_t x) { return (x >> 9) & 0xFu; }
+__host__ __device__ __forceinline__ uint32_t xinc_role(uint32_t x) { return x >> 13; }
 
 // Per-query join bookkeeping and results (slot arrays).
 struct QState {

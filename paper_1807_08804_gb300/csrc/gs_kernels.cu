@@ -87,6 +87,41 @@ __device__ __forceinline__ void rel_range(const cg::thread_block_tile<G> &t, con
   hi = tile_lower_bound<G>(t, a, lo, e, (rel + 1) << kNbrBits);
 }
 
+// The same run, with a fast path for a row that fits the tile: one load per
+// lane (lane r holds entry base + r in x, all ones past the row) and two
+// ballots.  Returns true on the fast path, where the run's entries can be
+// taken from the lanes by shuffles instead of reloads.
+template <int G>
+__device__ __forceinline__ bool rel_run(const cg::thread_block_tile<G> &t, const DevGraph &Gr, int dir, uint32_t v,
+                                        uint32_t rel, uint64_t &base, uint64_t &lo, uint64_t &hi, uint32_t &x) {
+  const uint32_t *a = Gr.adj[dir];
+  const uint64_t b = Gr.off[dir][v], e = Gr.off[dir][v + 1];
+  base = b;
+  if (e - b <= G) {
+    const uint32_t r = t.thread_rank();
+    x = r < e - b ? a[b + r] : 0xFFFFFFFFu;
+    lo = b + __popc(t.ballot(x < (rel << kNbrBits)));
+    hi = b + __popc(t.ballot(x < ((rel + 1) << kNbrBits)));
+    return true;
+  }
+  x = 0xFFFFFFFFu;
+  lo = tile_lower_bound<G>(t, a, b, e, rel << kNbrBits);
+  hi = tile_lower_bound<G>(t, a, lo, e, (rel + 1) << kNbrBits);
+  return false;
+}
+
+// Entry j of the run scanned by lane r in the tile: from the lanes on the
+// fast path, from memory otherwise (all lanes call it: it may shuffle).
+template <int G>
+__device__ __forceinline__ uint32_t run_entry(const cg::thread_block_tile<G> &t, const DevGraph &Gr, int dir,
+                                              bool fast, uint64_t base, uint32_t x, uint64_t j, uint64_t hi) {
+  if (fast) {
+    const uint32_t y = t.shfl(x, (unsigned)((j - base) & (G - 1)));
+    return j < hi ? y : 0xFFFFFFFFu;
+  }
+  return j < hi ? Gr.adj[dir][j] : 0xFFFFFFFFu;
+}
+
 // Binary search of a sorted uint32 list (all lanes do the same search).
 __device__ __forceinline__ int64_t list_find(const uint32_t *a, uint64_t n, uint32_t key) {
   uint64_t lo = 0, hi = n;
@@ -241,6 +276,28 @@ __global__ void k_plan(Wave W, const uint32_t *type_count) {
     }
     Q.nvisit = nv;
     atomicMax(&W.ctrl->max_nvisit, nv);
+    // every incident edge of every query vertex, packed for exploration and
+    // refinement: direction, relation, other endpoint and, for a vertex that
+    // is explored (leaves of the spanning tree are not), the endpoint's role
+    // at that step (0: set not built yet, 1: set built, 2: child initialised
+    // now)
+    uint8_t step_of[kMaxK];
+    for (uint32_t u = 0; u < k; ++u) step_of[u] = 0xFF;
+    for (uint32_t s = 0; s < nv; ++s) step_of[Q.visit[s]] = (uint8_t)s;
+    for (uint32_t u = 0; u < k; ++u) {
+      const uint32_t s = step_of[u];
+      for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1]; ++i) {
+        const uint32_t e = Q.inc_edge[i];
+        const uint32_t dir = Q.esrc[e] == u ? 0u : 1u;
+        const uint32_t w = dir == 0 ? Q.edst[e] : Q.esrc[e];
+        uint32_t role = 0;
+        if (s != 0xFF) {
+          role = Q.init_step[w] <= s ? 1u : 0u;
+          if (Q.parent[w] == u && Q.init_step[w] == s + 1 && Q.pedge[w] == e) role = 2u;
+        }
+        Q.xinc[i] = xinc_pack(dir, Q.erel[e], w, role);
+      }
+    }
   }
 }
 
@@ -567,24 +624,27 @@ __global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
     if (Q.status != QS_OK) continue;
     const uint32_t u = Q.visit[step];
     const uint32_t v = W.tlist[it];
+    const uint32_t i0 = Q.inc_begin[u], i1 = Q.inc_begin[u + 1];
     uint64_t bytes = 0;
     bool keep = true;
     // edges to vertices other than the children initialised by this step
-    for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1] && keep; ++i) {
-      const uint32_t e = Q.inc_edge[i];
-      const int dir = Q.esrc[e] == u ? 0 : 1;
-      const uint32_t w = dir == 0 ? Q.edst[e] : Q.esrc[e];
-      if (Q.parent[w] == u && Q.init_step[w] == step + 1 && Q.pedge[w] == e) continue;
-      uint64_t lo, hi;
-      rel_range<G>(tile, Gr, dir, v, Q.erel[e], lo, hi);
-      const bool built = Q.init_step[w] <= step;
+    for (uint32_t i = i0; i < i1 && keep; ++i) {
+      const uint32_t xi = Q.xinc[i];
+      if (xinc_role(xi) == 2) continue;
+      const int dir = xinc_dir(xi);
+      const uint32_t w = xinc_w(xi);
+      uint64_t base, lo, hi;
+      uint32_t xs;
+      const bool fast = rel_run<G>(tile, Gr, dir, v, xinc_rel(xi), base, lo, hi, xs);
+      const bool built = xinc_role(xi) == 1;
       const uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
       for (uint64_t b = lo; b < hi && !found; b += G) {
-        uint64_t j = b + r;
+        const uint64_t j = b + r;
+        const uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, j, hi);
         bool ok = false;
         if (j < hi) {
-          uint32_t x = Gr.adj[dir][j] & kNbrMask;
+          const uint32_t x = e & kNbrMask;
           ok = built ? bit_test(ws, x) : cand_ok(Gr, Q, w, x);
         }
         found = tile.any(ok);
@@ -593,20 +653,22 @@ __global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
       if (!found) keep = false;
     }
     // tree edges to the children: test, expand and check existence in one scan
-    for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1] && keep; ++i) {
-      const uint32_t e = Q.inc_edge[i];
-      const int dir = Q.esrc[e] == u ? 0 : 1;
-      const uint32_t w = dir == 0 ? Q.edst[e] : Q.esrc[e];
-      if (!(Q.parent[w] == u && Q.init_step[w] == step + 1 && Q.pedge[w] == e)) continue;
-      uint64_t lo, hi;
-      rel_range<G>(tile, Gr, dir, v, Q.erel[e], lo, hi);
+    for (uint32_t i = i0; i < i1 && keep; ++i) {
+      const uint32_t xi = Q.xinc[i];
+      if (xinc_role(xi) != 2) continue;
+      const int dir = xinc_dir(xi);
+      const uint32_t w = xinc_w(xi);
+      uint64_t base, lo, hi;
+      uint32_t xs;
+      const bool fast = rel_run<G>(tile, Gr, dir, v, xinc_rel(xi), base, lo, hi, xs);
       uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
       for (uint64_t b = lo; b < hi; b += G) {
-        uint64_t j = b + r;
+        const uint64_t j = b + r;
+        const uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, j, hi);
         bool ok = false;
         if (j < hi) {
-          uint32_t x = Gr.adj[dir][j] & kNbrMask;
+          const uint32_t x = e & kNbrMask;
           ok = cand_ok(Gr, Q, w, x);
           if (ok) bit_set(W, ws, x);
         }
@@ -647,16 +709,18 @@ __global__ void __launch_bounds__(kThreads) k_refine(Wave W, uint32_t round) {
     if (!bit_test(us, v)) continue;
     uint64_t bytes = 0;
     for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1]; ++i) {
-      const uint32_t e = Q.inc_edge[i];
-      const int dir = Q.esrc[e] == u ? 0 : 1;
-      const uint32_t w = dir == 0 ? Q.edst[e] : Q.esrc[e];
-      uint64_t lo, hi;
-      rel_range<G>(tile, Gr, dir, v, Q.erel[e], lo, hi);
+      const uint32_t xi = Q.xinc[i];
+      const int dir = xinc_dir(xi);
+      const uint32_t w = xinc_w(xi);
+      uint64_t base, lo, hi;
+      uint32_t xs;
+      const bool fast = rel_run<G>(tile, Gr, dir, v, xinc_rel(xi), base, lo, hi, xs);
       const uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
       for (uint64_t b = lo; b < hi && !found; b += G) {
-        uint64_t j = b + r;
-        found = tile.any(j < hi && bit_test(ws, Gr.adj[dir][j] & kNbrMask));
+        const uint64_t j = b + r;
+        const uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, j, hi);
+        found = tile.any(j < hi && bit_test(ws, e & kNbrMask));
       }
       bytes += 16 + 4 * (hi - lo);
       if (!found) {
