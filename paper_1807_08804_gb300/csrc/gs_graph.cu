@@ -8,6 +8,7 @@
 //   - per-vertex, per-(direction, relation) distinct-neighbour counts kept
 //     as 4-bit signatures for the candidate test (Definition 3.3's degree
 //     condition, read per direction and relation).
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -114,6 +115,26 @@ __global__ void k_signatures(uint32_t V, uint32_t R, const uint64_t *off, const 
       i = j;
     }
   }
+}
+
+// Vertices per (type, signature plane, nibble value): one block per (plane,
+// vertex chunk), counts gathered in shared memory first.  hist holds
+// (T + 1) * P * 16 counters; row T counts every vertex (the untyped case).
+__global__ void __launch_bounds__(256) k_sig_hist(uint32_t V, uint32_t T, uint32_t P, const uint8_t *vtype,
+                                                  const uint32_t *sig, uint64_t sig_words, uint32_t *hist) {
+  __shared__ uint32_t h[257 * 16];
+  const uint32_t p = blockIdx.y;
+  for (uint32_t i = threadIdx.x; i < (T + 1) * 16; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const uint32_t *plane = sig + (uint64_t)p * sig_words;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t n = (plane[v >> 3] >> ((v & 7) * 4)) & 15u;
+    atomicAdd(&h[vtype[v] * 16 + n], 1u);
+    atomicAdd(&h[T * 16 + n], 1u);
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < (T + 1) * 16; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[((uint64_t)(i >> 4) * P + p) * 16 + (i & 15)], h[i]);
 }
 
 __global__ void k_iota(uint32_t n, uint32_t *out) {
@@ -323,6 +344,26 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
     GS_CUDA(cudaMemcpyAsync(g->tvid, res ? v1.p : v0.p, sizeof(uint32_t) * V, cudaMemcpyDeviceToDevice, s));
     GS_CUDA(cudaStreamSynchronize(s));
   }
+  // Signature statistics for the plan: sigge[(t * P + p) * 16 + c] = vertices
+  // of type t (t = T: any type) whose count in plane p is at least c.
+  {
+    const uint32_t P = 2 * R;
+    const uint64_t nh = (uint64_t)(T + 1) * P * 16;
+    uint32_t *dh = nullptr;
+    GS_CUDA(cudaMalloc(&dh, sizeof(uint32_t) * nh));
+    GS_CUDA(cudaMemsetAsync(dh, 0, sizeof(uint32_t) * nh, s));
+    const dim3 grid((unsigned)std::min<uint64_t>((V + 255) / 256, 64), P);
+    k_sig_hist<<<grid, 256, 0, s>>>(V, T, P, g->vtype, g->sig, sig_words, dh);
+    std::vector<uint32_t> hh(nh);
+    GS_CUDA(cudaMemcpyAsync(hh.data(), dh, sizeof(uint32_t) * nh, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    cudaFree(dh);
+    for (uint64_t row = 0; row < (uint64_t)(T + 1) * P; ++row)
+      for (int c = 14; c >= 0; --c) hh[row * 16 + c] += hh[row * 16 + c + 1];
+    if (cudaMalloc(&g->sigge, sizeof(uint32_t) * nh) != cudaSuccess) return cleanup(fail(GS_ERR_OOM, "signature statistics"));
+    GS_CUDA(cudaMemcpyAsync(g->sigge, hh.data(), sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+  }
   uint64_t h = 1469598103934665603ull;
   auto mixin = [&](uint64_t x) { h = (h ^ x) * 1099511628211ull; };
   mixin(V); mixin(kept); mixin(T); mixin(R);
@@ -336,6 +377,7 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   d.vtype = g->vtype;
   d.tvid = g->tvid;
   d.toff = g->toff;
+  d.sigge = g->sigge;
   d.sig = g->sig;
   d.sig_words = sig_words;
   d.W0 = (V + 31) / 32;
@@ -359,6 +401,7 @@ extern "C" void gs_graph_free(gs_graph *g) {
   cudaFree(g->vtype);
   cudaFree(g->tvid);
   cudaFree(g->toff);
+  cudaFree(g->sigge);
   cudaFree(g->sig);
   delete[] g->type_count;
   delete g;

@@ -202,9 +202,12 @@ __device__ __forceinline__ uint64_t row_hash(const DQuery &Q, const uint32_t *ro
 
 // ============================================================ plan
 // Section 3.5 ("Modify the query plan"): start at the bound vertex of largest
-// degree, else at the vertex of largest deg(u)/freq(type(u)) (Section 3.3.2's
-// ranking); then repeatedly explore the already-covered vertex with the most
-// uncovered neighbours until every vertex is covered.  The explored vertices
+// degree; with no bound vertex, Section 3.3.2 ranks by deg(u)/freq(type(u)),
+// which this plan refines into the expected size of u's filtered set (type
+// frequency times, per degree need, the measured fraction of that type's
+// vertices meeting it), so the exploration starts from the fewest
+// candidates; then repeatedly explore the already-covered vertex with the
+// most uncovered neighbours until every vertex is covered.  The explored vertices
 // form the visit order; each newly covered vertex hangs below the vertex that
 // covered it (the spanning tree T).
 __global__ void k_plan(Wave W, const uint32_t *type_count) {
@@ -239,12 +242,21 @@ __global__ void k_plan(Wave W, const uint32_t *type_count) {
       for (uint32_t u = 0; u < k; ++u)
         if (Q.vbind[u] != kUnbound && (root < 0 || __popc(nbr[u]) > __popc(nbr[root]))) root = (int)u;
     if (root < 0) {
-      uint64_t bn = 0, bf = 1;
+      // no bound vertex: the vertex whose filtered candidate set is expected
+      // to be smallest (its type's vertex count times, per degree need, the
+      // fraction of those vertices that meet it; ties: more neighbours)
+      const uint32_t P = 2 * W.G.R;
+      float best = 0.f;
       for (uint32_t u = 0; u < k; ++u) {
-        uint64_t d = __popc(nbr[u]);
-        uint64_t f = Q.vtype[u] == kAny ? W.G.V : type_count[Q.vtype[u]];
-        if (f == 0) f = 1;
-        if (root < 0 || d * bf > bn * f) { root = (int)u; bn = d; bf = f; }
+        const uint32_t t = Q.vtype[u] == kAny ? W.G.T : Q.vtype[u];
+        const float f = (float)(t == W.G.T ? W.G.V : type_count[t]);
+        float est = f;
+        for (uint32_t i = Q.need_begin[u]; i < Q.need_begin[u + 1] && f > 0.f; ++i)
+          est *= (float)W.G.sigge[((uint64_t)t * P + Q.need_plane[i]) * 16 + Q.need_cnt[i]] / f;
+        if (root < 0 || est < best || (est == best && __popc(nbr[u]) > __popc(nbr[root]))) {
+          root = (int)u;
+          best = est;
+        }
       }
     }
     for (uint32_t u = 0; u < kMaxK; ++u) { Q.parent[u] = 0xFF; Q.pedge[u] = 0xFF; Q.init_step[u] = 0xFF; }
