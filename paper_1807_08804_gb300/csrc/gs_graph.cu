@@ -137,6 +137,23 @@ __global__ void __launch_bounds__(256) k_sig_hist(uint32_t V, uint32_t T, uint32
     if (h[i]) atomicAdd(&hist[((uint64_t)(i >> 4) * P + p) * 16 + (i & 15)], h[i]);
 }
 
+// Neighbour-type masks: for each vertex v and each (direction, relation)
+// plane, the OR of 1 << (type mod 32) over v's neighbours in that plane.
+__global__ void k_type_masks(uint32_t V, uint32_t R, const uint64_t *off, const uint32_t *adj, int dir,
+                             const uint8_t *vtype, uint32_t *tmask) {
+  uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = tid; v < V; v += stride) {
+    const uint64_t b = off[v], e = off[v + 1];
+    uint64_t i = b;
+    while (i < e) {
+      const uint32_t r = adj[i] >> kNbrBits;
+      uint32_t m = 0;
+      for (; i < e && (adj[i] >> kNbrBits) == r; ++i) m |= 1u << (vtype[adj[i] & kNbrMask] & 31u);
+      tmask[(uint64_t)(dir * R + r) * V + v] = m;
+    }
+  }
+}
+
 __global__ void k_iota(uint32_t n, uint32_t *out) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
     out[i] = (uint32_t)i;
@@ -344,6 +361,12 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
     GS_CUDA(cudaMemcpyAsync(g->tvid, res ? v1.p : v0.p, sizeof(uint32_t) * V, cudaMemcpyDeviceToDevice, s));
     GS_CUDA(cudaStreamSynchronize(s));
   }
+  // neighbour-type masks (zero where a vertex has no neighbour in a plane)
+  if (cudaMalloc(&g->tmask, sizeof(uint32_t) * (uint64_t)V * 2 * R) != cudaSuccess)
+    return cleanup(fail(GS_ERR_OOM, "neighbour-type masks"));
+  GS_CUDA(cudaMemsetAsync(g->tmask, 0, sizeof(uint32_t) * (uint64_t)V * 2 * R, s));
+  k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, R, g->off_out, g->adj_out, 0, g->vtype, g->tmask);
+  k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, R, g->off_in, g->adj_in, 1, g->vtype, g->tmask);
   // Signature statistics for the plan: sigge[(t * P + p) * 16 + c] = vertices
   // of type t (t = T: any type) whose count in plane p is at least c.
   {
@@ -378,6 +401,7 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   d.tvid = g->tvid;
   d.toff = g->toff;
   d.sigge = g->sigge;
+  d.tmask = g->tmask;
   d.sig = g->sig;
   d.sig_words = sig_words;
   d.W0 = (V + 31) / 32;
@@ -402,6 +426,7 @@ extern "C" void gs_graph_free(gs_graph *g) {
   cudaFree(g->tvid);
   cudaFree(g->toff);
   cudaFree(g->sigge);
+  cudaFree(g->tmask);
   cudaFree(g->sig);
   delete[] g->type_count;
   delete g;

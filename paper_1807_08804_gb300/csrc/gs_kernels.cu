@@ -638,7 +638,18 @@ __global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
     const uint32_t v = W.tlist[it];
     const uint32_t i0 = Q.inc_begin[u], i1 = Q.inc_begin[u + 1];
     uint64_t bytes = 0;
+    // every edge to a typed vertex w needs a neighbour of w's type over its
+    // relation and direction: the neighbour-type masks of all edges, loaded
+    // together, reject most candidates before any row is read
     bool keep = true;
+    for (uint32_t i = i0; i < i1; ++i) {
+      const uint32_t xi = Q.xinc[i];
+      const uint32_t t = Q.vtype[xinc_w(xi)];
+      if (t == kAny) continue;
+      const uint32_t m = Gr.tmask[(uint64_t)(xinc_dir(xi) * Gr.R + xinc_rel(xi)) * Gr.V + v];
+      keep = keep && ((m >> (t & 31u)) & 1u);
+    }
+    bytes += 4ull * (i1 - i0);
     // edges to vertices other than the children initialised by this step
     for (uint32_t i = i0; i < i1 && keep; ++i) {
       const uint32_t xi = Q.xinc[i];
