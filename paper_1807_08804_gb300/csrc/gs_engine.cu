@@ -448,7 +448,7 @@ void enqueue_large_sort(Pipe &P, uint64_t max_rows) {
   }
   P.end();
   P.begin(KK_GATHER);
-  launch_gather(W, perm[cur], P.cur, sms);
+  launch_gather(W, perm[0], perm[1], P.cur, sms);
   P.end();
 }
 

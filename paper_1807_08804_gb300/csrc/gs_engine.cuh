@@ -15,6 +15,7 @@ constexpr uint32_t kAny = 0xFFFFFFFFu;
 constexpr uint32_t kMaxRounds = 64;
 constexpr uint32_t kSmallRows = 2048;    // outputs sorted by one block in shared memory
 constexpr uint32_t kTileRows = 1024;     // rows per tile of the large-output merge sort
+constexpr uint64_t kOverCap = 16;        // outputs up to kOverCap * cap rows are sorted on the device
 
 // Per-query status.
 enum : uint32_t {
@@ -204,7 +205,7 @@ void launch_small_sort(const Wave &W, cudaStream_t s, int sms);
 void launch_tile_sort(const Wave &W, uint32_t *perm, uint64_t *keys, cudaStream_t s, int sms);
 void launch_merge_pass(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
                        uint64_t run, cudaStream_t s, int sms);
-void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms);
+void launch_gather(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, cudaStream_t s, int sms);
 void launch_epilogue(const Wave &W, cudaStream_t s, int sms);
 
 }  // namespace gs

@@ -982,9 +982,9 @@ __device__ __forceinline__ void level_sizes(const Wave &W, uint32_t qi, uint32_t
   if (Q.k == lvl + 1) {
     if (Q.mode == GS_COUNT_ONLY || Q.cap == 0) return;
     // More rows than cap are still written (and the smallest cap kept after
-    // the sort) while they stay within 8 * cap; beyond, the chunked path
-    // keeps a running top-cap instead.
-    if (S.count > Q.cap && S.count > 8 * Q.cap) {
+    // the sort) while they stay within kOverCap * cap; beyond, the chunked
+    // path keeps a running top-cap instead.
+    if (S.count > Q.cap && S.count > kOverCap * Q.cap) {
       if (pass0) mark(Q, QS_TOPCAP);
       return;
     }
@@ -1481,72 +1481,99 @@ __global__ void __launch_bounds__(256) k_tile_sort(Wave W, uint32_t *perm, uint6
 }
 
 // Where output tile t of a merge pass with runs of `run` rows sits: its
-// query, the start of its pair of runs and their lengths (nb = 0: a lone run).
+// query, the start of its pair of runs and their lengths (nb = 0: a lone
+// run).  Only the smallest cap rows of a query are returned, so only the
+// first cap entries of a run are kept (va, vb: the valid prefixes; out: the
+// valid length of the merged run).  A query whose rows already form one run
+// (n <= run) is finished and takes no part in the pass.
 struct MergeTile {
   uint32_t qi;
-  uint64_t base, first, a0, na, nb;
+  bool active;
+  uint64_t base, first, a0, na, nb, va, vb, out;
 };
 __device__ __forceinline__ MergeTile merge_tile(const Wave &W, uint64_t t, uint64_t run) {
   MergeTile m;
   m.qi = seg_of_large(W.qs, W.nq, t, true);
   const QState &S = W.qs[m.qi];
-  const uint64_t n = S.out_rows;
+  const uint64_t n = S.out_rows, cap = W.dq[m.qi].cap;
   m.base = S.lrg_row_base;
   m.first = (t - S.lrg_tile_base) * kTileRows;
   m.a0 = (m.first / (2 * run)) * 2 * run;
   m.na = min(run, n - m.a0);
   m.nb = n - m.a0 > run ? min(run, n - m.a0 - run) : 0;
+  m.va = min(m.na, cap);
+  m.vb = min(m.nb, cap);
+  m.out = min(m.va + m.vb, cap);
+  m.active = n > run && m.first - m.a0 < m.out;
   return m;
 }
 
-// Merge-path split of every output tile: how many of its first outputs come
-// from the left run (stable: the left run wins ties).  One thread per tile.
+// Merge-path split at diagonal o of runs A (va valid) and B (vb valid): how
+// many of the first o outputs come from A (stable: A wins ties).
+__device__ __forceinline__ uint64_t merge_split_at(const Wave &W, const DQuery &Q, const QState &S, const uint32_t *perm,
+                                                   const uint64_t *key, uint64_t A, uint64_t B, uint64_t va,
+                                                   uint64_t vb, uint64_t o) {
+  uint64_t lo = o > vb ? o - vb : 0, hi = min(o, va);
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1, j = o - 1 - mid;
+    if (kr_le(W, Q, S, key[A + mid], perm[A + mid], key[B + j], perm[B + j])) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Split of every active output tile at its first output.  One thread per tile.
 __global__ void k_merge_split(Wave W, const uint32_t *perm, const uint64_t *key, uint64_t run) {
   const uint64_t ntiles = W.ctrl->len[7];
   for (uint64_t t = gtid(); t < ntiles; t += gthreads()) {
     const MergeTile m = merge_tile(W, t, run);
+    if (!m.active) continue;
     const uint64_t o = m.first - m.a0;
     if (m.nb == 0) {
       W.msplit[t] = o;
       continue;
     }
-    const DQuery &Q = W.dq[m.qi];
-    const QState &S = W.qs[m.qi];
-    const uint64_t A = m.base + m.a0, B = A + m.na;
-    uint64_t lo = o > m.nb ? o - m.nb : 0, hi = min(o, m.na);
-    while (lo < hi) {
-      const uint64_t mid = (lo + hi) >> 1, j = o - 1 - mid;
-      if (kr_le(W, Q, S, key[A + mid], perm[A + mid], key[B + j], perm[B + j])) lo = mid + 1; else hi = mid;
-    }
-    W.msplit[t] = lo;
+    const uint64_t A = m.base + m.a0;
+    W.msplit[t] = merge_split_at(W, W.dq[m.qi], W.qs[m.qi], perm, key, A, A + m.na, m.va, m.vb, o);
   }
 }
 
 // One merge pass: runs of `run` (>= kTileRows) rows become runs of 2*run.
-// One block per output tile: the tile's slices of both runs (bounded by the
-// splits of this tile and the next) are staged in shared memory with their
-// keys; each thread places four outputs after a short search in the slices.
+// One block per active output tile: the tile's slices of both runs (bounded
+// by the splits at its first and last output) are staged in shared memory
+// with their keys; each thread places four outputs after a short search in
+// the slices.
 __global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout,
                                                      uint64_t *kout, uint64_t run) {
   __shared__ uint64_t sk[kTileRows];
   __shared__ uint32_t si[kTileRows];
+  __shared__ uint64_t s_end;
   const uint64_t ntiles = W.ctrl->len[7];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const MergeTile m = merge_tile(W, t, run);
-    const uint64_t n = m.na + m.nb, o0 = m.first - m.a0, o1 = min(o0 + kTileRows, n);
+    if (!m.active) continue;  // block-uniform
+    const uint64_t o0 = m.first - m.a0, o1 = min(o0 + kTileRows, m.out);
     if (m.nb == 0) {
       for (uint64_t i = m.base + m.first + threadIdx.x; i < m.base + m.a0 + o1; i += blockDim.x) {
         pout[i] = pin[i];
         kout[i] = kin[i];
       }
-      continue;  // block-uniform
+      continue;
     }
     const DQuery &Q = W.dq[m.qi];
     const QState &S = W.qs[m.qi];
+    const uint64_t A0 = m.base + m.a0, B0 = A0 + m.na;
+    // the end split: the next tile's start, the end of both runs, or (a run
+    // cut at cap inside this tile) a search at the cut
+    if (threadIdx.x == 0) {
+      if (o1 < m.out) s_end = W.msplit[t + 1];
+      else if (m.out == m.va + m.vb) s_end = m.va;
+      else s_end = merge_split_at(W, Q, S, pin, kin, A0, B0, m.va, m.vb, o1);
+    }
+    __syncthreads();
     const uint64_t ab = W.msplit[t], bb = o0 - ab;
-    const uint64_t ae = o1 == n ? m.na : W.msplit[t + 1], be = o1 - ae;
+    const uint64_t ae = s_end, be = o1 - ae;
     const uint32_t la = (uint32_t)(ae - ab), lb = (uint32_t)(be - bb), total = la + lb;
-    const uint64_t A = m.base + m.a0 + ab, B = m.base + m.a0 + m.na + bb;
+    const uint64_t A = A0 + ab, B = B0 + bb;
     for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
       const uint64_t src = i < la ? A + i : B + (i - la);
       sk[i] = kin[src];
@@ -1574,17 +1601,27 @@ __global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *pin
   }
 }
 
-// Sorted large rows in query-vertex column order, laid out query by query.
-__global__ void k_gather(Wave W, const uint32_t *perm) {
+// Merge passes a query of n large rows takes: its runs double from
+// kTileRows until one run holds every row; the tile sort writes buffer 0 and
+// pass p writes buffer (p + 1) & 1, so the query ends in buffer passes & 1.
+__device__ __forceinline__ uint32_t merge_passes(uint64_t n) {
+  uint32_t p = 0;
+  for (uint64_t run = kTileRows; run < n; run *= 2) ++p;
+  return p;
+}
+
+// Sorted large rows in query-vertex column order, laid out query by query:
+// the first cap rows of each query, from the buffer its last pass wrote.
+__global__ void k_gather(Wave W, const uint32_t *perm0, const uint32_t *perm1) {
   const uint64_t n = W.ctrl->len[6];
   for (uint64_t i = gtid(); i < n; i += gthreads()) {
-    const uint32_t row = perm[i];
-    const uint32_t qi = W.out_q[row];
+    const uint32_t qi = seg_of_large(W.qs, W.nq, i, false);
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
     if (i - S.lrg_row_base >= Q.cap) continue;  // past the rows returned
+    const uint32_t row = ((merge_passes(S.out_rows) & 1) ? perm1 : perm0)[i];
     const uint32_t *src = W.out + S.out_word_base + (uint64_t)(row - S.out_row_base) * Q.k;
-    uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.lrg_row_base) * Q.k;  // perm is query-grouped
+    uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.lrg_row_base) * Q.k;
     for (uint32_t u = 0; u < Q.k; ++u) dst[u] = src[Q.pos[u]];
   }
 }
@@ -1751,8 +1788,8 @@ void launch_merge_pass(const Wave &W, const uint32_t *pin, const uint64_t *kin, 
   k_merge_split<<<persistent_grid(k_merge_split, sms), kThreads, 0, s>>>(W, pin, kin, run);
   k_merge_tiles<<<persistent_grid(k_merge_tiles, sms, 256), 256, 0, s>>>(W, pin, kin, pout, kout, run);
 }
-void launch_gather(const Wave &W, const uint32_t *perm, cudaStream_t s, int sms) {
-  k_gather<<<persistent_grid(k_gather, sms), kThreads, 0, s>>>(W, perm);
+void launch_gather(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, cudaStream_t s, int sms) {
+  k_gather<<<persistent_grid(k_gather, sms), kThreads, 0, s>>>(W, perm0, perm1);
 }
 void launch_epilogue(const Wave &W, cudaStream_t s, int sms) {
   k_epilogue_copy<<<persistent_grid(k_epilogue_copy, sms), kThreads, 0, s>>>(W);
