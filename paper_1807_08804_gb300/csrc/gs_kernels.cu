@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, co
 // an earlier child's set, which keeps the sets supersets of the exact ones
 // (refinement removes them).
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
+__global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) {
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const DevGraph &Gr = W.G;
   const uint32_t r = tile.thread_rank();
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(kThreads) k_explore(Wave W, uint32_t step) {
 // neighbour of v over that relation and direction is a live candidate of the
 // other endpoint.  Rounds repeat until one clears nothing (the fixpoint).
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_refine(Wave W, uint32_t round) {
+__global__ void __launch_bounds__(kThreads, 6) k_refine(Wave W, uint32_t round) {
   if (round > 0 && W.ctrl->changed[round - 1] == 0) return;
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const DevGraph &Gr = W.G;
