@@ -179,6 +179,7 @@ struct Wave {
   uint32_t *sval[2];                    // row indices of the large-output merge sort
   uint64_t *msplit;                     // merge-path split of each output tile
   int stats;
+  int c0_only;                      // filter: exactly Definition 3.3's set (no neighbour-type test)
 };
 
 // ------------------------------------------------------------ launchers

@@ -58,7 +58,9 @@ extern "C" gs_status gs_inspect_candidates(gs_graph *g, const gs_query *q, uint3
       launch_prologue(b->W, s, b->sms);
       launch_plan(b->W, b->type_count, s, b->sms);
       scan_u32(b->W.fcnt, b->W.fscan, &b->W.ctrl->len[8], b->W.nq, b->scan_tmp, s, b->sms);
-      launch_filter(b->W, s, b->sms);
+      Wave wc = b->W;
+      wc.c0_only = 1;  // the filter stage as Definition 3.3 defines it
+      launch_filter(wc, s, b->sms);
       launch_compact_count(b->W, 0, 0, s, b->sms);
       scan_u32(b->W.ccount, b->W.cscan, &b->W.ctrl->len[0], (uint64_t)b->W.nq * cps, b->scan_tmp, s, b->sms);
       launch_compact_write(b->W, 0, 0, b->W.cscan, b->W.tlist, b->W.tlist_q, b->W.tlist_cap, HW_TLIST, s, b->sms);

@@ -318,8 +318,10 @@ __global__ void k_plan(Wave W, const uint32_t *type_count) {
 // (one warp each) per query: a bound u has one (its binding, if it passes the
 // test); a typed u has one per 1024 vertices of its type, taken from the
 // per-type vertex lists, so the filter reads only vertices that can pass the
-// type test; an untyped u has one per summary word (1024 vertices), which
-// writes 32 level-0 words and the summary word outright.
+// type test, and there the neighbour-type test (masks_ok) is applied as well
+// unless the exact Definition 3.3 set is asked for (W.c0_only, inspection);
+// an untyped u has one per summary word (1024 vertices), which writes 32
+// level-0 words and the summary word outright.
 __device__ __forceinline__ uint32_t filter_items(const DevGraph &G, const DQuery &Q) {
   if (Q.status != QS_OK || Q.nvisit == 0) return 0;
   const uint32_t u = Q.visit[0];
@@ -335,6 +337,25 @@ __device__ __forceinline__ bool sig_ok(const DevGraph &G, const DQuery &Q, uint3
     if (((w >> ((v & 7) * 4)) & 15u) < Q.need_cnt[i]) return false;
   }
   return true;
+}
+
+// Neighbour-type test of v for query vertex u: for every edge of u to a
+// typed vertex w, v's neighbours over the edge's relation and direction
+// include one whose type matches w's modulo 32 (the masks are loaded
+// together).  Every candidate exploration keeps passes it, so applying it
+// to the first visited vertex in the filter changes no set after the first
+// exploration step; it only spares the exploration the candidates that
+// fail.
+__device__ __forceinline__ bool masks_ok(const DevGraph &G, const DQuery &Q, uint32_t u, uint32_t v) {
+  bool ok = true;
+  for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1]; ++i) {
+    const uint32_t xi = Q.xinc[i];
+    const uint32_t t = Q.vtype[xinc_w(xi)];
+    if (t == kAny) continue;
+    const uint32_t m = G.tmask[(uint64_t)(xinc_dir(xi) * G.R + xinc_rel(xi)) * G.V + v];
+    ok = ok && ((m >> (t & 31u)) & 1u);
+  }
+  return ok;
 }
 
 // OR `bits` into level-0 word w0, raising the summary bits when the word was empty.
@@ -378,7 +399,7 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
         if (x < e0) {
           const uint32_t v = G.tvid[x];
           w = v >> 5;
-          if (sig_ok(G, Q, u, v)) bits = 1u << (v & 31);
+          if (sig_ok(G, Q, u, v) && (W.c0_only || masks_ok(G, Q, u, v))) bits = 1u << (v & 31);
         }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
