@@ -154,6 +154,28 @@ __global__ void k_type_masks(uint32_t V, uint32_t R, const uint64_t *off, const 
   }
 }
 
+// Type-ordered copies of the signature planes and neighbour-type masks:
+// entry x of a plane belongs to vertex tvid[x], so a filter that walks a
+// type's list reads them contiguously.  One thread per 8 list entries (one
+// signature word) and plane.
+__global__ void k_type_order(uint32_t V, uint32_t P, const uint32_t *tvid, const uint32_t *sig, uint64_t sig_words,
+                             const uint32_t *tmask, uint32_t *sig_t, uint32_t *tmask_t) {
+  const uint64_t words = (V + 7) / 8;
+  const uint64_t n = words * P;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t p = i / words, wd = i % words;
+    uint32_t out = 0;
+    for (uint32_t e = 0; e < 8; ++e) {
+      const uint64_t x = wd * 8 + e;
+      if (x >= V) break;
+      const uint32_t v = tvid[x];
+      out |= ((sig[p * sig_words + (v >> 3)] >> ((v & 7) * 4)) & 15u) << (e * 4);
+      tmask_t[p * V + x] = tmask[p * V + v];
+    }
+    sig_t[p * sig_words + wd] = out;
+  }
+}
+
 __global__ void k_iota(uint32_t n, uint32_t *out) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
     out[i] = (uint32_t)i;
@@ -367,6 +389,16 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   GS_CUDA(cudaMemsetAsync(g->tmask, 0, sizeof(uint32_t) * (uint64_t)V * 2 * R, s));
   k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, R, g->off_out, g->adj_out, 0, g->vtype, g->tmask);
   k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, R, g->off_in, g->adj_in, 1, g->vtype, g->tmask);
+  // the same planes in type-list order (needs the type lists, built above)
+  {
+    const uint64_t P = 2ull * R;
+    if (cudaMalloc(&g->sig_t, sizeof(uint32_t) * sig_words * P) != cudaSuccess ||
+        cudaMalloc(&g->tmask_t, sizeof(uint32_t) * (uint64_t)V * P) != cudaSuccess)
+      return cleanup(fail(GS_ERR_OOM, "type-ordered planes"));
+    GS_CUDA(cudaMemsetAsync(g->sig_t, 0, sizeof(uint32_t) * sig_words * P, s));
+    k_type_order<<<blocks_for((V + 7) / 8 * P), kT, 0, s>>>(V, (uint32_t)P, g->tvid, g->sig, sig_words, g->tmask,
+                                                           g->sig_t, g->tmask_t);
+  }
   // Signature statistics for the plan: sigge[(t * P + p) * 16 + c] = vertices
   // of type t (t = T: any type) whose count in plane p is at least c.
   {
@@ -402,6 +434,8 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   d.toff = g->toff;
   d.sigge = g->sigge;
   d.tmask = g->tmask;
+  d.sig_t = g->sig_t;
+  d.tmask_t = g->tmask_t;
   d.sig = g->sig;
   d.sig_words = sig_words;
   d.W0 = (V + 31) / 32;
@@ -427,6 +461,8 @@ extern "C" void gs_graph_free(gs_graph *g) {
   cudaFree(g->toff);
   cudaFree(g->sigge);
   cudaFree(g->tmask);
+  cudaFree(g->sig_t);
+  cudaFree(g->tmask_t);
   cudaFree(g->sig);
   delete[] g->type_count;
   delete g;

@@ -42,6 +42,8 @@ struct DevGraph {
   const uint32_t *toff;     // [T+1] start of each type's run in tvid
   const uint32_t *sigge;    // [(T+1) * 2R * 16] vertices of type t (t = T: any) with plane count >= c
   const uint32_t *tmask;    // [2R][V] OR of 1 << (type mod 32) over v's neighbours in each plane
+  const uint32_t *sig_t;    // sig with entry x of each plane belonging to vertex tvid[x]
+  const uint32_t *tmask_t;  // tmask likewise
   const uint32_t *sig;      // [2R][sig_words]
   uint64_t sig_words;       // ceil(V / 8)
   uint32_t W0;              // bitmap words per candidate set: ceil(V/32)
@@ -60,7 +62,7 @@ struct gs_graph {
   uint64_t *off_out, *off_in;
   uint32_t *adj_out, *adj_in;
   uint8_t *vtype;
-  uint32_t *tvid, *toff, *sigge, *tmask;
+  uint32_t *tvid, *toff, *sigge, *tmask, *sig_t, *tmask_t;
   uint32_t *sig;
   uint32_t *type_count;     // host copy [T]
   uint64_t hash;            // content hash (tuning cache key)

@@ -330,29 +330,29 @@ __device__ __forceinline__ uint32_t filter_items(const DevGraph &G, const DQuery
   return G.W1;
 }
 
-// Degree-signature part of the candidate test (type and binding known to pass).
-__device__ __forceinline__ bool sig_ok(const DevGraph &G, const DQuery &Q, uint32_t u, uint32_t v) {
+// Degree-signature part of the candidate test (type and binding known to
+// pass) and the neighbour-type test, for the vertex at position x of the
+// type lists, read from the type-ordered planes (contiguous for consecutive
+// x).  The neighbour-type test: for every edge of u to a typed vertex w, the
+// vertex's neighbours over the edge's relation and direction include one
+// whose type matches w's modulo 32.  Every candidate exploration keeps
+// passes it, so applying it to the first visited vertex in the filter
+// changes no set after the first exploration step; it only spares the
+// exploration the candidates that fail.
+__device__ __forceinline__ bool sig_ok_listed(const DevGraph &G, const DQuery &Q, uint32_t u, uint32_t x) {
   for (uint32_t i = Q.need_begin[u]; i < Q.need_begin[u + 1]; ++i) {
-    uint32_t w = G.sig[(uint64_t)Q.need_plane[i] * G.sig_words + (v >> 3)];
-    if (((w >> ((v & 7) * 4)) & 15u) < Q.need_cnt[i]) return false;
+    const uint32_t w = G.sig_t[(uint64_t)Q.need_plane[i] * G.sig_words + (x >> 3)];
+    if (((w >> ((x & 7) * 4)) & 15u) < Q.need_cnt[i]) return false;
   }
   return true;
 }
-
-// Neighbour-type test of v for query vertex u: for every edge of u to a
-// typed vertex w, v's neighbours over the edge's relation and direction
-// include one whose type matches w's modulo 32 (the masks are loaded
-// together).  Every candidate exploration keeps passes it, so applying it
-// to the first visited vertex in the filter changes no set after the first
-// exploration step; it only spares the exploration the candidates that
-// fail.
-__device__ __forceinline__ bool masks_ok(const DevGraph &G, const DQuery &Q, uint32_t u, uint32_t v) {
+__device__ __forceinline__ bool masks_ok_listed(const DevGraph &G, const DQuery &Q, uint32_t u, uint32_t x) {
   bool ok = true;
   for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1]; ++i) {
     const uint32_t xi = Q.xinc[i];
     const uint32_t t = Q.vtype[xinc_w(xi)];
     if (t == kAny) continue;
-    const uint32_t m = G.tmask[(uint64_t)(xinc_dir(xi) * G.R + xinc_rel(xi)) * G.V + v];
+    const uint32_t m = G.tmask_t[(uint64_t)(xinc_dir(xi) * G.R + xinc_rel(xi)) * G.V + x];
     ok = ok && ((m >> (t & 31u)) & 1u);
   }
   return ok;
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
         if (x < e0) {
           const uint32_t v = G.tvid[x];
           w = v >> 5;
-          if (sig_ok(G, Q, u, v) && (W.c0_only || masks_ok(G, Q, u, v))) bits = 1u << (v & 31);
+          if (sig_ok_listed(G, Q, u, x) && (W.c0_only || masks_ok_listed(G, Q, u, x))) bits = 1u << (v & 31);
         }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
