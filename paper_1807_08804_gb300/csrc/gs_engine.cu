@@ -244,6 +244,8 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
     A(W.sval[i], s.out_rows);
   }
   A(W.msplit, s.out_rows / kTileRows + W.nq + 1);
+  A(W.sel, W.nq);
+  A(W.shist, (uint64_t)W.nq * 256);
   uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * cps, (uint64_t)W.nqe, s.ec_items, W.row_cap}));
   A(b->scan_tmp, tmpw);
   b->scan_tmp_words = tmpw;
@@ -251,6 +253,7 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
 #undef A
   GS_CUDA(cudaMemsetAsync(W.bm, 0, sizeof(uint32_t) * (uint64_t)W.nqv * W.slot_words, b->stream));
   GS_CUDA(cudaMemsetAsync(b->scan_tmp, 0, sizeof(uint64_t) * b->scan_tmp_words, b->stream));
+  GS_CUDA(cudaMemsetAsync(W.shist, 0, sizeof(uint32_t) * (uint64_t)W.nq * 256, b->stream));
   GS_CUDA(cudaMemsetAsync(W.ctrl, 0, sizeof(Ctrl), b->stream));
   GS_CUDA(cudaMemsetAsync(W.dq, 0, sizeof(DQuery) * (W.nq + 1), b->stream));
   const uint64_t lens[3] = {(uint64_t)W.nq * cps, (uint64_t)W.nqv * cps, (uint64_t)W.nqe};
@@ -431,17 +434,29 @@ void enqueue_back(Pipe &P, int K, int stop) {
 // Merge sort of the outputs above the one-block limit: tiles sorted in
 // shared memory, then ceil(log2(largest / tile)) merge passes (launched
 // directly: the host reads the largest output first).
-void enqueue_large_sort(Pipe &P, uint64_t max_rows) {
+// Launches of enqueue_large_sort for the largest output and the number of
+// outputs cut at cap.
+uint64_t large_sort_launches(uint64_t max_rows, uint64_t over_cap) {
+  uint64_t passes = 0;
+  for (uint64_t run = kTileRows; run < max_rows; run *= 2) ++passes;
+  return 3 + 2 * passes + (over_cap ? 3 + 2 * 3 : 0);
+}
+
+void enqueue_large_sort(Pipe &P, uint64_t max_rows, uint64_t over_cap) {
   gs_batch *b = P.b;
   Wave &W = b->W;
   const int sms = b->sms;
-  P.begin(KK_SORT);
   uint32_t *perm[2] = {W.sval[0], W.sval[1]};
   uint64_t *keys[2] = {W.skey[0], W.skey[1]};
   int cur = 0;
-  P.end();
   P.begin(KK_SORT_LARGE);
-  launch_tile_sort(W, perm[cur], keys[cur], P.cur, sms);
+  launch_sort_keys(W, perm[0], keys[0], P.cur, sms);
+  int in = 0;
+  if (over_cap) {  // cut the outputs above cap to about cap rows before sorting
+    launch_select(W, perm[0], keys[0], perm[1], keys[1], P.cur, sms);
+    in = 1;
+  }
+  launch_tile_sort(W, perm[in], keys[in], perm[0], keys[0], P.cur, sms);
   for (uint64_t run = kTileRows; run < max_rows; run *= 2) {
     launch_merge_pass(W, perm[cur], keys[cur], perm[cur ^ 1], keys[cur ^ 1], run, P.cur, sms);
     cur ^= 1;
@@ -545,7 +560,7 @@ gs_status run_waves(gs_batch *b) {
   GS_CUDA(cudaMemsetAsync(b->W.ctrl->hw, 0, sizeof(b->W.ctrl->hw), b->stream));
   GS_CUDA(cudaMemsetAsync(&b->W.ctrl->wave, 0, sizeof(uint32_t), b->stream));
   GS_CUDA(cudaMemsetAsync(&b->W.ctrl->store_top, 0, sizeof(uint64_t), b->stream));
-  if (!b->flag) GS_CUDA(cudaMallocHost((void **)&b->flag, 2 * sizeof(uint64_t)));
+  if (!b->flag) GS_CUDA(cudaMallocHost((void **)&b->flag, 3 * sizeof(uint64_t)));
   const bool sorting = rows_wanted(b);
   for (size_t w = 0; w < b->waves.size(); ++w) {
     const int K = b->wave_k[w];
@@ -567,14 +582,14 @@ gs_status run_waves(gs_batch *b) {
       GS_CUDA(cudaMemcpyAsync(b->flag, &b->W.ctrl->len[6], sizeof(uint64_t), cudaMemcpyDeviceToHost, b->stream));
       GS_CUDA(cudaMemcpyAsync(b->flag + 1, &b->W.ctrl->max_large_rows, sizeof(uint64_t), cudaMemcpyDeviceToHost,
                               b->stream));
+      GS_CUDA(cudaMemcpyAsync(b->flag + 2, &b->W.ctrl->over_cap, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                              b->stream));
       GS_CUDA(cudaStreamSynchronize(b->stream));
       large = b->flag[0] != 0;
       if (large) {
         Pipe P{b, &b->sort_evs_direct, false, b->stream};
-        enqueue_large_sort(P, b->flag[1]);
-        uint64_t passes = 0;
-        for (uint64_t run = kTileRows; run < b->flag[1]; run *= 2) ++passes;
-        b->kernel_launches += 2 + 2 * passes;
+        enqueue_large_sort(P, b->flag[1], b->flag[2]);
+        b->kernel_launches += large_sort_launches(b->flag[1], b->flag[2]);
         b->large_sorts++;
       }
     }

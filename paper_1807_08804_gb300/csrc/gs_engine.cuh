@@ -89,6 +89,19 @@ struct QState {
   uint64_t fin_row_base, fin_word_base;             // sorted rows in query order
   uint64_t lrg_row_base;                             // rows sorted by the merge path
   uint64_t lrg_tile_base;                            // their first tile
+  uint64_t sort_rows;                                // rows entering the merge sort (after selection)
+};
+
+// Top-cap selection of a query with more than cap large rows (radix select
+// on the packed sort keys): rows with key <= thresh go into the sort.
+struct SelState {
+  uint64_t lo, hi;        // smallest and largest key of the query's rows
+  uint64_t prefix;        // key bits chosen so far (bits >= mbits)
+  uint64_t need;          // rows still to take from the current bucket
+  uint64_t thresh;        // the cut, once chosen
+  uint64_t kept;          // rows kept (compaction counter)
+  uint32_t mbits, shift, width;  // rows in play match prefix at bits >= mbits; digit = bits [shift, shift + width)
+  uint32_t state;         // 0: not selected, 1: choosing, 2: cut chosen
 };
 
 // Rows of level s kept aside while the allocator lays out level s+1.
@@ -124,6 +137,7 @@ struct Ctrl {
   uint64_t fb_src[3];               // source rows staged by the chunked join
   uint64_t hw[10];                  // sizes the run asked of each pool (see HW_*)
   uint64_t max_large_rows;          // largest output above the one-block sort limit
+  uint64_t over_cap;                // large outputs with more rows than cap (selected before sorting)
   uint64_t fin_words;               // words of the rows returned by this wave
   uint64_t bytes[KK_N];             // algorithmic bytes per kernel kind
 };
@@ -178,6 +192,8 @@ struct Wave {
   uint64_t *skey[2];                    // sort keys of the large-output merge sort
   uint32_t *sval[2];                    // row indices of the large-output merge sort
   uint64_t *msplit;                     // merge-path split of each output tile
+  SelState *sel;                        // [nq] top-cap selection
+  uint32_t *shist;                      // [nq][256] digit histograms of the selection
   int stats;
   int c0_only;                      // filter: exactly Definition 3.3's set (no neighbour-type test)
 };
@@ -203,7 +219,11 @@ void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s);
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms);
 void launch_final_bases(const Wave &W, cudaStream_t s);
 void launch_small_sort(const Wave &W, cudaStream_t s, int sms);
-void launch_tile_sort(const Wave &W, uint32_t *perm, uint64_t *keys, cudaStream_t s, int sms);
+void launch_sort_keys(const Wave &W, uint32_t *perm, uint64_t *keys, cudaStream_t s, int sms);
+void launch_select(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+                   cudaStream_t s, int sms);
+void launch_tile_sort(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+                      cudaStream_t s, int sms);
 void launch_merge_pass(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
                        uint64_t run, cudaStream_t s, int sms);
 void launch_gather(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, cudaStream_t s, int sms);

@@ -1294,7 +1294,10 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
   __shared__ uint64_t carry[4];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < 4) carry[threadIdx.x] = 0;
-  if (threadIdx.x == 0) W.ctrl->max_large_rows = 0;
+  if (threadIdx.x == 0) {
+    W.ctrl->max_large_rows = 0;
+    W.ctrl->over_cap = 0;
+  }
   __syncthreads();
   for (uint32_t base = 0; base < W.nq; base += blockDim.x) {
     const uint32_t qi = base + threadIdx.x;
@@ -1306,6 +1309,12 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
       v[2] = small_output(W.dq[qi], W.qs[qi]) ? 0 : W.qs[qi].out_rows;
       v[3] = (v[2] + kTileRows - 1) / kTileRows;
       if (v[2]) atomicMax((unsigned long long *)&W.ctrl->max_large_rows, (unsigned long long)v[2]);
+    }
+    if (qi < W.nq) {
+      W.qs[qi].sort_rows = v[2];
+      const bool over = v[2] > W.dq[qi].cap;
+      W.sel[qi] = SelState{~0ull, 0, 0, W.dq[qi].cap, ~0ull, 0, 0, 0, 0, over ? 1u : 0u};
+      if (over) atomicAdd((unsigned long long *)&W.ctrl->over_cap, 1ull);
     }
     for (int a = 0; a < 4; ++a) {
       uint64_t x = v[a];
@@ -1449,28 +1458,264 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
   }
 }
 
-// Tile sort: keys (and row indices) in shared memory, bitonic network;
-// rows are read from the output pool only to build the keys and to order
-// equal keys.
-__global__ void __launch_bounds__(256) k_tile_sort(Wave W, uint32_t *perm, uint64_t *keys) {
+// Sort keys of every large row, in query order (row i of a query at
+// lrg_row_base + i); for a query to be cut at cap, the smallest and largest
+// key (one atomic per warp when the warp's rows share a query).
+__global__ void k_sort_keys(Wave W, uint32_t *perm, uint64_t *keys) {
+  const uint64_t n = W.ctrl->len[6];
+  const uint32_t b = W.G.idbits, lane = threadIdx.x & 31;
+  for (uint64_t base = gtid() - lane; base < n; base += gthreads()) {
+    const uint64_t i = base + lane;
+    uint32_t qi = 0xFFFFFFFFu;
+    uint64_t key = 0;
+    if (i < n) {
+      qi = seg_of_large(W.qs, W.nq, i, false);
+      const DQuery &Q = W.dq[qi];
+      const QState &S = W.qs[qi];
+      const uint64_t local = i - S.lrg_row_base;
+      const uint32_t *x = W.out + S.out_word_base + local * Q.k;
+      key = pack_key(Q.k, b, [&](uint32_t u) { return x[Q.pos[u]]; });
+      keys[i] = key;
+      perm[i] = (uint32_t)(S.out_row_base + local);
+    }
+    const bool sel = i < n && W.sel[qi].state == 1;
+    const uint32_t q0 = __shfl_sync(kFull, qi, 0);
+    if (__all_sync(kFull, sel && qi == q0)) {
+      uint64_t lo = key, hi = key;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+        hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+      }
+      if (lane == 0) {
+        atomicMin((unsigned long long *)&W.sel[q0].lo, (unsigned long long)lo);
+        atomicMax((unsigned long long *)&W.sel[q0].hi, (unsigned long long)hi);
+      }
+    } else if (sel) {
+      atomicMin((unsigned long long *)&W.sel[qi].lo, (unsigned long long)key);
+      atomicMax((unsigned long long *)&W.sel[qi].hi, (unsigned long long)key);
+    }
+  }
+}
+
+// Top-cap selection (radix select on the keys, most significant digit
+// first).  The smallest cap rows of a query are among its rows with key <=
+// K, K the cap-th smallest key; each round histograms one 8-bit digit of the
+// keys still in play and keeps the bucket that holds K.  The first digit
+// starts at the highest bit where the query's keys differ; selection stops
+// when the chosen bucket exceeds what is still needed by at most cap / 8,
+// when the key bits run out, or after kSelRounds rounds, and the cut is then
+// every key up to the end of the bucket.  The cut keeps at least cap rows,
+// and every row with key K, so sorting the kept rows gives the same first
+// cap rows as sorting all of them.
+constexpr int kSelRounds = 3;
+
+__device__ __forceinline__ void sel_finish(SelState &s) {
+  s.thresh = s.prefix | (s.shift ? ((1ull << s.shift) - 1) : 0);
+  s.state = 2;
+}
+
+__global__ void k_sel_start(Wave W) {
+  for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
+    SelState &s = W.sel[qi];
+    if (s.state != 1) continue;
+    const uint64_t x = s.lo ^ s.hi;
+    if (x == 0) {  // all keys equal: no cut
+      s.thresh = ~0ull;
+      s.state = 2;
+      continue;
+    }
+    const uint32_t hb = 63 - __clzll((long long)x);
+    s.mbits = hb + 1;
+    s.prefix = hb == 63 ? 0 : s.lo & ~((2ull << hb) - 1);
+    s.width = min(8u, hb + 1);
+    s.shift = hb + 1 - s.width;
+  }
+}
+
+__device__ __forceinline__ bool sel_in_play(const SelState &s, uint64_t key) {
+  return s.mbits >= 64 || (key >> s.mbits) == (s.prefix >> s.mbits);
+}
+
+// Digit histogram of the keys in play; a block's rows are nearly always
+// one query's, so counts gather in shared memory for the block's first
+// query and go to global memory directly for any other.
+__global__ void __launch_bounds__(256) k_sel_hist(Wave W, const uint64_t *keys) {
+  __shared__ uint32_t h[256];
+  const uint64_t n = W.ctrl->len[6];
+  const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const uint64_t b0 = blockIdx.x * per, b1 = min(n, b0 + per);
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t q0 = b0 < n ? seg_of_large(W.qs, W.nq, b0, false) : 0;
+  for (uint64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    const uint32_t qi = seg_of_large(W.qs, W.nq, i, false);
+    const SelState &s = W.sel[qi];
+    if (s.state != 1) continue;
+    const uint64_t key = keys[i];
+    if (!sel_in_play(s, key)) continue;
+    const uint32_t d = (uint32_t)(key >> s.shift) & ((1u << s.width) - 1);
+    if (qi == q0) atomicAdd(&h[d], 1u);
+    else atomicAdd(&W.shist[(uint64_t)qi * 256 + d], 1u);
+  }
+  __syncthreads();
+  if (b0 < n && W.sel[q0].state == 1 && h[threadIdx.x])
+    atomicAdd(&W.shist[(uint64_t)q0 * 256 + threadIdx.x], h[threadIdx.x]);
+}
+
+// Choose the bucket holding the need-th key; one warp per query.
+__global__ void k_sel_pick(Wave W, int last) {
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint64_t qi = gtid() / 32; qi < W.nq; qi += gthreads() / 32) {
+    SelState &s = W.sel[qi];
+    if (s.state != 1) continue;  // warp-uniform
+    uint32_t *hq = W.shist + qi * 256;
+    uint32_t c[8];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      c[j] = hq[lane * 8 + j];
+      sum += c[j];
+    }
+    uint64_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    // the lane whose 8 digits hold the need-th key
+    const uint64_t need = s.need;
+    const uint32_t mine = __ballot_sync(kFull, incl >= need && incl - sum < need);
+    if (!mine) {  // fewer rows in play than needed (cannot happen): keep every row
+      if (lane == 0) {
+        s.thresh = ~0ull;
+        s.state = 2;
+      }
+      continue;
+    }
+    const int owner = __ffs(mine) - 1;
+    uint32_t v = 0;
+    uint64_t below = 0, bucket = 0;
+    if (lane == owner) {
+      uint64_t run = incl - sum;
+      for (int j = 0; j < 8; ++j) {
+        if (run + c[j] >= need) { v = lane * 8 + j; below = run; bucket = c[j]; break; }
+        run += c[j];
+      }
+    }
+    v = __shfl_sync(kFull, v, owner);
+    below = __shfl_sync(kFull, below, owner);
+    bucket = __shfl_sync(kFull, bucket, owner);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) hq[lane * 8 + j] = 0;
+    if (lane == 0) {
+      s.need = need - below;
+      s.prefix |= (uint64_t)v << s.shift;
+      s.mbits = s.shift;
+      if (s.shift == 0 || bucket - s.need <= W.dq[qi].cap / 8 || last) {
+        sel_finish(s);
+      } else {
+        s.width = min(8u, s.shift);
+        s.shift -= s.width;
+      }
+    }
+  }
+}
+
+// Rows of a cut query with key <= thresh, packed at the front of its range
+// (order does not matter: the sort follows); other rows are copied as they
+// are.  One atomic per warp and query.
+__global__ void k_sel_compact(Wave W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout) {
+  const uint64_t n = W.ctrl->len[6];
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint64_t base = gtid() - lane; base < n; base += gthreads()) {
+    const uint64_t i = base + lane;
+    uint32_t qi = 0xFFFFFFFFu;
+    bool cut = false, keep = false;
+    uint64_t key = 0;
+    if (i < n) {
+      qi = seg_of_large(W.qs, W.nq, i, false);
+      key = kin[i];
+      cut = W.sel[qi].state == 2;
+      keep = !cut || key <= W.sel[qi].thresh;
+      if (!cut) {
+        pout[i] = pin[i];
+        kout[i] = key;
+      }
+    }
+    const uint32_t peers = __match_any_sync(kFull, cut && keep ? qi : 0xFFFFFFFFu);
+    if (cut && keep) {
+      const int leader = __ffs(peers) - 1;
+      unsigned long long pos = 0;
+      if (lane == leader) pos = atomicAdd((unsigned long long *)&W.sel[qi].kept, (unsigned long long)__popc(peers));
+      pos = __shfl_sync(peers, pos, leader) + __popc(peers & ((1u << lane) - 1));
+      const uint64_t at = W.qs[qi].lrg_row_base + pos;
+      pout[at] = pin[i];
+      kout[at] = key;
+    }
+  }
+}
+
+// Rows entering the sort and the tile layout after the cut.
+__global__ void __launch_bounds__(1024) k_sort_bases(Wave W) {
+  __shared__ uint64_t sm[32];
+  __shared__ uint64_t carry;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < W.nq; base += blockDim.x) {
+    const uint32_t qi = base + threadIdx.x;
+    uint64_t tiles = 0;
+    if (qi < W.nq) {
+      QState &S = W.qs[qi];
+      if (W.sel[qi].state == 2) S.sort_rows = W.sel[qi].kept;
+      tiles = (S.sort_rows + kTileRows - 1) / kTileRows;
+    }
+    uint64_t x = tiles;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t w = sm[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(kFull, w, o);
+        if (lane >= o) w += y;
+      }
+      sm[lane] = w;
+    }
+    __syncthreads();
+    if (qi < W.nq) W.qs[qi].lrg_tile_base = carry + x - tiles + (warp ? sm[warp - 1] : 0);
+    __syncthreads();
+    if (threadIdx.x == 0) carry += sm[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) W.ctrl->len[7] = carry;
+}
+
+// Tile sort: keys (and row indices) in shared memory, bitonic network; rows
+// are read from the output pool only to order equal keys.
+__global__ void __launch_bounds__(256) k_tile_sort(Wave W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout,
+                                                   uint64_t *kout) {
   __shared__ uint64_t key[kTileRows];
+  __shared__ uint32_t row[kTileRows];
   __shared__ uint32_t idx[kTileRows];
   const uint64_t ntiles = W.ctrl->len[7];
-  const uint32_t b = W.G.idbits;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint32_t qi = seg_of_large(W.qs, W.nq, t, true);
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
-    const uint64_t first = (t - S.lrg_tile_base) * kTileRows;
-    const uint32_t n = (uint32_t)min((uint64_t)kTileRows, S.out_rows - first), k = Q.k;
-    const uint32_t r0 = (uint32_t)(S.out_row_base + first);  // pool index of the tile's first row
+    const uint64_t first = (t - S.lrg_tile_base) * kTileRows, at = S.lrg_row_base + first;
+    const uint32_t n = (uint32_t)min((uint64_t)kTileRows, S.sort_rows - first);
     uint32_t np2 = 1;
     while (np2 < n) np2 <<= 1;
     for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
       idx[i] = i;
       if (i < n) {
-        const uint32_t *x = W.out + S.out_word_base + (first + i) * k;
-        key[i] = pack_key(k, b, [&](uint32_t u) { return x[Q.pos[u]]; });
+        key[i] = kin[at + i];
+        row[i] = pin[at + i];
       }
     }
     __syncthreads();
@@ -1479,7 +1724,7 @@ __global__ void __launch_bounds__(256) k_tile_sort(Wave W, uint32_t *perm, uint6
       if (a >= n) return false;
       if (c >= n) return true;
       if (key[a] != key[c]) return key[a] < key[c];
-      return !out_row_le(W, Q, S, r0 + c, r0 + a);
+      return !out_row_le(W, Q, S, row[c], row[a]);
     };
     for (uint32_t size = 2; size <= np2; size <<= 1)
       for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
@@ -1494,8 +1739,8 @@ __global__ void __launch_bounds__(256) k_tile_sort(Wave W, uint32_t *perm, uint6
         __syncthreads();
       }
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      perm[S.lrg_row_base + first + i] = r0 + idx[i];
-      keys[S.lrg_row_base + first + i] = key[idx[i]];
+      pout[at + i] = row[idx[i]];
+      kout[at + i] = key[idx[i]];
     }
     __syncthreads();
   }
@@ -1516,7 +1761,7 @@ __device__ __forceinline__ MergeTile merge_tile(const Wave &W, uint64_t t, uint6
   MergeTile m;
   m.qi = seg_of_large(W.qs, W.nq, t, true);
   const QState &S = W.qs[m.qi];
-  const uint64_t n = S.out_rows, cap = W.dq[m.qi].cap;
+  const uint64_t n = S.sort_rows, cap = W.dq[m.qi].cap;
   m.base = S.lrg_row_base;
   m.first = (t - S.lrg_tile_base) * kTileRows;
   m.a0 = (m.first / (2 * run)) * 2 * run;
@@ -1640,7 +1885,7 @@ __global__ void k_gather(Wave W, const uint32_t *perm0, const uint32_t *perm1) {
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
     if (i - S.lrg_row_base >= Q.cap) continue;  // past the rows returned
-    const uint32_t row = ((merge_passes(S.out_rows) & 1) ? perm1 : perm0)[i];
+    const uint32_t row = ((merge_passes(S.sort_rows) & 1) ? perm1 : perm0)[i];
     const uint32_t *src = W.out + S.out_word_base + (uint64_t)(row - S.out_row_base) * Q.k;
     uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.lrg_row_base) * Q.k;
     for (uint32_t u = 0; u < Q.k; ++u) dst[u] = src[Q.pos[u]];
@@ -1801,8 +2046,22 @@ void launch_small_sort(const Wave &W, cudaStream_t s, int sms) {
   const unsigned cap = persistent_grid(k_small_sort, sms, 256);
   k_small_sort<<<W.nq < cap ? (W.nq ? W.nq : 1) : cap, 256, 0, s>>>(W);
 }
-void launch_tile_sort(const Wave &W, uint32_t *perm, uint64_t *keys, cudaStream_t s, int sms) {
-  k_tile_sort<<<persistent_grid(k_tile_sort, sms, 256), 256, 0, s>>>(W, perm, keys);
+void launch_sort_keys(const Wave &W, uint32_t *perm, uint64_t *keys, cudaStream_t s, int sms) {
+  k_sort_keys<<<persistent_grid(k_sort_keys, sms), kThreads, 0, s>>>(W, perm, keys);
+}
+void launch_select(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+                   cudaStream_t s, int sms) {
+  k_sel_start<<<blocks_for(W.nq, 256), 256, 0, s>>>(W);
+  for (int r = 0; r < kSelRounds; ++r) {
+    k_sel_hist<<<persistent_grid(k_sel_hist, sms, 256), 256, 0, s>>>(W, kin);
+    k_sel_pick<<<blocks_for((uint64_t)W.nq * 32, 256), 256, 0, s>>>(W, r == kSelRounds - 1);
+  }
+  k_sel_compact<<<persistent_grid(k_sel_compact, sms), kThreads, 0, s>>>(W, pin, kin, pout, kout);
+  k_sort_bases<<<1, 1024, 0, s>>>(W);
+}
+void launch_tile_sort(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+                      cudaStream_t s, int sms) {
+  k_tile_sort<<<persistent_grid(k_tile_sort, sms, 256), 256, 0, s>>>(W, pin, kin, pout, kout);
 }
 void launch_merge_pass(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
                        uint64_t run, cudaStream_t s, int sms) {

@@ -146,6 +146,25 @@ def test_more_embeddings_than_cap_returns_the_smallest_rows():
             assert r.truncated == (o.count > cap)
 
 
+def test_outputs_cut_at_cap_before_sorting():
+    """More than 2,048 rows and more than cap, within 16 x cap: the rows stay
+    on the device, a radix select on the sort keys keeps about cap of them
+    and the sorted first cap equal the oracle's, also when every key shares
+    its top bits (a bound first vertex)."""
+    n = 16
+    g = graph_from_triples(n, complete_digraph_triples(n))
+    og = O.OracleGraph.from_graph(g)
+    dg = gs.DeviceGraph(g)
+    path4 = query(4, [(i, i + 1, 0) for i in range(3)])                       # 43,680 rows
+    bound = query(4, [(i, i + 1, 0) for i in range(3)], vbind=[3, I.UNBOUND, I.UNBOUND, I.UNBOUND])  # 2,730 rows
+    star = query(4, [(1, 0, 0), (2, 0, 0), (3, 0, 0)])                        # 43,680 rows, centre last in keys
+    for q, cap in ((path4, 3000), (path4, 2731), (bound, 300), (bound, 2729), (star, 4096)):
+        r = gs.match_batch(dg, [q], cap=cap)[0]
+        o = O.match(og, q, cap=cap)
+        assert o.count > 2048 and cap < o.count <= 16 * cap
+        assert_same(r, o, cap)
+
+
 def test_chunked_join_with_small_level_buffers(monkeypatch):
     """Partial embeddings that overflow the level budget finish on the
     chunked depth-first path; tiny buffers force many chunks."""
