@@ -556,64 +556,98 @@ gs_status refine_to_fixpoint(gs_batch *b) {
   }
 }
 
-gs_status run_waves(gs_batch *b) {
+// A run of a batch: every wave in two halves.  The first half launches the
+// wave's pipeline and, when rows are wanted, copies the large-output flags
+// to pinned host words; the second half, once those words have arrived,
+// sorts the large outputs if there are any and moves the wave's results to
+// the batch store.
+static gs_status run_reset(gs_batch *b) {
   GS_CUDA(cudaMemsetAsync(b->W.ctrl->hw, 0, sizeof(b->W.ctrl->hw), b->stream));
   GS_CUDA(cudaMemsetAsync(&b->W.ctrl->wave, 0, sizeof(uint32_t), b->stream));
   GS_CUDA(cudaMemsetAsync(&b->W.ctrl->store_top, 0, sizeof(uint64_t), b->stream));
   if (!b->flag) GS_CUDA(cudaMallocHost((void **)&b->flag, 3 * sizeof(uint64_t)));
-  const bool sorting = rows_wanted(b);
-  for (size_t w = 0; w < b->waves.size(); ++w) {
-    const int K = b->wave_k[w];
-    if (b->use_graph) {
-      gs_status st = capture_k(b, K);
+  b->sorting = rows_wanted(b);
+  return GS_OK;
+}
+
+static gs_status wave_begin(gs_batch *b, size_t w) {
+  const int K = b->wave_k[w];
+  if (b->use_graph) {
+    gs_status st = capture_k(b, K);
+    if (st != GS_OK) return st;
+    GS_CUDA(cudaGraphLaunch(b->execs[K], b->stream));
+    b->kernel_launches += b->kernels_per_exec[K];
+  } else {
+    enqueue_wave(b, K, false, &b->evs);
+    if (b->fixpoint) {
+      gs_status st = refine_to_fixpoint(b);
       if (st != GS_OK) return st;
-      GS_CUDA(cudaGraphLaunch(b->execs[K], b->stream));
-      b->kernel_launches += b->kernels_per_exec[K];
-    } else {
-      enqueue_wave(b, K, false, &b->evs);
-      if (b->fixpoint) {
-        gs_status st = refine_to_fixpoint(b);
-        if (st != GS_OK) return st;
-      }
-      enqueue_wave_tail(b, K, false, &b->evs, 0);
     }
-    bool large = false;
-    if (sorting) {  // any output too large for the one-block sort?
-      GS_CUDA(cudaMemcpyAsync(b->flag, &b->W.ctrl->len[6], sizeof(uint64_t), cudaMemcpyDeviceToHost, b->stream));
-      GS_CUDA(cudaMemcpyAsync(b->flag + 1, &b->W.ctrl->max_large_rows, sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                              b->stream));
-      GS_CUDA(cudaMemcpyAsync(b->flag + 2, &b->W.ctrl->over_cap, sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                              b->stream));
-      GS_CUDA(cudaStreamSynchronize(b->stream));
-      large = b->flag[0] != 0;
-      if (large) {
-        Pipe P{b, &b->sort_evs_direct, false, b->stream};
-        enqueue_large_sort(P, b->flag[1], b->flag[2]);
-        b->kernel_launches += large_sort_launches(b->flag[1], b->flag[2]);
-        b->large_sorts++;
-      }
-    }
+    enqueue_wave_tail(b, K, false, &b->evs, 0);
+  }
+  if (b->sorting) {  // any output too large for the one-block sort?
+    GS_CUDA(cudaMemcpyAsync(b->flag, &b->W.ctrl->len[6], sizeof(uint64_t), cudaMemcpyDeviceToHost, b->stream));
+    GS_CUDA(cudaMemcpyAsync(b->flag + 1, &b->W.ctrl->max_large_rows, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                            b->stream));
+    GS_CUDA(cudaMemcpyAsync(b->flag + 2, &b->W.ctrl->over_cap, sizeof(uint64_t), cudaMemcpyDeviceToHost, b->stream));
+  }
+  return GS_OK;
+}
+
+static gs_status wave_end(gs_batch *b, size_t w) {
+  const int K = b->wave_k[w];
+  if (b->sorting && b->flag[0] != 0) {
+    Pipe P{b, &b->sort_evs_direct, false, b->stream};
+    enqueue_large_sort(P, b->flag[1], b->flag[2]);
+    b->kernel_launches += large_sort_launches(b->flag[1], b->flag[2]);
+    b->large_sorts++;
+  }
+  if (b->use_graph) {
+    GS_CUDA(cudaGraphLaunch(b->epi_exec, b->stream));
+    b->kernel_launches += b->epi_kernels;
+  } else {
+    Pipe P{b, &b->evs, false, b->stream};
+    enqueue_epilogue(P);
+  }
+  if (b->stats_on) {
+    GS_CUDA(cudaStreamSynchronize(b->stream));
     if (b->use_graph) {
-      GS_CUDA(cudaGraphLaunch(b->epi_exec, b->stream));
-      b->kernel_launches += b->epi_kernels;
+      harvest_events(b, b->graph_evs[K], false);
+      harvest_events(b, b->sort_evs_direct, true);
+      harvest_events(b, b->epi_evs, false);
     } else {
-      Pipe P{b, &b->evs, false, b->stream};
-      enqueue_epilogue(P);
-    }
-    if (b->stats_on) {
-      GS_CUDA(cudaStreamSynchronize(b->stream));
-      if (b->use_graph) {
-        harvest_events(b, b->graph_evs[K], false);
-        harvest_events(b, b->sort_evs_direct, true);
-        harvest_events(b, b->epi_evs, false);
-      } else {
-        harvest_events(b, b->evs, true);
-      }
+      harvest_events(b, b->evs, true);
     }
   }
+  return GS_OK;
+}
+
+gs_status run_waves(gs_batch *b) {
+  gs_status st = run_reset(b);
+  for (size_t w = 0; w < b->waves.size() && st == GS_OK; ++w) {
+    st = wave_begin(b, w);
+    if (st == GS_OK && b->sorting) GS_CUDA(cudaStreamSynchronize(b->stream));
+    if (st == GS_OK) st = wave_end(b, w);
+  }
+  if (st != GS_OK) return st;
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
+
+gs_status run_begin(gs_batch *b) {
+  if (b->waves.size() != 1) return fail(GS_ERR_INVALID, "run_begin: one wave only");
+  gs_status st = run_reset(b);
+  if (st == GS_OK) st = wave_begin(b, 0);
+  return st;
+}
+
+gs_status run_end(gs_batch *b) {
+  gs_status st = wave_end(b, 0);
+  if (st != GS_OK) return st;
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
 static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match_opts *opts) {
   b->n = n;
   b->hq.assign(n, DQuery{});

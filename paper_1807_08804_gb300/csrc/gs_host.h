@@ -108,6 +108,7 @@ struct gs_batch {
   std::vector<Ev> epi_evs;
   uint64_t epi_kernels = 0;
   uint64_t *flag = nullptr;        // pinned words read between graphs
+  bool sorting = false;            // this run wants rows (reads the large-output flags)
   uint64_t large_sorts = 0;
   uint64_t fallbacks = 0;          // queries finished on the chunked path by the last finish
   uint64_t regrows = 0;            // times pools were enlarged after a run
@@ -123,6 +124,11 @@ bool batch_rearm(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match_opt
 gs_status batch_create_capacity(gs_graph *g, const gs_match_opts *opts, uint32_t n_cap, uint32_t nqv_s, uint32_t nqe_s,
                                 gs_batch **out);
 gs_status run_waves(gs_batch *b);
+// The two halves of a one-wave run, for callers that must not block: after
+// run_begin, wait (poll an event recorded on the batch's stream) before
+// run_end.
+gs_status run_begin(gs_batch *b);
+gs_status run_end(gs_batch *b);
 gs_status batch_finish(gs_batch *b);
 gs_status batch_fetch(gs_batch *b, gs_result *outs);
 // Finish query i of a finished run on the host-driven path (chunked join).

@@ -44,10 +44,15 @@ struct Done {
   double latency_s;
 };
 
+// A slot runs one micro-batch at a time in two halves on its own stream
+// (phase 1: the pipeline graph and the copy of the large-output flags;
+// phase 2: the large-output sort if needed and the epilogue), each ended by
+// an event the worker polls, so that no slot blocks the others.
 struct Slot {
   gs_batch *b = nullptr;
   cudaEvent_t ev = nullptr;
   bool busy = false;
+  int phase = 0;
   std::vector<Req> reqs;
   uint64_t est = 0;
   gs_match_opts opts{};
@@ -135,11 +140,21 @@ std::vector<Req> admit(gs_server *s, uint64_t &est_sum) {
   return take;
 }
 
+// Start a micro-batch on a free slot.  The slot owns the requests from the
+// start, so that a failure completes every one of them with the error.
 gs_status launch(gs_server *s, Slot &sl, std::vector<Req> &&reqs, uint64_t est) {
+  sl.reqs = std::move(reqs);
+  sl.est = est;
+  sl.busy = true;
+  sl.phase = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto &r : sl.reqs) s->inflight[r.ticket] = (int)(&sl - s->slots.data());
+  }
   std::vector<gs_query> qs;
-  qs.reserve(reqs.size());
-  for (auto &r : reqs) qs.push_back(r.view());
-  const gs_match_opts &o = reqs.front().opts;
+  qs.reserve(sl.reqs.size());
+  for (auto &r : sl.reqs) qs.push_back(r.view());
+  const gs_match_opts &o = sl.reqs.front().opts;
   if (!sl.b || !batch_rearm(sl.b, qs.data(), (uint32_t)qs.size(), &o)) {
     if (sl.b) batch_destroy(sl.b);
     sl.b = nullptr;
@@ -147,19 +162,42 @@ gs_status launch(gs_server *s, Slot &sl, std::vector<Req> &&reqs, uint64_t est) 
     if (st != GS_OK) return st;
     if (!batch_rearm(sl.b, qs.data(), (uint32_t)qs.size(), &o)) return fail(GS_ERR_INVALID, "serving slot too small");
   }
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    for (auto &r : reqs) s->inflight[r.ticket] = (int)(&sl - s->slots.data());
-  }
-  sl.reqs = std::move(reqs);
-  sl.est = est;
   sl.opts = o;
-  sl.busy = true;
-  gs_status st = run_waves(sl.b);
-  sl.b->ran = st == GS_OK;
+  sl.b->ran = false;
+  gs_status st = run_begin(sl.b);
   if (st != GS_OK) return st;
   GS_CUDA(cudaEventRecord(sl.ev, sl.b->stream));
+  sl.phase = 1;
   return GS_OK;
+}
+
+// The pipeline half has completed (its flags are on the host): launch the tail.
+gs_status launch_tail(Slot &sl) {
+  gs_status st = run_end(sl.b);
+  if (st != GS_OK) return st;
+  sl.b->ran = true;
+  GS_CUDA(cudaEventRecord(sl.ev, sl.b->stream));
+  sl.phase = 2;
+  return GS_OK;
+}
+
+// A slot whose launch failed: its requests complete with the error.
+void fail_slot(gs_server *s, Slot &sl, gs_status st) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->worker_error = st;
+  s->worker_msg = gs_last_error();
+  for (auto &r : sl.reqs) {
+    Done d;
+    memset(&d.r, 0, sizeof(d.r));
+    d.r.status = st;
+    d.latency_s = 0;
+    s->inflight.erase(r.ticket);
+    s->done.emplace(r.ticket, d);
+  }
+  s->inflight_est -= sl.est;
+  sl.reqs.clear();
+  sl.busy = false;
+  sl.phase = 0;
 }
 
 void worker_main(gs_server *s) {
@@ -168,10 +206,15 @@ void worker_main(gs_server *s) {
   for (;;) {
     bool worked = false;
     for (Slot &sl : s->slots) {
-      if (sl.busy && cudaEventQuery(sl.ev) == cudaSuccess) {
+      if (!sl.busy || cudaEventQuery(sl.ev) != cudaSuccess) continue;
+      if (sl.phase == 1) {
+        gs_status st = launch_tail(sl);
+        if (st != GS_OK) fail_slot(s, sl, st);
+      } else {
         harvest(s, sl);
-        worked = true;
+        sl.phase = 0;
       }
+      worked = true;
     }
     for (Slot &sl : s->slots) {
       if (sl.busy) continue;
@@ -179,22 +222,7 @@ void worker_main(gs_server *s) {
       std::vector<Req> reqs = admit(s, est);
       if (reqs.empty()) break;
       gs_status st = launch(s, sl, std::move(reqs), est);
-      if (st != GS_OK) {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->worker_error = st;
-        s->worker_msg = gs_last_error();
-        for (auto &r : sl.reqs) {
-          Done d;
-          memset(&d.r, 0, sizeof(d.r));
-          d.r.status = st;
-          d.latency_s = 0;
-          s->inflight.erase(r.ticket);
-          s->done.emplace(r.ticket, d);
-        }
-        s->inflight_est -= sl.est;
-        sl.reqs.clear();
-        sl.busy = false;
-      }
+      if (st != GS_OK) fail_slot(s, sl, st);
       worked = true;
     }
     std::unique_lock<std::mutex> lk(s->mu);
