@@ -1181,6 +1181,15 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Wave W, uint32_t s) {
   const uint64_t items = W.ctrl->len[3];
   const uint32_t *lvl = W.lvl[s & 1];
   uint64_t acc = 0;
+  uint32_t run_q = 0xFFFFFFFFu;
+  uint64_t run_cnt = 0, run_fp = 0;
+  auto flush_run = [&]() {
+    if (run_q == 0xFFFFFFFFu) return;
+    QState &R = W.qs[run_q];
+    if (run_cnt) atomicAdd((unsigned long long *)&R.count, (unsigned long long)run_cnt);
+    if (run_fp) atomicAdd((unsigned long long *)&R.fp, (unsigned long long)run_fp);
+    run_cnt = run_fp = 0;
+  };
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
     const uint32_t qi = tile_seg<G>(tile, W.nq, it, [&](uint32_t s) { return W.qs[s].cur_row_base; });
     const DQuery &Q = W.dq[qi];
@@ -1210,13 +1219,20 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Wave W, uint32_t s) {
     }
     if (r == 0) {
       W.row_cnt[it] = cnt;
-      if (live && Q.k == s + 2) {
-        if (cnt) atomicAdd((unsigned long long *)&S.count, (unsigned long long)cnt);
-        if (fp) atomicAdd((unsigned long long *)&S.fp, (unsigned long long)fp);
+      if (live && Q.k == s + 2 && (cnt || fp)) {
+        // a query's final embeddings are summed in registers while the
+        // tile's items stay in that query, then added with one atomic pair
+        if (run_q != qi) {
+          flush_run();
+          run_q = qi;
+        }
+        run_cnt += cnt;
+        run_fp += fp;
       }
       acc += bytes;
     }
   }
+  if (r == 0) flush_run();
   flush_bytes(W, KK_JOIN_COUNT, acc);
 }
 
