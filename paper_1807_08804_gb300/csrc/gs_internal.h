@@ -80,16 +80,17 @@ void release_fallback(gs_graph *g);
 // ------------------------------------------------------------ primitives
 // Exclusive prefix sum of n uint32 counts into out[0..n] (out[n] = total),
 // where n is read from device memory (*d_n), in one kernel (single-pass scan
-// with decoupled look-back).  max_n bounds n and sizes the launch.  tmp
-// holds scan_tmp_words(max_n) uint64 words that are zeroed once when
-// allocated and used by nothing but scans; scans that share it must run in
-// order (one stream).  scan_error_word() points at a device word that turns
-// non-zero if a look-back wait ever hit its bound on that scratch (a scan
-// result may then be wrong).
+// with decoupled look-back, after a memset of its tile counter and
+// descriptors).  max_n bounds n and sizes the launch.  tmp holds
+// scan_tmp_words(max_n) uint64 words, zeroed once when allocated and used by
+// nothing but scans; scans that share it must run in order (one stream).
+// scan_error_word() points at a device word that turns non-zero if a
+// look-back wait ever hit its bound on that scratch (a scan result may then
+// be wrong).
 uint64_t scan_tmp_words(uint64_t max_n);
 void scan_u32(const uint32_t *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp,
               cudaStream_t s, int num_sms);
-inline const uint32_t *scan_error_word(const uint64_t *tmp) { return reinterpret_cast<const uint32_t *>(tmp) + 3; }
+inline const uint32_t *scan_error_word(const uint64_t *tmp) { return reinterpret_cast<const uint32_t *>(tmp); }
 // Same for uint64 inputs.
 void scan_u64(const uint64_t *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp,
               cudaStream_t s, int num_sms);

@@ -29,25 +29,23 @@ constexpr int kRadixBins = 256;
 // its inclusive prefix, and publishes its own.  A block only waits on tiles
 // claimed before its own, by blocks that are already running, so the waits
 // end; each is bounded all the same and records an error when the bound is
-// hit.  Descriptors carry the scan's epoch, so the scratch needs zeroing
-// only once, when it is allocated; the last block to finish resets the tile
-// counter and advances the epoch for the next scan on the same scratch.
+// hit.  The tile counter and the descriptors are zeroed by a memset in
+// front of every scan; the error word before them is sticky.
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr uint64_t kScanTile = (uint64_t)kScanThreads * kScanItems;  // 2048
 constexpr uint32_t kLookbackLimit = 1u << 22;
-constexpr uint32_t kEpochMask = (1u << 30) - 1;  // epochs wrap after 2^30 scans
 
-struct ScanState {  // the first 16 bytes of the scratch (the error word is read by scan_error_word)
-  uint32_t tiles;  // next tile to claim
-  uint32_t done;   // blocks finished
-  uint32_t epoch;  // scans completed on this scratch
-  uint32_t err;    // a look-back wait hit its bound
+struct ScanState {  // the first 16 bytes of the scratch
+  uint32_t err;     // a look-back wait hit its bound (sticky; read by scan_error_word)
+  uint32_t pad0;
+  uint32_t tiles;   // next tile to claim (zeroed before each scan)
+  uint32_t pad1;
 };
 struct __align__(32) ScanDesc {
   uint64_t agg;   // the tile's total
   uint64_t incl;  // prefix through the tile
-  uint32_t flag;  // (epoch << 2) | 1 (aggregate) or 2 (inclusive)
+  uint32_t flag;  // 0: nothing yet, 1: aggregate, 2: inclusive prefix
   uint32_t pad[3];
 };
 static_assert(sizeof(ScanState) == 16 && sizeof(ScanDesc) == 32, "scan scratch layout");
@@ -87,7 +85,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
   __shared__ uint64_t s_prefix;
   const uint64_t n = *d_n;
   const uint64_t ntiles = (n + kScanTile - 1) / kScanTile;
-  const uint32_t epoch = *reinterpret_cast<volatile uint32_t *>(&st->epoch);
   const int lane = threadIdx.x & 31;
   if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
   for (;;) {
@@ -111,17 +108,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
     }
     uint64_t agg;
     const uint64_t ex = block_scan_excl(sum, &agg, red);
-    const uint32_t tag = (epoch & kEpochMask) << 2;
     if (threadIdx.x == 0) {
       ScanDesc &d = desc[t];
       if (t == 0) {
         __stcg(&d.incl, agg);
         __threadfence();
-        __stcg(&d.flag, tag | 2u);
+        __stcg(&d.flag, 2u);
       } else {
         __stcg(&d.agg, agg);
         __threadfence();
-        __stcg(&d.flag, tag | 1u);
+        __stcg(&d.flag, 1u);
       }
     }
     if (threadIdx.x < 32) {  // look-back
@@ -134,7 +130,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
           uint32_t status = 2;  // before tile 0: an inclusive prefix of 0
           if (p >= 0) {
             const uint32_t f = __ldcg(&desc[p].flag);
-            status = (f & ~3u) == tag ? (f & 3u) : 0u;
+            status = f & 3u;
           }
           const uint32_t incl_mask = __ballot_sync(kFull, status == 2);
           const uint32_t zero_mask = __ballot_sync(kFull, status == 0);
@@ -157,7 +153,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
           ScanDesc &d = desc[t];
           __stcg(&d.incl, prefix + agg);
           __threadfence();
-          __stcg(&d.flag, tag | 2u);
+          __stcg(&d.flag, 2u);
         }
       }
       if (lane == 0) s_prefix = prefix;
@@ -174,15 +170,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
     }
     if (t == ntiles - 1 && threadIdx.x == 0) out[n] = s_prefix + agg;
     __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&st->done, 1u) == gridDim.x - 1) {  // every block has stopped claiming tiles
-      st->tiles = 0;
-      st->done = 0;
-      st->epoch = (epoch + 1) & kEpochMask;
-      __threadfence();
-    }
   }
 }
 
@@ -204,13 +191,15 @@ template <typename T>
 void scan_impl(const T *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp, cudaStream_t s,
                int num_sms) {
   const uint64_t tiles = std::max<uint64_t>((max_n + kScanTile - 1) / kScanTile, 1);
-  // at most two blocks per SM: every block claims one tile past the end and
-  // counts itself done with an atomic, so a small scan sized for a large
-  // max_n stays cheap; large scans loop over tiles
+  // at most two blocks per SM: every block claims one tile past the end, so
+  // a small scan sized for a large max_n stays cheap; large scans loop over
+  // tiles
   const uint64_t cap = (uint64_t)num_sms * std::min(2, scan_resident((const void *)k_scan<T>));
   const unsigned grid = (unsigned)std::min(tiles, cap);
   ScanState *st = reinterpret_cast<ScanState *>(tmp);
-  ScanDesc *desc = reinterpret_cast<ScanDesc *>(tmp + 4);
+  ScanDesc *desc = reinterpret_cast<ScanDesc *>(tmp + 4);  // 32 bytes in
+  // the counter (bytes 8-15) through the last descriptor, inside scan_tmp_words(max_n)
+  cudaMemsetAsync(&st->tiles, 0, 24 + sizeof(ScanDesc) * tiles, s);
   k_scan<T><<<grid, kScanThreads, 0, s>>>(in, d_n, out, st, desc);
 }
 
