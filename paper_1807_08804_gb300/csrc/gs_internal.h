@@ -80,10 +80,10 @@ void release_fallback(gs_graph *g);
 // ------------------------------------------------------------ primitives
 // Exclusive prefix sum of n uint32 counts into out[0..n] (out[n] = total),
 // where n is read from device memory (*d_n), in one kernel (single-pass scan
-// with decoupled look-back, after a memset of its tile counter and
-// descriptors).  max_n bounds n and sizes the launch.  tmp holds
-// scan_tmp_words(max_n) uint64 words, zeroed once when allocated and used by
-// nothing but scans; scans that share it must run in order (one stream).
+// with decoupled look-back).  max_n bounds n and sizes the launch.  tmp
+// holds scan_tmp_words(max_n) uint64 words, zeroed once when allocated and
+// used by nothing but scans; scans that share it must run in order (one
+// stream).
 // scan_error_word() points at a device word that turns non-zero if a
 // look-back wait ever hit its bound on that scratch (a scan result may then
 // be wrong).

@@ -29,26 +29,30 @@ constexpr int kRadixBins = 256;
 // its inclusive prefix, and publishes its own.  A block only waits on tiles
 // claimed before its own, by blocks that are already running, so the waits
 // end; each is bounded all the same and records an error when the bound is
-// hit.  The tile counter and the descriptors are zeroed by a memset in
-// front of every scan; the error word before them is sticky.
+// hit.  Descriptors carry the scan's 62-bit epoch, so the scratch needs
+// zeroing only once, when it is allocated; the last block to finish resets
+// the tile counter and advances the epoch for the next scan on the same
+// scratch.
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr uint64_t kScanTile = (uint64_t)kScanThreads * kScanItems;  // 2048
 constexpr uint32_t kLookbackLimit = 1u << 22;
 
-struct ScanState {  // the first 16 bytes of the scratch
+struct ScanState {  // the first 32 bytes of the scratch
   uint32_t err;     // a look-back wait hit its bound (sticky; read by scan_error_word)
-  uint32_t pad0;
-  uint32_t tiles;   // next tile to claim (zeroed before each scan)
-  uint32_t pad1;
+  uint32_t tiles;   // next tile to claim
+  uint32_t done;    // blocks finished
+  uint32_t pad;
+  uint64_t epoch;   // scans completed on this scratch
+  uint64_t pad2;
 };
 struct __align__(32) ScanDesc {
   uint64_t agg;   // the tile's total
   uint64_t incl;  // prefix through the tile
-  uint32_t flag;  // 0: nothing yet, 1: aggregate, 2: inclusive prefix
-  uint32_t pad[3];
+  uint64_t flag;  // (epoch << 2) | 1 (aggregate) or 2 (inclusive)
+  uint64_t pad;
 };
-static_assert(sizeof(ScanState) == 16 && sizeof(ScanDesc) == 32, "scan scratch layout");
+static_assert(sizeof(ScanState) == 32 && sizeof(ScanDesc) == 32, "scan scratch layout");
 
 __device__ __forceinline__ uint64_t block_scan_excl(uint64_t v, uint64_t *total, uint64_t *smem) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -85,6 +89,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
   __shared__ uint64_t s_prefix;
   const uint64_t n = *d_n;
   const uint64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  const uint64_t tag = *reinterpret_cast<volatile uint64_t *>(&st->epoch) << 2;
   const int lane = threadIdx.x & 31;
   if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
   for (;;) {
@@ -113,11 +118,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
       if (t == 0) {
         __stcg(&d.incl, agg);
         __threadfence();
-        __stcg(&d.flag, 2u);
+        __stcg(&d.flag, tag | 2u);
       } else {
         __stcg(&d.agg, agg);
         __threadfence();
-        __stcg(&d.flag, 1u);
+        __stcg(&d.flag, tag | 1u);
       }
     }
     if (threadIdx.x < 32) {  // look-back
@@ -129,8 +134,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
           const int64_t p = pos - lane;
           uint32_t status = 2;  // before tile 0: an inclusive prefix of 0
           if (p >= 0) {
-            const uint32_t f = __ldcg(&desc[p].flag);
-            status = f & 3u;
+            const uint64_t f = __ldcg(&desc[p].flag);
+            status = (f & ~3ull) == tag ? (uint32_t)(f & 3u) : 0u;
           }
           const uint32_t incl_mask = __ballot_sync(kFull, status == 2);
           const uint32_t zero_mask = __ballot_sync(kFull, status == 0);
@@ -153,7 +158,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
           ScanDesc &d = desc[t];
           __stcg(&d.incl, prefix + agg);
           __threadfence();
-          __stcg(&d.flag, 2u);
+          __stcg(&d.flag, tag | 2u);
         }
       }
       if (lane == 0) s_prefix = prefix;
@@ -170,6 +175,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
     }
     if (t == ntiles - 1 && threadIdx.x == 0) out[n] = s_prefix + agg;
     __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&st->done, 1u) == gridDim.x - 1) {  // every block has stopped claiming tiles
+      st->tiles = 0;
+      st->done = 0;
+      st->epoch = (tag >> 2) + 1;
+      __threadfence();
+    }
   }
 }
 
@@ -191,15 +205,13 @@ template <typename T>
 void scan_impl(const T *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp, cudaStream_t s,
                int num_sms) {
   const uint64_t tiles = std::max<uint64_t>((max_n + kScanTile - 1) / kScanTile, 1);
-  // at most two blocks per SM: every block claims one tile past the end, so
-  // a small scan sized for a large max_n stays cheap; large scans loop over
-  // tiles
+  // at most two blocks per SM: every block claims one tile past the end and
+  // counts itself done with an atomic, so a small scan sized for a large
+  // max_n stays cheap; large scans loop over tiles
   const uint64_t cap = (uint64_t)num_sms * std::min(2, scan_resident((const void *)k_scan<T>));
   const unsigned grid = (unsigned)std::min(tiles, cap);
   ScanState *st = reinterpret_cast<ScanState *>(tmp);
   ScanDesc *desc = reinterpret_cast<ScanDesc *>(tmp + 4);  // 32 bytes in
-  // the counter (bytes 8-15) through the last descriptor, inside scan_tmp_words(max_n)
-  cudaMemsetAsync(&st->tiles, 0, 24 + sizeof(ScanDesc) * tiles, s);
   k_scan<T><<<grid, kScanThreads, 0, s>>>(in, d_n, out, st, desc);
 }
 
