@@ -418,7 +418,6 @@ void enqueue_back(Pipe &P, int K, int stop) {
     P.end();
     P.begin(KK_SCAN);
     scan_u32(W.row_cnt, W.row_scan, &W.ctrl->len[3], W.row_cap, b->scan_tmp, P.cur, sms);
-    launch_join_totals(W, P.cur, sms);
     launch_level_alloc(W, lvl + 1, P.cur);
     P.end();
     P.begin(KK_JOIN_WRITE);

@@ -214,7 +214,6 @@ void launch_ec(const Wave &W, bool write, int group, cudaStream_t s, int sms);
 void launch_clear(const Wave &W, cudaStream_t s, int sms);
 void launch_join0(const Wave &W, cudaStream_t s, int sms);
 void launch_join_count(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms);
-void launch_join_totals(const Wave &W, cudaStream_t s, int sms);
 void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s);
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms);
 void launch_final_bases(const Wave &W, cudaStream_t s);

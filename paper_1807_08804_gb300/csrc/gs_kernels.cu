@@ -528,6 +528,10 @@ __global__ void __launch_bounds__(kThreads) k_chunk_list(Wave W, int mode, uint3
     uint32_t s, gqv = 0;
     const uint32_t *slot;
     const uint32_t m = group_word(W, mode, step, it, s, slot);
+    // every chunk count of the group starts at zero (the count kernel fills
+    // in the listed ones)
+    const uint32_t c0 = (uint32_t)(it % G.ipg) * 32 + lane;
+    if (c0 < G.nchunks) W.ccount[(uint64_t)s * G.nchunks + c0] = 0;
     if (!m) continue;
     sel_slot(W, mode, step, s, gqv);
     unsigned long long base = 0;
@@ -540,9 +544,9 @@ __global__ void __launch_bounds__(kThreads) k_chunk_list(Wave W, int mode, uint3
   }
 }
 
-// Candidates per listed chunk (the others were zeroed before the list was
-// built).  Lane j owns level-1 word j and counts its level-0 words; the
-// level-1 words of kCU chunks are loaded together.
+// Candidates per listed chunk (the list kernel zeroed every count).  Lane j
+// owns level-1 word j and counts its level-0 words; the level-1 words of kCU
+// chunks are loaded together.
 __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W) {
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
@@ -1023,6 +1027,18 @@ __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
   __shared__ uint64_t sm[4][32];
   __shared__ uint64_t carry[4];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lvl > 0) {
+    // after a count pass: rows produced per query (from the scan of the
+    // per-row counts), and the current level kept aside as the source of
+    // the write pass
+    for (uint32_t qi = threadIdx.x; qi < W.nq; qi += blockDim.x) {
+      QState &S = W.qs[qi];
+      S.nxt_rows = S.cur_rows ? W.row_scan[S.cur_row_base + S.cur_rows] - W.row_scan[S.cur_row_base] : 0;
+      W.src[qi] = SrcRows{S.cur_row_base, S.cur_rows, S.cur_word_base};
+    }
+    if (threadIdx.x == 0) W.ctrl->len[4] = W.ctrl->len[3];
+    __syncthreads();
+  }
   for (int pass = 0; pass < 2; ++pass) {
     if (threadIdx.x == 0) {
       carry[0] = 0; carry[1] = 0;
@@ -1234,17 +1250,6 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Wave W, uint32_t s) {
   }
   if (r == 0) flush_run();
   flush_bytes(W, KK_JOIN_COUNT, acc);
-}
-
-// Rows produced per query (scan of the per-row counts), and the current
-// level kept aside as the source of the write pass.
-__global__ void k_join_totals(Wave W) {
-  for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
-    QState &S = W.qs[qi];
-    S.nxt_rows = S.cur_rows ? W.row_scan[S.cur_row_base + S.cur_rows] - W.row_scan[S.cur_row_base] : 0;
-    W.src[qi] = SrcRows{S.cur_row_base, S.cur_rows, S.cur_word_base};
-  }
-  if (gtid() == 0) W.ctrl->len[4] = W.ctrl->len[3];
 }
 
 // Write pass of level s -> s+1 into the layout made by k_level_alloc.
@@ -1989,7 +1994,6 @@ void launch_filter(const Wave &W, cudaStream_t s, int sms) {
 }
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms) {
   const uint64_t sets = mode == 0 ? W.nq : W.nqv;
-  cudaMemsetAsync(W.ccount, 0, sizeof(uint32_t) * sets * W.G.nchunks, s);
   cudaMemsetAsync(&W.ctrl->len[9], 0, sizeof(uint64_t), s);
   k_chunk_list<<<grid_items(k_chunk_list, sets * W.G.ipg, sms), kThreads, 0, s>>>(W, mode, step);
   k_compact_count<<<persistent_grid(k_compact_count, sms), kThreads, 0, s>>>(W);
@@ -2044,9 +2048,6 @@ void launch_join_count(const Wave &W, uint32_t lvl, int group, cudaStream_t s, i
     case 16: k_join_count<16><<<persistent_grid(k_join_count<16>, sms), kThreads, 0, s>>>(W, lvl); break;
     default: k_join_count<32><<<persistent_grid(k_join_count<32>, sms), kThreads, 0, s>>>(W, lvl); break;
   }
-}
-void launch_join_totals(const Wave &W, cudaStream_t s, int sms) {
-  k_join_totals<<<blocks_for(W.nq, 256), 256, 0, s>>>(W);
 }
 void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s) { k_level_alloc<<<1, 1024, 0, s>>>(W, lvl); }
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms) {
