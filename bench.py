@@ -259,8 +259,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--tune-cache", default=os.path.join(ROOT, "paper_1807_08804_gb300", "_build", "tune_cache.txt"),
                     help="autotuner cache file: a choice made once for this graph, GPU and load is reused")
-    ap.add_argument("--mode", default=None, choices=["enumerate", "count"],
-                    help="enumerate rows (default) or count only (default for stress-16m)")
+    ap.add_argument("--mode", default=None, choices=["enumerate", "count", "chunked"],
+                    help="enumerate rows (default), count only (default for stress-16m), or stream every "
+                         "embedding through the chunk callback (chunked enumeration)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -278,21 +279,32 @@ def main():
     qs = w.queries(g)
     n = len(qs)
     mode = args.mode or ("count" if w.shapes else "enumerate")
-    gmode = gs.GS_COUNT_ONLY if mode == "count" else gs.GS_ENUMERATE
-    cap = 0 if mode == "count" else w.cap
+    gmode = {"count": gs.GS_COUNT_ONLY, "chunked": gs.GS_CHUNKED}.get(mode, gs.GS_ENUMERATE)
+    cap = 0 if mode != "enumerate" else w.cap
+    streamed = [0]  # rows delivered to the chunk callback (chunked mode)
+
+    def on_chunk(ptr, n_rows, k, query):  # device pointer, nothing copied
+        streamed[0] += n_rows
+
+    chunk_cb = on_chunk if mode == "chunked" else None
+    chunk_bytes = (8 << 30) if mode == "chunked" else 0  # 8 GB output chunks
     dg = gs.DeviceGraph(g)
     tuned = None
     if not args.no_tune:  # untimed
         os.makedirs(os.path.dirname(os.path.abspath(args.tune_cache)), exist_ok=True)
-        tuned = gs.tune(dg, qs, cap=cap, mode=gmode, cache_path=args.tune_cache)
+        # chunked mode runs the count-only pipeline on the device and streams
+        # on the chunked join, so it is tuned as count-only
+        tuned = gs.tune(dg, qs, cap=cap, mode=gs.GS_COUNT_ONLY if mode == "chunked" else gmode,
+                        cache_path=args.tune_cache)
     # A dedicated stream: the library launches on it and the CUDA events are
     # recorded on it (the legacy default stream would not order with it).
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     sh = stream.cuda_stream
     assert sh != 0
-    b = gs.Batch(dg, qs, cap=cap, mode=gmode, stream=sh)
-    one = gs.Batch(dg, qs, cap=cap, mode=gmode, wave_queries=1, stream=sh)
+    b = gs.Batch(dg, qs, cap=cap, mode=gmode, stream=sh, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, raw_chunks=True)
+    one = gs.Batch(dg, qs, cap=cap, mode=gmode, wave_queries=1, stream=sh, chunk_bytes=chunk_bytes, on_chunk=chunk_cb,
+                   raw_chunks=True)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     for _ in range(max(args.warmup, 3)):
@@ -301,7 +313,9 @@ def main():
     res = b.fetch()
     embeddings = sum(r.count for r in res)
     bad = [i for i, r in enumerate(res) if r.status != 0]
-    fallback_needed = b.counters().get("fallback_queries", 0) > 0
+    # queries that finish on the chunked path (and, in chunked mode, the
+    # streaming itself) run inside the timed steps
+    fallback_needed = b.counters().get("fallback_queries", 0) > 0 or mode == "chunked"
     if args.one_steps:
         one.run()
         one.finish()
@@ -314,6 +328,7 @@ def main():
     b.finish()
     b.stats_reset()
     launches0 = b.counters()["kernel_launches"]
+    streamed[0] = 0
     clocks = ClockSampler(local)
     clocks.start()
     barrier(world)
@@ -333,7 +348,9 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
-    b.finish()
+    streamed_timed = streamed[0]
+    if not fallback_needed:
+        b.finish()
     launches = b.counters()["kernel_launches"] - launches0
     stats = b.stats()
     tot_ms = max_over_ranks(sum(step_ms), world, dev)
@@ -357,14 +374,15 @@ def main():
 
     # ---- end to end through the public API with host buffers
     h0, d0 = dg.io_bytes()
-    gs.match_batch(dg, qs, cap=cap, mode=gmode)  # warm the reusable pools
+    gs.match_batch(dg, qs, cap=cap, mode=gmode, chunk_bytes=chunk_bytes, on_chunk=chunk_cb,
+                   raw_chunks=True)  # warm the reusable pools
     h0, d0 = dg.io_bytes()
     barrier(world)
     torch.cuda.synchronize()
     t = time.perf_counter()
     e2e_steps = max(2, args.steps // 2)
     for _ in range(e2e_steps):
-        out = gs.match_batch(dg, qs, cap=cap, mode=gmode)
+        out = gs.match_batch(dg, qs, cap=cap, mode=gmode, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, raw_chunks=True)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t, world, dev)
     h1, d1 = dg.io_bytes()
@@ -396,6 +414,7 @@ def main():
                        "parallelism": f"replicas x{world}", "tuned": tuned},
             "embeddings_per_s": embeddings * world * args.steps / (tot_ms / 1e3),
             "embeddings_per_step": embeddings,
+            **({"streamed_rows_per_step": streamed_timed / args.steps} if mode == "chunked" else {}),
             "one_at_a_time": ({"value": one_qps, "unit": "queries/s", "ms_per_step": one_tot / args.one_steps,
                                "speedup_batched": value / one_qps} if one_qps else None),
             "e2e": {"value": n * world * e2e_steps / e2e_s, "unit": "queries/s",

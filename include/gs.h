@@ -100,20 +100,37 @@ typedef struct {
 /* gs_match_opts.mode */
 #define GS_ENUMERATE 0u    /* count + fingerprint + smallest `cap` rows */
 #define GS_COUNT_ONLY 1u   /* count + fingerprint, no rows */
+#define GS_CHUNKED 2u      /* count + fingerprint, and EVERY embedding streamed to on_chunk */
+
+/* Chunk callback of GS_CHUNKED: `rows` is a DEVICE pointer to num_rows rows
+ * of k uint32 ids each (row-major, query-vertex order; rows in no particular
+ * order), valid only during the call (copy with gs_memcpy_d2h or a kernel
+ * of the caller's).  `query` is the index of the query in the batch.  The
+ * callback runs on the thread that called gs_match / gs_match_batch /
+ * gs_batch_finish, after the chunk's kernels have completed; it must not
+ * call back into the library except gs_memcpy_d2h. */
+typedef void (*gs_chunk_cb)(const uint32_t *rows, uint64_t num_rows, uint32_t k, uint32_t query, void *user);
 
 typedef struct {
   uint64_t cap;               /* rows to return (0 = none); the count is always exact */
-  uint32_t mode;              /* GS_ENUMERATE or GS_COUNT_ONLY */
+  uint32_t mode;              /* GS_ENUMERATE, GS_COUNT_ONLY or GS_CHUNKED */
   uint32_t max_refine_rounds; /* 0 = refine until nothing changes (Section 3.3.3) */
   uint64_t chunk_bytes;       /* partial-embedding budget per join level before the
-                                 join switches to chunked depth-first expansion;
+                                 join switches to chunked depth-first expansion, and
+                                 (GS_CHUNKED) the size bound of each streamed chunk;
                                  0 = library default (1 GiB) */
   void *cuda_stream;          /* cudaStream_t; NULL = the library's own stream */
+  gs_chunk_cb on_chunk;       /* GS_CHUNKED: required; otherwise ignored */
+  void *user;                 /* passed to on_chunk */
 } gs_match_opts;
+
+/* Synchronous copy of `bytes` bytes from device memory to host memory, for
+ * chunk callbacks.  Returns GS_ERR_CUDA if the copy fails. */
+gs_status gs_memcpy_d2h(void *dst, const void *src, uint64_t bytes);
 
 typedef struct {
   uint64_t count;        /* exact number of embeddings */
-  uint64_t num_rows;     /* rows returned = min(count, cap) */
+  uint64_t num_rows;     /* rows returned = min(count, cap); 0 for GS_CHUNKED */
   uint64_t fingerprint;  /* sum over ALL embeddings of an order-free 64-bit row hash */
   uint32_t k;            /* row width */
   uint32_t truncated;    /* 1 if count > cap */

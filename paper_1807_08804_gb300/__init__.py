@@ -24,7 +24,7 @@ STATUS_NAMES = ["OK", "INVALID", "OOM", "CUDA", "TIMEOUT", "UNSUPPORTED", "BUSY"
 UNBOUND = 0xFFFFFFFF
 ANY = 0xFFFFFFFF
 GS_DEVICE_PTRS = 1
-GS_ENUMERATE, GS_COUNT_ONLY = 0, 1
+GS_ENUMERATE, GS_COUNT_ONLY, GS_CHUNKED = 0, 1, 2
 GS_STAGE_FILTER, GS_STAGE_FIXPOINT = 0, 1
 NUM_KERNEL_KINDS = 16
 
@@ -49,8 +49,13 @@ class QueryDesc(ctypes.Structure):
     _fields_ = [("k", U32), ("m", U32), ("vtype", P), ("vbind", P), ("esrc", P), ("edst", P), ("erel", P)]
 
 
+# void (*)(const uint32_t *rows_dev, uint64_t num_rows, uint32_t k, uint32_t query, void *user)
+ChunkCallback = ctypes.CFUNCTYPE(None, ctypes.c_void_p, U64, U32, U32, ctypes.c_void_p)
+
+
 class MatchOpts(ctypes.Structure):
-    _fields_ = [("cap", U64), ("mode", U32), ("max_refine_rounds", U32), ("chunk_bytes", U64), ("cuda_stream", P)]
+    _fields_ = [("cap", U64), ("mode", U32), ("max_refine_rounds", U32), ("chunk_bytes", U64), ("cuda_stream", P),
+                ("on_chunk", ChunkCallback), ("user", P)]
 
 
 class ResultDesc(ctypes.Structure):
@@ -80,6 +85,7 @@ SIGNATURES = {
     "gs_match": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), ctypes.POINTER(MatchOpts), ctypes.POINTER(ResultDesc)]),
     "gs_match_batch": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts),
                                       ctypes.POINTER(ResultDesc)]),
+    "gs_memcpy_d2h": (ctypes.c_int, [P, ctypes.c_void_p, U64]),
     "gs_result_free": (None, [ctypes.POINTER(ResultDesc)]),
     "gs_results_free": (None, [ctypes.POINTER(ResultDesc), U32]),
     "gs_last_error": (ctypes.c_char_p, []),
@@ -181,8 +187,32 @@ class _QueryPack:
         self.arr = ctypes.cast(d.ctypes.data, ctypes.POINTER(QueryDesc))
 
 
-def _opts(cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0, stream=None) -> MatchOpts:
-    return MatchOpts(cap, mode, max_refine_rounds, chunk_bytes, stream)
+def _opts(cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0, stream=None, on_chunk=None) -> MatchOpts:
+    o = MatchOpts(cap, mode, max_refine_rounds, chunk_bytes, stream)
+    if on_chunk is not None:
+        o.on_chunk = on_chunk
+    return o
+
+
+def _chunk_callback(fn, raw=False):
+    """Wrap fn as the library's chunk callback.  By default fn(rows, query)
+    gets each chunk copied to a uint32 [n, k] array while the call lasts;
+    with raw=True, fn(ptr, n, k, query) gets the device pointer (valid only
+    during the call) and nothing is copied.  The wrapper must stay
+    referenced until the match call returns."""
+    if fn is None:
+        return None
+
+    def cb(ptr, n, k, query, user):
+        if raw:
+            fn(ptr, n, k, query)
+            return
+        rows = np.empty((n, k), np.uint32)
+        if n:
+            _check(lib().gs_memcpy_d2h(rows.ctypes.data_as(P), ctypes.c_void_p(ptr), 4 * n * k))
+        fn(rows, query)
+
+    return ChunkCallback(cb)
 
 
 @dataclass
@@ -274,18 +304,23 @@ class DeviceGraph:
             pass
 
 
-def match(dg: DeviceGraph, q, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0) -> MatchResult:
+def match(dg: DeviceGraph, q, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0,
+          on_chunk=None) -> MatchResult:
+    """on_chunk(rows, query): with mode=GS_CHUNKED, called with every chunk
+    of embeddings (uint32 [n, k], query-vertex order) as it is produced."""
     pack = _QueryPack([q])
-    o = _opts(cap, mode, max_refine_rounds, chunk_bytes)
+    cb = _chunk_callback(on_chunk)
+    o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb)
     r = ResultDesc()
     _check(lib().gs_match(dg._h, pack.arr, ctypes.byref(o), ctypes.byref(r)))
     return _take(r)
 
 
 def match_batch(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0,
-                chunk_bytes=0) -> list[MatchResult]:
+                chunk_bytes=0, on_chunk=None, raw_chunks=False) -> list[MatchResult]:
     pack = _QueryPack(queries)
-    o = _opts(cap, mode, max_refine_rounds, chunk_bytes)
+    cb = _chunk_callback(on_chunk, raw_chunks)
+    o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb)
     res = (ResultDesc * max(len(queries), 1))()
     _check(lib().gs_match_batch(dg._h, pack.arr, len(queries), ctypes.byref(o), res))
     return _take_all(res, len(queries))
@@ -295,11 +330,12 @@ class Batch:
     """A prepared batch (device-resident queries, captured pipeline graph)."""
 
     def __init__(self, dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0,
-                 wave_queries=0, stream=None):
+                 wave_queries=0, stream=None, on_chunk=None, raw_chunks=False):
         self.dg = dg
         self.n = len(queries)
         self._pack = _QueryPack(queries)
-        o = _opts(cap, mode, max_refine_rounds, chunk_bytes, stream)
+        self._cb = _chunk_callback(on_chunk, raw_chunks)  # kept alive: every finish() may call it
+        o = _opts(cap, mode, max_refine_rounds, chunk_bytes, stream, on_chunk=self._cb)
         self._h = P()
         if wave_queries:
             _check(lib().gs_batch_create_waves(dg._h, self._pack.arr, self.n, ctypes.byref(o), wave_queries,

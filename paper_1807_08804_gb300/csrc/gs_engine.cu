@@ -78,7 +78,12 @@ gs_status pack_query(const DevGraph &G, const gs_query *q, const gs_match_opts *
   }
   d->inc_begin[k] = (uint8_t)ni;
   d->need_begin[k] = (uint8_t)nn;
-  d->mode = o ? o->mode : GS_ENUMERATE;
+  const uint32_t mode = o ? o->mode : GS_ENUMERATE;
+  if (mode > GS_CHUNKED) return fail(GS_ERR_INVALID, "unknown match mode");
+  if (mode == GS_CHUNKED && !o->on_chunk) return fail(GS_ERR_INVALID, "GS_CHUNKED needs an on_chunk callback");
+  // a chunked query is counted by the batched pipeline and its embeddings
+  // are streamed by the chunked join when the batch finishes
+  d->mode = mode == GS_CHUNKED ? GS_COUNT_ONLY : mode;
   d->cap = o ? o->cap : 0;
   d->force_root = 0xFF;
   d->force_from_src = 0xFF;
@@ -663,6 +668,9 @@ static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match
 }
 
 static void opts_key(gs_batch *b, const gs_match_opts *opts) {
+  const bool chunked = opts && opts->mode == GS_CHUNKED;
+  b->on_chunk = chunked ? opts->on_chunk : nullptr;
+  b->chunk_user = chunked ? opts->user : nullptr;
   b->key_cap = opts ? opts->cap : 0;
   b->key_mode = opts ? opts->mode : 0;
   b->key_rounds = opts ? opts->max_refine_rounds : 0;
@@ -803,6 +811,7 @@ bool batch_rearm(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match_opt
   pack_all(b, qs, n, opts);
   for (uint32_t i = 0; i < n; ++i)
     if (b->hq[i].k > b->nqv_s || b->hq[i].m > b->nqe_s) return false;
+  opts_key(b, opts);  // the same options, but a callback of this call's
   make_waves(b, b->nq_s, b->nqv_s, b->nqe_s);
   return batch_upload(b) == GS_OK;
 }
@@ -937,10 +946,13 @@ gs_status batch_finish(gs_batch *b) {
   b->fallbacks = 0;
   for (uint32_t i = 0; i < n; ++i) {
     if (b->hstatus[i] != GS_OK) continue;
-    if (b->status[i] == QS_OVERFLOW || b->status[i] == QS_TOPCAP) {
+    // GS_CHUNKED: every query with embeddings streams them on the chunked
+    // path; otherwise only the queries the device pools could not finish
+    const bool stream = b->on_chunk && b->status[i] != QS_EMPTY && !(b->status[i] == QS_OK && b->count[i] == 0);
+    if (stream || b->status[i] == QS_OVERFLOW || b->status[i] == QS_TOPCAP) {
       gs_status st = fallback_query(b, i);
       if (st != GS_OK) return st;
-      b->fallbacks++;
+      b->fallbacks += stream ? 0 : 1;
     }
   }
   b->finished = true;
@@ -961,7 +973,7 @@ gs_status batch_fetch(gs_batch *b, gs_result *outs) {
     r.count = b->count[i];
     r.fingerprint = b->fp[i];
     const uint64_t cap = b->hq[i].mode == GS_COUNT_ONLY ? 0 : b->hq[i].cap;
-    r.truncated = r.count > cap ? 1 : 0;
+    r.truncated = !b->on_chunk && r.count > cap ? 1 : 0;  // GS_CHUNKED delivered every row
     if (b->fb_done[i]) {
       r.num_rows = b->fb_rows[i].size() / (r.k ? r.k : 1);
       if (r.num_rows) {
@@ -990,6 +1002,12 @@ gs_status batch_fetch(gs_batch *b, gs_result *outs) {
 }  // namespace gs
 
 // ------------------------------------------------------------ C ABI
+extern "C" gs_status gs_memcpy_d2h(void *dst, const void *src, uint64_t bytes) {
+  if (bytes && (!dst || !src)) return fail(GS_ERR_INVALID, "gs_memcpy_d2h: null pointer");
+  GS_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+  return GS_OK;
+}
+
 extern "C" gs_status gs_batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
                                      gs_batch **out) {
   if (!g || !out || (n && !qs)) return fail(GS_ERR_INVALID, "gs_batch_create: null argument");

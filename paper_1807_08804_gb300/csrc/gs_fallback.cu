@@ -235,6 +235,10 @@ struct FbRun {
   uint64_t cap;
   uint64_t top_n = 0;
   int nbits;
+  // GS_CHUNKED: final rows go to the callback instead of a running top-cap
+  gs_chunk_cb cb = nullptr;
+  void *user = nullptr;
+  uint32_t query = 0;
 };
 
 template <typename T>
@@ -269,6 +273,23 @@ gs_status sort_top(FbRun &R, uint64_t keep, bool final) {
     R.top_n = keep;
   }
   GS_CUDA(cudaStreamSynchronize(R.s));
+  return GS_OK;
+}
+
+// GS_CHUNKED: the collected final rows, in query-vertex column order, to the
+// callback; the buffer starts over.
+gs_status flush_chunk(FbRun &R) {
+  Fallback *f = R.f;
+  const uint64_t n = R.top_n;
+  if (n == 0) return GS_OK;
+  GS_CUDA(cudaMemcpyAsync(f->d_n, &n, sizeof(n), cudaMemcpyHostToDevice, R.s));
+  k_iota_n<<<grid_n(n, R.sms), kT, 0, R.s>>>(f->perm[0], f->d_n);
+  ColOrder ord;
+  for (uint32_t u = 0; u < R.k; ++u) ord.c[u] = R.pos[u];
+  k_take_rows<<<grid_n(n, R.sms), kT, 0, R.s>>>(f->top, R.k, f->perm[0], n, ord, f->top2);
+  GS_CUDA(cudaStreamSynchronize(R.s));
+  R.cb(f->top2, n, R.k, R.query, R.user);
+  R.top_n = 0;
   return GS_OK;
 }
 
@@ -321,7 +342,7 @@ gs_status expand(FbRun &R, uint32_t s, uint64_t n) {
     const SrcRows src{0, b - a, a * (s + 1)};
     if (final) {
       if (R.top_n + out > f->top_rows) {
-        if ((st = sort_top(R, R.cap, false)) != GS_OK) return st;
+        if ((st = R.cb ? flush_chunk(R) : sort_top(R, R.cap, false)) != GS_OK) return st;
         if (R.top_n + out > f->top_rows) return fail(GS_ERR_OOM, "chunked join: row buffer too small");
       }
       Wc.out = f->top;
@@ -370,7 +391,11 @@ gs_status fallback_query(gs_batch *b, uint32_t i) {
   DQuery dq;
   GS_CUDA(cudaMemcpyAsync(&dq, fb->W.dq, sizeof(DQuery), cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaStreamSynchronize(s));
-  const bool want_rows = src.mode != GS_COUNT_ONLY && src.cap > 0;
+  const bool stream = b->on_chunk != nullptr;  // GS_CHUNKED: every embedding to the callback
+  const bool want_rows = stream || (src.mode != GS_COUNT_ONLY && src.cap > 0);
+  // rows per streamed chunk: the chunk budget (default 1 GiB) over the row width
+  const uint64_t chunk_rows =
+      std::max<uint64_t>((b->key_chunk ? b->key_chunk : (1ull << 30)) / (4ull * std::max<uint32_t>(src.k, 1)), 4096);
   std::vector<uint32_t> rows;
   uint64_t count = 0, fp = 0;
   if (dq.status == QS_OK) {
@@ -378,11 +403,16 @@ gs_status fallback_query(gs_batch *b, uint32_t i) {
     memcpy(R.pos, dq.pos, sizeof(R.pos));
     R.rows = want_rows;
     R.cap = src.cap;
+    if (stream) {
+      R.cb = b->on_chunk;
+      R.user = b->chunk_user;
+      R.query = i;
+    }
     int nb = 1;
     while (nb < 32 && ((uint64_t)(b->g->d.V - 1) >> nb)) ++nb;
     R.nbits = nb;
     if (want_rows) {
-      st = ensure_top(f, 2 * std::max<uint64_t>(src.cap, 1ull << 16), src.k);
+      st = ensure_top(f, stream ? chunk_rows : 2 * std::max<uint64_t>(src.cap, 1ull << 16), src.k);
       if (st != GS_OK) return st;
     }
     uint32_t len = 0;
@@ -396,7 +426,11 @@ gs_status fallback_query(gs_batch *b, uint32_t i) {
       GS_CUDA(cudaMemsetAsync(&fb->W.qs[0].count, 0, 8, s));
       uint64_t c = len;
       GS_CUDA(cudaMemcpyAsync(&fb->W.qs[0].count, &c, 8, cudaMemcpyHostToDevice, s));
-      if (want_rows) {
+      if (stream) {  // the rows are the candidates themselves
+        GS_CUDA(cudaStreamSynchronize(s));
+        for (uint64_t a = 0; a < len; a += chunk_rows)
+          R.cb(fb->W.flist + off + a, std::min<uint64_t>(chunk_rows, len - a), 1, i, R.user);
+      } else if (want_rows) {
         const uint64_t keep = std::min<uint64_t>(len, src.cap);
         rows.resize(keep);
         if (keep) GS_CUDA(cudaMemcpyAsync(rows.data(), fb->W.flist + off, 4 * keep, cudaMemcpyDeviceToHost, s));
@@ -410,7 +444,9 @@ gs_status fallback_query(gs_batch *b, uint32_t i) {
         GS_CUDA(cudaMemcpyAsync(f->buf[0], fb->W.flist + off + a, 4 * m, cudaMemcpyDeviceToDevice, s));
         st = expand(R, 0, m);
       }
-      if (st == GS_OK && want_rows && R.top_n) {
+      if (st == GS_OK && stream) {
+        st = flush_chunk(R);
+      } else if (st == GS_OK && want_rows && R.top_n) {
         const uint64_t keep = std::min(R.top_n, src.cap);
         st = sort_top(R, keep, true);
         if (st == GS_OK) {

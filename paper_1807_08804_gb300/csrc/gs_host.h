@@ -92,6 +92,8 @@ struct gs_batch {
   std::vector<uint8_t> fb_done;
   // capacity and options (for reuse by later calls with the same options)
   uint32_t n_cap = 0;
+  gs_chunk_cb on_chunk = nullptr;  // GS_CHUNKED: where every embedding goes
+  void *chunk_user = nullptr;
   uint64_t key_cap = 0, key_chunk = 0;
   uint32_t key_mode = 0, key_rounds = 0;
   void *key_stream = nullptr;

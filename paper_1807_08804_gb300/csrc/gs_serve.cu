@@ -269,6 +269,8 @@ extern "C" gs_status gs_serve_create(gs_graph *g, const gs_serve_opts *opts, gs_
 
 extern "C" gs_status gs_serve_submit(gs_server *s, const gs_query *q, const gs_match_opts *opts, uint64_t *ticket) {
   if (!s || !q || !ticket) return fail(GS_ERR_INVALID, "gs_serve_submit: null argument");
+  if (opts && opts->mode == GS_CHUNKED)
+    return fail(GS_ERR_UNSUPPORTED, "GS_CHUNKED is not served (its callback would run on the serving thread)");
   // validate now so that a bad query fails at submit
   DQuery d;
   gs_status st = pack_query(s->g->d, q, opts, &d);

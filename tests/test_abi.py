@@ -36,6 +36,6 @@ def test_struct_layouts_match_the_header():
     # sizes the C compiler gives these structs on LP64 targets
     assert ctypes.sizeof(gs.GraphDesc) == 72
     assert ctypes.sizeof(gs.QueryDesc) == 48
-    assert ctypes.sizeof(gs.MatchOpts) == 32
+    assert ctypes.sizeof(gs.MatchOpts) == 48
     assert ctypes.sizeof(gs.ResultDesc) == 48
     assert ctypes.sizeof(gs.ServeOpts) == 24

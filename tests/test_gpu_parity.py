@@ -165,6 +165,36 @@ def test_outputs_cut_at_cap_before_sorting():
         assert_same(r, o, cap)
 
 
+def test_chunked_mode_streams_every_embedding():
+    """GS_CHUNKED: every embedding reaches the callback exactly once (rows in
+    query-vertex order, chunks in any order), with the exact count and
+    fingerprint; small chunk budgets force many chunks."""
+    n = 12
+    g = graph_from_triples(n, complete_digraph_triples(n))
+    og = O.OracleGraph.from_graph(g)
+    dg = gs.DeviceGraph(g)
+    path6 = query(6, [(i, i + 1, 0) for i in range(5)])                        # 665,280 embeddings
+    star = query(4, [(0, 1, 0), (0, 2, 0), (0, 3, 0)], vbind=[5, I.UNBOUND, I.UNBOUND, I.UNBOUND])
+    single = query(1, [], vtype=[0])
+    none = query(2, [(0, 1, 0)], vbind=[3, 3])                                 # injectivity: no embedding
+    qs = [path6, star, single, none]
+    for chunk_bytes in (1 << 16, 1 << 22):
+        got = {i: [] for i in range(len(qs))}
+        res = gs.match_batch(dg, qs, cap=0, mode=gs.GS_CHUNKED, chunk_bytes=chunk_bytes,
+                             on_chunk=lambda rows, q: got[q].append(rows))
+        for i, q in enumerate(qs):
+            o = O.match(og, q, cap=1 << 21)
+            rows = np.concatenate(got[i]) if got[i] else np.zeros((0, len(q.vtype)), np.uint32)
+            order = np.lexsort(rows.T[::-1]) if rows.shape[0] else np.zeros(0, int)
+            np.testing.assert_array_equal(rows[order], o.rows)
+            assert (res[i].count, res[i].fingerprint) == (o.count, o.fingerprint) == (rows.shape[0], o.fingerprint)
+            assert res[i].rows.shape[0] == 0 and not res[i].truncated
+        if chunk_bytes == 1 << 16:
+            assert len(got[0]) > 10
+    with pytest.raises(gs.GSError):
+        gs.match(dg, path6, mode=gs.GS_CHUNKED)  # no callback
+
+
 def test_chunked_join_with_small_level_buffers(monkeypatch):
     """Partial embeddings that overflow the level budget finish on the
     chunked depth-first path; tiny buffers force many chunks."""
