@@ -46,6 +46,8 @@ def _load():
         lib.orc_graph_num_edges.argtypes = [P]
         lib.orc_row_hash.restype = U64
         lib.orc_row_hash.argtypes = [U32, P]
+        lib.orc_fingerprint.restype = U64
+        lib.orc_fingerprint.argtypes = [U32, P, U64]
         lib.orc_match.restype = I
         lib.orc_match.argtypes = [P, U32, U32, P, P, P, P, P, U64, P, P, P, P, ctypes.c_double]
         lib.orc_match_many.restype = I
@@ -223,7 +225,7 @@ def row_hash(row) -> int:
 
 def fingerprint(rows: np.ndarray) -> int:
     """Sum (mod 2^64) of row_hash over rows [n, k]."""
-    acc = 0
-    for r in np.asarray(rows, np.uint32):
-        acc = (acc + row_hash(r)) & 0xFFFFFFFFFFFFFFFF
-    return acc
+    r = np.ascontiguousarray(np.asarray(rows, np.uint32))
+    if r.ndim != 2 or r.shape[0] == 0:
+        return 0
+    return int(_load().orc_fingerprint(r.shape[1], _p(r), r.shape[0]))

@@ -173,6 +173,13 @@ uint64_t orc_row_hash(uint32_t k, const uint32_t *row) {
   return h;
 }
 
+/* Fingerprint of n rows of width k (row-major): the sum of their hashes. */
+uint64_t orc_fingerprint(uint32_t k, const uint32_t *rows, uint64_t n) {
+  uint64_t acc = 0;
+  for (uint64_t i = 0; i < n; ++i) acc += orc_row_hash(k, rows + i * k);
+  return acc;
+}
+
 /* --------------------------------------------------------- row collection */
 typedef struct {
   uint32_t k;
