@@ -19,7 +19,11 @@
  *     (drop a candidate that has no candidate neighbour for some query
  *     neighbour) repeated "until no more can be pruned" (Section 3.3.3,
  *     "Candidate Nodes Refinement");
- *   - the candidate-edge tables of Section 3.3.4 ("Joining Phase").
+ *   - the candidate-edge tables of Section 3.3.4 ("Joining Phase");
+ *   - variable edges (Section 3.2: a relation may itself be a variable):
+ *     a query edge with relation ORC_ANY maps onto a data edge of any
+ *     relation.  An embedding is still a map of vertices, so two data edges
+ *     of different relations between the same pair count once.
  *
  * Every function keeps its own data structures: per-vertex adjacency built
  * from a sorted, de-duplicated triple array, and binary search in that array
@@ -101,8 +105,15 @@ void orc_graph_free(orc_graph *g) {
 
 uint64_t orc_graph_num_edges(const orc_graph *g) { return g->E; }
 
-/* Is (a, r, b) a data edge?  Binary search in the (src, rel, dst) order. */
+/* Is (a, r, b) a data edge?  Binary search in the (src, rel, dst) order;
+ * r = ORC_ANY: is there a data edge a -> b of any relation (scan of a's
+ * out-edges). */
 static int orc_has_edge(const orc_graph *g, uint32_t a, uint32_t r, uint32_t b) {
+  if (r == ORC_ANY) {
+    for (uint64_t i = g->src_begin[a]; i < g->src_begin[a + 1]; ++i)
+      if (g->by_src[i].dst == b) return 1;
+    return 0;
+  }
   orc_triple key = {a, r, b};
   uint64_t lo = g->src_begin[a], hi = g->src_begin[a + 1];
   while (lo < hi) {
@@ -114,11 +125,32 @@ static int orc_has_edge(const orc_graph *g, uint32_t a, uint32_t r, uint32_t b) 
   return 0;
 }
 
+/* The neighbour of v held by entry t of its out-edges (dir 0) or in-edges
+ * (dir 1), and that entry's relation. */
+static uint32_t orc_nbr(const orc_graph *g, int dir, uint64_t t) { return dir == 0 ? g->by_src[t].dst : g->by_dst[t].src; }
+static uint32_t orc_rel(const orc_graph *g, int dir, uint64_t t) { return dir == 0 ? g->by_src[t].rel : g->by_dst[t].rel; }
+static uint64_t orc_begin(const orc_graph *g, int dir, uint32_t v) { return dir == 0 ? g->src_begin[v] : g->dst_begin[v]; }
+
+/* Does entry t of v's edges in direction dir match relation r, and (for
+ * r = ORC_ANY) is it the first of v's edges to its neighbour?  Walking v's
+ * edges and keeping the entries for which this holds visits each neighbour
+ * over r exactly once. */
+static int orc_first_nbr(const orc_graph *g, int dir, uint32_t v, uint64_t t, uint32_t r) {
+  if (r != ORC_ANY) return orc_rel(g, dir, t) == r;
+  for (uint64_t i = orc_begin(g, dir, v); i < t; ++i)
+    if (orc_nbr(g, dir, i) == orc_nbr(g, dir, t)) return 0;
+  return 1;
+}
+
 /* Number of distinct out-neighbours of v over relation r (dir 0) or of
- * distinct in-neighbours (dir 1).  Triples are distinct, so counting
- * triples counts neighbours. */
+ * distinct in-neighbours (dir 1); r = ORC_ANY counts distinct neighbours
+ * over all relations. */
 static uint64_t orc_degree(const orc_graph *g, uint32_t v, int dir, uint32_t r) {
   uint64_t c = 0;
+  if (r == ORC_ANY) {
+    for (uint64_t t = orc_begin(g, dir, v); t < orc_begin(g, dir, v + 1); ++t) c += orc_first_nbr(g, dir, v, t, r);
+    return c;
+  }
   if (dir == 0) { for (uint64_t i = g->src_begin[v]; i < g->src_begin[v + 1]; ++i) c += g->by_src[i].rel == r; }
   else { for (uint64_t i = g->dst_begin[v]; i < g->dst_begin[v + 1]; ++i) c += g->by_dst[i].rel == r; }
   return c;
@@ -271,14 +303,13 @@ void orc_extend(orc_bt *b, uint32_t depth) {
     int matched = 0;
     for (uint32_t t = 0; t < depth; ++t) if (b->order[t] == other) matched = 1;
     if (!matched) continue;
+    /* edge other -> i: out-neighbours of f(other) over relation r (dir 0);
+     * edge i -> other: its in-neighbours (dir 1); each neighbour once */
     const orc_graph *g = b->g;
-    if (d == i) {  /* edge other -> i: out-neighbours of f(other) with relation r */
-      for (uint64_t t = g->src_begin[b->f[other]]; t < g->src_begin[b->f[other] + 1]; ++t)
-        if (g->by_src[t].rel == q->erel[e]) orc_try(b, depth, i, g->by_src[t].dst);
-    } else {       /* edge i -> other: in-neighbours of f(other) with relation r */
-      for (uint64_t t = g->dst_begin[b->f[other]]; t < g->dst_begin[b->f[other] + 1]; ++t)
-        if (g->by_dst[t].rel == q->erel[e]) orc_try(b, depth, i, g->by_dst[t].src);
-    }
+    const int dir = d == i ? 0 : 1;
+    const uint32_t x = b->f[other];
+    for (uint64_t t = orc_begin(g, dir, x); t < orc_begin(g, dir, x + 1); ++t)
+      if (orc_first_nbr(g, dir, x, t, q->erel[e])) orc_try(b, depth, i, orc_nbr(g, dir, t));
     return;
   }
   for (uint32_t v = 0; v < b->g->V; ++v) orc_try(b, depth, i, v);
@@ -306,7 +337,7 @@ int orc_match(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype,
     if (vbind[u] != ORC_UNBOUND && vbind[u] >= g->V) return 1;
     if (vtype[u] != ORC_ANY && vtype[u] >= g->T) return 1;
   }
-  for (uint32_t e = 0; e < q.m; ++e) if (q.erel[e] >= g->R) return 1;
+  for (uint32_t e = 0; e < q.m; ++e) if (q.erel[e] >= g->R && q.erel[e] != ORC_ANY) return 1;
   orc_bt b;
   memset(&b, 0, sizeof b);
   b.g = g; b.q = &q;
@@ -418,8 +449,10 @@ int orc_brute(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype,
  * (1 = candidate).  v is a candidate of u when the binding and the type
  * allow it and, for every direction and relation, v has at least as many
  * distinct neighbours as u has query neighbours (Definition 3.3's degree
- * test, read per direction and relation).  signature = 0 leaves the degree
- * test out (binding and type only).
+ * test, read per direction and relation; the variable relation ORC_ANY is
+ * one more relation whose neighbours are all of v's distinct neighbours in
+ * that direction, needed by u's variable edges only).  signature = 0 leaves
+ * the degree test out (binding and type only).
  */
 int orc_candidates(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype, const uint32_t *vbind,
                    const uint32_t *esrc, const uint32_t *edst, const uint32_t *erel, int signature,
@@ -448,8 +481,9 @@ int orc_candidates(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *v
  * orc_refine: the refinement of Section 3.3.3 run until nothing changes.
  * For every query edge (a -> b, r): a candidate x of a stays only if some
  * candidate y of b has (x, r, y) in E, and a candidate y of b stays only if
- * some candidate x of a has (x, r, y) in E.  sets is [k][V] bytes, updated in
- * place.  Returns the number of passes over the edges.
+ * some candidate x of a has (x, r, y) in E (r = ORC_ANY: an edge of any
+ * relation).  sets is [k][V] bytes, updated in place.  Returns the number of
+ * passes over the edges.
  */
 int orc_refine(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype, const uint32_t *vbind,
                const uint32_t *esrc, const uint32_t *edst, const uint32_t *erel, uint8_t *sets) {
@@ -465,14 +499,14 @@ int orc_refine(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype
         if (!sa[x]) continue;
         int found = 0;
         for (uint64_t t = g->src_begin[x]; t < g->src_begin[x + 1] && !found; ++t)
-          if (g->by_src[t].rel == r && sb[g->by_src[t].dst]) found = 1;
+          if ((r == ORC_ANY || g->by_src[t].rel == r) && sb[g->by_src[t].dst]) found = 1;
         if (!found) { sa[x] = 0; changed = 1; }
       }
       for (uint32_t y = 0; y < g->V; ++y) {
         if (!sb[y]) continue;
         int found = 0;
         for (uint64_t t = g->dst_begin[y]; t < g->dst_begin[y + 1] && !found; ++t)
-          if (g->by_dst[t].rel == r && sa[g->by_dst[t].src]) found = 1;
+          if ((r == ORC_ANY || g->by_dst[t].rel == r) && sa[g->by_dst[t].src]) found = 1;
         if (!found) { sb[y] = 0; changed = 1; }
       }
     }
@@ -486,7 +520,8 @@ int orc_refine(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype
  * the list of key x holds every y with (x, r, y) in E and y a candidate of
  * edst[e]; from_src = 0: keys are the candidates y of edst[e] and each list
  * holds every x with (x, r, y) in E and x a candidate of esrc[e].
- * Lists ascend.  Outputs keys[nkeys], off[nkeys+1], vals[off[nkeys]]; with
+ * Lists ascend and hold each vertex once (r = ORC_ANY: edges of any
+ * relation).  Outputs keys[nkeys], off[nkeys+1], vals[off[nkeys]]; with
  * vals == NULL only *nkeys and *nvals are written.  e indexes the query's
  * edges as given (before de-duplication).
  */
@@ -502,13 +537,15 @@ int orc_edge_table(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *e
     if (!sx[v]) continue;
     if (vals) { keys[nk] = v; off[nk] = nv; }
     nk++;
-    if (from_src) {
-      for (uint64_t t = g->src_begin[v]; t < g->src_begin[v + 1]; ++t)
-        if (g->by_src[t].rel == r && sy[g->by_src[t].dst]) { if (vals) vals[nv] = g->by_src[t].dst; nv++; }
-    } else {
-      for (uint64_t t = g->dst_begin[v]; t < g->dst_begin[v + 1]; ++t)
-        if (g->by_dst[t].rel == r && sy[g->by_dst[t].src]) { if (vals) vals[nv] = g->by_dst[t].src; nv++; }
-    }
+    const int dir = from_src ? 0 : 1;
+    const uint64_t first = nv;
+    for (uint64_t t = orc_begin(g, dir, v); t < orc_begin(g, dir, v + 1); ++t)
+      if (orc_first_nbr(g, dir, v, t, r) && sy[orc_nbr(g, dir, t)]) { if (vals) vals[nv] = orc_nbr(g, dir, t); nv++; }
+    /* a relation's entries ascend by neighbour; over all relations they do
+     * not, so sort the list (insertion sort) */
+    if (vals && r == ORC_ANY)
+      for (uint64_t i = first + 1; i < nv; ++i)
+        for (uint64_t j = i; j > first && vals[j - 1] > vals[j]; --j) { uint32_t t = vals[j]; vals[j] = vals[j - 1]; vals[j - 1] = t; }
   }
   if (vals) off[nk] = nv;
   *nkeys = nk; *nvals = nv;

@@ -36,8 +36,9 @@ def query(k, edges, vtype=None, vbind=None) -> Query:
     return Query(vt, vb, e[:, 0].copy(), e[:, 1].copy(), e[:, 2].copy())
 
 
-def random_tiny(rng: np.random.Generator, n_max=7, k_max=5):
-    """A tiny random instance: dense multi-relation digraph + random query."""
+def random_tiny(rng: np.random.Generator, n_max=7, k_max=5, p_any=0.0):
+    """A tiny random instance: dense multi-relation digraph + random query;
+    each query edge becomes a variable edge (relation ANY) with p_any."""
     V = int(rng.integers(2, n_max + 1))
     T = int(rng.integers(1, 4))
     R = int(rng.integers(1, 4))
@@ -58,6 +59,8 @@ def random_tiny(rng: np.random.Generator, n_max=7, k_max=5):
             edges.append((int(a), int(b), int(rng.integers(R))))
     qt = [int(rng.integers(T)) if rng.random() < 0.6 else ANY for _ in range(k)]
     qb = [int(rng.integers(V)) if rng.random() < 0.15 else UNBOUND for _ in range(k)]
+    if p_any > 0:
+        edges = [(a, b, ANY if rng.random() < p_any else r) for a, b, r in edges]
     return g, query(k, edges, qt, qb)
 
 
@@ -72,20 +75,40 @@ def connected_random_query(rng, k, R=1, extra=0):
     return edges
 
 
+def edge_sets(g: Graph):
+    """(triples, pairs): the set of (src, rel, dst) data triples and the set
+    of (src, dst) pairs joined by an edge of any relation."""
+    E = set()
+    for s in range(g.num_vertices):
+        for e in range(int(g.row_offsets[s]), int(g.row_offsets[s + 1])):
+            E.add((s, int(g.edge_rel[e]), int(g.col_targets[e])))
+    return E, {(a, b) for a, _, b in E}
+
+
+def _keeps(g, q, E, P, f):
+    """Does the vertex map f keep bindings, types and every query edge (a
+    variable edge, relation ANY, needs an edge of any relation)?"""
+    ok = all((q.vbind[u] == UNBOUND or f[u] == q.vbind[u]) and (q.vtype[u] == ANY or g.vertex_type[f[u]] == q.vtype[u])
+             for u in range(q.k))
+    return ok and all(((f[a], f[b]) in P) if r == ANY else ((f[a], int(r), f[b]) in E)
+                      for a, b, r in zip(q.esrc, q.edst, q.erel))
+
+
+def python_brute(g: Graph, q: Query):
+    """Every embedding (injective map keeping bindings, types and edges) in
+    lexicographic order, found by trying every injective map in Python."""
+    E, P = edge_sets(g)
+    return [f for f in itertools.permutations(range(g.num_vertices), q.k) if _keeps(g, q, E, P, f)]
+
+
 def homomorphism_projections(g: Graph, q: Query):
     """Sets {f(u)} over every map f (injective or not) that keeps bindings,
     types and all query edges: computed by trying every map."""
     V, k = g.num_vertices, q.k
-    E = set()
-    for s in range(V):
-        for e in range(int(g.row_offsets[s]), int(g.row_offsets[s + 1])):
-            E.add((s, int(g.edge_rel[e]), int(g.col_targets[e])))
+    E, P = edge_sets(g)
     out = np.zeros((k, V), bool)
     for f in itertools.product(range(V), repeat=k):
-        ok = all((q.vbind[u] == UNBOUND or f[u] == q.vbind[u]) and (q.vtype[u] == ANY or g.vertex_type[f[u]] == q.vtype[u])
-                 for u in range(k))
-        ok = ok and all((f[a], int(r), f[b]) in E for a, b, r in zip(q.esrc, q.edst, q.erel))
-        if ok:
+        if _keeps(g, q, E, P, f):
             for u in range(k):
                 out[u, f[u]] = True
     return out

@@ -8,8 +8,8 @@ import pytest
 
 import oracle as O
 from paper_1807_08804_gb300.inputs import ANY, UNBOUND
-from tests.helpers import (connected_random_query, graph_from_triples, homomorphism_projections,
-                           parse_worked_example, query, random_tiny)
+from tests.helpers import (connected_random_query, edge_sets, graph_from_triples, homomorphism_projections,
+                           parse_worked_example, python_brute, query, random_tiny)
 
 
 def og(g):
@@ -137,6 +137,93 @@ def test_relation_labels_matter():
     assert O.match(o, query(3, [(0, 1, 0), (1, 2, 1)]), cap=0).count == 1  # 0->1->2
 
 
+# ------------------------------------------------- variable edges (ANY)
+def test_variable_edges_equal_python_brute_force():
+    """A query edge with relation ANY (a variable edge) maps onto a data edge
+    of any relation; embeddings stay vertex maps, so a pair joined under
+    several relations counts once.  The oracle equals a Python enumeration
+    of every injective map that uses its own triple and pair sets."""
+    rng = np.random.default_rng(808)
+    nonzero = wild = 0
+    for case in range(400):
+        g, q = random_tiny(rng, n_max=6, k_max=4, p_any=0.5)
+        o = og(g)
+        want = python_brute(g, q)
+        r = O.match(o, q, cap=1 << 16)
+        assert r.status == 0 and r.count == len(want), case
+        np.testing.assert_array_equal(r.rows, np.asarray(want, np.uint32).reshape(-1, q.k))
+        assert r.fingerprint == O.fingerprint(r.rows)
+        b = O.brute(o, q, cap=1 << 16)
+        assert (b.count, b.fingerprint) == (r.count, r.fingerprint)
+        nonzero += r.count > 0
+        wild += int((q.erel == ANY).any())
+    assert nonzero > 100 and wild > 200
+
+
+def test_variable_edges_on_multi_relation_complete_digraph():
+    """K_n where every ordered pair carries a random non-empty set of the
+    R relations: any connected query whose edges are all variable gives
+    n!/(n-k)! (counting a pair once per relation would give more); with one
+    edge fixed to relation r the count drops to what the r-pairs allow."""
+    rng = np.random.default_rng(17)
+    n, R = 7, 3
+    tr = []
+    for s_ in range(n):
+        for d in range(n):
+            if s_ != d:
+                rels = [r for r in range(R) if rng.random() < 0.5] or [int(rng.integers(R))]
+                tr += [(s_, r, d) for r in rels]
+    g = graph_from_triples(n, tr, R=R)
+    o = og(g)
+    for k in (2, 3, 4, 5):
+        for extra in (0, 2):
+            edges = [(a, b, ANY) for a, b, _ in connected_random_query(rng, k, 1, extra)]
+            assert O.match(o, query(k, edges), cap=0).count == perm(n, k)
+    r0 = sum(1 for s_, r, d in tr if r == 0)
+    assert O.match(o, query(2, [(0, 1, 0)]), cap=0).count == r0 < perm(n, 2)
+    assert O.match(o, query(2, [(0, 1, ANY)]), cap=0).count == perm(n, 2)
+
+
+def test_variable_edge_is_the_union_over_relations():
+    """When every ordered pair carries at most one relation, the embeddings
+    with edge e variable are the disjoint union over r of those with e set
+    to r, so the counts add up; with pairs that carry two relations the
+    variable count is strictly smaller than the sum."""
+    rng = np.random.default_rng(23)
+    for case in range(60):
+        n, R = int(rng.integers(4, 7)), int(rng.integers(2, 4))
+        tr = [(a, int(rng.integers(R)), b) for a in range(n) for b in range(n) if a != b and rng.random() < 0.6]
+        g = graph_from_triples(n, tr, R=R)
+        o = og(g)
+        k = int(rng.integers(2, 5))
+        edges = connected_random_query(rng, k, R, int(rng.integers(0, 2)))
+        j = int(rng.integers(len(edges)))
+        with_any = [(a, b, ANY) if i == j else (a, b, r) for i, (a, b, r) in enumerate(edges)]
+        total = sum(O.match(o, query(k, [(a, b, rr) if i == j else (a, b, r) for i, (a, b, r) in enumerate(edges)]),
+                            cap=0).count for rr in range(R))
+        assert O.match(o, query(k, with_any), cap=0).count == total, case
+    g = graph_from_triples(3, [(0, 0, 1), (0, 1, 1), (1, 0, 2)], R=2)
+    o = og(g)
+    assert O.match(o, query(2, [(0, 1, ANY)]), cap=0).count == 2       # (0,1), (1,2)
+    assert sum(O.match(o, query(2, [(0, 1, r)]), cap=0).count for r in range(2)) == 3
+
+
+def test_variable_edge_degree_test_counts_distinct_neighbours():
+    """The degree test of a variable edge counts v's distinct neighbours over
+    all relations in that direction (counted here from the pair set)."""
+    rng = np.random.default_rng(29)
+    for _ in range(50):
+        g, _ = random_tiny(rng, n_max=7)
+        s_ = int(rng.integers(1, 4))
+        q = query(s_ + 1, [(0, i, ANY) for i in range(1, s_ + 1)])
+        c0 = O.candidates(og(g), q, True)
+        _, P = edge_sets(g)
+        outs = [sum(1 for a, b in P if a == v) for v in range(g.num_vertices)]
+        ins = [sum(1 for a, b in P if b == v) for v in range(g.num_vertices)]
+        assert [bool(x) for x in c0[0]] == [outs[v] >= s_ for v in range(g.num_vertices)]
+        assert [bool(x) for x in c0[1]] == [ins[v] >= 1 for v in range(g.num_vertices)]
+
+
 # --------------------------------------------------------- worked example
 def test_worked_example():
     """Facts printed for the thesis's sample query/data graph (Section 3.3):
@@ -172,10 +259,12 @@ def test_refinement_on_trees_equals_homomorphism_projection():
     (not necessarily injective) edge-preserving maps."""
     rng = np.random.default_rng(99)
     checked = 0
-    for _ in range(150):
+    for case in range(300):
         g, _ = random_tiny(rng, n_max=5, k_max=4)
         k = int(rng.integers(1, 5))
         edges = connected_random_query(rng, k, g.num_rels, 0)  # a tree
+        if case >= 150:  # variable edges
+            edges = [(a, b, ANY if rng.random() < 0.5 else r) for a, b, r in edges]
         qt = [int(rng.integers(g.num_types)) if rng.random() < 0.5 else ANY for _ in range(k)]
         qb = [int(rng.integers(g.num_vertices)) if rng.random() < 0.15 else UNBOUND for _ in range(k)]
         q = query(k, edges, qt, qb)
@@ -189,7 +278,7 @@ def test_refinement_on_trees_equals_homomorphism_projection():
         else:
             np.testing.assert_array_equal(fix, want)
         checked += 1
-    assert checked == 150
+    assert checked == 300
 
 
 def test_filter_and_fixpoint_are_sound():
@@ -241,8 +330,8 @@ def test_edge_tables_against_single_edge_matches():
     size equals the number of embeddings, in both orientations, and every
     embedding's (f(a), f(b)) pair is in the table of any query edge."""
     rng = np.random.default_rng(21)
-    for _ in range(200):
-        g, q = random_tiny(rng)
+    for case in range(300):
+        g, q = random_tiny(rng, p_any=0.0 if case < 200 else 0.5)
         o = og(g)
         if q.m == 0:
             continue
@@ -256,7 +345,8 @@ def test_edge_tables_against_single_edge_matches():
                 for i, key in enumerate(keys):
                     for v in vals[int(off[i]):int(off[i + 1])]:
                         pairs.add((int(key), int(v)) if from_src else (int(v), int(key)))
-                    assert list(vals[int(off[i]):int(off[i + 1])]) == sorted(vals[int(off[i]):int(off[i + 1])])
+                    lst = [int(x) for x in vals[int(off[i]):int(off[i + 1])]]
+                    assert lst == sorted(set(lst))  # ascending, each vertex once
                 for row in emb.rows:
                     assert (int(row[a]), int(row[b])) in pairs
         # one-edge query: table size == embeddings
