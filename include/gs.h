@@ -10,7 +10,10 @@
  * f: [0,k) -> V such that
  *   - a bound query vertex i (a "concept node", Section 3.2) has f(i) = vbind[i];
  *   - a typed query vertex i has type(f(i)) = vtype[i] (GS_ANY: no constraint);
- *   - every query edge (i -> j, r) has (f(i), r, f(j)) in E.
+ *   - every query edge (i -> j, r) has (f(i), r, f(j)) in E; a variable edge
+ *     (r = GS_ANY, Section 3.2: a relation may be a variable) needs
+ *     (f(i), r', f(j)) in E for some relation r'.  An embedding is a map of
+ *     vertices, so a pair joined under several relations counts once.
  * The engine returns every embedding: the exact count always, plus the
  * lexicographically smallest `cap` embeddings written in query-vertex order.
  *
@@ -46,7 +49,7 @@ typedef enum {
 } gs_status;
 
 #define GS_UNBOUND 0xFFFFFFFFu  /* vbind[i]: variable vertex (no binding) */
-#define GS_ANY 0xFFFFFFFFu      /* vtype[i]: no type constraint */
+#define GS_ANY 0xFFFFFFFFu      /* vtype[i]: no type constraint; erel[j]: any relation */
 
 /* gs_graph_desc.flags */
 #define GS_DEVICE_PTRS 1u       /* the arrays are device pointers (read on cuda_stream) */
@@ -57,7 +60,8 @@ typedef enum {
  * Rows may be in any order and may repeat a (src, rel, dst) triple; the
  * library sorts each row by (relation, neighbour), drops repeats and builds
  * the incoming CSR as well (Section 3.5, "incoming and outgoing graph
- * representations").
+ * representations"), plus, per direction, the rows of distinct neighbours
+ * over all relations that variable edges read.
  */
 typedef struct {
   uint32_t num_vertices;        /* V */
@@ -94,7 +98,7 @@ typedef struct {
   const uint32_t *vbind;  /* [k], < V or GS_UNBOUND */
   const uint32_t *esrc;   /* [m] */
   const uint32_t *edst;   /* [m] */
-  const uint32_t *erel;   /* [m], < num_rels */
+  const uint32_t *erel;   /* [m], < num_rels or GS_ANY (variable edge) */
 } gs_query;
 
 /* gs_match_opts.mode */

@@ -36,7 +36,8 @@ gs_status pack_query(const DevGraph &G, const gs_query *q, const gs_match_opts *
     uint32_t a = q->esrc[j], b = q->edst[j], r = q->erel[j];
     if (a >= k || b >= k) return fail(GS_ERR_INVALID, "query edge endpoint out of range");
     if (a == b) return fail(GS_ERR_INVALID, "query self-loop");
-    if (r >= G.R) return fail(GS_ERR_INVALID, "query relation out of range");
+    if (r == kAny) r = kRelAny8;  // variable edge
+    else if (r >= G.R) return fail(GS_ERR_INVALID, "query relation out of range");
     bool dup = false;
     for (uint32_t i = 0; i < m; ++i)
       if (d->esrc[i] == a && d->edst[i] == b && d->erel[i] == r) dup = true;
@@ -65,11 +66,12 @@ gs_status pack_query(const DevGraph &G, const gs_query *q, const gs_match_opts *
     d->need_begin[u] = (uint8_t)nn;
     for (uint32_t i = 0; i < m; ++i)
       if (d->esrc[i] == u || d->edst[i] == u) d->inc_edge[ni++] = (uint8_t)i;
-    // degree needs per (direction, relation)
+    // degree needs per (direction, relation); variable edges count
+    // distinct neighbours over all relations
     for (uint32_t i = 0; i < m; ++i) {
       int dir = d->esrc[i] == u ? 0 : (d->edst[i] == u ? 1 : -1);
       if (dir < 0) continue;
-      uint16_t plane = (uint16_t)(dir * G.R + d->erel[i]);
+      uint16_t plane = (uint16_t)sig_plane(dir, d->erel[i], G.R);
       bool found = false;
       for (uint32_t t = d->need_begin[u]; t < nn; ++t)
         if (d->need_plane[t] == plane) { d->need_cnt[t]++; found = true; }

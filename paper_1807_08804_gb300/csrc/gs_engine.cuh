@@ -47,11 +47,11 @@ struct DQuery {
   uint32_t qe_base;                 // slot index of query edge 0
   uint32_t vtype[kMaxK];            // type or kAny
   uint32_t vbind[kMaxK];            // data id or kUnbound
-  uint8_t esrc[kMaxM], edst[kMaxM], erel[kMaxM];
+  uint8_t esrc[kMaxM], edst[kMaxM], erel[kMaxM];  // erel kRelAny8: variable edge
   uint8_t inc_begin[kMaxK + 1];     // incident edges of u: inc_edge[inc_begin[u] .. inc_begin[u+1])
   uint8_t inc_edge[2 * kMaxM];
   uint8_t need_begin[kMaxK + 1];    // degree needs of u: (plane, count) pairs
-  uint16_t need_plane[2 * kMaxM];   // dir * R + rel
+  uint16_t need_plane[2 * kMaxM];   // sig_plane(dir, rel, R)
   uint8_t need_cnt[2 * kMaxM];
   uint32_t mode;
   uint64_t cap;
@@ -79,6 +79,17 @@ __host__ __device__ __forceinline__ int xinc_dir(uint32_t x) { return (int)(x & 
 __host__ __device__ __forceinline__ uint32_t xinc_rel(uint32_t x) { return (x >> 1) & 0xFFu; }
 __host__ __device__ __forceinline__ uint32_t xinc_w(uint32_t x) { return (x >> 9) & 0xFu; }
 __host__ __device__ __forceinline__ uint32_t xinc_role(uint32_t x) { return x >> 13; }
+
+// Variable edges (a relation that is itself a variable, Section 3.2): erel
+// kRelAny8 matches a data edge of any relation.  Such an edge reads the
+// adjacency planes of distinct neighbours (2 + direction) as relation 0, and
+// its signature and neighbour-type planes are 2R + direction.
+constexpr uint32_t kRelAny8 = 0xFFu;
+__host__ __device__ __forceinline__ int adj_plane(int dir, uint32_t rel) { return rel == kRelAny8 ? dir + 2 : dir; }
+__host__ __device__ __forceinline__ uint32_t adj_rel(uint32_t rel) { return rel == kRelAny8 ? 0u : rel; }
+__host__ __device__ __forceinline__ uint32_t sig_plane(int dir, uint32_t rel, uint32_t R) {
+  return rel == kRelAny8 ? 2 * R + (uint32_t)dir : (uint32_t)dir * R + rel;
+}
 
 // Per-query join bookkeeping and results (slot arrays).
 struct QState {

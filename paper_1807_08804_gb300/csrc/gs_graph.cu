@@ -5,9 +5,12 @@
 //   - each row sorted by (relation, neighbour) and packed rel << 24 | nbr, so
 //     a relation's neighbours form one ascending run found by binary search;
 //   - repeated (src, rel, dst) triples dropped;
+//   - per direction, a second CSR of the distinct neighbours over all
+//     relations (ascending), read by variable edges;
 //   - per-vertex, per-(direction, relation) distinct-neighbour counts kept
 //     as 4-bit signatures for the candidate test (Definition 3.3's degree
-//     condition, read per direction and relation).
+//     condition, read per direction and relation, plus one plane per
+//     direction over all relations).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -98,9 +101,18 @@ __global__ void k_rekey_in(uint64_t n, const uint32_t *src, const uint32_t *pack
   }
 }
 
-// Signatures: one thread per (direction, vertex) walks its sorted row and
-// ORs each relation's saturated count into its plane.
-__global__ void k_signatures(uint32_t V, uint32_t R, const uint64_t *off, const uint32_t *adj, int dir, uint32_t *sig,
+// Any-relation rows: key = neighbour (relation field 0), val = row vertex.
+__global__ void k_strip_rel(uint64_t n, const uint32_t *packed, const uint32_t *row, uint32_t *key, uint32_t *val) {
+  uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < n; i += stride) {
+    key[i] = packed[i] & kNbrMask;
+    val[i] = row[i];
+  }
+}
+
+// Signatures: one thread per vertex of one adjacency plane walks its sorted
+// row and ORs each relation's saturated count into plane plane0 + relation.
+__global__ void k_signatures(uint32_t V, const uint64_t *off, const uint32_t *adj, uint32_t plane0, uint32_t *sig,
                              uint64_t sig_words) {
   uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = tid; v < V; v += stride) {
@@ -111,7 +123,7 @@ __global__ void k_signatures(uint32_t V, uint32_t R, const uint64_t *off, const 
       uint64_t j = i;
       while (j < e && (adj[j] >> kNbrBits) == r) ++j;
       uint32_t c = (uint32_t)((j - i) > 15 ? 15 : (j - i));
-      atomicOr(&sig[(uint64_t)(dir * R + r) * sig_words + (v >> 3)], c << ((v & 7) * 4));
+      atomicOr(&sig[(uint64_t)(plane0 + r) * sig_words + (v >> 3)], c << ((v & 7) * 4));
       i = j;
     }
   }
@@ -137,9 +149,10 @@ __global__ void __launch_bounds__(256) k_sig_hist(uint32_t V, uint32_t T, uint32
     if (h[i]) atomicAdd(&hist[((uint64_t)(i >> 4) * P + p) * 16 + (i & 15)], h[i]);
 }
 
-// Neighbour-type masks: for each vertex v and each (direction, relation)
-// plane, the OR of 1 << (type mod 32) over v's neighbours in that plane.
-__global__ void k_type_masks(uint32_t V, uint32_t R, const uint64_t *off, const uint32_t *adj, int dir,
+// Neighbour-type masks: for each vertex v and each relation of one adjacency
+// plane, the OR of 1 << (type mod 32) over v's neighbours over that relation,
+// stored in mask plane plane0 + relation.
+__global__ void k_type_masks(uint32_t V, const uint64_t *off, const uint32_t *adj, uint32_t plane0,
                              const uint8_t *vtype, uint32_t *tmask) {
   uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = tid; v < V; v += stride) {
@@ -149,7 +162,7 @@ __global__ void k_type_masks(uint32_t V, uint32_t R, const uint64_t *off, const 
       const uint32_t r = adj[i] >> kNbrBits;
       uint32_t m = 0;
       for (; i < e && (adj[i] >> kNbrBits) == r; ++i) m |= 1u << (vtype[adj[i] & kNbrMask] & 31u);
-      tmask[(uint64_t)(dir * R + r) * V + v] = m;
+      tmask[(uint64_t)(plane0 + r) * V + v] = m;
     }
   }
 }
@@ -336,18 +349,34 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   st = build_direction(V, R, kept, k0.as<uint32_t>(), v0.as<uint32_t>(), k1.as<uint32_t>(), v1.as<uint32_t>(),
                        scanb.as<uint64_t>(), tmpb.as<uint64_t>(), stmpb.as<uint64_t>(), dn.as<uint64_t>(), s, sms, &g->off_in, &g->adj_in,
                        &dst_rows, &kept_in);
+  // distinct neighbours over all relations, per direction
+  for (int d = 0; d < 2 && st == GS_OK; ++d) {
+    const uint64_t n = d == 0 ? kept : kept_in;
+    GS_CUDA(cudaMemcpyAsync(dn.p, &n, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    k_strip_rel<<<blocks_for(n), kT, 0, s>>>(n, d == 0 ? g->adj_out : g->adj_in, d == 0 ? src_rows : dst_rows,
+                                             k0.as<uint32_t>(), v0.as<uint32_t>());
+    uint32_t *rows = nullptr;
+    uint64_t kept_any = 0;
+    st = build_direction(V, 1, n, k0.as<uint32_t>(), v0.as<uint32_t>(), k1.as<uint32_t>(), v1.as<uint32_t>(),
+                         scanb.as<uint64_t>(), tmpb.as<uint64_t>(), stmpb.as<uint64_t>(), dn.as<uint64_t>(), s, sms,
+                         d == 0 ? &g->off_aout : &g->off_ain, d == 0 ? &g->adj_aout : &g->adj_ain, &rows, &kept_any);
+    cudaFree(rows);
+  }
   cudaFree(src_rows);
   cudaFree(dst_rows);
   if (st != GS_OK) return cleanup(st);
+  const uint64_t P = 2ull * R + 2;  // signature / mask planes
 
   // Planes hold whole 16-byte groups (32 vertices) so the filter can read
   // them as aligned uint4 vectors up to the last partial group.
   const uint64_t sig_words = ((V + 7) / 8 + 3) / 4 * 4;
-  if (cudaMalloc(&g->sig, sizeof(uint32_t) * sig_words * 2 * R) != cudaSuccess)
+  if (cudaMalloc(&g->sig, sizeof(uint32_t) * sig_words * P) != cudaSuccess)
     return cleanup(fail(GS_ERR_OOM, "signature planes"));
-  GS_CUDA(cudaMemsetAsync(g->sig, 0, sizeof(uint32_t) * sig_words * 2 * R, s));
-  k_signatures<<<blocks_for(V), kT, 0, s>>>(V, R, g->off_out, g->adj_out, 0, g->sig, sig_words);
-  k_signatures<<<blocks_for(V), kT, 0, s>>>(V, R, g->off_in, g->adj_in, 1, g->sig, sig_words);
+  GS_CUDA(cudaMemsetAsync(g->sig, 0, sizeof(uint32_t) * sig_words * P, s));
+  k_signatures<<<blocks_for(V), kT, 0, s>>>(V, g->off_out, g->adj_out, 0, g->sig, sig_words);
+  k_signatures<<<blocks_for(V), kT, 0, s>>>(V, g->off_in, g->adj_in, R, g->sig, sig_words);
+  k_signatures<<<blocks_for(V), kT, 0, s>>>(V, g->off_aout, g->adj_aout, 2 * R, g->sig, sig_words);
+  k_signatures<<<blocks_for(V), kT, 0, s>>>(V, g->off_ain, g->adj_ain, 2 * R + 1, g->sig, sig_words);
   const uint64_t vt_bytes = ((uint64_t)V + 127) / 128 * 128;  // whole 32-vertex groups, zero padded
   if (cudaMalloc(&g->vtype, vt_bytes) != cudaSuccess) return cleanup(fail(GS_ERR_OOM, "types"));
   GS_CUDA(cudaMemsetAsync(g->vtype, 0, vt_bytes, s));
@@ -384,14 +413,15 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
     GS_CUDA(cudaStreamSynchronize(s));
   }
   // neighbour-type masks (zero where a vertex has no neighbour in a plane)
-  if (cudaMalloc(&g->tmask, sizeof(uint32_t) * (uint64_t)V * 2 * R) != cudaSuccess)
+  if (cudaMalloc(&g->tmask, sizeof(uint32_t) * (uint64_t)V * P) != cudaSuccess)
     return cleanup(fail(GS_ERR_OOM, "neighbour-type masks"));
-  GS_CUDA(cudaMemsetAsync(g->tmask, 0, sizeof(uint32_t) * (uint64_t)V * 2 * R, s));
-  k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, R, g->off_out, g->adj_out, 0, g->vtype, g->tmask);
-  k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, R, g->off_in, g->adj_in, 1, g->vtype, g->tmask);
+  GS_CUDA(cudaMemsetAsync(g->tmask, 0, sizeof(uint32_t) * (uint64_t)V * P, s));
+  k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, g->off_out, g->adj_out, 0, g->vtype, g->tmask);
+  k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, g->off_in, g->adj_in, R, g->vtype, g->tmask);
+  k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, g->off_aout, g->adj_aout, 2 * R, g->vtype, g->tmask);
+  k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, g->off_ain, g->adj_ain, 2 * R + 1, g->vtype, g->tmask);
   // the same planes in type-list order (needs the type lists, built above)
   {
-    const uint64_t P = 2ull * R;
     if (cudaMalloc(&g->sig_t, sizeof(uint32_t) * sig_words * P) != cudaSuccess ||
         cudaMalloc(&g->tmask_t, sizeof(uint32_t) * (uint64_t)V * P) != cudaSuccess)
       return cleanup(fail(GS_ERR_OOM, "type-ordered planes"));
@@ -402,13 +432,12 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   // Signature statistics for the plan: sigge[(t * P + p) * 16 + c] = vertices
   // of type t (t = T: any type) whose count in plane p is at least c.
   {
-    const uint32_t P = 2 * R;
     const uint64_t nh = (uint64_t)(T + 1) * P * 16;
     uint32_t *dh = nullptr;
     GS_CUDA(cudaMalloc(&dh, sizeof(uint32_t) * nh));
     GS_CUDA(cudaMemsetAsync(dh, 0, sizeof(uint32_t) * nh, s));
-    const dim3 grid((unsigned)std::min<uint64_t>((V + 255) / 256, 64), P);
-    k_sig_hist<<<grid, 256, 0, s>>>(V, T, P, g->vtype, g->sig, sig_words, dh);
+    const dim3 grid((unsigned)std::min<uint64_t>((V + 255) / 256, 64), (unsigned)P);
+    k_sig_hist<<<grid, 256, 0, s>>>(V, T, (uint32_t)P, g->vtype, g->sig, sig_words, dh);
     std::vector<uint32_t> hh(nh);
     GS_CUDA(cudaMemcpyAsync(hh.data(), dh, sizeof(uint32_t) * nh, cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));
@@ -427,8 +456,8 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
 
   DevGraph &d = g->d;
   d.V = V; d.T = T; d.R = R; d.E = kept;
-  d.off[0] = g->off_out; d.off[1] = g->off_in;
-  d.adj[0] = g->adj_out; d.adj[1] = g->adj_in;
+  d.off[0] = g->off_out; d.off[1] = g->off_in; d.off[2] = g->off_aout; d.off[3] = g->off_ain;
+  d.adj[0] = g->adj_out; d.adj[1] = g->adj_in; d.adj[2] = g->adj_aout; d.adj[3] = g->adj_ain;
   d.vtype = g->vtype;
   d.tvid = g->tvid;
   d.toff = g->toff;
@@ -456,6 +485,10 @@ extern "C" void gs_graph_free(gs_graph *g) {
   cudaFree(g->off_in);
   cudaFree(g->adj_out);
   cudaFree(g->adj_in);
+  cudaFree(g->off_aout);
+  cudaFree(g->off_ain);
+  cudaFree(g->adj_aout);
+  cudaFree(g->adj_ain);
   cudaFree(g->vtype);
   cudaFree(g->tvid);
   cudaFree(g->toff);

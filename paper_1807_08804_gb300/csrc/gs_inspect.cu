@@ -124,9 +124,10 @@ extern "C" gs_status gs_inspect_edge_table(gs_graph *g, const gs_query *q, uint3
   gs_status st = make_single(g, q, &b);
   if (st != GS_OK) return st;
   const DQuery &d = b->hq[0];
+  const uint32_t rel = q->erel[e] == kAny ? kRelAny8 : q->erel[e];
   uint32_t j = 0;
   for (; j < d.m; ++j)
-    if (d.esrc[j] == q->esrc[e] && d.edst[j] == q->edst[e] && d.erel[j] == q->erel[e]) break;
+    if (d.esrc[j] == q->esrc[e] && d.edst[j] == q->edst[e] && d.erel[j] == rel) break;
   const uint32_t x = from_src ? d.esrc[j] : d.edst[j];
   b->hq[0].force_from_src = from_src ? 1 : 0;
   const cudaStream_t s = b->stream;

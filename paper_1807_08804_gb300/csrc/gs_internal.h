@@ -35,16 +35,21 @@ gs_status cuda_fail(cudaError_t e, const char *what);
 struct DevGraph {
   uint32_t V, T, R;
   uint64_t E;
-  const uint64_t *off[2];   // [dir][V+1]; dir 0 = out, 1 = in
-  const uint32_t *adj[2];   // [dir][E]
+  // Adjacency planes: 0 = out, 1 = in, rows of rel << 24 | nbr sorted by
+  // (relation, neighbour); 2 = out, 3 = in, rows of the distinct neighbours
+  // over all relations, ascending (read by variable edges as relation 0).
+  const uint64_t *off[4];   // [plane][V+1]
+  const uint32_t *adj[4];   // [plane][row entries]
   const uint8_t *vtype;     // [V]
   const uint32_t *tvid;     // [V] vertex ids grouped by type, ascending within a type
   const uint32_t *toff;     // [T+1] start of each type's run in tvid
-  const uint32_t *sigge;    // [(T+1) * 2R * 16] vertices of type t (t = T: any) with plane count >= c
-  const uint32_t *tmask;    // [2R][V] OR of 1 << (type mod 32) over v's neighbours in each plane
+  // Signature and neighbour-type planes: dir * R + rel, then 2R + dir for
+  // the distinct neighbours over all relations (P = 2R + 2 planes).
+  const uint32_t *sigge;    // [(T+1) * P * 16] vertices of type t (t = T: any) with plane count >= c
+  const uint32_t *tmask;    // [P][V] OR of 1 << (type mod 32) over v's neighbours in each plane
   const uint32_t *sig_t;    // sig with entry x of each plane belonging to vertex tvid[x]
   const uint32_t *tmask_t;  // tmask likewise
-  const uint32_t *sig;      // [2R][sig_words]
+  const uint32_t *sig;      // [P][sig_words]
   uint64_t sig_words;       // ceil(V / 8)
   uint32_t W0;              // bitmap words per candidate set: ceil(V/32)
   uint32_t W1;              // summary words: ceil(W0/32)
@@ -59,8 +64,8 @@ struct gs_graph {
   gs::DevGraph d;
   int device;
   int num_sms;
-  uint64_t *off_out, *off_in;
-  uint32_t *adj_out, *adj_in;
+  uint64_t *off_out, *off_in, *off_aout, *off_ain;
+  uint32_t *adj_out, *adj_in, *adj_aout, *adj_ain;
   uint8_t *vtype;
   uint32_t *tvid, *toff, *sigge, *tmask, *sig_t, *tmask_t;
   uint32_t *sig;

@@ -245,7 +245,7 @@ __global__ void k_plan(Wave W, const uint32_t *type_count) {
       // no bound vertex: the vertex whose filtered candidate set is expected
       // to be smallest (its type's vertex count times, per degree need, the
       // fraction of those vertices that meet it; ties: more neighbours)
-      const uint32_t P = 2 * W.G.R;
+      const uint32_t P = 2 * W.G.R + 2;
       float best = 0.f;
       for (uint32_t u = 0; u < k; ++u) {
         const uint32_t t = Q.vtype[u] == kAny ? W.G.T : Q.vtype[u];
@@ -352,7 +352,7 @@ __device__ __forceinline__ bool masks_ok_listed(const DevGraph &G, const DQuery 
     const uint32_t xi = Q.xinc[i];
     const uint32_t t = Q.vtype[xinc_w(xi)];
     if (t == kAny) continue;
-    const uint32_t m = G.tmask_t[(uint64_t)(xinc_dir(xi) * G.R + xinc_rel(xi)) * G.V + x];
+    const uint32_t m = G.tmask_t[(uint64_t)sig_plane(xinc_dir(xi), xinc_rel(xi), G.R) * G.V + x];
     ok = ok && ((m >> (t & 31u)) & 1u);
   }
   return ok;
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
       const uint32_t xi = Q.xinc[i];
       const uint32_t t = Q.vtype[xinc_w(xi)];
       if (t == kAny) continue;
-      const uint32_t m = Gr.tmask[(uint64_t)(xinc_dir(xi) * Gr.R + xinc_rel(xi)) * Gr.V + v];
+      const uint32_t m = Gr.tmask[(uint64_t)sig_plane(xinc_dir(xi), xinc_rel(xi), Gr.R) * Gr.V + v];
       keep = keep && ((m >> (t & 31u)) & 1u);
     }
     bytes += 4ull * (i1 - i0);
@@ -679,11 +679,11 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
     for (uint32_t i = i0; i < i1 && keep; ++i) {
       const uint32_t xi = Q.xinc[i];
       if (xinc_role(xi) == 2) continue;
-      const int dir = xinc_dir(xi);
+      const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
       const uint32_t w = xinc_w(xi);
       uint64_t base, lo, hi;
       uint32_t xs;
-      const bool fast = rel_run<G>(tile, Gr, dir, v, xinc_rel(xi), base, lo, hi, xs);
+      const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
       const bool built = xinc_role(xi) == 1;
       const uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
@@ -704,11 +704,11 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
     for (uint32_t i = i0; i < i1 && keep; ++i) {
       const uint32_t xi = Q.xinc[i];
       if (xinc_role(xi) != 2) continue;
-      const int dir = xinc_dir(xi);
+      const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
       const uint32_t w = xinc_w(xi);
       uint64_t base, lo, hi;
       uint32_t xs;
-      const bool fast = rel_run<G>(tile, Gr, dir, v, xinc_rel(xi), base, lo, hi, xs);
+      const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
       uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
       for (uint64_t b = lo; b < hi; b += G) {
@@ -758,11 +758,11 @@ __global__ void __launch_bounds__(kThreads, 6) k_refine(Wave W, uint32_t round) 
     uint64_t bytes = 0;
     for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1]; ++i) {
       const uint32_t xi = Q.xinc[i];
-      const int dir = xinc_dir(xi);
+      const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
       const uint32_t w = xinc_w(xi);
       uint64_t base, lo, hi;
       uint32_t xs;
-      const bool fast = rel_run<G>(tile, Gr, dir, v, xinc_rel(xi), base, lo, hi, xs);
+      const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
       const uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
       for (uint64_t b = lo; b < hi && !found; b += G) {
@@ -864,10 +864,10 @@ __global__ void __launch_bounds__(kThreads) k_ec(Wave W) {
     const uint32_t e = ge - Q.qe_base;
     const uint32_t x = Q.from_src[e] ? Q.esrc[e] : Q.edst[e];
     const uint32_t y = Q.from_src[e] ? Q.edst[e] : Q.esrc[e];
-    const int dir = Q.from_src[e] ? 0 : 1;
+    const int dir = adj_plane(Q.from_src[e] ? 0 : 1, Q.erel[e]);
     const uint32_t key = W.flist[W.flist_off[Q.qv_base + x] + (it - W.ec_key_base[ge])];
     uint64_t lo, hi;
-    rel_range<G>(tile, Gr, dir, key, Q.erel[e], lo, hi);
+    rel_range<G>(tile, Gr, dir, key, adj_rel(Q.erel[e]), lo, hi);
     const uint32_t *ys = slot_of(W, Q.qv_base + y);
     if (!WRITE) {
       uint32_t cnt = 0;

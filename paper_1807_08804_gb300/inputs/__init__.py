@@ -174,6 +174,18 @@ def make_shape_queries(g: Graph, n: int, seed: int = 1, ntop: int = 4) -> list[Q
     return _split(qk, qm, vtype, vbind, None, esrc, edst, erel)
 
 
+def with_variable_edges(queries: list[Query], p_var: float, seed: int = 1) -> list[Query]:
+    """The same queries with each edge's relation replaced by ANY (a variable
+    edge) with probability p_var; the walked vertices still match."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in queries:
+        erel = q.erel.copy()
+        erel[rng.random(q.m) < p_var] = ANY
+        out.append(Query(q.vtype, q.vbind, q.esrc, q.edst, erel, q.walked))
+    return out
+
+
 def make_arrivals(n: int, qps: float, seed: int = 1) -> np.ndarray:
     """Poisson arrival times in seconds (exponential inter-arrival gaps)."""
     lib = _load()
@@ -197,6 +209,7 @@ class Workload:
     cyclic_half: bool = False
     shapes: bool = False
     qps: tuple = field(default_factory=tuple)
+    p_var: float = 0.0  # share of query edges made variable (relation ANY)
 
     def graph(self) -> Graph:
         return make_graph(self.V, self.E, seed=self.seed)
@@ -204,12 +217,14 @@ class Workload:
     def queries(self, g: Graph, n: int | None = None) -> list[Query]:
         n = self.n_queries if n is None else n
         if self.shapes:
-            return make_shape_queries(g, n, seed=self.seed)
-        return make_walk_queries(g, n, self.kmin, self.kmax, p_close=0.3, p_bind=self.p_bind,
-                                 cyclic_half=self.cyclic_half, seed=self.seed)
+            qs = make_shape_queries(g, n, seed=self.seed)
+        else:
+            qs = make_walk_queries(g, n, self.kmin, self.kmax, p_close=0.3, p_bind=self.p_bind,
+                                   cyclic_half=self.cyclic_half, seed=self.seed)
+        return with_variable_edges(qs, self.p_var, self.seed + 0x76) if self.p_var > 0 else qs
 
 
-# The five workloads: sizes, label distributions and query recipes.
+# The workloads: sizes, label distributions and query recipes.
 WORKLOADS = {
     # 10k vertices / 60k edges; 100 queries of 3-6 vertices; cap 2^20
     "single-10k": Workload("single-10k", 10_000, 60_000, 100, 3, 6, 0.2, 1 << 20, 0x6753001),
@@ -224,4 +239,8 @@ WORKLOADS = {
     # 16M vertices / 200M edges; 200 unbound shape queries
     "stress-16m": Workload("stress-16m", 16_000_000, 200_000_000, 200, 4, 6, 0.0, 1 << 20, 0x6753005,
                            shapes=True),
+    # the single-10k and single-1m workloads with 30% of query edges variable
+    "single-10k-var": Workload("single-10k-var", 10_000, 60_000, 100, 3, 6, 0.2, 1 << 20, 0x6753001, p_var=0.3),
+    "single-1m-var": Workload("single-1m-var", 1_000_000, 8_000_000, 1000, 4, 10, 0.2, 1 << 22, 0x6753002,
+                              p_var=0.3),
 }

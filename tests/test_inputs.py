@@ -45,3 +45,23 @@ def test_shape_queries_and_arrivals():
     assert all((q.vbind == I.UNBOUND).all() for q in qs)
     t = I.make_arrivals(20000, 1000.0, seed=1)
     assert (np.diff(t) > 0).all() and abs(t[-1] - 20.0) < 1.0
+
+
+def test_variable_edge_queries():
+    """single-10k-var: the single-10k queries with about 30% of edges made
+    variable, the rest unchanged, deterministic, the walked map still a
+    match."""
+    w, wv = I.WORKLOADS["single-10k"], I.WORKLOADS["single-10k-var"]
+    g = wv.graph()
+    og = O.OracleGraph.from_graph(g)
+    base, qs, again = w.queries(g), wv.queries(g), wv.queries(g)
+    var = tot = 0
+    for b, q, a in zip(base, qs, again):
+        np.testing.assert_array_equal(q.erel, a.erel)
+        np.testing.assert_array_equal(q.esrc, b.esrc)
+        fixed = q.erel != I.ANY
+        np.testing.assert_array_equal(q.erel[fixed], b.erel[fixed])
+        assert O.verify(og, q, q.walked[None, :]) == -1
+        var += int((~fixed).sum())
+        tot += q.m
+    assert 0.22 < var / tot < 0.38
