@@ -50,6 +50,8 @@ def _load():
         lib.orc_fingerprint.argtypes = [U32, P, U64]
         lib.orc_match.restype = I
         lib.orc_match.argtypes = [P, U32, U32, P, P, P, P, P, U64, P, P, P, P, ctypes.c_double]
+        lib.orc_match_proj.restype = I
+        lib.orc_match_proj.argtypes = [P, U32, U32, P, P, P, P, P, U32, U64, P, P, P, P, P, ctypes.c_double]
         lib.orc_match_many.restype = I
         lib.orc_match_many.argtypes = [P, U32, P, P, P, P, P, P, P, P, P, I, ctypes.c_double, P, P, P]
         lib.orc_brute.restype = I
@@ -105,23 +107,40 @@ def _q(q):
 
 
 class Result:
-    def __init__(self, status, count, fingerprint, rows):
+    def __init__(self, status, count, fingerprint, rows, truncated=None):
         self.status = status  # 0 ok, 1 invalid query, 2 time-out
         self.count = count
         self.fingerprint = fingerprint
-        self.rows = rows      # uint32 [nrows, k], lexicographically ascending
+        self.rows = rows      # uint32 [nrows, w], lexicographically ascending
+        self.truncated = truncated  # more distinct rows than returned
 
 
-def match(g: OracleGraph, q, cap: int = 1 << 20, time_limit_s: float = 0.0) -> Result:
-    """Every embedding (count, fingerprint, smallest `cap` rows)."""
+def project_mask(project) -> int:
+    """Bit mask of projected query vertices from a mask or a vertex list."""
+    if project is None:
+        return 0
+    if isinstance(project, (int, np.integer)):
+        return int(project)
+    m = 0
+    for u in project:
+        m |= 1 << int(u)
+    return m
+
+
+def match(g: OracleGraph, q, cap: int = 1 << 20, time_limit_s: float = 0.0, project=None) -> Result:
+    """Every embedding (count, fingerprint) and the smallest `cap` distinct
+    rows over the projected vertices (all vertices when project is None)."""
     lib = _load()
     vt, vb, es, ed, er = _q(q)
     k = vt.shape[0]
-    cnt, fp, nr = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
-    rows = np.zeros((max(cap, 0), k), np.uint32) if cap else np.zeros((0, k), np.uint32)
-    st = lib.orc_match(g._h, k, es.shape[0], _p(vt), _p(vb), _p(es), _p(ed), _p(er), cap, ctypes.byref(cnt),
-                       ctypes.byref(fp), _p(rows) if cap else None, ctypes.byref(nr), time_limit_s)
-    return Result(st, cnt.value, fp.value, rows[: nr.value].copy())
+    pm = project_mask(project)
+    w = k if pm == 0 else bin(pm & ((1 << k) - 1)).count("1")
+    cnt, fp, nr, tr = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint32()
+    rows = np.zeros((max(cap, 0), w), np.uint32) if cap else np.zeros((0, w), np.uint32)
+    st = lib.orc_match_proj(g._h, k, es.shape[0], _p(vt), _p(vb), _p(es), _p(ed), _p(er), pm, cap,
+                            ctypes.byref(cnt), ctypes.byref(fp), _p(rows) if cap else None, ctypes.byref(nr),
+                            ctypes.byref(tr), time_limit_s)
+    return Result(st, cnt.value, fp.value, rows[: nr.value].copy(), bool(tr.value))
 
 
 def match_many(g: OracleGraph, queries, threads: int = 0, time_limit_s: float = 0.0):

@@ -20,6 +20,10 @@
  *     neighbour) repeated "until no more can be pruned" (Section 3.3.3,
  *     "Candidate Nodes Refinement");
  *   - the candidate-edge tables of Section 3.3.4 ("Joining Phase");
+ *   - projection (Section 3.5, "Modify the query plan": only the matches of
+ *     a subset of the query vertices are wanted): the rows returned are the
+ *     distinct tuples (f(u)) over the projected vertices u, ascending, while
+ *     the count and fingerprint still cover every embedding;
  *   - variable edges (Section 3.2: a relation may itself be a variable):
  *     a query edge with relation ORC_ANY maps onto a data edge of any
  *     relation.  An embedding is still a map of vertices, so two data edges
@@ -215,10 +219,12 @@ uint64_t orc_fingerprint(uint32_t k, const uint32_t *rows, uint64_t n) {
 /* --------------------------------------------------------- row collection */
 typedef struct {
   uint32_t k;
-  uint64_t cap;        /* keep the cap lexicographically smallest rows */
+  uint32_t w, proj[32];  /* stored row: f(proj[0]), ..., f(proj[w-1]) */
+  uint64_t cap;          /* keep the cap lexicographically smallest distinct rows */
   uint64_t n, room;
   uint32_t *rows;
   uint64_t count, fp;
+  int more;              /* more than cap distinct rows were seen */
 } orc_sink;
 
 static __thread uint32_t g_sort_k;
@@ -227,17 +233,26 @@ static int cmp_row(const void *a, const void *b) {
   for (uint32_t i = 0; i < g_sort_k; ++i) if (x[i] != y[i]) return x[i] < y[i] ? -1 : 1;
   return 0;
 }
+/* Sort the stored rows, drop repeats (only projected rows can repeat) and
+ * keep the first cap. */
 static void orc_sink_trim(orc_sink *s) {
-  g_sort_k = s->k;
-  qsort(s->rows, s->n, sizeof(uint32_t) * s->k, cmp_row);
-  if (s->n > s->cap) s->n = s->cap;
+  g_sort_k = s->w;
+  qsort(s->rows, s->n, sizeof(uint32_t) * s->w, cmp_row);
+  uint64_t d = 0;
+  for (uint64_t i = 0; i < s->n; ++i)
+    if (d == 0 || cmp_row(s->rows + (d - 1) * s->w, s->rows + i * s->w) != 0) {
+      if (d != i) memcpy(s->rows + d * s->w, s->rows + i * s->w, sizeof(uint32_t) * s->w);
+      d++;
+    }
+  s->n = d;
+  if (s->n > s->cap) { s->n = s->cap; s->more = 1; }
 }
 static void orc_sink_put(orc_sink *s, const uint32_t *row) {
   s->count++;
   s->fp += orc_row_hash(s->k, row);
   if (s->cap == 0) return;
   if (s->n == s->room) orc_sink_trim(s);
-  memcpy(s->rows + s->n * s->k, row, sizeof(uint32_t) * s->k);
+  for (uint32_t i = 0; i < s->w; ++i) s->rows[s->n * s->w + i] = row[s->proj[i]];
   s->n++;
 }
 
@@ -316,23 +331,28 @@ void orc_extend(orc_bt *b, uint32_t depth) {
 }
 
 /*
- * orc_match: every embedding of the query (Definition 3.2 read for directed,
- * relation-labelled graphs with bound and typed vertices).
+ * orc_match_proj: every embedding of the query (Definition 3.2 read for
+ * directed, relation-labelled graphs with bound and typed vertices).
  * Outputs: *count = number of embeddings; *fp = fingerprint (sum of
- * orc_row_hash); rows_out = the min(count, cap) lexicographically smallest
- * embeddings in query-vertex order, row-major [nrows][k]; *nrows.
- * time_limit_s > 0 stops the search after that long (returns 2).
- * Returns 0 on success, 1 for an invalid query, 2 on time-out.
+ * orc_row_hash over the embeddings); rows_out = the lexicographically
+ * smallest min(D, cap) of the D distinct tuples (f(u)) over the query
+ * vertices u in `project` (a bit mask, ascending u; 0 = every vertex, when
+ * the tuples are the embeddings themselves), row-major [nrows][w];
+ * *truncated = D > cap.  time_limit_s > 0 stops the search after that long
+ * (returns 2).  Returns 0 on success, 1 for an invalid query, 2 on
+ * time-out.
  *
  * Matching order: a bound vertex first (lowest index), else vertex 0; then
  * repeatedly the unmatched vertex with the most edges to matched vertices
  * (lowest index on ties).  The order only changes the running time.
  */
-int orc_match(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype, const uint32_t *vbind,
-              const uint32_t *esrc, const uint32_t *edst, const uint32_t *erel, uint64_t cap,
-              uint64_t *count, uint64_t *fp, uint32_t *rows_out, uint64_t *nrows, double time_limit_s) {
+int orc_match_proj(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype, const uint32_t *vbind,
+                   const uint32_t *esrc, const uint32_t *edst, const uint32_t *erel, uint32_t project, uint64_t cap,
+                   uint64_t *count, uint64_t *fp, uint32_t *rows_out, uint64_t *nrows, uint32_t *truncated,
+                   double time_limit_s) {
   orc_query q;
   if (orc_query_make(&q, k, m, vtype, vbind, esrc, edst, erel) != 0) return 1;
+  if (k < 32 && (project >> k) != 0) return 1;
   for (uint32_t u = 0; u < k; ++u) {
     if (vbind[u] != ORC_UNBOUND && vbind[u] >= g->V) return 1;
     if (vtype[u] != ORC_ANY && vtype[u] >= g->T) return 1;
@@ -359,8 +379,10 @@ int orc_match(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype,
   orc_sink sink;
   memset(&sink, 0, sizeof sink);
   sink.k = k; sink.cap = cap;
+  for (uint32_t u = 0; u < k; ++u)
+    if (project == 0 || ((project >> u) & 1u)) sink.proj[sink.w++] = u;
   sink.room = cap == 0 ? 0 : (cap < (1u << 20) ? 2 * cap : cap + (1u << 20));
-  sink.rows = cap ? (uint32_t *)malloc(sizeof(uint32_t) * k * sink.room) : NULL;
+  sink.rows = cap ? (uint32_t *)malloc(sizeof(uint32_t) * sink.w * sink.room) : NULL;
   b.sink = &sink;
   b.used = (uint8_t *)calloc(g->V ? g->V : 1, 1);
   b.deadline = time_limit_s > 0 ? orc_now() + time_limit_s : 0;
@@ -368,9 +390,18 @@ int orc_match(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype,
   free(b.used);
   if (cap) orc_sink_trim(&sink);
   *count = sink.count; *fp = sink.fp; *nrows = sink.n;
-  if (cap && rows_out) memcpy(rows_out, sink.rows, sizeof(uint32_t) * k * sink.n);
+  if (truncated) *truncated = cap ? (uint32_t)sink.more : (sink.count > 0);
+  if (cap && rows_out) memcpy(rows_out, sink.rows, sizeof(uint32_t) * sink.w * sink.n);
   free(sink.rows);
   return b.timed_out ? 2 : 0;
+}
+
+/* orc_match_proj over every query vertex: rows are the embeddings. */
+int orc_match(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *vtype, const uint32_t *vbind,
+              const uint32_t *esrc, const uint32_t *edst, const uint32_t *erel, uint64_t cap,
+              uint64_t *count, uint64_t *fp, uint32_t *rows_out, uint64_t *nrows, double time_limit_s) {
+  return orc_match_proj(g, k, m, vtype, vbind, esrc, edst, erel, 0, cap, count, fp, rows_out, nrows, NULL,
+                        time_limit_s);
 }
 
 /*

@@ -224,6 +224,53 @@ def test_variable_edge_degree_test_counts_distinct_neighbours():
         assert [bool(x) for x in c0[1]] == [ins[v] >= 1 for v in range(g.num_vertices)]
 
 
+# ------------------------------------------------------------ projection
+def test_projection_is_the_distinct_projected_embeddings():
+    """Projection (only some query vertices' matches are wanted): the rows
+    are the distinct tuples of the projected columns of the embeddings,
+    ascending (here from a Python enumeration and numpy's unique), cut at
+    cap with `truncated` when more exist; count and fingerprint still cover
+    every embedding."""
+    rng = np.random.default_rng(606)
+    dup = 0
+    for case in range(400):
+        g, q = random_tiny(rng, n_max=6, k_max=4, p_any=0.2)
+        o = og(g)
+        full = np.asarray(python_brute(g, q), np.uint32).reshape(-1, q.k)
+        cols = [u for u in range(q.k) if rng.random() < 0.5] or [int(rng.integers(q.k))]
+        want = np.unique(full[:, cols], axis=0) if len(full) else np.zeros((0, len(cols)), np.uint32)
+        dup += len(want) < len(full)
+        r = O.match(o, q, cap=1 << 16, project=cols)
+        assert (r.count, r.fingerprint) == (len(full), O.fingerprint(full))
+        np.testing.assert_array_equal(r.rows, want)
+        assert r.truncated is False
+        for cap in (1, 2, 3):
+            t = O.match(o, q, cap=cap, project=cols)
+            np.testing.assert_array_equal(t.rows, want[:cap])
+            assert t.truncated == (len(want) > cap) and t.count == len(full)
+        a = O.match(o, q, cap=1 << 16, project=list(range(q.k)))
+        np.testing.assert_array_equal(a.rows, full)
+    assert dup > 40
+
+
+@pytest.mark.parametrize("n,k", [(7, 3), (8, 4), (9, 5)])
+def test_projection_closed_forms(n, k):
+    """Complete digraph K_n, directed k-path: the endpoints take every
+    ordered pair of distinct vertices (n(n-1) rows), the start every vertex
+    (n rows).  Transitive tournament (i->j iff i<j), directed k-path: the
+    start takes 0..n-k and the end k-1..n-1 (n-k+1 rows each)."""
+    path = query(k, [(i, i + 1, 0) for i in range(k - 1)])
+    o = og(complete_digraph(n))
+    r = O.match(o, path, cap=1 << 16, project=[0, k - 1])
+    assert r.count == perm(n, k) and len(r.rows) == perm(n, 2)
+    assert {tuple(x) for x in r.rows} == {(a, b) for a in range(n) for b in range(n) if a != b}
+    assert O.match(o, path, cap=1 << 16, project=[0]).rows[:, 0].tolist() == list(range(n))
+    t = og(transitive_tournament(n))
+    assert O.match(t, path, cap=1 << 16, project=[0]).rows[:, 0].tolist() == list(range(n - k + 1))
+    assert O.match(t, path, cap=1 << 16, project=[k - 1]).rows[:, 0].tolist() == list(range(k - 1, n))
+    assert O.match(t, path, cap=1 << 16, project=1 << k).status == 1   # vertex out of range
+
+
 # --------------------------------------------------------- worked example
 def test_worked_example():
     """Facts printed for the thesis's sample query/data graph (Section 3.3):
