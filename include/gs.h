@@ -16,6 +16,11 @@
  *     vertices, so a pair joined under several relations counts once.
  * The engine returns every embedding: the exact count always, plus the
  * lexicographically smallest `cap` embeddings written in query-vertex order.
+ * With a projection (gs_match_opts.project, Section 3.5: only the matches
+ * of a subset of the query vertices are wanted) the rows are instead the
+ * lexicographically smallest `cap` DISTINCT tuples (f(u)) over the
+ * projected vertices u, in ascending u; count and fingerprint still cover
+ * every embedding.
  *
  * Conventions for every call:
  *   - Return value: a gs_status.  On failure nothing is returned through the
@@ -126,6 +131,10 @@ typedef struct {
   void *cuda_stream;          /* cudaStream_t; NULL = the library's own stream */
   gs_chunk_cb on_chunk;       /* GS_CHUNKED: required; otherwise ignored */
   void *user;                 /* passed to on_chunk */
+  uint32_t project;           /* bit u set: return f(u); 0 (or every vertex) = whole
+                                 embeddings.  A bit >= k -> GS_ERR_INVALID; with
+                                 GS_CHUNKED -> GS_ERR_UNSUPPORTED */
+  uint32_t reserved;          /* 0 */
 } gs_match_opts;
 
 /* Synchronous copy of `bytes` bytes from device memory to host memory, for
@@ -134,10 +143,11 @@ gs_status gs_memcpy_d2h(void *dst, const void *src, uint64_t bytes);
 
 typedef struct {
   uint64_t count;        /* exact number of embeddings */
-  uint64_t num_rows;     /* rows returned = min(count, cap); 0 for GS_CHUNKED */
+  uint64_t num_rows;     /* rows returned = min(count, cap) (projected: min(distinct
+                            tuples, cap)); 0 for GS_CHUNKED */
   uint64_t fingerprint;  /* sum over ALL embeddings of an order-free 64-bit row hash */
-  uint32_t k;            /* row width */
-  uint32_t truncated;    /* 1 if count > cap */
+  uint32_t k;            /* row width: query vertices, or projected vertices */
+  uint32_t truncated;    /* 1 if count > cap (projected: more distinct tuples than cap) */
   uint32_t *rows;        /* [num_rows * k] row-major, query-vertex order, ascending; owned */
   uint32_t status;       /* gs_status of this query (batch calls) */
   uint32_t reserved;

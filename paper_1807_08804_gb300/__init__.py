@@ -55,7 +55,7 @@ ChunkCallback = ctypes.CFUNCTYPE(None, ctypes.c_void_p, U64, U32, U32, ctypes.c_
 
 class MatchOpts(ctypes.Structure):
     _fields_ = [("cap", U64), ("mode", U32), ("max_refine_rounds", U32), ("chunk_bytes", U64), ("cuda_stream", P),
-                ("on_chunk", ChunkCallback), ("user", P)]
+                ("on_chunk", ChunkCallback), ("user", P), ("project", U32), ("reserved", U32)]
 
 
 class ResultDesc(ctypes.Structure):
@@ -187,10 +187,25 @@ class _QueryPack:
         self.arr = ctypes.cast(d.ctypes.data, ctypes.POINTER(QueryDesc))
 
 
-def _opts(cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0, stream=None, on_chunk=None) -> MatchOpts:
+def project_mask(project) -> int:
+    """Projection as the library's bit mask: None = whole embeddings, an int
+    is taken as the mask, else an iterable of query vertices."""
+    if project is None:
+        return 0
+    if isinstance(project, (int, np.integer)):
+        return int(project)
+    m = 0
+    for u in project:
+        m |= 1 << int(u)
+    return m
+
+
+def _opts(cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0, stream=None, on_chunk=None,
+          project=None) -> MatchOpts:
     o = MatchOpts(cap, mode, max_refine_rounds, chunk_bytes, stream)
     if on_chunk is not None:
         o.on_chunk = on_chunk
+    o.project = project_mask(project)
     return o
 
 
@@ -305,22 +320,23 @@ class DeviceGraph:
 
 
 def match(dg: DeviceGraph, q, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0,
-          on_chunk=None) -> MatchResult:
+          on_chunk=None, project=None) -> MatchResult:
     """on_chunk(rows, query): with mode=GS_CHUNKED, called with every chunk
-    of embeddings (uint32 [n, k], query-vertex order) as it is produced."""
+    of embeddings (uint32 [n, k], query-vertex order) as it is produced.
+    project: query vertices whose distinct tuples are returned as rows."""
     pack = _QueryPack([q])
     cb = _chunk_callback(on_chunk)
-    o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb)
+    o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb, project=project)
     r = ResultDesc()
     _check(lib().gs_match(dg._h, pack.arr, ctypes.byref(o), ctypes.byref(r)))
     return _take(r)
 
 
 def match_batch(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0,
-                chunk_bytes=0, on_chunk=None, raw_chunks=False) -> list[MatchResult]:
+                chunk_bytes=0, on_chunk=None, raw_chunks=False, project=None) -> list[MatchResult]:
     pack = _QueryPack(queries)
     cb = _chunk_callback(on_chunk, raw_chunks)
-    o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb)
+    o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb, project=project)
     res = (ResultDesc * max(len(queries), 1))()
     _check(lib().gs_match_batch(dg._h, pack.arr, len(queries), ctypes.byref(o), res))
     return _take_all(res, len(queries))
@@ -330,12 +346,12 @@ class Batch:
     """A prepared batch (device-resident queries, captured pipeline graph)."""
 
     def __init__(self, dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0,
-                 wave_queries=0, stream=None, on_chunk=None, raw_chunks=False):
+                 wave_queries=0, stream=None, on_chunk=None, raw_chunks=False, project=None):
         self.dg = dg
         self.n = len(queries)
         self._pack = _QueryPack(queries)
         self._cb = _chunk_callback(on_chunk, raw_chunks)  # kept alive: every finish() may call it
-        o = _opts(cap, mode, max_refine_rounds, chunk_bytes, stream, on_chunk=self._cb)
+        o = _opts(cap, mode, max_refine_rounds, chunk_bytes, stream, on_chunk=self._cb, project=project)
         self._h = P()
         if wave_queries:
             _check(lib().gs_batch_create_waves(dg._h, self._pack.arr, self.n, ctypes.byref(o), wave_queries,
@@ -442,9 +458,9 @@ class Server:
         self._h = P()
         _check(lib().gs_serve_create(dg._h, ctypes.byref(o), ctypes.byref(self._h)))
 
-    def submit(self, q, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0) -> int:
+    def submit(self, q, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, project=None) -> int:
         pack = _QueryPack([q])
-        o = _opts(cap, mode, max_refine_rounds, 0)
+        o = _opts(cap, mode, max_refine_rounds, 0, project=project)
         t = U64()
         _check(lib().gs_serve_submit(self._h, pack.arr, ctypes.byref(o), ctypes.byref(t)))
         return t.value

@@ -87,6 +87,13 @@ gs_status pack_query(const DevGraph &G, const gs_query *q, const gs_match_opts *
   // are streamed by the chunked join when the batch finishes
   d->mode = mode == GS_CHUNKED ? GS_COUNT_ONLY : mode;
   d->cap = o ? o->cap : 0;
+  // projection (Section 3.5): output columns of the projected vertices
+  const uint32_t pm = o ? o->project : 0;
+  if (pm >> k) return fail(GS_ERR_INVALID, "projection names a vertex >= k");
+  d->proj = pm == (1u << k) - 1 ? 0u : pm;
+  if (d->proj && mode == GS_CHUNKED) return fail(GS_ERR_UNSUPPORTED, "projection with GS_CHUNKED");
+  for (uint32_t u = 0; u < k; ++u)
+    if (!d->proj || ((d->proj >> u) & 1u)) d->pu[d->kp++] = (uint8_t)u;
   d->force_root = 0xFF;
   d->force_from_src = 0xFF;
   d->status = QS_OK;
@@ -251,9 +258,12 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
     A(W.sval[i], s.out_rows);
   }
   A(W.msplit, s.out_rows / kTileRows + W.nq + 1);
+  A(W.ptcount, s.out_rows / kTileRows + W.nq + 1);
+  A(W.ptscan, s.out_rows / kTileRows + W.nq + 2);
   A(W.sel, W.nq);
   A(W.shist, (uint64_t)W.nq * 256);
-  uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * cps, (uint64_t)W.nqe, s.ec_items, W.row_cap}));
+  uint64_t tmpw = scan_tmp_words(std::max<uint64_t>(
+      {(uint64_t)W.nqv * cps, (uint64_t)W.nqe, s.ec_items, W.row_cap, s.out_rows / kTileRows + W.nq + 1}));
   A(b->scan_tmp, tmpw);
   b->scan_tmp_words = tmpw;
   A(b->type_count, G.T);
@@ -442,13 +452,13 @@ void enqueue_back(Pipe &P, int K, int stop) {
 // directly: the host reads the largest output first).
 // Launches of enqueue_large_sort for the largest output and the number of
 // outputs cut at cap.
-uint64_t large_sort_launches(uint64_t max_rows, uint64_t over_cap) {
+uint64_t large_sort_launches(uint64_t max_rows, uint64_t over_cap, bool proj) {
   uint64_t passes = 0;
   for (uint64_t run = kTileRows; run < max_rows; run *= 2) ++passes;
-  return 3 + 2 * passes + (over_cap ? 3 + 2 * 3 : 0);
+  return 3 + 2 * passes + (over_cap ? 3 + 2 * 3 : 0) + (proj ? 3 : 0);
 }
 
-void enqueue_large_sort(Pipe &P, uint64_t max_rows, uint64_t over_cap) {
+void enqueue_large_sort(Pipe &P, uint64_t max_rows, uint64_t over_cap, bool proj) {
   gs_batch *b = P.b;
   Wave &W = b->W;
   const int sms = b->sms;
@@ -470,6 +480,9 @@ void enqueue_large_sort(Pipe &P, uint64_t max_rows, uint64_t over_cap) {
   P.end();
   P.begin(KK_GATHER);
   launch_gather(W, perm[0], perm[1], P.cur, sms);
+  if (proj)  // projected outputs: first row of each distinct tuple, first cap of them
+    launch_project(W, perm[0], perm[1], keys[0], keys[1], W.out_rows_cap / kTileRows + W.nq + 1, b->scan_tmp, P.cur,
+                   sms);
   P.end();
 }
 
@@ -604,8 +617,8 @@ static gs_status wave_end(gs_batch *b, size_t w) {
   const int K = b->wave_k[w];
   if (b->sorting && b->flag[0] != 0) {
     Pipe P{b, &b->sort_evs_direct, false, b->stream};
-    enqueue_large_sort(P, b->flag[1], b->flag[2]);
-    b->kernel_launches += large_sort_launches(b->flag[1], b->flag[2]);
+    enqueue_large_sort(P, b->flag[1], b->flag[2], b->has_proj);
+    b->kernel_launches += large_sort_launches(b->flag[1], b->flag[2], b->has_proj);
     b->large_sorts++;
   }
   if (b->use_graph) {
@@ -658,6 +671,7 @@ static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match
   b->n = n;
   b->hq.assign(n, DQuery{});
   b->hstatus.assign(n, GS_OK);
+  b->has_proj = false;
   for (uint32_t i = 0; i < n; ++i) {
     gs_status st = pack_query(b->g->d, &qs[i], opts, &b->hq[i]);
     b->hstatus[i] = st;
@@ -665,6 +679,7 @@ static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match
       memset(&b->hq[i], 0, sizeof(DQuery));
       b->hq[i].status = QS_INVALID;
     }
+    b->has_proj = b->has_proj || b->hq[i].proj != 0;
   }
   b->ran = b->finished = false;
 }
@@ -894,6 +909,8 @@ gs_status grow_pools(gs_batch *b) {
     bool ok = regrow(b, &W.out_q, n) == GS_OK;
     for (int i = 0; i < 2 && ok; ++i) ok = regrow(b, &W.skey[i], n) == GS_OK && regrow(b, &W.sval[i], n) == GS_OK;
     ok = ok && regrow(b, &W.msplit, n / kTileRows + W.nq + 1) == GS_OK;
+    ok = ok && regrow(b, &W.ptcount, n / kTileRows + W.nq + 1) == GS_OK;
+    ok = ok && regrow(b, &W.ptscan, n / kTileRows + W.nq + 2) == GS_OK;
     if (ok) { W.out_rows_cap = n; changed = true; }
   }
   if (hw[HW_OUT_WORDS] > W.out_words && hw[HW_OUT_WORDS] <= kMaxEntries) {
@@ -906,7 +923,8 @@ gs_status grow_pools(gs_batch *b) {
   }
   if (changed) {
     const uint64_t cps = W.G.nchunks;  // chunks per set: one candidate count per chunk
-    uint64_t tmpw = scan_tmp_words(std::max<uint64_t>({(uint64_t)W.nqv * cps, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap}));
+    uint64_t tmpw = scan_tmp_words(std::max<uint64_t>(
+        {(uint64_t)W.nqv * cps, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap, W.out_rows_cap / kTileRows + W.nq + 1}));
     if (regrow(b, &b->scan_tmp, tmpw) == GS_OK) {
       b->scan_tmp_words = tmpw;
       GS_CUDA(cudaMemsetAsync(b->scan_tmp, 0, sizeof(uint64_t) * tmpw, b->stream));
@@ -945,6 +963,7 @@ gs_status batch_finish(gs_batch *b) {
   if (gst != GS_OK) return gst;
   b->fb_rows.assign(n, {});
   b->fb_done.assign(n, 0);
+  b->fb_more.assign(n, 0);
   b->fallbacks = 0;
   for (uint32_t i = 0; i < n; ++i) {
     if (b->hstatus[i] != GS_OK) continue;
@@ -967,6 +986,7 @@ gs_status batch_fetch(gs_batch *b, gs_result *outs) {
     gs_result &r = outs[i];
     memset(&r, 0, sizeof(r));
     r.k = b->hq[i].k;
+    const bool proj = b->hq[i].proj != 0;
     if (b->hstatus[i] != GS_OK) {
       r.status = b->hstatus[i];
       continue;
@@ -976,7 +996,12 @@ gs_status batch_fetch(gs_batch *b, gs_result *outs) {
     r.fingerprint = b->fp[i];
     const uint64_t cap = b->hq[i].mode == GS_COUNT_ONLY ? 0 : b->hq[i].cap;
     r.truncated = !b->on_chunk && r.count > cap ? 1 : 0;  // GS_CHUNKED delivered every row
+    if (proj) {  // rows of the projected vertices; truncated when distinct tuples exceed cap
+      r.k = b->hq[i].kp;
+      if (cap) r.truncated = 0;
+    }
     if (b->fb_done[i]) {
+      if (proj && cap) r.truncated = b->fb_more[i];
       r.num_rows = b->fb_rows[i].size() / (r.k ? r.k : 1);
       if (r.num_rows) {
         r.rows = static_cast<uint32_t *>(malloc(4 * b->fb_rows[i].size()));
@@ -988,7 +1013,8 @@ gs_status batch_fetch(gs_batch *b, gs_result *outs) {
     if (st == QS_OK || st == QS_EMPTY) {
       r.status = GS_OK;
       if (st == QS_EMPTY) { r.count = 0; r.fingerprint = 0; r.truncated = 0; }
-      r.num_rows = b->nrows[i];
+      r.num_rows = b->nrows[i] & ~kRowsMore;
+      if (proj && cap && (b->nrows[i] & kRowsMore)) r.truncated = 1;
       if (r.num_rows) {
         const uint64_t words = r.num_rows * r.k;
         r.rows = static_cast<uint32_t *>(malloc(4 * words));

@@ -55,6 +55,9 @@ struct DQuery {
   uint8_t need_cnt[2 * kMaxM];
   uint32_t mode;
   uint64_t cap;
+  uint32_t proj;                    // projected vertices (bit mask); 0 = whole embeddings
+  uint8_t kp;                       // output columns: the projected vertices pu[0..kp), ascending
+  uint8_t pu[kMaxK];                //   (every vertex when proj == 0)
   uint8_t force_root;               // 0xFF, or the first visited vertex (inspection runs)
   uint8_t force_from_src;           // 0xFF, or a fixed edge-table orientation (inspection runs)
   // plan (device)
@@ -65,6 +68,7 @@ struct DQuery {
   uint8_t init_step[kMaxK];         // exploration step after which u has a candidate set
   uint8_t join[kMaxK];              // join order
   uint8_t pos[kMaxK];               // position of u in the join order
+  uint8_t opos[kMaxK];              // join-order column of output column i (pos[pu[i]])
   uint8_t from_src[kMaxM];          // edge-table orientation (1: keyed by esrc)
   uint32_t xinc[2 * kMaxM];         // incident edges packed by the plan (xinc_pack), same order as inc_edge
   uint32_t status;
@@ -101,7 +105,13 @@ struct QState {
   uint64_t lrg_row_base;                             // rows sorted by the merge path
   uint64_t lrg_tile_base;                            // their first tile
   uint64_t sort_rows;                                // rows entering the merge sort (after selection)
+  uint64_t nfinal;                                   // rows returned (projected: distinct tuples, at most cap)
+  uint32_t more;                                     // projected: more distinct tuples than cap
 };
+
+// BatchOut::nrows top bit: a projected query had more distinct tuples than
+// the rows returned.
+constexpr uint64_t kRowsMore = 1ull << 63;
 
 // Top-cap selection of a query with more than cap large rows (radix select
 // on the packed sort keys): rows with key <= thresh go into the sort.
@@ -203,6 +213,8 @@ struct Wave {
   uint64_t *skey[2];                    // sort keys of the large-output merge sort
   uint32_t *sval[2];                    // row indices of the large-output merge sort
   uint64_t *msplit;                     // merge-path split of each output tile
+  uint32_t *ptcount;                    // projected outputs: distinct tuples starting in each tile
+  uint64_t *ptscan;                     //   and their scan [tiles + 1]
   SelState *sel;                        // [nq] top-cap selection
   uint32_t *shist;                      // [nq][256] digit histograms of the selection
   int stats;
@@ -237,6 +249,8 @@ void launch_tile_sort(const Wave &W, const uint32_t *pin, const uint64_t *kin, u
 void launch_merge_pass(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
                        uint64_t run, cudaStream_t s, int sms);
 void launch_gather(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, cudaStream_t s, int sms);
+void launch_project(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, const uint64_t *key0,
+                    const uint64_t *key1, uint64_t max_tiles, uint64_t *scan_tmp, cudaStream_t s, int sms);
 void launch_epilogue(const Wave &W, cudaStream_t s, int sms);
 
 }  // namespace gs

@@ -39,16 +39,46 @@ __global__ void k_col_keys(const uint32_t *rows, uint32_t k, const uint32_t *per
     key[i] = rows[(uint64_t)perm[i] * k + col];
 }
 
-// out[i] = row perm[i] for i < keep, columns reordered by `order` (order[u] =
+// out[i] = row perm[i] for i < keep, w columns taken in `order` (order[u] =
 // source column of output column u).
 struct ColOrder {
   uint8_t c[kMaxK];
 };
 __global__ void k_take_rows(const uint32_t *rows, uint32_t k, const uint32_t *perm, uint64_t keep, ColOrder order,
-                            uint32_t *out) {
+                            uint32_t w, uint32_t *out) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < keep; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t *src = rows + (uint64_t)perm[i] * k;
-    for (uint32_t u = 0; u < k; ++u) out[i * k + u] = src[order.c[u]];
+    for (uint32_t u = 0; u < w; ++u) out[i * w + u] = src[order.c[u]];
+  }
+}
+
+// Projection: flag[i] = 1 when row perm[i] starts a new tuple of the
+// projected columns `cols` (rows sorted on them), i.e. differs from row
+// perm[i-1] on one of them.
+__global__ void k_proj_flags(const uint32_t *rows, uint32_t k, const uint32_t *perm, const uint64_t *d_n, ColOrder cols,
+                             uint32_t ncols, uint32_t *flag) {
+  const uint64_t n = *d_n;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t f = 1;
+    if (i > 0) {
+      const uint32_t *a = rows + (uint64_t)perm[i] * k, *b = rows + (uint64_t)perm[i - 1] * k;
+      f = 0;
+      for (uint32_t j = 0; j < ncols; ++j) f |= a[cols.c[j]] != b[cols.c[j]];
+    }
+    flag[i] = f;
+  }
+}
+
+// out[scan[i]] = row perm[i] (w columns in `order`) for every flagged i whose
+// rank scan[i] is below keep.
+__global__ void k_take_distinct(const uint32_t *rows, uint32_t k, const uint32_t *perm, const uint32_t *flag,
+                                const uint64_t *scan, const uint64_t *d_n, uint64_t keep, ColOrder order, uint32_t w,
+                                uint32_t *out) {
+  const uint64_t n = *d_n;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (!flag[i] || scan[i] >= keep) continue;
+    const uint32_t *src = rows + (uint64_t)perm[i] * k;
+    for (uint32_t u = 0; u < w; ++u) out[scan[i] * w + u] = src[order.c[u]];
   }
 }
 
@@ -122,6 +152,8 @@ struct Fallback {
   uint64_t *stmp = nullptr;  // scan scratch (zeroed when allocated)
   // rows of queries with more than cap embeddings
   uint32_t *top = nullptr, *top2 = nullptr, *perm[2] = {}, *key[2] = {};
+  uint32_t *pflag = nullptr;                     // projection: run starts [top_rows]
+  uint64_t *pscan = nullptr, *ptmp = nullptr;    //   their scan [top_rows + 1] and scan scratch
   uint64_t top_rows = 0;  // capacity in rows
   uint32_t top_k = 0;
   std::vector<void *> allocs;
@@ -193,18 +225,24 @@ static gs_status fallback_ctx(gs_graph *g, Fallback **out) {
 static gs_status ensure_top(Fallback *f, uint64_t rows, uint32_t k) {
   if (f->top && f->top_rows >= rows && f->top_k >= k) return GS_OK;
   for (void *p : {(void *)f->top, (void *)f->top2, (void *)f->perm[0], (void *)f->perm[1], (void *)f->key[0],
-                  (void *)f->key[1]}) {
+                  (void *)f->key[1], (void *)f->pflag, (void *)f->pscan, (void *)f->ptmp}) {
     if (!p) continue;
     cudaFree(p);
     f->allocs.erase(std::remove(f->allocs.begin(), f->allocs.end(), p), f->allocs.end());
   }
-  f->top = f->top2 = f->perm[0] = f->perm[1] = f->key[0] = f->key[1] = nullptr;
+  f->top = f->top2 = f->perm[0] = f->perm[1] = f->key[0] = f->key[1] = f->pflag = nullptr;
+  f->pscan = f->ptmp = nullptr;
   gs_status st = falloc(f, &f->top, rows * k);
   if (st == GS_OK) st = falloc(f, &f->top2, rows * k);
   for (int i = 0; i < 2 && st == GS_OK; ++i) {
     st = falloc(f, &f->perm[i], rows);
     if (st == GS_OK) st = falloc(f, &f->key[i], rows);
   }
+  if (st == GS_OK) st = falloc(f, &f->pflag, rows);
+  if (st == GS_OK) st = falloc(f, &f->pscan, rows + 1);
+  if (st == GS_OK) st = falloc(f, &f->ptmp, scan_tmp_words(rows));
+  if (st == GS_OK && cudaMemset(f->ptmp, 0, sizeof(uint64_t) * scan_tmp_words(rows)) != cudaSuccess)
+    st = fail(GS_ERR_CUDA, "cudaMemset (fallback projection scratch)");
   if (st != GS_OK) return st;
   // radix scratch for `rows` items
   void *t = nullptr;
@@ -239,6 +277,12 @@ struct FbRun {
   gs_chunk_cb cb = nullptr;
   void *user = nullptr;
   uint32_t query = 0;
+  // output columns: the projected vertices pu[0..kp) (every vertex when not
+  // projecting); more: more distinct projected tuples than cap were seen
+  uint32_t kp = 0;
+  uint8_t pu[kMaxK] = {};
+  bool proj = false, more = false;
+  uint64_t kept = 0;  // rows the last sort kept
 };
 
 template <typename T>
@@ -248,30 +292,49 @@ gs_status d2h1(T *dst, const T *src, cudaStream_t s) {
   return GS_OK;
 }
 
-// Sort the collected rows (join-order columns) into query-vertex
-// lexicographic order and keep the first `keep`; if `final`, write them in
-// query-vertex column order into top2.
+// Sort the collected rows (join-order columns) lexicographically on the
+// output columns in query-vertex order and keep the first `keep` (for a
+// projection: the first row of each distinct projected tuple, the first
+// `keep` of those); if `final`, write the output columns in query-vertex
+// order into top2, else keep whole rows in top.
 gs_status sort_top(FbRun &R, uint64_t keep, bool final) {
   Fallback *f = R.f;
   const uint64_t n = R.top_n;
+  R.kept = 0;
   if (n == 0) return GS_OK;
   GS_CUDA(cudaMemcpyAsync(f->d_n, &n, sizeof(n), cudaMemcpyHostToDevice, R.s));
   k_iota_n<<<grid_n(n, R.sms), kT, 0, R.s>>>(f->perm[0], f->d_n);
   int cur = 0;
-  for (int u = (int)R.k - 1; u >= 0; --u) {
-    k_col_keys<<<grid_n(n, R.sms), kT, 0, R.s>>>(f->top, R.k, f->perm[cur], f->d_n, R.pos[u], f->key[0]);
+  for (int c = (int)R.kp - 1; c >= 0; --c) {  // least significant column first (stable passes)
+    k_col_keys<<<grid_n(n, R.sms), kT, 0, R.s>>>(f->top, R.k, f->perm[cur], f->d_n, R.pos[R.pu[c]], f->key[0]);
     int r = radix_sort_pairs(f->key[0], f->perm[cur], f->key[1], f->perm[cur ^ 1], f->d_n, f->top_rows, 0, R.nbits,
                              f->tmp, R.s, R.sms);
     cur = r ? cur ^ 1 : cur;
   }
-  keep = std::min(keep, n);
+  const uint32_t w = final ? R.kp : R.k;
   ColOrder ord;
-  for (uint32_t u = 0; u < R.k; ++u) ord.c[u] = final ? R.pos[u] : (uint8_t)u;
-  k_take_rows<<<grid_n(keep, R.sms), kT, 0, R.s>>>(f->top, R.k, f->perm[cur], keep, ord, f->top2);
+  for (uint32_t u = 0; u < w; ++u) ord.c[u] = final ? R.pos[R.pu[u]] : (uint8_t)u;
+  if (R.proj) {
+    ColOrder cols;
+    for (uint32_t c = 0; c < R.kp; ++c) cols.c[c] = R.pos[R.pu[c]];
+    k_proj_flags<<<grid_n(n, R.sms), kT, 0, R.s>>>(f->top, R.k, f->perm[cur], f->d_n, cols, R.kp, f->pflag);
+    scan_u32(f->pflag, f->pscan, f->d_n, f->top_rows, f->ptmp, R.s, R.sms);
+    uint64_t d = 0;
+    gs_status st = d2h1(&d, f->pscan + n, R.s);
+    if (st != GS_OK) return st;
+    if (d > R.cap) R.more = true;
+    keep = std::min(keep, d);
+    k_take_distinct<<<grid_n(n, R.sms), kT, 0, R.s>>>(f->top, R.k, f->perm[cur], f->pflag, f->pscan, f->d_n, keep, ord,
+                                                       w, f->top2);
+  } else {
+    keep = std::min(keep, n);
+    k_take_rows<<<grid_n(keep, R.sms), kT, 0, R.s>>>(f->top, R.k, f->perm[cur], keep, ord, w, f->top2);
+  }
   if (!final) {
     GS_CUDA(cudaMemcpyAsync(f->top, f->top2, 4ull * keep * R.k, cudaMemcpyDeviceToDevice, R.s));
     R.top_n = keep;
   }
+  R.kept = keep;
   GS_CUDA(cudaStreamSynchronize(R.s));
   return GS_OK;
 }
@@ -286,7 +349,7 @@ gs_status flush_chunk(FbRun &R) {
   k_iota_n<<<grid_n(n, R.sms), kT, 0, R.s>>>(f->perm[0], f->d_n);
   ColOrder ord;
   for (uint32_t u = 0; u < R.k; ++u) ord.c[u] = R.pos[u];
-  k_take_rows<<<grid_n(n, R.sms), kT, 0, R.s>>>(f->top, R.k, f->perm[0], n, ord, f->top2);
+  k_take_rows<<<grid_n(n, R.sms), kT, 0, R.s>>>(f->top, R.k, f->perm[0], n, ord, R.k, f->top2);
   GS_CUDA(cudaStreamSynchronize(R.s));
   R.cb(f->top2, n, R.k, R.query, R.user);
   R.top_n = 0;
@@ -398,11 +461,15 @@ gs_status fallback_query(gs_batch *b, uint32_t i) {
       std::max<uint64_t>((b->key_chunk ? b->key_chunk : (1ull << 30)) / (4ull * std::max<uint32_t>(src.k, 1)), 4096);
   std::vector<uint32_t> rows;
   uint64_t count = 0, fp = 0;
+  bool more = false;
   if (dq.status == QS_OK) {
     FbRun R{f, fb, fb->W, s, fb->sms, fb->group, src.k};
     memcpy(R.pos, dq.pos, sizeof(R.pos));
     R.rows = want_rows;
     R.cap = src.cap;
+    R.kp = src.kp;
+    memcpy(R.pu, src.pu, sizeof(R.pu));
+    R.proj = src.proj != 0;
     if (stream) {
       R.cb = b->on_chunk;
       R.user = b->chunk_user;
@@ -447,10 +514,9 @@ gs_status fallback_query(gs_batch *b, uint32_t i) {
       if (st == GS_OK && stream) {
         st = flush_chunk(R);
       } else if (st == GS_OK && want_rows && R.top_n) {
-        const uint64_t keep = std::min(R.top_n, src.cap);
-        st = sort_top(R, keep, true);
+        st = sort_top(R, src.cap, true);
         if (st == GS_OK) {
-          rows.resize(keep * src.k);
+          rows.resize(R.kept * R.kp);
           GS_CUDA(cudaMemcpyAsync(rows.data(), f->top2, 4 * rows.size(), cudaMemcpyDeviceToHost, s));
           GS_CUDA(cudaStreamSynchronize(s));
         }
@@ -463,6 +529,7 @@ gs_status fallback_query(gs_batch *b, uint32_t i) {
     }
     GS_CUDA(cudaMemcpyAsync(&count, &fb->W.qs[0].count, 8, cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaMemcpyAsync(&fp, &fb->W.qs[0].fp, 8, cudaMemcpyDeviceToHost, s));
+    more = R.more;
   }
   launch_clear(fb->W, s, fb->sms);
   GS_CUDA(cudaStreamSynchronize(s));
@@ -471,6 +538,7 @@ gs_status fallback_query(gs_batch *b, uint32_t i) {
   b->fp[i] = dq.status == QS_OK ? fp : 0;
   b->status[i] = dq.status == QS_EMPTY ? QS_EMPTY : QS_OK;
   b->fb_rows[i] = std::move(rows);
+  b->fb_more[i] = more ? 1 : 0;
   b->fb_done[i] = 1;
   return GS_OK;
 }

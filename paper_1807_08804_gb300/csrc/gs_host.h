@@ -90,6 +90,8 @@ struct gs_batch {
   PinnedVec<uint32_t> rows;          // store contents
   std::vector<std::vector<uint32_t>> fb_rows;  // rows of queries finished on the fallback path
   std::vector<uint8_t> fb_done;
+  std::vector<uint8_t> fb_more;      // fallback, projected: more distinct tuples than cap
+  bool has_proj = false;             // some query returns projected rows
   // capacity and options (for reuse by later calls with the same options)
   uint32_t n_cap = 0;
   gs_chunk_cb on_chunk = nullptr;  // GS_CHUNKED: where every embedding goes

@@ -829,6 +829,7 @@ __global__ void k_join_plan(Wave W) {
         joined |= 1u << best;
       }
     }
+    for (uint32_t i = 0; i < Q.kp; ++i) Q.opos[i] = Q.pos[Q.pu[i]];
     for (uint32_t e = 0; e < Q.m; ++e) {
       uint32_t n = 0;
       if (ok) {
@@ -1324,16 +1325,20 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
     const uint32_t qi = base + threadIdx.x;
     uint64_t v[4] = {0, 0, 0, 0}, ex[4];
     if (qi < W.nq && W.dq[qi].status == QS_OK) {
-      const uint64_t keep = min(W.qs[qi].out_rows, W.dq[qi].cap);  // rows returned
+      const uint64_t keep = min(W.qs[qi].out_rows, W.dq[qi].cap);  // rows returned (at most)
       v[0] = keep;
-      v[1] = keep * W.dq[qi].k;
+      v[1] = keep * W.dq[qi].kp;
       v[2] = small_output(W.dq[qi], W.qs[qi]) ? 0 : W.qs[qi].out_rows;
       v[3] = (v[2] + kTileRows - 1) / kTileRows;
       if (v[2]) atomicMax((unsigned long long *)&W.ctrl->max_large_rows, (unsigned long long)v[2]);
     }
     if (qi < W.nq) {
       W.qs[qi].sort_rows = v[2];
-      const bool over = v[2] > W.dq[qi].cap;
+      W.qs[qi].nfinal = v[0];  // projected queries replace it once duplicates are dropped
+      W.qs[qi].more = 0;
+      // a projected output is never cut before sorting: the cap-th distinct
+      // tuple can lie past the cap-th row
+      const bool over = v[2] > W.dq[qi].cap && !W.dq[qi].proj;
       W.sel[qi] = SelState{~0ull, 0, 0, W.dq[qi].cap, ~0ull, 0, 0, 0, 0, over ? 1u : 0u};
       if (over) atomicAdd((unsigned long long *)&W.ctrl->over_cap, 1ull);
     }
@@ -1410,14 +1415,25 @@ __device__ __forceinline__ uint64_t pack_key(uint32_t k, uint32_t b, Col col) {
   return key;
 }
 
-// Row r of the output pool (query qi) compared in query-vertex order.
+// Row r of the output pool (query qi) compared on its output columns (the
+// projected vertices, or every vertex) in query-vertex order.
 __device__ __forceinline__ bool out_row_le(const Wave &W, const DQuery &Q, const QState &S, uint32_t a, uint32_t b) {
   const uint32_t *x = W.out + S.out_word_base + (uint64_t)(a - S.out_row_base) * Q.k;
   const uint32_t *y = W.out + S.out_word_base + (uint64_t)(b - S.out_row_base) * Q.k;
-  for (uint32_t u = 0; u < Q.k; ++u) {
-    const uint32_t xa = x[Q.pos[u]], yb = y[Q.pos[u]];
+  for (uint32_t i = 0; i < Q.kp; ++i) {
+    const uint32_t c = Q.opos[i];
+    const uint32_t xa = x[c], yb = y[c];
     if (xa != yb) return xa < yb;
   }
+  return true;
+}
+
+// Do rows a and b of the output pool agree on every output column?
+__device__ __forceinline__ bool out_row_eq(const Wave &W, const DQuery &Q, const QState &S, uint32_t a, uint32_t b) {
+  const uint32_t *x = W.out + S.out_word_base + (uint64_t)(a - S.out_row_base) * Q.k;
+  const uint32_t *y = W.out + S.out_word_base + (uint64_t)(b - S.out_row_base) * Q.k;
+  for (uint32_t i = 0; i < Q.kp; ++i)
+    if (x[Q.opos[i]] != y[Q.opos[i]]) return false;
   return true;
 }
 
@@ -1428,10 +1444,50 @@ __device__ __forceinline__ bool kr_le(const Wave &W, const DQuery &Q, const QSta
   return out_row_le(W, Q, S, ra, rb);
 }
 
+// Exclusive scan of v[0..n) in shared memory by one block of 256 threads,
+// each taking n / 256 consecutive entries (n a multiple of 256 up to 2048);
+// returns the total.
+__device__ __forceinline__ uint32_t block_scan_excl(uint32_t *v, uint32_t n) {
+  __shared__ uint32_t wsum[8];
+  __shared__ uint32_t total;
+  const uint32_t per = n / 256, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *mine = v + threadIdx.x * per;
+  uint32_t sum = 0;
+  for (uint32_t j = 0; j < per; ++j) sum += mine[j];
+  uint32_t x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int w = 0; w < 8; ++w) {
+      const uint32_t t = wsum[w];
+      wsum[w] = acc;
+      acc += t;
+    }
+    total = acc;
+  }
+  __syncthreads();
+  uint32_t run = wsum[warp] + x - sum;
+  for (uint32_t j = 0; j < per; ++j) {
+    const uint32_t t = mine[j];
+    mine[j] = run;
+    run += t;
+  }
+  const uint32_t tot = total;
+  __syncthreads();
+  return tot;
+}
+
 // One block sorts one query's rows: packed 64-bit keys of the rows (see the
 // large-output sort below) and row indices in shared memory, bitonic
 // network, full rows compared on equal keys only; then the first `cap` rows
-// are written in query-vertex column order.
+// are written in query-vertex column order.  A projected query keeps only
+// the first row of each run of equal projected tuples (its rank among the
+// runs from a block scan) and writes the first `cap` of them.
 __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
   __shared__ uint64_t key[kSmallRows];
   __shared__ uint32_t idx[kSmallRows];
@@ -1449,7 +1505,7 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
       idx[i] = i;
       if (i < n) {
         const uint32_t *x = rows + (uint64_t)i * k;
-        key[i] = pack_key(k, b, [&](uint32_t u) { return x[Q.pos[u]]; });
+        key[i] = pack_key(Q.kp, b, [&](uint32_t c) { return x[Q.opos[c]]; });
       }
     }
     __syncthreads();
@@ -1470,10 +1526,38 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
         __syncthreads();
       }
     uint32_t *dst = W.out_final + S.fin_word_base;
-    const uint32_t keep = (uint32_t)min((uint64_t)n, Q.cap);
-    for (uint32_t t = threadIdx.x; t < keep * k; t += blockDim.x) {
-      const uint32_t i = t / k, u = t % k;
-      dst[t] = rows[(uint64_t)idx[i] * k + Q.pos[u]];
+    if (!Q.proj) {
+      const uint32_t keep = (uint32_t)min((uint64_t)n, Q.cap);
+      for (uint32_t t = threadIdx.x; t < keep * k; t += blockDim.x) {
+        const uint32_t i = t / k, u = t % k;
+        dst[t] = rows[(uint64_t)idx[i] * k + Q.pos[u]];
+      }
+      __syncthreads();
+      continue;
+    }
+    // run starts marked in bit 31 of idx (entries are below kSmallRows; a
+    // neighbour's read masks the bit, so marking in place is safe); then the
+    // keys are done with and their space holds the ranks
+    constexpr uint32_t kMark = 0x80000000u;
+    const uint32_t kp = Q.kp, nr = (np2 + 255) / 256 * 256;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t a = idx[i] & ~kMark, p = i ? idx[i - 1] & ~kMark : 0;
+      if (i == 0 || key[a] != key[p] || !out_row_eq(W, Q, S, r0 + a, r0 + p)) idx[i] = a | kMark;
+    }
+    __syncthreads();
+    uint32_t *rnk = reinterpret_cast<uint32_t *>(key);
+    for (uint32_t i = threadIdx.x; i < nr; i += blockDim.x) rnk[i] = i < n ? idx[i] >> 31 : 0;
+    __syncthreads();
+    const uint32_t d = block_scan_excl(rnk, nr);  // distinct tuples
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t r = rnk[i];
+      if (!(idx[i] & kMark) || r >= Q.cap) continue;  // not a run start, or past cap
+      const uint32_t *x = rows + (uint64_t)(idx[i] & ~kMark) * k;
+      for (uint32_t c = 0; c < kp; ++c) dst[(uint64_t)r * kp + c] = x[Q.opos[c]];
+    }
+    if (threadIdx.x == 0) {
+      W.qs[qi].nfinal = min((uint64_t)d, Q.cap);
+      W.qs[qi].more = d > Q.cap;
     }
     __syncthreads();
   }
@@ -1495,7 +1579,7 @@ __global__ void k_sort_keys(Wave W, uint32_t *perm, uint64_t *keys) {
       const QState &S = W.qs[qi];
       const uint64_t local = i - S.lrg_row_base;
       const uint32_t *x = W.out + S.out_word_base + local * Q.k;
-      key = pack_key(Q.k, b, [&](uint32_t u) { return x[Q.pos[u]]; });
+      key = pack_key(Q.kp, b, [&](uint32_t i) { return x[Q.opos[i]]; });
       keys[i] = key;
       perm[i] = (uint32_t)(S.out_row_base + local);
     }
@@ -1782,7 +1866,8 @@ __device__ __forceinline__ MergeTile merge_tile(const Wave &W, uint64_t t, uint6
   MergeTile m;
   m.qi = seg_of_large(W.qs, W.nq, t, true);
   const QState &S = W.qs[m.qi];
-  const uint64_t n = S.sort_rows, cap = W.dq[m.qi].cap;
+  // a projected output keeps every row: duplicates go only after sorting
+  const uint64_t n = S.sort_rows, cap = W.dq[m.qi].proj ? ~0ull : W.dq[m.qi].cap;
   m.base = S.lrg_row_base;
   m.first = (t - S.lrg_tile_base) * kTileRows;
   m.a0 = (m.first / (2 * run)) * 2 * run;
@@ -1905,11 +1990,86 @@ __global__ void k_gather(Wave W, const uint32_t *perm0, const uint32_t *perm1) {
     const uint32_t qi = seg_of_large(W.qs, W.nq, i, false);
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
-    if (i - S.lrg_row_base >= Q.cap) continue;  // past the rows returned
+    if (Q.proj || i - S.lrg_row_base >= Q.cap) continue;  // projected: k_proj_write; past the rows returned
     const uint32_t row = ((merge_passes(S.sort_rows) & 1) ? perm1 : perm0)[i];
     const uint32_t *src = W.out + S.out_word_base + (uint64_t)(row - S.out_row_base) * Q.k;
     uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.lrg_row_base) * Q.k;
     for (uint32_t u = 0; u < Q.k; ++u) dst[u] = src[Q.pos[u]];
+  }
+}
+
+// Projected large outputs: after the merge sort, rows with equal projected
+// tuples sit next to each other, and a row starts a new tuple when it
+// differs from the row before it.  Per tile of kTileRows sorted rows, one
+// kernel counts the starts; a scan of the counts gives each tile's first
+// rank; a second kernel writes every start whose rank is below cap.
+__device__ __forceinline__ bool proj_start(const Wave &W, const DQuery &Q, const QState &S, const uint32_t *perm,
+                                           const uint64_t *key, uint64_t i) {
+  if (i == 0) return true;
+  const uint64_t a = S.lrg_row_base + i;
+  return key[a] != key[a - 1] || !out_row_eq(W, Q, S, perm[a], perm[a - 1]);
+}
+
+__global__ void __launch_bounds__(256) k_proj_count(Wave W, const uint32_t *perm0, const uint32_t *perm1,
+                                                    const uint64_t *key0, const uint64_t *key1) {
+  __shared__ uint32_t wsum[8];
+  const uint64_t ntiles = W.ctrl->len[7];
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint32_t qi = seg_of_large(W.qs, W.nq, t, true);
+    const DQuery &Q = W.dq[qi];
+    const QState &S = W.qs[qi];
+    uint32_t c = 0;
+    if (Q.proj) {  // block-uniform
+      const bool odd = merge_passes(S.sort_rows) & 1;
+      const uint64_t first = (t - S.lrg_tile_base) * kTileRows;
+      const uint64_t n = min((uint64_t)kTileRows, S.sort_rows - first);
+      for (uint64_t i = threadIdx.x; i < n; i += blockDim.x)
+        c += proj_start(W, Q, S, odd ? perm1 : perm0, odd ? key1 : key0, first + i);
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (int w = 0; w < 8; ++w) tot += wsum[w];
+      W.ptcount[t] = tot;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_proj_write(Wave W, const uint32_t *perm0, const uint32_t *perm1,
+                                                    const uint64_t *key0, const uint64_t *key1) {
+  __shared__ uint32_t rk[kTileRows];
+  const uint64_t ntiles = W.ctrl->len[7];
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint32_t qi = seg_of_large(W.qs, W.nq, t, true);
+    const DQuery &Q = W.dq[qi];
+    const QState &S = W.qs[qi];
+    if (!Q.proj) continue;  // block-uniform
+    const bool odd = merge_passes(S.sort_rows) & 1;
+    const uint32_t *perm = odd ? perm1 : perm0;
+    const uint64_t *key = odd ? key1 : key0;
+    const uint64_t first = (t - S.lrg_tile_base) * kTileRows;
+    const uint32_t n = (uint32_t)min((uint64_t)kTileRows, S.sort_rows - first);
+    for (uint32_t i = threadIdx.x; i < kTileRows; i += blockDim.x) rk[i] = i < n && proj_start(W, Q, S, perm, key, first + i);
+    __syncthreads();
+    const uint32_t here = block_scan_excl(rk, kTileRows);
+    const uint64_t q0 = W.ptscan[S.lrg_tile_base], base = W.ptscan[t] - q0;
+    uint32_t *dst = W.out_final + S.fin_word_base;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t r = rk[i];
+      if ((i + 1 < n ? rk[i + 1] : here) == r || base + r >= Q.cap) continue;  // not a start, or past cap
+      const uint32_t *x = W.out + S.out_word_base + (uint64_t)(perm[S.lrg_row_base + first + i] - S.out_row_base) * Q.k;
+      for (uint32_t c = 0; c < Q.kp; ++c) dst[(base + r) * Q.kp + c] = x[Q.opos[c]];
+    }
+    if (threadIdx.x == 0 && t == S.lrg_tile_base) {
+      const uint64_t tiles = (S.sort_rows + kTileRows - 1) / kTileRows;
+      const uint64_t d = W.ptscan[S.lrg_tile_base + tiles] - q0;
+      W.qs[qi].nfinal = min(d, Q.cap);
+      W.qs[qi].more = d > Q.cap;
+    }
+    __syncthreads();
   }
 }
 
@@ -1927,7 +2087,7 @@ __global__ void k_epilogue_copy(Wave W) {
     W.bo.count[b] = S.count;
     W.bo.fp[b] = S.fp;
     W.bo.status[b] = st;
-    W.bo.nrows[b] = st == QS_OK ? min(S.out_rows, Q.cap) : 0;
+    W.bo.nrows[b] = st == QS_OK ? (S.nfinal | (S.more ? kRowsMore : 0)) : 0;
     W.bo.word_off[b] = top + S.fin_word_base;
   }
   if (fits)
@@ -2087,6 +2247,14 @@ void launch_merge_pass(const Wave &W, const uint32_t *pin, const uint64_t *kin, 
 }
 void launch_gather(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, cudaStream_t s, int sms) {
   k_gather<<<persistent_grid(k_gather, sms), kThreads, 0, s>>>(W, perm0, perm1);
+}
+
+void launch_project(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, const uint64_t *key0,
+                    const uint64_t *key1, uint64_t max_tiles, uint64_t *scan_tmp, cudaStream_t s, int sms) {
+  const unsigned grid = (unsigned)std::min<uint64_t>(std::max<uint64_t>(max_tiles, 1), (uint64_t)sms * 8);
+  k_proj_count<<<grid, 256, 0, s>>>(W, perm0, perm1, key0, key1);
+  scan_u32(W.ptcount, W.ptscan, &W.ctrl->len[7], max_tiles, scan_tmp, s, sms);
+  k_proj_write<<<grid, 256, 0, s>>>(W, perm0, perm1, key0, key1);
 }
 void launch_epilogue(const Wave &W, cudaStream_t s, int sms) {
   k_epilogue_copy<<<persistent_grid(k_epilogue_copy, sms), kThreads, 0, s>>>(W);

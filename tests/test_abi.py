@@ -4,10 +4,13 @@ import ctypes
 import os
 import re
 
+import pytest
+
 import paper_1807_08804_gb300 as gs
 from paper_1807_08804_gb300 import buildlib
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gs.h")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gs.h")
 
 
 def declared_symbols():
@@ -32,10 +35,28 @@ def test_binding_covers_the_header():
     gs.lib()  # loads with every signature set
 
 
-def test_struct_layouts_match_the_header():
-    # sizes the C compiler gives these structs on LP64 targets
-    assert ctypes.sizeof(gs.GraphDesc) == 72
-    assert ctypes.sizeof(gs.QueryDesc) == 48
-    assert ctypes.sizeof(gs.MatchOpts) == 48
-    assert ctypes.sizeof(gs.ResultDesc) == 48
-    assert ctypes.sizeof(gs.ServeOpts) == 24
+def test_struct_layouts_match_the_header(tmp_path):
+    """Sizes and field offsets of the binding's structs equal what the C
+    compiler gives the header's structs."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    pairs = [("gs_graph_desc", gs.GraphDesc), ("gs_query", gs.QueryDesc), ("gs_match_opts", gs.MatchOpts),
+             ("gs_result", gs.ResultDesc), ("gs_serve_opts", gs.ServeOpts)]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gs.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    for cname, py in pairs:
+        assert int(got[f"{cname} size"]) == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert int(got[f"{cname} {f[0]}"]) == getattr(py, f[0]).offset, (cname, f[0])
