@@ -262,6 +262,8 @@ def main():
     ap.add_argument("--mode", default=None, choices=["enumerate", "count", "chunked"],
                     help="enumerate rows (default), count only (default for stress-16m), or stream every "
                          "embedding through the chunk callback (chunked enumeration)")
+    ap.add_argument("--project", default=None,
+                    help="comma-separated query vertices whose distinct tuples are returned (projection)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -287,6 +289,7 @@ def main():
         streamed[0] += n_rows
 
     chunk_cb = on_chunk if mode == "chunked" else None
+    project = [int(x) for x in args.project.split(",")] if args.project else None
     chunk_bytes = (8 << 30) if mode == "chunked" else 0  # 8 GB output chunks
     dg = gs.DeviceGraph(g)
     tuned = None
@@ -302,8 +305,10 @@ def main():
     torch.cuda.set_stream(stream)
     sh = stream.cuda_stream
     assert sh != 0
-    b = gs.Batch(dg, qs, cap=cap, mode=gmode, stream=sh, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, raw_chunks=True)
+    b = gs.Batch(dg, qs, cap=cap, mode=gmode, stream=sh, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, raw_chunks=True,
+                 project=project)
     one = gs.Batch(dg, qs, cap=cap, mode=gmode, wave_queries=1, stream=sh, chunk_bytes=chunk_bytes, on_chunk=chunk_cb,
+                   project=project,
                    raw_chunks=True)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -312,6 +317,7 @@ def main():
         b.finish()  # finishes queries that need the chunked path too
     res = b.fetch()
     embeddings = sum(r.count for r in res)
+    proj_rows = sum(r.rows.shape[0] for r in res)  # distinct projected tuples returned
     bad = [i for i, r in enumerate(res) if r.status != 0]
     # queries that finish on the chunked path (and, in chunked mode, the
     # streaming itself) run inside the timed steps
@@ -374,7 +380,7 @@ def main():
 
     # ---- end to end through the public API with host buffers
     h0, d0 = dg.io_bytes()
-    gs.match_batch(dg, qs, cap=cap, mode=gmode, chunk_bytes=chunk_bytes, on_chunk=chunk_cb,
+    gs.match_batch(dg, qs, cap=cap, mode=gmode, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, project=project,
                    raw_chunks=True)  # warm the reusable pools
     h0, d0 = dg.io_bytes()
     barrier(world)
@@ -382,7 +388,8 @@ def main():
     t = time.perf_counter()
     e2e_steps = max(2, args.steps // 2)
     for _ in range(e2e_steps):
-        out = gs.match_batch(dg, qs, cap=cap, mode=gmode, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, raw_chunks=True)
+        out = gs.match_batch(dg, qs, cap=cap, mode=gmode, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, raw_chunks=True,
+                             project=project)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t, world, dev)
     h1, d1 = dg.io_bytes()
@@ -411,10 +418,12 @@ def main():
             "config": {"workload": w.name, "vertices": w.V, "edges": w.E, "queries": n, "mode": mode,
                        "query_vertices": [w.kmin, w.kmax], "p_bind": w.p_bind, "cap": cap,
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
-                       "parallelism": f"replicas x{world}", "tuned": tuned},
+                       "parallelism": f"replicas x{world}", "tuned": tuned,
+                       **({"project": project} if project else {})},
             "embeddings_per_s": embeddings * world * args.steps / (tot_ms / 1e3),
             "embeddings_per_step": embeddings,
             **({"streamed_rows_per_step": streamed_timed / args.steps} if mode == "chunked" else {}),
+            **({"projected_rows_per_step": proj_rows} if project else {}),
             "one_at_a_time": ({"value": one_qps, "unit": "queries/s", "ms_per_step": one_tot / args.one_steps,
                                "speedup_batched": value / one_qps} if one_qps else None),
             "e2e": {"value": n * world * e2e_steps / e2e_s, "unit": "queries/s",
