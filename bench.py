@@ -141,6 +141,45 @@ def stored_traffic(kind, workload):
     return None
 
 
+def refinement_ablation(gs, dg, qs, cap, gmode, sh, stream, flush, steps, want):
+    """The refinement variants the thesis compares (converged in visit order,
+    converged in reversed order, one reversed round, none) plus one reversed
+    round that skips degree-1 query vertices: batched time per step, run and
+    finish (CUDA events, L2 flushed between steps), and the partial-embedding words of the
+    join levels (sum over queries of every level before the last, and the
+    largest level of any query).  Every variant must give the same counts and
+    fingerprints."""
+    import torch
+    variants = [("converged", 0, 64), ("converged-reversed", gs.GS_REFINE_REVERSED, 64),
+                ("one-round-reversed", gs.GS_REFINE_REVERSED, 1), ("none", gs.GS_REFINE_OFF, 1),
+                ("one-round-reversed-skip-degree-1", gs.GS_REFINE_REVERSED | gs.GS_REFINE_LOW(1), 1)]
+    out = []
+    for name, refine, rounds in variants:
+        b = gs.Batch(dg, qs, cap=cap, mode=gmode, stream=sh, max_refine_rounds=rounds, refine=refine)
+        for _ in range(3):
+            b.run()
+            b.finish()
+        res = b.fetch()
+        same = all((r.count, r.fingerprint) == (x.count, x.fingerprint) for r, x in zip(res, want))
+        tot, peak = b.join_sizes()
+        ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1)
+            stream.wait_stream(torch.cuda.current_stream())
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run()
+            b.finish()  # queries sent to the chunked path finish inside the timed region
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        out.append({"variant": name, "ms_per_step": ms / steps, "queries_per_s": len(qs) * steps / (ms / 1e3),
+                    "partial_words_total": int(tot.sum()), "partial_words_peak": int(peak.max()) if len(peak) else 0,
+                    "results_identical": same, "fallback_queries": b.counters().get("fallback_queries", 0)})
+        b.close()
+    return out
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -262,6 +301,9 @@ def main():
     ap.add_argument("--mode", default=None, choices=["enumerate", "count", "chunked"],
                     help="enumerate rows (default), count only (default for stress-16m), or stream every "
                          "embedding through the chunk callback (chunked enumeration)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also time the refinement variants (converged, reversed order, one round, none, "
+                         "low-connectivity skip) and report their partial-embedding words")
     ap.add_argument("--project", default=None,
                     help="comma-separated query vertices whose distinct tuples are returned (projection)")
     args = ap.parse_args()
@@ -342,6 +384,7 @@ def main():
     step_ms = []
     for _ in range(args.steps):
         flush.zero_()
+        stream.wait_stream(torch.cuda.current_stream())  # the flush ends before the timed work starts
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -366,6 +409,7 @@ def main():
     one_ms = []
     for _ in range(args.one_steps if args.one_steps else 0):
         flush.zero_()
+        stream.wait_stream(torch.cuda.current_stream())
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -434,6 +478,8 @@ def main():
             "clocks": clk,
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in stats.items() if v["launches"]},
             "fallback_queries": b.counters().get("fallback_queries", 0), "failed_queries": len(bad)}
+    if args.ablation:
+        line["ablation"] = refinement_ablation(gs, dg, qs, cap, gmode, sh, stream, flush, args.steps, res)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, g, qs)
     if rank == 0:

@@ -134,8 +134,20 @@ typedef struct {
   uint32_t project;           /* bit u set: return f(u); 0 (or every vertex) = whole
                                  embeddings.  A bit >= k -> GS_ERR_INVALID; with
                                  GS_CHUNKED -> GS_ERR_UNSUPPORTED */
-  uint32_t reserved;          /* 0 */
+  uint32_t refine;            /* refinement variant (Section 3.3.3 and the refinement
+                                 experiments of Section 3.6): 0 = every query vertex
+                                 at once; GS_REFINE_OFF, GS_REFINE_REVERSED, and
+                                 GS_REFINE_LOW(d) (may be or-ed).  Results never depend
+                                 on it: refinement only prunes candidates */
 } gs_match_opts;
+
+/* gs_match_opts.refine */
+#define GS_REFINE_OFF 1u       /* no refinement after exploration */
+#define GS_REFINE_REVERSED 2u  /* one query vertex at a time, in the reverse of the order in
+                                  which exploration gave the vertices candidate sets */
+#define GS_REFINE_LOW(d) (((uint32_t)(d) & 0xFFu) << 8)  /* skip "low connectivity" query
+                                  vertices (at most d incident edges): not refined, and
+                                  their edges not used to refine others */
 
 /* Synchronous copy of `bytes` bytes from device memory to host memory, for
  * chunk callbacks.  Returns GS_ERR_CUDA if the copy fails. */
@@ -188,6 +200,14 @@ gs_status gs_batch_run(gs_batch *b);
 gs_status gs_batch_finish(gs_batch *b);
 /* Copy results of the last finished run to the host (outs[n]). */
 gs_status gs_batch_fetch(gs_batch *b, gs_result *outs);
+
+/* Partial-embedding words of each query in the last finished run, for
+ * measuring refinement (Section 3.6: "intermediate results"): words_total[i]
+ * = sum over the join levels before the last of rows x width, words_peak[i]
+ * = the largest of those levels (uint32 words; the device pipeline's levels,
+ * not those of a query finished on the chunked path).  Host arrays of the
+ * batch's n entries.  Errors: GS_ERR_INVALID before gs_batch_finish. */
+gs_status gs_batch_join_sizes(gs_batch *b, uint64_t *words_total, uint64_t *words_peak);
 void gs_batch_destroy(gs_batch *b);
 /* Waves of `wave_queries` queries each: every phase runs per wave (1 = one
  * query at a time through the same device pipeline). */

@@ -26,6 +26,12 @@ ANY = 0xFFFFFFFF
 GS_DEVICE_PTRS = 1
 GS_ENUMERATE, GS_COUNT_ONLY, GS_CHUNKED = 0, 1, 2
 GS_STAGE_FILTER, GS_STAGE_FIXPOINT = 0, 1
+GS_REFINE_OFF, GS_REFINE_REVERSED = 1, 2
+
+
+def GS_REFINE_LOW(d: int) -> int:
+    """Refinement flag: skip query vertices with at most d incident edges."""
+    return (int(d) & 0xFF) << 8
 NUM_KERNEL_KINDS = 16
 
 
@@ -55,7 +61,7 @@ ChunkCallback = ctypes.CFUNCTYPE(None, ctypes.c_void_p, U64, U32, U32, ctypes.c_
 
 class MatchOpts(ctypes.Structure):
     _fields_ = [("cap", U64), ("mode", U32), ("max_refine_rounds", U32), ("chunk_bytes", U64), ("cuda_stream", P),
-                ("on_chunk", ChunkCallback), ("user", P), ("project", U32), ("reserved", U32)]
+                ("on_chunk", ChunkCallback), ("user", P), ("project", U32), ("refine", U32)]
 
 
 class ResultDesc(ctypes.Structure):
@@ -93,6 +99,7 @@ SIGNATURES = {
     "gs_batch_run": (ctypes.c_int, [P]),
     "gs_batch_finish": (ctypes.c_int, [P]),
     "gs_batch_fetch": (ctypes.c_int, [P, ctypes.POINTER(ResultDesc)]),
+    "gs_batch_join_sizes": (ctypes.c_int, [P, P, P]),
     "gs_batch_destroy": (None, [P]),
     "gs_stats_enable": (ctypes.c_int, [P, ctypes.c_int]),
     "gs_stats_get": (ctypes.c_int, [P, ctypes.POINTER(KernelStats)]),
@@ -201,11 +208,12 @@ def project_mask(project) -> int:
 
 
 def _opts(cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0, stream=None, on_chunk=None,
-          project=None) -> MatchOpts:
+          project=None, refine=0) -> MatchOpts:
     o = MatchOpts(cap, mode, max_refine_rounds, chunk_bytes, stream)
     if on_chunk is not None:
         o.on_chunk = on_chunk
     o.project = project_mask(project)
+    o.refine = refine
     return o
 
 
@@ -320,23 +328,23 @@ class DeviceGraph:
 
 
 def match(dg: DeviceGraph, q, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0,
-          on_chunk=None, project=None) -> MatchResult:
+          on_chunk=None, project=None, refine=0) -> MatchResult:
     """on_chunk(rows, query): with mode=GS_CHUNKED, called with every chunk
     of embeddings (uint32 [n, k], query-vertex order) as it is produced.
     project: query vertices whose distinct tuples are returned as rows."""
     pack = _QueryPack([q])
     cb = _chunk_callback(on_chunk)
-    o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb, project=project)
+    o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb, project=project, refine=refine)
     r = ResultDesc()
     _check(lib().gs_match(dg._h, pack.arr, ctypes.byref(o), ctypes.byref(r)))
     return _take(r)
 
 
 def match_batch(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0,
-                chunk_bytes=0, on_chunk=None, raw_chunks=False, project=None) -> list[MatchResult]:
+                chunk_bytes=0, on_chunk=None, raw_chunks=False, project=None, refine=0) -> list[MatchResult]:
     pack = _QueryPack(queries)
     cb = _chunk_callback(on_chunk, raw_chunks)
-    o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb, project=project)
+    o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb, project=project, refine=refine)
     res = (ResultDesc * max(len(queries), 1))()
     _check(lib().gs_match_batch(dg._h, pack.arr, len(queries), ctypes.byref(o), res))
     return _take_all(res, len(queries))
@@ -346,12 +354,13 @@ class Batch:
     """A prepared batch (device-resident queries, captured pipeline graph)."""
 
     def __init__(self, dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0,
-                 wave_queries=0, stream=None, on_chunk=None, raw_chunks=False, project=None):
+                 wave_queries=0, stream=None, on_chunk=None, raw_chunks=False, project=None, refine=0):
         self.dg = dg
         self.n = len(queries)
         self._pack = _QueryPack(queries)
         self._cb = _chunk_callback(on_chunk, raw_chunks)  # kept alive: every finish() may call it
-        o = _opts(cap, mode, max_refine_rounds, chunk_bytes, stream, on_chunk=self._cb, project=project)
+        o = _opts(cap, mode, max_refine_rounds, chunk_bytes, stream, on_chunk=self._cb, project=project,
+                  refine=refine)
         self._h = P()
         if wave_queries:
             _check(lib().gs_batch_create_waves(dg._h, self._pack.arr, self.n, ctypes.byref(o), wave_queries,
@@ -372,6 +381,14 @@ class Batch:
         res = (ResultDesc * max(self.n, 1))()
         _check(lib().gs_batch_fetch(self._h, res))
         return _take_all(res, self.n)
+
+    def join_sizes(self):
+        """(words_total, words_peak) per query: partial-embedding words of the
+        last finished run over the join levels before the last."""
+        tot = np.zeros(max(self.n, 1), np.uint64)
+        peak = np.zeros(max(self.n, 1), np.uint64)
+        _check(lib().gs_batch_join_sizes(self._h, tot.ctypes.data_as(P), peak.ctypes.data_as(P)))
+        return tot[: self.n], peak[: self.n]
 
     def counters(self) -> dict:
         k, h, d, f = U64(), U64(), U64(), U64()

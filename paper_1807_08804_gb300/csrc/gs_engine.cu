@@ -94,6 +94,12 @@ gs_status pack_query(const DevGraph &G, const gs_query *q, const gs_match_opts *
   if (d->proj && mode == GS_CHUNKED) return fail(GS_ERR_UNSUPPORTED, "projection with GS_CHUNKED");
   for (uint32_t u = 0; u < k; ++u)
     if (!d->proj || ((d->proj >> u) & 1u)) d->pu[d->kp++] = (uint8_t)u;
+  // refinement variant
+  const uint32_t rf = o ? o->refine : 0;
+  if (rf & ~(GS_REFINE_OFF | GS_REFINE_REVERSED | GS_REFINE_LOW(0xFF)))
+    return fail(GS_ERR_INVALID, "unknown refinement flags");
+  d->refine_flags = (uint8_t)(((rf & GS_REFINE_OFF) ? kRefineOff : 0u) | ((rf & GS_REFINE_REVERSED) ? kRefineRev : 0u));
+  d->refine_low = (uint8_t)((rf >> 8) & 0xFFu);
   d->force_root = 0xFF;
   d->force_from_src = 0xFF;
   d->status = QS_OK;
@@ -219,6 +225,8 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   A(W.bo.fp, b->n_cap);
   A(W.bo.nrows, b->n_cap);
   A(W.bo.word_off, b->n_cap);
+  A(W.bo.inter, b->n_cap);
+  A(W.bo.peak, b->n_cap);
   A(W.bo.status, b->n_cap);
   A(W.bo.store, s.store_words);
   W.bo.store_cap = s.store_words;
@@ -359,6 +367,18 @@ static bool rows_wanted(const gs_batch *b) {
   return false;
 }
 
+// Refinement rounds of a wave: one launch per round, or, when a query asks
+// for the reversed order, one launch per query vertex position per round.
+void launch_refine_rounds(gs_batch *b, const Wave &W, int K, cudaStream_t s) {
+  for (uint32_t r = 0; r < b->refine_rounds; ++r) {
+    if (!b->has_rev) {
+      launch_refine(W, r, kAllSub, b->group, s, b->sms);
+      continue;
+    }
+    for (int j = 0; j < std::max(K, 1); ++j) launch_refine(W, r, (uint32_t)j, b->group, s, b->sms);
+  }
+}
+
 void enqueue_front(Pipe &P, int K) {
   gs_batch *b = P.b;
   Wave &W = b->W;
@@ -390,7 +410,7 @@ void enqueue_front(Pipe &P, int K) {
   launch_compact_write(W, 1, 0, W.ascan, W.alist, W.alist_q, W.alist_cap, HW_ALIST, P.cur, sms);
   P.end();
   P.begin(KK_REFINE);
-  for (uint32_t r = 0; r < b->refine_rounds; ++r) launch_refine(W, r, grp, P.cur, sms);
+  launch_refine_rounds(b, W, K, P.cur);
   P.end();
 }
 
@@ -571,7 +591,7 @@ gs_status refine_to_fixpoint(gs_batch *b) {
     uint32_t last = b->refine_rounds - 1;
     if (!changed[last]) return GS_OK;
     GS_CUDA(cudaMemsetAsync(b->W.ctrl->changed, 0, sizeof(changed), b->stream));
-    for (uint32_t r = 0; r < b->refine_rounds; ++r) launch_refine(b->W, r, b->group, b->stream, b->sms);
+    launch_refine_rounds(b, b->W, b->max_k, b->stream);
   }
 }
 
@@ -671,7 +691,8 @@ static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match
   b->n = n;
   b->hq.assign(n, DQuery{});
   b->hstatus.assign(n, GS_OK);
-  b->has_proj = false;
+  b->has_proj = b->has_rev = false;
+  b->max_k = 1;
   for (uint32_t i = 0; i < n; ++i) {
     gs_status st = pack_query(b->g->d, &qs[i], opts, &b->hq[i]);
     b->hstatus[i] = st;
@@ -680,6 +701,8 @@ static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match
       b->hq[i].status = QS_INVALID;
     }
     b->has_proj = b->has_proj || b->hq[i].proj != 0;
+    b->has_rev = b->has_rev || (b->hq[i].refine_flags & kRefineRev);
+    b->max_k = std::max<uint32_t>(b->max_k, b->hq[i].k);
   }
   b->ran = b->finished = false;
 }
@@ -1033,6 +1056,18 @@ gs_status batch_fetch(gs_batch *b, gs_result *outs) {
 extern "C" gs_status gs_memcpy_d2h(void *dst, const void *src, uint64_t bytes) {
   if (bytes && (!dst || !src)) return fail(GS_ERR_INVALID, "gs_memcpy_d2h: null pointer");
   GS_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+  return GS_OK;
+}
+
+extern "C" gs_status gs_batch_join_sizes(gs_batch *b, uint64_t *words_total, uint64_t *words_peak) {
+  if (!b || !words_total || !words_peak) return fail(GS_ERR_INVALID, "gs_batch_join_sizes: null argument");
+  if (!b->finished) return fail(GS_ERR_INVALID, "gs_batch_join_sizes: call gs_batch_finish first");
+  GS_CUDA(cudaSetDevice(b->g->device));
+  if (b->n) {
+    GS_CUDA(cudaMemcpyAsync(words_total, b->W.bo.inter, 8ull * b->n, cudaMemcpyDeviceToHost, b->stream));
+    GS_CUDA(cudaMemcpyAsync(words_peak, b->W.bo.peak, 8ull * b->n, cudaMemcpyDeviceToHost, b->stream));
+    GS_CUDA(cudaStreamSynchronize(b->stream));
+  }
   return GS_OK;
 }
 

@@ -56,6 +56,8 @@ struct DQuery {
   uint32_t mode;
   uint64_t cap;
   uint32_t proj;                    // projected vertices (bit mask); 0 = whole embeddings
+  uint8_t refine_flags;             // kRefineOff, kRefineRev
+  uint8_t refine_low;               // refinement skips vertices with at most this many incident edges (0: none)
   uint8_t kp;                       // output columns: the projected vertices pu[0..kp), ascending
   uint8_t pu[kMaxK];                //   (every vertex when proj == 0)
   uint8_t force_root;               // 0xFF, or the first visited vertex (inspection runs)
@@ -69,6 +71,7 @@ struct DQuery {
   uint8_t join[kMaxK];              // join order
   uint8_t pos[kMaxK];               // position of u in the join order
   uint8_t opos[kMaxK];              // join-order column of output column i (pos[pu[i]])
+  uint8_t rorder[kMaxK];            // reversed refinement: vertex refined at sub-round j
   uint8_t from_src[kMaxM];          // edge-table orientation (1: keyed by esrc)
   uint32_t xinc[2 * kMaxM];         // incident edges packed by the plan (xinc_pack), same order as inc_edge
   uint32_t status;
@@ -89,6 +92,8 @@ __host__ __device__ __forceinline__ uint32_t xinc_role(uint32_t x) { return x >>
 // adjacency planes of distinct neighbours (2 + direction) as relation 0, and
 // its signature and neighbour-type planes are 2R + direction.
 constexpr uint32_t kRelAny8 = 0xFFu;
+// Refinement variants (DQuery::refine_flags).
+constexpr uint32_t kRefineOff = 1u, kRefineRev = 2u;
 __host__ __device__ __forceinline__ int adj_plane(int dir, uint32_t rel) { return rel == kRelAny8 ? dir + 2 : dir; }
 __host__ __device__ __forceinline__ uint32_t adj_rel(uint32_t rel) { return rel == kRelAny8 ? 0u : rel; }
 __host__ __device__ __forceinline__ uint32_t sig_plane(int dir, uint32_t rel, uint32_t R) {
@@ -106,6 +111,7 @@ struct QState {
   uint64_t lrg_tile_base;                            // their first tile
   uint64_t sort_rows;                                // rows entering the merge sort (after selection)
   uint64_t nfinal;                                   // rows returned (projected: distinct tuples, at most cap)
+  uint64_t inter_words, peak_words;                  // partial-embedding words over the levels before the last
   uint32_t more;                                     // projected: more distinct tuples than cap
 };
 
@@ -140,6 +146,7 @@ struct WaveDesc {
 // Batch-level results written by the epilogue of each wave.
 struct BatchOut {
   uint64_t *count, *fp, *nrows, *word_off;  // [n]
+  uint64_t *inter, *peak;                    // [n] partial-embedding words: total and largest level
   uint32_t *status;                          // [n]
   uint32_t *store;                           // rows of every query, query-vertex order
   uint64_t store_cap;                        // words
@@ -229,7 +236,10 @@ void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint32_t *owner,
                           uint64_t cap, int hw_slot, cudaStream_t s, int sms);
 void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms);
-void launch_refine(const Wave &W, uint32_t round, int group, cudaStream_t s, int sms);
+// sub: kAllSub refines every vertex of every query; j < kMaxK refines, in
+// queries with kRefineRev, the vertex rorder[j] (other queries at j = 0).
+constexpr uint32_t kAllSub = 0xFFFFFFFFu;
+void launch_refine(const Wave &W, uint32_t round, uint32_t sub, int group, cudaStream_t s, int sms);
 void launch_list_table(const Wave &W, cudaStream_t s, int sms);
 void launch_join_plan(const Wave &W, cudaStream_t s, int sms);
 void launch_ec_limit(const Wave &W, cudaStream_t s, int sms);

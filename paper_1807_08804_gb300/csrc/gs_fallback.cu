@@ -441,6 +441,8 @@ gs_status fallback_query(gs_batch *b, uint32_t i) {
   fb->hq[0].status = QS_OK;
   fb->hstatus.assign(1, GS_OK);
   fb->n = 1;
+  fb->has_rev = (src.refine_flags & kRefineRev) != 0;
+  fb->max_k = src.k;
   fb->waves.assign(1, WaveDesc{0, 1, 0, src.k, 0, src.m});
   fb->wave_k.assign(1, (int)src.k);
   cudaStream_t s = fb->stream;

@@ -92,6 +92,8 @@ struct gs_batch {
   std::vector<uint8_t> fb_done;
   std::vector<uint8_t> fb_more;      // fallback, projected: more distinct tuples than cap
   bool has_proj = false;             // some query returns projected rows
+  bool has_rev = false;              // some query refines in reversed order
+  uint32_t max_k = 1;                // largest query
   // capacity and options (for reuse by later calls with the same options)
   uint32_t n_cap = 0;
   gs_chunk_cb on_chunk = nullptr;  // GS_CHUNKED: where every embedding goes

@@ -288,6 +288,19 @@ __global__ void k_plan(Wave W, const uint32_t *type_count) {
     }
     Q.nvisit = nv;
     atomicMax(&W.ctrl->max_nvisit, nv);
+    // reversed refinement order: vertices by the step that gave them a
+    // candidate set, last first (ties: higher index first)
+    for (uint32_t j = 0; j < k; ++j) {
+      int pick = -1;
+      for (uint32_t u = 0; u < k; ++u) {
+        bool taken = false;
+        for (uint32_t i = 0; i < j; ++i) taken = taken || Q.rorder[i] == u;
+        if (taken) continue;
+        if (pick < 0 || Q.init_step[u] > Q.init_step[pick] || (Q.init_step[u] == Q.init_step[pick] && u > (uint32_t)pick))
+          pick = (int)u;
+      }
+      Q.rorder[j] = (uint8_t)pick;
+    }
     // every incident edge of every query vertex, packed for exploration and
     // refinement: direction, relation, other endpoint and, for a vertex that
     // is explored (leaves of the spanning tree are not), the endpoint's role
@@ -736,8 +749,11 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
 // vertex u keeps its place only if, for every query edge at u, some data
 // neighbour of v over that relation and direction is a live candidate of the
 // other endpoint.  Rounds repeat until one clears nothing (the fixpoint).
+// Variants per query: no refinement; one vertex per launch in reversed order
+// (launch `sub` refines rorder[sub]); low-connectivity vertices (at most
+// refine_low incident edges) neither refined nor used to refine.
 template <int G>
-__global__ void __launch_bounds__(kThreads, 6) k_refine(Wave W, uint32_t round) {
+__global__ void __launch_bounds__(kThreads, 6) k_refine(Wave W, uint32_t round, uint32_t sub) {
   if (round > 0 && W.ctrl->changed[round - 1] == 0) return;
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const DevGraph &Gr = W.G;
@@ -752,14 +768,20 @@ __global__ void __launch_bounds__(kThreads, 6) k_refine(Wave W, uint32_t round) 
     DQuery &Q = W.dq[W.qv_q[gqv]];
     if (Q.status != QS_OK) continue;
     const uint32_t u = gqv - Q.qv_base;
+    if (Q.refine_flags | Q.refine_low | sub) {  // a variant, or a sub-round of the reversed order
+      if (Q.refine_flags & kRefineOff) continue;
+      const bool mine = (Q.refine_flags & kRefineRev) ? (sub < Q.k && Q.rorder[sub] == u) : (sub == kAllSub || sub == 0);
+      if (!mine || (uint32_t)(Q.inc_begin[u + 1] - Q.inc_begin[u]) <= Q.refine_low) continue;
+    }
     const uint32_t v = W.alist[it];
     uint32_t *us = slot_of(W, gqv);
     if (!bit_test(us, v)) continue;
     uint64_t bytes = 0;
     for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1]; ++i) {
       const uint32_t xi = Q.xinc[i];
-      const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
       const uint32_t w = xinc_w(xi);
+      if (Q.refine_low && (uint32_t)(Q.inc_begin[w + 1] - Q.inc_begin[w]) <= Q.refine_low) continue;
+      const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
       uint64_t base, lo, hi;
       uint32_t xs;
       const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
@@ -990,6 +1012,8 @@ __global__ void k_join0_rows(Wave W) {
     QState &S = W.qs[qi];
     S.nxt_rows = Q.status == QS_OK ? W.flist_len[Q.qv_base + Q.join[0]] : 0;
     if (Q.status == QS_OK && Q.k == 1) S.count = S.nxt_rows;
+    S.inter_words = 0;
+    S.peak_words = 0;
   }
 }
 
@@ -1082,6 +1106,10 @@ __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
           S.cur_row_base = pos[0];
           S.cur_word_base = pos[1];
           S.cur_rows = v[0];
+          if (mid) {
+            S.inter_words += v[1];
+            S.peak_words = max(S.peak_words, v[1]);
+          }
           if (to_out) {
             S.out_row_base = pos[2];
             S.out_word_base = pos[3];
@@ -2089,6 +2117,8 @@ __global__ void k_epilogue_copy(Wave W) {
     W.bo.status[b] = st;
     W.bo.nrows[b] = st == QS_OK ? (S.nfinal | (S.more ? kRowsMore : 0)) : 0;
     W.bo.word_off[b] = top + S.fin_word_base;
+    W.bo.inter[b] = S.inter_words;
+    W.bo.peak[b] = S.peak_words;
   }
   if (fits)
     for (uint64_t i = gtid(); i < words; i += gthreads()) W.bo.store[top + i] = W.out_final[i];
@@ -2170,12 +2200,12 @@ void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int
     default: k_explore<32><<<persistent_grid(k_explore<32>, sms), kThreads, 0, s>>>(W, step); break;
   }
 }
-void launch_refine(const Wave &W, uint32_t round, int group, cudaStream_t s, int sms) {
+void launch_refine(const Wave &W, uint32_t round, uint32_t sub, int group, cudaStream_t s, int sms) {
   switch (group) {
-    case 4: k_refine<4><<<persistent_grid(k_refine<4>, sms), kThreads, 0, s>>>(W, round); break;
-    case 8: k_refine<8><<<persistent_grid(k_refine<8>, sms), kThreads, 0, s>>>(W, round); break;
-    case 16: k_refine<16><<<persistent_grid(k_refine<16>, sms), kThreads, 0, s>>>(W, round); break;
-    default: k_refine<32><<<persistent_grid(k_refine<32>, sms), kThreads, 0, s>>>(W, round); break;
+    case 4: k_refine<4><<<persistent_grid(k_refine<4>, sms), kThreads, 0, s>>>(W, round, sub); break;
+    case 8: k_refine<8><<<persistent_grid(k_refine<8>, sms), kThreads, 0, s>>>(W, round, sub); break;
+    case 16: k_refine<16><<<persistent_grid(k_refine<16>, sms), kThreads, 0, s>>>(W, round, sub); break;
+    default: k_refine<32><<<persistent_grid(k_refine<32>, sms), kThreads, 0, s>>>(W, round, sub); break;
   }
 }
 void launch_list_table(const Wave &W, cudaStream_t s, int sms) {

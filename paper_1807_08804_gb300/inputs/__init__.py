@@ -239,6 +239,8 @@ WORKLOADS = {
     # 16M vertices / 200M edges; 200 unbound shape queries
     "stress-16m": Workload("stress-16m", 16_000_000, 200_000_000, 200, 4, 6, 0.0, 1 << 20, 0x6753005,
                            shapes=True),
+    # the single-1m graph with 200 queries of 12-16 vertices (refinement measurements)
+    "ablation-1m": Workload("ablation-1m", 1_000_000, 8_000_000, 200, 12, 16, 0.2, 1 << 20, 0x6753002),
     # the single-10k and single-1m workloads with 30% of query edges variable
     "single-10k-var": Workload("single-10k-var", 10_000, 60_000, 100, 3, 6, 0.2, 1 << 20, 0x6753001, p_var=0.3),
     "single-1m-var": Workload("single-1m-var", 1_000_000, 8_000_000, 1000, 4, 10, 0.2, 1 << 22, 0x6753002,
