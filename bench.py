@@ -322,7 +322,7 @@ def main():
     g = w.graph()
     qs = w.queries(g)
     n = len(qs)
-    mode = args.mode or ("count" if w.shapes else "enumerate")
+    mode = args.mode or ("count" if w.shapes or w.anchored else "enumerate")
     gmode = {"count": gs.GS_COUNT_ONLY, "chunked": gs.GS_CHUNKED}.get(mode, gs.GS_ENUMERATE)
     cap = 0 if mode != "enumerate" else w.cap
     streamed = [0]  # rows delivered to the chunk callback (chunked mode)

@@ -186,6 +186,19 @@ def with_variable_edges(queries: list[Query], p_var: float, seed: int = 1) -> li
     return out
 
 
+def anchor_untyped(queries: list[Query]) -> list[Query]:
+    """The same query shapes with one concept node: vertex 0 (where the walk
+    started) bound to its walked vertex, every other vertex an untyped
+    variable."""
+    out = []
+    for q in queries:
+        vt = np.full(q.k, ANY, np.uint32)
+        vb = np.full(q.k, UNBOUND, np.uint32)
+        vb[0] = q.walked[0]
+        out.append(Query(vt, vb, q.esrc, q.edst, q.erel, q.walked))
+    return out
+
+
 def make_arrivals(n: int, qps: float, seed: int = 1) -> np.ndarray:
     """Poisson arrival times in seconds (exponential inter-arrival gaps)."""
     lib = _load()
@@ -210,6 +223,7 @@ class Workload:
     shapes: bool = False
     qps: tuple = field(default_factory=tuple)
     p_var: float = 0.0  # share of query edges made variable (relation ANY)
+    anchored: bool = False  # one bound vertex (the walk start), every other vertex untyped
 
     def graph(self) -> Graph:
         return make_graph(self.V, self.E, seed=self.seed)
@@ -221,6 +235,8 @@ class Workload:
         else:
             qs = make_walk_queries(g, n, self.kmin, self.kmax, p_close=0.3, p_bind=self.p_bind,
                                    cyclic_half=self.cyclic_half, seed=self.seed)
+        if self.anchored:
+            qs = anchor_untyped(qs)
         return with_variable_edges(qs, self.p_var, self.seed + 0x76) if self.p_var > 0 else qs
 
 
@@ -239,8 +255,10 @@ WORKLOADS = {
     # 16M vertices / 200M edges; 200 unbound shape queries
     "stress-16m": Workload("stress-16m", 16_000_000, 200_000_000, 200, 4, 6, 0.0, 1 << 20, 0x6753005,
                            shapes=True),
-    # the single-1m graph with 200 queries of 12-16 vertices (refinement measurements)
-    "ablation-1m": Workload("ablation-1m", 1_000_000, 8_000_000, 200, 12, 16, 0.2, 1 << 20, 0x6753002),
+    # the single-1m graph with 200 queries of 10-12 vertices, half of them cyclic, each with one
+    # concept node and untyped variables elsewhere (refinement measurements, count only)
+    "ablation-1m": Workload("ablation-1m", 1_000_000, 8_000_000, 200, 10, 12, 0.0, 1 << 20, 0x6753002,
+                            cyclic_half=True, anchored=True),
     # the single-10k and single-1m workloads with 30% of query edges variable
     "single-10k-var": Workload("single-10k-var", 10_000, 60_000, 100, 3, 6, 0.2, 1 << 20, 0x6753001, p_var=0.3),
     "single-1m-var": Workload("single-1m-var", 1_000_000, 8_000_000, 1000, 4, 10, 0.2, 1 << 22, 0x6753002,

@@ -65,3 +65,14 @@ def test_variable_edge_queries():
         var += int((~fixed).sum())
         tot += q.m
     assert 0.22 < var / tot < 0.38
+
+
+def test_anchored_untyped_queries():
+    """ablation-1m's recipe on a small graph: one concept node (the walk
+    start, bound), untyped variables elsewhere; the walked map matches."""
+    g = I.make_graph(3000, 18000, seed=9)
+    og = O.OracleGraph.from_graph(g)
+    qs = I.anchor_untyped(I.make_walk_queries(g, 30, 4, 8, p_bind=0.0, cyclic_half=True, seed=3))
+    for q in qs:
+        assert q.vbind[0] == q.walked[0] and (q.vbind[1:] == I.UNBOUND).all() and (q.vtype == I.ANY).all()
+        assert O.verify(og, q, q.walked[None, :]) == -1
