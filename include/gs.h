@@ -177,6 +177,10 @@ gs_status gs_match_batch(gs_graph *g, const gs_query *qs, uint32_t n, const gs_m
 void gs_result_free(gs_result *r);
 /* gs_result_free on each of r[0..n). */
 void gs_results_free(gs_result *r, uint32_t n);
+/* Copy the rows of r[0..n) into dst back to back: r[0]'s num_rows*k words,
+ * then r[1]'s, and so on (dst holds the sum; host memory).  The results keep
+ * their rows.  Errors: GS_ERR_INVALID for a null pointer. */
+gs_status gs_results_copy_rows(const gs_result *r, uint32_t n, uint32_t *dst);
 const char *gs_last_error(void);
 
 /* Bytes copied host->device and device->host by all gs_match and

@@ -10,7 +10,6 @@ from __future__ import annotations
 
 import ctypes
 import os
-from dataclasses import dataclass
 
 import numpy as np
 
@@ -100,6 +99,7 @@ SIGNATURES = {
     "gs_batch_finish": (ctypes.c_int, [P]),
     "gs_batch_fetch": (ctypes.c_int, [P, ctypes.POINTER(ResultDesc)]),
     "gs_batch_join_sizes": (ctypes.c_int, [P, P, P]),
+    "gs_results_copy_rows": (ctypes.c_int, [P, U32, P]),
     "gs_batch_destroy": (None, [P]),
     "gs_stats_enable": (ctypes.c_int, [P, ctypes.c_int]),
     "gs_stats_get": (ctypes.c_int, [P, ctypes.POINTER(KernelStats)]),
@@ -173,11 +173,17 @@ class _QueryPack:
 
     def __init__(self, queries):
         n = len(queries)
-        ks = np.fromiter((len(q.vtype) for q in queries), np.int64, n)
-        ms = np.fromiter((len(q.esrc) for q in queries), np.int64, n)
-        cat = lambda f: np.ascontiguousarray(np.concatenate(
-            [np.asarray(getattr(q, f), np.uint32).ravel() for q in queries] + [np.zeros(1, np.uint32)]))
-        self.flat = [cat("vtype"), cat("vbind"), cat("esrc"), cat("edst"), cat("erel")]
+        cols = ([], [], [], [], [])  # one pass over the queries, one concatenation per field
+        for q in queries:
+            cols[0].append(q.vtype)
+            cols[1].append(q.vbind)
+            cols[2].append(q.esrc)
+            cols[3].append(q.edst)
+            cols[4].append(q.erel)
+        ks = np.fromiter(map(len, cols[0]), np.int64, n)
+        ms = np.fromiter(map(len, cols[2]), np.int64, n)
+        z = np.zeros(1, np.uint32)
+        self.flat = [np.ascontiguousarray(np.concatenate(c + [z]).astype(np.uint32, copy=False)) for c in cols]
         voff = np.zeros(n, np.uint64)
         eoff = np.zeros(n, np.uint64)
         if n:
@@ -238,13 +244,33 @@ def _chunk_callback(fn, raw=False):
     return ChunkCallback(cb)
 
 
-@dataclass
 class MatchResult:
-    count: int
-    fingerprint: int
-    rows: np.ndarray      # uint32 [num_rows, k], query-vertex order, ascending
-    truncated: bool
-    status: int
+    """One query's result: count, fingerprint, rows (uint32 [num_rows, k],
+    query-vertex order, ascending), truncated, status.  Results of a batch
+    share one host array; each `rows` view is made on first access."""
+    __slots__ = ("count", "fingerprint", "truncated", "status", "_rows", "_src")
+
+    def __init__(self, count, fingerprint, rows, truncated, status):
+        self.count, self.fingerprint, self.truncated, self.status = count, fingerprint, truncated, status
+        self._rows, self._src = rows, None
+
+    @classmethod
+    def _view(cls, count, fingerprint, big, o0, o1, nrows, k, truncated, status):
+        r = cls.__new__(cls)
+        r.count, r.fingerprint, r.truncated, r.status = count, fingerprint, truncated, status
+        r._rows, r._src = None, (big, o0, o1, nrows, k)
+        return r
+
+    @property
+    def rows(self) -> np.ndarray:
+        if self._rows is None:
+            big, o0, o1, nrows, k = self._src
+            self._rows, self._src = big[o0:o1].reshape(nrows, k), None
+        return self._rows
+
+    def __repr__(self):
+        return (f"MatchResult(count={self.count}, fingerprint={self.fingerprint}, rows={self.rows!r}, "
+                f"truncated={self.truncated}, status={self.status})")
 
 
 def _take(r: ResultDesc) -> MatchResult:
@@ -269,17 +295,15 @@ def _take_all(res, n: int) -> list[MatchResult]:
         return []
     a = np.frombuffer(res, dtype=_RES_DTYPE, count=n)
     nr, ks = a["num_rows"].astype(np.int64), a["k"].astype(np.int64)
-    words = nr * ks
     off = np.zeros(n + 1, np.int64)
-    np.cumsum(words, out=off[1:])
+    np.cumsum(nr * ks, out=off[1:])
     big = np.empty(int(off[-1]), np.uint32)
-    base = big.ctypes.data
-    ptrs = a["rows"]
-    for i in np.flatnonzero(words):
-        ctypes.memmove(base + 4 * int(off[i]), int(ptrs[i]), 4 * int(words[i]))
-    counts, fps, tr, st = a["count"].tolist(), a["fingerprint"].tolist(), a["truncated"].tolist(), a["status"].tolist()
-    out = [MatchResult(counts[i], fps[i], big[off[i]:off[i + 1]].reshape(int(nr[i]), int(ks[i])), bool(tr[i]), st[i])
-           for i in range(n)]
+    _check(lib().gs_results_copy_rows(res, n, big.ctypes.data_as(P)))  # every result's rows, back to back
+    offl, nrl, kl = off.tolist(), nr.tolist(), ks.tolist()
+    view = MatchResult._view
+    out = [view(c, f, big, o0, o1, r, k, t != 0, s)
+           for c, f, o0, o1, r, k, t, s in zip(a["count"].tolist(), a["fingerprint"].tolist(), offl, offl[1:], nrl,
+                                                kl, a["truncated"].tolist(), a["status"].tolist())]
     lib().gs_results_free(res, n)
     return out
 

@@ -1227,6 +1227,17 @@ extern "C" void gs_result_free(gs_result *r) {
   r->num_rows = 0;
 }
 
+extern "C" gs_status gs_results_copy_rows(const gs_result *r, uint32_t n, uint32_t *dst) {
+  if (n && (!r || !dst)) return fail(GS_ERR_INVALID, "gs_results_copy_rows: null pointer");
+  uint64_t at = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint64_t words = r[i].num_rows * r[i].k;
+    if (words && r[i].rows) memcpy(dst + at, r[i].rows, 4 * words);
+    at += words;
+  }
+  return GS_OK;
+}
+
 extern "C" void gs_results_free(gs_result *r, uint32_t n) {
   if (!r) return;
   for (uint32_t i = 0; i < n; ++i) gs_result_free(&r[i]);
