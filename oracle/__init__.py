@@ -62,6 +62,8 @@ def _load():
         lib.orc_refine.argtypes = [P, U32, U32, P, P, P, P, P, P]
         lib.orc_edge_table.restype = I
         lib.orc_edge_table.argtypes = [P, U32, U32, P, P, P, P, U32, I, P, P, P, P, P]
+        lib.orc_khop.restype = I
+        lib.orc_khop.argtypes = [P, P, U32, U32, U32, P, P, P]
         lib.orc_verify.restype = ctypes.c_int64
         lib.orc_verify.argtypes = [P, U32, U32, P, P, P, P, P, P, U64]
         _lib = lib
@@ -248,3 +250,25 @@ def fingerprint(rows: np.ndarray) -> int:
     if r.ndim != 2 or r.shape[0] == 0:
         return 0
     return int(_load().orc_fingerprint(r.shape[1], _p(r), r.shape[0]))
+
+
+def relmask(rels=None) -> np.ndarray:
+    """256-bit relation mask (8 uint32 words): every relation when None."""
+    m = np.zeros(8, np.uint32)
+    if rels is None:
+        m[:] = 0xFFFFFFFF
+    else:
+        for r in rels:
+            m[int(r) >> 5] |= np.uint32(1 << (int(r) & 31))
+    return m
+
+
+def khop(g: OracleGraph, seeds, levels: int, dirs: int = 3, rels=None):
+    """Domain-graph exploration: (status, level[V] uint8 with 255 = not
+    reached, counts[levels + 1])."""
+    lib = _load()
+    s = _u32(seeds)
+    lv = np.zeros(g.V, np.uint8)
+    cnt = np.zeros(levels + 1, np.uint64)
+    st = lib.orc_khop(g._h, _p(s), s.shape[0], levels, dirs, _p(relmask(rels)), _p(lv), _p(cnt))
+    return st, lv, cnt

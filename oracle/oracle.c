@@ -603,3 +603,41 @@ int64_t orc_verify(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *v
   }
   return -1;
 }
+
+/*
+ * orc_khop: domain-graph exploration (Ch. 5, "Domain-specific knowledge
+ * graph generation": from some key concepts, explore the knowledge graph a
+ * few levels out).  level_out[v] = the number of hops of a shortest path
+ * from any seed to v, when that is at most `levels`, else 255.  A hop
+ * follows a data edge forwards (dirs bit 0) or backwards (dirs bit 1) whose
+ * relation r has bit r set in relmask (8 words, 256 relations).  Plain
+ * breadth-first search with a queue.  counts[l] = vertices at level l
+ * (levels + 1 entries).  Returns 1 for a seed out of range, else 0.
+ */
+int orc_khop(const orc_graph *g, const uint32_t *seeds, uint32_t nseeds, uint32_t levels, uint32_t dirs,
+             const uint32_t *relmask, uint8_t *level_out, uint64_t *counts) {
+  for (uint32_t i = 0; i < nseeds; ++i) if (seeds[i] >= g->V) return 1;
+  for (uint32_t v = 0; v < g->V; ++v) level_out[v] = 255;
+  for (uint32_t l = 0; l <= levels; ++l) counts[l] = 0;
+  uint32_t *queue = (uint32_t *)malloc(sizeof(uint32_t) * (g->V ? g->V : 1));
+  uint64_t head = 0, tail = 0;
+  for (uint32_t i = 0; i < nseeds; ++i)
+    if (level_out[seeds[i]] == 255) { level_out[seeds[i]] = 0; queue[tail++] = seeds[i]; counts[0]++; }
+  while (head < tail) {
+    const uint32_t u = queue[head++];
+    const uint32_t l = level_out[u];
+    if (l >= levels) continue;
+    for (int dir = 0; dir < 2; ++dir) {
+      if (!((dirs >> dir) & 1u)) continue;
+      for (uint64_t t = orc_begin(g, dir, u); t < orc_begin(g, dir, u + 1); ++t) {
+        const uint32_t r = orc_rel(g, dir, t), w = orc_nbr(g, dir, t);
+        if (!((relmask[r >> 5] >> (r & 31)) & 1u) || level_out[w] != 255) continue;
+        level_out[w] = (uint8_t)(l + 1);
+        counts[l + 1]++;
+        queue[tail++] = w;
+      }
+    }
+  }
+  free(queue);
+  return 0;
+}

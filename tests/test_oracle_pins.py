@@ -271,6 +271,73 @@ def test_projection_closed_forms(n, k):
     assert O.match(t, path, cap=1 << 16, project=1 << k).status == 1   # vertex out of range
 
 
+# ----------------------------------------------- domain-graph exploration
+def min_plus_distances(g, dirs, rels=None):
+    """All-pairs hop distances by repeated min-plus products of the one-hop
+    matrix (edges kept by direction and relation), independent of any
+    queue-based search."""
+    V = g.num_vertices
+    INF = 10 ** 6
+    A = np.full((V, V), INF, np.int64)
+    np.fill_diagonal(A, 0)
+    for s_ in range(V):
+        for e in range(int(g.row_offsets[s_]), int(g.row_offsets[s_ + 1])):
+            r, d = int(g.edge_rel[e]), int(g.col_targets[e])
+            if rels is not None and r not in rels:
+                continue
+            if dirs & 1:
+                A[s_, d] = min(A[s_, d], 1)
+            if dirs & 2:
+                A[d, s_] = min(A[d, s_], 1)
+    D = A.copy()
+    for _ in range(V):
+        D2 = np.minimum(D, (D[:, :, None] + A[None, :, :]).min(axis=1))
+        if (D2 == D).all():
+            break
+        D = D2
+    return D
+
+
+def test_khop_equals_min_plus_distances():
+    """Domain-graph exploration (Ch. 5): the level of v is its hop distance
+    from the nearest seed when within `levels`, for out-, in- and both
+    directions and relation subsets."""
+    rng = np.random.default_rng(4040)
+    for case in range(150):
+        g, _ = random_tiny(rng, n_max=9)
+        V = g.num_vertices
+        dirs = int(rng.integers(1, 4))
+        rels = None if rng.random() < 0.5 else [r for r in range(g.num_rels) if rng.random() < 0.6]
+        seeds = [int(x) for x in rng.choice(V, int(rng.integers(1, 3)), replace=True)]
+        L = int(rng.integers(0, 5))
+        st, lv, cnt = O.khop(og(g), seeds, L, dirs, rels)
+        D = min_plus_distances(g, dirs, rels)[seeds].min(axis=0)
+        want = np.where(D <= L, D, 255).astype(np.uint8)
+        assert st == 0
+        np.testing.assert_array_equal(lv, want, err_msg=str(case))
+        np.testing.assert_array_equal(cnt, [(want == l).sum() for l in range(L + 1)])
+
+
+def test_khop_closed_forms():
+    """Directed path 0->1->...->9: out from 0 reaches level i at vertex i;
+    in from 9 mirrors it; both directions from 5 give |v - 5|.  A directed
+    6-cycle out from 0 gives v.  An out-star from its hub reaches every leaf
+    at level 1 and nothing in reverse."""
+    n = 10
+    p = og(graph_from_triples(n, [(i, 0, i + 1) for i in range(n - 1)]))
+    assert O.khop(p, [0], 20, 1)[1].tolist() == list(range(n))
+    assert O.khop(p, [9], 20, 2)[1].tolist() == list(range(n))[::-1]
+    assert O.khop(p, [5], 3, 3)[1].tolist() == [abs(v - 5) if abs(v - 5) <= 3 else 255 for v in range(n)]
+    assert O.khop(p, [0], 3, 2)[1].tolist() == [0] + [255] * (n - 1)
+    c = og(graph_from_triples(6, [(i, 0, (i + 1) % 6) for i in range(6)]))
+    assert O.khop(c, [0], 10, 1)[1].tolist() == list(range(6))
+    star = og(graph_from_triples(8, [(0, 0, i) for i in range(1, 8)]))
+    assert O.khop(star, [0], 2, 1)[1].tolist() == [0] + [1] * 7
+    assert O.khop(star, [0], 2, 2)[1].tolist() == [0] + [255] * 7
+    assert O.khop(star, [3], 2, 3)[1].tolist() == [1, 2, 2, 0, 2, 2, 2, 2]
+    assert O.khop(star, [8], 2, 3)[0] == 1  # seed out of range
+
+
 # --------------------------------------------------------- worked example
 def test_worked_example():
     """Facts printed for the thesis's sample query/data graph (Section 3.3):
