@@ -284,6 +284,92 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+KHOP_METRIC = "domain-graph exploration: adjacency entries scanned/s (k-hop from seed concepts)"
+
+
+def run_khop(args, world, rank, local):
+    """Domain-graph exploration (k hops from seed concepts, both directions)
+    on a workload's graph: seeds and the level array resident on the device;
+    each step is one whole exploration (level array reset, seeds, every
+    level), timed with CUDA events on the library's stream with L2 flushed
+    between steps; e2e runs the same call from host buffers (seeds in, the
+    V-byte level array out)."""
+    import numpy as np
+    import torch
+    import paper_1807_08804_gb300 as gs
+    from paper_1807_08804_gb300 import inputs as I
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = I.WORKLOADS[args.workload]
+    g = w.graph()
+    dg = gs.DeviceGraph(g)
+    rng = np.random.default_rng(w.seed + 0x6B)
+    seeds = rng.choice(g.num_vertices, args.khop_seeds, replace=False).astype(np.uint32)
+    L = args.khop
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    ts = torch.tensor(seeds.astype(np.int32), device=dev)
+    tl = torch.empty(g.num_vertices, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    run = lambda: gs.khop(dg, None, L, device=(ts.data_ptr(), len(seeds), tl.data_ptr()), stream=sh)
+    for _ in range(max(args.warmup, 3)):
+        _, cnt, edges = run()
+    lv, hc, he = gs.khop(dg, seeds, L)  # the host path gives the same exploration
+    assert hc.tolist() == cnt.tolist() and he == edges and (torch.from_numpy(lv).to(dev) == tl).all().item()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        stream.wait_stream(torch.cuda.current_stream())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    tot_ms = max_over_ranks(sum(ms), world, dev)
+    value = edges * world * args.steps / (tot_ms / 1e3)
+    t = time.perf_counter()
+    e2e_steps = max(2, args.steps // 2)
+    for _ in range(e2e_steps):
+        gs.khop(dg, seeds, L)
+    e2e_s = max_over_ranks(time.perf_counter() - t, world, dev)
+    # algorithmic bytes of one exploration: level array fill and visited
+    # bitmap clear, per frontier vertex its list entry and one row-offset pair
+    # per direction, 4 bytes per adjacency entry scanned, per reached vertex
+    # its level byte and next-frontier entry
+    V = g.num_vertices
+    front = int(cnt[:L].sum())
+    reached = int(cnt.sum())
+    algo = V + V // 8 + front * (4 + 2 * 16) + 4 * edges + 5 * reached
+    peak, peak_kind = measured_peaks()
+    achieved = algo / (tot_ms / args.steps / 1e3) / 1e9
+    line = {"metric": KHOP_METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": w.name, "vertices": V, "edges": w.E, "seeds": len(seeds), "levels": L,
+                       "directions": "both", "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "vertices_per_level": [int(x) for x in cnt], "edges_scanned_per_step": edges,
+            "e2e": {"value": edges * world * e2e_steps / e2e_s, "unit": "edges/s",
+                    "h2d_bytes_per_step": 4 * len(seeds), "d2h_bytes_per_step": V + 8 * (L + 1) + 8},
+            "gpu_launches": 2 + L,
+            "roofline": {"bound": "hbm", "kernel": "khop (one exploration)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                         "bytes_per_step": algo},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dg.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,12 +390,18 @@ def main():
     ap.add_argument("--ablation", action="store_true",
                     help="also time the refinement variants (converged, reversed order, one round, none, "
                          "low-connectivity skip) and report their partial-embedding words")
+    ap.add_argument("--khop", type=int, default=0,
+                    help="time the domain-graph exploration instead: this many hops from --khop-seeds seeds")
+    ap.add_argument("--khop-seeds", type=int, default=16)
     ap.add_argument("--project", default=None,
                     help="comma-separated query vertices whose distinct tuples are returned (projection)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.khop:
+        run_khop(args, world, rank, local)
         return
 
     import torch

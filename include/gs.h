@@ -91,6 +91,30 @@ void gs_graph_free(gs_graph *g);
 uint64_t gs_graph_num_edges(const gs_graph *g);
 
 /*
+ * Domain-graph exploration (Ch. 5, "Domain-specific knowledge graph
+ * generation": from some key concepts, the knowledge graph is explored a few
+ * levels out to collect the concepts of a domain).  level_out[v] = the hop
+ * count of a shortest path from any seed to v when it is at most `levels`,
+ * else 255 (seeds are level 0).  A hop follows an edge forwards
+ * (GS_KHOP_OUT) and/or backwards (GS_KHOP_IN) over the listed relations.
+ * counts[l] = vertices at level l (host array of levels + 1); edges_scanned
+ * (may be NULL) = adjacency entries read.  Errors: levels > 254, directions
+ * 0 or unknown, a relation or a seed out of range -> GS_ERR_INVALID.
+ */
+#define GS_KHOP_OUT 1u
+#define GS_KHOP_IN 2u
+typedef struct {
+  uint32_t levels;         /* hops to explore, 0..254 */
+  uint32_t directions;     /* GS_KHOP_OUT, GS_KHOP_IN or both */
+  const uint32_t *rels;    /* host array of the relations to follow; NULL = every relation */
+  uint32_t nrels;
+  uint32_t flags;          /* GS_DEVICE_PTRS: seeds and level_out are device pointers */
+  void *cuda_stream;       /* stream for the work; NULL = the library's own */
+} gs_khop_opts;
+gs_status gs_khop(gs_graph *g, const uint32_t *seeds, uint32_t nseeds, const gs_khop_opts *opts,
+                  uint8_t *level_out /* [V] */, uint64_t *counts /* [levels + 1] */, uint64_t *edges_scanned);
+
+/*
  * A query graph (Section 3.2: concept nodes, variable nodes, labeled edges).
  * Edges are directed esrc[j] -> edst[j] with relation erel[j].  Repeated
  * edges are dropped.  Errors: k = 0 or k > 16, m > 120, an endpoint >= k, a

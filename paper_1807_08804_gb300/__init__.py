@@ -26,6 +26,7 @@ GS_DEVICE_PTRS = 1
 GS_ENUMERATE, GS_COUNT_ONLY, GS_CHUNKED = 0, 1, 2
 GS_STAGE_FILTER, GS_STAGE_FIXPOINT = 0, 1
 GS_REFINE_OFF, GS_REFINE_REVERSED = 1, 2
+GS_KHOP_OUT, GS_KHOP_IN = 1, 2
 
 
 def GS_REFINE_LOW(d: int) -> int:
@@ -61,6 +62,11 @@ ChunkCallback = ctypes.CFUNCTYPE(None, ctypes.c_void_p, U64, U32, U32, ctypes.c_
 class MatchOpts(ctypes.Structure):
     _fields_ = [("cap", U64), ("mode", U32), ("max_refine_rounds", U32), ("chunk_bytes", U64), ("cuda_stream", P),
                 ("on_chunk", ChunkCallback), ("user", P), ("project", U32), ("refine", U32)]
+
+
+class KhopOpts(ctypes.Structure):
+    _fields_ = [("levels", U32), ("directions", U32), ("rels", P), ("nrels", U32), ("flags", U32),
+                ("cuda_stream", P)]
 
 
 class ResultDesc(ctypes.Structure):
@@ -100,6 +106,7 @@ SIGNATURES = {
     "gs_batch_fetch": (ctypes.c_int, [P, ctypes.POINTER(ResultDesc)]),
     "gs_batch_join_sizes": (ctypes.c_int, [P, P, P]),
     "gs_results_copy_rows": (ctypes.c_int, [P, U32, P]),
+    "gs_khop": (ctypes.c_int, [P, P, U32, ctypes.POINTER(KhopOpts), P, P, P]),
     "gs_batch_destroy": (None, [P]),
     "gs_stats_enable": (ctypes.c_int, [P, ctypes.c_int]),
     "gs_stats_get": (ctypes.c_int, [P, ctypes.POINTER(KernelStats)]),
@@ -372,6 +379,29 @@ def match_batch(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_re
     res = (ResultDesc * max(len(queries), 1))()
     _check(lib().gs_match_batch(dg._h, pack.arr, len(queries), ctypes.byref(o), res))
     return _take_all(res, len(queries))
+
+
+def khop(dg: "DeviceGraph", seeds, levels: int, directions: int = GS_KHOP_OUT | GS_KHOP_IN, rels=None,
+         device=None, stream=None):
+    """Domain-graph exploration from `seeds`: (level uint8 [V], 255 = not
+    reached; counts per level; adjacency entries scanned).  With
+    device=(seeds_ptr, nseeds, level_ptr) the seeds and the level array are
+    device memory (level is then written there and None is returned for it)."""
+    rl = None if rels is None else np.ascontiguousarray(np.asarray(rels, np.uint32))
+    o = KhopOpts(levels, directions, rl.ctypes.data if rl is not None else None, 0 if rl is None else rl.shape[0],
+                 GS_DEVICE_PTRS if device else 0, stream)
+    counts = np.zeros(levels + 1, np.uint64)
+    edges = U64()
+    if device:
+        sp, n, lp = device
+        _check(lib().gs_khop(dg._h, ctypes.c_void_p(sp), n, ctypes.byref(o), ctypes.c_void_p(lp),
+                             counts.ctypes.data_as(P), ctypes.byref(edges)))
+        return None, counts, edges.value
+    sd = np.ascontiguousarray(np.asarray(seeds, np.uint32))
+    level = np.zeros(dg.num_vertices, np.uint8)
+    _check(lib().gs_khop(dg._h, sd.ctypes.data_as(P), sd.shape[0], ctypes.byref(o), level.ctypes.data_as(P),
+                         counts.ctypes.data_as(P), ctypes.byref(edges)))
+    return level, counts, edges.value
 
 
 class Batch:

@@ -481,6 +481,7 @@ extern "C" void gs_graph_free(gs_graph *g) {
   if (!g) return;
   gs::release_cache(g);
   gs::release_fallback(g);
+  gs::release_khop(g);
   cudaFree(g->off_out);
   cudaFree(g->off_in);
   cudaFree(g->adj_out);

@@ -73,6 +73,7 @@ struct gs_graph {
   uint64_t hash;            // content hash (tuning cache key)
   void *cache;              // batches reused by gs_match / gs_match_batch
   void *fallback;           // context of the chunked join
+  void *khop;               // buffers of the domain-graph exploration
   uint32_t tuned_group;     // lanes per work item chosen by gs_tune (0 = default)
   uint32_t tuned_rounds;    // refinement rounds chosen by gs_tune (0 = default)
 };
@@ -81,6 +82,7 @@ namespace gs {
 
 void release_cache(gs_graph *g);
 void release_fallback(gs_graph *g);
+void release_khop(gs_graph *g);
 
 // ------------------------------------------------------------ primitives
 // Exclusive prefix sum of n uint32 counts into out[0..n] (out[n] = total),

@@ -1,0 +1,238 @@
+// Domain-graph exploration (Ch. 5, "Domain-specific knowledge graph
+// generation"): from a set of key concepts, the concepts within a few hops
+// of the knowledge graph, found level by level the way the filtering phase
+// explores (one warp per frontier vertex over its coalesced adjacency row).
+//
+// State: level[V] (uint8, 255 = not reached), a visited bitmap claimed with
+// atomicOr, and two frontier lists.  A level step reads the frontier size
+// from device memory, so the whole exploration runs without a host sync.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+constexpr int kKT = 256;  // threads per block
+constexpr uint32_t kFullMask = 0xFFFFFFFFu;
+
+struct KhopArgs {
+  const uint64_t *off[2];
+  const uint32_t *adj[2];
+  uint32_t dirs;           // bit 0: follow edges forwards, bit 1: backwards
+  uint32_t relmask[8];     // relations followed (bit r)
+  uint32_t all_rels;       // every relation: skip the mask test
+  uint32_t V;
+  uint8_t *level;
+  uint32_t *vis;           // visited bitmap [ceil(V/32)]
+  uint32_t *front[2];      // frontier lists [V]
+  unsigned long long *cnt; // vertices per level [levels + 2]
+  unsigned long long *edges;  // adjacency entries scanned
+  uint32_t *err;           // bit 0: a seed out of range
+};
+
+__device__ __forceinline__ bool claim(const KhopArgs &A, uint32_t v) {
+  const uint32_t bit = 1u << (v & 31);
+  if (A.vis[v >> 5] & bit) return false;
+  return !(atomicOr(&A.vis[v >> 5], bit) & bit);
+}
+
+// Seeds: level 0, frontier 0 (repeated seeds claimed once).
+__global__ void k_khop_seeds(KhopArgs A, const uint32_t *seeds, uint32_t n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t s = seeds[i];
+    if (s >= A.V) {
+      atomicOr(A.err, 1u);
+      continue;
+    }
+    if (claim(A, s)) {
+      A.level[s] = 0;
+      A.front[0][atomicAdd(&A.cnt[0], 1ull)] = s;
+    }
+  }
+}
+
+// One level: every frontier vertex of level l (front[l & 1], cnt[l] of
+// them) scans its rows in the followed directions; each neighbour over a
+// followed relation that is not yet visited is claimed, gets level l + 1 and
+// joins the next frontier (one atomic per warp and row chunk).
+__global__ void __launch_bounds__(kKT) k_khop_level(KhopArgs A, uint32_t l) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nfront = A.cnt[l];
+  const uint32_t *front = A.front[l & 1];
+  uint32_t *next = A.front[(l + 1) & 1];
+  const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  uint64_t scanned = 0;
+  for (uint64_t i = warp0; i < nfront; i += nwarps) {
+    const uint32_t u = front[i];
+    for (int d = 0; d < 2; ++d) {
+      if (!((A.dirs >> d) & 1u)) continue;
+      const uint64_t b = A.off[d][u], e = A.off[d][u + 1];
+      scanned += e - b;
+      for (uint64_t j0 = b; j0 < e; j0 += 32) {
+        const uint64_t j = j0 + lane;
+        bool mine = false;
+        uint32_t w = 0;
+        if (j < e) {
+          const uint32_t x = A.adj[d][j];
+          const uint32_t r = x >> kNbrBits;
+          w = x & kNbrMask;
+          if (A.all_rels || ((A.relmask[r >> 5] >> (r & 31)) & 1u)) mine = claim(A, w);
+        }
+        const uint32_t m = __ballot_sync(kFullMask, mine);
+        if (m) {
+          unsigned long long base = 0;
+          const int leader = __ffs(m) - 1;
+          if (lane == leader) base = atomicAdd(&A.cnt[l + 1], (unsigned long long)__popc(m));
+          base = __shfl_sync(kFullMask, base, leader);
+          if (mine) {
+            A.level[w] = (uint8_t)(l + 1);
+            next[base + __popc(m & ((1u << lane) - 1))] = w;
+          }
+        }
+      }
+    }
+  }
+  if (lane == 0 && scanned) atomicAdd(A.edges, (unsigned long long)scanned);
+}
+
+__global__ void k_fill_u8(uint8_t *p, uint64_t n, uint8_t v) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+}  // namespace
+
+// Per-graph buffers of the exploration, made on first use.
+struct Khop {
+  uint8_t *level = nullptr;
+  uint32_t *vis = nullptr, *front[2] = {}, *seeds = nullptr, *err = nullptr;
+  unsigned long long *cnt = nullptr, *edges = nullptr;
+  uint32_t seeds_cap = 0;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  ~Khop() {
+    for (void *p : {(void *)level, (void *)vis, (void *)front[0], (void *)front[1], (void *)seeds, (void *)err,
+                    (void *)cnt, (void *)edges})
+      if (p) cudaFree(p);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+void release_khop(gs_graph *g) {
+  delete static_cast<Khop *>(g->khop);
+  g->khop = nullptr;
+}
+
+static gs_status khop_ctx(gs_graph *g, Khop **out) {
+  if (g->khop) {
+    *out = static_cast<Khop *>(g->khop);
+    return GS_OK;
+  }
+  Khop *k = new Khop();
+  const uint64_t V = g->d.V, words = (V + 31) / 32;
+  cudaError_t e = cudaMalloc(&k->level, V);
+  if (e == cudaSuccess) e = cudaMalloc(&k->vis, 4 * words);
+  if (e == cudaSuccess) e = cudaMalloc(&k->front[0], 4 * V);
+  if (e == cudaSuccess) e = cudaMalloc(&k->front[1], 4 * V);
+  if (e == cudaSuccess) e = cudaMalloc(&k->err, 4);
+  if (e == cudaSuccess) e = cudaMalloc(&k->cnt, 8 * 257);
+  if (e == cudaSuccess) e = cudaMalloc(&k->edges, 8);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete k;
+    return cuda_fail(e, "gs_khop buffers");
+  }
+  g->khop = k;
+  *out = k;
+  return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" gs_status gs_khop(gs_graph *g, const uint32_t *seeds, uint32_t nseeds, const gs_khop_opts *opts,
+                             uint8_t *level_out, uint64_t *counts, uint64_t *edges_scanned) {
+  if (!g || !opts || !level_out || !counts || (nseeds && !seeds)) return fail(GS_ERR_INVALID, "gs_khop: null argument");
+  if (opts->levels > 254) return fail(GS_ERR_INVALID, "gs_khop: levels must be at most 254");
+  if (opts->directions == 0 || opts->directions > (GS_KHOP_OUT | GS_KHOP_IN))
+    return fail(GS_ERR_INVALID, "gs_khop: directions must be GS_KHOP_OUT, GS_KHOP_IN or both");
+  if (opts->nrels && !opts->rels) return fail(GS_ERR_INVALID, "gs_khop: null relation list");
+  KhopArgs A;
+  memset(&A, 0, sizeof(A));
+  A.all_rels = opts->rels ? 0u : 1u;
+  for (uint32_t i = 0; opts->rels && i < opts->nrels; ++i) {
+    const uint32_t r = opts->rels[i];
+    if (r >= g->d.R) return fail(GS_ERR_INVALID, "gs_khop: relation out of range");
+    A.relmask[r >> 5] |= 1u << (r & 31);
+  }
+  const bool on_dev = (opts->flags & GS_DEVICE_PTRS) != 0;
+  if (!on_dev)
+    for (uint32_t i = 0; i < nseeds; ++i)
+      if (seeds[i] >= g->d.V) return fail(GS_ERR_INVALID, "gs_khop: seed out of range");
+  GS_CUDA(cudaSetDevice(g->device));
+  Khop *k = nullptr;
+  gs_status st = khop_ctx(g, &k);
+  if (st != GS_OK) return st;
+  std::lock_guard<std::mutex> lk(k->mu);
+  const cudaStream_t s = opts->cuda_stream ? static_cast<cudaStream_t>(opts->cuda_stream) : k->stream;
+  const uint32_t V = g->d.V, L = opts->levels;
+  const uint32_t *dseeds = seeds;
+  if (!on_dev && nseeds) {
+    if (nseeds > k->seeds_cap) {
+      if (k->seeds) cudaFree(k->seeds);
+      k->seeds = nullptr;
+      k->seeds_cap = 0;
+      GS_CUDA(cudaMalloc(&k->seeds, 4ull * nseeds));
+      k->seeds_cap = nseeds;
+    }
+    GS_CUDA(cudaMemcpyAsync(k->seeds, seeds, 4ull * nseeds, cudaMemcpyHostToDevice, s));
+    dseeds = k->seeds;
+  }
+  A.off[0] = g->d.off[0]; A.off[1] = g->d.off[1];
+  A.adj[0] = g->d.adj[0]; A.adj[1] = g->d.adj[1];
+  A.dirs = opts->directions;
+  A.V = V;
+  A.level = on_dev ? level_out : k->level;
+  A.vis = k->vis;
+  A.front[0] = k->front[0]; A.front[1] = k->front[1];
+  A.cnt = k->cnt;
+  A.edges = k->edges;
+  A.err = k->err;
+  const unsigned fill_grid = (unsigned)std::min<uint64_t>((V + kKT - 1) / kKT, (uint64_t)g->num_sms * 8);
+  k_fill_u8<<<fill_grid, kKT, 0, s>>>(A.level, V, 255);
+  GS_CUDA(cudaMemsetAsync(A.vis, 0, 4ull * ((V + 31) / 32), s));
+  GS_CUDA(cudaMemsetAsync(A.cnt, 0, 8ull * (L + 2), s));
+  GS_CUDA(cudaMemsetAsync(A.edges, 0, 8, s));
+  GS_CUDA(cudaMemsetAsync(A.err, 0, 4, s));
+  if (nseeds) {
+    const unsigned sg = (unsigned)std::min<uint64_t>((nseeds + kKT - 1) / kKT, (uint64_t)g->num_sms * 4);
+    k_khop_seeds<<<sg, kKT, 0, s>>>(A, dseeds, nseeds);
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_khop_level, kKT, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const unsigned grid = (unsigned)(g->num_sms * std::min(per_sm, 8));
+  for (uint32_t l = 0; l < L; ++l) k_khop_level<<<grid, kKT, 0, s>>>(A, l);
+  GS_CUDA(cudaGetLastError());
+  std::vector<unsigned long long> c(L + 1);
+  uint32_t err = 0;
+  unsigned long long ed = 0;
+  GS_CUDA(cudaMemcpyAsync(c.data(), A.cnt, 8ull * (L + 1), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaMemcpyAsync(&err, A.err, 4, cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaMemcpyAsync(&ed, A.edges, 8, cudaMemcpyDeviceToHost, s));
+  if (!on_dev) GS_CUDA(cudaMemcpyAsync(level_out, A.level, V, cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  if (err & 1u) return fail(GS_ERR_INVALID, "gs_khop: seed out of range");
+  for (uint32_t l = 0; l <= L; ++l) counts[l] = c[l];
+  if (edges_scanned) *edges_scanned = ed;
+  return GS_OK;
+}
