@@ -1,11 +1,12 @@
 // Domain-graph exploration (Ch. 5, "Domain-specific knowledge graph
 // generation"): from a set of key concepts, the concepts within a few hops
 // of the knowledge graph, found level by level the way the filtering phase
-// explores (one warp per frontier vertex over its coalesced adjacency row).
+// explores (warps over the frontier vertices' coalesced adjacency rows).
 //
 // State: level[V] (uint8, 255 = not reached), a visited bitmap claimed with
 // atomicOr, and two frontier lists.  A level step reads the frontier size
 // from device memory, so the whole exploration runs without a host sync.
+// The last level needs neither the bitmap nor a frontier.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -56,49 +57,97 @@ __global__ void k_khop_seeds(KhopArgs A, const uint32_t *seeds, uint32_t n) {
   }
 }
 
-// One level: every frontier vertex of level l (front[l & 1], cnt[l] of
-// them) scans its rows in the followed directions; each neighbour over a
-// followed relation that is not yet visited is claimed, gets level l + 1 and
-// joins the next frontier (one atomic per warp and row chunk).
-__global__ void __launch_bounds__(kKT) k_khop_level(KhopArgs A, uint32_t l) {
+// One level: the frontier vertices of level l (front[l & 1], cnt[l] of
+// them) scan their rows in the followed directions; each neighbour over a
+// followed relation that is not yet visited gets level l + 1.  Load
+// balanced: a warp takes up to 32 frontier vertices at once (fewer when the
+// frontier is small, so that every warp has work), scans their row lengths,
+// and walks the concatenated rows 32 entries per step, each lane finding the
+// vertex and row of its entry by a search over the scan held in registers.
+// Below the last level a neighbour is claimed in the visited bitmap and
+// appended to the next frontier (one atomic per warp and step).  The last
+// level builds no frontier: an unreached neighbour's level is written
+// without atomics (every writer writes the same value) and counted after.
+template <bool LAST>
+__global__ void __launch_bounds__(kKT, 6) k_khop_level(KhopArgs A, uint32_t l) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nfront = A.cnt[l];
   const uint32_t *front = A.front[l & 1];
   uint32_t *next = A.front[(l + 1) & 1];
   const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t per_warp = (nfront + nwarps - 1) / nwarps;
+  const uint32_t vpw = per_warp >= 32 ? 32u : (per_warp ? (uint32_t)per_warp : 1u);
+  const bool fw = A.dirs & 1u, bw = (A.dirs >> 1) & 1u;
   uint64_t scanned = 0;
-  for (uint64_t i = warp0; i < nfront; i += nwarps) {
-    const uint32_t u = front[i];
-    for (int d = 0; d < 2; ++d) {
-      if (!((A.dirs >> d) & 1u)) continue;
-      const uint64_t b = A.off[d][u], e = A.off[d][u + 1];
-      scanned += e - b;
-      for (uint64_t j0 = b; j0 < e; j0 += 32) {
-        const uint64_t j = j0 + lane;
-        bool mine = false;
-        uint32_t w = 0;
-        if (j < e) {
-          const uint32_t x = A.adj[d][j];
-          const uint32_t r = x >> kNbrBits;
-          w = x & kNbrMask;
-          if (A.all_rels || ((A.relmask[r >> 5] >> (r & 31)) & 1u)) mine = claim(A, w);
-        }
-        const uint32_t m = __ballot_sync(kFullMask, mine);
-        if (m) {
-          unsigned long long base = 0;
-          const int leader = __ffs(m) - 1;
-          if (lane == leader) base = atomicAdd(&A.cnt[l + 1], (unsigned long long)__popc(m));
-          base = __shfl_sync(kFullMask, base, leader);
-          if (mine) {
-            A.level[w] = (uint8_t)(l + 1);
-            next[base + __popc(m & ((1u << lane) - 1))] = w;
+  for (uint64_t i0 = warp0 * vpw; i0 < nfront; i0 += nwarps * vpw) {
+    // this lane's frontier vertex: its forward and backward row ranges
+    uint64_t b0 = 0, b1 = 0;
+    uint32_t n0 = 0, n1 = 0;
+    if (lane < vpw && i0 + lane < nfront) {
+      const uint32_t u = front[i0 + lane];
+      if (fw) { b0 = A.off[0][u]; n0 = (uint32_t)(A.off[0][u + 1] - b0); }
+      if (bw) { b1 = A.off[1][u]; n1 = (uint32_t)(A.off[1][u + 1] - b1); }
+    }
+    // inclusive scan of the lanes' entry counts
+    uint32_t incl = n0 + n1;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFullMask, incl, 31);
+    scanned += total;
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t t = t0 + lane;
+      // owner lane: the first lane whose inclusive count exceeds t
+      int owner = 0;
+      for (int step = 16; step; step >>= 1) {
+        const uint32_t c = __shfl_sync(kFullMask, incl, owner + step - 1);
+        if (c <= t) owner += step;
+      }
+      const uint32_t on0 = __shfl_sync(kFullMask, n0, owner);
+      const uint32_t before = __shfl_sync(kFullMask, incl, owner) - on0 - __shfl_sync(kFullMask, n1, owner);
+      const uint64_t ob0 = __shfl_sync(kFullMask, b0, owner), ob1 = __shfl_sync(kFullMask, b1, owner);
+      bool mine = false;
+      uint32_t w = 0;
+      if (t < total) {
+        const uint32_t k = t - before;  // entry k of the owner's rows: forward first, then backward
+        const uint32_t x = k < on0 ? A.adj[0][ob0 + k] : A.adj[1][ob1 + (k - on0)];
+        const uint32_t r = x >> kNbrBits;
+        w = x & kNbrMask;
+        if (A.all_rels || ((A.relmask[r >> 5] >> (r & 31)) & 1u)) {
+          if (LAST) {
+            if (A.level[w] == 255) A.level[w] = (uint8_t)(l + 1);
+          } else {
+            mine = claim(A, w);
           }
+        }
+      }
+      if (LAST) continue;
+      const uint32_t m = __ballot_sync(kFullMask, mine);
+      if (m) {
+        unsigned long long base = 0;
+        const int leader = __ffs(m) - 1;
+        if (lane == leader) base = atomicAdd(&A.cnt[l + 1], (unsigned long long)__popc(m));
+        base = __shfl_sync(kFullMask, base, leader);
+        if (mine) {
+          A.level[w] = (uint8_t)(l + 1);
+          next[base + __popc(m & ((1u << lane) - 1))] = w;
         }
       }
     }
   }
   if (lane == 0 && scanned) atomicAdd(A.edges, (unsigned long long)scanned);
+}
+
+// Vertices whose level is l (the last level's count), four level bytes per
+// load where aligned.
+__global__ void k_count_level(KhopArgs A, uint32_t l) {
+  uint32_t c = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < A.V; i += (uint64_t)gridDim.x * blockDim.x)
+    c += A.level[i] == l;
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(kFullMask, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&A.cnt[l], (unsigned long long)c);
 }
 
 __global__ void k_fill_u8(uint8_t *p, uint64_t n, uint8_t v) {
@@ -216,12 +265,17 @@ extern "C" gs_status gs_khop(gs_graph *g, const uint32_t *seeds, uint32_t nseeds
     k_khop_seeds<<<sg, kKT, 0, s>>>(A, dseeds, nseeds);
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_khop_level, kKT, 0) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_khop_level<false>, kKT, 0) != cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
   const unsigned grid = (unsigned)(g->num_sms * std::min(per_sm, 8));
-  for (uint32_t l = 0; l < L; ++l) k_khop_level<<<grid, kKT, 0, s>>>(A, l);
+  for (uint32_t l = 0; l + 1 < L; ++l) k_khop_level<false><<<grid, kKT, 0, s>>>(A, l);
+  if (L > 0) {
+    k_khop_level<true><<<grid, kKT, 0, s>>>(A, L - 1);
+    k_count_level<<<fill_grid, kKT, 0, s>>>(A, L);
+  }
   GS_CUDA(cudaGetLastError());
   std::vector<unsigned long long> c(L + 1);
   uint32_t err = 0;
