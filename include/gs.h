@@ -92,8 +92,8 @@ uint64_t gs_graph_num_edges(const gs_graph *g);
 
 /*
  * Domain-graph exploration (Ch. 5, "Domain-specific knowledge graph
- * generation": from some key concepts, the knowledge graph is explored a few
- * levels out to collect the concepts of a domain).  level_out[v] = the hop
+ * generation": the knowledge graph is explored a few levels out from chosen
+ * seed concepts to collect the concepts of a domain).  level_out[v] = the hop
  * count of a shortest path from any seed to v when it is at most `levels`,
  * else 255 (seeds are level 0).  A hop follows an edge forwards
  * (GS_KHOP_OUT) and/or backwards (GS_KHOP_IN) over the listed relations.

@@ -606,8 +606,8 @@ int64_t orc_verify(const orc_graph *g, uint32_t k, uint32_t m, const uint32_t *v
 
 /*
  * orc_khop: domain-graph exploration (Ch. 5, "Domain-specific knowledge
- * graph generation": from some key concepts, explore the knowledge graph a
- * few levels out).  level_out[v] = the number of hops of a shortest path
+ * graph generation": the knowledge graph explored a few levels out from
+ * chosen seed concepts).  level_out[v] = the number of hops of a shortest path
  * from any seed to v, when that is at most `levels`, else 255.  A hop
  * follows a data edge forwards (dirs bit 0) or backwards (dirs bit 1) whose
  * relation r has bit r set in relmask (8 words, 256 relations).  Plain

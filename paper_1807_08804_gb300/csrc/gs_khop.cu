@@ -1,7 +1,7 @@
 // Domain-graph exploration (Ch. 5, "Domain-specific knowledge graph
-// generation"): from a set of key concepts, the concepts within a few hops
-// of the knowledge graph, found level by level the way the filtering phase
-// explores (warps over the frontier vertices' coalesced adjacency rows).
+// generation"): the concepts within a few hops of a set of seed concepts,
+// found level by level the way the filtering phase explores (warps over the
+// frontier vertices' coalesced adjacency rows).
 //
 // State: level[V] (uint8, 255 = not reached), a visited bitmap claimed with
 // atomicOr, and two frontier lists.  A level step reads the frontier size
