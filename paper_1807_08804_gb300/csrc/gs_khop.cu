@@ -32,6 +32,7 @@ struct KhopArgs {
   uint32_t *vis;           // visited bitmap [ceil(V/32)]
   uint32_t *front[2];      // frontier lists [V]
   unsigned long long *cnt; // vertices per level [levels + 2]
+  unsigned long long *grab;  // per level: frontier entries handed out to warps so far
   unsigned long long *edges;  // adjacency entries scanned
   uint32_t *err;           // bit 0: a seed out of range
 };
@@ -60,27 +61,61 @@ __global__ void k_khop_seeds(KhopArgs A, const uint32_t *seeds, uint32_t n) {
 // One level: the frontier vertices of level l (front[l & 1], cnt[l] of
 // them) scan their rows in the followed directions; each neighbour over a
 // followed relation that is not yet visited gets level l + 1.  Load
-// balanced: a warp takes up to 32 frontier vertices at once (fewer when the
-// frontier is small, so that every warp has work), scans their row lengths,
+// balanced: a warp takes up to 32 frontier vertices at a time from a shared
+// counter (fewer when the frontier is small, and when it is smaller than the
+// grid several warps share one vertex's rows), scans their row lengths,
 // and walks the concatenated rows 32 entries per step, each lane finding the
 // vertex and row of its entry by a search over the scan held in registers.
 // Below the last level a neighbour is claimed in the visited bitmap and
 // appended to the next frontier (one atomic per warp and step).  The last
 // level builds no frontier: an unreached neighbour's level is written
 // without atomics (every writer writes the same value) and counted after.
+// Entry t of a warp's concatenated rows: the owner lane (a search over the
+// inclusive counts held in registers) and the adjacency entry itself.
+__device__ __forceinline__ uint32_t row_entry(const KhopArgs &A, uint32_t incl, uint32_t n0, uint32_t n1, uint64_t b0,
+                                              uint64_t b1, uint32_t t, uint32_t total, bool &valid) {
+  int owner = 0;
+  for (int step = 16; step; step >>= 1) {
+    const uint32_t c = __shfl_sync(kFullMask, incl, owner + step - 1);
+    if (c <= t) owner += step;
+  }
+  const uint32_t on0 = __shfl_sync(kFullMask, n0, owner);
+  const uint32_t before = __shfl_sync(kFullMask, incl, owner) - on0 - __shfl_sync(kFullMask, n1, owner);
+  const uint64_t ob0 = __shfl_sync(kFullMask, b0, owner), ob1 = __shfl_sync(kFullMask, b1, owner);
+  valid = t < total;
+  if (!valid) return 0;
+  const uint32_t k = t - before;  // entry k of the owner's rows: forward first, then backward
+  return k < on0 ? A.adj[0][ob0 + k] : A.adj[1][ob1 + (k - on0)];
+}
+
+__device__ __forceinline__ bool follow(const KhopArgs &A, uint32_t x) {
+  const uint32_t r = x >> kNbrBits;
+  return A.all_rels || ((A.relmask[r >> 5] >> (r & 31)) & 1u);
+}
+
 template <bool LAST>
 __global__ void __launch_bounds__(kKT, 6) k_khop_level(KhopArgs A, uint32_t l) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nfront = A.cnt[l];
   const uint32_t *front = A.front[l & 1];
   uint32_t *next = A.front[(l + 1) & 1];
-  const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  // work units: vpw frontier vertices per warp when the frontier is large;
+  // when it is smaller than the grid, wpv warps share each vertex's rows
   const uint64_t per_warp = (nfront + nwarps - 1) / nwarps;
   const uint32_t vpw = per_warp >= 32 ? 32u : (per_warp ? (uint32_t)per_warp : 1u);
+  const uint32_t wpv = nfront && nfront < nwarps ? (uint32_t)min((uint64_t)32, nwarps / nfront) : 1u;
   const bool fw = A.dirs & 1u, bw = (A.dirs >> 1) & 1u;
   uint64_t scanned = 0;
-  for (uint64_t i0 = warp0 * vpw; i0 < nfront; i0 += nwarps * vpw) {
+  for (;;) {
+    // the next unit, taken from a shared counter so that warps that drew
+    // short rows take more
+    unsigned long long g = 0;
+    if (lane == 0) g = atomicAdd(&A.grab[l], (unsigned long long)(wpv > 1 ? 1u : vpw));
+    g = __shfl_sync(kFullMask, g, 0);
+    const uint64_t i0 = wpv > 1 ? g / wpv : g;
+    const uint32_t sub = wpv > 1 ? (uint32_t)(g % wpv) : 0u;
+    if (i0 >= nfront) break;
     // this lane's frontier vertex: its forward and backward row ranges
     uint64_t b0 = 0, b1 = 0;
     uint32_t n0 = 0, n1 = 0;
@@ -96,34 +131,27 @@ __global__ void __launch_bounds__(kKT, 6) k_khop_level(KhopArgs A, uint32_t l) {
       if (lane >= o) incl += y;
     }
     const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-    scanned += total;
-    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
-      const uint32_t t = t0 + lane;
-      // owner lane: the first lane whose inclusive count exceeds t
-      int owner = 0;
-      for (int step = 16; step; step >>= 1) {
-        const uint32_t c = __shfl_sync(kFullMask, incl, owner + step - 1);
-        if (c <= t) owner += step;
+    if (sub == 0) scanned += total;
+    const uint32_t stride = 32 * wpv;
+    if (LAST) {
+      // two entries per lane and step: independent loads in flight
+      for (uint32_t t0 = 32 * sub; t0 < total; t0 += 2 * stride) {
+        bool v0, v1;
+        const uint32_t x0 = row_entry(A, incl, n0, n1, b0, b1, t0 + lane, total, v0);
+        const uint32_t x1 = row_entry(A, incl, n0, n1, b0, b1, t0 + stride + lane, total, v1);
+        const uint32_t w0 = x0 & kNbrMask, w1 = x1 & kNbrMask;
+        const bool f0 = v0 && follow(A, x0), f1 = v1 && follow(A, x1);
+        const uint8_t l0 = f0 ? A.level[w0] : 0, l1 = f1 ? A.level[w1] : 0;
+        if (f0 && l0 == 255) A.level[w0] = (uint8_t)(l + 1);
+        if (f1 && l1 == 255) A.level[w1] = (uint8_t)(l + 1);
       }
-      const uint32_t on0 = __shfl_sync(kFullMask, n0, owner);
-      const uint32_t before = __shfl_sync(kFullMask, incl, owner) - on0 - __shfl_sync(kFullMask, n1, owner);
-      const uint64_t ob0 = __shfl_sync(kFullMask, b0, owner), ob1 = __shfl_sync(kFullMask, b1, owner);
-      bool mine = false;
-      uint32_t w = 0;
-      if (t < total) {
-        const uint32_t k = t - before;  // entry k of the owner's rows: forward first, then backward
-        const uint32_t x = k < on0 ? A.adj[0][ob0 + k] : A.adj[1][ob1 + (k - on0)];
-        const uint32_t r = x >> kNbrBits;
-        w = x & kNbrMask;
-        if (A.all_rels || ((A.relmask[r >> 5] >> (r & 31)) & 1u)) {
-          if (LAST) {
-            if (A.level[w] == 255) A.level[w] = (uint8_t)(l + 1);
-          } else {
-            mine = claim(A, w);
-          }
-        }
-      }
-      if (LAST) continue;
+      continue;
+    }
+    for (uint32_t t0 = 32 * sub; t0 < total; t0 += stride) {
+      bool valid;
+      const uint32_t x = row_entry(A, incl, n0, n1, b0, b1, t0 + lane, total, valid);
+      const uint32_t w = x & kNbrMask;
+      const bool mine = valid && follow(A, x) && claim(A, w);
       const uint32_t m = __ballot_sync(kFullMask, mine);
       if (m) {
         unsigned long long base = 0;
@@ -190,7 +218,7 @@ static gs_status khop_ctx(gs_graph *g, Khop **out) {
   if (e == cudaSuccess) e = cudaMalloc(&k->front[0], 4 * V);
   if (e == cudaSuccess) e = cudaMalloc(&k->front[1], 4 * V);
   if (e == cudaSuccess) e = cudaMalloc(&k->err, 4);
-  if (e == cudaSuccess) e = cudaMalloc(&k->cnt, 8 * 257);
+  if (e == cudaSuccess) e = cudaMalloc(&k->cnt, 8 * 512);  // counts [0, 256), hand-out counters [256, 512)
   if (e == cudaSuccess) e = cudaMalloc(&k->edges, 8);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -252,12 +280,14 @@ extern "C" gs_status gs_khop(gs_graph *g, const uint32_t *seeds, uint32_t nseeds
   A.vis = k->vis;
   A.front[0] = k->front[0]; A.front[1] = k->front[1];
   A.cnt = k->cnt;
+  A.grab = k->cnt + 256;
   A.edges = k->edges;
   A.err = k->err;
   const unsigned fill_grid = (unsigned)std::min<uint64_t>((V + kKT - 1) / kKT, (uint64_t)g->num_sms * 8);
   k_fill_u8<<<fill_grid, kKT, 0, s>>>(A.level, V, 255);
   GS_CUDA(cudaMemsetAsync(A.vis, 0, 4ull * ((V + 31) / 32), s));
   GS_CUDA(cudaMemsetAsync(A.cnt, 0, 8ull * (L + 2), s));
+  GS_CUDA(cudaMemsetAsync(A.grab, 0, 8ull * (L + 1), s));
   GS_CUDA(cudaMemsetAsync(A.edges, 0, 8, s));
   GS_CUDA(cudaMemsetAsync(A.err, 0, 4, s));
   if (nseeds) {
