@@ -688,6 +688,7 @@ gs_status run_end(gs_batch *b) {
 }
 
 static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match_opts *opts) {
+  const bool had_rev = b->has_rev;
   b->n = n;
   b->hq.assign(n, DQuery{});
   b->hstatus.assign(n, GS_OK);
@@ -704,6 +705,9 @@ static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match
     b->has_rev = b->has_rev || (b->hq[i].refine_flags & kRefineRev);
     b->max_k = std::max<uint32_t>(b->max_k, b->hq[i].k);
   }
+  // the captured graphs launch refinement once per round, or once per query
+  // vertex position per round for the reversed order: recapture on a change
+  if (b->has_rev != had_rev) ::drop_graphs(b);
   b->ran = b->finished = false;
 }
 

@@ -206,7 +206,10 @@ void release_khop(gs_graph *g) {
   g->khop = nullptr;
 }
 
+static std::mutex g_khop_ctx_mu;  // first use on a graph from several threads
+
 static gs_status khop_ctx(gs_graph *g, Khop **out) {
+  std::lock_guard<std::mutex> lk(g_khop_ctx_mu);
   if (g->khop) {
     *out = static_cast<Khop *>(g->khop);
     return GS_OK;

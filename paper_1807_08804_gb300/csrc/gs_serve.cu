@@ -60,7 +60,7 @@ struct Slot {
 
 bool same_opts(const gs_match_opts &a, const gs_match_opts &b) {
   return a.cap == b.cap && a.mode == b.mode && a.max_refine_rounds == b.max_refine_rounds &&
-         a.chunk_bytes == b.chunk_bytes && a.project == b.project;
+         a.chunk_bytes == b.chunk_bytes && a.project == b.project && a.refine == b.refine;
 }
 
 }  // namespace
