@@ -1518,8 +1518,10 @@ __device__ __forceinline__ uint32_t block_scan_excl(uint32_t *v, uint32_t n) {
 // runs from a block scan) and writes the first `cap` of them.
 __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
   __shared__ uint64_t key[kSmallRows];
+  __shared__ uint64_t key2[kSmallRows];  // the columns from the first one key does not hold whole
   __shared__ uint32_t idx[kSmallRows];
   const uint32_t b = W.G.idbits;
+  const uint32_t f = 64 / b;  // output columns held whole by one key word
   for (uint32_t qi = blockIdx.x; qi < W.nq; qi += gridDim.x) {
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
@@ -1529,11 +1531,14 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
     const uint32_t r0 = (uint32_t)S.out_row_base;
     uint32_t np2 = 1;
     while (np2 < n) np2 <<= 1;
+    const uint32_t kp = Q.kp;
+    const bool exact = kp <= 2 * f;  // the two key words decide every comparison
     for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
       idx[i] = i;
       if (i < n) {
         const uint32_t *x = rows + (uint64_t)i * k;
-        key[i] = pack_key(Q.kp, b, [&](uint32_t c) { return x[Q.opos[c]]; });
+        key[i] = pack_key(kp, b, [&](uint32_t c) { return x[Q.opos[c]]; });
+        key2[i] = kp > f ? pack_key(kp - f, b, [&](uint32_t c) { return x[Q.opos[f + c]]; }) : 0;
       }
     }
     __syncthreads();
@@ -1541,7 +1546,8 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
       if (a >= n) return false;
       if (c >= n) return true;
       if (key[a] != key[c]) return key[a] < key[c];
-      return !out_row_le(W, Q, S, r0 + c, r0 + a);
+      if (key2[a] != key2[c]) return key2[a] < key2[c];
+      return !exact && !out_row_le(W, Q, S, r0 + c, r0 + a);
     };
     for (uint32_t size = 2; size <= np2; size <<= 1)
       for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
@@ -1567,10 +1573,11 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
     // neighbour's read masks the bit, so marking in place is safe); then the
     // keys are done with and their space holds the ranks
     constexpr uint32_t kMark = 0x80000000u;
-    const uint32_t kp = Q.kp, nr = (np2 + 255) / 256 * 256;
+    const uint32_t nr = (np2 + 255) / 256 * 256;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
       const uint32_t a = idx[i] & ~kMark, p = i ? idx[i - 1] & ~kMark : 0;
-      if (i == 0 || key[a] != key[p] || !out_row_eq(W, Q, S, r0 + a, r0 + p)) idx[i] = a | kMark;
+      if (i == 0 || key[a] != key[p] || key2[a] != key2[p] || (!exact && !out_row_eq(W, Q, S, r0 + a, r0 + p)))
+        idx[i] = a | kMark;
     }
     __syncthreads();
     uint32_t *rnk = reinterpret_cast<uint32_t *>(key);
