@@ -483,7 +483,7 @@ void enqueue_large_sort(Pipe &P, uint64_t max_rows, uint64_t over_cap, bool proj
   Wave &W = b->W;
   const int sms = b->sms;
   uint32_t *perm[2] = {W.sval[0], W.sval[1]};
-  uint64_t *keys[2] = {W.skey[0], W.skey[1]};
+  SortKey *keys[2] = {W.skey[0], W.skey[1]};
   int cur = 0;
   P.begin(KK_SORT_LARGE);
   launch_sort_keys(W, perm[0], keys[0], P.cur, sms);

@@ -119,6 +119,18 @@ struct QState {
 // the rows returned.
 constexpr uint64_t kRowsMore = 1ull << 63;
 
+// Sort key of the large-output merge sort: the row's output columns packed
+// at the graph's id width, the leading ones in hi, the following ones
+// (from the first column hi does not hold whole) in lo.
+struct SortKey {
+  uint64_t hi, lo;
+};
+__host__ __device__ __forceinline__ bool operator==(const SortKey &a, const SortKey &b) { return a.hi == b.hi && a.lo == b.lo; }
+__host__ __device__ __forceinline__ bool operator!=(const SortKey &a, const SortKey &b) { return !(a == b); }
+__host__ __device__ __forceinline__ bool operator<(const SortKey &a, const SortKey &b) {
+  return a.hi != b.hi ? a.hi < b.hi : a.lo < b.lo;
+}
+
 // Top-cap selection of a query with more than cap large rows (radix select
 // on the packed sort keys): rows with key <= thresh go into the sort.
 struct SelState {
@@ -217,7 +229,7 @@ struct Wave {
   uint64_t out_rows_cap;
   uint32_t *out_final;              // sorted rows, query-vertex order
   // sort
-  uint64_t *skey[2];                    // sort keys of the large-output merge sort
+  SortKey *skey[2];                     // sort keys of the large-output merge sort
   uint32_t *sval[2];                    // row indices of the large-output merge sort
   uint64_t *msplit;                     // merge-path split of each output tile
   uint32_t *ptcount;                    // projected outputs: distinct tuples starting in each tile
@@ -251,16 +263,16 @@ void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s);
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms);
 void launch_final_bases(const Wave &W, cudaStream_t s);
 void launch_small_sort(const Wave &W, cudaStream_t s, int sms);
-void launch_sort_keys(const Wave &W, uint32_t *perm, uint64_t *keys, cudaStream_t s, int sms);
-void launch_select(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+void launch_sort_keys(const Wave &W, uint32_t *perm, SortKey *keys, cudaStream_t s, int sms);
+void launch_select(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                    cudaStream_t s, int sms);
-void launch_tile_sort(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+void launch_tile_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                       cudaStream_t s, int sms);
-void launch_merge_pass(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+void launch_merge_pass(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                        uint64_t run, cudaStream_t s, int sms);
 void launch_gather(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, cudaStream_t s, int sms);
-void launch_project(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, const uint64_t *key0,
-                    const uint64_t *key1, uint64_t max_tiles, uint64_t *scan_tmp, cudaStream_t s, int sms);
+void launch_project(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, const SortKey *key0,
+                    const SortKey *key1, uint64_t max_tiles, uint64_t *scan_tmp, cudaStream_t s, int sms);
 void launch_epilogue(const Wave &W, cudaStream_t s, int sms);
 
 }  // namespace gs

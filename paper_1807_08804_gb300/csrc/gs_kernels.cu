@@ -1466,10 +1466,23 @@ __device__ __forceinline__ bool out_row_eq(const Wave &W, const DQuery &Q, const
 }
 
 // (ka, a) <= (kb, b): keys first, the rows on equal keys.
-__device__ __forceinline__ bool kr_le(const Wave &W, const DQuery &Q, const QState &S, uint64_t ka, uint32_t ra,
-                                      uint64_t kb, uint32_t rb) {
+// Do the two key words hold every output column whole?
+__device__ __forceinline__ bool keys_exact(const Wave &W, const DQuery &Q) { return Q.kp <= 2 * (64 / W.G.idbits); }
+
+__device__ __forceinline__ bool kr_le(const Wave &W, const DQuery &Q, const QState &S, SortKey ka, uint32_t ra,
+                                      SortKey kb, uint32_t rb) {
   if (ka != kb) return ka < kb;
-  return out_row_le(W, Q, S, ra, rb);
+  return keys_exact(W, Q) || out_row_le(W, Q, S, ra, rb);
+}
+
+// The sort key of a row whose output column c is col(c).
+template <class Col>
+__device__ __forceinline__ SortKey sort_key(uint32_t kp, uint32_t b, Col col) {
+  const uint32_t f = 64 / b;
+  SortKey k;
+  k.hi = pack_key(kp, b, col);
+  k.lo = kp > f ? pack_key(kp - f, b, [&](uint32_t c) { return col(f + c); }) : 0;
+  return k;
 }
 
 // Exclusive scan of v[0..n) in shared memory by one block of 256 threads,
@@ -1601,7 +1614,7 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
 // Sort keys of every large row, in query order (row i of a query at
 // lrg_row_base + i); for a query to be cut at cap, the smallest and largest
 // key (one atomic per warp when the warp's rows share a query).
-__global__ void k_sort_keys(Wave W, uint32_t *perm, uint64_t *keys) {
+__global__ void k_sort_keys(Wave W, uint32_t *perm, SortKey *keys) {
   const uint64_t n = W.ctrl->len[6];
   const uint32_t b = W.G.idbits, lane = threadIdx.x & 31;
   for (uint64_t base = gtid() - lane; base < n; base += gthreads()) {
@@ -1614,8 +1627,9 @@ __global__ void k_sort_keys(Wave W, uint32_t *perm, uint64_t *keys) {
       const QState &S = W.qs[qi];
       const uint64_t local = i - S.lrg_row_base;
       const uint32_t *x = W.out + S.out_word_base + local * Q.k;
-      key = pack_key(Q.kp, b, [&](uint32_t i) { return x[Q.opos[i]]; });
-      keys[i] = key;
+      const SortKey k2 = sort_key(Q.kp, b, [&](uint32_t c) { return x[Q.opos[c]]; });
+      key = k2.hi;  // the selection works on the leading word
+      keys[i] = k2;
       perm[i] = (uint32_t)(S.out_row_base + local);
     }
     const bool sel = i < n && W.sel[qi].state == 1;
@@ -1680,7 +1694,7 @@ __device__ __forceinline__ bool sel_in_play(const SelState &s, uint64_t key) {
 // Digit histogram of the keys in play; a block's rows are nearly always
 // one query's, so counts gather in shared memory for the block's first
 // query and go to global memory directly for any other.
-__global__ void __launch_bounds__(256) k_sel_hist(Wave W, const uint64_t *keys) {
+__global__ void __launch_bounds__(256) k_sel_hist(Wave W, const SortKey *keys) {
   __shared__ uint32_t h[256];
   const uint64_t n = W.ctrl->len[6];
   const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
@@ -1692,7 +1706,7 @@ __global__ void __launch_bounds__(256) k_sel_hist(Wave W, const uint64_t *keys) 
     const uint32_t qi = seg_of_large(W.qs, W.nq, i, false);
     const SelState &s = W.sel[qi];
     if (s.state != 1) continue;
-    const uint64_t key = keys[i];
+    const uint64_t key = keys[i].hi;
     if (!sel_in_play(s, key)) continue;
     const uint32_t d = (uint32_t)(key >> s.shift) & ((1u << s.width) - 1);
     if (qi == q0) atomicAdd(&h[d], 1u);
@@ -1765,19 +1779,19 @@ __global__ void k_sel_pick(Wave W, int last) {
 // Rows of a cut query with key <= thresh, packed at the front of its range
 // (order does not matter: the sort follows); other rows are copied as they
 // are.  One atomic per warp and query.
-__global__ void k_sel_compact(Wave W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout) {
+__global__ void k_sel_compact(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout) {
   const uint64_t n = W.ctrl->len[6];
   const uint32_t lane = threadIdx.x & 31;
   for (uint64_t base = gtid() - lane; base < n; base += gthreads()) {
     const uint64_t i = base + lane;
     uint32_t qi = 0xFFFFFFFFu;
     bool cut = false, keep = false;
-    uint64_t key = 0;
+    SortKey key{0, 0};
     if (i < n) {
       qi = seg_of_large(W.qs, W.nq, i, false);
       key = kin[i];
       cut = W.sel[qi].state == 2;
-      keep = !cut || key <= W.sel[qi].thresh;
+      keep = !cut || key.hi <= W.sel[qi].thresh;
       if (!cut) {
         pout[i] = pin[i];
         kout[i] = key;
@@ -1837,9 +1851,9 @@ __global__ void __launch_bounds__(1024) k_sort_bases(Wave W) {
 
 // Tile sort: keys (and row indices) in shared memory, bitonic network; rows
 // are read from the output pool only to order equal keys.
-__global__ void __launch_bounds__(256) k_tile_sort(Wave W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout,
-                                                   uint64_t *kout) {
-  __shared__ uint64_t key[kTileRows];
+__global__ void __launch_bounds__(256) k_tile_sort(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout,
+                                                   SortKey *kout) {
+  __shared__ SortKey key[kTileRows];
   __shared__ uint32_t row[kTileRows];
   __shared__ uint32_t idx[kTileRows];
   const uint64_t ntiles = W.ctrl->len[7];
@@ -1864,7 +1878,7 @@ __global__ void __launch_bounds__(256) k_tile_sort(Wave W, const uint32_t *pin, 
       if (a >= n) return false;
       if (c >= n) return true;
       if (key[a] != key[c]) return key[a] < key[c];
-      return !out_row_le(W, Q, S, row[c], row[a]);
+      return !keys_exact(W, Q) && !out_row_le(W, Q, S, row[c], row[a]);
     };
     for (uint32_t size = 2; size <= np2; size <<= 1)
       for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
@@ -1918,7 +1932,7 @@ __device__ __forceinline__ MergeTile merge_tile(const Wave &W, uint64_t t, uint6
 // Merge-path split at diagonal o of runs A (va valid) and B (vb valid): how
 // many of the first o outputs come from A (stable: A wins ties).
 __device__ __forceinline__ uint64_t merge_split_at(const Wave &W, const DQuery &Q, const QState &S, const uint32_t *perm,
-                                                   const uint64_t *key, uint64_t A, uint64_t B, uint64_t va,
+                                                   const SortKey *key, uint64_t A, uint64_t B, uint64_t va,
                                                    uint64_t vb, uint64_t o) {
   uint64_t lo = o > vb ? o - vb : 0, hi = min(o, va);
   while (lo < hi) {
@@ -1929,7 +1943,7 @@ __device__ __forceinline__ uint64_t merge_split_at(const Wave &W, const DQuery &
 }
 
 // Split of every active output tile at its first output.  One thread per tile.
-__global__ void k_merge_split(Wave W, const uint32_t *perm, const uint64_t *key, uint64_t run) {
+__global__ void k_merge_split(Wave W, const uint32_t *perm, const SortKey *key, uint64_t run) {
   const uint64_t ntiles = W.ctrl->len[7];
   for (uint64_t t = gtid(); t < ntiles; t += gthreads()) {
     const MergeTile m = merge_tile(W, t, run);
@@ -1949,9 +1963,9 @@ __global__ void k_merge_split(Wave W, const uint32_t *perm, const uint64_t *key,
 // by the splits at its first and last output) are staged in shared memory
 // with their keys; each thread places four outputs after a short search in
 // the slices.
-__global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout,
-                                                     uint64_t *kout, uint64_t run) {
-  __shared__ uint64_t sk[kTileRows];
+__global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout,
+                                                     SortKey *kout, uint64_t run) {
+  __shared__ SortKey sk[kTileRows];
   __shared__ uint32_t si[kTileRows];
   __shared__ uint64_t s_end;
   const uint64_t ntiles = W.ctrl->len[7];
@@ -2039,14 +2053,14 @@ __global__ void k_gather(Wave W, const uint32_t *perm0, const uint32_t *perm1) {
 // kernel counts the starts; a scan of the counts gives each tile's first
 // rank; a second kernel writes every start whose rank is below cap.
 __device__ __forceinline__ bool proj_start(const Wave &W, const DQuery &Q, const QState &S, const uint32_t *perm,
-                                           const uint64_t *key, uint64_t i) {
+                                           const SortKey *key, uint64_t i) {
   if (i == 0) return true;
   const uint64_t a = S.lrg_row_base + i;
-  return key[a] != key[a - 1] || !out_row_eq(W, Q, S, perm[a], perm[a - 1]);
+  return key[a] != key[a - 1] || (!keys_exact(W, Q) && !out_row_eq(W, Q, S, perm[a], perm[a - 1]));
 }
 
 __global__ void __launch_bounds__(256) k_proj_count(Wave W, const uint32_t *perm0, const uint32_t *perm1,
-                                                    const uint64_t *key0, const uint64_t *key1) {
+                                                    const SortKey *key0, const SortKey *key1) {
   __shared__ uint32_t wsum[8];
   const uint64_t ntiles = W.ctrl->len[7];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -2074,7 +2088,7 @@ __global__ void __launch_bounds__(256) k_proj_count(Wave W, const uint32_t *perm
 }
 
 __global__ void __launch_bounds__(256) k_proj_write(Wave W, const uint32_t *perm0, const uint32_t *perm1,
-                                                    const uint64_t *key0, const uint64_t *key1) {
+                                                    const SortKey *key0, const SortKey *key1) {
   __shared__ uint32_t rk[kTileRows];
   const uint64_t ntiles = W.ctrl->len[7];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -2084,7 +2098,7 @@ __global__ void __launch_bounds__(256) k_proj_write(Wave W, const uint32_t *perm
     if (!Q.proj) continue;  // block-uniform
     const bool odd = merge_passes(S.sort_rows) & 1;
     const uint32_t *perm = odd ? perm1 : perm0;
-    const uint64_t *key = odd ? key1 : key0;
+    const SortKey *key = odd ? key1 : key0;
     const uint64_t first = (t - S.lrg_tile_base) * kTileRows;
     const uint32_t n = (uint32_t)min((uint64_t)kTileRows, S.sort_rows - first);
     for (uint32_t i = threadIdx.x; i < kTileRows; i += blockDim.x) rk[i] = i < n && proj_start(W, Q, S, perm, key, first + i);
@@ -2260,10 +2274,10 @@ void launch_small_sort(const Wave &W, cudaStream_t s, int sms) {
   const unsigned cap = persistent_grid(k_small_sort, sms, 256);
   k_small_sort<<<W.nq < cap ? (W.nq ? W.nq : 1) : cap, 256, 0, s>>>(W);
 }
-void launch_sort_keys(const Wave &W, uint32_t *perm, uint64_t *keys, cudaStream_t s, int sms) {
+void launch_sort_keys(const Wave &W, uint32_t *perm, SortKey *keys, cudaStream_t s, int sms) {
   k_sort_keys<<<persistent_grid(k_sort_keys, sms), kThreads, 0, s>>>(W, perm, keys);
 }
-void launch_select(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+void launch_select(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                    cudaStream_t s, int sms) {
   k_sel_start<<<blocks_for(W.nq, 256), 256, 0, s>>>(W);
   for (int r = 0; r < kSelRounds; ++r) {
@@ -2273,11 +2287,11 @@ void launch_select(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint
   k_sel_compact<<<persistent_grid(k_sel_compact, sms), kThreads, 0, s>>>(W, pin, kin, pout, kout);
   k_sort_bases<<<1, 1024, 0, s>>>(W);
 }
-void launch_tile_sort(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+void launch_tile_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                       cudaStream_t s, int sms) {
   k_tile_sort<<<persistent_grid(k_tile_sort, sms, 256), 256, 0, s>>>(W, pin, kin, pout, kout);
 }
-void launch_merge_pass(const Wave &W, const uint32_t *pin, const uint64_t *kin, uint32_t *pout, uint64_t *kout,
+void launch_merge_pass(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                        uint64_t run, cudaStream_t s, int sms) {
   k_merge_split<<<persistent_grid(k_merge_split, sms), kThreads, 0, s>>>(W, pin, kin, run);
   k_merge_tiles<<<persistent_grid(k_merge_tiles, sms, 256), 256, 0, s>>>(W, pin, kin, pout, kout, run);
@@ -2286,8 +2300,8 @@ void launch_gather(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, 
   k_gather<<<persistent_grid(k_gather, sms), kThreads, 0, s>>>(W, perm0, perm1);
 }
 
-void launch_project(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, const uint64_t *key0,
-                    const uint64_t *key1, uint64_t max_tiles, uint64_t *scan_tmp, cudaStream_t s, int sms) {
+void launch_project(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, const SortKey *key0,
+                    const SortKey *key1, uint64_t max_tiles, uint64_t *scan_tmp, cudaStream_t s, int sms) {
   const unsigned grid = (unsigned)std::min<uint64_t>(std::max<uint64_t>(max_tiles, 1), (uint64_t)sms * 8);
   k_proj_count<<<grid, 256, 0, s>>>(W, perm0, perm1, key0, key1);
   scan_u32(W.ptcount, W.ptscan, &W.ctrl->len[7], max_tiles, scan_tmp, s, sms);
