@@ -288,19 +288,16 @@ __global__ void k_plan(Wave W, const uint32_t *type_count) {
     }
     Q.nvisit = nv;
     atomicMax(&W.ctrl->max_nvisit, nv);
-    // reversed refinement order: vertices by the step that gave them a
-    // candidate set, last first (ties: higher index first)
-    for (uint32_t j = 0; j < k; ++j) {
-      int pick = -1;
+    // reversed refinement order (only when asked for): vertices by the step
+    // that gave them a candidate set, last first (ties: higher index first);
+    // u's position is the number of vertices that come before it
+    if (Q.refine_flags & kRefineRev)
       for (uint32_t u = 0; u < k; ++u) {
-        bool taken = false;
-        for (uint32_t i = 0; i < j; ++i) taken = taken || Q.rorder[i] == u;
-        if (taken) continue;
-        if (pick < 0 || Q.init_step[u] > Q.init_step[pick] || (Q.init_step[u] == Q.init_step[pick] && u > (uint32_t)pick))
-          pick = (int)u;
+        uint32_t before = 0;
+        for (uint32_t w = 0; w < k; ++w)
+          before += Q.init_step[w] > Q.init_step[u] || (Q.init_step[w] == Q.init_step[u] && w > u);
+        Q.rorder[before] = (uint8_t)u;
       }
-      Q.rorder[j] = (uint8_t)pick;
-    }
     // every incident edge of every query vertex, packed for exploration and
     // refinement: direction, relation, other endpoint and, for a vertex that
     // is explored (leaves of the spanning tree are not), the endpoint's role
