@@ -43,7 +43,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
     pairs = [("gs_graph_desc", gs.GraphDesc), ("gs_query", gs.QueryDesc), ("gs_match_opts", gs.MatchOpts),
-             ("gs_result", gs.ResultDesc), ("gs_serve_opts", gs.ServeOpts)]
+             ("gs_result", gs.ResultDesc), ("gs_serve_opts", gs.ServeOpts), ("gs_khop_opts", gs.KhopOpts)]
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gs.h"', "int main(void) {"]
     for cname, py in pairs:
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -60,3 +60,24 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[f"{cname} size"]) == ctypes.sizeof(py), cname
         for f in py._fields_:
             assert int(got[f"{cname} {f[0]}"]) == getattr(py, f[0]).offset, (cname, f[0])
+
+
+def test_binding_helpers():
+    """Host-side marshalling of the binding: projection masks, refinement
+    flags, the query pack (same flat arrays as a plain concatenation) and the
+    lazy per-query row views of a batch result."""
+    import numpy as np
+    from paper_1807_08804_gb300 import inputs as I
+    assert gs.project_mask(None) == 0 and gs.project_mask([0, 2]) == 5 and gs.project_mask(6) == 6
+    assert gs.GS_REFINE_LOW(1) == 1 << 8 and gs.GS_REFINE_LOW(300) == (300 & 0xFF) << 8
+    g = I.make_graph(2000, 12000, seed=5)
+    qs = I.make_walk_queries(g, 40, 3, 7, seed=6)
+    pack = gs._QueryPack(qs)
+    for i, f in enumerate(("vtype", "vbind", "esrc", "edst", "erel")):
+        want = np.concatenate([np.asarray(getattr(q, f), np.uint32) for q in qs] + [np.zeros(1, np.uint32)])
+        np.testing.assert_array_equal(pack.flat[i], want)
+    assert [int(d["k"]) for d in pack.desc] == [q.k for q in qs]
+    big = np.arange(30, dtype=np.uint32)
+    r = gs.MatchResult._view(4, 9, big, 6, 18, 4, 3, True, 0)
+    np.testing.assert_array_equal(r.rows, big[6:18].reshape(4, 3))
+    assert r.count == 4 and r.truncated and "count=4" in repr(r)
