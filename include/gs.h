@@ -99,7 +99,11 @@ uint64_t gs_graph_num_edges(const gs_graph *g);
  * (GS_KHOP_OUT) and/or backwards (GS_KHOP_IN) over the listed relations.
  * counts[l] = vertices at level l (host array of levels + 1); edges_scanned
  * (may be NULL) = adjacency entries read.  Errors: levels > 254, directions
- * 0 or unknown, a relation or a seed out of range -> GS_ERR_INVALID.
+ * 0 or unknown, a relation or a seed out of range -> GS_ERR_INVALID.  Host
+ * seeds are checked before any work; device seeds (GS_DEVICE_PTRS) are
+ * checked on the device, so on that error the device level_out may already
+ * have been written (counts and edges_scanned are not).  Calls on one graph
+ * are serialised.
  */
 #define GS_KHOP_OUT 1u
 #define GS_KHOP_IN 2u
