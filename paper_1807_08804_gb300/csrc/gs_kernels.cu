@@ -1405,10 +1405,12 @@ __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
 
 // ============================================================ sort + gather
 // Large outputs (more than the one-block limit) are sorted as a merge sort
-// of (key, row index) pairs.  The key packs the row's leading columns in
-// query-vertex order at the graph's id width (the first column in the top
-// bits; the column that does not fit whole contributes its top bits), so key
-// order is row order on those bits and only equal keys compare full rows.
+// of (key, row index) pairs.  The key packs the row's output columns in
+// query-vertex order at the graph's id width into two words: the first
+// holds the leading columns (the first column in the top bits; the column
+// that does not fit whole contributes its top bits), the second the columns
+// from that one on.  Key order is row order on those bits, and only equal
+// keys compare full rows (never when the two words hold every column).
 // Each block first sorts one tile of kTileRows rows of one query in shared
 // memory (bitonic network); merge passes then double the sorted runs within
 // each query, one partition kernel placing every output tile's split and one
@@ -1520,9 +1522,9 @@ __device__ __forceinline__ uint32_t block_scan_excl(uint32_t *v, uint32_t n) {
   return tot;
 }
 
-// One block sorts one query's rows: packed 64-bit keys of the rows (see the
-// large-output sort below) and row indices in shared memory, bitonic
-// network, full rows compared on equal keys only; then the first `cap` rows
+// One block sorts one query's rows: the two-word packed keys of the rows
+// (see the large-output sort below) and row indices in shared memory,
+// bitonic network, full rows compared on equal keys only; then the first `cap` rows
 // are written in query-vertex column order.  A projected query keeps only
 // the first row of each run of equal projected tuples (its rank among the
 // runs from a block scan) and writes the first `cap` of them.
