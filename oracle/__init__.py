@@ -44,6 +44,8 @@ def _load():
         lib.orc_graph_free.argtypes = [P]
         lib.orc_graph_num_edges.restype = U64
         lib.orc_graph_num_edges.argtypes = [P]
+        lib.orc_mix64.restype = U64
+        lib.orc_mix64.argtypes = [U64]
         lib.orc_row_hash.restype = U64
         lib.orc_row_hash.argtypes = [U32, P]
         lib.orc_fingerprint.restype = U64
@@ -242,6 +244,11 @@ def row_hash(row) -> int:
     lib = _load()
     r = _u32(row)
     return int(lib.orc_row_hash(r.shape[0], _p(r)))
+
+
+def mix64(z: int) -> int:
+    """The splitmix64 finaliser the row hash is built from."""
+    return int(_load().orc_mix64(z & 0xFFFFFFFFFFFFFFFF))
 
 
 def fingerprint(rows: np.ndarray) -> int:

@@ -194,8 +194,11 @@ static int orc_unary_ok(const orc_graph *g, const orc_query *q, uint32_t u, uint
 }
 
 /* ----------------------------------------------------------- fingerprint */
-/* splitmix64 finaliser (Steele, Lea & Flood 2014). */
-static uint64_t orc_mix64(uint64_t z) {
+/* splitmix64 finaliser (Steele, Lea & Flood 2014): the output function of
+ * the splitmix64 generator, whose n-th output from seed s is
+ * orc_mix64(s + n * 0x9E3779B97F4A7C15).  Exported so that the tests can pin
+ * it to that generator's published outputs. */
+uint64_t orc_mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);

@@ -1,6 +1,7 @@
 """Pins for the CPU oracle: each check comes from somewhere other than the
 oracle's own code (brute force, closed-form counts, homomorphism projections,
 the thesis's worked example, planted mistakes)."""
+import os
 from math import comb, perm
 
 import numpy as np
@@ -527,3 +528,87 @@ def test_duplicate_query_edges_and_shared_binding():
     b = O.match(o, query(3, [(0, 1, 0), (1, 2, 0), (0, 1, 0)]), cap=0).count
     assert a == b == perm(5, 3)
     assert O.match(o, query(2, [(0, 1, 0)], vbind=[2, 2]), cap=0).count == 0  # injectivity
+
+
+# ----------------------------------------------------------- fingerprint
+GOLDEN_RATIO_64 = 0x9E3779B97F4A7C15
+M64 = (1 << 64) - 1
+
+
+def _splitmix64_golden():
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64.txt")
+    seed, outs = None, []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("seed"):
+            seed = int(line.split()[1])
+        else:
+            outs.append(int(line))
+    return seed, outs
+
+
+def test_mix64_equals_published_splitmix64_outputs():
+    """The finaliser under the fingerprint is splitmix64's output function:
+    its values at seed + n * golden ratio are the generator's published first
+    outputs.  A wrong shift or multiplier constant fails here."""
+    seed, outs = _splitmix64_golden()
+    assert len(outs) == 5
+    for n, want in enumerate(outs, start=1):
+        assert O.mix64((seed + n * GOLDEN_RATIO_64) & M64) == want
+
+
+def test_row_hash_is_the_stated_fold_of_the_pinned_finaliser():
+    """h(f) starts at k and folds f(0..k-1) in column order, each step
+    h <- mix64(h xor (f(i) + (i+1) * golden ratio)), with mix64 the finaliser
+    pinned above."""
+    rng = np.random.default_rng(77)
+    for _ in range(200):
+        k = int(rng.integers(1, 13))
+        row = rng.integers(0, 1 << 32, size=k, dtype=np.uint64).astype(np.uint32)
+        h = k
+        for i, v in enumerate(row.tolist()):
+            h = O.mix64(h ^ ((v + (i + 1) * GOLDEN_RATIO_64) & M64))
+        assert O.row_hash(row) == h
+
+
+def test_row_hash_depends_on_column_position_and_width():
+    """Swapping two different columns, or appending a column, changes the
+    hash: an embedding is a map of query vertices, not a set of data ids."""
+    rng = np.random.default_rng(78)
+    for _ in range(500):
+        k = int(rng.integers(2, 13))
+        row = rng.choice(1 << 24, size=k, replace=False).astype(np.uint32)
+        i, j = rng.choice(k, size=2, replace=False)
+        sw = row.copy()
+        sw[[i, j]] = sw[[j, i]]
+        assert O.row_hash(sw) != O.row_hash(row)
+        assert O.row_hash(np.append(row, np.uint32(0))) != O.row_hash(row)
+        assert O.row_hash(row[:-1]) != O.row_hash(row)
+
+
+def test_fingerprint_sums_row_hashes_mod_2_64():
+    rng = np.random.default_rng(79)
+    for _ in range(50):
+        n, k = int(rng.integers(1, 200)), int(rng.integers(1, 9))
+        rows = rng.integers(0, 1 << 32, size=(n, k), dtype=np.uint64).astype(np.uint32)
+        assert O.fingerprint(rows) == sum(O.row_hash(r) for r in rows) & M64
+
+
+@pytest.mark.parametrize("threads", [1, 0])
+def test_match_many_equals_match_per_query(threads):
+    """The batched oracle entry (used by the large parity tests and the CPU
+    baseline) gives per query exactly what orc_match gives: same status,
+    count and fingerprint, on one thread and on every host thread."""
+    from paper_1807_08804_gb300 import inputs as I
+    g = I.make_graph(10_000, 60_000, seed=0x6753001)
+    qs = I.make_walk_queries(g, 120, 3, 6, p_bind=0.2, seed=5) + I.make_walk_queries(g, 80, 3, 8, p_bind=0.0,
+                                                                                      seed=6)
+    o = og(g)
+    cnt, fp, st, used = O.match_many(o, qs, threads=threads)
+    assert used >= 1 and (threads == 0 or used == threads)
+    assert sum(int(c) > 0 for c in cnt) == len(qs)  # every walked query matches itself
+    for i, q in enumerate(qs):
+        r = O.match(o, q, cap=0)
+        assert (int(st[i]), int(cnt[i]), int(fp[i])) == (r.status, r.count, r.fingerprint), i
