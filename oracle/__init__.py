@@ -66,6 +66,21 @@ def _load():
         lib.orc_edge_table.argtypes = [P, U32, U32, P, P, P, P, U32, I, P, P, P, P, P]
         lib.orc_khop.restype = I
         lib.orc_khop.argtypes = [P, P, U32, U32, U32, P, P, P]
+        lib.orc_compress.restype = P
+        lib.orc_compress.argtypes = [P, U32, P]
+        lib.orc_wgraph_free.argtypes = [P]
+        lib.orc_wgraph_nodes.restype = U32
+        lib.orc_wgraph_nodes.argtypes = [P]
+        lib.orc_wgraph_edges.restype = U64
+        lib.orc_wgraph_edges.argtypes = [P]
+        lib.orc_wgraph_get.restype = None
+        lib.orc_wgraph_get.argtypes = [P] + [P] * 10
+        lib.orc_wcandidates.restype = I
+        lib.orc_wcandidates.argtypes = [P, U32, U32, P, P, P, P, P, P]
+        lib.orc_wrefine.restype = I
+        lib.orc_wrefine.argtypes = [P, U32, U32, P, P, P, P]
+        lib.orc_match_compressed.restype = I
+        lib.orc_match_compressed.argtypes = [P, P, U32, U32, P, P, P, P, P, U64, P, P, P, P, P]
         lib.orc_verify.restype = ctypes.c_int64
         lib.orc_verify.argtypes = [P, U32, U32, P, P, P, P, P, P, U64]
         _lib = lib
@@ -279,3 +294,75 @@ def khop(g: OracleGraph, seeds, levels: int, dirs: int = 3, rels=None):
     cnt = np.zeros(levels + 1, np.uint64)
     st = lib.orc_khop(g._h, _p(s), s.shape[0], levels, dirs, _p(relmask(rels)), _p(lv), _p(cnt))
     return st, lv, cnt
+
+
+class WeightedGraph:
+    """The oracle's multi-level compression of a graph (Section 3.4): the
+    weighted graph, its mapping lists and its weights, as numpy arrays."""
+
+    def __init__(self, g: OracleGraph, deltas):
+        lib = _load()
+        d = np.ascontiguousarray(np.asarray(list(deltas), np.float64))
+        self.g = g
+        self.levels = d.shape[0]
+        self._h = lib.orc_compress(g._h, self.levels, _p(d) if self.levels else None)
+        self.n = int(lib.orc_wgraph_nodes(self._h))
+        self.ne = int(lib.orc_wgraph_edges(self._h))
+        V, n, ne, R = g.V, self.n, self.ne, g.R
+        self.group = np.zeros(V, np.uint32)
+        self.moff = np.zeros(n + 1, np.uint32)
+        self.mem = np.zeros(V, np.uint32)
+        self.type = np.zeros(max(n, 1), np.uint32)
+        self.src, self.rel, self.dst = (np.zeros(max(ne, 1), np.uint32) for _ in range(3))
+        self.wout, self.win = np.zeros(max(ne, 1), np.uint32), np.zeros(max(ne, 1), np.uint32)
+        self.wnode = np.zeros(max(2 * R * n, 1), np.uint32)
+        lib.orc_wgraph_get(self._h, _p(self.group), _p(self.moff), _p(self.mem), _p(self.type), _p(self.src),
+                           _p(self.rel), _p(self.dst), _p(self.wout), _p(self.win), _p(self.wnode))
+        self.type, self.src, self.rel, self.dst = self.type[:n], self.src[:ne], self.rel[:ne], self.dst[:ne]
+        self.wout, self.win = self.wout[:ne], self.win[:ne]
+        self.wnode = self.wnode[: 2 * R * n].reshape(2, R, n)
+
+    def ratio(self) -> float:
+        """(nodes + edges) of the weighted graph over (vertices + edges) of the
+        data graph; an edge inside a node counts once per relation."""
+        inner = int((self.wnode[0] > 0).sum())
+        return (self.n + self.ne + inner) / (self.g.V + self.g.E)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.orc_wgraph_free(self._h)
+            self._h = None
+
+
+def wcandidates(w: WeightedGraph, q) -> np.ndarray:
+    """Definition 3.5 on the weighted graph: bool [k, n]."""
+    lib = _load()
+    vt, vb, es, ed, er = _q(q)
+    out = np.zeros((vt.shape[0], max(w.n, 1)), np.uint8)
+    if lib.orc_wcandidates(w._h, vt.shape[0], es.shape[0], _p(vt), _p(vb), _p(es), _p(ed), _p(er), _p(out)):
+        raise ValueError("invalid query")
+    return out[:, : w.n].astype(bool)
+
+
+def wrefine(w: WeightedGraph, q, sets: np.ndarray) -> np.ndarray:
+    """The refinement rule on the weighted graph, to its fixpoint."""
+    lib = _load()
+    es, ed, er = _u32(q.esrc), _u32(q.edst), _u32(q.erel)
+    s = np.ascontiguousarray(sets.astype(np.uint8))
+    if lib.orc_wrefine(w._h, s.shape[0], es.shape[0], _p(es), _p(ed), _p(er), _p(s)) < 0:
+        raise ValueError("invalid query")
+    return s.astype(bool)
+
+
+def match_compressed(g: OracleGraph, w: WeightedGraph, q, cap: int = 1 << 20):
+    """Embeddings found through the weighted graph and the mapping lists:
+    (Result, number of weighted-graph solutions)."""
+    lib = _load()
+    vt, vb, es, ed, er = _q(q)
+    k = vt.shape[0]
+    cnt, fp, nr, homs = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    rows = np.zeros((max(cap, 1), k), np.uint32)
+    st = lib.orc_match_compressed(g._h, w._h, k, es.shape[0], _p(vt), _p(vb), _p(es), _p(ed), _p(er), cap,
+                                  ctypes.byref(cnt), ctypes.byref(fp), _p(rows) if cap else None, ctypes.byref(nr),
+                                  ctypes.byref(homs))
+    return Result(st, cnt.value, fp.value, rows[: nr.value].copy()), homs.value

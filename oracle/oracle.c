@@ -644,3 +644,471 @@ int orc_khop(const orc_graph *g, const uint32_t *seeds, uint32_t nseeds, uint32_
   free(queue);
   return 0;
 }
+
+/* ================================================ multi-level compression
+ * Section 3.4 ("Multi-level Graph Compression") and Section 3.5 (matching on
+ * the weighted graph, then expanding through the mapping lists), read for
+ * directed graphs whose edges carry relations and whose vertices carry types.
+ *
+ * Weighted graph G_i (Definition 3.4): its nodes are groups of data vertices
+ * (the mapping list M(x) of node x); there is an edge (x, r, y), x != y,
+ * when some a in M(x), b in M(y) have (a, r, b) in E.  Edges inside one
+ * group are not edges of G_i: the node weight accounts for them.
+ *
+ * Weights, per direction d (0 = out, 1 = in) and relation r:
+ *   - node weight w_{d,r}(x) = max over a in M(x) of the number of distinct
+ *     d-neighbours of a over r that lie in M(x) (the thesis's "maximum degree
+ *     among nodes in the graph constructed by" the merged lists, per plane);
+ *   - edge weights start at 1 on every data edge and, when the nodes p, q of
+ *     a level merge into u and n, m into v, become the thesis's
+ *     w(u, v) = max(w(p, n), w(q, n)) + max(w(p, m), w(q, m)) (a missing
+ *     edge weighs 0, an unmerged node is its own only part).  wout(x, r, y)
+ *     bounds the r-out-neighbours in M(y) of any a in M(x); win(x, r, y), the
+ *     same recursion with the roles of the two ends swapped, bounds the
+ *     r-in-neighbours in M(x) of any b in M(y).
+ *
+ * Similar nodes (garbled in the thesis: its test max(|adj(u)| / |common|,
+ * |adj(v)| / |common|) >= delta always holds for 0 < delta <= 1).  Reading:
+ * x and y have the same type and common(x, y) makes up at least delta of
+ * each adjacency, |common| >= delta * |adj(x)| and |common| >= delta *
+ * |adj(y)|, where adj(x) = the (direction, relation, neighbour node) triples
+ * of x's edges in G_i and common(x, y) = adj(x) intersected with adj(y)
+ * (Section 3.4: an edge to/from v with the same label from both); with
+ * delta = 1 similar nodes have the same adjacency list, as in the thesis's
+ * example.  Two nodes without edges are similar; one without edges is
+ * similar to no node with edges.  The comparisons are the double-precision
+ * products (double)|common| >= delta * (double)|adj|.
+ *
+ * Each level combines pairs of similar nodes (Section 3.4: a weighted node of
+ * G_i is a combination of two nodes of G_{i-1}): nodes are visited in
+ * ascending index order, and a node not yet paired is paired with the
+ * lowest-indexed later node that is not paired and is similar to it.  The
+ * nodes of G_i are numbered by ascending smallest member (level 0: node v =
+ * vertex v).
+ * ====================================================================== */
+typedef struct {
+  uint32_t V, T, R, n;  /* data vertices, types, relations, weighted nodes */
+  uint32_t *group;      /* [V] node whose mapping list holds v */
+  uint32_t *moff;       /* [n+1] mapping lists: mem[moff[x] .. moff[x+1]), ascending */
+  uint32_t *mem;        /* [V] */
+  uint32_t *type;       /* [n] */
+  uint64_t ne;          /* edges between different nodes */
+  orc_triple *e;        /* [ne] sorted by (src, rel, dst) */
+  uint32_t *wout, *win; /* [ne] */
+  uint32_t *wnode;      /* [(d * R + r) * n + x] node weight per direction and relation */
+} orc_wgraph;
+
+typedef struct { uint32_t src, rel, dst, wout, win; } orc_wedge;
+
+static int cmp_wedge(const void *a, const void *b) { return cmp_src(a, b); }
+
+typedef struct { uint32_t node; uint64_t key; } orc_adjkey;
+static int cmp_adjkey(const void *a, const void *b) {
+  const orc_adjkey *x = (const orc_adjkey *)a, *y = (const orc_adjkey *)b;
+  if (x->node != y->node) return x->node < y->node ? -1 : 1;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return 0;
+}
+
+/* One compression level: pair similar nodes of the weighted graph
+ * (n nodes, edges e[ne] with weights, node types) and write the merged
+ * level.  newidx[x] = x's node at the next level.  Returns the new node
+ * count. */
+static uint32_t orc_level_pairs(uint32_t n, const uint32_t *type, const orc_wedge *e, uint64_t ne, double delta,
+                                uint32_t *newidx) {
+  /* adjacency lists: (out, r, y) for x -> y and (in, r, x) for x -> y at y */
+  orc_adjkey *ak = (orc_adjkey *)malloc(sizeof(orc_adjkey) * (2 * ne + 1));
+  for (uint64_t i = 0; i < ne; ++i) {
+    ak[2 * i].node = e[i].src;
+    ak[2 * i].key = ((uint64_t)0 << 40) | ((uint64_t)e[i].rel << 32) | e[i].dst;
+    ak[2 * i + 1].node = e[i].dst;
+    ak[2 * i + 1].key = ((uint64_t)1 << 40) | ((uint64_t)e[i].rel << 32) | e[i].src;
+  }
+  qsort(ak, 2 * ne, sizeof(orc_adjkey), cmp_adjkey);
+  uint64_t *aoff = (uint64_t *)calloc(n + 1, sizeof(uint64_t));
+  for (uint64_t i = 0; i < 2 * ne; ++i) aoff[ak[i].node + 1]++;
+  for (uint32_t x = 0; x < n; ++x) aoff[x + 1] += aoff[x];
+  int64_t *partner = (int64_t *)malloc(sizeof(int64_t) * (n ? n : 1));
+  for (uint32_t x = 0; x < n; ++x) partner[x] = -1;
+  for (uint32_t x = 0; x < n; ++x) {
+    if (partner[x] >= 0) continue;
+    for (uint32_t y = x + 1; y < n; ++y) {
+      if (partner[y] >= 0 || type[y] != type[x]) continue;
+      const uint64_t a = aoff[x + 1] - aoff[x], b = aoff[y + 1] - aoff[y];
+      int similar;
+      if (a == 0 || b == 0) {
+        similar = a == 0 && b == 0;
+      } else {
+        uint64_t c = 0, i = aoff[x], j = aoff[y];
+        while (i < aoff[x + 1] && j < aoff[y + 1]) {
+          if (ak[i].key == ak[j].key) { c++; i++; j++; }
+          else if (ak[i].key < ak[j].key) i++;
+          else j++;
+        }
+        similar = (double)c >= delta * (double)a && (double)c >= delta * (double)b;
+      }
+      if (similar) { partner[x] = y; partner[y] = x; break; }
+    }
+  }
+  uint32_t cnt = 0;
+  for (uint32_t x = 0; x < n; ++x) {
+    if (partner[x] >= 0 && (uint32_t)partner[x] < x) continue;  /* numbered with its lower partner */
+    newidx[x] = cnt;
+    if (partner[x] >= 0) newidx[partner[x]] = cnt;
+    cnt++;
+  }
+  free(ak); free(aoff); free(partner);
+  return cnt;
+}
+
+/* Edges of the merged level with the thesis's weight recursion.  Old edge
+ * (A, r, B) -> new edge (U, r, V) with U = newidx[A], V = newidx[B]; U == V
+ * (an edge inside a merged node) is dropped.  wout(U, r, V) = sum over the
+ * parts B of V of the max over the parts A of U of wout(A, r, B); win(U, r, V)
+ * = sum over the parts A of U of the max over the parts B of V of
+ * win(A, r, B). */
+typedef struct { uint32_t u, rel, v, a, b, wout, win; } orc_lift;
+static int cmp_lift_b(const void *p, const void *q) {  /* (u, rel, v, b) */
+  const orc_lift *x = (const orc_lift *)p, *y = (const orc_lift *)q;
+  if (x->u != y->u) return x->u < y->u ? -1 : 1;
+  if (x->rel != y->rel) return x->rel < y->rel ? -1 : 1;
+  if (x->v != y->v) return x->v < y->v ? -1 : 1;
+  if (x->b != y->b) return x->b < y->b ? -1 : 1;
+  return 0;
+}
+static int cmp_lift_a(const void *p, const void *q) {  /* (u, rel, v, a) */
+  const orc_lift *x = (const orc_lift *)p, *y = (const orc_lift *)q;
+  if (x->u != y->u) return x->u < y->u ? -1 : 1;
+  if (x->rel != y->rel) return x->rel < y->rel ? -1 : 1;
+  if (x->v != y->v) return x->v < y->v ? -1 : 1;
+  if (x->a != y->a) return x->a < y->a ? -1 : 1;
+  return 0;
+}
+static orc_wedge *orc_level_edges(const orc_wedge *e, uint64_t ne, const uint32_t *newidx, uint64_t *ne_out) {
+  orc_lift *l = (orc_lift *)malloc(sizeof(orc_lift) * (ne ? ne : 1));
+  uint64_t nl = 0;
+  for (uint64_t i = 0; i < ne; ++i) {
+    const uint32_t u = newidx[e[i].src], v = newidx[e[i].dst];
+    if (u == v) continue;
+    l[nl].u = u; l[nl].rel = e[i].rel; l[nl].v = v; l[nl].a = e[i].src; l[nl].b = e[i].dst;
+    l[nl].wout = e[i].wout; l[nl].win = e[i].win; nl++;
+  }
+  orc_wedge *out = (orc_wedge *)malloc(sizeof(orc_wedge) * (nl ? nl : 1));
+  uint64_t no = 0;
+  /* wout: per (u, rel, v, b) the max over a, summed over b */
+  qsort(l, nl, sizeof(orc_lift), cmp_lift_b);
+  for (uint64_t i = 0; i < nl;) {
+    uint64_t j = i;
+    uint32_t sum = 0;
+    while (j < nl && l[j].u == l[i].u && l[j].rel == l[i].rel && l[j].v == l[i].v) {
+      uint32_t mx = 0;
+      const uint32_t b = l[j].b;
+      while (j < nl && l[j].u == l[i].u && l[j].rel == l[i].rel && l[j].v == l[i].v && l[j].b == b) {
+        if (l[j].wout > mx) mx = l[j].wout;
+        j++;
+      }
+      sum += mx;
+    }
+    out[no].src = l[i].u; out[no].rel = l[i].rel; out[no].dst = l[i].v; out[no].wout = sum; out[no].win = 0; no++;
+    i = j;
+  }
+  /* win: per (u, rel, v, a) the max over b, summed over a (same edge order) */
+  qsort(l, nl, sizeof(orc_lift), cmp_lift_a);
+  uint64_t k = 0;
+  for (uint64_t i = 0; i < nl;) {
+    uint64_t j = i;
+    uint32_t sum = 0;
+    while (j < nl && l[j].u == l[i].u && l[j].rel == l[i].rel && l[j].v == l[i].v) {
+      uint32_t mx = 0;
+      const uint32_t a = l[j].a;
+      while (j < nl && l[j].u == l[i].u && l[j].rel == l[i].rel && l[j].v == l[i].v && l[j].a == a) {
+        if (l[j].win > mx) mx = l[j].win;
+        j++;
+      }
+      sum += mx;
+    }
+    out[k++].win = sum;  /* both passes visit the (u, rel, v) groups in the same order */
+    i = j;
+  }
+  free(l);
+  *ne_out = no;
+  return out;
+}
+
+void orc_wgraph_free(orc_wgraph *w) {
+  if (!w) return;
+  free(w->group); free(w->moff); free(w->mem); free(w->type); free(w->e); free(w->wout); free(w->win);
+  free(w->wnode); free(w);
+}
+
+/*
+ * orc_compress: `levels` levels of compression of g with thresholds
+ * delta[0..levels).  Returns the final weighted graph (levels = 0: g itself
+ * with unit weights).
+ */
+orc_wgraph *orc_compress(const orc_graph *g, uint32_t levels, const double *delta) {
+  const uint32_t V = g->V, R = g->R;
+  uint32_t n = V;
+  uint32_t *group = (uint32_t *)malloc(sizeof(uint32_t) * (V ? V : 1));
+  uint32_t *type = (uint32_t *)malloc(sizeof(uint32_t) * (V ? V : 1));
+  for (uint32_t v = 0; v < V; ++v) { group[v] = v; type[v] = g->vtype[v]; }
+  /* level 0: the data edges between different vertices, weight 1 */
+  orc_wedge *e = (orc_wedge *)malloc(sizeof(orc_wedge) * (g->E ? g->E : 1));
+  uint64_t ne = 0;
+  for (uint64_t i = 0; i < g->E; ++i) {
+    if (g->by_src[i].src == g->by_src[i].dst) continue;
+    e[ne].src = g->by_src[i].src; e[ne].rel = g->by_src[i].rel; e[ne].dst = g->by_src[i].dst;
+    e[ne].wout = 1; e[ne].win = 1; ne++;
+  }
+  uint32_t *newidx = (uint32_t *)malloc(sizeof(uint32_t) * (V ? V : 1));
+  for (uint32_t lv = 0; lv < levels; ++lv) {
+    const uint32_t n2 = orc_level_pairs(n, type, e, ne, delta[lv], newidx);
+    uint64_t ne2 = 0;
+    orc_wedge *e2 = orc_level_edges(e, ne, newidx, &ne2);
+    uint32_t *type2 = (uint32_t *)malloc(sizeof(uint32_t) * (n2 ? n2 : 1));
+    for (uint32_t x = 0; x < n; ++x) type2[newidx[x]] = type[x];
+    for (uint32_t v = 0; v < V; ++v) group[v] = newidx[group[v]];
+    free(e); free(type);
+    e = e2; ne = ne2; type = type2; n = n2;
+  }
+  free(newidx);
+  orc_wgraph *w = (orc_wgraph *)calloc(1, sizeof(orc_wgraph));
+  w->V = V; w->T = g->T; w->R = R; w->n = n; w->group = group; w->type = type;
+  /* mapping lists (members ascending) */
+  w->moff = (uint32_t *)calloc(n + 1, sizeof(uint32_t));
+  w->mem = (uint32_t *)malloc(sizeof(uint32_t) * (V ? V : 1));
+  for (uint32_t v = 0; v < V; ++v) w->moff[group[v] + 1]++;
+  for (uint32_t x = 0; x < n; ++x) w->moff[x + 1] += w->moff[x];
+  uint32_t *fill = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+  for (uint32_t x = 0; x < n; ++x) fill[x] = w->moff[x];
+  for (uint32_t v = 0; v < V; ++v) w->mem[fill[group[v]]++] = v;
+  free(fill);
+  /* edges sorted by (src, rel, dst) */
+  qsort(e, ne, sizeof(orc_wedge), cmp_wedge);
+  w->ne = ne;
+  w->e = (orc_triple *)malloc(sizeof(orc_triple) * (ne ? ne : 1));
+  w->wout = (uint32_t *)malloc(sizeof(uint32_t) * (ne ? ne : 1));
+  w->win = (uint32_t *)malloc(sizeof(uint32_t) * (ne ? ne : 1));
+  for (uint64_t i = 0; i < ne; ++i) {
+    w->e[i].src = e[i].src; w->e[i].rel = e[i].rel; w->e[i].dst = e[i].dst;
+    w->wout[i] = e[i].wout; w->win[i] = e[i].win;
+  }
+  free(e);
+  /* node weights, straight from the data graph */
+  w->wnode = (uint32_t *)calloc((uint64_t)2 * R * (n ? n : 1), sizeof(uint32_t));
+  for (uint32_t a = 0; a < V; ++a) {
+    const uint32_t x = group[a];
+    for (int dir = 0; dir < 2; ++dir)
+      for (uint32_t r = 0; r < R; ++r) {
+        uint32_t c = 0;
+        for (uint64_t t = orc_begin(g, dir, a); t < orc_begin(g, dir, a + 1); ++t)
+          if (orc_rel(g, dir, t) == r && group[orc_nbr(g, dir, t)] == x) c++;
+        uint32_t *slot = &w->wnode[((uint64_t)dir * R + r) * n + x];
+        if (c > *slot) *slot = c;
+      }
+  }
+  return w;
+}
+
+uint32_t orc_wgraph_nodes(const orc_wgraph *w) { return w->n; }
+uint64_t orc_wgraph_edges(const orc_wgraph *w) { return w->ne; }
+/* Copy out the weighted graph: group[V], moff[n+1], mem[V], type[n],
+ * edges src/rel/dst/wout/win [ne], wnode[2 * R * n] (any may be NULL). */
+void orc_wgraph_get(const orc_wgraph *w, uint32_t *group, uint32_t *moff, uint32_t *mem, uint32_t *type,
+                    uint32_t *src, uint32_t *rel, uint32_t *dst, uint32_t *wout, uint32_t *win, uint32_t *wnode) {
+  if (group) memcpy(group, w->group, sizeof(uint32_t) * w->V);
+  if (moff) memcpy(moff, w->moff, sizeof(uint32_t) * (w->n + 1));
+  if (mem) memcpy(mem, w->mem, sizeof(uint32_t) * w->V);
+  if (type) memcpy(type, w->type, sizeof(uint32_t) * w->n);
+  for (uint64_t i = 0; i < w->ne; ++i) {
+    if (src) src[i] = w->e[i].src;
+    if (rel) rel[i] = w->e[i].rel;
+    if (dst) dst[i] = w->e[i].dst;
+    if (wout) wout[i] = w->wout[i];
+    if (win) win[i] = w->win[i];
+  }
+  if (wnode) memcpy(wnode, w->wnode, sizeof(uint32_t) * 2 * w->R * w->n);
+}
+
+/* Is there a weighted edge (x, r, y) (x != y), or, for x == y, an edge of
+ * relation r inside x (node weight > 0)?  r = ORC_ANY: any relation. */
+static int orc_wedge_exists(const orc_wgraph *w, uint32_t x, uint32_t r, uint32_t y) {
+  if (x == y) {
+    for (uint32_t rr = 0; rr < w->R; ++rr)
+      if ((r == ORC_ANY || rr == r) && w->wnode[(uint64_t)rr * w->n + x] > 0) return 1;
+    return 0;
+  }
+  for (uint64_t i = 0; i < w->ne; ++i)  /* plain scan */
+    if (w->e[i].src == x && w->e[i].dst == y && (r == ORC_ANY || w->e[i].rel == r)) return 1;
+  return 0;
+}
+
+/* Definition 3.5's weight of node x in direction dir over relation r: its
+ * node weight plus the weights of its edges (r = ORC_ANY: the sum over
+ * every relation). */
+static uint64_t orc_wbound(const orc_wgraph *w, uint32_t x, int dir, uint32_t r) {
+  uint64_t s = 0;
+  for (uint32_t rr = 0; rr < w->R; ++rr) {
+    if (r != ORC_ANY && rr != r) continue;
+    s += w->wnode[((uint64_t)dir * w->R + rr) * w->n + x];
+    for (uint64_t i = 0; i < w->ne; ++i)
+      if (w->e[i].rel == rr && (dir == 0 ? w->e[i].src : w->e[i].dst) == x) s += dir == 0 ? w->wout[i] : w->win[i];
+  }
+  return s;
+}
+
+/*
+ * orc_wcandidates: Definition 3.5 on the weighted graph: node x is a
+ * candidate of query vertex u when its type is u's (or u is untyped), u's
+ * binding (a data vertex) lies in M(x), and for every direction and
+ * relation the query degree of u is at most x's weight there.
+ * sets[u * n + x] = 1 for candidates.  Returns 1 for an invalid query.
+ */
+int orc_wcandidates(const orc_wgraph *w, uint32_t k, uint32_t m, const uint32_t *vtype, const uint32_t *vbind,
+                    const uint32_t *esrc, const uint32_t *edst, const uint32_t *erel, uint8_t *sets) {
+  orc_query q;
+  if (orc_query_make(&q, k, m, vtype, vbind, esrc, edst, erel) != 0) return 1;
+  for (uint32_t u = 0; u < k; ++u)
+    for (uint32_t x = 0; x < w->n; ++x) {
+      int ok = (vtype[u] == ORC_ANY || w->type[x] == vtype[u]) &&
+               (vbind[u] == ORC_UNBOUND || (vbind[u] < w->V && w->group[vbind[u]] == x));
+      for (uint32_t e = 0; e < q.m && ok; ++e) {
+        if (q.esrc[e] != u && q.edst[e] != u) continue;
+        const int dir = q.esrc[e] == u ? 0 : 1;
+        uint64_t need = 0;  /* query neighbours of u over this direction and relation */
+        for (uint32_t f = 0; f < q.m; ++f)
+          need += q.erel[f] == q.erel[e] && (dir == 0 ? q.esrc[f] == u : q.edst[f] == u);
+        if (need > orc_wbound(w, x, dir, q.erel[e])) ok = 0;
+      }
+      sets[(uint64_t)u * w->n + x] = (uint8_t)ok;
+    }
+  return 0;
+}
+
+/*
+ * orc_wrefine: the pruning rule of the refinement (Section 3.3.3) on the
+ * weighted graph, repeated until nothing changes: candidate x of u stays when
+ * every query edge at u has, at its other end w, a candidate y of w joined
+ * to x by a weighted edge of that relation and direction, or y == x with an
+ * edge of that relation inside x (two query vertices may map to one node of
+ * the weighted graph).  sets as orc_wcandidates, refined in place.
+ */
+int orc_wrefine(const orc_wgraph *w, uint32_t k, uint32_t m, const uint32_t *esrc, const uint32_t *edst,
+                const uint32_t *erel, uint8_t *sets) {
+  int changed = 1, passes = 0;
+  while (changed) {
+    changed = 0; passes++;
+    for (uint32_t e = 0; e < m; ++e) {
+      const uint32_t a = esrc[e], b = edst[e], r = erel[e];
+      if (a >= k || b >= k) return -1;
+      uint8_t *sa = sets + (uint64_t)a * w->n, *sb = sets + (uint64_t)b * w->n;
+      for (uint32_t x = 0; x < w->n; ++x) {
+        if (!sa[x]) continue;
+        int found = 0;
+        for (uint32_t y = 0; y < w->n && !found; ++y) found = sb[y] && orc_wedge_exists(w, x, r, y);
+        if (!found) { sa[x] = 0; changed = 1; }
+      }
+      for (uint32_t y = 0; y < w->n; ++y) {
+        if (!sb[y]) continue;
+        int found = 0;
+        for (uint32_t x = 0; x < w->n && !found; ++x) found = sa[x] && orc_wedge_exists(w, x, r, y);
+        if (!found) { sb[y] = 0; changed = 1; }
+      }
+    }
+  }
+  return passes;
+}
+
+/* Matching on the weighted graph (Section 3.5): every map h from the query
+ * vertices to nodes with h(u) among u's refined candidates and every query
+ * edge on a weighted edge (or inside a node); for each such h, the injective
+ * maps f with f(u) in M(h(u)) that keep types, bindings and every query edge
+ * in g go to the sink.  Every embedding f of the query in g arises from
+ * exactly one h (h(u) = the node holding f(u)). */
+typedef struct {
+  const orc_graph *g;
+  const orc_wgraph *w;
+  const orc_query *q;
+  const uint8_t *sets;
+  uint32_t h[32], f[32];
+  uint8_t *used;
+  orc_sink *sink;
+  uint64_t homs;
+} orc_cbt;
+
+static void orc_expand(orc_cbt *c, uint32_t u) {
+  const orc_query *q = c->q;
+  if (u == q->k) { orc_sink_put(c->sink, c->f); return; }
+  const uint32_t x = c->h[u];
+  for (uint32_t i = c->w->moff[x]; i < c->w->moff[x + 1]; ++i) {
+    const uint32_t v = c->w->mem[i];
+    if (c->used[v] || !orc_unary_ok(c->g, q, u, v)) continue;
+    int ok = 1;
+    for (uint32_t e = 0; e < q->m && ok; ++e) {
+      const uint32_t s = q->esrc[e], d = q->edst[e];
+      if ((s == u && d < u) || (d == u && s < u))
+        ok = orc_has_edge(c->g, s == u ? v : c->f[s], q->erel[e], d == u ? v : c->f[d]);
+    }
+    if (!ok) continue;
+    c->f[u] = v; c->used[v] = 1;
+    orc_expand(c, u + 1);
+    c->used[v] = 0;
+  }
+}
+
+static void orc_hom(orc_cbt *c, uint32_t u) {
+  const orc_query *q = c->q;
+  if (u == q->k) { c->homs++; orc_expand(c, 0); return; }
+  for (uint32_t x = 0; x < c->w->n; ++x) {
+    if (!c->sets[(uint64_t)u * c->w->n + x]) continue;
+    int ok = 1;
+    for (uint32_t e = 0; e < q->m && ok; ++e) {
+      const uint32_t s = q->esrc[e], d = q->edst[e];
+      if ((s == u && d < u) || (d == u && s < u))
+        ok = orc_wedge_exists(c->w, s == u ? x : c->h[s], q->erel[e], d == u ? x : c->h[d]);
+    }
+    if (!ok) continue;
+    c->h[u] = x;
+    orc_hom(c, u + 1);
+  }
+}
+
+/*
+ * orc_match_compressed: the embeddings of the query in g found through the
+ * weighted graph: Definition 3.5's candidates on w, refined to the fixpoint,
+ * every weighted-graph solution h, and each expanded through the mapping
+ * lists.  Outputs as orc_match, plus *homs = the number of weighted-graph
+ * solutions.  Returns 1 for an invalid query.
+ */
+int orc_match_compressed(const orc_graph *g, const orc_wgraph *w, uint32_t k, uint32_t m, const uint32_t *vtype,
+                         const uint32_t *vbind, const uint32_t *esrc, const uint32_t *edst, const uint32_t *erel,
+                         uint64_t cap, uint64_t *count, uint64_t *fp, uint32_t *rows_out, uint64_t *nrows,
+                         uint64_t *homs) {
+  orc_query q;
+  if (orc_query_make(&q, k, m, vtype, vbind, esrc, edst, erel) != 0) return 1;
+  for (uint32_t u = 0; u < k; ++u) {
+    if (vbind[u] != ORC_UNBOUND && vbind[u] >= g->V) return 1;
+    if (vtype[u] != ORC_ANY && vtype[u] >= g->T) return 1;
+  }
+  for (uint32_t e = 0; e < q.m; ++e) if (q.erel[e] >= g->R && q.erel[e] != ORC_ANY) return 1;
+  uint8_t *sets = (uint8_t *)malloc((uint64_t)k * (w->n ? w->n : 1));
+  orc_wcandidates(w, k, m, vtype, vbind, esrc, edst, erel, sets);
+  orc_wrefine(w, k, q.m, q.esrc, q.edst, q.erel, sets);
+  orc_sink sink;
+  memset(&sink, 0, sizeof sink);
+  sink.k = k; sink.cap = cap; sink.w = k;
+  for (uint32_t u = 0; u < k; ++u) sink.proj[u] = u;
+  sink.room = cap == 0 ? 0 : (cap < (1u << 20) ? 2 * cap : cap + (1u << 20));
+  sink.rows = cap ? (uint32_t *)malloc(sizeof(uint32_t) * k * sink.room) : NULL;
+  orc_cbt c;
+  memset(&c, 0, sizeof c);
+  c.g = g; c.w = w; c.q = &q; c.sets = sets; c.sink = &sink;
+  c.used = (uint8_t *)calloc(g->V ? g->V : 1, 1);
+  orc_hom(&c, 0);
+  free(c.used); free(sets);
+  if (cap) orc_sink_trim(&sink);
+  *count = sink.count; *fp = sink.fp; *nrows = sink.n; *homs = c.homs;
+  if (cap && rows_out) memcpy(rows_out, sink.rows, sizeof(uint32_t) * k * sink.n);
+  free(sink.rows);
+  return 0;
+}
