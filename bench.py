@@ -3,15 +3,19 @@
 
 One step = the whole device pipeline (plan, filter, exploration, refinement,
 candidate-edge tables, join, sort) over one batch of queries: by default the
-1,000 queries of 4-10 vertices on the 1M-vertex / 8M-edge graph.  Prints one
-JSON line.
+10,000 queries of 3-12 vertices (half of them cyclic) on the 4M-vertex /
+32M-edge graph, as one batch.  Prints one JSON line.
 
   value   queries/s of the batched pipeline, inputs resident in HBM
           (CUDA events on the launching stream; L2 flushed between steps)
   e2e     the same metric through gs_match_batch with host buffers
           (query upload and result download inside the timed region)
   one_at_a_time   queries/s when the same device pipeline runs each query
-                  as its own wave (the baseline the batching is measured against)
+                  as its own wave (the baseline the batching is measured against),
+                  on a sample of the queries when the workload is large
+  serving  p50/p99/p999 latency and sustained queries/s of the serving loop
+           under Poisson arrivals (for the 4M-vertex graph: 1k, 5k, 20k and
+           50k queries/s of queries of 3-12 vertices)
 
 --impl reference times the CPU oracle (test infrastructure) on the same
 workload on the host cores instead.
@@ -31,6 +35,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "queries/s and embeddings/s, batched vs one-at-a-time (exact); serving p50/p99 ms"
+# queries the CPU oracle times per workload (all of them for the two small
+# workloads; a seeded sample of the large ones, labelled "sampled")
+CPU_SAMPLE = {"batch-4m": 200, "serve-4m": 200, "stress-16m": 50}
+# queries of the one-at-a-time comparison (a sample where one step of all of
+# them would take seconds)
+ONE_SAMPLE = {"batch-4m": 1000, "serve-4m": 1000}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -190,13 +200,22 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def cpu_sample(qs, n, seed):
+    """A seeded sample of n of the queries (all of them when n >= len(qs))."""
+    import numpy as np
+    if n >= len(qs):
+        return list(qs), "all"
+    idx = np.sort(np.random.default_rng(seed).choice(len(qs), n, replace=False))
+    return [qs[i] for i in idx], f"a seeded sample of {n}"
+
+
 def cpu_baseline(workload, g, qs, sample_n=None, min_seconds=10.0, max_repeats=30):
     """The oracle as it stands, counts and fingerprints, on every host core:
     the sample is run repeatedly until at least min_seconds have passed (at
     most max_repeats times), so that the rate rests on 10-30 s of CPU work."""
     import oracle
     og = oracle.OracleGraph.from_graph(g)
-    sample = qs if sample_n is None else qs[:sample_n]
+    sample, how = cpu_sample(qs, len(qs) if sample_n is None else sample_n, workload.seed + 0x5A)
     reps, done, emb, timed_out, used = 0, 0, 0, 0, 0
     t = time.perf_counter()
     while reps < max_repeats and (reps == 0 or time.perf_counter() - t < min_seconds):
@@ -207,8 +226,9 @@ def cpu_baseline(workload, g, qs, sample_n=None, min_seconds=10.0, max_repeats=3
         timed_out += int((st == 2).sum())
     dt = time.perf_counter() - t
     return {"value": done / dt, "unit": "queries/s", "cores": int(used), "kind": "oracle",
-            "sample": f"{len(sample)} of the {len(qs)} queries of {workload.name} (counts and fingerprints, "
-                      f"all embeddings enumerated), run {reps} times in {dt:.2f} s, {timed_out} timed out",
+            "sample": f"{how} of the {len(qs)} queries of {workload.name} (counts and fingerprints, "
+                      f"all embeddings enumerated), run {reps} times in {dt:.2f} s, {timed_out} timed out"
+                      + ("" if how == "all" else "; sampled"),
             "embeddings_per_s": emb / dt}
 
 
@@ -260,7 +280,8 @@ def run_reference(args, world, rank):
     g = w.graph()
     qs = w.queries(g)
     og = oracle.OracleGraph.from_graph(g)
-    per_step = qs if args.ref_sample is None else qs[:args.ref_sample]
+    n_ref = args.ref_sample if args.ref_sample is not None else CPU_SAMPLE.get(w.name, len(qs))
+    per_step, how = cpu_sample(qs, n_ref, w.seed + 0x5A)
     for _ in range(args.warmup):
         oracle.match_many(og, per_step, threads=0, time_limit_s=60.0)
     times, used, emb = [], 1, 0
@@ -278,8 +299,8 @@ def run_reference(args, world, rank):
                        "query_vertices": [w.kmin, w.kmax], "p_bind": w.p_bind, "cap": w.cap},
             "embeddings_per_s": emb * args.steps / tot,
             "cpu_baseline": {"value": value, "unit": "queries/s", "cores": int(used), "kind": "oracle",
-                             "sample": f"{len(per_step)} queries per step (the whole workload), counts and "
-                                       f"fingerprints"},
+                             "sample": f"{how} of the {len(qs)} queries of {w.name} per step, counts and "
+                                       f"fingerprints" + ("" if how == "all" else "; sampled")},
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -370,17 +391,82 @@ def run_khop(args, world, rank, local):
     dg.free()
 
 
+COMPRESS_METRIC = "queries/s through a multi-level compressed graph (exact), with the compression ratio"
+
+
+def run_compressed(args, world, rank, local):
+    """Matching through a multi-level compression (the compress-* workloads):
+    the compression is built once (offline, untimed; its time is reported),
+    then each step matches every query through the compressed graph from host
+    buffers (weighted-graph stage, data-graph stage, results to the host),
+    timed with CUDA events on the library's work and wall clock around the
+    call.  The same queries on the uncompressed graph are timed beside it."""
+    import torch
+    import paper_1807_08804_gb300 as gs
+    from paper_1807_08804_gb300 import inputs as I
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = I.WORKLOADS[args.workload]
+    g = w.graph()
+    qs = w.queries(g)
+    n = len(qs)
+    t = time.perf_counter()
+    cg = gs.CompressedGraph(g, w.deltas)
+    build_s = time.perf_counter() - t
+    info = cg.info()
+    dg = gs.DeviceGraph(g)
+    for _ in range(max(args.warmup, 3)):
+        res = cg.match_batch(qs, cap=w.cap)
+    plain = gs.match_batch(dg, qs, cap=w.cap)
+    assert all((a.count, a.fingerprint) == (b.count, b.fingerprint) for a, b in zip(res, plain)), "paths disagree"
+    embeddings = sum(r.count for r in res)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        res = cg.match_batch(qs, cap=w.cap)
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t, world, dev)
+    barrier(world)
+    clk = clocks.stop()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        plain = gs.match_batch(dg, qs, cap=w.cap)
+    torch.cuda.synchronize()
+    dt_plain = max_over_ranks(time.perf_counter() - t, world, dev)
+    value = n * world * args.steps / dt
+    line = {"metric": COMPRESS_METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": w.name, "vertices": w.V, "edges": w.E, "queries": n, "deltas": list(w.deltas),
+                       "target_s": w.target_s, "copy_p": w.copy_p, "cap": w.cap,
+                       "parallelism": f"replicas x{world}"},
+            "compression": {**info, "build_s": build_s},
+            "embeddings_per_step": embeddings,
+            "e2e": {"value": value, "unit": "queries/s", "note": "host buffers in and out each step"},
+            "uncompressed": {"value": n * world * args.steps / dt_plain, "unit": "queries/s"},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    cg.free()
+    dg.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
-    ap.add_argument("--workload", default="single-1m")
+    ap.add_argument("--workload", default="batch-4m")
     ap.add_argument("--one-steps", type=int, default=2, help="steps of the one-query-at-a-time comparison")
     ap.add_argument("--ref-sample", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of arrivals per serving rate (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="seconds of arrivals per serving rate (0 = skip)")
+    ap.add_argument("--one-sample", type=int, default=None,
+                    help="queries in the one-at-a-time comparison (default: all, or 1,000 of the 4M workloads)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--tune-cache", default=os.path.join(ROOT, "paper_1807_08804_gb300", "_build", "tune_cache.txt"),
                     help="autotuner cache file: a choice made once for this graph, GPU and load is reused")
@@ -402,6 +488,10 @@ def main():
         return
     if args.khop:
         run_khop(args, world, rank, local)
+        return
+    from paper_1807_08804_gb300 import inputs as _inputs
+    if _inputs.WORKLOADS[args.workload].deltas:
+        run_compressed(args, world, rank, local)
         return
 
     import torch
@@ -441,9 +531,10 @@ def main():
     assert sh != 0
     b = gs.Batch(dg, qs, cap=cap, mode=gmode, stream=sh, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, raw_chunks=True,
                  project=project)
-    one = gs.Batch(dg, qs, cap=cap, mode=gmode, wave_queries=1, stream=sh, chunk_bytes=chunk_bytes, on_chunk=chunk_cb,
-                   project=project,
-                   raw_chunks=True)
+    n_one = args.one_sample if args.one_sample is not None else ONE_SAMPLE.get(w.name, n)
+    one_qs = qs[:n_one]
+    one = gs.Batch(dg, one_qs, cap=cap, mode=gmode, wave_queries=1, stream=sh, chunk_bytes=chunk_bytes,
+                   on_chunk=chunk_cb, project=project, raw_chunks=True)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     for _ in range(max(args.warmup, 3)):
@@ -460,6 +551,7 @@ def main():
         one.run()
         one.finish()
         ref = one.fetch()
+        assert len(ref) == len(one_qs)
         assert all((x.count, x.fingerprint) == (y.count, y.fingerprint) for x, y in zip(res, ref)), "modes disagree"
 
     # ---- timed region: batched pipeline, device-resident inputs
@@ -512,7 +604,7 @@ def main():
     if args.one_steps:
         one.finish()
     one_tot = max_over_ranks(sum(one_ms), world, dev)
-    one_qps = n * world * args.one_steps / (one_tot / 1e3) if args.one_steps else None
+    one_qps = len(one_qs) * world * args.one_steps / (one_tot / 1e3) if args.one_steps else None
 
     # ---- end to end through the public API with host buffers
     h0, d0 = dg.io_bytes()
@@ -531,10 +623,13 @@ def main():
     h1, d1 = dg.io_bytes()
     assert sum(r.count for r in out) == embeddings
 
-    # ---- serving: continuous batching under Poisson arrivals
-    rates = w.qps if w.qps else (20000.0,)
-    serving = ([serve_measure(gs, dg, qs, r, args.serve_seconds, cap) for r in rates]
-               if args.serve_seconds > 0 and not w.shapes else [])
+    # ---- serving: continuous batching under Poisson arrivals (on the 4M
+    # graph, the serving workload's own queries and rates)
+    sw = I.WORKLOADS["serve-4m"] if w.name in ("batch-4m", "serve-4m") else w
+    sqs = qs if sw is w else sw.queries(g)
+    rates = sw.qps if sw.qps else (20000.0,)
+    serving = ([serve_measure(gs, dg, sqs, r, args.serve_seconds, sw.cap) for r in rates]
+               if args.serve_seconds > 0 and not w.shapes and mode == "enumerate" and not project else [])
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
@@ -561,7 +656,9 @@ def main():
             **({"streamed_rows_per_step": streamed_timed / args.steps} if mode == "chunked" else {}),
             **({"projected_rows_per_step": proj_rows} if project else {}),
             "one_at_a_time": ({"value": one_qps, "unit": "queries/s", "ms_per_step": one_tot / args.one_steps,
-                               "speedup_batched": value / one_qps} if one_qps else None),
+                               "queries": len(one_qs), "speedup_batched": value / one_qps,
+                               "sample": "all" if len(one_qs) == n else f"the first {len(one_qs)} queries; sampled"}
+                              if one_qps else None),
             "e2e": {"value": n * world * e2e_steps / e2e_s, "unit": "queries/s",
                     "h2d_bytes_per_step": (h1 - h0) // e2e_steps, "d2h_bytes_per_step": (d1 - d0) // e2e_steps},
             "gpu_launches": launches,
@@ -569,11 +666,12 @@ def main():
             "roofline": roof,
             "clocks": clk,
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in stats.items() if v["launches"]},
+            "kernel_bytes_per_step": {k: v["bytes"] // args.steps for k, v in stats.items() if v["bytes"]},
             "fallback_queries": b.counters().get("fallback_queries", 0), "failed_queries": len(bad)}
     if args.ablation:
         line["ablation"] = refinement_ablation(gs, dg, qs, cap, gmode, sh, stream, flush, args.steps, res)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, g, qs)
+        line["cpu_baseline"] = cpu_baseline(w, g, qs, sample_n=CPU_SAMPLE.get(w.name))
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()

@@ -188,9 +188,11 @@ typedef struct {
   uint64_t fingerprint;  /* sum over ALL embeddings of an order-free 64-bit row hash */
   uint32_t k;            /* row width: query vertices, or projected vertices */
   uint32_t truncated;    /* 1 if count > cap (projected: more distinct tuples than cap) */
-  uint32_t *rows;        /* [num_rows * k] row-major, query-vertex order, ascending; owned */
+  uint32_t *rows;        /* [num_rows * k] row-major, query-vertex order, ascending; owned
+                            unless `shared` */
   uint32_t status;       /* gs_status of this query (batch calls) */
-  uint32_t reserved;
+  uint32_t shared;       /* 1: rows lie in a block shared by the results of one
+                            gs_match_batch_shared call (gs_result_free leaves them) */
 } gs_result;
 
 /* Match one query (a batch of one).  Blocks until the result is on the host. */
@@ -201,6 +203,21 @@ gs_status gs_match(gs_graph *g, const gs_query *q, const gs_match_opts *opts, gs
  * valid).  Returns GS_OK unless the call itself failed. */
 gs_status gs_match_batch(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
                          gs_result *outs);
+
+/* gs_match_batch without a copy of the rows on the host: the results' rows
+ * lie in one block of page-locked host memory that the device wrote
+ * directly, and each such result has shared = 1.  *block receives the
+ * block (NULL when no row is shared); the rows stay valid until
+ * gs_rows_release(block), which returns the block to a library pool for
+ * later calls.  gs_rows_base/gs_rows_words give the block's address and size
+ * in uint32 words.  Results of queries finished on the chunked path own
+ * their rows as usual.  Errors as gs_match_batch. */
+typedef struct gs_rows gs_rows;
+gs_status gs_match_batch_shared(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
+                                gs_result *outs, gs_rows **block);
+const uint32_t *gs_rows_base(const gs_rows *block);
+uint64_t gs_rows_words(const gs_rows *block);
+void gs_rows_release(gs_rows *block);
 
 void gs_result_free(gs_result *r);
 /* gs_result_free on each of r[0..n). */
@@ -246,8 +263,25 @@ void gs_batch_destroy(gs_batch *b);
 gs_status gs_batch_create_waves(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
                                 uint32_t wave_queries, gs_batch **out);
 /* Execution knobs: captured graph or direct launches, lanes per work item
- * (8, 16 or 32), refinement rounds (0 = until nothing changes). */
+ * (4, 8, 16 or 32), refinement rounds (0 = until nothing changes;
+ * GS_ROUNDS_NONE = no refinement round after exploration). */
+#define GS_ROUNDS_NONE 0xFFFFFFFFu
 gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_t refine_rounds);
+/* Bound on the one device-side wait of the pipeline: the look-back of the
+ * single-pass prefix scans that size every output (Section 3.3.4's two-step
+ * output scheme: count, prefix sum, write).  A block waits there only on
+ * tiles that earlier, running blocks claimed, so the wait ends; it is bounded
+ * all the same.  max_polls = reads of a predecessor tile's state before the
+ * wait gives up (0 = the default, 2^22).  A wait that gives up sums the scan's
+ * inputs before its tile directly, so every result stays exact, and records
+ * the event; the next gs_batch_finish then returns GS_ERR_TIMEOUT and clears
+ * the record (fetch nothing from that run).  GS_WAIT_WITHHOLD_FIRST_TILE is
+ * for tests of this path: the first tile of every scan of more than one tile
+ * (2,048 counts) publishes nothing, so each later tile's wait runs to the
+ * bound.  Applies to the batch's later runs, in stream order.  Errors:
+ * GS_ERR_INVALID (null batch, unknown flag), GS_ERR_CUDA. */
+#define GS_WAIT_WITHHOLD_FIRST_TILE 1u
+gs_status gs_batch_set_wait(gs_batch *b, uint32_t max_polls, uint32_t flags);
 /* Kernels launched by runs so far, bytes moved between host and device, and
  * queries finished on the host-driven chunked path by the last finish. */
 gs_status gs_batch_counters(gs_batch *b, uint64_t *kernel_launches, uint64_t *h2d, uint64_t *d2h,
@@ -271,7 +305,7 @@ gs_status gs_stats_reset(gs_batch *b);
  * Autotuning.  Times the captured pipeline on the given queries for each
  * lanes-per-work-item setting (4, 8, 16, 32: the lanes that share one
  * candidate vertex, edge-table key or partial embedding) and each number of
- * refinement rounds (2, 4, 8), and keeps the fastest for batches created on
+ * refinement rounds (none, 1, 2, 4), and keeps the fastest for batches created on
  * this graph afterwards.  Results never depend on these settings.  With
  * cache_path != NULL the choice is read from / appended to that text file,
  * keyed by graph content hash, GPU name and a signature of the query load
@@ -286,7 +320,8 @@ typedef struct {
 } gs_tuning;
 gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts, const char *cache_path,
                   gs_tuning *out);
-/* Set the tuned values by hand (0 = library default). */
+/* Set the tuned values by hand (0 = library default; refine_rounds may be
+ * GS_ROUNDS_NONE). */
 gs_status gs_tune_set(gs_graph *g, uint32_t group, uint32_t refine_rounds);
 
 /* ------------------------------------------------------------------------
@@ -336,6 +371,84 @@ gs_status gs_filter_candidates_static(gs_graph *g, const gs_query *q, uint32_t u
                                       uint64_t *d_count, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Multi-level graph compression (Section 3.4) and matching through it
+ * (Section 3.5).  gs_cgraph_build compresses a data graph offline, on the
+ * host: `levels` levels (0-32), each pairing similar nodes with threshold
+ * delta[l] in (0, 1], into a weighted graph whose nodes stand for groups of
+ * data vertices (mapping lists).  Readings, for directed graphs with
+ * relations and vertex types:
+ *   - adj(x) = the (direction, relation, other node) triples of x's edges to
+ *     other nodes; x and y are similar when they have one type and the
+ *     triples both have number at least delta * |adj(x)| and at least
+ *     delta * |adj(y)| (double-precision products; the thesis's test as
+ *     printed always holds), or when neither has edges; with delta = 1 similar
+ *     nodes have equal adjacency lists;
+ *   - a level visits nodes in index order and pairs each unpaired node with
+ *     the lowest-indexed later unpaired node similar to it; merged nodes are
+ *     numbered by ascending smallest member;
+ *   - edge weights start at 1 and follow w(u, v) = max(w(p, n), w(q, n)) +
+ *     max(w(p, m), w(q, m)) per relation (Definition 3.4's recursion), wout
+ *     bounding the out-neighbours in M(v) of any member of M(u), win the
+ *     in-neighbours in M(u) of any member of M(v); edges inside a node are not
+ *     edges of the weighted graph; the node weight per direction and relation
+ *     is the most neighbours a member has inside its own node;
+ *   - Definition 3.5, per direction and relation: a node is a candidate of a
+ *     query vertex with c neighbours there when its node weight plus the
+ *     weights of its edges there is at least c (variable edges: the sum over
+ *     every relation).
+ * The data graph and the weighted graph are both loaded on the current
+ * device; the arrays must be host pointers (GS_DEVICE_PTRS ->
+ * GS_ERR_UNSUPPORTED).  Errors as gs_graph_load, and GS_ERR_INVALID for more
+ * than 32 levels or a threshold outside (0, 1].
+ * ------------------------------------------------------------------------ */
+/* The compression alone, on the host (no CUDA call, no device needed):
+ * *nodes and *weighted_edges receive the sizes; then, for each non-NULL
+ * array, group[V], src/rel/dst/wout/win[*weighted_edges] and
+ * wnode[2 * num_rels * *nodes] as gs_cgraph_export writes them.  Arrays
+ * sized for the bounds (num_edges entries, 2 * num_rels * V words) are
+ * always large enough.  The graph's arrays are checked on the host. */
+gs_status gs_compress_host(const gs_graph_desc *desc, uint32_t levels, const double *delta, uint32_t *nodes,
+                           uint64_t *weighted_edges, uint32_t *group, uint32_t *src, uint32_t *rel, uint32_t *dst,
+                           uint32_t *wout, uint32_t *win, uint32_t *wnode);
+typedef struct gs_cgraph gs_cgraph;
+gs_status gs_cgraph_build(const gs_graph_desc *desc, uint32_t levels, const double *delta, gs_cgraph **out);
+void gs_cgraph_free(gs_cgraph *cg);
+typedef struct {
+  uint32_t levels;
+  uint32_t vertices;        /* V of the data graph */
+  uint64_t edges;           /* distinct data triples */
+  uint32_t nodes;           /* nodes of the weighted graph */
+  uint32_t reserved;
+  uint64_t weighted_edges;  /* its edges between different nodes */
+  uint64_t inner_edges;     /* (node, relation) pairs with edges inside the node */
+  double ratio;             /* (nodes + weighted_edges + inner_edges) / (vertices + edges),
+                               the thesis's compression ratio */
+} gs_cgraph_info;
+gs_status gs_cgraph_get_info(const gs_cgraph *cg, gs_cgraph_info *out);
+/* The compression itself, for checks: group[vertices] = the node holding
+ * each data vertex; the weighted edges src/rel/dst/wout/win[weighted_edges]
+ * sorted by (src, rel, dst); wnode[(dir * num_rels + rel) * nodes + x]
+ * (dir 0 = out, 1 = in).  Host arrays; any may be NULL. */
+gs_status gs_cgraph_export(const gs_cgraph *cg, uint32_t *group, uint32_t *src, uint32_t *rel, uint32_t *dst,
+                           uint32_t *wout, uint32_t *win, uint32_t *wnode);
+/* Candidate sets of a query on the weighted graph (Definition 3.5, then
+ * exploration and refinement to the fixpoint, two query vertices allowed on
+ * one node), as gs_inspect_candidates: node ids per query vertex.  Bindings
+ * are data vertices; each is replaced by the node holding it. */
+gs_status gs_cgraph_candidates(gs_cgraph *cg, const gs_query *q, uint64_t *off, uint32_t *ids, uint64_t cap_ids,
+                               uint64_t *n_ids);
+/* gs_match_batch through the compressed graph: the queries' candidate sets
+ * on the weighted graph (as gs_cgraph_candidates) restrict every candidate
+ * test of the device pipeline on the data graph to the vertices of their
+ * nodes' mapping lists (Theorem 3.2: no other vertex is a match), so the
+ * results are every embedding in the data graph, the same as gs_match_batch
+ * on it.  GS_CHUNKED -> GS_ERR_UNSUPPORTED; a batch too large for one wave
+ * of the weighted-graph stage -> GS_ERR_UNSUPPORTED.  Calls on one compressed
+ * graph are serialised. */
+gs_status gs_match_batch_compressed(gs_cgraph *cg, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
+                                    gs_result *outs);
+
+/* ------------------------------------------------------------------------
  * Serving: a request loop that keeps the graph device-resident and admits
  * queries while slots and the working-set budget allow (continuous batching:
  * requests that arrive while others run are admitted as slots free up).
@@ -357,6 +470,21 @@ gs_status gs_serve_submit(gs_server *s, const gs_query *q, const gs_match_opts *
  * receives submit-to-completion time in seconds. */
 gs_status gs_serve_poll(gs_server *s, uint64_t ticket, gs_result *out, double *latency_s);
 gs_status gs_serve_destroy(gs_server *s);
+
+/* ------------------------------------------------------------------------
+ * Failure injection for tests, on the host side only: no kernel is made to
+ * fault.  The thesis has no counterpart.
+ * ------------------------------------------------------------------------ */
+/* After `after` more device allocations by the library (any thread, any
+ * graph), the next one fails as if the device were out of memory, without
+ * allocating; the call that made it returns GS_ERR_OOM (or reports it per
+ * request) and frees what it had allocated.  One-shot; after < 0 disarms. */
+void gs_debug_fail_alloc(int64_t after);
+/* Serving: the next n completion checks of in-flight micro-batches (across
+ * servers) report a CUDA error, as a failed kernel would.  Each such
+ * micro-batch is dropped after its work drains and its requests complete with
+ * GS_ERR_CUDA; the server keeps serving.  n = 0 disarms. */
+void gs_debug_fail_serve_wait(uint32_t n);
 
 #ifdef __cplusplus
 }

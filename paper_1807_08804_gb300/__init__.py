@@ -27,6 +27,8 @@ GS_ENUMERATE, GS_COUNT_ONLY, GS_CHUNKED = 0, 1, 2
 GS_STAGE_FILTER, GS_STAGE_FIXPOINT = 0, 1
 GS_REFINE_OFF, GS_REFINE_REVERSED = 1, 2
 GS_KHOP_OUT, GS_KHOP_IN = 1, 2
+GS_WAIT_WITHHOLD_FIRST_TILE = 1
+GS_ROUNDS_NONE = 0xFFFFFFFF
 
 
 def GS_REFINE_LOW(d: int) -> int:
@@ -71,7 +73,7 @@ class KhopOpts(ctypes.Structure):
 
 class ResultDesc(ctypes.Structure):
     _fields_ = [("count", U64), ("num_rows", U64), ("fingerprint", U64), ("k", U32), ("truncated", U32),
-                ("rows", ctypes.POINTER(U32)), ("status", U32), ("reserved", U32)]
+                ("rows", ctypes.POINTER(U32)), ("status", U32), ("shared", U32)]
 
 
 class KernelStats(ctypes.Structure):
@@ -86,6 +88,11 @@ class Tuning(ctypes.Structure):
 
 class ServeOpts(ctypes.Structure):
     _fields_ = [("budget_bytes", U64), ("slots", U32), ("max_batch", U32), ("queue_depth", U32), ("reserved", U32)]
+
+
+class CGraphInfo(ctypes.Structure):
+    _fields_ = [("levels", U32), ("vertices", U32), ("edges", U64), ("nodes", U32), ("reserved", U32),
+                ("weighted_edges", U64), ("inner_edges", U64), ("ratio", ctypes.c_double)]
 
 
 # Every entry point of include/gs.h with its argument types.
@@ -131,6 +138,23 @@ EXTRA_SIGNATURES = {
     "gs_tune": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts), ctypes.c_char_p,
                                ctypes.POINTER(Tuning)]),
     "gs_tune_set": (ctypes.c_int, [P, U32, U32]),
+    "gs_batch_set_wait": (ctypes.c_int, [P, U32, U32]),
+    "gs_match_batch_shared": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts),
+                                             ctypes.POINTER(ResultDesc), ctypes.POINTER(P)]),
+    "gs_rows_base": (P, [P]),
+    "gs_rows_words": (U64, [P]),
+    "gs_rows_release": (None, [P]),
+    "gs_compress_host": (ctypes.c_int, [ctypes.POINTER(GraphDesc), U32, P, ctypes.POINTER(U32), ctypes.POINTER(U64),
+                                        P, P, P, P, P, P, P]),
+    "gs_cgraph_build": (ctypes.c_int, [ctypes.POINTER(GraphDesc), U32, P, ctypes.POINTER(P)]),
+    "gs_cgraph_free": (None, [P]),
+    "gs_cgraph_get_info": (ctypes.c_int, [P, ctypes.POINTER(CGraphInfo)]),
+    "gs_cgraph_export": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
+    "gs_cgraph_candidates": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), P, P, U64, ctypes.POINTER(U64)]),
+    "gs_match_batch_compressed": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts),
+                                                 ctypes.POINTER(ResultDesc)]),
+    "gs_debug_fail_alloc": (None, [ctypes.c_int64]),
+    "gs_debug_fail_serve_wait": (None, [U32]),
 }
 
 _lib = None
@@ -290,9 +314,9 @@ def _take(r: ResultDesc) -> MatchResult:
     return out
 
 
-_RES_DTYPE = np.dtype({"names": ["count", "num_rows", "fingerprint", "k", "truncated", "rows", "status"],
-                       "formats": ["<u8", "<u8", "<u8", "<u4", "<u4", "<u8", "<u4"],
-                       "offsets": [0, 8, 16, 24, 28, 32, 40], "itemsize": 48})
+_RES_DTYPE = np.dtype({"names": ["count", "num_rows", "fingerprint", "k", "truncated", "rows", "status", "shared"],
+                       "formats": ["<u8", "<u8", "<u8", "<u4", "<u4", "<u8", "<u4", "<u4"],
+                       "offsets": [0, 8, 16, 24, 28, 32, 40, 44], "itemsize": 48})
 
 
 def _take_all(res, n: int) -> list[MatchResult]:
@@ -312,6 +336,54 @@ def _take_all(res, n: int) -> list[MatchResult]:
            for c, f, o0, o1, r, k, t, s in zip(a["count"].tolist(), a["fingerprint"].tolist(), offl, offl[1:], nrl,
                                                 kl, a["truncated"].tolist(), a["status"].tolist())]
     lib().gs_results_free(res, n)
+    return out
+
+
+class _RowsBlock:
+    """Owner of a row block of gs_match_batch_shared: the block goes back to
+    the library when the last array viewing it is gone."""
+
+    def __init__(self, h):
+        self._h = h
+
+    def __del__(self):
+        try:
+            lib().gs_rows_release(self._h)
+        except Exception:
+            pass
+
+
+def _take_shared(res, n: int, blk) -> list[MatchResult]:
+    """Results of gs_match_batch_shared: shared rows are views of the block
+    (no copy); rows a result owns are copied and freed."""
+    if n == 0:
+        return []
+    a = np.frombuffer(res, dtype=_RES_DTYPE, count=n)
+    words = int(lib().gs_rows_words(blk)) if blk else 0
+    if words:
+        base = int(lib().gs_rows_base(blk) or 0)
+        buf = (ctypes.c_uint32 * words).from_address(base)
+        buf._owner = _RowsBlock(blk)  # released with the last view
+        big = np.frombuffer(buf, np.uint32)
+    else:
+        if blk:
+            lib().gs_rows_release(blk)
+        base, big = 0, np.empty(0, np.uint32)
+    nr, ks = a["num_rows"].astype(np.int64), a["k"].astype(np.int64)
+    shared = a["shared"].astype(bool)
+    o0 = np.where(shared, (a["rows"].astype(np.int64) - base) // 4, 0)
+    o1 = o0 + nr * ks
+    view = MatchResult._view
+    out = [view(c, f, big, x0, x1, r, k, t != 0, st)
+           for c, f, x0, x1, r, k, t, st in zip(a["count"].tolist(), a["fingerprint"].tolist(), o0.tolist(),
+                                                o1.tolist(), nr.tolist(), ks.tolist(), a["truncated"].tolist(),
+                                                a["status"].tolist())]
+    for i in np.flatnonzero(~shared & (nr > 0)).tolist():  # rows the result owns
+        rows = np.empty(int(nr[i] * ks[i]), np.uint32)
+        ctypes.memmove(rows.ctypes.data, int(a["rows"][i]), 4 * rows.shape[0])
+        out[i] = MatchResult(out[i].count, out[i].fingerprint, rows.reshape(int(nr[i]), int(ks[i])),
+                             out[i].truncated, out[i].status)
+    lib().gs_results_free(res, n)  # frees owned rows only
     return out
 
 
@@ -377,8 +449,9 @@ def match_batch(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, max_re
     cb = _chunk_callback(on_chunk, raw_chunks)
     o = _opts(cap, mode, max_refine_rounds, chunk_bytes, on_chunk=cb, project=project, refine=refine)
     res = (ResultDesc * max(len(queries), 1))()
-    _check(lib().gs_match_batch(dg._h, pack.arr, len(queries), ctypes.byref(o), res))
-    return _take_all(res, len(queries))
+    blk = P()
+    _check(lib().gs_match_batch_shared(dg._h, pack.arr, len(queries), ctypes.byref(o), res, ctypes.byref(blk)))
+    return _take_shared(res, len(queries), blk)
 
 
 def khop(dg: "DeviceGraph", seeds, levels: int, directions: int = GS_KHOP_OUT | GS_KHOP_IN, rels=None,
@@ -424,6 +497,13 @@ class Batch:
 
     def configure(self, use_graph=True, group=32, refine_rounds=0):
         _check(lib().gs_batch_set(self._h, 1 if use_graph else 0, group, refine_rounds))
+
+    def set_wait(self, max_polls=0, withhold_first_tile=False):
+        """Bound of the prefix scans' look-back waits (0 = default); with
+        withhold_first_tile the first tile of every multi-tile scan publishes
+        nothing (tests of the timeout path)."""
+        _check(lib().gs_batch_set_wait(self._h, max_polls,
+                                       GS_WAIT_WITHHOLD_FIRST_TILE if withhold_first_tile else 0))
 
     def run(self):
         _check(lib().gs_batch_run(self._h))
@@ -517,6 +597,109 @@ def inspect_edge_table(dg: DeviceGraph, q, e: int, from_src: bool):
     _check(lib().gs_inspect_edge_table(dg._h, pack.arr, e, 1 if from_src else 0, _ptr(keys), _ptr(off), _ptr(vals),
                                        keys.shape[0], vals.shape[0], ctypes.byref(nk), ctypes.byref(nv)))
     return keys[: nk.value], off, vals[: nv.value]
+
+
+def compress_host(g, deltas) -> dict:
+    """The library's multi-level compression of g, computed on the host
+    (no device needed): node of each vertex, weighted edges and weights."""
+    d = np.ascontiguousarray(np.asarray(list(deltas), np.float64))
+    ro = np.ascontiguousarray(np.asarray(g.row_offsets, dtype=np.uint64))
+    keep = (ro, _u32(g.col_targets), _u32(g.edge_rel), _u32(g.vertex_type))
+    desc = GraphDesc(int(g.num_vertices), int(ro[-1]), *[_ptr(x) for x in keep], int(g.num_types), int(g.num_rels),
+                     0, None)
+    n, ne = U32(), U64()
+    dp = _ptr(d) if d.shape[0] else None
+    R, V, E = int(g.num_rels), int(g.num_vertices), int(ro[-1])
+    a = {k: np.zeros(max(E, 1), np.uint32) for k in ("src", "rel", "dst", "wout", "win")}  # bounds: one call
+    group = np.zeros(V, np.uint32)
+    wnode = np.zeros(max(2 * R * V, 1), np.uint32)
+    _check(lib().gs_compress_host(ctypes.byref(desc), d.shape[0], dp, ctypes.byref(n), ctypes.byref(ne), _ptr(group),
+                                  _ptr(a["src"]), _ptr(a["rel"]), _ptr(a["dst"]), _ptr(a["wout"]), _ptr(a["win"]),
+                                  _ptr(wnode)))
+    out = {k: v[: ne.value] for k, v in a.items()}
+    out["group"] = group
+    out["nodes"] = n.value
+    out["wnode"] = wnode[: 2 * R * n.value].reshape(2, R, n.value)
+    return out
+
+
+class CompressedGraph:
+    """A data graph and its multi-level compression (Section 3.4), both
+    device-resident; queries matched through it give the data graph's
+    embeddings (Section 3.5)."""
+
+    def __init__(self, g, deltas):
+        d = np.ascontiguousarray(np.asarray(list(deltas), np.float64))
+        ro = np.ascontiguousarray(np.asarray(g.row_offsets, dtype=np.uint64))
+        keep = (ro, _u32(g.col_targets), _u32(g.edge_rel), _u32(g.vertex_type))
+        desc = GraphDesc(int(g.num_vertices), int(ro[-1]), *[_ptr(x) for x in keep], int(g.num_types),
+                         int(g.num_rels), 0, None)
+        self._h = P()
+        self.num_vertices, self.num_rels = int(g.num_vertices), int(g.num_rels)
+        _check(lib().gs_cgraph_build(ctypes.byref(desc), d.shape[0], _ptr(d) if d.shape[0] else None,
+                                     ctypes.byref(self._h)))
+        del keep
+
+    def info(self) -> dict:
+        i = CGraphInfo()
+        _check(lib().gs_cgraph_get_info(self._h, ctypes.byref(i)))
+        return {"levels": i.levels, "vertices": i.vertices, "edges": i.edges, "nodes": i.nodes,
+                "weighted_edges": i.weighted_edges, "inner_edges": i.inner_edges, "ratio": i.ratio}
+
+    def export(self) -> dict:
+        """The compression: node of each vertex, weighted edges and weights."""
+        i = self.info()
+        V, n, ne, R = i["vertices"], i["nodes"], i["weighted_edges"], self.num_rels
+        a = {k: np.zeros(max(ne, 1), np.uint32) for k in ("src", "rel", "dst", "wout", "win")}
+        group = np.zeros(V, np.uint32)
+        wnode = np.zeros(max(2 * R * n, 1), np.uint32)
+        _check(lib().gs_cgraph_export(self._h, _ptr(group), _ptr(a["src"]), _ptr(a["rel"]), _ptr(a["dst"]),
+                                      _ptr(a["wout"]), _ptr(a["win"]), _ptr(wnode)))
+        out = {k: v[:ne] for k, v in a.items()}
+        out["group"] = group
+        out["wnode"] = wnode[: 2 * R * n].reshape(2, R, n)
+        return out
+
+    def candidates(self, q) -> list[np.ndarray]:
+        """Weighted-graph candidate sets of q after refinement to the fixpoint."""
+        pack = _QueryPack([q])
+        k = len(q.vtype)
+        off = np.zeros(k + 1, np.uint64)
+        n = U64()
+        _check(lib().gs_cgraph_candidates(self._h, pack.arr, _ptr(off), None, 0, ctypes.byref(n)))
+        ids = np.zeros(max(n.value, 1), np.uint32)
+        _check(lib().gs_cgraph_candidates(self._h, pack.arr, _ptr(off), _ptr(ids), ids.shape[0], ctypes.byref(n)))
+        return [ids[int(off[u]):int(off[u + 1])].copy() for u in range(k)]
+
+    def match_batch(self, queries, cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, project=None,
+                    refine=0) -> list[MatchResult]:
+        pack = _QueryPack(queries)
+        o = _opts(cap, mode, max_refine_rounds, 0, project=project, refine=refine)
+        res = (ResultDesc * max(len(queries), 1))()
+        _check(lib().gs_match_batch_compressed(self._h, pack.arr, len(queries), ctypes.byref(o), res))
+        return _take_all(res, len(queries))
+
+    def free(self):
+        if self._h:
+            lib().gs_cgraph_free(self._h)
+            self._h = P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def debug_fail_alloc(after: int) -> None:
+    """Make the library's device allocation after `after` more succeed
+    fail as out-of-memory (one-shot; negative disarms)."""
+    lib().gs_debug_fail_alloc(after)
+
+
+def debug_fail_serve_wait(n: int) -> None:
+    """Make the serving worker's next n completion checks report a CUDA error."""
+    lib().gs_debug_fail_serve_wait(n)
 
 
 class Server:

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libgs.so")
 BUILD = os.path.join(PKG, "_build")
-SOURCES = ["gs_prims.cu", "gs_graph.cu", "gs_kernels.cu", "gs_engine.cu", "gs_inspect.cu", "gs_fallback.cu", "gs_serve.cu", "gs_static.cu", "gs_tune.cu", "gs_khop.cu"]
+SOURCES = ["gs_prims.cu", "gs_graph.cu", "gs_kernels.cu", "gs_engine.cu", "gs_inspect.cu", "gs_fallback.cu", "gs_serve.cu", "gs_static.cu", "gs_tune.cu", "gs_khop.cu", "gs_compress.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -114,7 +114,7 @@ namespace gs {
 template <typename T>
 static gs_status dalloc(gs_batch *b, T **p, uint64_t count) {
   void *q = nullptr;
-  cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+  cudaError_t e = gs::dev_malloc(&q, sizeof(T) * (count ? count : 1));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (batch pools)");
   b->allocs.push_back(q);
   *p = static_cast<T *>(q);
@@ -239,6 +239,10 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   A(W.tlist_q, s.tlist);
   A(W.alist_q, s.alist);
   A(W.fcnt, W.nq);
+  A(W.xneed, s.tlist);
+  A(W.xfound, s.tlist);
+  W.xq_cap = std::min<uint64_t>(std::max<uint64_t>(s.tlist / 4, 1ull << 12), 1ull << 20);
+  A(W.xq, W.xq_cap);
   if ((uint64_t)W.nqv * cps >= (1ull << 32)) return fail(GS_ERR_UNSUPPORTED, "batch too large for the chunk index");
   A(W.clist, (uint64_t)W.nqv * cps);
   A(W.fscan, (uint64_t)W.nq + 1);
@@ -299,6 +303,15 @@ static gs_status batch_upload(gs_batch *b) {
   GS_CUDA(cudaMemcpyAsync(b->dwaves, b->waves.data(), sizeof(WaveDesc) * b->waves.size(), cudaMemcpyHostToDevice,
                           b->stream));
   return GS_OK;
+}
+
+gs_status batch_set_wmasks(gs_batch *b, const uint64_t *wmask, uint32_t wstride, const uint32_t *wgroup) {
+  for (uint32_t i = 0; i < b->n; ++i) {
+    b->hq[i].wmask = wmask[i];
+    b->hq[i].wstride = wstride;
+    b->hq[i].wgroup = (uint64_t)(uintptr_t)wgroup;
+  }
+  return batch_upload(b);
 }
 
 // Greedy waves of consecutive queries within the slot capacities.
@@ -585,6 +598,10 @@ static void harvest_events(gs_batch *b, std::vector<gs_batch::Ev> &evs, bool des
 // is not captured and an exact fixpoint is asked for).
 gs_status refine_to_fixpoint(gs_batch *b) {
   uint32_t changed[kMaxRounds];
+  if (b->refine_rounds == 0) {  // a batch set to skip refinement ran no round yet
+    b->refine_rounds = 1;
+    launch_refine_rounds(b, b->W, b->max_k, b->stream);
+  }
   for (;;) {
     GS_CUDA(cudaMemcpyAsync(changed, b->W.ctrl->changed, sizeof(changed), cudaMemcpyDeviceToHost, b->stream));
     GS_CUDA(cudaStreamSynchronize(b->stream));
@@ -739,7 +756,7 @@ gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_mat
   b->n_cap = std::max<uint32_t>(n, 1);
   opts_key(b, opts);
   if (g->tuned_group) b->group = g->tuned_group;
-  if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds;
+  if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds == GS_ROUNDS_NONE ? 0 : g->tuned_rounds;
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
     b->fixpoint = false;
@@ -808,7 +825,7 @@ gs_status batch_create_capacity(gs_graph *g, const gs_match_opts *opts, uint32_t
   b->n_cap = std::max<uint32_t>(n_cap, 1);
   opts_key(b, opts);
   if (g->tuned_group) b->group = g->tuned_group;
-  if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds;
+  if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds == GS_ROUNDS_NONE ? 0 : g->tuned_rounds;
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
     b->fixpoint = false;
@@ -880,7 +897,7 @@ template <typename T>
 static gs_status regrow(gs_batch *b, T **p, uint64_t count) {
   void *old = *p;
   void *q = nullptr;
-  cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+  cudaError_t e = gs::dev_malloc(&q, sizeof(T) * (count ? count : 1));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return GS_ERR_OOM;  // keep the old pool; overflowing queries keep taking the fallback path
@@ -979,7 +996,14 @@ gs_status batch_finish(gs_batch *b) {
   GS_CUDA(cudaMemcpyAsync(&top, &b->W.ctrl->store_top, 8, cudaMemcpyDeviceToHost, b->stream));
   GS_CUDA(cudaMemcpyAsync(&scan_err, scan_error_word(b->scan_tmp), 4, cudaMemcpyDeviceToHost, b->stream));
   GS_CUDA(cudaStreamSynchronize(b->stream));
-  if (scan_err) return fail(GS_ERR_CUDA, "a prefix scan gave up waiting on a predecessor tile; results are invalid");
+  if (scan_err) {
+    // the scans stayed exact (a wait that gives up sums its inputs directly),
+    // but a bounded device wait ran out: report it and clear the record so
+    // that later runs on this batch start clean
+    GS_CUDA(cudaMemsetAsync(b->scan_tmp, 0, 4, b->stream));
+    GS_CUDA(cudaStreamSynchronize(b->stream));
+    return fail(GS_ERR_TIMEOUT, "a prefix scan's look-back wait reached its bound");
+  }
   b->rows.resize(top);
   b->d2h_bytes += 36ull * n + 8 + 4ull * top;
   if (top) {
@@ -1007,7 +1031,12 @@ gs_status batch_finish(gs_batch *b) {
   return GS_OK;
 }
 
-gs_status batch_fetch(gs_batch *b, gs_result *outs) {
+gs_status batch_fetch(gs_batch *b, gs_result *outs) { return batch_fetch_views(b, outs, nullptr); }
+
+// Results of a finished run; with `store` (the buffer that holds the run's
+// rows as batch_finish copied them) the results' rows point into it
+// (shared = 1) instead of being copied.
+gs_status batch_fetch_views(gs_batch *b, gs_result *outs, uint32_t *store) {
   if (!b->finished) return fail(GS_ERR_INVALID, "gs_batch_fetch: call gs_batch_finish first");
   for (uint32_t i = 0; i < b->n; ++i) {
     gs_result &r = outs[i];
@@ -1042,7 +1071,10 @@ gs_status batch_fetch(gs_batch *b, gs_result *outs) {
       if (st == QS_EMPTY) { r.count = 0; r.fingerprint = 0; r.truncated = 0; }
       r.num_rows = b->nrows[i] & ~kRowsMore;
       if (proj && cap && (b->nrows[i] & kRowsMore)) r.truncated = 1;
-      if (r.num_rows) {
+      if (r.num_rows && store) {
+        r.rows = store + b->word_off[i];
+        r.shared = 1;
+      } else if (r.num_rows) {
         const uint64_t words = r.num_rows * r.k;
         r.rows = static_cast<uint32_t *>(malloc(4 * words));
         memcpy(r.rows, b->rows.data() + b->word_off[i], 4 * words);
@@ -1127,7 +1159,10 @@ extern "C" gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_
   drop_graphs(b);
   b->use_graph = use_graph != 0;
   b->group = group;
-  if (refine_rounds) {
+  if (refine_rounds == GS_ROUNDS_NONE) {
+    b->refine_rounds = 0;
+    b->fixpoint = false;
+  } else if (refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(refine_rounds, kMaxRounds);
     b->fixpoint = false;
   } else {
@@ -1136,6 +1171,14 @@ extern "C" gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_
   }
   return GS_OK;
 }
+
+extern "C" gs_status gs_batch_set_wait(gs_batch *b, uint32_t max_polls, uint32_t flags) {
+  if (!b) return fail(GS_ERR_INVALID, "gs_batch_set_wait: null batch");
+  if (flags & ~GS_WAIT_WITHHOLD_FIRST_TILE) return fail(GS_ERR_INVALID, "gs_batch_set_wait: unknown flags");
+  return scan_set_wait(b->scan_tmp, max_polls, flags & GS_WAIT_WITHHOLD_FIRST_TILE, b->stream);
+}
+
+extern "C" void gs_debug_fail_alloc(int64_t after) { debug_fail_alloc(after); }
 
 namespace gs {
 
@@ -1152,6 +1195,27 @@ static MatchCache *cache_of(gs_graph *g) {
   std::lock_guard<std::mutex> lk(init_mu);
   if (!g->cache) g->cache = new MatchCache();
   return static_cast<MatchCache *>(g->cache);
+}
+
+// A batch of the cache re-armed with the queries, or a new one (the oldest
+// of four is dropped).
+static gs_status cached_batch(gs_graph *g, MatchCache *c, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
+                              gs_batch **out) {
+  for (gs_batch *x : c->batches)
+    if (batch_rearm(x, qs, n, opts)) {
+      *out = x;
+      return GS_OK;
+    }
+  gs_batch *b = nullptr;
+  gs_status st = batch_create(g, qs, n, opts, 0, &b);
+  if (st != GS_OK) return st;
+  if (c->batches.size() >= 4) {
+    batch_destroy(c->batches.front());
+    c->batches.erase(c->batches.begin());
+  }
+  c->batches.push_back(b);
+  *out = b;
+  return GS_OK;
 }
 
 void release_cache(gs_graph *g) {
@@ -1172,17 +1236,8 @@ extern "C" gs_status gs_match_batch(gs_graph *g, const gs_query *qs, uint32_t n,
   MatchCache *c = cache_of(g);
   std::lock_guard<std::mutex> lk(c->mu);
   gs_batch *b = nullptr;
-  for (gs_batch *x : c->batches)
-    if (batch_rearm(x, qs, n, opts)) { b = x; break; }
-  if (!b) {
-    gs_status st = batch_create(g, qs, n, opts, 0, &b);
-    if (st != GS_OK) return st;
-    if (c->batches.size() >= 4) {
-      batch_destroy(c->batches.front());
-      c->batches.erase(c->batches.begin());
-    }
-    c->batches.push_back(b);
-  }
+  gs_status cst = cached_batch(g, c, qs, n, opts, &b);
+  if (cst != GS_OK) return cst;
   const uint64_t d0 = b->d2h_bytes;
   c->h2d += b->last_upload_bytes;
   gs_status st = run_waves(b);
@@ -1226,9 +1281,88 @@ extern "C" gs_status gs_match(gs_graph *g, const gs_query *q, const gs_match_opt
 
 extern "C" void gs_result_free(gs_result *r) {
   if (!r) return;
-  free(r->rows);
+  if (!r->shared) free(r->rows);
   r->rows = nullptr;
   r->num_rows = 0;
+}
+
+// Blocks of page-locked host memory handed out by gs_match_batch_shared:
+// a released block goes back to a small process-wide pool, from which a
+// batch takes its next result buffer, so a steady stream of calls
+// allocates no page-locked memory.
+struct gs_rows {
+  uint32_t *p = nullptr;
+  size_t cap = 0;      // words
+  uint64_t words = 0;  // words written by the call
+};
+
+namespace {
+std::mutex g_rows_mu;
+std::vector<gs_rows *> g_rows_pool;
+constexpr size_t kRowsPoolMax = 4;
+}  // namespace
+
+extern "C" const uint32_t *gs_rows_base(const gs_rows *block) { return block ? block->p : nullptr; }
+extern "C" uint64_t gs_rows_words(const gs_rows *block) { return block ? block->words : 0; }
+
+extern "C" void gs_rows_release(gs_rows *block) {
+  if (!block) return;
+  std::lock_guard<std::mutex> lk(g_rows_mu);
+  if (g_rows_pool.size() < kRowsPoolMax) {
+    g_rows_pool.push_back(block);
+    return;
+  }
+  if (block->p) cudaFreeHost(block->p);
+  delete block;
+}
+
+extern "C" gs_status gs_match_batch_shared(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
+                                           gs_result *outs, gs_rows **block) {
+  if (!block) return fail(GS_ERR_INVALID, "gs_match_batch_shared: null block");
+  *block = nullptr;
+  if (!g || !outs || (n && !qs)) return fail(GS_ERR_INVALID, "gs_match_batch_shared: null argument");
+  if (n == 0) return GS_OK;
+  GS_CUDA(cudaSetDevice(g->device));
+  MatchCache *c = cache_of(g);
+  std::lock_guard<std::mutex> lk(c->mu);
+  gs_batch *b = nullptr;
+  gs_status st = cached_batch(g, c, qs, n, opts, &b);
+  if (st != GS_OK) return st;
+  const uint64_t d0 = b->d2h_bytes;
+  c->h2d += b->last_upload_bytes;
+  st = run_waves(b);
+  b->ran = st == GS_OK;
+  if (st == GS_OK) st = batch_finish(b);
+  if (st != GS_OK) return st;
+  // the results point into the batch's result buffer, which the call hands
+  // over; the batch takes a pooled buffer for its next run
+  gs_rows *blk = new gs_rows();
+  blk->p = b->rows.p;
+  blk->cap = b->rows.cap;
+  blk->words = b->rows.n;
+  {
+    std::lock_guard<std::mutex> pl(g_rows_mu);
+    gs_rows *spare = nullptr;
+    if (!g_rows_pool.empty()) {
+      spare = g_rows_pool.back();
+      g_rows_pool.pop_back();
+    }
+    b->rows.p = spare ? spare->p : nullptr;
+    b->rows.cap = spare ? spare->cap : 0;
+    b->rows.n = 0;
+    delete spare;
+  }
+  st = batch_fetch_views(b, outs, blk->p);
+  for (uint32_t i = 0; i < n && st == GS_OK; ++i) b->d2h_bytes += 4ull * outs[i].num_rows * outs[i].k;
+  c->d2h += b->d2h_bytes - d0;
+  bool any = false;
+  for (uint32_t i = 0; i < n && st == GS_OK; ++i) any = any || outs[i].shared;
+  if (st != GS_OK || !any) {
+    gs_rows_release(blk);
+    return st;
+  }
+  *block = blk;
+  return GS_OK;
 }
 
 extern "C" gs_status gs_results_copy_rows(const gs_result *r, uint32_t n, uint32_t *dst) {

@@ -75,6 +75,12 @@ struct DQuery {
   uint8_t from_src[kMaxM];          // edge-table orientation (1: keyed by esrc)
   uint32_t xinc[2 * kMaxM];         // incident edges packed by the plan (xinc_pack), same order as inc_edge
   uint32_t status;
+  // Matching through a compressed graph (Section 3.5): data vertex v may be
+  // a candidate of u only if its weighted node wgroup[v] is set in u's
+  // weighted-graph candidate bitmap, wmask + u * wstride words (device
+  // addresses; wmask = 0: no restriction).
+  uint32_t wstride;
+  uint64_t wmask, wgroup;
 };
 
 // Packed incident edge: bit 0 direction (0: u is the source), bits 1-8
@@ -180,6 +186,16 @@ struct Ctrl {
   uint64_t over_cap;                // large outputs with more rows than cap (selected before sorting)
   uint64_t fin_words;               // words of the rows returned by this wave
   uint64_t bytes[KK_N];             // algorithmic bytes per kernel kind
+  uint64_t xq_top;                  // exploration: chunks of long relation runs queued this step
+};
+
+// A piece of a long relation run that exploration hands to a second launch:
+// entries [lo, lo + len) of the adjacency row of candidate tlist[it], over its
+// incident edge `inc` (position in u's incident list).
+struct XChunk {
+  uint32_t it, inc;
+  uint64_t lo;
+  uint32_t len, pad;
 };
 
 // Everything a kernel needs, passed by value.  Capacities are fixed when the
@@ -209,6 +225,8 @@ struct Wave {
   uint32_t *alist; uint64_t alist_cap;   // every set before refinement
   uint32_t *tlist_q, *alist_q;           // owner of each entry: query / global query vertex
   uint32_t *fcnt; uint64_t *fscan;       // filter work items per query [nq] and their scan [nq + 1]
+  uint32_t *xneed, *xfound;              // per exploration item: incident edges whose runs were queued / found
+  XChunk *xq; uint64_t xq_cap;           // queued chunks of long relation runs
   uint64_t *clist;                       // non-empty chunks of a compaction: (gqv << 32) | count index
   uint32_t *flist; uint64_t flist_cap;   // final sets
   uint64_t *flist_off;              // [nqv]

@@ -171,7 +171,7 @@ void release_fallback(gs_graph *g) {
 template <typename T>
 static gs_status falloc(Fallback *f, T **p, uint64_t n) {
   void *q = nullptr;
-  cudaError_t e = cudaMalloc(&q, sizeof(T) * (n ? n : 1));
+  cudaError_t e = gs::dev_malloc(&q, sizeof(T) * (n ? n : 1));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (fallback buffers)");
   f->allocs.push_back(q);
   *p = static_cast<T *>(q);
@@ -246,10 +246,13 @@ static gs_status ensure_top(Fallback *f, uint64_t rows, uint32_t k) {
   if (st != GS_OK) return st;
   // radix scratch for `rows` items
   void *t = nullptr;
-  cudaError_t e = cudaMalloc(&t, sizeof(uint64_t) * radix_tmp_words(rows));
+  cudaError_t e = gs::dev_malloc(&t, sizeof(uint64_t) * radix_tmp_words(rows));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (fallback sort scratch)");
   e = cudaMemset(t, 0, sizeof(uint64_t) * radix_tmp_words(rows));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset (fallback sort scratch)");
+  if (e != cudaSuccess) {
+    cudaFree(t);
+    return cuda_fail(e, "cudaMemset (fallback sort scratch)");
+  }
   f->allocs.erase(std::remove(f->allocs.begin(), f->allocs.end(), (void *)f->tmp), f->allocs.end());
   cudaFree(f->tmp);
   f->tmp = static_cast<uint64_t *>(t);

@@ -12,6 +12,7 @@
 //     condition, read per direction and relation, plus one plane per
 //     direction over all relations).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -28,6 +29,26 @@ gs_status fail(gs_status st, const std::string &msg) {
   set_error(msg);
   return st;
 }
+namespace {
+std::atomic<int64_t> g_fail_alloc_after{-1};  // allocations left before the armed failure; -1 = none
+}
+
+void debug_fail_alloc(int64_t after) { g_fail_alloc_after.store(after < 0 ? -1 : after); }
+
+cudaError_t dev_malloc_bytes(void **p, size_t bytes) {
+  int64_t left = g_fail_alloc_after.load(std::memory_order_relaxed);
+  while (left >= 0) {
+    if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+      if (left == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 gs_status cuda_fail(cudaError_t e, const char *what) {
   set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
@@ -239,17 +260,18 @@ static gs_status build_direction(uint32_t V, uint32_t R, uint64_t n, uint32_t *k
   uint64_t total = 0;
   GS_CUDA(cudaMemcpyAsync(&total, scan_buf + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaStreamSynchronize(s));
-  uint32_t *adj = nullptr, *crow = nullptr;
-  GS_CUDA(cudaMalloc(&adj, sizeof(uint32_t) * (total ? total : 1)));
-  GS_CUDA(cudaMalloc(&crow, sizeof(uint32_t) * (total ? total : 1)));
+  DevBuf adj_b, crow_b, off_b;  // freed on an early return, handed out at the end
+  GS_CUDA(gs::dev_malloc(&adj_b.p, sizeof(uint32_t) * (total ? total : 1)));
+  GS_CUDA(gs::dev_malloc(&crow_b.p, sizeof(uint32_t) * (total ? total : 1)));
+  uint32_t *adj = adj_b.as<uint32_t>(), *crow = crow_b.as<uint32_t>();
   k_compact_triples<<<blocks_for(n), kT, 0, s>>>(n, row, packed, keep, scan_buf, crow, adj);
   (void)fpacked;
   // offsets
   uint32_t *cnt = frow;  // keep flags no longer needed after compaction
   GS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (V + 1), s));
   k_row_count<<<blocks_for(total), kT, 0, s>>>(total, crow, cnt);
-  uint64_t *off = nullptr;
-  GS_CUDA(cudaMalloc(&off, sizeof(uint64_t) * (V + 1)));
+  GS_CUDA(gs::dev_malloc(&off_b.p, sizeof(uint64_t) * (V + 1)));
+  uint64_t *off = off_b.as<uint64_t>();
   uint64_t nv = V;
   GS_CUDA(cudaMemcpyAsync(d_n, &nv, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
   scan_u32(cnt, off, d_n, V, stmp, s, sms);
@@ -258,6 +280,7 @@ static gs_status build_direction(uint32_t V, uint32_t R, uint64_t n, uint32_t *k
   *off_out = off;
   *adj_out = adj;
   *row_out = crow;
+  off_b.p = adj_b.p = crow_b.p = nullptr;
   *kept = total;
   return GS_OK;
 }
@@ -265,6 +288,11 @@ static gs_status build_direction(uint32_t V, uint32_t R, uint64_t n, uint32_t *k
 }  // namespace gs
 
 using namespace gs;
+
+static gs_status build_graph(gs_graph *g, uint32_t V, uint64_t E, uint32_t T, uint32_t R, uint64_t nmax,
+                             cudaStream_t s, int sms, DevBuf &ro, DevBuf &col, DevBuf &rel, DevBuf &vt, DevBuf &k0,
+                             DevBuf &v0, DevBuf &k1, DevBuf &v1, DevBuf &scanb, DevBuf &tmpb, DevBuf &stmpb,
+                             DevBuf &dn);
 
 extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   if (!desc || !out) return fail(GS_ERR_INVALID, "gs_graph_load: null argument");
@@ -286,10 +314,10 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   const uint64_t En = E ? E : 1;
 
   DevBuf ro, col, rel, vt, k0, v0, k1, v1, scanb, tmpb, stmpb, dn, err;
-  GS_CUDA(cudaMalloc(&ro.p, sizeof(uint64_t) * (V + 1)));
-  GS_CUDA(cudaMalloc(&col.p, sizeof(uint32_t) * En));
-  GS_CUDA(cudaMalloc(&rel.p, sizeof(uint32_t) * En));
-  GS_CUDA(cudaMalloc(&vt.p, sizeof(uint32_t) * V));
+  GS_CUDA(gs::dev_malloc(&ro.p, sizeof(uint64_t) * (V + 1)));
+  GS_CUDA(gs::dev_malloc(&col.p, sizeof(uint32_t) * En));
+  GS_CUDA(gs::dev_malloc(&rel.p, sizeof(uint32_t) * En));
+  GS_CUDA(gs::dev_malloc(&vt.p, sizeof(uint32_t) * V));
   cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   GS_CUDA(cudaMemcpyAsync(ro.p, desc->row_offsets, sizeof(uint64_t) * (V + 1), kind, s));
   if (E) {
@@ -297,7 +325,7 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
     GS_CUDA(cudaMemcpyAsync(rel.p, desc->edge_rel, sizeof(uint32_t) * E, kind, s));
   }
   GS_CUDA(cudaMemcpyAsync(vt.p, desc->vertex_type, sizeof(uint32_t) * V, kind, s));
-  GS_CUDA(cudaMalloc(&err.p, sizeof(uint32_t)));
+  GS_CUDA(gs::dev_malloc(&err.p, sizeof(uint32_t)));
   GS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(uint32_t), s));
   k_validate<<<blocks_for(V > E ? V : E), kT, 0, s>>>(V, E, ro.as<uint64_t>(), col.as<uint32_t>(), rel.as<uint32_t>(),
                                                        vt.as<uint32_t>(), T, R, err.as<uint32_t>());
@@ -310,36 +338,96 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   if (herr & 8) return fail(GS_ERR_INVALID, "vertex_type holds a type >= num_types");
 
   const uint64_t nmax = En > V + 1 ? En : V + 1;
-  GS_CUDA(cudaMalloc(&k0.p, sizeof(uint32_t) * nmax));
-  GS_CUDA(cudaMalloc(&v0.p, sizeof(uint32_t) * nmax));
-  GS_CUDA(cudaMalloc(&k1.p, sizeof(uint32_t) * nmax));
-  GS_CUDA(cudaMalloc(&v1.p, sizeof(uint32_t) * nmax));
-  GS_CUDA(cudaMalloc(&scanb.p, sizeof(uint64_t) * (nmax + 1)));
+  GS_CUDA(gs::dev_malloc(&k0.p, sizeof(uint32_t) * nmax));
+  GS_CUDA(gs::dev_malloc(&v0.p, sizeof(uint32_t) * nmax));
+  GS_CUDA(gs::dev_malloc(&k1.p, sizeof(uint32_t) * nmax));
+  GS_CUDA(gs::dev_malloc(&v1.p, sizeof(uint32_t) * nmax));
+  GS_CUDA(gs::dev_malloc(&scanb.p, sizeof(uint64_t) * (nmax + 1)));
   uint64_t tw = radix_tmp_words(nmax);
   uint64_t sw = scan_tmp_words(nmax);
-  GS_CUDA(cudaMalloc(&tmpb.p, sizeof(uint64_t) * tw));   // radix sort scratch
-  GS_CUDA(cudaMalloc(&stmpb.p, sizeof(uint64_t) * sw));  // scan scratch
+  GS_CUDA(gs::dev_malloc(&tmpb.p, sizeof(uint64_t) * tw));   // radix sort scratch
+  GS_CUDA(gs::dev_malloc(&stmpb.p, sizeof(uint64_t) * sw));  // scan scratch
   GS_CUDA(cudaMemsetAsync(tmpb.p, 0, sizeof(uint64_t) * tw, s));
   GS_CUDA(cudaMemsetAsync(stmpb.p, 0, sizeof(uint64_t) * sw, s));
-  GS_CUDA(cudaMalloc(&dn.p, sizeof(uint64_t)));
+  GS_CUDA(gs::dev_malloc(&dn.p, sizeof(uint64_t)));
   GS_CUDA(cudaMemcpyAsync(dn.p, &E, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
 
   gs_graph *g = new gs_graph();
   memset(g, 0, sizeof(*g));
   g->device = dev;
   g->num_sms = sms;
-  auto cleanup = [&](gs_status st) {
-    gs_graph_free(g);
+  gs_status st = build_graph(g, V, E, T, R, nmax, s, sms, ro, col, rel, vt, k0, v0, k1, v1, scanb, tmpb, stmpb, dn);
+  if (st != GS_OK) {
+    gs_graph_free(g);  // frees whatever the build had attached to g
     return st;
-  };
+  }
+  *out = g;
+  return GS_OK;
+}
 
+// Tables derived from the signature planes and neighbour-type masks: the
+// same planes in type-list order (sig_t, tmask_t; needs the type lists) and
+// the signature statistics of the plan, sigge[(t * P + p) * 16 + c] =
+// vertices of type t (t = T: any type) whose count in plane p is at least c.
+// With alloc the three arrays are allocated (graph load), else rewritten in
+// place (after the signatures were replaced).
+static gs_status derive_sig_tables(gs_graph *g, uint32_t V, uint32_t T, uint64_t P, uint64_t sig_words, cudaStream_t s,
+                                   bool alloc) {
+  if (alloc && (gs::dev_malloc(&g->sig_t, sizeof(uint32_t) * sig_words * P) != cudaSuccess ||
+                gs::dev_malloc(&g->tmask_t, sizeof(uint32_t) * (uint64_t)V * P) != cudaSuccess))
+    return fail(GS_ERR_OOM, "type-ordered planes");
+  GS_CUDA(cudaMemsetAsync(g->sig_t, 0, sizeof(uint32_t) * sig_words * P, s));
+  k_type_order<<<blocks_for((V + 7) / 8 * P), kT, 0, s>>>(V, (uint32_t)P, g->tvid, g->sig, sig_words, g->tmask,
+                                                         g->sig_t, g->tmask_t);
+  const uint64_t nh = (uint64_t)(T + 1) * P * 16;
+  DevBuf dh_b;
+  GS_CUDA(gs::dev_malloc(&dh_b.p, sizeof(uint32_t) * nh));
+  uint32_t *dh = dh_b.as<uint32_t>();
+  GS_CUDA(cudaMemsetAsync(dh, 0, sizeof(uint32_t) * nh, s));
+  const dim3 grid((unsigned)std::min<uint64_t>((V + 255) / 256, 64), (unsigned)P);
+  k_sig_hist<<<grid, 256, 0, s>>>(V, T, (uint32_t)P, g->vtype, g->sig, sig_words, dh);
+  std::vector<uint32_t> hh(nh);
+  GS_CUDA(cudaMemcpyAsync(hh.data(), dh, sizeof(uint32_t) * nh, cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  for (uint64_t row = 0; row < (uint64_t)(T + 1) * P; ++row)
+    for (int c = 14; c >= 0; --c) hh[row * 16 + c] += hh[row * 16 + c + 1];
+  if (alloc && gs::dev_malloc(&g->sigge, sizeof(uint32_t) * nh) != cudaSuccess)
+    return fail(GS_ERR_OOM, "signature statistics");
+  GS_CUDA(cudaMemcpyAsync(g->sigge, hh.data(), sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  return GS_OK;
+}
+
+gs_status gs::graph_set_signatures(gs_graph *g, const uint8_t *counts) {
+  const DevGraph &d = g->d;
+  const uint64_t P = 2ull * d.R + 2, V = d.V;
+  std::vector<uint32_t> words(P * d.sig_words, 0);
+  for (uint64_t p = 0; p < P; ++p)
+    for (uint64_t v = 0; v < V; ++v) {
+      const uint32_t c = counts[p * V + v] > 15 ? 15u : counts[p * V + v];
+      words[p * d.sig_words + (v >> 3)] |= c << ((v & 7) * 4);
+    }
+  GS_CUDA(cudaMemcpy(g->sig, words.data(), sizeof(uint32_t) * words.size(), cudaMemcpyHostToDevice));
+  return derive_sig_tables(g, d.V, d.T, P, d.sig_words, nullptr, false);
+}
+
+// Everything after the inputs are validated and the work buffers exist:
+// on an error return, g holds only buffers gs_graph_free releases, and every
+// temporary is released here.
+static gs_status build_graph(gs_graph *g, uint32_t V, uint64_t E, uint32_t T, uint32_t R, uint64_t nmax,
+                             cudaStream_t s, int sms, DevBuf &ro, DevBuf &col, DevBuf &rel, DevBuf &vt, DevBuf &k0,
+                             DevBuf &v0, DevBuf &k1, DevBuf &v1, DevBuf &scanb, DevBuf &tmpb, DevBuf &stmpb,
+                             DevBuf &dn) {
+  auto cleanup = [](gs_status st) { return st; };
   k_expand<<<blocks_for(V), kT, 0, s>>>(V, ro.as<uint64_t>(), col.as<uint32_t>(), rel.as<uint32_t>(), k0.as<uint32_t>(),
                                         v0.as<uint32_t>());
+  DevBuf src_rows_b, dst_rows_b;
   uint32_t *src_rows = nullptr;
   uint64_t kept = 0;
   gs_status st = build_direction(V, R, E, k0.as<uint32_t>(), v0.as<uint32_t>(), k1.as<uint32_t>(), v1.as<uint32_t>(),
                                  scanb.as<uint64_t>(), tmpb.as<uint64_t>(), stmpb.as<uint64_t>(), dn.as<uint64_t>(), s, sms, &g->off_out,
                                  &g->adj_out, &src_rows, &kept);
+  src_rows_b.p = src_rows;
   if (st != GS_OK) return cleanup(st);
   // incoming direction from the kept triples
   GS_CUDA(cudaMemcpyAsync(dn.p, &kept, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
@@ -349,6 +437,7 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   st = build_direction(V, R, kept, k0.as<uint32_t>(), v0.as<uint32_t>(), k1.as<uint32_t>(), v1.as<uint32_t>(),
                        scanb.as<uint64_t>(), tmpb.as<uint64_t>(), stmpb.as<uint64_t>(), dn.as<uint64_t>(), s, sms, &g->off_in, &g->adj_in,
                        &dst_rows, &kept_in);
+  dst_rows_b.p = dst_rows;
   // distinct neighbours over all relations, per direction
   for (int d = 0; d < 2 && st == GS_OK; ++d) {
     const uint64_t n = d == 0 ? kept : kept_in;
@@ -362,15 +451,13 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
                          d == 0 ? &g->off_aout : &g->off_ain, d == 0 ? &g->adj_aout : &g->adj_ain, &rows, &kept_any);
     cudaFree(rows);
   }
-  cudaFree(src_rows);
-  cudaFree(dst_rows);
   if (st != GS_OK) return cleanup(st);
   const uint64_t P = 2ull * R + 2;  // signature / mask planes
 
   // Planes hold whole 16-byte groups (32 vertices) so the filter can read
   // them as aligned uint4 vectors up to the last partial group.
   const uint64_t sig_words = ((V + 7) / 8 + 3) / 4 * 4;
-  if (cudaMalloc(&g->sig, sizeof(uint32_t) * sig_words * P) != cudaSuccess)
+  if (gs::dev_malloc(&g->sig, sizeof(uint32_t) * sig_words * P) != cudaSuccess)
     return cleanup(fail(GS_ERR_OOM, "signature planes"));
   GS_CUDA(cudaMemsetAsync(g->sig, 0, sizeof(uint32_t) * sig_words * P, s));
   k_signatures<<<blocks_for(V), kT, 0, s>>>(V, g->off_out, g->adj_out, 0, g->sig, sig_words);
@@ -378,10 +465,11 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   k_signatures<<<blocks_for(V), kT, 0, s>>>(V, g->off_aout, g->adj_aout, 2 * R, g->sig, sig_words);
   k_signatures<<<blocks_for(V), kT, 0, s>>>(V, g->off_ain, g->adj_ain, 2 * R + 1, g->sig, sig_words);
   const uint64_t vt_bytes = ((uint64_t)V + 127) / 128 * 128;  // whole 32-vertex groups, zero padded
-  if (cudaMalloc(&g->vtype, vt_bytes) != cudaSuccess) return cleanup(fail(GS_ERR_OOM, "types"));
+  if (gs::dev_malloc(&g->vtype, vt_bytes) != cudaSuccess) return cleanup(fail(GS_ERR_OOM, "types"));
   GS_CUDA(cudaMemsetAsync(g->vtype, 0, vt_bytes, s));
-  uint32_t *hist = nullptr;
-  GS_CUDA(cudaMalloc(&hist, sizeof(uint32_t) * T));
+  DevBuf hist_b;
+  GS_CUDA(gs::dev_malloc(&hist_b.p, sizeof(uint32_t) * T));
+  uint32_t *hist = hist_b.as<uint32_t>();
   GS_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * T, s));
   k_types<<<blocks_for(V), kT, 0, s>>>(V, vt.as<uint32_t>(), g->vtype, hist);
   g->type_count = new uint32_t[T];
@@ -391,14 +479,13 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   uint64_t ns = kept < 1024 ? kept : 1024;
   if (ns) GS_CUDA(cudaMemcpyAsync(sample.data(), g->adj_out + (kept - ns), ns * 4, cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaStreamSynchronize(s));
-  cudaFree(hist);
   // Vertices grouped by type (stable radix sort of (type, id) pairs keeps
   // the ids ascending within a type); run starts from the type counts.
   {
     std::vector<uint32_t> toff(T + 1, 0);
     for (uint32_t t = 0; t < T; ++t) toff[t + 1] = toff[t] + g->type_count[t];
-    if (cudaMalloc(&g->toff, sizeof(uint32_t) * (T + 1)) != cudaSuccess ||
-        cudaMalloc(&g->tvid, sizeof(uint32_t) * V) != cudaSuccess)
+    if (gs::dev_malloc(&g->toff, sizeof(uint32_t) * (T + 1)) != cudaSuccess ||
+        gs::dev_malloc(&g->tvid, sizeof(uint32_t) * V) != cudaSuccess)
       return cleanup(fail(GS_ERR_OOM, "type lists"));
     GS_CUDA(cudaMemcpyAsync(g->toff, toff.data(), sizeof(uint32_t) * (T + 1), cudaMemcpyHostToDevice, s));
     uint64_t nv = V;
@@ -413,41 +500,15 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
     GS_CUDA(cudaStreamSynchronize(s));
   }
   // neighbour-type masks (zero where a vertex has no neighbour in a plane)
-  if (cudaMalloc(&g->tmask, sizeof(uint32_t) * (uint64_t)V * P) != cudaSuccess)
+  if (gs::dev_malloc(&g->tmask, sizeof(uint32_t) * (uint64_t)V * P) != cudaSuccess)
     return cleanup(fail(GS_ERR_OOM, "neighbour-type masks"));
   GS_CUDA(cudaMemsetAsync(g->tmask, 0, sizeof(uint32_t) * (uint64_t)V * P, s));
   k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, g->off_out, g->adj_out, 0, g->vtype, g->tmask);
   k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, g->off_in, g->adj_in, R, g->vtype, g->tmask);
   k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, g->off_aout, g->adj_aout, 2 * R, g->vtype, g->tmask);
   k_type_masks<<<blocks_for(V), kT, 0, s>>>(V, g->off_ain, g->adj_ain, 2 * R + 1, g->vtype, g->tmask);
-  // the same planes in type-list order (needs the type lists, built above)
-  {
-    if (cudaMalloc(&g->sig_t, sizeof(uint32_t) * sig_words * P) != cudaSuccess ||
-        cudaMalloc(&g->tmask_t, sizeof(uint32_t) * (uint64_t)V * P) != cudaSuccess)
-      return cleanup(fail(GS_ERR_OOM, "type-ordered planes"));
-    GS_CUDA(cudaMemsetAsync(g->sig_t, 0, sizeof(uint32_t) * sig_words * P, s));
-    k_type_order<<<blocks_for((V + 7) / 8 * P), kT, 0, s>>>(V, (uint32_t)P, g->tvid, g->sig, sig_words, g->tmask,
-                                                           g->sig_t, g->tmask_t);
-  }
-  // Signature statistics for the plan: sigge[(t * P + p) * 16 + c] = vertices
-  // of type t (t = T: any type) whose count in plane p is at least c.
-  {
-    const uint64_t nh = (uint64_t)(T + 1) * P * 16;
-    uint32_t *dh = nullptr;
-    GS_CUDA(cudaMalloc(&dh, sizeof(uint32_t) * nh));
-    GS_CUDA(cudaMemsetAsync(dh, 0, sizeof(uint32_t) * nh, s));
-    const dim3 grid((unsigned)std::min<uint64_t>((V + 255) / 256, 64), (unsigned)P);
-    k_sig_hist<<<grid, 256, 0, s>>>(V, T, (uint32_t)P, g->vtype, g->sig, sig_words, dh);
-    std::vector<uint32_t> hh(nh);
-    GS_CUDA(cudaMemcpyAsync(hh.data(), dh, sizeof(uint32_t) * nh, cudaMemcpyDeviceToHost, s));
-    GS_CUDA(cudaStreamSynchronize(s));
-    cudaFree(dh);
-    for (uint64_t row = 0; row < (uint64_t)(T + 1) * P; ++row)
-      for (int c = 14; c >= 0; --c) hh[row * 16 + c] += hh[row * 16 + c + 1];
-    if (cudaMalloc(&g->sigge, sizeof(uint32_t) * nh) != cudaSuccess) return cleanup(fail(GS_ERR_OOM, "signature statistics"));
-    GS_CUDA(cudaMemcpyAsync(g->sigge, hh.data(), sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s));
-    GS_CUDA(cudaStreamSynchronize(s));
-  }
+  st = derive_sig_tables(g, V, T, P, sig_words, s, true);
+  if (st != GS_OK) return cleanup(st);
   uint64_t h = 1469598103934665603ull;
   auto mixin = [&](uint64_t x) { h = (h ^ x) * 1099511628211ull; };
   mixin(V); mixin(kept); mixin(T); mixin(R);
@@ -473,7 +534,6 @@ extern "C" gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out) {
   d.ipg = (d.nchunks + 31) / 32;
   d.idbits = 1;
   while (d.idbits < 32 && ((V - 1) >> d.idbits)) ++d.idbits;
-  *out = g;
   return GS_OK;
 }
 

@@ -137,10 +137,16 @@ gs_status run_begin(gs_batch *b);
 gs_status run_end(gs_batch *b);
 gs_status batch_finish(gs_batch *b);
 gs_status batch_fetch(gs_batch *b, gs_result *outs);
+gs_status batch_fetch_views(gs_batch *b, gs_result *outs, uint32_t *store);
 // Finish query i of a finished run on the host-driven path (chunked join).
 gs_status fallback_query(gs_batch *b, uint32_t i);
 void enqueue_wave(gs_batch *b, int K, bool capture, std::vector<gs_batch::Ev> *evs);
 void enqueue_wave_tail(gs_batch *b, int K, bool capture, std::vector<gs_batch::Ev> *evs, int stop);
 gs_status refine_to_fixpoint(gs_batch *b);
+// Matching through a compressed graph: query i's candidates must lie in
+// nodes set in the weighted-graph bitmaps at device address wmask[i] (one
+// bitmap per query vertex, wstride words apart; 0 = no restriction), the node
+// of data vertex v being wgroup[v].  Uploads the batch's queries again.
+gs_status batch_set_wmasks(gs_batch *b, const uint64_t *wmask, uint32_t wstride, const uint32_t *wgroup);
 
 }  // namespace gs

@@ -20,6 +20,17 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 void set_error(const std::string &msg);
 gs_status fail(gs_status st, const std::string &msg);
 gs_status cuda_fail(cudaError_t e, const char *what);
+// Every device allocation of the library goes through dev_malloc: plain
+// cudaMalloc, except that a test can arm a simulated allocation failure with
+// gs_debug_fail_alloc (the armed call then returns cudaErrorMemoryAllocation
+// and allocates nothing), so that out-of-memory paths run without exhausting
+// the device.
+cudaError_t dev_malloc_bytes(void **p, size_t bytes);
+void debug_fail_alloc(int64_t after);  // gs_debug_fail_alloc
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+  return dev_malloc_bytes(reinterpret_cast<void **>(p), bytes);
+}
 #define GS_CUDA(call)                                         \
   do {                                                        \
     cudaError_t e_ = (call);                                  \
@@ -81,6 +92,10 @@ struct gs_graph {
 namespace gs {
 
 void release_cache(gs_graph *g);
+// Replace a loaded graph's degree signatures by counts[plane * V + v]
+// (saturated at 15; planes as DevGraph::sig) and rebuild the tables derived
+// from them (type-ordered planes, signature statistics).  Synchronous.
+gs_status graph_set_signatures(gs_graph *g, const uint8_t *counts);
 void release_fallback(gs_graph *g);
 void release_khop(gs_graph *g);
 
@@ -91,13 +106,18 @@ void release_khop(gs_graph *g);
 // holds scan_tmp_words(max_n) uint64 words, zeroed once when allocated and
 // used by nothing but scans; scans that share it must run in order (one
 // stream).
-// scan_error_word() points at a device word that turns non-zero if a
-// look-back wait ever hit its bound on that scratch (a scan result may then
-// be wrong).
+// scan_error_word() points at a device word that turns non-zero when a
+// look-back wait hits its bound on that scratch (the scan then takes that
+// tile's prefix by summing its inputs directly, so its result is still
+// exact); the word stays set until the host clears it.  scan_set_wait sets
+// the bound (polls; 0 = the default, 2^22) and, for tests, makes the first
+// tile of every multi-tile scan on the scratch publish nothing, so that every
+// later tile's wait runs to the bound.  Both copy from the host on stream s.
 uint64_t scan_tmp_words(uint64_t max_n);
 void scan_u32(const uint32_t *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp,
               cudaStream_t s, int num_sms);
 inline const uint32_t *scan_error_word(const uint64_t *tmp) { return reinterpret_cast<const uint32_t *>(tmp); }
+gs_status scan_set_wait(uint64_t *tmp, uint32_t max_polls, uint32_t withhold_first_tile, cudaStream_t s);
 // Same for uint64 inputs.
 void scan_u64(const uint64_t *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, uint64_t *tmp,
               cudaStream_t s, int num_sms);

@@ -39,6 +39,16 @@ __device__ __forceinline__ void bit_set(const Wave &W, uint32_t *slot, uint32_t 
 }
 __device__ __forceinline__ void bit_clear(uint32_t *slot, uint32_t v) { atomicAnd(&slot[v >> 5], ~(1u << (v & 31))); }
 
+// Matching through a compressed graph (Section 3.5, Theorem 3.2): v can be
+// a match of u only if the weighted node whose mapping list holds v is a
+// candidate of u in the weighted graph.
+__device__ __forceinline__ bool wmask_ok(const DQuery &Q, uint32_t u, uint32_t v) {
+  if (!Q.wmask) return true;
+  const uint32_t x = reinterpret_cast<const uint32_t *>(Q.wgroup)[v];
+  const uint32_t *m = reinterpret_cast<const uint32_t *>(Q.wmask) + (uint64_t)u * Q.wstride;
+  return (m[x >> 5] >> (x & 31)) & 1u;
+}
+
 // Candidate test of Definition 3.3 read per direction and relation: binding,
 // type, and for every (direction, relation) at least as many distinct data
 // neighbours as the query vertex has query neighbours.
@@ -47,6 +57,7 @@ __device__ __forceinline__ bool cand_ok(const DevGraph &G, const DQuery &Q, uint
   if (b != kUnbound && b != v) return false;
   uint32_t t = Q.vtype[u];
   if (t != kAny && G.vtype[v] != t) return false;
+  if (!wmask_ok(Q, u, v)) return false;
   for (uint32_t i = Q.need_begin[u]; i < Q.need_begin[u + 1]; ++i) {
     uint32_t w = G.sig[(uint64_t)Q.need_plane[i] * G.sig_words + (v >> 3)];
     if (((w >> ((v & 7) * 4)) & 15u) < Q.need_cnt[i]) return false;
@@ -409,7 +420,8 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
         if (x < e0) {
           const uint32_t v = G.tvid[x];
           w = v >> 5;
-          if (sig_ok_listed(G, Q, u, x) && (W.c0_only || masks_ok_listed(G, Q, u, x))) bits = 1u << (v & 31);
+          if (sig_ok_listed(G, Q, u, x) && (W.c0_only || masks_ok_listed(G, Q, u, x)) && wmask_ok(Q, u, v))
+            bits = 1u << (v & 31);
         }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -445,6 +457,10 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
         ok &= m;
       }
       if (v0 + 32 > G.V) ok &= (G.V - v0 >= 32) ? 0xFFFFFFFFu : ((1u << (G.V - v0)) - 1);
+      for (uint32_t m = Q.wmask ? ok : 0u; m; m &= m - 1) {
+        const uint32_t b = __ffs(m) - 1;
+        if (!wmask_ok(Q, u, v0 + b)) ok &= ~(1u << b);
+      }
       word = ok;
       slot[w0] = word;
     }
@@ -646,7 +662,10 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, co
 
 // ============================================================ explore
 // kernel_explore (Algorithm "Candidate nodes initialization"): one tile of G
-// lanes per candidate v of the visited vertex u.  v is dropped when some
+// lanes per candidate v of the visited vertex u (the thesis gives a hub a
+// whole block; here a relation run longer than 16 passes of the tile is cut
+// into chunks that a second launch spreads over whole warps, and a third
+// launch drops the candidates whose queued runs held no match).  v is dropped when some
 // query neighbour w of u has no candidate among v's data neighbours over the
 // edge's relation and direction (a neighbour whose set is not built yet is
 // tested with the candidate test); otherwise v's neighbours that pass the
@@ -657,6 +676,32 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, co
 // nothing; a candidate dropped by a later child edge may leave extra bits in
 // an earlier child's set, which keeps the sets supersets of the exact ones
 // (refinement removes them).
+constexpr uint32_t kXChunk = 256;  // entries per queued chunk
+
+// Queue the run [lo, hi) of item `it` over its incident edge `inc` as chunks
+// for k_explore_runs.  Returns false (nothing queued, the tile scans the run
+// itself) when the queue is full.
+template <int G>
+__device__ __forceinline__ bool queue_run(const cg::thread_block_tile<G> &t, const Wave &W, uint64_t it, uint32_t inc,
+                                          uint64_t lo, uint64_t hi) {
+  const uint64_t n = (hi - lo + kXChunk - 1) / kXChunk;
+  uint64_t at = 0;
+  if (t.thread_rank() == 0) at = atomicAdd((unsigned long long *)&W.ctrl->xq_top, (unsigned long long)n);
+  at = t.shfl(at, 0);
+  const bool fits = at + n <= W.xq_cap;
+  for (uint64_t c = t.thread_rank(); c < n && at + c < W.xq_cap; c += G) {
+    XChunk x;
+    x.it = (uint32_t)it;
+    x.inc = inc;
+    x.lo = lo + c * kXChunk;
+    // a reservation that does not fit entirely is written as empty chunks
+    x.len = fits ? (uint32_t)(hi - x.lo < kXChunk ? hi - x.lo : kXChunk) : 0u;
+    x.pad = 0;
+    W.xq[at + c] = x;
+  }
+  return fits;
+}
+
 template <int G>
 __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) {
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
@@ -668,10 +713,14 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
     if (it >= W.tlist_cap) break;  // entries past the list belong to overflowed queries
     DQuery &Q = W.dq[W.tlist_q[it]];
-    if (Q.status != QS_OK) continue;
+    if (Q.status != QS_OK) {
+      if (r == 0) W.xneed[it] = 0;
+      continue;
+    }
     const uint32_t u = Q.visit[step];
     const uint32_t v = W.tlist[it];
     const uint32_t i0 = Q.inc_begin[u], i1 = Q.inc_begin[u + 1];
+    uint32_t need = 0;  // incident edges (position < 32) whose runs were queued
     uint64_t bytes = 0;
     // every edge to a typed vertex w needs a neighbour of w's type over its
     // relation and direction: the neighbour-type masks of all edges, loaded
@@ -694,6 +743,11 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
       uint64_t base, lo, hi;
       uint32_t xs;
       const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
+      if (hi - lo > 16 * G && i - i0 < 32 && queue_run<G>(tile, W, it, i - i0, lo, hi)) {
+        need |= 1u << (i - i0);
+        bytes += 16;
+        continue;
+      }
       const bool built = xinc_role(xi) == 1;
       const uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
@@ -719,6 +773,11 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
       uint64_t base, lo, hi;
       uint32_t xs;
       const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
+      if (hi - lo > 16 * G && i - i0 < 32 && queue_run<G>(tile, W, it, i - i0, lo, hi)) {
+        need |= 1u << (i - i0);
+        bytes += 16;
+        continue;
+      }
       uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
       for (uint64_t b = lo; b < hi; b += G) {
@@ -736,9 +795,67 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
       if (!found) keep = false;
     }
     if (!keep && r == 0) bit_clear(slot_of(W, Q.qv_base + u), v);
-    if (r == 0) acc += bytes + 4;
+    if (r == 0) {
+      W.xneed[it] = keep ? need : 0u;  // a dropped candidate's queued runs are skipped
+      W.xfound[it] = 0;
+      acc += bytes + 4;
+    }
   }
   flush_bytes(W, KK_EXPLORE, acc);
+}
+
+// The queued chunks of long runs, one warp each: a child edge's chunk sets
+// the child's bits for every entry that passes the candidate test; every
+// chunk reports whether it held a match for its edge.
+__global__ void __launch_bounds__(kThreads) k_explore_runs(Wave W, uint32_t step) {
+  const DevGraph &Gr = W.G;
+  auto warp = cg::tiled_partition<32>(cg::this_thread_block());
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = gthreads() / 32;
+  const uint64_t n = W.ctrl->xq_top < W.xq_cap ? W.ctrl->xq_top : W.xq_cap;
+  uint64_t acc = 0;
+  for (uint64_t c = gtid() / 32; c < n; c += warps) {
+    const XChunk ch = W.xq[c];
+    if (ch.len == 0 || W.xneed[ch.it] == 0) continue;
+    DQuery &Q = W.dq[W.tlist_q[ch.it]];
+    const uint32_t u = Q.visit[step];
+    const uint32_t xi = Q.xinc[Q.inc_begin[u] + ch.inc];
+    const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
+    const uint32_t w = xinc_w(xi), role = xinc_role(xi);
+    uint32_t *ws = slot_of(W, Q.qv_base + w);
+    const uint32_t *a = Gr.adj[dir];
+    bool found = false;
+    uint64_t scanned = 0;
+    for (uint64_t j0 = ch.lo; j0 < ch.lo + ch.len; j0 += 32) {
+      const uint64_t j = j0 + lane;
+      bool ok = false;
+      if (j < ch.lo + ch.len) {
+        const uint32_t x = a[j] & kNbrMask;
+        ok = role == 1 ? bit_test(ws, x) : cand_ok(Gr, Q, w, x);
+        if (ok && role == 2) bit_set(W, ws, x);
+      }
+      found = warp.any(ok) || found;
+      scanned += ch.lo + ch.len - j0 < 32 ? ch.lo + ch.len - j0 : 32;
+      if (found && role != 2) break;  // existence is all a non-child edge needs
+    }
+    if (found && lane == 0) atomicOr(&W.xfound[ch.it], 1u << ch.inc);
+    if (lane == 0) acc += 24 + 4 * scanned;
+  }
+  flush_bytes(W, KK_EXPLORE, acc);
+}
+
+// Candidates with queued runs: dropped unless every queued edge found a match.
+__global__ void __launch_bounds__(kThreads) k_explore_decide(Wave W, uint32_t step) {
+  const uint64_t all = W.cscan[(uint64_t)W.nq * W.G.nchunks];
+  const uint64_t items = all < W.tlist_cap ? all : W.tlist_cap;
+  for (uint64_t it = gtid(); it < items; it += gthreads()) {
+    const uint32_t need = W.xneed[it];
+    if (need && (W.xfound[it] & need) != need) {
+      const DQuery &Q = W.dq[W.tlist_q[it]];
+      bit_clear(slot_of(W, Q.qv_base + Q.visit[step]), W.tlist[it]);
+    }
+  }
+  if (gtid() == 0) W.ctrl->xq_top = 0;
 }
 
 // ============================================================ refine
@@ -2219,6 +2336,8 @@ void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int
     case 16: k_explore<16><<<persistent_grid(k_explore<16>, sms), kThreads, 0, s>>>(W, step); break;
     default: k_explore<32><<<persistent_grid(k_explore<32>, sms), kThreads, 0, s>>>(W, step); break;
   }
+  k_explore_runs<<<persistent_grid(k_explore_runs, sms), kThreads, 0, s>>>(W, step);
+  k_explore_decide<<<persistent_grid(k_explore_decide, sms), kThreads, 0, s>>>(W, step);
 }
 void launch_refine(const Wave &W, uint32_t round, uint32_t sub, int group, cudaStream_t s, int sms) {
   switch (group) {

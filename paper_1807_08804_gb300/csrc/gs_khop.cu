@@ -216,13 +216,13 @@ static gs_status khop_ctx(gs_graph *g, Khop **out) {
   }
   Khop *k = new Khop();
   const uint64_t V = g->d.V, words = (V + 31) / 32;
-  cudaError_t e = cudaMalloc(&k->level, V);
-  if (e == cudaSuccess) e = cudaMalloc(&k->vis, 4 * words);
-  if (e == cudaSuccess) e = cudaMalloc(&k->front[0], 4 * V);
-  if (e == cudaSuccess) e = cudaMalloc(&k->front[1], 4 * V);
-  if (e == cudaSuccess) e = cudaMalloc(&k->err, 4);
-  if (e == cudaSuccess) e = cudaMalloc(&k->cnt, 8 * 512);  // counts [0, 256), hand-out counters [256, 512)
-  if (e == cudaSuccess) e = cudaMalloc(&k->edges, 8);
+  cudaError_t e = gs::dev_malloc(&k->level, V);
+  if (e == cudaSuccess) e = gs::dev_malloc(&k->vis, 4 * words);
+  if (e == cudaSuccess) e = gs::dev_malloc(&k->front[0], 4 * V);
+  if (e == cudaSuccess) e = gs::dev_malloc(&k->front[1], 4 * V);
+  if (e == cudaSuccess) e = gs::dev_malloc(&k->err, 4);
+  if (e == cudaSuccess) e = gs::dev_malloc(&k->cnt, 8 * 512);  // counts [0, 256), hand-out counters [256, 512)
+  if (e == cudaSuccess) e = gs::dev_malloc(&k->edges, 8);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     delete k;
@@ -269,7 +269,7 @@ extern "C" gs_status gs_khop(gs_graph *g, const uint32_t *seeds, uint32_t nseeds
       if (k->seeds) cudaFree(k->seeds);
       k->seeds = nullptr;
       k->seeds_cap = 0;
-      GS_CUDA(cudaMalloc(&k->seeds, 4ull * nseeds));
+      GS_CUDA(gs::dev_malloc(&k->seeds, 4ull * nseeds));
       k->seeds_cap = nseeds;
     }
     GS_CUDA(cudaMemcpyAsync(k->seeds, seeds, 4ull * nseeds, cudaMemcpyHostToDevice, s));

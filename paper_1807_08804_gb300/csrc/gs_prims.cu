@@ -29,22 +29,25 @@ constexpr int kRadixBins = 256;
 // its inclusive prefix, and publishes its own.  A block only waits on tiles
 // claimed before its own, by blocks that are already running, so the waits
 // end; each is bounded all the same and records an error when the bound is
-// hit.  Descriptors carry the scan's 62-bit epoch, so the scratch needs
-// zeroing only once, when it is allocated; the last block to finish resets
-// the tile counter and advances the epoch for the next scan on the same
-// scratch.
+// hit: a wait that gives up records the event in the scratch's error word
+// and takes its prefix directly, as the sum of every input before its tile,
+// so the scan's result stays exact either way.  Descriptors carry the scan's
+// 62-bit epoch, so the scratch needs zeroing only once, when it is
+// allocated; the last block to finish resets the tile counter and advances
+// the epoch for the next scan on the same scratch.
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr uint64_t kScanTile = (uint64_t)kScanThreads * kScanItems;  // 2048
 constexpr uint32_t kLookbackLimit = 1u << 22;
 
 struct ScanState {  // the first 32 bytes of the scratch
-  uint32_t err;     // a look-back wait hit its bound (sticky; read by scan_error_word)
-  uint32_t tiles;   // next tile to claim
-  uint32_t done;    // blocks finished
+  uint32_t err;       // a look-back wait hit its bound (kept until the host clears it)
+  uint32_t tiles;     // next tile to claim
+  uint32_t done;      // blocks finished
+  uint32_t limit;     // polls before a look-back wait gives up (0 = kLookbackLimit); set by the host
+  uint64_t epoch;     // scans completed on this scratch
+  uint32_t withhold;  // test setting: tile 0 of a multi-tile scan publishes nothing
   uint32_t pad;
-  uint64_t epoch;   // scans completed on this scratch
-  uint64_t pad2;
 };
 struct __align__(32) ScanDesc {
   uint64_t agg;   // the tile's total
@@ -90,6 +93,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
   const uint64_t n = *d_n;
   const uint64_t ntiles = (n + kScanTile - 1) / kScanTile;
   const uint64_t tag = *reinterpret_cast<volatile uint64_t *>(&st->epoch) << 2;
+  const uint32_t limit = st->limit ? st->limit : kLookbackLimit;
+  const bool withhold = st->withhold != 0 && ntiles > 1;
   const int lane = threadIdx.x & 31;
   if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
   for (;;) {
@@ -116,9 +121,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
     if (threadIdx.x == 0) {
       ScanDesc &d = desc[t];
       if (t == 0) {
-        __stcg(&d.incl, agg);
-        __threadfence();
-        __stcg(&d.flag, tag | 2u);
+        if (!withhold) {
+          __stcg(&d.incl, agg);
+          __threadfence();
+          __stcg(&d.flag, tag | 2u);
+        }
       } else {
         __stcg(&d.agg, agg);
         __threadfence();
@@ -141,9 +148,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
           const uint32_t zero_mask = __ballot_sync(kFull, status == 0);
           const int first = incl_mask ? __ffs(incl_mask) - 1 : 32;
           const uint32_t need = first >= 31 ? kFull : ((2u << first) - 1);
-          if ((zero_mask & need) && ++spins < kLookbackLimit) continue;
-          if (zero_mask & need) {  // bound hit: record it and stop waiting
+          if ((zero_mask & need) && ++spins < limit) continue;
+          if (zero_mask & need) {  // bound hit: record it, then sum the inputs before this tile
             if (lane == 0) atomicExch(&st->err, 1u);
+            uint64_t v = 0;
+            for (uint64_t i = lane; i < base; i += 32) v += (uint64_t)in[i];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+            prefix = v;
+            break;
           }
           __threadfence();
           uint64_t v = 0;
@@ -151,7 +164,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64
 #pragma unroll
           for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
           prefix += v;
-          if (first < 32 || (zero_mask & need)) break;
+          if (first < 32) break;
           pos -= 32;
         }
         if (lane == 0) {
@@ -293,6 +306,14 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const uint32_t 
 }
 
 }  // namespace
+
+gs_status scan_set_wait(uint64_t *tmp, uint32_t max_polls, uint32_t withhold_first_tile, cudaStream_t s) {
+  ScanState *st = reinterpret_cast<ScanState *>(tmp);
+  const uint32_t w = withhold_first_tile ? 1u : 0u;
+  GS_CUDA(cudaMemcpyAsync(&st->limit, &max_polls, 4, cudaMemcpyHostToDevice, s));
+  GS_CUDA(cudaMemcpyAsync(&st->withhold, &w, 4, cudaMemcpyHostToDevice, s));
+  return GS_OK;
+}
 
 uint64_t scan_tmp_words(uint64_t max_n) {
   const uint64_t tiles = std::max<uint64_t>((max_n + kScanTile - 1) / kScanTile, 1);

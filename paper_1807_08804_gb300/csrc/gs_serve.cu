@@ -10,6 +10,7 @@
 // one candidate, a typed vertex at most the number of data vertices of its
 // type, an untyped one at most V; each candidate costs its list entry, its
 // candidate-edge table entries and a bitmap slot share.
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -17,6 +18,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "gs_host.h"
@@ -74,6 +76,7 @@ struct gs_server {
   std::deque<Req> pending;
   std::unordered_map<uint64_t, Done> done;
   std::unordered_map<uint64_t, int> inflight;  // ticket -> slot
+  std::unordered_set<uint64_t> live;           // submitted and not yet polled to completion
   uint64_t next_ticket = 1;
   uint64_t inflight_est = 0;
   std::vector<Slot> slots;
@@ -83,6 +86,17 @@ struct gs_server {
 };
 
 namespace {
+
+std::atomic<uint32_t> g_fail_waits{0};  // completion checks left to report a simulated CUDA error
+
+// Completion check of a slot's event: cudaEventQuery, or a simulated failure
+// armed by gs_debug_fail_serve_wait.
+cudaError_t slot_query(cudaEvent_t ev) {
+  uint32_t n = g_fail_waits.load(std::memory_order_relaxed);
+  while (n > 0)
+    if (g_fail_waits.compare_exchange_weak(n, n - 1)) return cudaErrorLaunchFailure;
+  return cudaEventQuery(ev);
+}
 
 uint64_t estimate(const gs_graph *g, const gs_query &q) {
   const uint64_t slot_bytes = 4 * (((uint64_t)g->d.W0 + g->d.W1 + g->d.ipg + 31) / 32 * 32);
@@ -181,11 +195,21 @@ gs_status launch_tail(Slot &sl) {
   return GS_OK;
 }
 
-// A slot whose launch failed: its requests complete with the error.
+// A slot whose micro-batch failed: wait until its stream has drained (at
+// once after a real fault), drop its batch so that no later micro-batch
+// reuses buffers that queued work may still touch, and complete its requests
+// with the error.
 void fail_slot(gs_server *s, Slot &sl, gs_status st) {
+  const std::string msg = gs_last_error();
+  if (sl.b) {
+    cudaStreamSynchronize(sl.b->stream);
+    cudaGetLastError();
+    batch_destroy(sl.b);
+    sl.b = nullptr;
+  }
   std::lock_guard<std::mutex> lk(s->mu);
   s->worker_error = st;
-  s->worker_msg = gs_last_error();
+  s->worker_msg = msg;
   for (auto &r : sl.reqs) {
     Done d;
     memset(&d.r, 0, sizeof(d.r));
@@ -206,7 +230,15 @@ void worker_main(gs_server *s) {
   for (;;) {
     bool worked = false;
     for (Slot &sl : s->slots) {
-      if (!sl.busy || cudaEventQuery(sl.ev) != cudaSuccess) continue;
+      if (!sl.busy) continue;
+      const cudaError_t e = slot_query(sl.ev);
+      if (e == cudaErrorNotReady) continue;
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail_slot(s, sl, cuda_fail(e, "serving: micro-batch completion"));
+        worked = true;
+        continue;
+      }
       if (sl.phase == 1) {
         gs_status st = launch_tail(sl);
         if (st != GS_OK) fail_slot(s, sl, st);
@@ -292,6 +324,7 @@ extern "C" gs_status gs_serve_submit(gs_server *s, const gs_query *q, const gs_m
     if (s->pending.size() >= s->o.queue_depth) return fail(GS_ERR_BUSY, "serving queue full");
     r.ticket = s->next_ticket++;
     *ticket = r.ticket;
+    s->live.insert(r.ticket);
     s->pending.push_back(std::move(r));
   }
   s->cv.notify_one();
@@ -303,14 +336,17 @@ extern "C" gs_status gs_serve_poll(gs_server *s, uint64_t ticket, gs_result *out
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->done.find(ticket);
   if (it == s->done.end()) {
-    if (ticket == 0 || ticket >= s->next_ticket) return fail(GS_ERR_INVALID, "unknown ticket");
+    if (!s->live.count(ticket)) return fail(GS_ERR_INVALID, "unknown or already collected ticket");
     return GS_ERR_NOT_READY;
   }
   *out = it->second.r;
   if (latency_s) *latency_s = it->second.latency_s;
   s->done.erase(it);
+  s->live.erase(ticket);
   return GS_OK;
 }
+
+extern "C" void gs_debug_fail_serve_wait(uint32_t n) { g_fail_waits.store(n); }
 
 extern "C" gs_status gs_serve_destroy(gs_server *s) {
   if (!s) return GS_OK;

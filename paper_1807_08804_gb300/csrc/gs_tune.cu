@@ -1,6 +1,8 @@
 // Autotuner: picks the lanes per work item (the "warps per vertex" of the
 // explore, refine, edge-table and join kernels: 4, 8, 16 or 32 lanes) and
-// the number of refinement rounds for a graph and a kind of query load, by
+// the number of refinement rounds (none, 1, 2 or 4: Section 3.6 finds one
+// round the fastest refined variant, and exploration already prunes every
+// candidate against all its query edges) for a graph and a kind of query load, by
 // timing the captured pipeline on the caller's queries.  Results do not
 // depend on either knob (refinement only prunes; the join checks every
 // edge), so the choice is purely about speed.
@@ -108,7 +110,7 @@ extern "C" gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const 
   GS_CUDA(cudaEventCreate(&e0));
   GS_CUDA(cudaEventCreate(&e1));
   const uint32_t groups[] = {4, 8, 16, 32};
-  const uint32_t round_opts[] = {2, 4, 8};
+  const uint32_t round_opts[] = {GS_ROUNDS_NONE, 1, 2, 4};
   best = 1e30;
   uint32_t tried = 0;
   for (uint32_t gi : groups) {
@@ -154,7 +156,8 @@ extern "C" gs_status gs_tune_set(gs_graph *g, uint32_t group, uint32_t refine_ro
   if (!g) return fail(GS_ERR_INVALID, "gs_tune_set: null graph");
   if (group && group != 4 && group != 8 && group != 16 && group != 32)
     return fail(GS_ERR_INVALID, "group must be 4, 8, 16 or 32 (0 = default)");
-  if (refine_rounds > kMaxRounds) return fail(GS_ERR_INVALID, "too many refinement rounds");
+  if (refine_rounds > kMaxRounds && refine_rounds != GS_ROUNDS_NONE)
+    return fail(GS_ERR_INVALID, "too many refinement rounds");
   g->tuned_group = group;
   g->tuned_rounds = refine_rounds;
   return GS_OK;

@@ -44,7 +44,7 @@ def _load():
         _lib.gsg_graph.restype = ctypes.c_int
         _lib.gsg_graph.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                    ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ctypes.c_uint32,
-                                   ctypes.c_uint64, P, P, P, P]
+                                   ctypes.c_uint64, P, P, P, P, ctypes.c_double, ctypes.c_double]
         _lib.gsg_walk_queries.restype = ctypes.c_int64
         _lib.gsg_walk_queries.argtypes = [ctypes.c_uint32, P, P, P, P, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -98,15 +98,20 @@ class Query:
 
 
 def make_graph(V: int, E: int, T: int = 64, type_s: float = 1.0, R: int = 34, rel_s: float = 1.1,
-               alpha: float = 2.1, dmax: int = 1000, seed: int = 1) -> Graph:
+               alpha: float = 2.1, dmax: int = 1000, seed: int = 1, target_s: float = 0.0,
+               copy_p: float = 0.0) -> Graph:
     """Power-law out-degree (density exponent alpha, scaled so the degrees sum
-    to E, clamped to [1, dmax]), uniform targets, Zipf types and relations."""
+    to E, clamped to [1, dmax]), Zipf types and relations, and uniform
+    targets (target_s = 0) or Zipf(target_s) targets over a seeded vertex
+    order; with copy_p a vertex copies, with that probability, the out-list
+    of the last earlier vertex of its type and out-degree."""
     lib = _load()
     ro = np.zeros(V + 1, np.uint64)
     col = np.zeros(max(E, 1), np.uint32)
     rel = np.zeros(max(E, 1), np.uint32)
     vt = np.zeros(V, np.uint32)
-    rc = lib.gsg_graph(V, E, T, type_s, R, rel_s, alpha, dmax, seed, _p(ro), _p(col), _p(rel), _p(vt))
+    rc = lib.gsg_graph(V, E, T, type_s, R, rel_s, alpha, dmax, seed, _p(ro), _p(col), _p(rel), _p(vt), target_s,
+                       copy_p)
     if rc != 0:
         raise ValueError(f"graph parameters impossible: V={V} E={E} dmax={dmax} R={R}")
     return Graph(V, ro, col[:E], rel[:E], vt, T, R)
@@ -224,9 +229,14 @@ class Workload:
     qps: tuple = field(default_factory=tuple)
     p_var: float = 0.0  # share of query edges made variable (relation ANY)
     anchored: bool = False  # one bound vertex (the walk start), every other vertex untyped
+    graph_seed: int | None = None  # the graph's seed when it differs from the queries' seed
+    target_s: float = 0.0  # Zipf exponent of edge targets (0 = uniform)
+    copy_p: float = 0.0  # share of vertices copying the out-list of an earlier vertex of their type and degree
+    deltas: tuple = ()  # compression thresholds per level (matching through a compressed graph)
 
     def graph(self) -> Graph:
-        return make_graph(self.V, self.E, seed=self.seed)
+        return make_graph(self.V, self.E, seed=self.seed if self.graph_seed is None else self.graph_seed,
+                          target_s=self.target_s, copy_p=self.copy_p)
 
     def queries(self, g: Graph, n: int | None = None) -> list[Query]:
         n = self.n_queries if n is None else n
@@ -249,9 +259,9 @@ WORKLOADS = {
     # 4M vertices / 32M edges; 10,000 queries of 3-12 vertices, half cyclic
     "batch-4m": Workload("batch-4m", 4_000_000, 32_000_000, 10_000, 3, 12, 0.1, 1 << 20, 0x6753003,
                          cyclic_half=True),
-    # 4M vertices / 32M edges; Poisson arrivals, 3-12 vertices
+    # the batch-4m graph kept device-resident; Poisson arrivals of queries of 3-12 vertices
     "serve-4m": Workload("serve-4m", 4_000_000, 32_000_000, 20_000, 3, 12, 0.2, 1 << 20, 0x6753004,
-                         qps=(1000.0, 5000.0, 20000.0, 50000.0)),
+                         qps=(1000.0, 5000.0, 20000.0, 50000.0), graph_seed=0x6753003),
     # 16M vertices / 200M edges; 200 unbound shape queries
     "stress-16m": Workload("stress-16m", 16_000_000, 200_000_000, 200, 4, 6, 0.0, 1 << 20, 0x6753005,
                            shapes=True),
@@ -259,6 +269,14 @@ WORKLOADS = {
     # concept node and untyped variables elsewhere (refinement measurements, count only)
     "ablation-1m": Workload("ablation-1m", 1_000_000, 8_000_000, 200, 10, 12, 0.0, 1 << 20, 0x6753002,
                             cyclic_half=True, anchored=True),
+    # matching through a multi-level compression (three levels at the thesis's SenticNet thresholds
+    # 0.8, 0.7, 0.7) of graphs with concept families: edge targets follow Zipf(1.3) over a seeded
+    # vertex order (rarely-cited concepts have few incoming edges) and 80% of the vertices copy the
+    # out-list of the last earlier vertex of their type and out-degree
+    "compress-10k": Workload("compress-10k", 10_000, 60_000, 100, 3, 6, 0.2, 1 << 20, 0x6753006, target_s=1.3,
+                             copy_p=0.8, deltas=(0.8, 0.7, 0.7)),
+    "compress-1m": Workload("compress-1m", 1_000_000, 8_000_000, 1000, 4, 10, 0.2, 1 << 22, 0x6753007,
+                            target_s=1.3, copy_p=0.8, deltas=(0.8, 0.7, 0.7)),
     # the single-10k and single-1m workloads with 30% of query edges variable
     "single-10k-var": Workload("single-10k-var", 10_000, 60_000, 100, 3, 6, 0.2, 1 << 20, 0x6753001, p_var=0.3),
     "single-1m-var": Workload("single-1m-var", 1_000_000, 8_000_000, 1000, 4, 10, 0.2, 1 << 22, 0x6753002,

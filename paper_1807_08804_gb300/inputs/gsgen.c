@@ -126,12 +126,32 @@ static int gsg_degrees(gsg_rng *r, uint32_t V, uint64_t E, double alpha, uint32_
  * (not sorted, so that consumers canonicalise it themselves):
  *   row_off[V+1] (uint64), col[E] (uint32), rel[E] (uint32), vtype[V] (uint32).
  * Types ~ Zipf(type_s) over T labels, relations ~ Zipf(rel_s) over R labels,
- * targets uniform over V \ {src}; duplicate (src, rel, dst) triples are
- * redrawn.  Returns 0 or -1 (parameters impossible).
+ * targets uniform over V \ {src} (target_s = 0) or, with target_s > 0,
+ * Zipf(target_s) over the vertices in a seeded random order, a vertex taking
+ * at most dmax incoming edges (popular concepts take most incoming edges);
+ * with copy_p > 0 a vertex copies, with
+ * that probability, the whole out-list (relations and targets) of the last
+ * earlier vertex of its type and out-degree, so families of concepts share
+ * their adjacency as in commonsense graphs (a copied target equal to the
+ * vertex itself is redrawn); duplicate (src, rel, dst) triples are redrawn.
+ * Returns 0 or -1 (parameters impossible).
  */
+static uint32_t gsg_target(gsg_rng *r, uint32_t V, uint32_t v, const double *tcdf, const uint32_t *perm,
+                           const uint32_t *indeg, uint32_t dmax) {
+  if (!tcdf) {
+    uint32_t t = (uint32_t)gsg_below(r, V - 1);
+    return t >= v ? t + 1 : t;
+  }
+  for (;;) {  /* popular targets fill up to dmax incoming edges, like out-degrees */
+    const uint32_t t = perm[gsg_zipf(r, tcdf, V)];
+    if (t != v && indeg[t] < dmax) return t;
+  }
+}
+
 int gsg_graph(uint32_t V, uint64_t E, uint32_t T, double type_s, uint32_t R, double rel_s,
               double alpha, uint32_t dmax, uint64_t seed,
-              uint64_t *row_off, uint32_t *col, uint32_t *rel, uint32_t *vtype) {
+              uint64_t *row_off, uint32_t *col, uint32_t *rel, uint32_t *vtype, double target_s,
+              double copy_p) {
   if (V < 2 || T == 0 || R == 0) return -1;
   uint64_t cap = (uint64_t)R * (V - 1);
   if (dmax > cap) dmax = (uint32_t)cap;
@@ -141,17 +161,50 @@ int gsg_graph(uint32_t V, uint64_t E, uint32_t T, double type_s, uint32_t R, dou
   gsg_stream(&re, seed, 3);
   double *tc = gsg_zipf_cdf(T, type_s), *rc = gsg_zipf_cdf(R, rel_s);
   for (uint32_t v = 0; v < V; ++v) vtype[v] = gsg_zipf(&rt, tc, T);
+  double *tcdf = NULL;
+  uint32_t *perm = NULL, *indeg = NULL;
+  if (target_s > 0) {  /* popularity order: a seeded Fisher-Yates shuffle */
+    gsg_rng rp;
+    gsg_stream(&rp, seed, 4);
+    tcdf = gsg_zipf_cdf(V, target_s);
+    indeg = (uint32_t *)calloc(V, sizeof(uint32_t));
+    perm = (uint32_t *)malloc(sizeof(uint32_t) * V);
+    for (uint32_t v = 0; v < V; ++v) perm[v] = v;
+    for (uint32_t v = V - 1; v > 0; --v) {
+      const uint32_t j = (uint32_t)gsg_below(&rp, (uint64_t)v + 1);
+      const uint32_t t = perm[v]; perm[v] = perm[j]; perm[j] = t;
+    }
+  }
   uint32_t *deg = (uint32_t *)malloc(sizeof(uint32_t) * V);
   if (gsg_degrees(&rd, V, E, alpha, dmax, deg) != 0) { free(deg); free(tc); free(rc); return -1; }
   row_off[0] = 0;
   for (uint32_t v = 0; v < V; ++v) row_off[v + 1] = row_off[v] + deg[v];
   uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (dmax + 1));
   uint64_t *srt = (uint64_t *)malloc(sizeof(uint64_t) * (dmax + 1));
+  /* copy model: last vertex of each (type, out-degree), -1 if none yet */
+  int64_t *last = NULL;
+  gsg_rng rcp;
+  if (copy_p > 0) {
+    gsg_stream(&rcp, seed, 5);
+    last = (int64_t *)malloc(sizeof(int64_t) * (uint64_t)T * (dmax + 1));
+    for (uint64_t i = 0; i < (uint64_t)T * (dmax + 1); ++i) last[i] = -1;
+  }
   for (uint32_t v = 0; v < V; ++v) {
     uint32_t d = deg[v];
     /* key = rel << 32 | dst; redraw duplicates until the list is distinct */
+    int64_t proto = -1;
+    if (last) {
+      int64_t *slot = &last[(uint64_t)vtype[v] * (dmax + 1) + d];
+      if (*slot >= 0 && gsg_unif(&rcp) < copy_p) proto = *slot;
+      *slot = v;
+    }
     for (uint32_t j = 0; j < d; ++j) {
-      uint32_t t = (uint32_t)gsg_below(&re, V - 1); if (t >= v) t++;
+      if (proto >= 0) {
+        const uint64_t o = row_off[proto] + j;
+        key[j] = ((uint64_t)rel[o] << 32) | col[o];
+        if (col[o] != v && (!indeg || indeg[col[o]] < dmax)) continue;
+      }
+      uint32_t t = gsg_target(&re, V, v, tcdf, perm, indeg, dmax);
       key[j] = ((uint64_t)gsg_zipf(&re, rc, R) << 32) | t;
     }
     for (;;) {
@@ -165,15 +218,17 @@ int gsg_graph(uint32_t V, uint64_t E, uint32_t T, double type_s, uint32_t R, dou
         int seen = 0;
         for (uint32_t i = 0; i < j; ++i) if (key[i] == key[j]) { seen = 1; break; }
         if (seen) {
-          uint32_t t = (uint32_t)gsg_below(&re, V - 1); if (t >= v) t++;
+          uint32_t t = gsg_target(&re, V, v, tcdf, perm, indeg, dmax);
           key[j] = ((uint64_t)gsg_zipf(&re, rc, R) << 32) | t;
         }
       }
     }
     uint64_t o = row_off[v];
     for (uint32_t j = 0; j < d; ++j) { col[o + j] = (uint32_t)key[j]; rel[o + j] = (uint32_t)(key[j] >> 32); }
+    if (indeg)
+      for (uint32_t j = 0; j < d; ++j) indeg[(uint32_t)key[j]]++;
   }
-  free(key); free(srt); free(deg); free(tc); free(rc);
+  free(key); free(srt); free(deg); free(tc); free(rc); free(tcdf); free(perm); free(last); free(indeg);
   return 0;
 }
 

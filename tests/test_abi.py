@@ -43,7 +43,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
     pairs = [("gs_graph_desc", gs.GraphDesc), ("gs_query", gs.QueryDesc), ("gs_match_opts", gs.MatchOpts),
-             ("gs_result", gs.ResultDesc), ("gs_serve_opts", gs.ServeOpts), ("gs_khop_opts", gs.KhopOpts)]
+             ("gs_result", gs.ResultDesc), ("gs_serve_opts", gs.ServeOpts), ("gs_khop_opts", gs.KhopOpts),
+             ("gs_cgraph_info", gs.CGraphInfo)]
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gs.h"', "int main(void) {"]
     for cname, py in pairs:
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
