@@ -162,7 +162,8 @@ def refinement_ablation(gs, dg, qs, cap, gmode, sh, stream, flush, steps, want):
     import torch
     variants = [("converged", 0, 64), ("converged-reversed", gs.GS_REFINE_REVERSED, 64),
                 ("one-round-reversed", gs.GS_REFINE_REVERSED, 1), ("none", gs.GS_REFINE_OFF, 1),
-                ("one-round-reversed-skip-degree-1", gs.GS_REFINE_REVERSED | gs.GS_REFINE_LOW(1), 1)]
+                ("one-round-reversed-skip-degree-1", gs.GS_REFINE_REVERSED | gs.GS_REFINE_LOW(1), 1),
+                ("baseline-outgoing-graph-tree-only", gs.GS_REFINE_BASELINE, 1)]
     out = []
     for name, refine, rounds in variants:
         b = gs.Batch(dg, qs, cap=cap, mode=gmode, stream=sh, max_refine_rounds=rounds, refine=refine)
@@ -454,6 +455,32 @@ def run_compressed(args, world, rank, local):
     dg.free()
 
 
+def run_profile_once(args):
+    """One small program for ncu captures: the workload's batch (or its first
+    --queries queries) run --runs times, with no timing, comparison modes,
+    serving or CPU baseline, so that a capture of a few kernels ends
+    quickly."""
+    import paper_1807_08804_gb300 as gs
+    from paper_1807_08804_gb300 import inputs as I
+    w = I.WORKLOADS[args.workload]
+    g = w.graph()
+    qs = w.queries(g, args.queries or None)
+    dg = gs.DeviceGraph(g)
+    if args.group or args.rounds:
+        gs.tune_set(dg, args.group, args.rounds)
+    b = gs.Batch(dg, qs, cap=w.cap)
+    if args.long_run is not None:
+        b.configure(use_graph=True, group=args.group or 32, refine_rounds=args.rounds, long_run=args.long_run)
+    for _ in range(args.runs):
+        b.run()
+        b.finish()
+    res = b.fetch()
+    print(f"{len(qs)} queries, {sum(r.count for r in res)} embeddings, {sum(r.status != 0 for r in res)} not ok",
+          flush=True)
+    b.close()
+    dg.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -481,7 +508,19 @@ def main():
     ap.add_argument("--khop-seeds", type=int, default=16)
     ap.add_argument("--project", default=None,
                     help="comma-separated query vertices whose distinct tuples are returned (projection)")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="run the workload's batch --runs times and nothing else (for ncu captures)")
+    ap.add_argument("--queries", type=int, default=0, help="--profile-once: the first this many queries (0 = all)")
+    ap.add_argument("--runs", type=int, default=1, help="--profile-once: runs of the batch")
+    ap.add_argument("--group", type=int, default=0, help="--profile-once: lanes per work item (0 = default)")
+    ap.add_argument("--rounds", type=int, default=0,
+                    help="--profile-once: refinement rounds (0 = default, 4294967295 = none)")
+    ap.add_argument("--long-run", type=int, default=None,
+                    help="--profile-once: exploration's long-run split (entries; 0 = none)")
     args = ap.parse_args()
+    if args.profile_once:
+        run_profile_once(args)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -504,7 +543,7 @@ def main():
     g = w.graph()
     qs = w.queries(g)
     n = len(qs)
-    mode = args.mode or ("count" if w.shapes or w.anchored else "enumerate")
+    mode = args.mode or ("count" if w.shapes or w.anchored or w.count_only else "enumerate")
     gmode = {"count": gs.GS_COUNT_ONLY, "chunked": gs.GS_CHUNKED}.get(mode, gs.GS_ENUMERATE)
     cap = 0 if mode != "enumerate" else w.cap
     streamed = [0]  # rows delivered to the chunk callback (chunked mode)

@@ -96,9 +96,10 @@ gs_status pack_query(const DevGraph &G, const gs_query *q, const gs_match_opts *
     if (!d->proj || ((d->proj >> u) & 1u)) d->pu[d->kp++] = (uint8_t)u;
   // refinement variant
   const uint32_t rf = o ? o->refine : 0;
-  if (rf & ~(GS_REFINE_OFF | GS_REFINE_REVERSED | GS_REFINE_LOW(0xFF)))
+  if (rf & ~(GS_REFINE_OFF | GS_REFINE_REVERSED | GS_REFINE_BASELINE | GS_REFINE_LOW(0xFF)))
     return fail(GS_ERR_INVALID, "unknown refinement flags");
   d->refine_flags = (uint8_t)(((rf & GS_REFINE_OFF) ? kRefineOff : 0u) | ((rf & GS_REFINE_REVERSED) ? kRefineRev : 0u));
+  if (rf & GS_REFINE_BASELINE) d->refine_flags = kRefineBase | kRefineOff;
   d->refine_low = (uint8_t)((rf >> 8) & 0xFFu);
   d->force_root = 0xFF;
   d->force_from_src = 0xFF;
@@ -414,7 +415,7 @@ void enqueue_front(Pipe &P, int K) {
     launch_compact_write(W, 0, step, W.cscan, W.tlist, W.tlist_q, W.tlist_cap, HW_TLIST, P.cur, sms);
     P.end();
     P.begin(KK_EXPLORE);
-    launch_explore(W, step, grp, P.cur, sms);
+    launch_explore(W, step, grp, b->long_run, P.cur, sms);
     P.end();
   }
   P.begin(KK_COMPACT_ALL);
@@ -707,7 +708,7 @@ gs_status run_end(gs_batch *b) {
 static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match_opts *opts) {
   const bool had_rev = b->has_rev;
   b->n = n;
-  b->hq.assign(n, DQuery{});
+  b->hq.resize(n);  // pack_query clears each entry before filling it
   b->hstatus.assign(n, GS_OK);
   b->has_proj = b->has_rev = false;
   b->max_k = 1;
@@ -757,6 +758,7 @@ gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_mat
   opts_key(b, opts);
   if (g->tuned_group) b->group = g->tuned_group;
   if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds == GS_ROUNDS_NONE ? 0 : g->tuned_rounds;
+  b->long_run = g->tuned_long_run;
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
     b->fixpoint = false;
@@ -826,6 +828,7 @@ gs_status batch_create_capacity(gs_graph *g, const gs_match_opts *opts, uint32_t
   opts_key(b, opts);
   if (g->tuned_group) b->group = g->tuned_group;
   if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds == GS_ROUNDS_NONE ? 0 : g->tuned_rounds;
+  b->long_run = g->tuned_long_run;
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
     b->fixpoint = false;
@@ -1169,6 +1172,14 @@ extern "C" gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_
     b->refine_rounds = 8;
     b->fixpoint = true;
   }
+  return GS_OK;
+}
+
+extern "C" gs_status gs_batch_set_long_run(gs_batch *b, uint32_t long_run) {
+  if (!b) return fail(GS_ERR_INVALID, "gs_batch_set_long_run: null batch");
+  if (long_run && long_run < 32) return fail(GS_ERR_INVALID, "long_run must be 0 or at least 32");
+  drop_graphs(b);
+  b->long_run = long_run;
   return GS_OK;
 }
 

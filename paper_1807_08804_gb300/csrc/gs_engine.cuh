@@ -99,7 +99,7 @@ __host__ __device__ __forceinline__ uint32_t xinc_role(uint32_t x) { return x >>
 // its signature and neighbour-type planes are 2R + direction.
 constexpr uint32_t kRelAny8 = 0xFFu;
 // Refinement variants (DQuery::refine_flags).
-constexpr uint32_t kRefineOff = 1u, kRefineRev = 2u;
+constexpr uint32_t kRefineOff = 1u, kRefineRev = 2u, kRefineBase = 4u;
 __host__ __device__ __forceinline__ int adj_plane(int dir, uint32_t rel) { return rel == kRelAny8 ? dir + 2 : dir; }
 __host__ __device__ __forceinline__ uint32_t adj_rel(uint32_t rel) { return rel == kRelAny8 ? 0u : rel; }
 __host__ __device__ __forceinline__ uint32_t sig_plane(int dir, uint32_t rel, uint32_t R) {
@@ -265,7 +265,9 @@ void launch_filter(const Wave &W, cudaStream_t s, int sms);
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms);
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint32_t *owner,
                           uint64_t cap, int hw_slot, cudaStream_t s, int sms);
-void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms);
+// long_run > 0: relation runs longer than long_run entries go to a queue of
+// chunks scanned by whole warps in a second launch (0 = every run inline).
+void launch_explore(const Wave &W, uint32_t step, int group, uint32_t long_run, cudaStream_t s, int sms);
 // sub: kAllSub refines every vertex of every query; j < kMaxK refines, in
 // queries with kRefineRev, the vertex rorder[j] (other queries at j = 0).
 constexpr uint32_t kAllSub = 0xFFFFFFFFu;

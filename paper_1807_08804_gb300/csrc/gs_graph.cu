@@ -393,6 +393,8 @@ static gs_status derive_sig_tables(gs_graph *g, uint32_t V, uint32_t T, uint64_t
     for (int c = 14; c >= 0; --c) hh[row * 16 + c] += hh[row * 16 + c + 1];
   if (alloc && gs::dev_malloc(&g->sigge, sizeof(uint32_t) * nh) != cudaSuccess)
     return fail(GS_ERR_OOM, "signature statistics");
+  if (!g->sigge_host) g->sigge_host = new uint32_t[nh];
+  memcpy(g->sigge_host, hh.data(), sizeof(uint32_t) * nh);
   GS_CUDA(cudaMemcpyAsync(g->sigge, hh.data(), sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s));
   GS_CUDA(cudaStreamSynchronize(s));
   return GS_OK;
@@ -559,6 +561,7 @@ extern "C" void gs_graph_free(gs_graph *g) {
   cudaFree(g->tmask_t);
   cudaFree(g->sig);
   delete[] g->type_count;
+  delete[] g->sigge_host;
   delete g;
 }
 

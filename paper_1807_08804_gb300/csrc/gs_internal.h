@@ -81,12 +81,14 @@ struct gs_graph {
   uint32_t *tvid, *toff, *sigge, *tmask, *sig_t, *tmask_t;
   uint32_t *sig;
   uint32_t *type_count;     // host copy [T]
+  uint32_t *sigge_host;     // host copy of DevGraph::sigge (admission estimates)
   uint64_t hash;            // content hash (tuning cache key)
   void *cache;              // batches reused by gs_match / gs_match_batch
   void *fallback;           // context of the chunked join
   void *khop;               // buffers of the domain-graph exploration
   uint32_t tuned_group;     // lanes per work item chosen by gs_tune (0 = default)
   uint32_t tuned_rounds;    // refinement rounds chosen by gs_tune (0 = default)
+  uint32_t tuned_long_run;  // exploration's long-run split chosen by gs_tune (0 = none)
 };
 
 namespace gs {

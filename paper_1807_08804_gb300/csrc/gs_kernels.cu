@@ -327,6 +327,8 @@ __global__ void k_plan(Wave W, const uint32_t *type_count) {
         if (s != 0xFF) {
           role = Q.init_step[w] <= s ? 1u : 0u;
           if (Q.parent[w] == u && Q.init_step[w] == s + 1 && Q.pedge[w] == e) role = 2u;
+          // the baseline checks only spanning-tree edges it can follow forwards
+          if ((Q.refine_flags & kRefineBase) && (role != 2u || dir != 0u)) role = 3u;
         }
         Q.xinc[i] = xinc_pack(dir, Q.erel[e], w, role);
       }
@@ -343,12 +345,25 @@ __global__ void k_plan(Wave W, const uint32_t *type_count) {
 // unless the exact Definition 3.3 set is asked for (W.c0_only, inspection);
 // an untyped u has one per summary word (1024 vertices), which writes 32
 // level-0 words and the summary word outright.
-__device__ __forceinline__ uint32_t filter_items(const DevGraph &G, const DQuery &Q) {
-  if (Q.status != QS_OK || Q.nvisit == 0) return 0;
-  const uint32_t u = Q.visit[0];
+__device__ __forceinline__ uint32_t vertex_filter_items(const DevGraph &G, const DQuery &Q, uint32_t u) {
   if (Q.vbind[u] != kUnbound) return 1;
   if (Q.vtype[u] != kAny) return (G.toff[Q.vtype[u] + 1] - G.toff[Q.vtype[u]] + 1023) / 1024;
   return G.W1;
+}
+// The vertices whose sets the filter builds: the first visited vertex, and
+// for the refinement baseline every spanning-tree child reached against its
+// edge's direction (without the incoming graph only a scan finds those).
+__device__ __forceinline__ bool filled_by_filter(const DQuery &Q, uint32_t u) {
+  if (u == Q.visit[0]) return true;
+  if (!(Q.refine_flags & kRefineBase) || Q.parent[u] == 0xFF) return false;
+  return Q.esrc[Q.pedge[u]] == u;  // edge u -> parent: the parent's in-edges would be needed
+}
+__device__ __forceinline__ uint32_t filter_items(const DevGraph &G, const DQuery &Q) {
+  if (Q.status != QS_OK || Q.nvisit == 0) return 0;
+  uint32_t n = 0;
+  for (uint32_t u = 0; u < Q.k; ++u)
+    if (filled_by_filter(Q, u)) n += vertex_filter_items(G, Q, u);
+  return n;
 }
 
 // Degree-signature part of the candidate test (type and binding known to
@@ -399,8 +414,17 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
     const uint32_t qi = tile_seg<32>(warp, W.nq, it, [&](uint32_t s) { return W.fscan[s]; });
     const DQuery &Q = W.dq[qi];
     if (Q.status != QS_OK) continue;
-    const uint32_t u = Q.visit[0];
-    const uint32_t j = (uint32_t)(it - W.fscan[qi]);
+    uint32_t u = Q.visit[0];
+    uint32_t j = (uint32_t)(it - W.fscan[qi]);
+    if (Q.refine_flags & kRefineBase) {  // item j of the filled vertices in index order
+      for (uint32_t x = 0; x < Q.k; ++x) {
+        if (!filled_by_filter(Q, x)) continue;
+        const uint32_t n = vertex_filter_items(G, Q, x);
+        u = x;
+        if (j < n) break;
+        j -= n;
+      }
+    }
     uint32_t *slot = slot_of(W, Q.qv_base + u);
     const uint32_t nneed = Q.need_begin[u + 1] - Q.need_begin[u];
     if (Q.vbind[u] != kUnbound) {
@@ -420,7 +444,8 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
         if (x < e0) {
           const uint32_t v = G.tvid[x];
           w = v >> 5;
-          if (sig_ok_listed(G, Q, u, x) && (W.c0_only || masks_ok_listed(G, Q, u, x)) && wmask_ok(Q, u, v))
+          const bool masks = W.c0_only || (Q.refine_flags & kRefineBase) || masks_ok_listed(G, Q, u, x);
+          if (sig_ok_listed(G, Q, u, x) && masks && wmask_ok(Q, u, v))
             bits = 1u << (v & 31);
         }
 #pragma unroll
@@ -663,9 +688,10 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, co
 // ============================================================ explore
 // kernel_explore (Algorithm "Candidate nodes initialization"): one tile of G
 // lanes per candidate v of the visited vertex u (the thesis gives a hub a
-// whole block; here a relation run longer than 16 passes of the tile is cut
-// into chunks that a second launch spreads over whole warps, and a third
-// launch drops the candidates whose queued runs held no match).  v is dropped when some
+// whole block; here, when long_run > 0, a relation run longer than long_run
+// entries is cut into chunks that a second launch spreads over whole warps,
+// and a third launch drops the candidates whose queued runs held no match;
+// the autotuner chooses long_run).  v is dropped when some
 // query neighbour w of u has no candidate among v's data neighbours over the
 // edge's relation and direction (a neighbour whose set is not built yet is
 // tested with the candidate test); otherwise v's neighbours that pass the
@@ -703,7 +729,7 @@ __device__ __forceinline__ bool queue_run(const cg::thread_block_tile<G> &t, con
 }
 
 template <int G>
-__global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) {
+__global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step, uint32_t long_run) {
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const DevGraph &Gr = W.G;
   const uint32_t r = tile.thread_rank();
@@ -726,7 +752,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
     // relation and direction: the neighbour-type masks of all edges, loaded
     // together, reject most candidates before any row is read
     bool keep = true;
-    for (uint32_t i = i0; i < i1; ++i) {
+    for (uint32_t i = i0; i < i1 && !(Q.refine_flags & kRefineBase); ++i) {
       const uint32_t xi = Q.xinc[i];
       const uint32_t t = Q.vtype[xinc_w(xi)];
       if (t == kAny) continue;
@@ -737,13 +763,13 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
     // edges to vertices other than the children initialised by this step
     for (uint32_t i = i0; i < i1 && keep; ++i) {
       const uint32_t xi = Q.xinc[i];
-      if (xinc_role(xi) == 2) continue;
+      if (xinc_role(xi) >= 2) continue;  // children below; role 3: not checked (refinement baseline)
       const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
       const uint32_t w = xinc_w(xi);
       uint64_t base, lo, hi;
       uint32_t xs;
       const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
-      if (hi - lo > 16 * G && i - i0 < 32 && queue_run<G>(tile, W, it, i - i0, lo, hi)) {
+      if (long_run && hi - lo > long_run && i - i0 < 32 && queue_run<G>(tile, W, it, i - i0, lo, hi)) {
         need |= 1u << (i - i0);
         bytes += 16;
         continue;
@@ -773,7 +799,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
       uint64_t base, lo, hi;
       uint32_t xs;
       const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
-      if (hi - lo > 16 * G && i - i0 < 32 && queue_run<G>(tile, W, it, i - i0, lo, hi)) {
+      if (long_run && hi - lo > long_run && i - i0 < 32 && queue_run<G>(tile, W, it, i - i0, lo, hi)) {
         need |= 1u << (i - i0);
         bytes += 16;
         continue;
@@ -1730,26 +1756,46 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
 // Sort keys of every large row, in query order (row i of a query at
 // lrg_row_base + i); for a query to be cut at cap, the smallest and largest
 // key (one atomic per warp when the warp's rows share a query).
-__global__ void k_sort_keys(Wave W, uint32_t *perm, SortKey *keys) {
+// A warp whose 32 rows belong to one query first copies their words into
+// shared memory with coalesced loads (rows are contiguous there), then each
+// lane builds its row's key from shared memory.
+__global__ void __launch_bounds__(256) k_sort_keys(Wave W, uint32_t *perm, SortKey *keys) {
+  __shared__ uint32_t stage[256 / 32][32 * kMaxK];
   const uint64_t n = W.ctrl->len[6];
-  const uint32_t b = W.G.idbits, lane = threadIdx.x & 31;
+  const uint32_t b = W.G.idbits, lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   for (uint64_t base = gtid() - lane; base < n; base += gthreads()) {
     const uint64_t i = base + lane;
     uint32_t qi = 0xFFFFFFFFu;
     uint64_t key = 0;
-    if (i < n) {
-      qi = seg_of_large(W.qs, W.nq, i, false);
+    if (i < n) qi = seg_of_large(W.qs, W.nq, i, false);
+    const uint32_t q0 = __shfl_sync(kFull, qi, 0);
+    if (__all_sync(kFull, i >= n || qi == q0)) {  // warp-uniform
+      const DQuery &Q = W.dq[q0];
+      const QState &S = W.qs[q0];
+      const uint64_t local0 = base - S.lrg_row_base;
+      const uint32_t rows = (uint32_t)(n - base < 32 ? n - base : 32), words = rows * Q.k;
+      const uint32_t *src = W.out + S.out_word_base + local0 * Q.k;
+      for (uint32_t w = lane; w < words; w += 32) stage[wib][w] = src[w];
+      __syncwarp();
+      if (i < n) {
+        const uint32_t *x = stage[wib] + lane * Q.k;
+        const SortKey k2 = sort_key(Q.kp, b, [&](uint32_t c) { return x[Q.opos[c]]; });
+        key = k2.hi;  // the selection works on the leading word
+        keys[i] = k2;
+        perm[i] = (uint32_t)(S.out_row_base + local0 + lane);
+      }
+      __syncwarp();
+    } else if (i < n) {
       const DQuery &Q = W.dq[qi];
       const QState &S = W.qs[qi];
       const uint64_t local = i - S.lrg_row_base;
       const uint32_t *x = W.out + S.out_word_base + local * Q.k;
       const SortKey k2 = sort_key(Q.kp, b, [&](uint32_t c) { return x[Q.opos[c]]; });
-      key = k2.hi;  // the selection works on the leading word
+      key = k2.hi;
       keys[i] = k2;
       perm[i] = (uint32_t)(S.out_row_base + local);
     }
     const bool sel = i < n && W.sel[qi].state == 1;
-    const uint32_t q0 = __shfl_sync(kFull, qi, 0);
     if (__all_sync(kFull, sel && qi == q0)) {
       uint64_t lo = key, hi = key;
 #pragma unroll
@@ -2329,13 +2375,14 @@ void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t
                           uint64_t cap, int hw_slot, cudaStream_t s, int sms) {
   k_compact_write<<<persistent_grid(k_compact_write, sms), kThreads, 0, s>>>(W, mode, scan, dst, owner, cap, hw_slot);
 }
-void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms) {
+void launch_explore(const Wave &W, uint32_t step, int group, uint32_t long_run, cudaStream_t s, int sms) {
   switch (group) {
-    case 4: k_explore<4><<<persistent_grid(k_explore<4>, sms), kThreads, 0, s>>>(W, step); break;
-    case 8: k_explore<8><<<persistent_grid(k_explore<8>, sms), kThreads, 0, s>>>(W, step); break;
-    case 16: k_explore<16><<<persistent_grid(k_explore<16>, sms), kThreads, 0, s>>>(W, step); break;
-    default: k_explore<32><<<persistent_grid(k_explore<32>, sms), kThreads, 0, s>>>(W, step); break;
+    case 4: k_explore<4><<<persistent_grid(k_explore<4>, sms), kThreads, 0, s>>>(W, step, long_run); break;
+    case 8: k_explore<8><<<persistent_grid(k_explore<8>, sms), kThreads, 0, s>>>(W, step, long_run); break;
+    case 16: k_explore<16><<<persistent_grid(k_explore<16>, sms), kThreads, 0, s>>>(W, step, long_run); break;
+    default: k_explore<32><<<persistent_grid(k_explore<32>, sms), kThreads, 0, s>>>(W, step, long_run); break;
   }
+  if (!long_run) return;
   k_explore_runs<<<persistent_grid(k_explore_runs, sms), kThreads, 0, s>>>(W, step);
   k_explore_decide<<<persistent_grid(k_explore_decide, sms), kThreads, 0, s>>>(W, step);
 }

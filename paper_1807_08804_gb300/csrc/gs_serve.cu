@@ -7,9 +7,11 @@
 // are kept per ticket until polled.
 //
 // Admission estimate per query (from candidate-set sizes): a bound vertex has
-// one candidate, a typed vertex at most the number of data vertices of its
-// type, an untyped one at most V; each candidate costs its list entry, its
-// candidate-edge table entries and a bitmap slot share.
+// one candidate; a free vertex has the expected size of its Definition 3.3
+// set, from the graph's per-type signature statistics (the vertices of its
+// type, or of any type, meeting each of its degree needs; exact for one
+// need, a product of fractions for several); each candidate costs its list
+// entry, its candidate-edge table entries and a bitmap slot share.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -98,14 +100,21 @@ cudaError_t slot_query(cudaEvent_t ev) {
   return cudaEventQuery(ev);
 }
 
-uint64_t estimate(const gs_graph *g, const gs_query &q) {
+uint64_t estimate(const gs_graph *g, const DQuery &d) {
   const uint64_t slot_bytes = 4 * (((uint64_t)g->d.W0 + g->d.W1 + g->d.ipg + 31) / 32 * 32);
+  const uint32_t T = g->d.T, P = 2 * g->d.R + 2;
   uint64_t est = 1 << 16;
-  for (uint32_t u = 0; u < q.k; ++u) {
-    uint64_t c = q.vbind[u] != GS_UNBOUND ? 1 : (q.vtype[u] != GS_ANY && q.vtype[u] < g->d.T ? g->type_count[q.vtype[u]] : g->d.V);
-    uint64_t deg = 0;
-    for (uint32_t j = 0; j < q.m; ++j) deg += (q.esrc[j] == u) + (q.edst[j] == u);
-    est += c * 4 * (2 + deg) + slot_bytes;
+  for (uint32_t u = 0; u < d.k; ++u) {
+    double c = 1.0;
+    if (d.vbind[u] == GS_UNBOUND) {
+      const uint32_t t = d.vtype[u] == GS_ANY ? T : d.vtype[u];
+      const double n = t == T ? (double)g->d.V : (double)g->type_count[t];
+      c = n;
+      for (uint32_t i = d.need_begin[u]; i < d.need_begin[u + 1] && n > 0; ++i)
+        c *= (double)g->sigge_host[((uint64_t)t * P + d.need_plane[i]) * 16 + d.need_cnt[i]] / n;
+    }
+    const uint64_t deg = d.inc_begin[u + 1] - d.inc_begin[u];
+    est += (uint64_t)(c + 1.0) * 4 * (2 + deg) + slot_bytes;
   }
   return est;
 }
@@ -318,7 +327,7 @@ extern "C" gs_status gs_serve_submit(gs_server *s, const gs_query *q, const gs_m
   if (opts) r.opts = *opts;
   r.opts.cuda_stream = nullptr;
   r.t_submit = Clock::now();
-  r.est = estimate(s->g, *q);
+  r.est = estimate(s->g, d);
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->pending.size() >= s->o.queue_depth) return fail(GS_ERR_BUSY, "serving queue full");

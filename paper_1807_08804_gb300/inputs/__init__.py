@@ -233,6 +233,7 @@ class Workload:
     target_s: float = 0.0  # Zipf exponent of edge targets (0 = uniform)
     copy_p: float = 0.0  # share of vertices copying the out-list of an earlier vertex of their type and degree
     deltas: tuple = ()  # compression thresholds per level (matching through a compressed graph)
+    count_only: bool = False  # measured in count-only mode
 
     def graph(self) -> Graph:
         return make_graph(self.V, self.E, seed=self.seed if self.graph_seed is None else self.graph_seed,
@@ -277,6 +278,10 @@ WORKLOADS = {
                              copy_p=0.8, deltas=(0.8, 0.7, 0.7)),
     "compress-1m": Workload("compress-1m", 1_000_000, 8_000_000, 1000, 4, 10, 0.2, 1 << 22, 0x6753007,
                             target_s=1.3, copy_p=0.8, deltas=(0.8, 0.7, 0.7)),
+    # the single-1m graph with 200 queries of 16 vertices (the most the engine takes), half of them
+    # cyclic, typed or bound as in single-1m (refinement measurements against the thesis's baseline)
+    "ablation16-1m": Workload("ablation16-1m", 1_000_000, 8_000_000, 200, 16, 16, 0.2, 1 << 20, 0x6753002,
+                              cyclic_half=True, count_only=True),
     # the single-10k and single-1m workloads with 30% of query edges variable
     "single-10k-var": Workload("single-10k-var", 10_000, 60_000, 100, 3, 6, 0.2, 1 << 20, 0x6753001, p_var=0.3),
     "single-1m-var": Workload("single-1m-var", 1_000_000, 8_000_000, 1000, 4, 10, 0.2, 1 << 22, 0x6753002,

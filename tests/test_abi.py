@@ -44,7 +44,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     pairs = [("gs_graph_desc", gs.GraphDesc), ("gs_query", gs.QueryDesc), ("gs_match_opts", gs.MatchOpts),
              ("gs_result", gs.ResultDesc), ("gs_serve_opts", gs.ServeOpts), ("gs_khop_opts", gs.KhopOpts),
-             ("gs_cgraph_info", gs.CGraphInfo)]
+             ("gs_cgraph_info", gs.CGraphInfo), ("gs_tuning", gs.Tuning)]
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gs.h"', "int main(void) {"]
     for cname, py in pairs:
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')

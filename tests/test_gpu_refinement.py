@@ -1,6 +1,7 @@
 """Refinement variants (Section 3.3.3 and the refinement experiments of
 Section 3.6): no refinement, one query vertex at a time in reversed order,
-and skipping low-connectivity vertices only prune candidates, so every
+skipping low-connectivity vertices and the thesis's comparison baseline
+(outgoing graph only, spanning-tree exploration) only prune candidates, so every
 result equals the oracle's; refined to convergence in either order the
 candidate sets are the unique fixpoint, so even the join's partial-embedding
 sizes agree."""
@@ -15,7 +16,7 @@ from tests.helpers import random_tiny
 pytestmark = pytest.mark.gpu
 
 VARIANTS = [(0, 64), (gs.GS_REFINE_REVERSED, 64), (gs.GS_REFINE_REVERSED, 1), (gs.GS_REFINE_OFF, 1),
-            (gs.GS_REFINE_REVERSED | gs.GS_REFINE_LOW(1), 1), (gs.GS_REFINE_LOW(2), 3)]
+            (gs.GS_REFINE_REVERSED | gs.GS_REFINE_LOW(1), 1), (gs.GS_REFINE_LOW(2), 3), (gs.GS_REFINE_BASELINE, 1)]
 
 
 def test_variants_on_tiny_instances():
@@ -57,6 +58,10 @@ def test_variants_on_workload(small):
     np.testing.assert_array_equal(conv[0], rev[0])
     np.testing.assert_array_equal(conv[1], rev[1])
     assert (conv[1] <= conv[0]).all() and conv[0].sum() > 0
+    # the baseline (outgoing graph only, spanning-tree exploration) never has
+    # smaller intermediate results than the converged sets
+    base = sizes[(gs.GS_REFINE_BASELINE, 1)]
+    assert (base[0] >= conv[0]).all() and base[0].sum() > conv[0].sum()
 
 
 def test_unknown_refine_flags_rejected(small):

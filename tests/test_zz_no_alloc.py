@@ -25,8 +25,10 @@ def test_static_filter_equals_allocating_filter_twice():
     count = torch.empty(1, dtype=torch.int64, device="cuda")
     L = gs.lib()
     checked = 0
-    for q in qs:
-        want = gs.inspect_candidates(dg, q, gs.GS_STAGE_FILTER)
+    wants = [gs.inspect_candidates(dg, q, gs.GS_STAGE_FILTER) for q in qs]  # allocating reference, first
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for q, want in zip(qs, wants):
         pack = gs._QueryPack([q])
         for u in range(q.k):
             for call in range(2):  # two calls in a row share the scratch
@@ -42,6 +44,9 @@ def test_static_filter_equals_allocating_filter_twice():
                 np.testing.assert_array_equal(got, want[u])
                 checked += 1
     assert checked >= 2 * 12 * 3
+    # the calls allocated nothing: the device's free memory did not move
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     # a short output buffer: the count stays exact, only cap_ids ids are written
     q = qs[0]
     u = int(np.argmax([x.shape[0] for x in gs.inspect_candidates(dg, q, gs.GS_STAGE_FILTER)]))
