@@ -469,8 +469,6 @@ def run_profile_once(args):
     if args.group or args.rounds:
         gs.tune_set(dg, args.group, args.rounds)
     b = gs.Batch(dg, qs, cap=w.cap)
-    if args.long_run is not None:
-        b.configure(use_graph=True, group=args.group or 32, refine_rounds=args.rounds, long_run=args.long_run)
     for _ in range(args.runs):
         b.run()
         b.finish()
@@ -515,8 +513,6 @@ def main():
     ap.add_argument("--group", type=int, default=0, help="--profile-once: lanes per work item (0 = default)")
     ap.add_argument("--rounds", type=int, default=0,
                     help="--profile-once: refinement rounds (0 = default, 4294967295 = none)")
-    ap.add_argument("--long-run", type=int, default=None,
-                    help="--profile-once: exploration's long-run split (entries; 0 = none)")
     args = ap.parse_args()
     if args.profile_once:
         run_profile_once(args)

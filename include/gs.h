@@ -286,11 +286,6 @@ gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_t refine_ro
  * (2,048 counts) publishes nothing, so each later tile's wait runs to the
  * bound.  Applies to the batch's later runs, in stream order.  Errors:
  * GS_ERR_INVALID (null batch, unknown flag), GS_ERR_CUDA. */
-/* Exploration (kernel_explore): relation runs longer than long_run entries
- * are cut into chunks that whole warps scan in a second launch instead of
- * one candidate's lanes (0 = never; otherwise at least 32).  Results do not
- * depend on it.  Errors: GS_ERR_INVALID. */
-gs_status gs_batch_set_long_run(gs_batch *b, uint32_t long_run);
 #define GS_WAIT_WITHHOLD_FIRST_TILE 1u
 gs_status gs_batch_set_wait(gs_batch *b, uint32_t max_polls, uint32_t flags);
 /* Kernels launched by runs so far, bytes moved between host and device, and
@@ -316,8 +311,7 @@ gs_status gs_stats_reset(gs_batch *b);
  * Autotuning.  Times the captured pipeline on the given queries for each
  * lanes-per-work-item setting (4, 8, 16, 32: the lanes that share one
  * candidate vertex, edge-table key or partial embedding) and each number of
- * refinement rounds (none, 1, 2, 4) and each exploration long-run length
- * (never, 256, 1,024 entries), and keeps the fastest for batches created on
+ * refinement rounds (none, 1, 2, 4), and keeps the fastest for batches created on
  * this graph afterwards.  Results never depend on these settings.  With
  * cache_path != NULL the choice is read from / appended to that text file,
  * keyed by graph content hash, GPU name and a signature of the query load
@@ -326,9 +320,6 @@ gs_status gs_stats_reset(gs_batch *b);
 typedef struct {
   uint32_t group;          /* lanes per work item */
   uint32_t refine_rounds;  /* refinement rounds in captured runs */
-  uint32_t long_run;       /* exploration: relation runs longer than this many entries are
-                              scanned by whole warps in a second launch (0 = never) */
-  uint32_t reserved;
   double ms;               /* best time of one run of the given queries */
   uint32_t from_cache;     /* 1 if read from cache_path */
   uint32_t configs_tried;

@@ -82,8 +82,8 @@ class KernelStats(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("group", U32), ("refine_rounds", U32), ("long_run", U32), ("reserved", U32),
-                ("ms", ctypes.c_double), ("from_cache", U32), ("configs_tried", U32)]
+    _fields_ = [("group", U32), ("refine_rounds", U32), ("ms", ctypes.c_double), ("from_cache", U32),
+                ("configs_tried", U32)]
 
 
 class ServeOpts(ctypes.Structure):
@@ -139,7 +139,6 @@ EXTRA_SIGNATURES = {
                                ctypes.POINTER(Tuning)]),
     "gs_tune_set": (ctypes.c_int, [P, U32, U32]),
     "gs_batch_set_wait": (ctypes.c_int, [P, U32, U32]),
-    "gs_batch_set_long_run": (ctypes.c_int, [P, U32]),
     "gs_match_batch_shared": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts),
                                              ctypes.POINTER(ResultDesc), ctypes.POINTER(P)]),
     "gs_rows_base": (P, [P]),
@@ -496,10 +495,8 @@ class Batch:
         else:
             _check(lib().gs_batch_create(dg._h, self._pack.arr, self.n, ctypes.byref(o), ctypes.byref(self._h)))
 
-    def configure(self, use_graph=True, group=32, refine_rounds=0, long_run=None):
+    def configure(self, use_graph=True, group=32, refine_rounds=0):
         _check(lib().gs_batch_set(self._h, 1 if use_graph else 0, group, refine_rounds))
-        if long_run is not None:
-            _check(lib().gs_batch_set_long_run(self._h, long_run))
 
     def set_wait(self, max_polls=0, withhold_first_tile=False):
         """Bound of the prefix scans' look-back waits (0 = default); with
@@ -568,8 +565,8 @@ def tune(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, cache_path: s
     t = Tuning()
     _check(lib().gs_tune(dg._h, pack.arr, len(queries), ctypes.byref(o),
                          cache_path.encode() if cache_path else None, ctypes.byref(t)))
-    return {"group": t.group, "refine_rounds": t.refine_rounds, "long_run": t.long_run, "ms": t.ms,
-            "from_cache": bool(t.from_cache), "configs_tried": t.configs_tried}
+    return {"group": t.group, "refine_rounds": t.refine_rounds, "ms": t.ms, "from_cache": bool(t.from_cache),
+            "configs_tried": t.configs_tried}
 
 
 def tune_set(dg: DeviceGraph, group: int = 0, refine_rounds: int = 0) -> None:

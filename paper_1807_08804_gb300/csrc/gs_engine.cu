@@ -240,10 +240,6 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   A(W.tlist_q, s.tlist);
   A(W.alist_q, s.alist);
   A(W.fcnt, W.nq);
-  A(W.xneed, s.tlist);
-  A(W.xfound, s.tlist);
-  W.xq_cap = std::min<uint64_t>(std::max<uint64_t>(s.tlist / 4, 1ull << 12), 1ull << 20);
-  A(W.xq, W.xq_cap);
   if ((uint64_t)W.nqv * cps >= (1ull << 32)) return fail(GS_ERR_UNSUPPORTED, "batch too large for the chunk index");
   A(W.clist, (uint64_t)W.nqv * cps);
   A(W.fscan, (uint64_t)W.nq + 1);
@@ -415,9 +411,13 @@ void enqueue_front(Pipe &P, int K) {
     launch_compact_write(W, 0, step, W.cscan, W.tlist, W.tlist_q, W.tlist_cap, HW_TLIST, P.cur, sms);
     P.end();
     P.begin(KK_EXPLORE);
-    launch_explore(W, step, grp, b->long_run, P.cur, sms);
+    launch_explore(W, step, grp, P.cur, sms);
     P.end();
   }
+  // the refinement work list (every candidate of every query vertex) is
+  // needed only when some refinement round will run
+  const bool refines = b->refine_rounds > 0 || (!b->use_graph && b->fixpoint);
+  if (!refines) return;
   P.begin(KK_COMPACT_ALL);
   launch_compact_count(W, 1, 0, P.cur, sms);
   scan_u32(W.ccount, W.ascan, &W.ctrl->len[1], (uint64_t)W.nqv * cps, b->scan_tmp, P.cur, sms);
@@ -758,7 +758,6 @@ gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_mat
   opts_key(b, opts);
   if (g->tuned_group) b->group = g->tuned_group;
   if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds == GS_ROUNDS_NONE ? 0 : g->tuned_rounds;
-  b->long_run = g->tuned_long_run;
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
     b->fixpoint = false;
@@ -828,7 +827,6 @@ gs_status batch_create_capacity(gs_graph *g, const gs_match_opts *opts, uint32_t
   opts_key(b, opts);
   if (g->tuned_group) b->group = g->tuned_group;
   if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds == GS_ROUNDS_NONE ? 0 : g->tuned_rounds;
-  b->long_run = g->tuned_long_run;
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
     b->fixpoint = false;
@@ -1172,14 +1170,6 @@ extern "C" gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_
     b->refine_rounds = 8;
     b->fixpoint = true;
   }
-  return GS_OK;
-}
-
-extern "C" gs_status gs_batch_set_long_run(gs_batch *b, uint32_t long_run) {
-  if (!b) return fail(GS_ERR_INVALID, "gs_batch_set_long_run: null batch");
-  if (long_run && long_run < 32) return fail(GS_ERR_INVALID, "long_run must be 0 or at least 32");
-  drop_graphs(b);
-  b->long_run = long_run;
   return GS_OK;
 }
 

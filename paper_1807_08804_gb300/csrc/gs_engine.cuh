@@ -186,16 +186,6 @@ struct Ctrl {
   uint64_t over_cap;                // large outputs with more rows than cap (selected before sorting)
   uint64_t fin_words;               // words of the rows returned by this wave
   uint64_t bytes[KK_N];             // algorithmic bytes per kernel kind
-  uint64_t xq_top;                  // exploration: chunks of long relation runs queued this step
-};
-
-// A piece of a long relation run that exploration hands to a second launch:
-// entries [lo, lo + len) of the adjacency row of candidate tlist[it], over its
-// incident edge `inc` (position in u's incident list).
-struct XChunk {
-  uint32_t it, inc;
-  uint64_t lo;
-  uint32_t len, pad;
 };
 
 // Everything a kernel needs, passed by value.  Capacities are fixed when the
@@ -225,8 +215,6 @@ struct Wave {
   uint32_t *alist; uint64_t alist_cap;   // every set before refinement
   uint32_t *tlist_q, *alist_q;           // owner of each entry: query / global query vertex
   uint32_t *fcnt; uint64_t *fscan;       // filter work items per query [nq] and their scan [nq + 1]
-  uint32_t *xneed, *xfound;              // per exploration item: incident edges whose runs were queued / found
-  XChunk *xq; uint64_t xq_cap;           // queued chunks of long relation runs
   uint64_t *clist;                       // non-empty chunks of a compaction: (gqv << 32) | count index
   uint32_t *flist; uint64_t flist_cap;   // final sets
   uint64_t *flist_off;              // [nqv]
@@ -265,9 +253,7 @@ void launch_filter(const Wave &W, cudaStream_t s, int sms);
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms);
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint32_t *owner,
                           uint64_t cap, int hw_slot, cudaStream_t s, int sms);
-// long_run > 0: relation runs longer than long_run entries go to a queue of
-// chunks scanned by whole warps in a second launch (0 = every run inline).
-void launch_explore(const Wave &W, uint32_t step, int group, uint32_t long_run, cudaStream_t s, int sms);
+void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms);
 // sub: kAllSub refines every vertex of every query; j < kMaxK refines, in
 // queries with kRefineRev, the vertex rorder[j] (other queries at j = 0).
 constexpr uint32_t kAllSub = 0xFFFFFFFFu;

@@ -59,7 +59,6 @@ struct gs_batch {
   int sms = 0;
   int group = 32;
   uint32_t refine_rounds = 8;
-  uint32_t long_run = 0;           // exploration: runs longer than this go to whole warps (0 = never)
   bool fixpoint = true;            // loop rounds on the host until nothing changes (non-graph runs)
   bool use_graph = true;
   uint32_t n = 0;

@@ -88,7 +88,6 @@ struct gs_graph {
   void *khop;               // buffers of the domain-graph exploration
   uint32_t tuned_group;     // lanes per work item chosen by gs_tune (0 = default)
   uint32_t tuned_rounds;    // refinement rounds chosen by gs_tune (0 = default)
-  uint32_t tuned_long_run;  // exploration's long-run split chosen by gs_tune (0 = none)
 };
 
 namespace gs {

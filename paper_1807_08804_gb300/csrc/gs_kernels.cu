@@ -366,33 +366,15 @@ __device__ __forceinline__ uint32_t filter_items(const DevGraph &G, const DQuery
   return n;
 }
 
-// Degree-signature part of the candidate test (type and binding known to
-// pass) and the neighbour-type test, for the vertex at position x of the
-// type lists, read from the type-ordered planes (contiguous for consecutive
-// x).  The neighbour-type test: for every edge of u to a typed vertex w, the
+// The typed path tests each vertex of u's type list (type and binding known
+// to pass) against the degree signatures and the neighbour-type masks, read
+// from the type-ordered planes (contiguous for consecutive list positions).
+// The neighbour-type test: for every edge of u to a typed vertex w, the
 // vertex's neighbours over the edge's relation and direction include one
 // whose type matches w's modulo 32.  Every candidate exploration keeps
 // passes it, so applying it to the first visited vertex in the filter
 // changes no set after the first exploration step; it only spares the
 // exploration the candidates that fail.
-__device__ __forceinline__ bool sig_ok_listed(const DevGraph &G, const DQuery &Q, uint32_t u, uint32_t x) {
-  for (uint32_t i = Q.need_begin[u]; i < Q.need_begin[u + 1]; ++i) {
-    const uint32_t w = G.sig_t[(uint64_t)Q.need_plane[i] * G.sig_words + (x >> 3)];
-    if (((w >> ((x & 7) * 4)) & 15u) < Q.need_cnt[i]) return false;
-  }
-  return true;
-}
-__device__ __forceinline__ bool masks_ok_listed(const DevGraph &G, const DQuery &Q, uint32_t u, uint32_t x) {
-  bool ok = true;
-  for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1]; ++i) {
-    const uint32_t xi = Q.xinc[i];
-    const uint32_t t = Q.vtype[xinc_w(xi)];
-    if (t == kAny) continue;
-    const uint32_t m = G.tmask_t[(uint64_t)sig_plane(xinc_dir(xi), xinc_rel(xi), G.R) * G.V + x];
-    ok = ok && ((m >> (t & 31u)) & 1u);
-  }
-  return ok;
-}
 
 // OR `bits` into level-0 word w0, raising the summary bits when the word was empty.
 __device__ __forceinline__ void word_or(const Wave &W, uint32_t *slot, uint32_t w0, uint32_t bits) {
@@ -436,26 +418,55 @@ __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
       // 32 rounds of 32 consecutive type-list entries; the ids ascend, so the
       // lanes that share a level-0 word are contiguous: a segmented OR over
       // them leaves one atomic per touched word
+      // Four rounds at a time: every test's loads for the four rounds are
+      // issued together (the entries' ids, each degree need's signature
+      // word, each typed neighbour's mask), then the four segmented ORs.
       const uint32_t t = Q.vtype[u];
       const uint32_t b0 = G.toff[t] + j * 1024, e0 = min(b0 + 1024, G.toff[t + 1]);
-      for (uint32_t x0 = b0; x0 < e0; x0 += 32) {
-        const uint32_t x = x0 + lane;
-        uint32_t w = 0xFFFFFFFFu, bits = 0;
-        if (x < e0) {
-          const uint32_t v = G.tvid[x];
-          w = v >> 5;
-          const bool masks = W.c0_only || (Q.refine_flags & kRefineBase) || masks_ok_listed(G, Q, u, x);
-          if (sig_ok_listed(G, Q, u, x) && masks && wmask_ok(Q, u, v))
-            bits = 1u << (v & 31);
+      const bool masks = !W.c0_only && !(Q.refine_flags & kRefineBase);
+      for (uint32_t x0 = b0; x0 < e0; x0 += 128) {
+        uint32_t v[4];
+        bool ok[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t x = x0 + 32 * q + lane;
+          ok[q] = x < e0;
+          v[q] = ok[q] ? G.tvid[x] : 0u;
+        }
+        for (uint32_t i = Q.need_begin[u]; i < Q.need_begin[u + 1]; ++i) {
+          const uint32_t *plane = G.sig_t + (uint64_t)Q.need_plane[i] * G.sig_words;
+          const uint32_t c = Q.need_cnt[i];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t x = x0 + 32 * q + lane;
+            if (ok[q]) ok[q] = ((plane[x >> 3] >> ((x & 7) * 4)) & 15u) >= c;
+          }
+        }
+        for (uint32_t i = Q.inc_begin[u]; i < Q.inc_begin[u + 1] && masks; ++i) {
+          const uint32_t xi = Q.xinc[i];
+          const uint32_t tw = Q.vtype[xinc_w(xi)];
+          if (tw == kAny) continue;
+          const uint32_t *mp = G.tmask_t + (uint64_t)sig_plane(xinc_dir(xi), xinc_rel(xi), G.R) * G.V;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t x = x0 + 32 * q + lane;
+            if (ok[q]) ok[q] = (mp[x] >> (tw & 31u)) & 1u;
+          }
         }
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_down_sync(kFull, bits, o);
-          const uint32_t w2 = __shfl_down_sync(kFull, w, o);
-          if (lane + o < 32 && w2 == w) bits |= y;
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t x = x0 + 32 * q + lane;
+          const uint32_t w = x < e0 ? v[q] >> 5 : 0xFFFFFFFFu;
+          uint32_t bits = ok[q] && wmask_ok(Q, u, v[q]) ? 1u << (v[q] & 31) : 0u;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_down_sync(kFull, bits, o);
+            const uint32_t w2 = __shfl_down_sync(kFull, w, o);
+            if (lane + o < 32 && w2 == w) bits |= y;
+          }
+          const uint32_t wp = __shfl_up_sync(kFull, w, 1);
+          if ((lane == 0 || wp != w) && w != 0xFFFFFFFFu && bits) word_or(W, slot, w, bits);
         }
-        const uint32_t wp = __shfl_up_sync(kFull, w, 1);
-        if ((lane == 0 || wp != w) && w != 0xFFFFFFFFu && bits) word_or(W, slot, w, bits);
       }
       if (lane == 0) acc += (uint64_t)(e0 - b0) * (4 + nneed);
       continue;
@@ -687,11 +698,7 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, co
 
 // ============================================================ explore
 // kernel_explore (Algorithm "Candidate nodes initialization"): one tile of G
-// lanes per candidate v of the visited vertex u (the thesis gives a hub a
-// whole block; here, when long_run > 0, a relation run longer than long_run
-// entries is cut into chunks that a second launch spreads over whole warps,
-// and a third launch drops the candidates whose queued runs held no match;
-// the autotuner chooses long_run).  v is dropped when some
+// lanes per candidate v of the visited vertex u.  v is dropped when some
 // query neighbour w of u has no candidate among v's data neighbours over the
 // edge's relation and direction (a neighbour whose set is not built yet is
 // tested with the candidate test); otherwise v's neighbours that pass the
@@ -702,34 +709,8 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, co
 // nothing; a candidate dropped by a later child edge may leave extra bits in
 // an earlier child's set, which keeps the sets supersets of the exact ones
 // (refinement removes them).
-constexpr uint32_t kXChunk = 256;  // entries per queued chunk
-
-// Queue the run [lo, hi) of item `it` over its incident edge `inc` as chunks
-// for k_explore_runs.  Returns false (nothing queued, the tile scans the run
-// itself) when the queue is full.
 template <int G>
-__device__ __forceinline__ bool queue_run(const cg::thread_block_tile<G> &t, const Wave &W, uint64_t it, uint32_t inc,
-                                          uint64_t lo, uint64_t hi) {
-  const uint64_t n = (hi - lo + kXChunk - 1) / kXChunk;
-  uint64_t at = 0;
-  if (t.thread_rank() == 0) at = atomicAdd((unsigned long long *)&W.ctrl->xq_top, (unsigned long long)n);
-  at = t.shfl(at, 0);
-  const bool fits = at + n <= W.xq_cap;
-  for (uint64_t c = t.thread_rank(); c < n && at + c < W.xq_cap; c += G) {
-    XChunk x;
-    x.it = (uint32_t)it;
-    x.inc = inc;
-    x.lo = lo + c * kXChunk;
-    // a reservation that does not fit entirely is written as empty chunks
-    x.len = fits ? (uint32_t)(hi - x.lo < kXChunk ? hi - x.lo : kXChunk) : 0u;
-    x.pad = 0;
-    W.xq[at + c] = x;
-  }
-  return fits;
-}
-
-template <int G>
-__global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step, uint32_t long_run) {
+__global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) {
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const DevGraph &Gr = W.G;
   const uint32_t r = tile.thread_rank();
@@ -739,14 +720,10 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step, 
   for (uint64_t it = gtid() / G; it < items; it += ntile) {
     if (it >= W.tlist_cap) break;  // entries past the list belong to overflowed queries
     DQuery &Q = W.dq[W.tlist_q[it]];
-    if (Q.status != QS_OK) {
-      if (r == 0) W.xneed[it] = 0;
-      continue;
-    }
+    if (Q.status != QS_OK) continue;
     const uint32_t u = Q.visit[step];
     const uint32_t v = W.tlist[it];
     const uint32_t i0 = Q.inc_begin[u], i1 = Q.inc_begin[u + 1];
-    uint32_t need = 0;  // incident edges (position < 32) whose runs were queued
     uint64_t bytes = 0;
     // every edge to a typed vertex w needs a neighbour of w's type over its
     // relation and direction: the neighbour-type masks of all edges, loaded
@@ -769,11 +746,6 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step, 
       uint64_t base, lo, hi;
       uint32_t xs;
       const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
-      if (long_run && hi - lo > long_run && i - i0 < 32 && queue_run<G>(tile, W, it, i - i0, lo, hi)) {
-        need |= 1u << (i - i0);
-        bytes += 16;
-        continue;
-      }
       const bool built = xinc_role(xi) == 1;
       const uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
@@ -799,11 +771,6 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step, 
       uint64_t base, lo, hi;
       uint32_t xs;
       const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
-      if (long_run && hi - lo > long_run && i - i0 < 32 && queue_run<G>(tile, W, it, i - i0, lo, hi)) {
-        need |= 1u << (i - i0);
-        bytes += 16;
-        continue;
-      }
       uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
       for (uint64_t b = lo; b < hi; b += G) {
@@ -821,67 +788,9 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step, 
       if (!found) keep = false;
     }
     if (!keep && r == 0) bit_clear(slot_of(W, Q.qv_base + u), v);
-    if (r == 0) {
-      W.xneed[it] = keep ? need : 0u;  // a dropped candidate's queued runs are skipped
-      W.xfound[it] = 0;
-      acc += bytes + 4;
-    }
+    if (r == 0) acc += bytes + 4;
   }
   flush_bytes(W, KK_EXPLORE, acc);
-}
-
-// The queued chunks of long runs, one warp each: a child edge's chunk sets
-// the child's bits for every entry that passes the candidate test; every
-// chunk reports whether it held a match for its edge.
-__global__ void __launch_bounds__(kThreads) k_explore_runs(Wave W, uint32_t step) {
-  const DevGraph &Gr = W.G;
-  auto warp = cg::tiled_partition<32>(cg::this_thread_block());
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t warps = gthreads() / 32;
-  const uint64_t n = W.ctrl->xq_top < W.xq_cap ? W.ctrl->xq_top : W.xq_cap;
-  uint64_t acc = 0;
-  for (uint64_t c = gtid() / 32; c < n; c += warps) {
-    const XChunk ch = W.xq[c];
-    if (ch.len == 0 || W.xneed[ch.it] == 0) continue;
-    DQuery &Q = W.dq[W.tlist_q[ch.it]];
-    const uint32_t u = Q.visit[step];
-    const uint32_t xi = Q.xinc[Q.inc_begin[u] + ch.inc];
-    const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
-    const uint32_t w = xinc_w(xi), role = xinc_role(xi);
-    uint32_t *ws = slot_of(W, Q.qv_base + w);
-    const uint32_t *a = Gr.adj[dir];
-    bool found = false;
-    uint64_t scanned = 0;
-    for (uint64_t j0 = ch.lo; j0 < ch.lo + ch.len; j0 += 32) {
-      const uint64_t j = j0 + lane;
-      bool ok = false;
-      if (j < ch.lo + ch.len) {
-        const uint32_t x = a[j] & kNbrMask;
-        ok = role == 1 ? bit_test(ws, x) : cand_ok(Gr, Q, w, x);
-        if (ok && role == 2) bit_set(W, ws, x);
-      }
-      found = warp.any(ok) || found;
-      scanned += ch.lo + ch.len - j0 < 32 ? ch.lo + ch.len - j0 : 32;
-      if (found && role != 2) break;  // existence is all a non-child edge needs
-    }
-    if (found && lane == 0) atomicOr(&W.xfound[ch.it], 1u << ch.inc);
-    if (lane == 0) acc += 24 + 4 * scanned;
-  }
-  flush_bytes(W, KK_EXPLORE, acc);
-}
-
-// Candidates with queued runs: dropped unless every queued edge found a match.
-__global__ void __launch_bounds__(kThreads) k_explore_decide(Wave W, uint32_t step) {
-  const uint64_t all = W.cscan[(uint64_t)W.nq * W.G.nchunks];
-  const uint64_t items = all < W.tlist_cap ? all : W.tlist_cap;
-  for (uint64_t it = gtid(); it < items; it += gthreads()) {
-    const uint32_t need = W.xneed[it];
-    if (need && (W.xfound[it] & need) != need) {
-      const DQuery &Q = W.dq[W.tlist_q[it]];
-      bit_clear(slot_of(W, Q.qv_base + Q.visit[step]), W.tlist[it]);
-    }
-  }
-  if (gtid() == 0) W.ctrl->xq_top = 0;
 }
 
 // ============================================================ refine
@@ -2375,16 +2284,13 @@ void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t
                           uint64_t cap, int hw_slot, cudaStream_t s, int sms) {
   k_compact_write<<<persistent_grid(k_compact_write, sms), kThreads, 0, s>>>(W, mode, scan, dst, owner, cap, hw_slot);
 }
-void launch_explore(const Wave &W, uint32_t step, int group, uint32_t long_run, cudaStream_t s, int sms) {
+void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms) {
   switch (group) {
-    case 4: k_explore<4><<<persistent_grid(k_explore<4>, sms), kThreads, 0, s>>>(W, step, long_run); break;
-    case 8: k_explore<8><<<persistent_grid(k_explore<8>, sms), kThreads, 0, s>>>(W, step, long_run); break;
-    case 16: k_explore<16><<<persistent_grid(k_explore<16>, sms), kThreads, 0, s>>>(W, step, long_run); break;
-    default: k_explore<32><<<persistent_grid(k_explore<32>, sms), kThreads, 0, s>>>(W, step, long_run); break;
+    case 4: k_explore<4><<<persistent_grid(k_explore<4>, sms), kThreads, 0, s>>>(W, step); break;
+    case 8: k_explore<8><<<persistent_grid(k_explore<8>, sms), kThreads, 0, s>>>(W, step); break;
+    case 16: k_explore<16><<<persistent_grid(k_explore<16>, sms), kThreads, 0, s>>>(W, step); break;
+    default: k_explore<32><<<persistent_grid(k_explore<32>, sms), kThreads, 0, s>>>(W, step); break;
   }
-  if (!long_run) return;
-  k_explore_runs<<<persistent_grid(k_explore_runs, sms), kThreads, 0, s>>>(W, step);
-  k_explore_decide<<<persistent_grid(k_explore_decide, sms), kThreads, 0, s>>>(W, step);
 }
 void launch_refine(const Wave &W, uint32_t round, uint32_t sub, int group, cudaStream_t s, int sms) {
   switch (group) {

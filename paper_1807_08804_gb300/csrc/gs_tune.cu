@@ -1,7 +1,6 @@
 // Autotuner: picks the lanes per work item (the "warps per vertex" of the
-// explore, refine, edge-table and join kernels: 4, 8, 16 or 32 lanes), the
-// length above which exploration hands a relation run to whole warps (never,
-// 256 or 1,024 entries) and the number of refinement rounds (none, 1, 2 or 4: Section 3.6 finds one
+// explore, refine, edge-table and join kernels: 4, 8, 16 or 32 lanes) and
+// the number of refinement rounds (none, 1, 2 or 4: Section 3.6 finds one
 // round the fastest refined variant, and exploration already prunes every
 // candidate against all its query edges) for a graph and a kind of query load, by
 // timing the captured pipeline on the caller's queries.  Results do not
@@ -9,7 +8,7 @@
 // edge), so the choice is purely about speed.
 //
 // The choice is cached in a text file, one line per entry:
-//   <graph hash> <gpu name with '_' for spaces> <load signature> <group> <rounds> <long run> <ms>
+//   <graph hash> <gpu name with '_' for spaces> <load signature> <group> <rounds> <ms>
 // and reused by later gs_tune calls with the same key.  Batches created on
 // the graph afterwards use the tuned values.
 #include <cstdio>
@@ -54,8 +53,7 @@ uint64_t load_signature(const gs_query *qs, uint32_t n, const gs_match_opts *o) 
   return h;
 }
 
-bool cache_lookup(const char *path, const std::string &key, uint32_t *group, uint32_t *rounds, uint32_t *long_run,
-                  double *ms) {
+bool cache_lookup(const char *path, const std::string &key, uint32_t *group, uint32_t *rounds, double *ms) {
   if (!path) return false;
   std::ifstream f(path);
   std::string line;
@@ -63,13 +61,12 @@ bool cache_lookup(const char *path, const std::string &key, uint32_t *group, uin
   while (std::getline(f, line)) {
     std::istringstream is(line);
     std::string h, gpu, sig;
-    uint32_t g, r, x;
+    uint32_t g, r;
     double t;
-    if (!(is >> h >> gpu >> sig >> g >> r >> x >> t)) continue;
+    if (!(is >> h >> gpu >> sig >> g >> r >> t)) continue;
     if (h + " " + gpu + " " + sig == key) {
       *group = g;
       *rounds = r;
-      *long_run = x;
       *ms = t;
       found = true;  // the last line for a key wins
     }
@@ -77,11 +74,10 @@ bool cache_lookup(const char *path, const std::string &key, uint32_t *group, uin
   return found;
 }
 
-void cache_store(const char *path, const std::string &key, uint32_t group, uint32_t rounds, uint32_t long_run,
-                 double ms) {
+void cache_store(const char *path, const std::string &key, uint32_t group, uint32_t rounds, double ms) {
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << " " << group << " " << rounds << " " << long_run << " " << ms << "\n";
+  f << key << " " << group << " " << rounds << " " << ms << "\n";
 }
 
 }  // namespace
@@ -96,17 +92,15 @@ extern "C" gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const 
   snprintf(sk, sizeof sk, "%016llx", (unsigned long long)load_signature(qs, n, opts));
   const std::string key = std::string(hk) + " " + gpu_name(g->device) + " " + sk;
   memset(out, 0, sizeof(*out));
-  uint32_t group = 0, rounds = 0, long_run = 0;
+  uint32_t group = 0, rounds = 0;
   double best = 0;
-  if (cache_lookup(cache_path, key, &group, &rounds, &long_run, &best)) {
+  if (cache_lookup(cache_path, key, &group, &rounds, &best)) {
     out->group = group;
     out->refine_rounds = rounds;
-    out->long_run = long_run;
     out->ms = best;
     out->from_cache = 1;
     g->tuned_group = group;
     g->tuned_rounds = rounds;
-    g->tuned_long_run = long_run;
     return GS_OK;
   }
   gs_batch *b = nullptr;
@@ -117,14 +111,11 @@ extern "C" gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const 
   GS_CUDA(cudaEventCreate(&e1));
   const uint32_t groups[] = {4, 8, 16, 32};
   const uint32_t round_opts[] = {GS_ROUNDS_NONE, 1, 2, 4};
-  const uint32_t long_runs[] = {0, 256, 1024};
   best = 1e30;
   uint32_t tried = 0;
   for (uint32_t gi : groups) {
     for (uint32_t r : round_opts) {
-     for (uint32_t x : long_runs) {
       st = gs_batch_set(b, 1, (int)gi, r);
-      if (st == GS_OK) st = gs_batch_set_long_run(b, x);
       if (st != GS_OK) break;
       double tmin = 1e30;
       for (int rep = 0; rep < 4 && st == GS_OK; ++rep) {  // first run captures the graphs
@@ -143,10 +134,7 @@ extern "C" gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const 
         best = tmin;
         group = gi;
         rounds = r;
-        long_run = x;
       }
-     }
-     if (st != GS_OK) break;
     }
     if (st != GS_OK) break;
   }
@@ -156,13 +144,11 @@ extern "C" gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const 
   if (st != GS_OK) return st;
   out->group = group;
   out->refine_rounds = rounds;
-  out->long_run = long_run;
   out->ms = best;
   out->configs_tried = tried;
   g->tuned_group = group;
   g->tuned_rounds = rounds;
-  g->tuned_long_run = long_run;
-  cache_store(cache_path, key, group, rounds, long_run, best);
+  cache_store(cache_path, key, group, rounds, best);
   return GS_OK;
 }
 
