@@ -120,15 +120,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+# source section (banner name in gs_kernels.cu) of each kernel kind the bench reports
+KIND_SECTION = {"sort_large": "sort + gather", "gather": "sort + gather", "join_count": "join", "join_write": "join",
+                "ec_count": "edge tables", "ec_write": "edge tables"}
+
+
 def kernel_section_sha(kind):
     """Hash of the source of one kernel kind: the shared device helpers at the
     top of gs_kernels.cu (before the first banner) plus the text between its
-    '// ====... <kind>' banner and the next one.  A stored DRAM-traffic figure
-    is used only while this still matches."""
+    '// ====... <section>' banner and the next one.  A stored DRAM-traffic
+    figure is used only while this still matches."""
     import hashlib
     src = open(os.path.join(ROOT, "paper_1807_08804_gb300", "csrc", "gs_kernels.cu")).read()
     banner = "// " + "=" * 60 + " "
-    i = src.find(banner + kind + "\n")
+    i = src.find(banner + KIND_SECTION.get(kind, kind) + "\n")
     if i < 0:
         return None
     j = src.find(banner, i + len(banner))
@@ -469,12 +474,16 @@ def run_profile_once(args):
     if args.group or args.rounds:
         gs.tune_set(dg, args.group, args.rounds)
     b = gs.Batch(dg, qs, cap=w.cap)
+    if args.stats:
+        b.stats_enable(True)
     for _ in range(args.runs):
         b.run()
         b.finish()
     res = b.fetch()
     print(f"{len(qs)} queries, {sum(r.count for r in res)} embeddings, {sum(r.status != 0 for r in res)} not ok",
           flush=True)
+    if args.stats:  # algorithmic bytes and launches per kernel kind over the runs
+        print(json.dumps({k: v for k, v in b.stats().items() if v["launches"]}), flush=True)
     b.close()
     dg.free()
 
@@ -509,6 +518,7 @@ def main():
     ap.add_argument("--profile-once", action="store_true",
                     help="run the workload's batch --runs times and nothing else (for ncu captures)")
     ap.add_argument("--queries", type=int, default=0, help="--profile-once: the first this many queries (0 = all)")
+    ap.add_argument("--stats", action="store_true", help="--profile-once: print bytes and launches per kernel kind")
     ap.add_argument("--runs", type=int, default=1, help="--profile-once: runs of the batch")
     ap.add_argument("--group", type=int, default=0, help="--profile-once: lanes per work item (0 = default)")
     ap.add_argument("--rounds", type=int, default=0,

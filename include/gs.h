@@ -89,6 +89,17 @@ gs_status gs_graph_load(const gs_graph_desc *desc, gs_graph **out);
 void gs_graph_free(gs_graph *g);
 /* Distinct (src, rel, dst) triples after canonicalisation. */
 uint64_t gs_graph_num_edges(const gs_graph *g);
+/* The canonical graph as loaded on the device, for checks: plane 0 = out,
+ * 1 = in (rows of rel << 24 | neighbour, ascending), 2 = out, 3 = in
+ * (distinct neighbours over every relation, ascending); off[V+1] and adj[off[V]]
+ * of that plane (host arrays; adj may be NULL to ask for the size, which *n
+ * receives).  sig (may be NULL) receives the degree signatures, one byte per
+ * (signature plane, vertex) = the distinct neighbours in that direction over
+ * that relation saturated at 15, planes dir * num_rels + rel, then
+ * 2 * num_rels + dir over every relation: (2 * num_rels + 2) * V bytes.
+ * Errors: GS_ERR_INVALID (plane > 3, null graph), GS_ERR_CUDA. */
+gs_status gs_graph_export(const gs_graph *g, uint32_t plane, uint64_t *off, uint32_t *adj, uint64_t *n,
+                          uint8_t *sig);
 
 /*
  * Domain-graph exploration (Ch. 5, "Domain-specific knowledge graph

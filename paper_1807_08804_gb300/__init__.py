@@ -139,6 +139,7 @@ EXTRA_SIGNATURES = {
                                ctypes.POINTER(Tuning)]),
     "gs_tune_set": (ctypes.c_int, [P, U32, U32]),
     "gs_batch_set_wait": (ctypes.c_int, [P, U32, U32]),
+    "gs_graph_export": (ctypes.c_int, [P, U32, P, P, ctypes.POINTER(U64), P]),
     "gs_match_batch_shared": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts),
                                              ctypes.POINTER(ResultDesc), ctypes.POINTER(P)]),
     "gs_rows_base": (P, [P]),
@@ -408,10 +409,27 @@ class DeviceGraph:
         _check(lib().gs_graph_load(ctypes.byref(d), ctypes.byref(self._h)))
         del keep
         self.num_vertices = int(num_vertices)
+        self.num_rels = int(num_rels)
 
     @property
     def num_edges(self) -> int:
         return int(lib().gs_graph_num_edges(self._h))
+
+    def export(self, plane: int, signatures: bool = False):
+        """The canonical CSR plane on the device (0 out, 1 in, 2 out and 3 in
+        over distinct neighbours) as (off, adj), and with signatures the
+        per-(plane, vertex) degree signatures [2R + 2, V]."""
+        off = np.zeros(self.num_vertices + 1, np.uint64)
+        n = U64()
+        _check(lib().gs_graph_export(self._h, plane, _ptr(off), None, ctypes.byref(n), None))
+        adj = np.zeros(max(n.value, 1), np.uint32)
+        sig = None
+        if signatures:
+            R = int(self.num_rels)
+            sig = np.zeros((2 * R + 2, self.num_vertices), np.uint8)
+        _check(lib().gs_graph_export(self._h, plane, _ptr(off), _ptr(adj), ctypes.byref(n),
+                                     _ptr(sig) if sig is not None else None))
+        return (off, adj[: n.value], sig) if signatures else (off, adj[: n.value])
 
     def io_bytes(self) -> tuple[int, int]:
         h, d = U64(), U64()

@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "gs_engine.cuh"
@@ -258,6 +259,7 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
   A(W.row_cnt, W.row_cap);
   A(W.row_scan, W.row_cap + 1);
   A(W.src, W.nq);
+  A(W.lsz, W.nq);
   A(W.out, s.out_words); W.out_words = s.out_words;
   A(W.out_q, s.out_rows);
   A(W.out_final, s.out_words);
@@ -712,13 +714,28 @@ static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match
   b->hstatus.assign(n, GS_OK);
   b->has_proj = b->has_rev = false;
   b->max_k = 1;
-  for (uint32_t i = 0; i < n; ++i) {
-    gs_status st = pack_query(b->g->d, &qs[i], opts, &b->hq[i]);
-    b->hstatus[i] = st;
-    if (st != GS_OK) {
-      memset(&b->hq[i], 0, sizeof(DQuery));
-      b->hq[i].status = QS_INVALID;
+  // queries pack independently: large batches split over host threads
+  auto pack_range = [&](uint32_t i0, uint32_t i1) {
+    for (uint32_t i = i0; i < i1; ++i) {
+      gs_status st = pack_query(b->g->d, &qs[i], opts, &b->hq[i]);
+      b->hstatus[i] = st;
+      if (st != GS_OK) {
+        memset(&b->hq[i], 0, sizeof(DQuery));
+        b->hq[i].status = QS_INVALID;
+      }
     }
+  };
+  const uint32_t hw = std::max(1u, std::min(8u, std::thread::hardware_concurrency()));
+  const uint32_t nt = n >= 2048 ? hw : 1;
+  if (nt > 1) {
+    std::vector<std::thread> th;
+    for (uint32_t t = 0; t < nt; ++t)
+      th.emplace_back(pack_range, (uint32_t)((uint64_t)n * t / nt), (uint32_t)((uint64_t)n * (t + 1) / nt));
+    for (auto &x : th) x.join();
+  } else {
+    pack_range(0, n);
+  }
+  for (uint32_t i = 0; i < n; ++i) {
     b->has_proj = b->has_proj || b->hq[i].proj != 0;
     b->has_rev = b->has_rev || (b->hq[i].refine_flags & kRefineRev);
     b->max_k = std::max<uint32_t>(b->max_k, b->hq[i].k);

@@ -154,6 +154,16 @@ struct SrcRows {
   uint64_t row_base, rows, word_base;
 };
 
+// What one join level asks of the pools for one query, gathered by a
+// grid-wide pass so that the one-block allocator reads it coalesced: rows
+// and words of the next level (v[0], v[1]) or of the final output (v[2],
+// v[3]); flags 1 = final output, 2 = next level, 4 = sent away by the
+// allocator's first pass.
+struct LevelSize {
+  uint64_t v[4];
+  uint32_t flags, pad;
+};
+
 // One wave of a batch, as listed in the batch's wave table.
 struct WaveDesc {
   uint32_t q0, nq;        // batch query range
@@ -230,6 +240,7 @@ struct Wave {
   uint32_t *row_cnt; uint64_t row_cap;
   uint64_t *row_scan;               // [row_cap + 1]
   SrcRows *src;                     // [nq]
+  LevelSize *lsz;                   // [nq]
   uint32_t *out; uint64_t out_words;  // final rows, join-order columns
   uint32_t *out_q;                  // slot query of each output row
   uint64_t out_rows_cap;

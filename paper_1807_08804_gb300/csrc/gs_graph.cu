@@ -567,4 +567,22 @@ extern "C" void gs_graph_free(gs_graph *g) {
 
 extern "C" uint64_t gs_graph_num_edges(const gs_graph *g) { return g ? g->d.E : 0; }
 
+extern "C" gs_status gs_graph_export(const gs_graph *g, uint32_t plane, uint64_t *off, uint32_t *adj, uint64_t *n,
+                                     uint8_t *sig) {
+  if (!g || plane > 3 || !off || !n) return fail(GS_ERR_INVALID, "gs_graph_export: bad argument");
+  GS_CUDA(cudaSetDevice(g->device));
+  const uint64_t V = g->d.V;
+  GS_CUDA(cudaMemcpy(off, g->d.off[plane], sizeof(uint64_t) * (V + 1), cudaMemcpyDeviceToHost));
+  *n = off[V];
+  if (adj && off[V]) GS_CUDA(cudaMemcpy(adj, g->d.adj[plane], sizeof(uint32_t) * off[V], cudaMemcpyDeviceToHost));
+  if (sig) {
+    const uint64_t P = 2ull * g->d.R + 2;
+    std::vector<uint32_t> words(P * g->d.sig_words);
+    GS_CUDA(cudaMemcpy(words.data(), g->d.sig, sizeof(uint32_t) * words.size(), cudaMemcpyDeviceToHost));
+    for (uint64_t p = 0; p < P; ++p)
+      for (uint64_t v = 0; v < V; ++v) sig[p * V + v] = (words[p * g->d.sig_words + (v >> 3)] >> ((v & 7) * 4)) & 15u;
+  }
+  return GS_OK;
+}
+
 extern "C" const char *gs_last_error(void) { return gs::t_last_error.c_str(); }

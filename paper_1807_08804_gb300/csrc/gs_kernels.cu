@@ -749,15 +749,17 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
       const bool built = xinc_role(xi) == 1;
       const uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
+      uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, lo + r, hi);
       for (uint64_t b = lo; b < hi && !found; b += G) {
         const uint64_t j = b + r;
-        const uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, j, hi);
+        const uint32_t en = run_entry<G>(tile, Gr, dir, fast, base, xs, j + G, hi);  // the next pass's entry, early
         bool ok = false;
         if (j < hi) {
           const uint32_t x = e & kNbrMask;
           ok = built ? bit_test(ws, x) : cand_ok(Gr, Q, w, x);
         }
         found = tile.any(ok);
+        e = en;
       }
       bytes += 16 + 4 * (hi - lo);
       if (!found) keep = false;
@@ -773,9 +775,10 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
       const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
       uint32_t *ws = slot_of(W, Q.qv_base + w);
       bool found = false;
+      uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, lo + r, hi);
       for (uint64_t b = lo; b < hi; b += G) {
         const uint64_t j = b + r;
-        const uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, j, hi);
+        const uint32_t en = run_entry<G>(tile, Gr, dir, fast, base, xs, j + G, hi);  // the next pass's entry, early
         bool ok = false;
         if (j < hi) {
           const uint32_t x = e & kNbrMask;
@@ -783,6 +786,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
           if (ok) bit_set(W, ws, x);
         }
         found = found || tile.any(ok);
+        e = en;
       }
       bytes += 16 + 4 * (hi - lo);
       if (!found) keep = false;
@@ -1097,22 +1101,34 @@ __device__ __forceinline__ void level_sizes(const Wave &W, uint32_t qi, uint32_t
   }
 }
 
-__global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
-  __shared__ uint64_t sm[4][32];
-  __shared__ uint64_t carry[4];
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lvl > 0) {
-    // after a count pass: rows produced per query (from the scan of the
-    // per-row counts), and the current level kept aside as the source of
-    // the write pass
-    for (uint32_t qi = threadIdx.x; qi < W.nq; qi += blockDim.x) {
+// Every query's sizes for level lvl, one thread per query; after a count
+// pass also the rows produced per query (from the scan of the per-row
+// counts), and the current level kept aside as the source of the write pass.
+__global__ void k_level_sizes(Wave W, uint32_t lvl) {
+  for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
+    if (lvl > 0) {
       QState &S = W.qs[qi];
       S.nxt_rows = S.cur_rows ? W.row_scan[S.cur_row_base + S.cur_rows] - W.row_scan[S.cur_row_base] : 0;
       W.src[qi] = SrcRows{S.cur_row_base, S.cur_rows, S.cur_word_base};
     }
-    if (threadIdx.x == 0) W.ctrl->len[4] = W.ctrl->len[3];
-    __syncthreads();
+    LevelSize z;
+    bool to_out, mid;
+    level_sizes(W, (uint32_t)qi, lvl, true, z.v, to_out, mid);
+    z.flags = (to_out ? 1u : 0u) | (mid ? 2u : 0u);
+    z.pad = 0;
+    W.lsz[qi] = z;
   }
+  if (gtid() == 0 && lvl > 0) W.ctrl->len[4] = W.ctrl->len[3];
+}
+
+// The row allocator of a join level (one block): an exclusive scan of the
+// sizes over the queries places every query's rows; a first pass sends away
+// (QS_OVERFLOW) each query that would pass a pool's end, the second assigns
+// the places of the others.
+__global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
+  __shared__ uint64_t sm[4][32];
+  __shared__ uint64_t carry[4];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int pass = 0; pass < 2; ++pass) {
     if (threadIdx.x == 0) {
       carry[0] = 0; carry[1] = 0;
@@ -1121,9 +1137,15 @@ __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
     __syncthreads();
     for (uint32_t base = 0; base < W.nq; base += blockDim.x) {
       const uint32_t qi = base + threadIdx.x;
-      uint64_t v[4], ex[4];
-      bool to_out, mid;
-      level_sizes(W, qi, lvl, pass == 0, v, to_out, mid);
+      uint64_t v[4] = {0, 0, 0, 0}, ex[4];
+      uint32_t flags = 0;
+      if (qi < W.nq) {
+        const LevelSize &z = W.lsz[qi];
+        flags = z.flags;
+        if (!(flags & 4u))
+          for (int a = 0; a < 4; ++a) v[a] = z.v[a];
+      }
+      const bool to_out = flags & 1u, mid = flags & 2u;
       for (int a = 0; a < 4; ++a) {
         uint64_t x = v[a];
         for (int o = 1; o < 32; o <<= 1) {
@@ -1146,20 +1168,23 @@ __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
       uint64_t pos[4];
       for (int a = 0; a < 4; ++a) pos[a] = carry[a] + ex[a] + (warp ? sm[a][warp - 1] : 0);
       if (qi < W.nq) {
-        DQuery &Q = W.dq[qi];
-        QState &S = W.qs[qi];
         if (pass == 0) {
-          if (mid && (pos[0] + v[0] > W.row_cap || pos[1] + v[1] > W.lvl_words)) mark(Q, QS_OVERFLOW);
-          if (to_out && (pos[2] + v[2] > W.out_rows_cap || pos[3] + v[3] > W.out_words)) mark(Q, QS_OVERFLOW);
+          const bool over = (mid && (pos[0] + v[0] > W.row_cap || pos[1] + v[1] > W.lvl_words)) ||
+                            (to_out && (pos[2] + v[2] > W.out_rows_cap || pos[3] + v[3] > W.out_words));
+          if (over) {
+            mark(W.dq[qi], QS_OVERFLOW);
+            W.lsz[qi].flags = flags | 4u;
+          }
         } else {
+          QState &S = W.qs[qi];
           S.cur_row_base = pos[0];
           S.cur_word_base = pos[1];
           S.cur_rows = v[0];
-          if (mid) {
+          if (mid && !(flags & 4u)) {
             S.inter_words += v[1];
             S.peak_words = max(S.peak_words, v[1]);
           }
-          if (to_out) {
+          if (to_out && !(flags & 4u)) {
             S.out_row_base = pos[2];
             S.out_word_base = pos[3];
             S.out_rows = v[2];
@@ -1177,6 +1202,7 @@ __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
       atomicMax((unsigned long long *)&W.ctrl->hw[HW_OUT_ROWS], (unsigned long long)carry[2]);
       atomicMax((unsigned long long *)&W.ctrl->hw[HW_OUT_WORDS], (unsigned long long)carry[3]);
     }
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
     W.ctrl->len[3] = carry[0];
@@ -1672,11 +1698,15 @@ __global__ void __launch_bounds__(256) k_sort_keys(Wave W, uint32_t *perm, SortK
   __shared__ uint32_t stage[256 / 32][32 * kMaxK];
   const uint64_t n = W.ctrl->len[6];
   const uint32_t b = W.G.idbits, lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint64_t acc = 0;
   for (uint64_t base = gtid() - lane; base < n; base += gthreads()) {
     const uint64_t i = base + lane;
     uint32_t qi = 0xFFFFFFFFu;
     uint64_t key = 0;
-    if (i < n) qi = seg_of_large(W.qs, W.nq, i, false);
+    if (i < n) {
+      qi = seg_of_large(W.qs, W.nq, i, false);
+      acc += 4ull * W.dq[qi].k + 20;  // the row read, its key and index written
+    }
     const uint32_t q0 = __shfl_sync(kFull, qi, 0);
     if (__all_sync(kFull, i >= n || qi == q0)) {  // warp-uniform
       const DQuery &Q = W.dq[q0];
@@ -1721,6 +1751,7 @@ __global__ void __launch_bounds__(256) k_sort_keys(Wave W, uint32_t *perm, SortK
       atomicMax((unsigned long long *)&W.sel[qi].hi, (unsigned long long)key);
     }
   }
+  flush_bytes(W, KK_SORT_LARGE, acc);
 }
 
 // Top-cap selection (radix select on the keys, most significant digit
@@ -1773,11 +1804,13 @@ __global__ void __launch_bounds__(256) k_sel_hist(Wave W, const SortKey *keys) {
   h[threadIdx.x] = 0;
   __syncthreads();
   const uint32_t q0 = b0 < n ? seg_of_large(W.qs, W.nq, b0, false) : 0;
+  uint64_t acc = 0;
   for (uint64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
     const uint32_t qi = seg_of_large(W.qs, W.nq, i, false);
     const SelState &s = W.sel[qi];
     if (s.state != 1) continue;
     const uint64_t key = keys[i].hi;
+    acc += 8;
     if (!sel_in_play(s, key)) continue;
     const uint32_t d = (uint32_t)(key >> s.shift) & ((1u << s.width) - 1);
     if (qi == q0) atomicAdd(&h[d], 1u);
@@ -1786,6 +1819,7 @@ __global__ void __launch_bounds__(256) k_sel_hist(Wave W, const SortKey *keys) {
   __syncthreads();
   if (b0 < n && W.sel[q0].state == 1 && h[threadIdx.x])
     atomicAdd(&W.shist[(uint64_t)q0 * 256 + threadIdx.x], h[threadIdx.x]);
+  flush_bytes(W, KK_SORT_LARGE, acc);
 }
 
 // Choose the bucket holding the need-th key; one warp per query.
@@ -1853,6 +1887,7 @@ __global__ void k_sel_pick(Wave W, int last) {
 __global__ void k_sel_compact(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout) {
   const uint64_t n = W.ctrl->len[6];
   const uint32_t lane = threadIdx.x & 31;
+  uint64_t acc = 0;
   for (uint64_t base = gtid() - lane; base < n; base += gthreads()) {
     const uint64_t i = base + lane;
     uint32_t qi = 0xFFFFFFFFu;
@@ -1863,6 +1898,7 @@ __global__ void k_sel_compact(Wave W, const uint32_t *pin, const SortKey *kin, u
       key = kin[i];
       cut = W.sel[qi].state == 2;
       keep = !cut || key.hi <= W.sel[qi].thresh;
+      acc += 16 + (keep ? 24 : 0);  // key read; a kept row's index read, key and index written
       if (!cut) {
         pout[i] = pin[i];
         kout[i] = key;
@@ -1879,6 +1915,7 @@ __global__ void k_sel_compact(Wave W, const uint32_t *pin, const SortKey *kin, u
       kout[at] = key;
     }
   }
+  flush_bytes(W, KK_SORT_LARGE, acc);
 }
 
 // Rows entering the sort and the tile layout after the cut.
@@ -1928,12 +1965,14 @@ __global__ void __launch_bounds__(256) k_tile_sort(Wave W, const uint32_t *pin, 
   __shared__ uint32_t row[kTileRows];
   __shared__ uint32_t idx[kTileRows];
   const uint64_t ntiles = W.ctrl->len[7];
+  uint64_t acc = 0;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint32_t qi = seg_of_large(W.qs, W.nq, t, true);
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
     const uint64_t first = (t - S.lrg_tile_base) * kTileRows, at = S.lrg_row_base + first;
     const uint32_t n = (uint32_t)min((uint64_t)kTileRows, S.sort_rows - first);
+    if (threadIdx.x == 0) acc += 40ull * n;  // keys and indices read and written
     uint32_t np2 = 1;
     while (np2 < n) np2 <<= 1;
     for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
@@ -1969,6 +2008,7 @@ __global__ void __launch_bounds__(256) k_tile_sort(Wave W, const uint32_t *pin, 
     }
     __syncthreads();
   }
+  flush_bytes(W, KK_SORT_LARGE, acc);
 }
 
 // Where output tile t of a merge pass with runs of `run` rows sits: its
@@ -2040,10 +2080,12 @@ __global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *pin
   __shared__ uint32_t si[kTileRows];
   __shared__ uint64_t s_end;
   const uint64_t ntiles = W.ctrl->len[7];
+  uint64_t acc = 0;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const MergeTile m = merge_tile(W, t, run);
     if (!m.active) continue;  // block-uniform
     const uint64_t o0 = m.first - m.a0, o1 = min(o0 + kTileRows, m.out);
+    if (threadIdx.x == 0) acc += 40 * (o1 - o0);  // keys and indices read and written
     if (m.nb == 0) {
       for (uint64_t i = m.base + m.first + threadIdx.x; i < m.base + m.a0 + o1; i += blockDim.x) {
         pout[i] = pin[i];
@@ -2091,6 +2133,7 @@ __global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *pin
     }
     __syncthreads();
   }
+  flush_bytes(W, KK_SORT_LARGE, acc);
 }
 
 // Merge passes a query of n large rows takes: its runs double from
@@ -2106,16 +2149,19 @@ __device__ __forceinline__ uint32_t merge_passes(uint64_t n) {
 // the first cap rows of each query, from the buffer its last pass wrote.
 __global__ void k_gather(Wave W, const uint32_t *perm0, const uint32_t *perm1) {
   const uint64_t n = W.ctrl->len[6];
+  uint64_t acc = 0;
   for (uint64_t i = gtid(); i < n; i += gthreads()) {
     const uint32_t qi = seg_of_large(W.qs, W.nq, i, false);
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
     if (Q.proj || i - S.lrg_row_base >= Q.cap) continue;  // projected: k_proj_write; past the rows returned
+    acc += 4 + 8ull * Q.k;  // index, the row read and written
     const uint32_t row = ((merge_passes(S.sort_rows) & 1) ? perm1 : perm0)[i];
     const uint32_t *src = W.out + S.out_word_base + (uint64_t)(row - S.out_row_base) * Q.k;
     uint32_t *dst = W.out_final + S.fin_word_base + (uint64_t)(i - S.lrg_row_base) * Q.k;
     for (uint32_t u = 0; u < Q.k; ++u) dst[u] = src[Q.pos[u]];
   }
+  flush_bytes(W, KK_GATHER, acc);
 }
 
 // Projected large outputs: after the merge sort, rows with equal projected
@@ -2320,6 +2366,7 @@ void launch_clear(const Wave &W, cudaStream_t s, int sms) {
 }
 void launch_join0(const Wave &W, cudaStream_t s, int sms) {
   k_join0_rows<<<blocks_for(W.nq, 256), 256, 0, s>>>(W);
+  k_level_sizes<<<blocks_for(W.nq, kThreads), kThreads, 0, s>>>(W, 0);
   k_level_alloc<<<1, 1024, 0, s>>>(W, 0);
   k_join0_write<<<persistent_grid(k_join0_write, sms), kThreads, 0, s>>>(W);
 }
@@ -2331,7 +2378,10 @@ void launch_join_count(const Wave &W, uint32_t lvl, int group, cudaStream_t s, i
     default: k_join_count<32><<<persistent_grid(k_join_count<32>, sms), kThreads, 0, s>>>(W, lvl); break;
   }
 }
-void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s) { k_level_alloc<<<1, 1024, 0, s>>>(W, lvl); }
+void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s) {
+  k_level_sizes<<<blocks_for(W.nq, kThreads), kThreads, 0, s>>>(W, lvl);
+  k_level_alloc<<<1, 1024, 0, s>>>(W, lvl);
+}
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms) {
   switch (group) {
     case 4: k_join_write<4><<<persistent_grid(k_join_write<4>, sms), kThreads, 0, s>>>(W, lvl); break;
