@@ -261,6 +261,13 @@ gs_status gs_batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_
                           gs_batch **out);
 /* Enqueue one run on the batch's stream (asynchronous). */
 gs_status gs_batch_run(gs_batch *b);
+/* Run nb prepared batches at once, each on its own stream (their streams
+ * must differ): every batch starts after the work queued so far on
+ * cuda_stream (NULL = the legacy default stream), their kernels overlap on
+ * the device, and cuda_stream waits for all of them.  Finish and fetch each
+ * batch as after gs_batch_run.  Errors: GS_ERR_INVALID (no batch, a null
+ * batch, two batches on one stream), GS_ERR_CUDA. */
+gs_status gs_batch_run_all(gs_batch **bs, uint32_t nb, void *cuda_stream);
 /* Wait for the last run, finish queries that overflowed the device budgets
  * (chunked join on the host-driven path), and make results fetchable. */
 gs_status gs_batch_finish(gs_batch *b);

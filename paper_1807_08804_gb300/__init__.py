@@ -139,6 +139,7 @@ EXTRA_SIGNATURES = {
                                ctypes.POINTER(Tuning)]),
     "gs_tune_set": (ctypes.c_int, [P, U32, U32]),
     "gs_batch_set_wait": (ctypes.c_int, [P, U32, U32]),
+    "gs_batch_run_all": (ctypes.c_int, [P, U32, P]),
     "gs_graph_export": (ctypes.c_int, [P, U32, P, P, ctypes.POINTER(U64), P]),
     "gs_match_batch_shared": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts),
                                              ctypes.POINTER(ResultDesc), ctypes.POINTER(P)]),
@@ -707,6 +708,13 @@ class CompressedGraph:
             self.free()
         except Exception:
             pass
+
+
+def run_all(batches, stream=None) -> None:
+    """Run several prepared batches at once, each on its own stream, after
+    the work queued on `stream`; `stream` then waits for all of them."""
+    hs = (P * len(batches))(*[b._h for b in batches])
+    _check(lib().gs_batch_run_all(hs, len(batches), stream))
 
 
 def debug_fail_alloc(after: int) -> None:

@@ -1148,6 +1148,45 @@ extern "C" gs_status gs_batch_run(gs_batch *b) {
   return st;
 }
 
+extern "C" gs_status gs_batch_run_all(gs_batch **bs, uint32_t nb, void *cuda_stream) {
+  if (!bs || nb == 0) return fail(GS_ERR_INVALID, "gs_batch_run_all: no batches");
+  for (uint32_t i = 0; i < nb; ++i) {
+    if (!bs[i]) return fail(GS_ERR_INVALID, "gs_batch_run_all: null batch");
+    for (uint32_t j = 0; j < i; ++j)
+      if (bs[j] == bs[i] || bs[j]->stream == bs[i]->stream)
+        return fail(GS_ERR_INVALID, "gs_batch_run_all: the batches need streams of their own");
+  }
+  const cudaStream_t parent = static_cast<cudaStream_t>(cuda_stream);
+  cudaEvent_t ev = nullptr;
+  GS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  // the batches start after the parent stream's earlier work
+  gs_status st = GS_OK;
+  if (cudaEventRecord(ev, parent) != cudaSuccess) st = fail(GS_ERR_CUDA, "gs_batch_run_all: fork");
+  for (uint32_t i = 0; i < nb && st == GS_OK; ++i)
+    if (cudaStreamWaitEvent(bs[i]->stream, ev, 0) != cudaSuccess) st = fail(GS_ERR_CUDA, "gs_batch_run_all: wait");
+  // first halves of every batch (pipeline graphs), then, once each one's
+  // large-output flags are on the host, the second halves: the batches'
+  // kernels overlap on the device, so one batch's low-occupancy steps run
+  // beside another's bulk work
+  bool multi = false;
+  for (uint32_t i = 0; i < nb; ++i) multi = multi || bs[i]->waves.size() != 1;
+  for (uint32_t i = 0; i < nb && st == GS_OK; ++i) {
+    bs[i]->ran = false;
+    bs[i]->finished = false;
+    st = multi ? run_waves(bs[i]) : run_begin(bs[i]);
+  }
+  for (uint32_t i = 0; i < nb && st == GS_OK && !multi; ++i)
+    if (bs[i]->sorting && cudaStreamSynchronize(bs[i]->stream) != cudaSuccess) st = fail(GS_ERR_CUDA, "sync");
+  for (uint32_t i = 0; i < nb && st == GS_OK && !multi; ++i) st = run_end(bs[i]);
+  for (uint32_t i = 0; i < nb && st == GS_OK; ++i) {
+    bs[i]->ran = true;
+    if (cudaEventRecord(ev, bs[i]->stream) != cudaSuccess || cudaStreamWaitEvent(parent, ev, 0) != cudaSuccess)
+      st = fail(GS_ERR_CUDA, "gs_batch_run_all: join");
+  }
+  cudaEventDestroy(ev);
+  return st;
+}
+
 extern "C" gs_status gs_batch_finish(gs_batch *b) {
   if (!b) return fail(GS_ERR_INVALID, "gs_batch_finish: null batch");
   return batch_finish(b);
