@@ -222,18 +222,21 @@ gs_status gs_match_batch(gs_graph *g, const gs_query *qs, uint32_t n, const gs_m
                          gs_result *outs);
 
 /* gs_match_batch without a copy of the rows on the host: the results' rows
- * lie in one block of page-locked host memory that the device wrote
- * directly, and each such result has shared = 1.  *block receives the
- * block (NULL when no row is shared); the rows stay valid until
- * gs_rows_release(block), which returns the block to a library pool for
- * later calls.  gs_rows_base/gs_rows_words give the block's address and size
- * in uint32 words.  Results of queries finished on the chunked path own
- * their rows as usual.  Errors as gs_match_batch. */
+ * lie in page-locked host buffers that the device wrote directly (one per
+ * sub-batch: a call of 4,096 queries or more, without a stream of the
+ * caller's, runs as four sub-batches at once on streams of their own), and
+ * each such result has shared = 1.  *block receives the buffers (NULL when
+ * no row is shared); the rows stay valid until gs_rows_release(block), which
+ * returns the buffers to a library pool for later calls.  gs_rows_count
+ * gives the number of buffers, gs_rows_base/gs_rows_words buffer i's address
+ * and size in uint32 words.  Results of queries finished on the chunked path
+ * own their rows as usual.  Errors as gs_match_batch. */
 typedef struct gs_rows gs_rows;
 gs_status gs_match_batch_shared(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
                                 gs_result *outs, gs_rows **block);
-const uint32_t *gs_rows_base(const gs_rows *block);
-uint64_t gs_rows_words(const gs_rows *block);
+uint32_t gs_rows_count(const gs_rows *block);
+const uint32_t *gs_rows_base(const gs_rows *block, uint32_t i);
+uint64_t gs_rows_words(const gs_rows *block, uint32_t i);
 void gs_rows_release(gs_rows *block);
 
 void gs_result_free(gs_result *r);
@@ -324,6 +327,15 @@ typedef struct {
 gs_status gs_stats_enable(gs_batch *b, int on);
 gs_status gs_stats_get(gs_batch *b, gs_kernel_stats *out);
 gs_status gs_stats_reset(gs_batch *b);
+/* Per kernel kind, the device time during which at least one launch of that
+ * kind was running, over the timed runs of the nb batches since their last
+ * resets: the union of the launches' intervals (CUDA events on the streams
+ * they ran on, taken from an anchor event recorded before each run's first
+ * launch; batches run together by gs_batch_run_all share one anchor), summed
+ * over runs.  Launches of one kind that overlap, as those of batches run
+ * together do, count once.  busy_ms: GS_NUM_KERNEL_KINDS doubles, written.
+ * Errors: GS_ERR_INVALID (null argument or batch). */
+gs_status gs_stats_busy(gs_batch *const *bs, uint32_t nb, double *busy_ms);
 
 /* ------------------------------------------------------------------------
  * Autotuning.  Times the captured pipeline on the given queries for each

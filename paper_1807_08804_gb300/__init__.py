@@ -118,6 +118,7 @@ SIGNATURES = {
     "gs_stats_enable": (ctypes.c_int, [P, ctypes.c_int]),
     "gs_stats_get": (ctypes.c_int, [P, ctypes.POINTER(KernelStats)]),
     "gs_stats_reset": (ctypes.c_int, [P]),
+    "gs_stats_busy": (ctypes.c_int, [ctypes.POINTER(P), U32, ctypes.POINTER(ctypes.c_double)]),
     "gs_inspect_candidates": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, P, P, U64, ctypes.POINTER(U64)]),
     "gs_inspect_edge_table": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, U32, P, P, P, U64, U64,
                                              ctypes.POINTER(U64), ctypes.POINTER(U64)]),
@@ -143,8 +144,9 @@ EXTRA_SIGNATURES = {
     "gs_graph_export": (ctypes.c_int, [P, U32, P, P, ctypes.POINTER(U64), P]),
     "gs_match_batch_shared": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts),
                                              ctypes.POINTER(ResultDesc), ctypes.POINTER(P)]),
-    "gs_rows_base": (P, [P]),
-    "gs_rows_words": (U64, [P]),
+    "gs_rows_count": (U32, [P]),
+    "gs_rows_base": (P, [P, U32]),
+    "gs_rows_words": (U64, [P, U32]),
     "gs_rows_release": (None, [P]),
     "gs_compress_host": (ctypes.c_int, [ctypes.POINTER(GraphDesc), U32, P, ctypes.POINTER(U32), ctypes.POINTER(U64),
                                         P, P, P, P, P, P, P]),
@@ -356,36 +358,50 @@ class _RowsBlock:
 
 
 def _take_shared(res, n: int, blk) -> list[MatchResult]:
-    """Results of gs_match_batch_shared: shared rows are views of the block
-    (no copy); rows a result owns are copied and freed."""
+    """Results of gs_match_batch_shared: shared rows are views of the
+    library's page-locked buffers (no copy); rows a result owns are copied
+    and freed."""
     if n == 0:
-        return []
-    a = np.frombuffer(res, dtype=_RES_DTYPE, count=n)
-    words = int(lib().gs_rows_words(blk)) if blk else 0
-    if words:
-        base = int(lib().gs_rows_base(blk) or 0)
-        buf = (ctypes.c_uint32 * words).from_address(base)
-        buf._owner = _RowsBlock(blk)  # released with the last view
-        big = np.frombuffer(buf, np.uint32)
-    else:
         if blk:
             lib().gs_rows_release(blk)
-        base, big = 0, np.empty(0, np.uint32)
+        return []
+    a = np.frombuffer(res, dtype=_RES_DTYPE, count=n)
+    nbuf = int(lib().gs_rows_count(blk)) if blk else 0
+    owner = _RowsBlock(blk) if blk else None  # the buffers go back with the last view
+    bases, arrays = [], []
+    for i in range(nbuf):
+        base, words = int(lib().gs_rows_base(blk, i) or 0), int(lib().gs_rows_words(blk, i))
+        if not words:
+            continue
+        buf = (ctypes.c_uint32 * words).from_address(base)
+        buf._owner = owner
+        bases.append(base)
+        arrays.append(np.frombuffer(buf, np.uint32))
+    order = np.argsort(np.array(bases, np.uint64)) if bases else np.zeros(0, np.int64)
+    sorted_bases = np.array(bases, np.uint64)[order] if bases else np.zeros(0, np.uint64)
     nr, ks = a["num_rows"].astype(np.int64), a["k"].astype(np.int64)
-    shared = a["shared"].astype(bool)
-    o0 = np.where(shared, (a["rows"].astype(np.int64) - base) // 4, 0)
+    shared = a["shared"].astype(bool) & (nr > 0)
+    ptr = a["rows"].astype(np.uint64)
+    which = np.searchsorted(sorted_bases, ptr, side="right").astype(np.int64) - 1
+    which = np.where(shared, which, 0)
+    buf_of = order[which] if len(order) else np.zeros(n, np.int64)
+    o0 = np.where(shared, (ptr.astype(np.int64) - sorted_bases[which].astype(np.int64)) // 4
+                  if len(order) else 0, 0)
     o1 = o0 + nr * ks
+    empty = np.empty(0, np.uint32)
     view = MatchResult._view
-    out = [view(c, f, big, x0, x1, r, k, t != 0, st)
-           for c, f, x0, x1, r, k, t, st in zip(a["count"].tolist(), a["fingerprint"].tolist(), o0.tolist(),
-                                                o1.tolist(), nr.tolist(), ks.tolist(), a["truncated"].tolist(),
-                                                a["status"].tolist())]
-    for i in np.flatnonzero(~shared & (nr > 0)).tolist():  # rows the result owns
+    out = [view(c, f, arrays[b] if sh else empty, x0, x1, r, k, t != 0, st)
+           for c, f, b, sh, x0, x1, r, k, t, st in zip(a["count"].tolist(), a["fingerprint"].tolist(),
+                                                       buf_of.tolist(), shared.tolist(), o0.tolist(), o1.tolist(),
+                                                       nr.tolist(), ks.tolist(), a["truncated"].tolist(),
+                                                       a["status"].tolist())]
+    for i in np.flatnonzero(~a["shared"].astype(bool) & (nr > 0)).tolist():  # rows the result owns
         rows = np.empty(int(nr[i] * ks[i]), np.uint32)
         ctypes.memmove(rows.ctypes.data, int(a["rows"][i]), 4 * rows.shape[0])
         out[i] = MatchResult(out[i].count, out[i].fingerprint, rows.reshape(int(nr[i]), int(ks[i])),
                              out[i].truncated, out[i].status)
     lib().gs_results_free(res, n)  # frees owned rows only
+    del owner
     return out
 
 
@@ -715,6 +731,17 @@ def run_all(batches, stream=None) -> None:
     the work queued on `stream`; `stream` then waits for all of them."""
     hs = (P * len(batches))(*[b._h for b in batches])
     _check(lib().gs_batch_run_all(hs, len(batches), stream))
+
+
+def stats_busy(batches) -> dict:
+    """Per kernel kind, the milliseconds during which at least one launch of
+    it was running, over the batches' timed runs since their stats resets
+    (overlapping launches of batches run together count once)."""
+    hs = (P * len(batches))(*[b._h for b in batches])
+    busy = (ctypes.c_double * NUM_KERNEL_KINDS)()
+    _check(lib().gs_stats_busy(hs, len(batches), busy))
+    names = batches[0].stats().keys() if batches else []
+    return {name: float(busy[i]) for i, name in enumerate(names)}
 
 
 def debug_fail_alloc(after: int) -> None:

@@ -2,6 +2,7 @@
 // captured pipeline graph, result transfer, and the C ABI entry points for
 // matching (Algorithm "FilteringAndJoining", thesis Ch. 3).
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -584,10 +585,13 @@ static gs_status capture_k(gs_batch *b, int K) {
 
 static void harvest_events(gs_batch *b, std::vector<gs_batch::Ev> &evs, bool destroy) {
   for (auto &ev : evs) {
-    float ms = 0;
+    float ms = 0, t0 = 0, t1 = 0;
     if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) {
       b->ms[ev.kind] += ms;
       b->launches[ev.kind] += 1;
+      if (b->anchor && cudaEventElapsedTime(&t0, b->anchor, ev.a) == cudaSuccess &&
+          cudaEventElapsedTime(&t1, b->anchor, ev.b) == cudaSuccess)
+        b->spans.push_back({b->run_id, ev.kind, t0, t1});
     }
     if (destroy) {
       cudaEventDestroy(ev.a);
@@ -620,7 +624,15 @@ gs_status refine_to_fixpoint(gs_batch *b) {
 // to pinned host words; the second half, once those words have arrived,
 // sorts the large outputs if there are any and moves the wave's results to
 // the batch store.
+static std::atomic<uint64_t> g_run_ids{0};
+
 static gs_status run_reset(gs_batch *b) {
+  if (b->stats_on && !b->shared_anchor) {
+    if (!b->own_anchor) GS_CUDA(cudaEventCreate(&b->own_anchor));
+    GS_CUDA(cudaEventRecord(b->own_anchor, b->stream));
+    b->anchor = b->own_anchor;
+    b->run_id = ++g_run_ids;
+  }
   GS_CUDA(cudaMemsetAsync(b->W.ctrl->hw, 0, sizeof(b->W.ctrl->hw), b->stream));
   GS_CUDA(cudaMemsetAsync(&b->W.ctrl->wave, 0, sizeof(uint32_t), b->stream));
   GS_CUDA(cudaMemsetAsync(&b->W.ctrl->store_top, 0, sizeof(uint64_t), b->stream));
@@ -653,6 +665,20 @@ static gs_status wave_begin(gs_batch *b, size_t w) {
   return GS_OK;
 }
 
+// Read a finished wave's launch events (graph events are re-recorded by the
+// next launch of their graph, so this comes before it).
+static gs_status harvest_wave(gs_batch *b, int K) {
+  GS_CUDA(cudaStreamSynchronize(b->stream));
+  if (b->use_graph) {
+    harvest_events(b, b->graph_evs[K], false);
+    harvest_events(b, b->sort_evs_direct, true);
+    harvest_events(b, b->epi_evs, false);
+  } else {
+    harvest_events(b, b->evs, true);
+  }
+  return GS_OK;
+}
+
 static gs_status wave_end(gs_batch *b, size_t w) {
   const int K = b->wave_k[w];
   if (b->sorting && b->flag[0] != 0) {
@@ -668,16 +694,7 @@ static gs_status wave_end(gs_batch *b, size_t w) {
     Pipe P{b, &b->evs, false, b->stream};
     enqueue_epilogue(P);
   }
-  if (b->stats_on) {
-    GS_CUDA(cudaStreamSynchronize(b->stream));
-    if (b->use_graph) {
-      harvest_events(b, b->graph_evs[K], false);
-      harvest_events(b, b->sort_evs_direct, true);
-      harvest_events(b, b->epi_evs, false);
-    } else {
-      harvest_events(b, b->evs, true);
-    }
-  }
+  if (b->stats_on && !b->defer_harvest) return harvest_wave(b, K);
   return GS_OK;
 }
 
@@ -705,6 +722,63 @@ gs_status run_end(gs_batch *b) {
   if (st != GS_OK) return st;
   GS_CUDA(cudaGetLastError());
   return GS_OK;
+}
+
+// Several batches at once, each on its own stream, after the work queued on
+// `parent`: first halves of every batch (pipeline graphs), then, once each
+// one's large-output flags are on the host, the second halves, so the
+// batches' kernels overlap on the device and one batch's steps with few work
+// items run beside another's bulk work; `parent` then waits for all of them.
+gs_status run_batches(gs_batch *const *bs, uint32_t nb, cudaStream_t parent) {
+  bool stats = false, multi = false;
+  for (uint32_t i = 0; i < nb; ++i) {
+    stats = stats || bs[i]->stats_on;
+    multi = multi || bs[i]->waves.size() != 1;
+  }
+  cudaEvent_t ev = nullptr;  // the fork; with timing on, the run's shared anchor
+  GS_CUDA(cudaEventCreateWithFlags(&ev, stats ? cudaEventDefault : cudaEventDisableTiming));
+  gs_status st = GS_OK;
+  if (cudaEventRecord(ev, parent) != cudaSuccess) st = fail(GS_ERR_CUDA, "run_batches: fork");
+  const uint64_t run = stats ? ++g_run_ids : 0;
+  for (uint32_t i = 0; i < nb && st == GS_OK; ++i) {
+    if (cudaStreamWaitEvent(bs[i]->stream, ev, 0) != cudaSuccess) st = fail(GS_ERR_CUDA, "run_batches: wait");
+    if (bs[i]->stats_on) {
+      bs[i]->anchor = ev;
+      bs[i]->shared_anchor = true;
+      bs[i]->run_id = run;
+      bs[i]->defer_harvest = !multi;
+    }
+  }
+  for (uint32_t i = 0; i < nb && st == GS_OK; ++i) {
+    bs[i]->ran = false;
+    bs[i]->finished = false;
+    st = multi ? run_waves(bs[i]) : run_begin(bs[i]);
+  }
+  for (uint32_t i = 0; i < nb && st == GS_OK && !multi; ++i)
+    if (bs[i]->sorting && cudaStreamSynchronize(bs[i]->stream) != cudaSuccess) st = fail(GS_ERR_CUDA, "run_batches: sync");
+  for (uint32_t i = 0; i < nb && st == GS_OK && !multi; ++i) st = run_end(bs[i]);
+  // with timing on, each batch's events are read once all of them are queued,
+  // so that the batches' launches still overlap
+  for (uint32_t i = 0; i < nb; ++i) {
+    gs_batch *b = bs[i];
+    if (b->stats_on && b->defer_harvest && st == GS_OK) st = harvest_wave(b, b->wave_k[0]);
+    if (b->anchor == ev) {
+      b->anchor = nullptr;
+      b->shared_anchor = false;
+      b->defer_harvest = false;
+    }
+  }
+  cudaEvent_t join = nullptr;
+  if (st == GS_OK && cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)
+    st = fail(GS_ERR_CUDA, "run_batches: join event");
+  for (uint32_t i = 0; i < nb && st == GS_OK; ++i) {
+    bs[i]->ran = true;
+    if (cudaEventRecord(join, bs[i]->stream) != cudaSuccess || cudaStreamWaitEvent(parent, join, 0) != cudaSuccess)
+      st = fail(GS_ERR_CUDA, "run_batches: join");
+  }
+  if (join) cudaEventDestroy(join);
+  cudaEventDestroy(ev);
+  return st;
 }
 
 static void pack_all(gs_batch *b, const gs_query *qs, uint32_t n, const gs_match_opts *opts) {
@@ -903,6 +977,8 @@ void batch_destroy(gs_batch *b) {
   harvest_events(b, b->epi_evs, true);
   harvest_events(b, b->sort_evs_direct, true);
   if (b->flag) cudaFreeHost(b->flag);
+  b->anchor = nullptr;
+  if (b->own_anchor) cudaEventDestroy(b->own_anchor);
   for (auto &kv : b->graph_evs) harvest_events(b, kv.second, true);
   harvest_events(b, b->evs, true);
   for (void *p : b->allocs) cudaFree(p);
@@ -997,6 +1073,8 @@ gs_status grow_pools(gs_batch *b) {
   return GS_OK;
 }
 
+void rows_from_pool(gs_batch *b, size_t words);
+
 gs_status batch_finish(gs_batch *b) {
   if (!b->ran) return fail(GS_ERR_INVALID, "gs_batch_finish: nothing was run");
   GS_CUDA(cudaStreamSynchronize(b->stream));
@@ -1022,6 +1100,7 @@ gs_status batch_finish(gs_batch *b) {
     GS_CUDA(cudaStreamSynchronize(b->stream));
     return fail(GS_ERR_TIMEOUT, "a prefix scan's look-back wait reached its bound");
   }
+  rows_from_pool(b, top);
   b->rows.resize(top);
   b->d2h_bytes += 36ull * n + 8 + 4ull * top;
   if (top) {
@@ -1156,35 +1235,7 @@ extern "C" gs_status gs_batch_run_all(gs_batch **bs, uint32_t nb, void *cuda_str
       if (bs[j] == bs[i] || bs[j]->stream == bs[i]->stream)
         return fail(GS_ERR_INVALID, "gs_batch_run_all: the batches need streams of their own");
   }
-  const cudaStream_t parent = static_cast<cudaStream_t>(cuda_stream);
-  cudaEvent_t ev = nullptr;
-  GS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  // the batches start after the parent stream's earlier work
-  gs_status st = GS_OK;
-  if (cudaEventRecord(ev, parent) != cudaSuccess) st = fail(GS_ERR_CUDA, "gs_batch_run_all: fork");
-  for (uint32_t i = 0; i < nb && st == GS_OK; ++i)
-    if (cudaStreamWaitEvent(bs[i]->stream, ev, 0) != cudaSuccess) st = fail(GS_ERR_CUDA, "gs_batch_run_all: wait");
-  // first halves of every batch (pipeline graphs), then, once each one's
-  // large-output flags are on the host, the second halves: the batches'
-  // kernels overlap on the device, so one batch's low-occupancy steps run
-  // beside another's bulk work
-  bool multi = false;
-  for (uint32_t i = 0; i < nb; ++i) multi = multi || bs[i]->waves.size() != 1;
-  for (uint32_t i = 0; i < nb && st == GS_OK; ++i) {
-    bs[i]->ran = false;
-    bs[i]->finished = false;
-    st = multi ? run_waves(bs[i]) : run_begin(bs[i]);
-  }
-  for (uint32_t i = 0; i < nb && st == GS_OK && !multi; ++i)
-    if (bs[i]->sorting && cudaStreamSynchronize(bs[i]->stream) != cudaSuccess) st = fail(GS_ERR_CUDA, "sync");
-  for (uint32_t i = 0; i < nb && st == GS_OK && !multi; ++i) st = run_end(bs[i]);
-  for (uint32_t i = 0; i < nb && st == GS_OK; ++i) {
-    bs[i]->ran = true;
-    if (cudaEventRecord(ev, bs[i]->stream) != cudaSuccess || cudaStreamWaitEvent(parent, ev, 0) != cudaSuccess)
-      st = fail(GS_ERR_CUDA, "gs_batch_run_all: join");
-  }
-  cudaEventDestroy(ev);
-  return st;
+  return run_batches(bs, nb, static_cast<cudaStream_t>(cuda_stream));
 }
 
 extern "C" gs_status gs_batch_finish(gs_batch *b) {
@@ -1257,18 +1308,24 @@ static MatchCache *cache_of(gs_graph *g) {
 // A batch of the cache re-armed with the queries, or a new one (the oldest
 // of four is dropped).
 static gs_status cached_batch(gs_graph *g, MatchCache *c, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
-                              gs_batch **out) {
+                              gs_batch **out, gs_batch *const *taken = nullptr, uint32_t ntaken = 0) {
+  auto is_taken = [&](const gs_batch *x) {
+    for (uint32_t i = 0; i < ntaken; ++i)
+      if (taken[i] == x) return true;
+    return false;
+  };
   for (gs_batch *x : c->batches)
-    if (batch_rearm(x, qs, n, opts)) {
+    if (!is_taken(x) && batch_rearm(x, qs, n, opts)) {
       *out = x;
       return GS_OK;
     }
   gs_batch *b = nullptr;
   gs_status st = batch_create(g, qs, n, opts, 0, &b);
   if (st != GS_OK) return st;
-  if (c->batches.size() >= 4) {
-    batch_destroy(c->batches.front());
-    c->batches.erase(c->batches.begin());
+  for (size_t i = 0; c->batches.size() >= 8 && i < c->batches.size();) {  // drop the oldest batch not in use
+    if (is_taken(c->batches[i])) { ++i; continue; }
+    batch_destroy(c->batches[i]);
+    c->batches.erase(c->batches.begin() + i);
   }
   c->batches.push_back(b);
   *out = b;
@@ -1343,35 +1400,80 @@ extern "C" void gs_result_free(gs_result *r) {
   r->num_rows = 0;
 }
 
-// Blocks of page-locked host memory handed out by gs_match_batch_shared:
-// a released block goes back to a small process-wide pool, from which a
-// batch takes its next result buffer, so a steady stream of calls
-// allocates no page-locked memory.
-struct gs_rows {
+// Page-locked result buffers handed out by gs_match_batch_shared, one per
+// batch the call ran: a released buffer goes back to a small process-wide
+// pool, from which a batch takes its next result buffer, so a steady stream
+// of calls allocates no page-locked memory.
+struct RowsBuf {
   uint32_t *p = nullptr;
   size_t cap = 0;      // words
   uint64_t words = 0;  // words written by the call
 };
+struct gs_rows {
+  std::vector<RowsBuf> bufs;
+};
 
-namespace {
+namespace gs {
 std::mutex g_rows_mu;
-std::vector<gs_rows *> g_rows_pool;
-constexpr size_t kRowsPoolMax = 4;
-}  // namespace
+std::vector<RowsBuf> g_rows_pool;
+constexpr size_t kRowsPoolMax = 16;
 
-extern "C" const uint32_t *gs_rows_base(const gs_rows *block) { return block ? block->p : nullptr; }
-extern "C" uint64_t gs_rows_words(const gs_rows *block) { return block ? block->words : 0; }
+// Hand a finished batch's result buffer over to `blk`; the batch takes a
+// pooled one when its next run has rows to copy out.
+void take_rows(gs_batch *b, gs_rows *blk) {
+  blk->bufs.push_back(RowsBuf{b->rows.p, b->rows.cap, b->rows.n});
+  b->rows.p = nullptr;
+  b->rows.cap = 0;
+  b->rows.n = 0;
+}
+
+// A batch without a result buffer takes the smallest pooled one that holds
+// `words`, else the largest (which then grows).
+void rows_from_pool(gs_batch *b, size_t words) {
+  if (b->rows.p || !words) return;
+  std::lock_guard<std::mutex> pl(g_rows_mu);
+  if (g_rows_pool.empty()) return;
+  size_t best = 0;
+  for (size_t i = 1; i < g_rows_pool.size(); ++i) {
+    const size_t c = g_rows_pool[i].cap, bc = g_rows_pool[best].cap;
+    if (bc >= words ? (c >= words && c < bc) : c > bc) best = i;
+  }
+  b->rows.p = g_rows_pool[best].p;
+  b->rows.cap = g_rows_pool[best].cap;
+  b->rows.n = 0;
+  g_rows_pool.erase(g_rows_pool.begin() + best);
+}
+}  // namespace gs
+
+extern "C" uint32_t gs_rows_count(const gs_rows *block) { return block ? (uint32_t)block->bufs.size() : 0; }
+extern "C" const uint32_t *gs_rows_base(const gs_rows *block, uint32_t i) {
+  return block && i < block->bufs.size() ? block->bufs[i].p : nullptr;
+}
+extern "C" uint64_t gs_rows_words(const gs_rows *block, uint32_t i) {
+  return block && i < block->bufs.size() ? block->bufs[i].words : 0;
+}
 
 extern "C" void gs_rows_release(gs_rows *block) {
   if (!block) return;
-  std::lock_guard<std::mutex> lk(g_rows_mu);
-  if (g_rows_pool.size() < kRowsPoolMax) {
-    g_rows_pool.push_back(block);
-    return;
+  {
+    std::lock_guard<std::mutex> lk(g_rows_mu);
+    for (RowsBuf &r : block->bufs) {
+      if (!r.p) continue;
+      if (g_rows_pool.size() < kRowsPoolMax) {
+        r.words = 0;
+        g_rows_pool.push_back(r);
+      } else {
+        cudaFreeHost(r.p);
+      }
+    }
   }
-  if (block->p) cudaFreeHost(block->p);
   delete block;
 }
+
+// Batches of at least this many queries are matched as kSplitParts
+// sub-batches running at once on their own streams (each sub-batch's steps
+// with few work items left run beside the others' bulk work).
+constexpr uint32_t kSplitMin = 4096, kSplitParts = 4;
 
 extern "C" gs_status gs_match_batch_shared(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts,
                                            gs_result *outs, gs_rows **block) {
@@ -1382,36 +1484,38 @@ extern "C" gs_status gs_match_batch_shared(gs_graph *g, const gs_query *qs, uint
   GS_CUDA(cudaSetDevice(g->device));
   MatchCache *c = cache_of(g);
   std::lock_guard<std::mutex> lk(c->mu);
-  gs_batch *b = nullptr;
-  gs_status st = cached_batch(g, c, qs, n, opts, &b);
+  const bool own_streams = !(opts && opts->cuda_stream);
+  const uint32_t parts = n >= kSplitMin && own_streams ? kSplitParts : 1;
+  std::vector<gs_batch *> bs(parts, nullptr);
+  std::vector<uint32_t> lo(parts + 1);
+  for (uint32_t p = 0; p <= parts; ++p) lo[p] = (uint32_t)((uint64_t)n * p / parts);
+  gs_status st = GS_OK;
+  for (uint32_t p = 0; p < parts && st == GS_OK; ++p)
+    st = cached_batch(g, c, qs + lo[p], lo[p + 1] - lo[p], opts, &bs[p], bs.data(), p);
   if (st != GS_OK) return st;
-  const uint64_t d0 = b->d2h_bytes;
-  c->h2d += b->last_upload_bytes;
-  st = run_waves(b);
-  b->ran = st == GS_OK;
-  if (st == GS_OK) st = batch_finish(b);
-  if (st != GS_OK) return st;
-  // the results point into the batch's result buffer, which the call hands
-  // over; the batch takes a pooled buffer for its next run
-  gs_rows *blk = new gs_rows();
-  blk->p = b->rows.p;
-  blk->cap = b->rows.cap;
-  blk->words = b->rows.n;
-  {
-    std::lock_guard<std::mutex> pl(g_rows_mu);
-    gs_rows *spare = nullptr;
-    if (!g_rows_pool.empty()) {
-      spare = g_rows_pool.back();
-      g_rows_pool.pop_back();
-    }
-    b->rows.p = spare ? spare->p : nullptr;
-    b->rows.cap = spare ? spare->cap : 0;
-    b->rows.n = 0;
-    delete spare;
+  uint64_t d0 = 0;
+  for (gs_batch *b : bs) {
+    d0 += b->d2h_bytes;
+    c->h2d += b->last_upload_bytes;
   }
-  st = batch_fetch_views(b, outs, blk->p);
-  for (uint32_t i = 0; i < n && st == GS_OK; ++i) b->d2h_bytes += 4ull * outs[i].num_rows * outs[i].k;
-  c->d2h += b->d2h_bytes - d0;
+  if (parts == 1) {
+    st = run_waves(bs[0]);
+    bs[0]->ran = st == GS_OK;
+  } else {
+    st = run_batches(bs.data(), parts, nullptr);
+  }
+  for (uint32_t p = 0; p < parts && st == GS_OK; ++p) st = batch_finish(bs[p]);
+  if (st != GS_OK) return st;
+  // the results point into the batches' result buffers, which the call hands over
+  gs_rows *blk = new gs_rows();
+  for (uint32_t p = 0; p < parts && st == GS_OK; ++p) {
+    take_rows(bs[p], blk);
+    st = batch_fetch_views(bs[p], outs + lo[p], blk->bufs.back().p);
+  }
+  uint64_t d1 = 0;
+  for (uint32_t i = 0; i < n && st == GS_OK; ++i) bs[0]->d2h_bytes += 4ull * outs[i].num_rows * outs[i].k;
+  for (gs_batch *b : bs) d1 += b->d2h_bytes;
+  c->d2h += d1 - d0;
   bool any = false;
   for (uint32_t i = 0; i < n && st == GS_OK; ++i) any = any || outs[i].shared;
   if (st != GS_OK || !any) {
@@ -1469,5 +1573,36 @@ extern "C" gs_status gs_stats_reset(gs_batch *b) {
   if (!b) return fail(GS_ERR_INVALID, "null batch");
   GS_CUDA(cudaMemcpy(b->bytes_base, b->W.ctrl->bytes, sizeof(b->bytes_base), cudaMemcpyDeviceToHost));
   for (int i = 0; i < KK_N; ++i) { b->ms[i] = 0; b->launches[i] = 0; }
+  b->spans.clear();
+  return GS_OK;
+}
+
+extern "C" gs_status gs_stats_busy(gs_batch *const *bs, uint32_t nb, double *busy_ms) {
+  if (!busy_ms || (nb && !bs)) return fail(GS_ERR_INVALID, "gs_stats_busy: null argument");
+  std::vector<gs_batch::Span> all;
+  for (uint32_t i = 0; i < nb; ++i) {
+    if (!bs[i]) return fail(GS_ERR_INVALID, "gs_stats_busy: null batch");
+    all.insert(all.end(), bs[i]->spans.begin(), bs[i]->spans.end());
+  }
+  for (int k = 0; k < GS_NUM_KERNEL_KINDS; ++k) busy_ms[k] = 0;
+  std::sort(all.begin(), all.end(), [](const gs_batch::Span &x, const gs_batch::Span &y) {
+    if (x.run != y.run) return x.run < y.run;
+    if (x.kind != y.kind) return x.kind < y.kind;
+    return x.t0 < y.t0;
+  });
+  // per run and kind, the length of the union of the launch intervals
+  for (size_t i = 0; i < all.size();) {
+    size_t j = i;
+    double lo = all[i].t0, hi = all[i].t1, sum = 0;
+    for (; j < all.size() && all[j].run == all[i].run && all[j].kind == all[i].kind; ++j) {
+      if (all[j].t0 > hi) {
+        sum += hi - lo;
+        lo = all[j].t0;
+      }
+      hi = std::max(hi, (double)all[j].t1);
+    }
+    busy_ms[all[i].kind] += sum + (hi - lo);
+    i = j;
+  }
   return GS_OK;
 }

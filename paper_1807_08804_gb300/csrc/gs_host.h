@@ -81,6 +81,16 @@ struct gs_batch {
   std::vector<Ev> evs;
   std::map<int, std::vector<Ev>> graph_evs;
   double ms[KK_N] = {0};
+  // each timed launch as an interval from the run's anchor event (recorded
+  // before the run's first launch; shared by batches run together), so that
+  // the time some launch of a kind was running can be taken over batches
+  // whose launches overlap
+  struct Span { uint64_t run; int kind; float t0, t1; };
+  std::vector<Span> spans;
+  cudaEvent_t anchor = nullptr, own_anchor = nullptr;
+  bool shared_anchor = false;  // the anchor belongs to a concurrent run
+  bool defer_harvest = false;  // events are read once every batch of the run is queued
+  uint64_t run_id = 0;
   uint64_t launches[KK_N] = {0};
   uint64_t bytes_base[KK_N] = {0};
   bool ran = false, finished = false;
@@ -135,6 +145,8 @@ gs_status run_waves(gs_batch *b);
 // run_end.
 gs_status run_begin(gs_batch *b);
 gs_status run_end(gs_batch *b);
+// Several single-stream batches at once on their own streams (see gs_batch_run_all).
+gs_status run_batches(gs_batch *const *bs, uint32_t nb, cudaStream_t parent);
 gs_status batch_finish(gs_batch *b);
 gs_status batch_fetch(gs_batch *b, gs_result *outs);
 gs_status batch_fetch_views(gs_batch *b, gs_result *outs, uint32_t *store);

@@ -324,3 +324,56 @@ def test_autotuner_choice_is_cached_and_results_unchanged(small, tmp_path):
         np.testing.assert_array_equal(x.rows, y.rows)
     b.close()
     gs.lib().gs_tune_set(dg._h, 0, 0)
+
+
+def test_large_call_as_concurrent_sub_batches(small):
+    """gs_match_batch with 4,096 queries or more runs as four sub-batches at
+    once on their own streams, their rows in four page-locked buffers: the
+    results equal one batch's, query by query, and the buffers come back to
+    the pool when the results go."""
+    import torch
+    g, qs, og, dg = small
+    many = I.make_walk_queries(g, 5000, 3, 7, p_bind=0.2, seed=31)
+    b = gs.Batch(dg, many, cap=1 << 12)
+    b.run()
+    b.finish()
+    want = b.fetch()
+    b.close()
+    for rep in range(3):  # pooled buffers are reused call after call
+        got = gs.match_batch(dg, many, cap=1 << 12)
+        assert len(got) == len(want)
+        for i, (x, y) in enumerate(zip(got, want)):
+            assert (x.count, x.fingerprint, x.status) == (y.count, y.fingerprint, y.status), i
+            np.testing.assert_array_equal(x.rows, y.rows)
+        del got
+    # prepared batches run together give the same results too
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    parts = [gs.Batch(dg, many[i * 1700:(i + 1) * 1700], cap=1 << 12, stream=streams[i].cuda_stream) for i in range(3)]
+    for p in parts:
+        p.stats_enable(True)
+    gs.run_all(parts, None)  # timed: each batch's events are read after all are queued
+    for p in parts:
+        p.finish()
+        p.stats_reset()
+    gs.run_all(parts, None)
+    res = []
+    for p in parts:
+        p.finish()
+        res += p.fetch()
+    for x, y in zip(res, want):
+        assert (x.count, x.fingerprint) == (y.count, y.fingerprint)
+        np.testing.assert_array_equal(x.rows, y.rows)
+    # the time some launch of a kind ran lies between the longest one batch
+    # spent in that kind (its launches run one after another on its stream)
+    # and the sum over the batches
+    busy = gs.stats_busy(parts)
+    per = [p.stats() for p in parts]
+    for kind in busy:
+        ms = [st[kind]["ms"] for st in per]
+        if sum(st[kind]["launches"] for st in per) == 0:
+            assert busy[kind] == 0.0
+            continue
+        assert max(ms) * 0.999 - 1e-3 <= busy[kind] <= sum(ms) * 1.001 + 1e-3, (kind, busy[kind], ms)
+    assert sum(busy.values()) > 0
+    for p in parts:
+        p.close()
