@@ -697,6 +697,88 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, co
 }
 
 // ============================================================ explore
+// One candidate v (item `it` of the step's list) explored by `tile`'s G lanes.
+template <int G>
+__device__ __forceinline__ void explore_item(const cg::thread_block_tile<G> &tile, const Wave &W, uint32_t step,
+                                             uint64_t it, uint64_t &acc) {
+  const DevGraph &Gr = W.G;
+  const uint32_t r = tile.thread_rank();
+  DQuery &Q = W.dq[W.tlist_q[it]];
+  if (Q.status != QS_OK) return;  // no kernel of this step changes a status
+  const uint32_t u = Q.visit[step];
+  const uint32_t v = W.tlist[it];
+  const uint32_t i0 = Q.inc_begin[u], i1 = Q.inc_begin[u + 1];
+  uint64_t bytes = 0;
+  // every edge to a typed vertex w needs a neighbour of w's type over its
+  // relation and direction: the neighbour-type masks of all edges, loaded
+  // together, reject most candidates before any row is read
+  bool keep = true;
+  for (uint32_t i = i0; i < i1 && !(Q.refine_flags & kRefineBase); ++i) {
+    const uint32_t xi = Q.xinc[i];
+    const uint32_t t = Q.vtype[xinc_w(xi)];
+    if (t == kAny) continue;
+    const uint32_t m = Gr.tmask[(uint64_t)sig_plane(xinc_dir(xi), xinc_rel(xi), Gr.R) * Gr.V + v];
+    keep = keep && ((m >> (t & 31u)) & 1u);
+  }
+  bytes += 4ull * (i1 - i0);
+  // edges to vertices other than the children initialised by this step
+  for (uint32_t i = i0; i < i1 && keep; ++i) {
+    const uint32_t xi = Q.xinc[i];
+    if (xinc_role(xi) >= 2) continue;  // children below; role 3: not checked (refinement baseline)
+    const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
+    const uint32_t w = xinc_w(xi);
+    uint64_t base, lo, hi;
+    uint32_t xs;
+    const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
+    const bool built = xinc_role(xi) == 1;
+    const uint32_t *ws = slot_of(W, Q.qv_base + w);
+    bool found = false;
+    uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, lo + r, hi);
+    for (uint64_t b = lo; b < hi && !found; b += G) {
+      const uint64_t j = b + r;
+      const uint32_t en = run_entry<G>(tile, Gr, dir, fast, base, xs, j + G, hi);  // the next pass's entry, early
+      bool ok = false;
+      if (j < hi) {
+        const uint32_t x = e & kNbrMask;
+        ok = built ? bit_test(ws, x) : cand_ok(Gr, Q, w, x);
+      }
+      found = tile.any(ok);
+      e = en;
+    }
+    bytes += 16 + 4 * (hi - lo);
+    if (!found) keep = false;
+  }
+  // tree edges to the children: test, expand and check existence in one scan
+  for (uint32_t i = i0; i < i1 && keep; ++i) {
+    const uint32_t xi = Q.xinc[i];
+    if (xinc_role(xi) != 2) continue;
+    const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
+    const uint32_t w = xinc_w(xi);
+    uint64_t base, lo, hi;
+    uint32_t xs;
+    const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
+    uint32_t *ws = slot_of(W, Q.qv_base + w);
+    bool found = false;
+    uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, lo + r, hi);
+    for (uint64_t b = lo; b < hi; b += G) {
+      const uint64_t j = b + r;
+      const uint32_t en = run_entry<G>(tile, Gr, dir, fast, base, xs, j + G, hi);  // the next pass's entry, early
+      bool ok = false;
+      if (j < hi) {
+        const uint32_t x = e & kNbrMask;
+        ok = cand_ok(Gr, Q, w, x);
+        if (ok) bit_set(W, ws, x);
+      }
+      found = found || tile.any(ok);
+      e = en;
+    }
+    bytes += 16 + 4 * (hi - lo);
+    if (!found) keep = false;
+  }
+  if (!keep && r == 0) bit_clear(slot_of(W, Q.qv_base + u), v);
+  if (r == 0) acc += bytes + 4;
+}
+
 // kernel_explore (Algorithm "Candidate nodes initialization"): one tile of G
 // lanes per candidate v of the visited vertex u.  v is dropped when some
 // query neighbour w of u has no candidate among v's data neighbours over the
@@ -709,90 +791,39 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, co
 // nothing; a candidate dropped by a later child edge may leave extra bits in
 // an earlier child's set, which keeps the sets supersets of the exact ones
 // (refinement removes them).
+// A warp takes 32/G consecutive items; a candidate with a row longer than
+// 8G entries in either direction (the thesis gives high-degree vertices a
+// whole block) is explored by the whole warp first, so that a hub's long
+// relation runs are not walked G entries at a time while the rest of the
+// grid waits for them.
 template <int G>
 __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) {
-  auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+  const auto warp = cg::tiled_partition<32>(cg::this_thread_block());
+  const auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const DevGraph &Gr = W.G;
-  const uint32_t r = tile.thread_rank();
-  const uint64_t ntile = gthreads() / G;
-  const uint64_t items = W.cscan[(uint64_t)W.nq * Gr.nchunks];
+  const uint64_t n = W.cscan[(uint64_t)W.nq * Gr.nchunks];
+  const uint64_t items = n < W.tlist_cap ? n : W.tlist_cap;  // entries past the list belong to overflowed queries
+  constexpr uint32_t T = 32 / G;
+  const uint32_t ti = (threadIdx.x & 31) / G;
+  const uint64_t nw = gthreads() / 32;
   uint64_t acc = 0;
-  for (uint64_t it = gtid() / G; it < items; it += ntile) {
-    if (it >= W.tlist_cap) break;  // entries past the list belong to overflowed queries
-    DQuery &Q = W.dq[W.tlist_q[it]];
-    if (Q.status != QS_OK) continue;
-    const uint32_t u = Q.visit[step];
-    const uint32_t v = W.tlist[it];
-    const uint32_t i0 = Q.inc_begin[u], i1 = Q.inc_begin[u + 1];
-    uint64_t bytes = 0;
-    // every edge to a typed vertex w needs a neighbour of w's type over its
-    // relation and direction: the neighbour-type masks of all edges, loaded
-    // together, reject most candidates before any row is read
-    bool keep = true;
-    for (uint32_t i = i0; i < i1 && !(Q.refine_flags & kRefineBase); ++i) {
-      const uint32_t xi = Q.xinc[i];
-      const uint32_t t = Q.vtype[xinc_w(xi)];
-      if (t == kAny) continue;
-      const uint32_t m = Gr.tmask[(uint64_t)sig_plane(xinc_dir(xi), xinc_rel(xi), Gr.R) * Gr.V + v];
-      keep = keep && ((m >> (t & 31u)) & 1u);
-    }
-    bytes += 4ull * (i1 - i0);
-    // edges to vertices other than the children initialised by this step
-    for (uint32_t i = i0; i < i1 && keep; ++i) {
-      const uint32_t xi = Q.xinc[i];
-      if (xinc_role(xi) >= 2) continue;  // children below; role 3: not checked (refinement baseline)
-      const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
-      const uint32_t w = xinc_w(xi);
-      uint64_t base, lo, hi;
-      uint32_t xs;
-      const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
-      const bool built = xinc_role(xi) == 1;
-      const uint32_t *ws = slot_of(W, Q.qv_base + w);
-      bool found = false;
-      uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, lo + r, hi);
-      for (uint64_t b = lo; b < hi && !found; b += G) {
-        const uint64_t j = b + r;
-        const uint32_t en = run_entry<G>(tile, Gr, dir, fast, base, xs, j + G, hi);  // the next pass's entry, early
-        bool ok = false;
-        if (j < hi) {
-          const uint32_t x = e & kNbrMask;
-          ok = built ? bit_test(ws, x) : cand_ok(Gr, Q, w, x);
-        }
-        found = tile.any(ok);
-        e = en;
+  for (uint64_t it0 = (gtid() / 32) * T; it0 < items; it0 += nw * T) {  // uniform in the warp
+    const uint64_t it = it0 + ti;
+    bool hub = false;
+    if (G < 32) {
+      if (it < items) {
+        const uint32_t v = W.tlist[it];
+        const uint64_t lim = 8 * G;
+        hub = Gr.off[0][v + 1] - Gr.off[0][v] > lim || Gr.off[1][v + 1] - Gr.off[1][v] > lim;
       }
-      bytes += 16 + 4 * (hi - lo);
-      if (!found) keep = false;
-    }
-    // tree edges to the children: test, expand and check existence in one scan
-    for (uint32_t i = i0; i < i1 && keep; ++i) {
-      const uint32_t xi = Q.xinc[i];
-      if (xinc_role(xi) != 2) continue;
-      const int dir = adj_plane(xinc_dir(xi), xinc_rel(xi));
-      const uint32_t w = xinc_w(xi);
-      uint64_t base, lo, hi;
-      uint32_t xs;
-      const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
-      uint32_t *ws = slot_of(W, Q.qv_base + w);
-      bool found = false;
-      uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, lo + r, hi);
-      for (uint64_t b = lo; b < hi; b += G) {
-        const uint64_t j = b + r;
-        const uint32_t en = run_entry<G>(tile, Gr, dir, fast, base, xs, j + G, hi);  // the next pass's entry, early
-        bool ok = false;
-        if (j < hi) {
-          const uint32_t x = e & kNbrMask;
-          ok = cand_ok(Gr, Q, w, x);
-          if (ok) bit_set(W, ws, x);
-        }
-        found = found || tile.any(ok);
-        e = en;
+      uint32_t hm = warp.ballot(hub && tile.thread_rank() == 0);
+      while (hm) {
+        const uint32_t src = __ffs(hm) - 1;
+        hm &= hm - 1;
+        explore_item<32>(warp, W, step, warp.shfl(it, src), acc);
       }
-      bytes += 16 + 4 * (hi - lo);
-      if (!found) keep = false;
     }
-    if (!keep && r == 0) bit_clear(slot_of(W, Q.qv_base + u), v);
-    if (r == 0) acc += bytes + 4;
+    if (it < items && !hub) explore_item<G>(tile, W, step, it, acc);
   }
   flush_bytes(W, KK_EXPLORE, acc);
 }
