@@ -8,8 +8,10 @@ candidate-edge tables, join, sort) over one batch of queries: by default the
 
   value   queries/s of the batched pipeline, inputs resident in HBM
           (CUDA events on the launching stream; L2 flushed between steps)
-  e2e     the same metric through gs_match_batch with host buffers
-          (query upload and result download inside the timed region)
+  e2e     the same metric through the C ABI (gs_match_batch_shared) with
+          host buffers: queries packed in host memory, counts, fingerprints
+          and rows back in host memory (upload and download inside the timed
+          region); also through the Python binding (gs.match_batch)
   one_at_a_time   queries/s when the same device pipeline runs each query
                   as its own wave (the baseline the batching is measured against),
                   on a sample of the queries when the workload is large
@@ -600,6 +602,7 @@ def main():
         run_compressed(args, world, rank, local)
         return
 
+    import numpy as np
     import torch
     import paper_1807_08804_gb300 as gs
     from paper_1807_08804_gb300 import inputs as I
@@ -715,22 +718,51 @@ def main():
     one_tot = max_over_ranks(sum(one_ms), world, dev)
     one_qps = len(one_qs) * world * args.one_steps / (one_tot / 1e3) if args.one_steps else None
 
-    # ---- end to end through the public API with host buffers
-    h0, d0 = dg.io_bytes()
-    gs.match_batch(dg, qs, cap=cap, mode=gmode, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, project=project,
-                   raw_chunks=True)  # warm the reusable pools
+    # ---- end to end through the C ABI with host buffers: gs_match_batch_shared
+    # on the queries packed once as gs_query structs over host arrays; the
+    # counts, fingerprints and sorted rows come back in host memory (rows in
+    # the library's page-locked buffers, released after each step)
+    import ctypes
+    pack = gs.QueryPack(qs)
+    ccb = gs.chunk_callback(chunk_cb, True)
+    copts = gs.match_opts(cap, gmode, 0, chunk_bytes, on_chunk=ccb, project=project)
+    cres = (gs.ResultDesc * n)()
+
+    def c_step():
+        blk = gs.P()
+        gs.check(gs.lib().gs_match_batch_shared(dg._h, pack.arr, n, ctypes.byref(copts), cres, ctypes.byref(blk)))
+        got = int(np.frombuffer(cres, gs.RES_DTYPE, count=n)["count"].sum())  # the result, read on the host
+        gs.lib().gs_results_free(cres, n)  # rows a result owns (none when all are shared)
+        if blk:
+            gs.lib().gs_rows_release(blk)
+        return got
+
+    c_step()  # warm the reusable pools
     h0, d0 = dg.io_bytes()
     barrier(world)
     torch.cuda.synchronize()
     t = time.perf_counter()
     e2e_steps = max(2, args.steps // 2)
     for _ in range(e2e_steps):
-        out = gs.match_batch(dg, qs, cap=cap, mode=gmode, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, raw_chunks=True,
-                             project=project)
+        got = c_step()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t, world, dev)
     h1, d1 = dg.io_bytes()
+    assert got == embeddings
+    # the same through the Python binding (Query objects in, MatchResult
+    # objects with row views out)
+    out = gs.match_batch(dg, qs, cap=cap, mode=gmode, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, project=project,
+                         raw_chunks=True)
+    del out
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        out = gs.match_batch(dg, qs, cap=cap, mode=gmode, chunk_bytes=chunk_bytes, on_chunk=chunk_cb, raw_chunks=True,
+                             project=project)
+    torch.cuda.synchronize()
+    py_s = max_over_ranks(time.perf_counter() - t, world, dev)
     assert sum(r.count for r in out) == embeddings
+    del out
 
     # ---- serving: continuous batching under Poisson arrivals (on the 4M
     # graph, the serving workload's own queries and rates)
@@ -777,7 +809,10 @@ def main():
                                "sample": "all" if len(one_qs) == n else f"the first {len(one_qs)} queries; sampled"}
                               if one_qps else None),
             "e2e": {"value": n * world * e2e_steps / e2e_s, "unit": "queries/s",
-                    "h2d_bytes_per_step": (h1 - h0) // e2e_steps, "d2h_bytes_per_step": (d1 - d0) // e2e_steps},
+                    "h2d_bytes_per_step": (h1 - h0) // e2e_steps, "d2h_bytes_per_step": (d1 - d0) // e2e_steps,
+                    "call": "gs_match_batch_shared, queries packed in host memory, results read on the host",
+                    "python_api": {"value": n * world * e2e_steps / py_s, "unit": "queries/s",
+                                   "call": "gs.match_batch: Query objects in, MatchResult objects out"}},
             "gpu_launches": launches,
             "serving": serving,
             "roofline": roof,

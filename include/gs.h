@@ -294,6 +294,16 @@ gs_status gs_batch_create_waves(gs_graph *g, const gs_query *qs, uint32_t n, con
  * GS_ROUNDS_NONE = no refinement round after exploration). */
 #define GS_ROUNDS_NONE 0xFFFFFFFFu
 gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_t refine_rounds);
+/* Sort of the outputs above the one-block limit (more than 2,048 rows) into
+ * the ascending lexicographic row order in which results are returned: by
+ * default a sample sort (buckets bounded by splitters drawn from the
+ * query's rows, each bucket sorted in shared memory), with the tile sort and
+ * merge passes for a query whose bucket overflows.  GS_SORT_MERGE_ONLY sorts
+ * every large output by the tile sort and merge passes (same results; for
+ * tests of that path).  Applies to the batch's later runs.  Errors:
+ * GS_ERR_INVALID (null batch, unknown flag). */
+#define GS_SORT_MERGE_ONLY 1u
+gs_status gs_batch_set_sort(gs_batch *b, uint32_t flags);
 /* Bound on the one device-side wait of the pipeline: the look-back of the
  * single-pass prefix scans that size every output (Section 3.3.4's two-step
  * output scheme: count, prefix sum, write).  A block waits there only on

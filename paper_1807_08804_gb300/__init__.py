@@ -29,6 +29,7 @@ GS_REFINE_OFF, GS_REFINE_REVERSED, GS_REFINE_BASELINE = 1, 2, 4
 GS_KHOP_OUT, GS_KHOP_IN = 1, 2
 GS_WAIT_WITHHOLD_FIRST_TILE = 1
 GS_ROUNDS_NONE = 0xFFFFFFFF
+GS_SORT_MERGE_ONLY = 1
 
 
 def GS_REFINE_LOW(d: int) -> int:
@@ -140,6 +141,7 @@ EXTRA_SIGNATURES = {
                                ctypes.POINTER(Tuning)]),
     "gs_tune_set": (ctypes.c_int, [P, U32, U32]),
     "gs_batch_set_wait": (ctypes.c_int, [P, U32, U32]),
+    "gs_batch_set_sort": (ctypes.c_int, [P, U32]),
     "gs_batch_run_all": (ctypes.c_int, [P, U32, P]),
     "gs_graph_export": (ctypes.c_int, [P, U32, P, P, ctypes.POINTER(U64), P]),
     "gs_match_batch_shared": (ctypes.c_int, [P, ctypes.POINTER(QueryDesc), U32, ctypes.POINTER(MatchOpts),
@@ -235,6 +237,12 @@ class _QueryPack:
         self.arr = ctypes.cast(d.ctypes.data, ctypes.POINTER(QueryDesc))
 
 
+# Lower-level names for callers of the C ABI through lib(): queries packed
+# once as gs_query structs over host arrays, match options, chunk callbacks,
+# the gs_result layout as a numpy dtype, and the status check.
+QueryPack = _QueryPack
+
+
 def project_mask(project) -> int:
     """Projection as the library's bit mask: None = whole embeddings, an int
     is taken as the mask, else an iterable of query vertices."""
@@ -256,6 +264,12 @@ def _opts(cap=1 << 20, mode=GS_ENUMERATE, max_refine_rounds=0, chunk_bytes=0, st
     o.project = project_mask(project)
     o.refine = refine
     return o
+
+
+def match_opts(*a, **kw) -> MatchOpts:
+    """gs_match_opts from cap, mode, max_refine_rounds, chunk_bytes, stream,
+    on_chunk (a wrapped callback), project and refine."""
+    return _opts(*a, **kw)
 
 
 def _chunk_callback(fn, raw=False):
@@ -321,6 +335,10 @@ def _take(r: ResultDesc) -> MatchResult:
 _RES_DTYPE = np.dtype({"names": ["count", "num_rows", "fingerprint", "k", "truncated", "rows", "status", "shared"],
                        "formats": ["<u8", "<u8", "<u8", "<u4", "<u4", "<u8", "<u4", "<u4"],
                        "offsets": [0, 8, 16, 24, 28, 32, 40, 44], "itemsize": 48})
+RES_DTYPE = _RES_DTYPE
+chunk_callback = _chunk_callback
+check = _check
+
 
 
 def _take_all(res, n: int) -> list[MatchResult]:
@@ -539,6 +557,11 @@ class Batch:
         nothing (tests of the timeout path)."""
         _check(lib().gs_batch_set_wait(self._h, max_polls,
                                        GS_WAIT_WITHHOLD_FIRST_TILE if withhold_first_tile else 0))
+
+    def set_sort(self, merge_only=False):
+        """Large outputs by the sample sort (default) or, with merge_only,
+        by the tile sort and merge passes only."""
+        _check(lib().gs_batch_set_sort(self._h, GS_SORT_MERGE_ONLY if merge_only else 0))
 
     def run(self):
         _check(lib().gs_batch_run(self._h))

@@ -269,13 +269,18 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
     A(W.skey[i], s.out_rows);
     A(W.sval[i], s.out_rows);
   }
-  A(W.msplit, s.out_rows / kTileRows + W.nq + 1);
-  A(W.ptcount, s.out_rows / kTileRows + W.nq + 1);
-  A(W.ptscan, s.out_rows / kTileRows + W.nq + 2);
+  A(W.bkt_id, s.out_rows);
+  // per tile of the large-output sort; two bucket slots per tile
+  A(W.msplit, 2 * (s.out_rows / kTileRows + W.nq + 1));
+  A(W.bspl_key, 2 * (s.out_rows / kTileRows + W.nq + 1));
+  A(W.bspl_key2, 2 * (s.out_rows / kTileRows + W.nq + 1));
+  A(W.bspl_row, 2 * (s.out_rows / kTileRows + W.nq + 1));
+  A(W.ptcount, 2 * (s.out_rows / kTileRows + W.nq + 1));
+  A(W.ptscan, 2 * (s.out_rows / kTileRows + W.nq + 1) + 1);
   A(W.sel, W.nq);
   A(W.shist, (uint64_t)W.nq * 256);
   uint64_t tmpw = scan_tmp_words(std::max<uint64_t>(
-      {(uint64_t)W.nqv * cps, (uint64_t)W.nqe, s.ec_items, W.row_cap, s.out_rows / kTileRows + W.nq + 1}));
+      {(uint64_t)W.nqv * cps, (uint64_t)W.nqe, s.ec_items, W.row_cap, 2 * (s.out_rows / kTileRows + W.nq + 1)}));
   A(b->scan_tmp, tmpw);
   b->scan_tmp_words = tmpw;
   A(b->type_count, G.T);
@@ -484,15 +489,17 @@ void enqueue_back(Pipe &P, int K, int stop) {
   P.end();
 }
 
-// Merge sort of the outputs above the one-block limit: tiles sorted in
-// shared memory, then ceil(log2(largest / tile)) merge passes (launched
-// directly: the host reads the largest output first).
+// Sort of the outputs above the one-block limit (launched directly: the
+// host reads the largest output first): a sample sort into buckets of about
+// one tile, each sorted in shared memory; a query with an overflowing bucket
+// takes the tile sort and ceil(log2(largest / tile)) merge passes instead
+// (those launches return at once when no query needs them).
 // Launches of enqueue_large_sort for the largest output and the number of
 // outputs cut at cap.
 uint64_t large_sort_launches(uint64_t max_rows, uint64_t over_cap, bool proj) {
   uint64_t passes = 0;
   for (uint64_t run = kTileRows; run < max_rows; run *= 2) ++passes;
-  return 3 + 2 * passes + (over_cap ? 3 + 2 * 3 : 0) + (proj ? 3 : 0);
+  return 3 + 5 + 2 * passes + (over_cap ? 3 + 2 * 3 : 0) + (proj ? 3 : 0);
 }
 
 void enqueue_large_sort(Pipe &P, uint64_t max_rows, uint64_t over_cap, bool proj) {
@@ -509,6 +516,9 @@ void enqueue_large_sort(Pipe &P, uint64_t max_rows, uint64_t over_cap, bool proj
     launch_select(W, perm[0], keys[0], perm[1], keys[1], P.cur, sms);
     in = 1;
   }
+  const int x = in ^ 1;  // the scatter's target: the other buffer
+  launch_bucket_sort(W, perm[in], keys[in], perm[x], keys[x], perm[0], keys[0], perm[1], keys[1], b->scan_tmp, P.cur,
+                     sms);
   launch_tile_sort(W, perm[in], keys[in], perm[0], keys[0], P.cur, sms);
   for (uint64_t run = kTileRows; run < max_rows; run *= 2) {
     launch_merge_pass(W, perm[cur], keys[cur], perm[cur ^ 1], keys[cur ^ 1], run, P.cur, sms);
@@ -1046,9 +1056,13 @@ gs_status grow_pools(gs_batch *b) {
     const uint64_t n = want(hw[HW_OUT_ROWS]);
     bool ok = regrow(b, &W.out_q, n) == GS_OK;
     for (int i = 0; i < 2 && ok; ++i) ok = regrow(b, &W.skey[i], n) == GS_OK && regrow(b, &W.sval[i], n) == GS_OK;
-    ok = ok && regrow(b, &W.msplit, n / kTileRows + W.nq + 1) == GS_OK;
-    ok = ok && regrow(b, &W.ptcount, n / kTileRows + W.nq + 1) == GS_OK;
-    ok = ok && regrow(b, &W.ptscan, n / kTileRows + W.nq + 2) == GS_OK;
+    ok = ok && regrow(b, &W.bkt_id, n) == GS_OK;
+    ok = ok && regrow(b, &W.msplit, 2 * (n / kTileRows + W.nq + 1)) == GS_OK;
+    ok = ok && regrow(b, &W.bspl_key, 2 * (n / kTileRows + W.nq + 1)) == GS_OK;
+    ok = ok && regrow(b, &W.bspl_key2, 2 * (n / kTileRows + W.nq + 1)) == GS_OK;
+    ok = ok && regrow(b, &W.bspl_row, 2 * (n / kTileRows + W.nq + 1)) == GS_OK;
+    ok = ok && regrow(b, &W.ptcount, 2 * (n / kTileRows + W.nq + 1)) == GS_OK;
+    ok = ok && regrow(b, &W.ptscan, 2 * (n / kTileRows + W.nq + 1) + 1) == GS_OK;
     if (ok) { W.out_rows_cap = n; changed = true; }
   }
   if (hw[HW_OUT_WORDS] > W.out_words && hw[HW_OUT_WORDS] <= kMaxEntries) {
@@ -1062,7 +1076,7 @@ gs_status grow_pools(gs_batch *b) {
   if (changed) {
     const uint64_t cps = W.G.nchunks;  // chunks per set: one candidate count per chunk
     uint64_t tmpw = scan_tmp_words(std::max<uint64_t>(
-        {(uint64_t)W.nqv * cps, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap, W.out_rows_cap / kTileRows + W.nq + 1}));
+        {(uint64_t)W.nqv * cps, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap, 2 * (W.out_rows_cap / kTileRows + W.nq + 1)}));
     if (regrow(b, &b->scan_tmp, tmpw) == GS_OK) {
       b->scan_tmp_words = tmpw;
       GS_CUDA(cudaMemsetAsync(b->scan_tmp, 0, sizeof(uint64_t) * tmpw, b->stream));
@@ -1277,6 +1291,13 @@ extern "C" gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_
     b->refine_rounds = 8;
     b->fixpoint = true;
   }
+  return GS_OK;
+}
+
+extern "C" gs_status gs_batch_set_sort(gs_batch *b, uint32_t flags) {
+  if (!b) return fail(GS_ERR_INVALID, "gs_batch_set_sort: null batch");
+  if (flags & ~GS_SORT_MERGE_ONLY) return fail(GS_ERR_INVALID, "gs_batch_set_sort: unknown flags");
+  b->W.merge_only = (flags & GS_SORT_MERGE_ONLY) ? 1u : 0u;
   return GS_OK;
 }
 

@@ -119,6 +119,7 @@ struct QState {
   uint64_t nfinal;                                   // rows returned (projected: distinct tuples, at most cap)
   uint64_t inter_words, peak_words;                  // partial-embedding words over the levels before the last
   uint32_t more;                                     // projected: more distinct tuples than cap
+  uint32_t bkt_fail;                                 // a bucket of the sample sort overflowed: merge path
 };
 
 // BatchOut::nrows top bit: a projected query had more distinct tuples than
@@ -196,6 +197,9 @@ struct Ctrl {
   uint64_t over_cap;                // large outputs with more rows than cap (selected before sorting)
   uint64_t fin_words;               // words of the rows returned by this wave
   uint64_t bytes[KK_N];             // algorithmic bytes per kernel kind
+  uint32_t bkt_fail;                // some query's sample-sort bucket overflowed (merge path runs)
+  uint32_t pad_;
+  uint64_t nbkt;                    // bucket slots of the sample sort (two per tile)
 };
 
 // Everything a kernel needs, passed by value.  Capacities are fixed when the
@@ -248,7 +252,12 @@ struct Wave {
   // sort
   SortKey *skey[2];                     // sort keys of the large-output merge sort
   uint32_t *sval[2];                    // row indices of the large-output merge sort
-  uint64_t *msplit;                     // merge-path split of each output tile
+  uint64_t *msplit;                     // merge-path split of each output tile (bucket sort: fill cursors)
+  uint32_t merge_only;                  // large outputs: skip the bucket sort, tile sort and merge passes only
+  uint32_t *bkt_id;                     // bucket sort: each large entry's bucket (count pass to scatter pass)
+  SortKey *bspl_key;                    // bucket sort: splitters of each query's buckets, one slot per tile
+  SortKey *bspl_key2;                   //   their second keys
+  uint32_t *bspl_row;                   //   and their row indices
   uint32_t *ptcount;                    // projected outputs: distinct tuples starting in each tile
   uint64_t *ptscan;                     //   and their scan [tiles + 1]
   SelState *sel;                        // [nq] top-cap selection
@@ -283,6 +292,9 @@ void launch_small_sort(const Wave &W, cudaStream_t s, int sms);
 void launch_sort_keys(const Wave &W, uint32_t *perm, SortKey *keys, cudaStream_t s, int sms);
 void launch_select(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                    cudaStream_t s, int sms);
+void launch_bucket_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *px, SortKey *kx,
+                        uint32_t *p0, SortKey *k0, uint32_t *p1, SortKey *k1, uint64_t *scan_tmp, cudaStream_t s,
+                        int sms);
 void launch_tile_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                       cudaStream_t s, int sms);
 void launch_merge_pass(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,

@@ -1551,12 +1551,18 @@ __device__ __forceinline__ uint64_t pack_key(uint32_t k, uint32_t b, Col col) {
   return key;
 }
 
+// Output columns the two sort-key words hold whole: rows with equal keys
+// agree on them.
+__device__ __forceinline__ uint32_t key_cols(const Wave &W) { return 2 * (64 / W.G.idbits); }
+
 // Row r of the output pool (query qi) compared on its output columns (the
-// projected vertices, or every vertex) in query-vertex order.
+// projected vertices, or every vertex) in query-vertex order.  Callers
+// compare rows only when their sort keys are equal, so the columns the keys
+// hold whole are skipped.
 __device__ __forceinline__ bool out_row_le(const Wave &W, const DQuery &Q, const QState &S, uint32_t a, uint32_t b) {
   const uint32_t *x = W.out + S.out_word_base + (uint64_t)(a - S.out_row_base) * Q.k;
   const uint32_t *y = W.out + S.out_word_base + (uint64_t)(b - S.out_row_base) * Q.k;
-  for (uint32_t i = 0; i < Q.kp; ++i) {
+  for (uint32_t i = key_cols(W); i < Q.kp; ++i) {
     const uint32_t c = Q.opos[i];
     const uint32_t xa = x[c], yb = y[c];
     if (xa != yb) return xa < yb;
@@ -1564,11 +1570,12 @@ __device__ __forceinline__ bool out_row_le(const Wave &W, const DQuery &Q, const
   return true;
 }
 
-// Do rows a and b of the output pool agree on every output column?
+// Do rows a and b of the output pool, with equal sort keys, agree on every
+// output column?
 __device__ __forceinline__ bool out_row_eq(const Wave &W, const DQuery &Q, const QState &S, uint32_t a, uint32_t b) {
   const uint32_t *x = W.out + S.out_word_base + (uint64_t)(a - S.out_row_base) * Q.k;
   const uint32_t *y = W.out + S.out_word_base + (uint64_t)(b - S.out_row_base) * Q.k;
-  for (uint32_t i = 0; i < Q.kp; ++i)
+  for (uint32_t i = key_cols(W); i < Q.kp; ++i)
     if (x[Q.opos[i]] != y[Q.opos[i]]) return false;
   return true;
 }
@@ -1988,19 +1995,22 @@ __global__ void __launch_bounds__(1024) k_sort_bases(Wave W) {
   if (threadIdx.x == 0) W.ctrl->len[7] = carry;
 }
 
-// Tile sort: keys (and row indices) in shared memory, bitonic network; rows
-// are read from the output pool only to order equal keys.
+// Tile sort (queries the bucket sort left): keys (and row indices) in
+// shared memory, bitonic network; rows are read from the output pool only to
+// order equal keys.
 __global__ void __launch_bounds__(256) k_tile_sort(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout,
                                                    SortKey *kout) {
   __shared__ SortKey key[kTileRows];
   __shared__ uint32_t row[kTileRows];
   __shared__ uint32_t idx[kTileRows];
+  if (!W.ctrl->bkt_fail) return;  // every query was sorted by buckets
   const uint64_t ntiles = W.ctrl->len[7];
   uint64_t acc = 0;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint32_t qi = seg_of_large(W.qs, W.nq, t, true);
     const DQuery &Q = W.dq[qi];
     const QState &S = W.qs[qi];
+    if (!S.bkt_fail) continue;  // block-uniform: sorted by buckets
     const uint64_t first = (t - S.lrg_tile_base) * kTileRows, at = S.lrg_row_base + first;
     const uint32_t n = (uint32_t)min((uint64_t)kTileRows, S.sort_rows - first);
     if (threadIdx.x == 0) acc += 40ull * n;  // keys and indices read and written
@@ -2067,7 +2077,7 @@ __device__ __forceinline__ MergeTile merge_tile(const Wave &W, uint64_t t, uint6
   m.va = min(m.na, cap);
   m.vb = min(m.nb, cap);
   m.out = min(m.va + m.vb, cap);
-  m.active = n > run && m.first - m.a0 < m.out;
+  m.active = S.bkt_fail && n > run && m.first - m.a0 < m.out;  // only queries the bucket sort left
   return m;
 }
 
@@ -2086,6 +2096,7 @@ __device__ __forceinline__ uint64_t merge_split_at(const Wave &W, const DQuery &
 
 // Split of every active output tile at its first output.  One thread per tile.
 __global__ void k_merge_split(Wave W, const uint32_t *perm, const SortKey *key, uint64_t run) {
+  if (!W.ctrl->bkt_fail) return;
   const uint64_t ntiles = W.ctrl->len[7];
   for (uint64_t t = gtid(); t < ntiles; t += gthreads()) {
     const MergeTile m = merge_tile(W, t, run);
@@ -2110,6 +2121,7 @@ __global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *pin
   __shared__ SortKey sk[kTileRows];
   __shared__ uint32_t si[kTileRows];
   __shared__ uint64_t s_end;
+  if (!W.ctrl->bkt_fail) return;
   const uint64_t ntiles = W.ctrl->len[7];
   uint64_t acc = 0;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -2174,6 +2186,333 @@ __device__ __forceinline__ uint32_t merge_passes(uint64_t n) {
   uint32_t p = 0;
   for (uint64_t run = kTileRows; run < n; run *= 2) ++p;
   return p;
+}
+
+// ------------------------------------------------------------ sample sort
+// The large outputs are sorted by a sample sort.  A query of n entries gets
+// nb = ceil(n / kBktAvg) buckets (two slots per tile of the query), bounded
+// by nb - 1 splitters taken at even ranks from a sorted stratified sample of
+// its entries; each entry goes to its bucket (count, scan, scatter), and one
+// block sorts each bucket in shared memory.  Entries are ordered by (key,
+// then, when the key does not hold the whole row, a second key of the next
+// output columns and the columns after those, then the entry's row index):
+// a total order, so only the sample decides bucket sizes.  The second keys
+// are built from the rows when entries are staged in shared memory, so that
+// the comparisons of rows with equal first keys stay on chip (rows of more
+// than twice the first key's columns still compare their last columns in
+// the output pool).  A query with a bucket above kBktCap entries (a sample
+// far off the data) is sorted by the tile sort and merge passes instead,
+// from the input its entries still hold there (every query is, when the
+// batch is set to the merge path only).
+constexpr uint32_t kBktAvg = kTileRows / 2;  // entries per bucket, on average
+constexpr uint32_t kBktSmall = 1024;       // buckets up to this size: small blocks, many per SM
+constexpr uint32_t kBktCap = 4096;         // entries one block sorts in shared memory
+constexpr uint32_t kBktOversample = 4;     // sample entries per bucket
+constexpr uint32_t kBktSampleMax = 4096;   // sample entries per query
+constexpr uint32_t kBktSmemSpl = 2048;     // splitters staged in shared memory for the bucket search
+
+// Three-way comparison of output rows a and b, equal on their first `from`
+// output columns, on the columns after those.
+__device__ __forceinline__ int out_row_cmp_from(const Wave &W, const DQuery &Q, const QState &S, uint32_t a,
+                                                uint32_t b, uint32_t from) {
+  const uint32_t *x = W.out + S.out_word_base + (uint64_t)(a - S.out_row_base) * Q.k;
+  const uint32_t *y = W.out + S.out_word_base + (uint64_t)(b - S.out_row_base) * Q.k;
+  for (uint32_t i = from; i < Q.kp; ++i) {
+    const uint32_t c = Q.opos[i];
+    const uint32_t xa = x[c], yb = y[c];
+    if (xa != yb) return xa < yb ? -1 : 1;
+  }
+  return 0;
+}
+
+// Second key of output row r: its output columns from key_cols(W) on,
+// packed as the first key packs the leading ones.
+__device__ __forceinline__ SortKey row_key2(const Wave &W, const DQuery &Q, const QState &S, uint32_t r) {
+  const uint32_t *x = W.out + S.out_word_base + (uint64_t)(r - S.out_row_base) * Q.k;
+  const uint32_t kc = key_cols(W);
+  return sort_key(Q.kp - kc, W.G.idbits, [&](uint32_t c) { return x[Q.opos[kc + c]]; });
+}
+
+// The sample sort's total order on entries (first key ka, second key ka2,
+// row index ra); exact: the first key holds every output column (second
+// keys unused).
+__device__ __forceinline__ bool ent_lt(const Wave &W, const DQuery &Q, const QState &S, bool exact, SortKey ka,
+                                       SortKey ka2, uint32_t ra, SortKey kb, SortKey kb2, uint32_t rb) {
+  if (ka != kb) return ka < kb;
+  if (ra == rb) return false;
+  if (!exact) {
+    if (ka2 != kb2) return ka2 < kb2;
+    if (Q.kp > 2 * key_cols(W)) {
+      const int c = out_row_cmp_from(W, Q, S, ra, rb, 2 * key_cols(W));
+      if (c) return c < 0;
+    }
+  }
+  return ra < rb;
+}
+
+// Entries staged in shared memory as arrays: first key words, second key
+// words (queries whose first key does not hold the whole row) and row
+// indices.  Padding entries past the live ones hold all-ones keys and the
+// row index kPadRow, so they sort last.
+constexpr uint32_t kPadRow = 0xFFFFFFFFu;
+struct SmemEnts {
+  uint64_t *hi, *lo, *hi2, *lo2;
+  uint32_t *row;
+};
+
+template <bool EXACT>
+__device__ __forceinline__ bool sm_less(const Wave &W, const DQuery &Q, const QState &S, const SmemEnts &e, uint32_t a,
+                                        uint32_t b) {
+  const uint64_t ah = e.hi[a], bh = e.hi[b];
+  if (ah != bh) return ah < bh;
+  const uint64_t al = e.lo[a], bl = e.lo[b];
+  if (al != bl) return al < bl;
+  const uint32_t ra = e.row[a], rb = e.row[b];
+  if (!EXACT && ra != rb && ra != kPadRow && rb != kPadRow) {
+    const uint64_t ah2 = e.hi2[a], bh2 = e.hi2[b];
+    if (ah2 != bh2) return ah2 < bh2;
+    const uint64_t al2 = e.lo2[a], bl2 = e.lo2[b];
+    if (al2 != bl2) return al2 < bl2;
+    if (Q.kp > 2 * key_cols(W)) {
+      const int c = out_row_cmp_from(W, Q, S, ra, rb, 2 * key_cols(W));
+      if (c) return c < 0;
+    }
+  }
+  return ra < rb;
+}
+
+// Bitonic network over the np2 staged entries (a power of two), exchanging
+// the entries themselves, so that every stage reads consecutive words.
+template <bool EXACT>
+__device__ __forceinline__ void block_sort_ents(const Wave &W, const DQuery &Q, const QState &S, const SmemEnts &e,
+                                                uint32_t np2) {
+  for (uint32_t size = 2; size <= np2; size <<= 1)
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t x = threadIdx.x; x < np2 / 2; x += blockDim.x) {
+        const uint32_t i = 2 * x - (x & (stride - 1));
+        const uint32_t p = i + stride;
+        const bool up = (i & size) == 0;
+        if (up ? sm_less<EXACT>(W, Q, S, e, p, i) : sm_less<EXACT>(W, Q, S, e, i, p)) {
+          uint64_t t = e.hi[i]; e.hi[i] = e.hi[p]; e.hi[p] = t;
+          t = e.lo[i]; e.lo[i] = e.lo[p]; e.lo[p] = t;
+          if (!EXACT) {
+            t = e.hi2[i]; e.hi2[i] = e.hi2[p]; e.hi2[p] = t;
+            t = e.lo2[i]; e.lo2[i] = e.lo2[p]; e.lo2[p] = t;
+          }
+          const uint32_t r = e.row[i]; e.row[i] = e.row[p]; e.row[p] = r;
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void block_sort_ents(const Wave &W, const DQuery &Q, const QState &S, const SmemEnts &e,
+                                                uint32_t np2, bool exact) {
+  if (exact) block_sort_ents<true>(W, Q, S, e, np2);
+  else block_sort_ents<false>(W, Q, S, e, np2);
+}
+
+// Entry j of the staged arrays: live (key k, row r, second key of r unless
+// exact) or padding.
+__device__ __forceinline__ void stage_ent(const Wave &W, const DQuery &Q, const QState &S, const SmemEnts &e, uint32_t j,
+                                          bool live, bool exact, SortKey k, uint32_t r) {
+  if (!live) {
+    e.hi[j] = e.lo[j] = e.hi2[j] = e.lo2[j] = ~0ull;
+    e.row[j] = kPadRow;
+    return;
+  }
+  e.hi[j] = k.hi;
+  e.lo[j] = k.lo;
+  e.row[j] = r;
+  if (!exact) {
+    const SortKey k2 = row_key2(W, Q, S, r);
+    e.hi2[j] = k2.hi;
+    e.lo2[j] = k2.lo;
+  }
+}
+
+__device__ __forceinline__ SmemEnts carve_ents(uint8_t *base, uint32_t cap) {
+  SmemEnts e;
+  e.hi = reinterpret_cast<uint64_t *>(base);
+  e.lo = e.hi + cap;
+  e.hi2 = e.lo + cap;
+  e.lo2 = e.hi2 + cap;
+  e.row = reinterpret_cast<uint32_t *>(e.lo2 + cap);
+  return e;
+}
+constexpr size_t kEntBytes = 4 * sizeof(uint64_t) + sizeof(uint32_t);
+
+__device__ __forceinline__ uint64_t bkt_count_of(uint64_t n) { return (n + kBktAvg - 1) / kBktAvg; }
+__device__ __forceinline__ uint64_t bkt_base(const QState &S) { return 2 * S.lrg_tile_base; }
+
+// Splitters: one block per query of more than one bucket samples
+// m = min(4 nb, 4096, n) entries, one at a hashed position in each of m
+// equal strata, sorts them, and keeps the entries at ranks b m / nb
+// (b = 1 .. nb - 1) with their second keys.  Also clears every query's
+// overflow flag and sets the number of bucket slots (two per tile).
+__global__ void __launch_bounds__(1024) k_bkt_split(Wave W, const uint32_t *pin, const SortKey *kin) {
+  extern __shared__ __align__(16) uint8_t bkt_smem[];
+  const SmemEnts e = carve_ents(bkt_smem, kBktSampleMax);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    W.ctrl->bkt_fail = W.merge_only;
+    W.ctrl->nbkt = 2 * W.ctrl->len[7];
+  }
+  uint64_t acc = 0;
+  for (uint32_t qi = blockIdx.x; qi < W.nq; qi += gridDim.x) {
+    QState &S = W.qs[qi];
+    if (threadIdx.x == 0) S.bkt_fail = W.merge_only;
+    const uint64_t n = S.sort_rows, nb = bkt_count_of(n);
+    if (nb <= 1 || W.merge_only) continue;  // block-uniform
+    const DQuery &Q = W.dq[qi];
+    const bool exact = keys_exact(W, Q);
+    uint64_t mm = nb * kBktOversample;
+    if (mm > kBktSampleMax) mm = kBktSampleMax;
+    if (mm > n) mm = n;
+    const uint32_t m = (uint32_t)mm;
+    uint32_t np2 = 1;
+    while (np2 < m) np2 <<= 1;
+    for (uint32_t j = threadIdx.x; j < np2; j += blockDim.x) {
+      SortKey k{0, 0};
+      uint32_t r = 0;
+      if (j < m) {
+        const uint64_t lo = (uint64_t)j * n / m, hi = (uint64_t)(j + 1) * n / m;
+        const uint64_t p = lo + (hi > lo ? mix64(((uint64_t)qi << 32) ^ j) % (hi - lo) : 0);
+        k = kin[S.lrg_row_base + p];
+        r = pin[S.lrg_row_base + p];
+      }
+      stage_ent(W, Q, S, e, j, j < m, exact, k, r);
+    }
+    __syncthreads();
+    block_sort_ents(W, Q, S, e, np2, exact);
+    for (uint64_t b = 1 + threadIdx.x; b < nb; b += blockDim.x) {
+      const uint32_t j = (uint32_t)(b * m / nb);
+      W.bspl_key[bkt_base(S) + b - 1] = SortKey{e.hi[j], e.lo[j]};
+      W.bspl_key2[bkt_base(S) + b - 1] = exact ? SortKey{0, 0} : SortKey{e.hi2[j], e.lo2[j]};
+      W.bspl_row[bkt_base(S) + b - 1] = e.row[j];
+    }
+    if (threadIdx.x == 0) acc += 20ull * m + 36ull * (nb - 1);  // samples read, splitters written
+    __syncthreads();
+  }
+  flush_bytes(W, KK_SORT_LARGE, acc);
+}
+
+// Bucket of each entry (count pass: found by a search of the query's
+// splitters, kept in bkt_id and counted into ptcount; scatter pass: each
+// entry to its bucket's next free slot, from the scan of the counts in ptscan
+// and the cursors in msplit, into pout / kout).  Each block takes a
+// contiguous range of tiles, so consecutive tiles are mostly one query's and
+// its splitters' first keys are staged in shared memory once.  An entry's
+// second key is built only when its first key equals a splitter's.
+__global__ void __launch_bounds__(256) k_bkt_place(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout,
+                                                   SortKey *kout, int scatter) {
+  __shared__ SortKey ssk[kBktSmemSpl];
+  if (W.merge_only) return;
+  const uint64_t nt = W.ctrl->len[7];
+  const uint64_t per = (nt + gridDim.x - 1) / gridDim.x;
+  const uint64_t t0 = (uint64_t)blockIdx.x * per, t1 = t0 + per < nt ? t0 + per : nt;
+  uint32_t qi = t0 < t1 ? seg_of_large(W.qs, W.nq, t0, true) : 0;
+  uint32_t staged_q = 0xFFFFFFFFu;
+  uint64_t acc = 0;
+  for (uint64_t t = t0; t < t1; ++t) {  // block-uniform
+    while (qi + 1 < W.nq && W.qs[qi + 1].lrg_tile_base <= t) ++qi;
+    QState &S = W.qs[qi];
+    const DQuery &Q = W.dq[qi];
+    const bool exact = keys_exact(W, Q);
+    const uint64_t nb = bkt_count_of(S.sort_rows), sb = bkt_base(S);
+    const bool staged = !scatter && nb > 1 && nb - 1 <= kBktSmemSpl;
+    if (staged && staged_q != qi) {
+      __syncthreads();  // every search in the previous query's splitters is done
+      for (uint32_t j = threadIdx.x; j < nb - 1; j += blockDim.x) ssk[j] = W.bspl_key[sb + j];
+      __syncthreads();
+      staged_q = qi;
+    }
+    const uint64_t first = (t - S.lrg_tile_base) * kTileRows;
+    const uint32_t cnt = (uint32_t)(S.sort_rows - first < kTileRows ? S.sort_rows - first : kTileRows);
+    for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const uint64_t i = S.lrg_row_base + first + e;
+      const SortKey key = kin[i];
+      const uint32_t row = pin[i];
+      if (scatter) {
+        const uint64_t tb = sb + W.bkt_id[i];
+        const uint64_t pos = S.lrg_row_base + (W.ptscan[tb] - W.ptscan[sb]) +
+                             atomicAdd((unsigned long long *)&W.msplit[tb], 1ull);
+        pout[pos] = row;
+        kout[pos] = key;
+        acc += 44;  // key, index and bucket read; key and index written
+        if (W.ptcount[tb] > kBktCap) {
+          S.bkt_fail = 1;
+          W.ctrl->bkt_fail = 1;
+        }
+        continue;
+      }
+      SortKey key2{0, 0};
+      bool have2 = exact;
+      uint32_t b = 0;
+      if (nb > 1) {  // splitters below the entry
+        uint32_t lo = 0, hi = (uint32_t)(nb - 1);
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          const SortKey s1 = staged ? ssk[mid] : W.bspl_key[sb + mid];
+          bool lt;
+          if (s1 != key) {
+            lt = s1 < key;
+          } else {
+            if (!have2) {
+              key2 = row_key2(W, Q, S, row);
+              have2 = true;
+            }
+            lt = ent_lt(W, Q, S, exact, s1, W.bspl_key2[sb + mid], W.bspl_row[sb + mid], key, key2, row);
+          }
+          if (lt) lo = mid + 1; else hi = mid;
+        }
+        b = lo;
+      }
+      W.bkt_id[i] = b;
+      atomicAdd(&W.ptcount[sb + b], 1u);
+      acc += 24;  // key and index read, bucket written
+    }
+  }
+  flush_bytes(W, KK_SORT_LARGE, acc);
+}
+
+// One block per bucket of (LO, CAP] entries: the entries, with their second
+// keys when the first does not hold the whole row, sorted in shared memory
+// and written, in place, to the buffer the query's sorted rows are read from
+// (the one the merge passes would have ended in).  Bucket slots are per
+// tile: the bucket of slot t belongs to the query holding tile t / 2.
+template <uint32_t LO, uint32_t CAP>
+__global__ void k_bkt_sort(Wave W, const uint32_t *px, const SortKey *kx, uint32_t *p0, SortKey *k0, uint32_t *p1,
+                           SortKey *k1) {
+  extern __shared__ __align__(16) uint8_t bkt_smem[];
+  const SmemEnts e = carve_ents(bkt_smem, CAP);
+  const uint64_t nt = W.ctrl->nbkt;
+  uint64_t acc = 0;
+  for (uint64_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    const uint32_t n = W.ptcount[t];
+    if (n <= LO || n > CAP) continue;  // block-uniform: another tier's, empty, or overflowed
+    const uint32_t qi = seg_of_large(W.qs, W.nq, t / 2, true);
+    const QState &S = W.qs[qi];
+    if (S.bkt_fail) continue;
+    const DQuery &Q = W.dq[qi];
+    const bool exact = keys_exact(W, Q);
+    const uint64_t at = S.lrg_row_base + (W.ptscan[t] - W.ptscan[bkt_base(S)]);
+    uint32_t np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (uint32_t j = threadIdx.x; j < np2; j += blockDim.x)
+      stage_ent(W, Q, S, e, j, j < n, exact, j < n ? kx[at + j] : SortKey{0, 0}, j < n ? px[at + j] : 0);
+    __syncthreads();
+    block_sort_ents(W, Q, S, e, np2, exact);
+    const bool odd = merge_passes(S.sort_rows) & 1;
+    uint32_t *po = odd ? p1 : p0;
+    SortKey *ko = odd ? k1 : k0;
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+      po[at + j] = e.row[j];
+      ko[at + j] = SortKey{e.hi[j], e.lo[j]};
+    }
+    if (threadIdx.x == 0) acc += (exact ? 40ull : 40ull + 4ull * Q.kp) * n;  // keys and indices (and rows) read, written
+    __syncthreads();
+  }
+  flush_bytes(W, KK_SORT_LARGE, acc);
 }
 
 // Sorted large rows in query-vertex column order, laid out query by query:
@@ -2438,6 +2777,31 @@ void launch_select(const Wave &W, const uint32_t *pin, const SortKey *kin, uint3
   }
   k_sel_compact<<<persistent_grid(k_sel_compact, sms), kThreads, 0, s>>>(W, pin, kin, pout, kout);
   k_sort_bases<<<1, 1024, 0, s>>>(W);
+}
+void launch_bucket_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *px, SortKey *kx,
+                        uint32_t *p0, SortKey *k0, uint32_t *p1, SortKey *k1, uint64_t *scan_tmp, cudaStream_t s,
+                        int sms) {
+  constexpr size_t split_smem = (size_t)kBktSampleMax * kEntBytes;
+  constexpr size_t small_smem = (size_t)kBktSmall * kEntBytes;
+  constexpr size_t big_smem = (size_t)kBktCap * kEntBytes;
+  static const bool attrs = [] {
+    cudaFuncSetAttribute(k_bkt_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem);
+    cudaFuncSetAttribute(k_bkt_sort<kBktSmall, kBktCap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
+    return true;
+  }();
+  (void)attrs;
+  const uint64_t slots = 2 * (W.out_rows_cap / kTileRows + W.nq + 1);
+  cudaMemsetAsync(W.ptcount, 0, 4 * slots, s);
+  cudaMemsetAsync(W.msplit, 0, 8 * slots, s);
+  k_bkt_split<<<std::max(1u, std::min<unsigned>(W.nq, (unsigned)sms * 2)), 1024, split_smem, s>>>(W, pin, kin);
+  const unsigned place = persistent_grid(k_bkt_place, sms);
+  k_bkt_place<<<place, kThreads, 0, s>>>(W, pin, kin, px, kx, 0);
+  scan_u32(W.ptcount, W.ptscan, &W.ctrl->nbkt, slots, scan_tmp, s, sms);
+  k_bkt_place<<<place, kThreads, 0, s>>>(W, pin, kin, px, kx, 1);
+  k_bkt_sort<0, kBktSmall><<<persistent_grid(k_bkt_sort<0, kBktSmall>, sms, 256, small_smem), 256, small_smem, s>>>(
+      W, px, kx, p0, k0, p1, k1);
+  k_bkt_sort<kBktSmall, kBktCap><<<persistent_grid(k_bkt_sort<kBktSmall, kBktCap>, sms, 1024, big_smem), 1024,
+                                   big_smem, s>>>(W, px, kx, p0, k0, p1, k1);
 }
 void launch_tile_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                       cudaStream_t s, int sms) {

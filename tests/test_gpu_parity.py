@@ -377,3 +377,51 @@ def test_large_call_as_concurrent_sub_batches(small):
     assert sum(busy.values()) > 0
     for p in parts:
         p.close()
+
+
+@pytest.fixture(scope="module")
+def wide_ids():
+    """A 12-vertex complete digraph placed at the top of 4.2M vertex ids
+    (ids need 23 bits, so a sort key holds four columns and rows of five or
+    more vertices tie on their keys), the other vertices isolated."""
+    V, n = 4_200_000, 12
+    hub = np.arange(V - n, V, dtype=np.uint32)
+    ro = np.zeros(V + 1, np.uint64)
+    ro[V - n + 1:] = np.cumsum(np.full(n, n - 1, np.uint64))
+    col = np.array([d for s in hub for d in hub if d != s], np.uint32)
+    g = I.Graph(V, ro, col, np.zeros(col.shape[0], np.uint32), np.zeros(V, np.uint32), 1, 1)
+    return g, O.OracleGraph.from_graph(g), gs.DeviceGraph(g), hub
+
+
+def test_sample_sort_and_merge_path_agree_with_the_oracle(wide_ids):
+    """Large outputs (above 2,048 rows) through the sample sort and through
+    the tile sort and merge passes give the oracle's rows: paths of 4-7
+    vertices (keys holding the whole row, and rows tying on their keys) with
+    a 3-vertex path of 1,320 rows beside them (one-block sort), a
+    path with more rows than cap (selection first), twelve outputs of 7,920
+    rows each (one per bound start vertex) and projected rows with repeats."""
+    g, og, dg, hub = wide_ids
+    cap = 1 << 20
+    paths = [query(k, [(i, i + 1, 0) for i in range(k - 1)]) for k in (3, 4, 5, 6, 7)]
+    bound = [query(5, [(i, i + 1, 0) for i in range(4)], vbind=[int(h)] + [I.UNBOUND] * 4) for h in hub]
+    qs = paths + bound
+    want = [O.match(og, q, cap=cap) for q in qs]
+    assert want[4].count > cap and all(w.count > 2048 for w in want[1:])  # the 3-path: one-block sort
+    for merge_only in (False, True):
+        b = gs.Batch(dg, qs, cap=cap)
+        b.set_sort(merge_only=merge_only)
+        for _ in range(2):  # the second run reuses every buffer
+            b.run()
+            b.finish()
+            for i, (r, o) in enumerate(zip(b.fetch(), want)):
+                assert_same(r, o, (merge_only, i))
+        b.close()
+    proj = [query(5, [(i, i + 1, 0) for i in range(4)])]
+    pw = O.match(og, proj[0], cap=cap, project=[0, 3])
+    for merge_only in (False, True):
+        b = gs.Batch(dg, proj, cap=cap, project=[0, 3])
+        b.set_sort(merge_only=merge_only)
+        b.run()
+        b.finish()
+        assert_same(b.fetch()[0], pw, ("projected", merge_only))
+        b.close()
