@@ -711,9 +711,11 @@ __device__ __forceinline__ void explore_item(const cg::thread_block_tile<G> &til
   uint64_t bytes = 0;
   // every edge to a typed vertex w needs a neighbour of w's type over its
   // relation and direction: the neighbour-type masks of all edges, loaded
-  // together, reject most candidates before any row is read
+  // together, reject most candidates before any row is read (the filter
+  // already applied them to the typed, unbound first vertex's candidates)
   bool keep = true;
-  for (uint32_t i = i0; i < i1 && !(Q.refine_flags & kRefineBase); ++i) {
+  const bool masked = step == 0 && Q.vbind[u] == kUnbound && Q.vtype[u] != kAny && !W.c0_only;
+  for (uint32_t i = i0; i < i1 && !(Q.refine_flags & kRefineBase) && !masked; ++i) {
     const uint32_t xi = Q.xinc[i];
     const uint32_t t = Q.vtype[xinc_w(xi)];
     if (t == kAny) continue;
