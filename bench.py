@@ -525,7 +525,10 @@ def run_profile_once(args):
     """One small program for ncu captures: the workload's batch (or its first
     --queries queries) run --runs times, with no timing, comparison modes,
     serving or CPU baseline, so that a capture of a few kernels ends
-    quickly."""
+    quickly.  The batch is split into sub-batches run together as the timed
+    step splits it (--parts; 4 from 4,096 queries), so every launch does the
+    work of one launch of the step."""
+    import torch
     import paper_1807_08804_gb300 as gs
     from paper_1807_08804_gb300 import inputs as I
     w = I.WORKLOADS[args.workload]
@@ -534,7 +537,9 @@ def run_profile_once(args):
     dg = gs.DeviceGraph(g)
     if args.group or args.rounds:
         gs.tune_set(dg, args.group, args.rounds)
-    b = gs.Batch(dg, qs, cap=w.cap)
+    stream = torch.cuda.Stream()
+    parts = args.parts if args.parts else (4 if len(qs) >= 4096 else 1)
+    b = SubBatches(gs, dg, qs, parts, stream.cuda_stream, cap=w.cap)
     if args.stats:
         b.stats_enable(True)
     for _ in range(args.runs):
