@@ -747,7 +747,7 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    e2e_steps = max(2, args.steps // 2)
+    e2e_steps = max(2, args.steps)
     for _ in range(e2e_steps):
         got = c_step()
     torch.cuda.synchronize()
