@@ -270,17 +270,17 @@ static gs_status batch_alloc(gs_batch *b, const gs_match_opts *o) {
     A(W.sval[i], s.out_rows);
   }
   A(W.bkt_id, s.out_rows);
-  // per tile of the large-output sort; two bucket slots per tile
-  A(W.msplit, 2 * (s.out_rows / kTileRows + W.nq + 1));
-  A(W.bspl_key, 2 * (s.out_rows / kTileRows + W.nq + 1));
-  A(W.bspl_key2, 2 * (s.out_rows / kTileRows + W.nq + 1));
-  A(W.bspl_row, 2 * (s.out_rows / kTileRows + W.nq + 1));
-  A(W.ptcount, 2 * (s.out_rows / kTileRows + W.nq + 1));
-  A(W.ptscan, 2 * (s.out_rows / kTileRows + W.nq + 1) + 1);
+  // per tile of the large-output sort, with kBktPerTile bucket slots per tile
+  A(W.msplit, kBktPerTile * (s.out_rows / kTileRows + W.nq + 1));
+  A(W.bspl_key, kBktPerTile * (s.out_rows / kTileRows + W.nq + 1));
+  A(W.bspl_key2, kBktPerTile * (s.out_rows / kTileRows + W.nq + 1));
+  A(W.bspl_row, kBktPerTile * (s.out_rows / kTileRows + W.nq + 1));
+  A(W.ptcount, kBktPerTile * (s.out_rows / kTileRows + W.nq + 1));
+  A(W.ptscan, kBktPerTile * (s.out_rows / kTileRows + W.nq + 1) + 1);
   A(W.sel, W.nq);
   A(W.shist, (uint64_t)W.nq * 256);
   uint64_t tmpw = scan_tmp_words(std::max<uint64_t>(
-      {(uint64_t)W.nqv * cps, (uint64_t)W.nqe, s.ec_items, W.row_cap, 2 * (s.out_rows / kTileRows + W.nq + 1)}));
+      {(uint64_t)W.nqv * cps, (uint64_t)W.nqe, s.ec_items, W.row_cap, kBktPerTile * (s.out_rows / kTileRows + W.nq + 1)}));
   A(b->scan_tmp, tmpw);
   b->scan_tmp_words = tmpw;
   A(b->type_count, G.T);
@@ -499,7 +499,7 @@ void enqueue_back(Pipe &P, int K, int stop) {
 uint64_t large_sort_launches(uint64_t max_rows, uint64_t over_cap, bool proj) {
   uint64_t passes = 0;
   for (uint64_t run = kTileRows; run < max_rows; run *= 2) ++passes;
-  return 3 + 5 + 2 * passes + (over_cap ? 3 + 2 * 3 : 0) + (proj ? 3 : 0);
+  return 3 + 7 + 2 * passes + (over_cap ? 3 + 2 * 3 : 0) + (proj ? 3 : 0);
 }
 
 void enqueue_large_sort(Pipe &P, uint64_t max_rows, uint64_t over_cap, bool proj) {
@@ -1057,12 +1057,12 @@ gs_status grow_pools(gs_batch *b) {
     bool ok = regrow(b, &W.out_q, n) == GS_OK;
     for (int i = 0; i < 2 && ok; ++i) ok = regrow(b, &W.skey[i], n) == GS_OK && regrow(b, &W.sval[i], n) == GS_OK;
     ok = ok && regrow(b, &W.bkt_id, n) == GS_OK;
-    ok = ok && regrow(b, &W.msplit, 2 * (n / kTileRows + W.nq + 1)) == GS_OK;
-    ok = ok && regrow(b, &W.bspl_key, 2 * (n / kTileRows + W.nq + 1)) == GS_OK;
-    ok = ok && regrow(b, &W.bspl_key2, 2 * (n / kTileRows + W.nq + 1)) == GS_OK;
-    ok = ok && regrow(b, &W.bspl_row, 2 * (n / kTileRows + W.nq + 1)) == GS_OK;
-    ok = ok && regrow(b, &W.ptcount, 2 * (n / kTileRows + W.nq + 1)) == GS_OK;
-    ok = ok && regrow(b, &W.ptscan, 2 * (n / kTileRows + W.nq + 1) + 1) == GS_OK;
+    ok = ok && regrow(b, &W.msplit, kBktPerTile * (n / kTileRows + W.nq + 1)) == GS_OK;
+    ok = ok && regrow(b, &W.bspl_key, kBktPerTile * (n / kTileRows + W.nq + 1)) == GS_OK;
+    ok = ok && regrow(b, &W.bspl_key2, kBktPerTile * (n / kTileRows + W.nq + 1)) == GS_OK;
+    ok = ok && regrow(b, &W.bspl_row, kBktPerTile * (n / kTileRows + W.nq + 1)) == GS_OK;
+    ok = ok && regrow(b, &W.ptcount, kBktPerTile * (n / kTileRows + W.nq + 1)) == GS_OK;
+    ok = ok && regrow(b, &W.ptscan, kBktPerTile * (n / kTileRows + W.nq + 1) + 1) == GS_OK;
     if (ok) { W.out_rows_cap = n; changed = true; }
   }
   if (hw[HW_OUT_WORDS] > W.out_words && hw[HW_OUT_WORDS] <= kMaxEntries) {
@@ -1076,7 +1076,7 @@ gs_status grow_pools(gs_batch *b) {
   if (changed) {
     const uint64_t cps = W.G.nchunks;  // chunks per set: one candidate count per chunk
     uint64_t tmpw = scan_tmp_words(std::max<uint64_t>(
-        {(uint64_t)W.nqv * cps, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap, 2 * (W.out_rows_cap / kTileRows + W.nq + 1)}));
+        {(uint64_t)W.nqv * cps, (uint64_t)W.nqe, W.ec_items_cap, W.row_cap, kBktPerTile * (W.out_rows_cap / kTileRows + W.nq + 1)}));
     if (regrow(b, &b->scan_tmp, tmpw) == GS_OK) {
       b->scan_tmp_words = tmpw;
       GS_CUDA(cudaMemsetAsync(b->scan_tmp, 0, sizeof(uint64_t) * tmpw, b->stream));

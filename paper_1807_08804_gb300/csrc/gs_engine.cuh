@@ -15,6 +15,7 @@ constexpr uint32_t kAny = 0xFFFFFFFFu;
 constexpr uint32_t kMaxRounds = 64;
 constexpr uint32_t kSmallRows = 2048;    // outputs sorted by one block in shared memory
 constexpr uint32_t kTileRows = 1024;     // rows per tile of the large-output merge sort
+constexpr uint32_t kBktPerTile = 4;      // sample-sort bucket slots per tile (buckets of 256 entries on average)
 constexpr uint64_t kOverCap = 16;        // outputs up to kOverCap * cap rows are sorted on the device
 
 // Per-query status.
@@ -199,7 +200,7 @@ struct Ctrl {
   uint64_t bytes[KK_N];             // algorithmic bytes per kernel kind
   uint32_t bkt_fail;                // some query's sample-sort bucket overflowed (merge path runs)
   uint32_t pad_;
-  uint64_t nbkt;                    // bucket slots of the sample sort (two per tile)
+  uint64_t nbkt;                    // bucket slots of the sample sort (kBktPerTile per tile)
 };
 
 // Everything a kernel needs, passed by value.  Capacities are fixed when the

@@ -2192,7 +2192,7 @@ __device__ __forceinline__ uint32_t merge_passes(uint64_t n) {
 
 // ------------------------------------------------------------ sample sort
 // The large outputs are sorted by a sample sort.  A query of n entries gets
-// nb = ceil(n / kBktAvg) buckets (two slots per tile of the query), bounded
+// nb = ceil(n / kBktAvg) buckets (kBktPerTile slots per tile of the query), bounded
 // by nb - 1 splitters taken at even ranks from a sorted stratified sample of
 // its entries; each entry goes to its bucket (count, scan, scatter), and one
 // block sorts each bucket in shared memory.  Entries are ordered by (key,
@@ -2206,12 +2206,13 @@ __device__ __forceinline__ uint32_t merge_passes(uint64_t n) {
 // far off the data) is sorted by the tile sort and merge passes instead,
 // from the input its entries still hold there (every query is, when the
 // batch is set to the merge path only).
-constexpr uint32_t kBktAvg = kTileRows / 2;  // entries per bucket, on average
-constexpr uint32_t kBktSmall = 1024;       // buckets up to this size: small blocks, many per SM
+constexpr uint32_t kBktAvg = kTileRows / kBktPerTile;  // entries per bucket, on average
+constexpr uint32_t kBktSmall = 512;        // buckets up to this size: small blocks, many per SM
+constexpr uint32_t kBktMid = 1024;         //   up to this size: small blocks, two pairs per thread
 constexpr uint32_t kBktCap = 4096;         // entries one block sorts in shared memory
 constexpr uint32_t kBktOversample = 4;     // sample entries per bucket
 constexpr uint32_t kBktSampleMax = 4096;   // sample entries per query
-constexpr uint32_t kBktSmemSpl = 2048;     // splitters staged in shared memory for the bucket search
+constexpr uint32_t kBktSmemSpl = 4096;     // splitters' leading key words staged in shared memory for the search
 
 // Three-way comparison of output rows a and b, equal on their first `from`
 // output columns, on the columns after those.
@@ -2285,6 +2286,10 @@ __device__ __forceinline__ bool sm_less(const Wave &W, const DQuery &Q, const QS
 
 // Bitonic network over the np2 staged entries (a power of two), exchanging
 // the entries themselves, so that every stage reads consecutive words.
+// Thread t takes the pairs t, t + blockDim.x, ...: a warp's pairs cover
+// whole 64-entry groups, so a stage of stride at most 32 exchanges only
+// inside the warp's own groups, and two such stages in a row need only a
+// warp barrier.
 template <bool EXACT>
 __device__ __forceinline__ void block_sort_ents(const Wave &W, const DQuery &Q, const QState &S, const SmemEnts &e,
                                                 uint32_t np2) {
@@ -2304,7 +2309,9 @@ __device__ __forceinline__ void block_sort_ents(const Wave &W, const DQuery &Q, 
           const uint32_t r = e.row[i]; e.row[i] = e.row[p]; e.row[p] = r;
         }
       }
-      __syncthreads();
+      const uint32_t next = stride > 1 ? stride >> 1 : size;  // the next stage's stride
+      if (stride <= 32 && next <= 32 && size < np2) __syncwarp();
+      else __syncthreads();
     }
 }
 
@@ -2345,19 +2352,19 @@ __device__ __forceinline__ SmemEnts carve_ents(uint8_t *base, uint32_t cap) {
 constexpr size_t kEntBytes = 4 * sizeof(uint64_t) + sizeof(uint32_t);
 
 __device__ __forceinline__ uint64_t bkt_count_of(uint64_t n) { return (n + kBktAvg - 1) / kBktAvg; }
-__device__ __forceinline__ uint64_t bkt_base(const QState &S) { return 2 * S.lrg_tile_base; }
+__device__ __forceinline__ uint64_t bkt_base(const QState &S) { return kBktPerTile * S.lrg_tile_base; }
 
 // Splitters: one block per query of more than one bucket samples
 // m = min(4 nb, 4096, n) entries, one at a hashed position in each of m
 // equal strata, sorts them, and keeps the entries at ranks b m / nb
 // (b = 1 .. nb - 1) with their second keys.  Also clears every query's
-// overflow flag and sets the number of bucket slots (two per tile).
+// overflow flag and sets the number of bucket slots (kBktPerTile per tile).
 __global__ void __launch_bounds__(1024) k_bkt_split(Wave W, const uint32_t *pin, const SortKey *kin) {
   extern __shared__ __align__(16) uint8_t bkt_smem[];
   const SmemEnts e = carve_ents(bkt_smem, kBktSampleMax);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     W.ctrl->bkt_fail = W.merge_only;
-    W.ctrl->nbkt = 2 * W.ctrl->len[7];
+    W.ctrl->nbkt = kBktPerTile * W.ctrl->len[7];
   }
   uint64_t acc = 0;
   for (uint32_t qi = blockIdx.x; qi < W.nq; qi += gridDim.x) {
@@ -2403,11 +2410,12 @@ __global__ void __launch_bounds__(1024) k_bkt_split(Wave W, const uint32_t *pin,
 // entry to its bucket's next free slot, from the scan of the counts in ptscan
 // and the cursors in msplit, into pout / kout).  Each block takes a
 // contiguous range of tiles, so consecutive tiles are mostly one query's and
-// its splitters' first keys are staged in shared memory once.  An entry's
+// the leading words of its splitters' keys are staged in shared memory once
+// (the rest of a splitter is read only when the leading words are equal).  An entry's
 // second key is built only when its first key equals a splitter's.
 __global__ void __launch_bounds__(256) k_bkt_place(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout,
                                                    SortKey *kout, int scatter) {
-  __shared__ SortKey ssk[kBktSmemSpl];
+  __shared__ uint64_t ssh[kBktSmemSpl];
   if (W.merge_only) return;
   const uint64_t nt = W.ctrl->len[7];
   const uint64_t per = (nt + gridDim.x - 1) / gridDim.x;
@@ -2424,7 +2432,7 @@ __global__ void __launch_bounds__(256) k_bkt_place(Wave W, const uint32_t *pin, 
     const bool staged = !scatter && nb > 1 && nb - 1 <= kBktSmemSpl;
     if (staged && staged_q != qi) {
       __syncthreads();  // every search in the previous query's splitters is done
-      for (uint32_t j = threadIdx.x; j < nb - 1; j += blockDim.x) ssk[j] = W.bspl_key[sb + j];
+      for (uint32_t j = threadIdx.x; j < nb - 1; j += blockDim.x) ssh[j] = W.bspl_key[sb + j].hi;
       __syncthreads();
       staged_q = qi;
     }
@@ -2454,9 +2462,12 @@ __global__ void __launch_bounds__(256) k_bkt_place(Wave W, const uint32_t *pin, 
         uint32_t lo = 0, hi = (uint32_t)(nb - 1);
         while (lo < hi) {
           const uint32_t mid = (lo + hi) >> 1;
-          const SortKey s1 = staged ? ssk[mid] : W.bspl_key[sb + mid];
           bool lt;
-          if (s1 != key) {
+          const uint64_t sh = staged ? ssh[mid] : W.bspl_key[sb + mid].hi;
+          const SortKey s1 = sh != key.hi ? SortKey{sh, 0} : W.bspl_key[sb + mid];
+          if (sh != key.hi) {
+            lt = sh < key.hi;
+          } else if (s1 != key) {
             lt = s1 < key;
           } else {
             if (!have2) {
@@ -2481,7 +2492,7 @@ __global__ void __launch_bounds__(256) k_bkt_place(Wave W, const uint32_t *pin, 
 // keys when the first does not hold the whole row, sorted in shared memory
 // and written, in place, to the buffer the query's sorted rows are read from
 // (the one the merge passes would have ended in).  Bucket slots are per
-// tile: the bucket of slot t belongs to the query holding tile t / 2.
+// tile: the bucket of slot t belongs to the query holding tile t / kBktPerTile.
 template <uint32_t LO, uint32_t CAP>
 __global__ void k_bkt_sort(Wave W, const uint32_t *px, const SortKey *kx, uint32_t *p0, SortKey *k0, uint32_t *p1,
                            SortKey *k1) {
@@ -2492,7 +2503,7 @@ __global__ void k_bkt_sort(Wave W, const uint32_t *px, const SortKey *kx, uint32
   for (uint64_t t = blockIdx.x; t < nt; t += gridDim.x) {
     const uint32_t n = W.ptcount[t];
     if (n <= LO || n > CAP) continue;  // block-uniform: another tier's, empty, or overflowed
-    const uint32_t qi = seg_of_large(W.qs, W.nq, t / 2, true);
+    const uint32_t qi = seg_of_large(W.qs, W.nq, t / kBktPerTile, true);
     const QState &S = W.qs[qi];
     if (S.bkt_fail) continue;
     const DQuery &Q = W.dq[qi];
@@ -2785,14 +2796,15 @@ void launch_bucket_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, 
                         int sms) {
   constexpr size_t split_smem = (size_t)kBktSampleMax * kEntBytes;
   constexpr size_t small_smem = (size_t)kBktSmall * kEntBytes;
+  constexpr size_t mid_smem = (size_t)kBktMid * kEntBytes;
   constexpr size_t big_smem = (size_t)kBktCap * kEntBytes;
   static const bool attrs = [] {
     cudaFuncSetAttribute(k_bkt_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem);
-    cudaFuncSetAttribute(k_bkt_sort<kBktSmall, kBktCap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
+    cudaFuncSetAttribute(k_bkt_sort<kBktMid, kBktCap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
     return true;
   }();
   (void)attrs;
-  const uint64_t slots = 2 * (W.out_rows_cap / kTileRows + W.nq + 1);
+  const uint64_t slots = kBktPerTile * (W.out_rows_cap / kTileRows + W.nq + 1);
   cudaMemsetAsync(W.ptcount, 0, 4 * slots, s);
   cudaMemsetAsync(W.msplit, 0, 8 * slots, s);
   k_bkt_split<<<std::max(1u, std::min<unsigned>(W.nq, (unsigned)sms * 2)), 1024, split_smem, s>>>(W, pin, kin);
@@ -2802,8 +2814,10 @@ void launch_bucket_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, 
   k_bkt_place<<<place, kThreads, 0, s>>>(W, pin, kin, px, kx, 1);
   k_bkt_sort<0, kBktSmall><<<persistent_grid(k_bkt_sort<0, kBktSmall>, sms, 256, small_smem), 256, small_smem, s>>>(
       W, px, kx, p0, k0, p1, k1);
-  k_bkt_sort<kBktSmall, kBktCap><<<persistent_grid(k_bkt_sort<kBktSmall, kBktCap>, sms, 1024, big_smem), 1024,
-                                   big_smem, s>>>(W, px, kx, p0, k0, p1, k1);
+  k_bkt_sort<kBktSmall, kBktMid><<<persistent_grid(k_bkt_sort<kBktSmall, kBktMid>, sms, 256, mid_smem), 256, mid_smem,
+                                   s>>>(W, px, kx, p0, k0, p1, k1);
+  k_bkt_sort<kBktMid, kBktCap><<<persistent_grid(k_bkt_sort<kBktMid, kBktCap>, sms, 1024, big_smem), 1024,
+                                 big_smem, s>>>(W, px, kx, p0, k0, p1, k1);
 }
 void launch_tile_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                       cudaStream_t s, int sms) {
