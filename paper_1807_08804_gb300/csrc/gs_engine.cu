@@ -499,7 +499,7 @@ void enqueue_back(Pipe &P, int K, int stop) {
 uint64_t large_sort_launches(uint64_t max_rows, uint64_t over_cap, bool proj) {
   uint64_t passes = 0;
   for (uint64_t run = kTileRows; run < max_rows; run *= 2) ++passes;
-  return 3 + 7 + 2 * passes + (over_cap ? 3 + 2 * 3 : 0) + (proj ? 3 : 0);
+  return 3 + 8 + 2 * passes + (over_cap ? 3 + 2 * 3 : 0) + (proj ? 3 : 0);
 }
 
 void enqueue_large_sort(Pipe &P, uint64_t max_rows, uint64_t over_cap, bool proj) {

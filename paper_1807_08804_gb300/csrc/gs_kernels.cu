@@ -2407,8 +2407,8 @@ __global__ void __launch_bounds__(1024) k_bkt_split(Wave W, const uint32_t *pin,
 
 // Bucket of each entry (count pass: found by a search of the query's
 // splitters, kept in bkt_id and counted into ptcount; scatter pass: each
-// entry to its bucket's next free slot, from the scan of the counts in ptscan
-// and the cursors in msplit, into pout / kout).  Each block takes a
+// entry to its bucket's next free place, from the cursors k_bkt_bases set in
+// msplit, into pout / kout).  Each block takes a
 // contiguous range of tiles, so consecutive tiles are mostly one query's and
 // the leading words of its splitters' keys are staged in shared memory once
 // (the rest of a splitter is read only when the leading words are equal).  An entry's
@@ -2443,16 +2443,10 @@ __global__ void __launch_bounds__(256) k_bkt_place(Wave W, const uint32_t *pin, 
       const SortKey key = kin[i];
       const uint32_t row = pin[i];
       if (scatter) {
-        const uint64_t tb = sb + W.bkt_id[i];
-        const uint64_t pos = S.lrg_row_base + (W.ptscan[tb] - W.ptscan[sb]) +
-                             atomicAdd((unsigned long long *)&W.msplit[tb], 1ull);
+        const uint64_t pos = atomicAdd((unsigned long long *)&W.msplit[sb + W.bkt_id[i]], 1ull);
         pout[pos] = row;
         kout[pos] = key;
         acc += 44;  // key, index and bucket read; key and index written
-        if (W.ptcount[tb] > kBktCap) {
-          S.bkt_fail = 1;
-          W.ctrl->bkt_fail = 1;
-        }
         continue;
       }
       SortKey key2{0, 0};
@@ -2486,6 +2480,22 @@ __global__ void __launch_bounds__(256) k_bkt_place(Wave W, const uint32_t *pin, 
     }
   }
   flush_bytes(W, KK_SORT_LARGE, acc);
+}
+
+// Each bucket slot's first place (from the scan of the counts) as its fill
+// cursor for the scatter pass; a bucket above kBktCap entries sends its
+// query to the merge path.
+__global__ void k_bkt_bases(Wave W) {
+  const uint64_t nt = W.ctrl->nbkt;
+  for (uint64_t t = gtid(); t < nt; t += gthreads()) {
+    const uint32_t qi = seg_of_large(W.qs, W.nq, t / kBktPerTile, true);
+    QState &S = W.qs[qi];
+    W.msplit[t] = S.lrg_row_base + (W.ptscan[t] - W.ptscan[bkt_base(S)]);
+    if (W.ptcount[t] > kBktCap) {
+      S.bkt_fail = 1;
+      W.ctrl->bkt_fail = 1;
+    }
+  }
 }
 
 // One block per bucket of (LO, CAP] entries: the entries, with their second
@@ -2806,11 +2816,11 @@ void launch_bucket_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, 
   (void)attrs;
   const uint64_t slots = kBktPerTile * (W.out_rows_cap / kTileRows + W.nq + 1);
   cudaMemsetAsync(W.ptcount, 0, 4 * slots, s);
-  cudaMemsetAsync(W.msplit, 0, 8 * slots, s);
   k_bkt_split<<<std::max(1u, std::min<unsigned>(W.nq, (unsigned)sms * 2)), 1024, split_smem, s>>>(W, pin, kin);
   const unsigned place = persistent_grid(k_bkt_place, sms);
   k_bkt_place<<<place, kThreads, 0, s>>>(W, pin, kin, px, kx, 0);
   scan_u32(W.ptcount, W.ptscan, &W.ctrl->nbkt, slots, scan_tmp, s, sms);
+  k_bkt_bases<<<persistent_grid(k_bkt_bases, sms), kThreads, 0, s>>>(W);
   k_bkt_place<<<place, kThreads, 0, s>>>(W, pin, kin, px, kx, 1);
   k_bkt_sort<0, kBktSmall><<<persistent_grid(k_bkt_sort<0, kBktSmall>, sms, 256, small_smem), 256, small_smem, s>>>(
       W, px, kx, p0, k0, p1, k1);
