@@ -736,7 +736,8 @@ __device__ __forceinline__ void explore_item(const cg::thread_block_tile<G> &til
     const uint32_t *ws = slot_of(W, Q.qv_base + w);
     bool found = false;
     uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, lo + r, hi);
-    for (uint64_t b = lo; b < hi && !found; b += G) {
+    uint64_t b = lo;
+    for (; b < hi && !found; b += G) {
       const uint64_t j = b + r;
       const uint32_t en = run_entry<G>(tile, Gr, dir, fast, base, xs, j + G, hi);  // the next pass's entry, early
       bool ok = false;
@@ -747,7 +748,9 @@ __device__ __forceinline__ void explore_item(const cg::thread_block_tile<G> &til
       found = tile.any(ok);
       e = en;
     }
-    bytes += 16 + 4 * (hi - lo);
+    // the run's entries, and per neighbour tested its bitmap word or type byte
+    const uint64_t tested = (b < hi ? b : hi) - lo;
+    bytes += 16 + 4 * (hi - lo) + tested * (built ? 4 : (Q.vtype[w] != kAny ? 1 : 0));
     if (!found) keep = false;
   }
   // tree edges to the children: test, expand and check existence in one scan
@@ -760,7 +763,7 @@ __device__ __forceinline__ void explore_item(const cg::thread_block_tile<G> &til
     uint32_t xs;
     const bool fast = rel_run<G>(tile, Gr, dir, v, adj_rel(xinc_rel(xi)), base, lo, hi, xs);
     uint32_t *ws = slot_of(W, Q.qv_base + w);
-    bool found = false;
+    uint32_t nset = 0;
     uint32_t e = run_entry<G>(tile, Gr, dir, fast, base, xs, lo + r, hi);
     for (uint64_t b = lo; b < hi; b += G) {
       const uint64_t j = b + r;
@@ -771,11 +774,12 @@ __device__ __forceinline__ void explore_item(const cg::thread_block_tile<G> &til
         ok = cand_ok(Gr, Q, w, x);
         if (ok) bit_set(W, ws, x);
       }
-      found = found || tile.any(ok);
+      nset += __popc(tile.ballot(ok));
       e = en;
     }
-    bytes += 16 + 4 * (hi - lo);
-    if (!found) keep = false;
+    // the run's entries, each neighbour's type byte, a bitmap word per bit set
+    bytes += 16 + 5 * (hi - lo) - (Q.vtype[w] != kAny ? 0 : hi - lo) + 4ull * nset;
+    if (nset == 0) keep = false;
   }
   if (!keep && r == 0) bit_clear(slot_of(W, Q.qv_base + u), v);
   if (r == 0) acc += bytes + 4;
