@@ -299,14 +299,27 @@ def cpu_baseline(workload, g, qs, sample_n=None, min_seconds=10.0, max_repeats=3
             "embeddings_per_s": emb / dt}
 
 
-def serve_measure(gs, dg, qs, rate_qps, duration_s, cap, seed=1):
-    """Poisson arrivals at rate_qps for duration_s into the serving loop;
-    latency is submit-to-completion as the server observes it."""
+def serve_measure(gs, dg, qs, rate_qps, duration_s, cap, seed=1, warmup_s=1.0):
+    """Poisson arrivals at rate_qps for duration_s into the serving loop,
+    after warmup_s of arrivals at the same rate whose results are dropped
+    (the slots capture their pipelines and size their pools then); latency
+    is submit-to-completion as the server observes it."""
     from paper_1807_08804_gb300 import inputs as I
-    n = max(1, int(rate_qps * duration_s))
-    arr = I.make_arrivals(n, rate_qps, seed=seed)
     pack = gs._QueryPack(qs)
     srv = gs.Server(dg, slots=4, max_batch=256)
+    nw = int(rate_qps * warmup_s)
+    if nw:
+        warr = I.make_arrivals(nw, rate_qps, seed=seed + 1000)
+        wt, t0 = [], time.perf_counter()
+        for i in range(nw):
+            while time.perf_counter() - t0 < warr[i]:
+                pass
+            wt.append(srv.submit_packed(pack, (i * 7919) % len(qs), cap=cap))
+        deadline = time.perf_counter() + 120
+        while wt and time.perf_counter() < deadline:
+            wt = [t for t in wt if srv.poll(t) is None]
+    n = max(1, int(rate_qps * duration_s))
+    arr = I.make_arrivals(n, rate_qps, seed=seed)
     tickets, t_sub = [], []
     t0 = time.perf_counter()
     for i in range(n):
@@ -335,7 +348,8 @@ def serve_measure(gs, dg, qs, rate_qps, duration_s, cap, seed=1):
     # loop here is slower than the server at the highest rates)
     last = max(done_at) if done_at else float("inf")
     return {"offered_qps": rate_qps, "requests": n, "completed": len(lat), "p50_ms": q(0.50), "p99_ms": q(0.99),
-            "p999_ms": q(0.999), "sustained_qps": len(lat) / max(last, submit_end), "submit_s": submit_end}
+            "p999_ms": q(0.999), "sustained_qps": len(lat) / max(last, submit_end), "submit_s": submit_end,
+            "warmup_s": warmup_s}
 
 
 def run_reference(args, world, rank):
