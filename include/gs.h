@@ -351,8 +351,9 @@ gs_status gs_stats_busy(gs_batch *const *bs, uint32_t nb, double *busy_ms);
  * Autotuning.  Times the captured pipeline on the given queries for each
  * lanes-per-work-item setting (4, 8, 16, 32: the lanes that share one
  * candidate vertex, edge-table key or partial embedding) and each number of
- * refinement rounds (none, 1, 2, 4), and keeps the fastest for batches created on
- * this graph afterwards.  Results never depend on these settings.  With
+ * refinement rounds (none, 1, 2, 4), then 4 or 8 lanes per partial embedding
+ * for the join alone, and keeps the fastest for batches created on this
+ * graph afterwards.  Results never depend on these settings.  With
  * cache_path != NULL the choice is read from / appended to that text file,
  * keyed by graph content hash, GPU name and a signature of the query load
  * (batch size class, mean k and m, bound fraction, mode).
@@ -363,11 +364,13 @@ typedef struct {
   double ms;               /* best time of one run of the given queries */
   uint32_t from_cache;     /* 1 if read from cache_path */
   uint32_t configs_tried;
+  uint32_t join_group;     /* lanes per partial row in the join */
+  uint32_t reserved;
 } gs_tuning;
 gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const gs_match_opts *opts, const char *cache_path,
                   gs_tuning *out);
 /* Set the tuned values by hand (0 = library default; refine_rounds may be
- * GS_ROUNDS_NONE). */
+ * GS_ROUNDS_NONE); the join takes the same lanes per work item. */
 gs_status gs_tune_set(gs_graph *g, uint32_t group, uint32_t refine_rounds);
 
 /* ------------------------------------------------------------------------

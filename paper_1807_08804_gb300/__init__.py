@@ -84,7 +84,7 @@ class KernelStats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("group", U32), ("refine_rounds", U32), ("ms", ctypes.c_double), ("from_cache", U32),
-                ("configs_tried", U32)]
+                ("configs_tried", U32), ("join_group", U32), ("reserved", U32)]
 
 
 class ServeOpts(ctypes.Structure):
@@ -616,15 +616,16 @@ class Batch:
 
 
 def tune(dg: DeviceGraph, queries, cap=1 << 20, mode=GS_ENUMERATE, cache_path: str | None = None) -> dict:
-    """Pick lanes per work item and refinement rounds for this graph and
-    query load (gs_tune); later batches on the graph use them."""
+    """Pick lanes per work item, the join's lanes per partial row and
+    refinement rounds for this graph and query load (gs_tune); later batches
+    on the graph use them."""
     pack = _QueryPack(queries)
     o = _opts(cap, mode)
     t = Tuning()
     _check(lib().gs_tune(dg._h, pack.arr, len(queries), ctypes.byref(o),
                          cache_path.encode() if cache_path else None, ctypes.byref(t)))
     return {"group": t.group, "refine_rounds": t.refine_rounds, "ms": t.ms, "from_cache": bool(t.from_cache),
-            "configs_tried": t.configs_tried}
+            "configs_tried": t.configs_tried, "join_group": t.join_group}
 
 
 def tune_set(dg: DeviceGraph, group: int = 0, refine_rounds: int = 0) -> None:

@@ -441,7 +441,7 @@ void enqueue_front(Pipe &P, int K) {
 void enqueue_back(Pipe &P, int K, int stop) {
   gs_batch *b = P.b;
   Wave &W = b->W;
-  const int sms = b->sms, grp = b->group;
+  const int sms = b->sms, grp = b->group, jgrp = b->jgroup ? b->jgroup : b->group;
   const uint64_t cps = W.G.nchunks;  // chunks per set: one candidate count per chunk
   P.begin(KK_COMPACT_ALL);
   launch_compact_count(W, 1, 0, P.cur, sms);
@@ -473,14 +473,14 @@ void enqueue_back(Pipe &P, int K, int stop) {
   P.end();
   for (int lvl = 0; lvl + 1 < K; ++lvl) {
     P.begin(KK_JOIN_COUNT);
-    launch_join_count(W, lvl, grp, P.cur, sms);
+    launch_join_count(W, lvl, jgrp, P.cur, sms);
     P.end();
     P.begin(KK_SCAN);
     scan_u32(W.row_cnt, W.row_scan, &W.ctrl->len[3], W.row_cap, b->scan_tmp, P.cur, sms);
     launch_level_alloc(W, lvl + 1, P.cur);
     P.end();
     P.begin(KK_JOIN_WRITE);
-    launch_join_write(W, lvl, grp, P.cur, sms);
+    launch_join_write(W, lvl, jgrp, P.cur, sms);
     P.end();
   }
   P.begin(KK_SORT);
@@ -858,13 +858,12 @@ gs_status batch_create(gs_graph *g, const gs_query *qs, uint32_t n, const gs_mat
   b->n_cap = std::max<uint32_t>(n, 1);
   opts_key(b, opts);
   if (g->tuned_group) b->group = g->tuned_group;
+  b->jgroup = (int)g->tuned_jgroup;
   if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds == GS_ROUNDS_NONE ? 0 : g->tuned_rounds;
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
     b->fixpoint = false;
   }
-  const char *env_g = getenv("GS_GROUP");
-  if (env_g) b->group = atoi(env_g);
   if (opts && opts->cuda_stream) {
     b->stream = static_cast<cudaStream_t>(opts->cuda_stream);
   } else {
@@ -927,6 +926,7 @@ gs_status batch_create_capacity(gs_graph *g, const gs_match_opts *opts, uint32_t
   b->n_cap = std::max<uint32_t>(n_cap, 1);
   opts_key(b, opts);
   if (g->tuned_group) b->group = g->tuned_group;
+  b->jgroup = (int)g->tuned_jgroup;
   if (g->tuned_rounds) b->refine_rounds = g->tuned_rounds == GS_ROUNDS_NONE ? 0 : g->tuned_rounds;
   if (opts && opts->max_refine_rounds) {
     b->refine_rounds = std::min<uint32_t>(opts->max_refine_rounds, kMaxRounds);
@@ -1281,6 +1281,7 @@ extern "C" gs_status gs_batch_set(gs_batch *b, int use_graph, int group, uint32_
   drop_graphs(b);
   b->use_graph = use_graph != 0;
   b->group = group;
+  b->jgroup = 0;
   if (refine_rounds == GS_ROUNDS_NONE) {
     b->refine_rounds = 0;
     b->fixpoint = false;

@@ -58,6 +58,7 @@ struct gs_batch {
   bool own_stream = false;
   int sms = 0;
   int group = 32;
+  int jgroup = 0;  // lanes per partial row in the join (0: the same as group)
   uint32_t refine_rounds = 8;
   bool fixpoint = true;            // loop rounds on the host until nothing changes (non-graph runs)
   bool use_graph = true;

@@ -88,6 +88,7 @@ struct gs_graph {
   void *khop;               // buffers of the domain-graph exploration
   uint32_t tuned_group;     // lanes per work item chosen by gs_tune (0 = default)
   uint32_t tuned_rounds;    // refinement rounds chosen by gs_tune (0 = default)
+  uint32_t tuned_jgroup;    // lanes per partial row in the join chosen by gs_tune (0 = tuned_group)
 };
 
 namespace gs {

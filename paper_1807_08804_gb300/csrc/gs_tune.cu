@@ -1,5 +1,6 @@
 // Autotuner: picks the lanes per work item (the "warps per vertex" of the
-// explore, refine, edge-table and join kernels: 4, 8, 16 or 32 lanes) and
+// explore, refine, edge-table and join kernels: 4, 8, 16 or 32 lanes; then,
+// for the join alone, 4 or 8 lanes per partial row when that is faster) and
 // the number of refinement rounds (none, 1, 2 or 4: Section 3.6 finds one
 // round the fastest refined variant, and exploration already prunes every
 // candidate against all its query edges) for a graph and a kind of query load, by
@@ -8,7 +9,7 @@
 // edge), so the choice is purely about speed.
 //
 // The choice is cached in a text file, one line per entry:
-//   <graph hash> <gpu name with '_' for spaces> <load signature> <group> <rounds> <ms>
+//   <graph hash> <gpu name with '_' for spaces> <load signature> <group> <rounds> <ms> <join group>
 // and reused by later gs_tune calls with the same key.  Batches created on
 // the graph afterwards use the tuned values.
 #include <cstdio>
@@ -53,7 +54,8 @@ uint64_t load_signature(const gs_query *qs, uint32_t n, const gs_match_opts *o) 
   return h;
 }
 
-bool cache_lookup(const char *path, const std::string &key, uint32_t *group, uint32_t *rounds, double *ms) {
+bool cache_lookup(const char *path, const std::string &key, uint32_t *group, uint32_t *rounds, double *ms,
+                  uint32_t *jgroup) {
   if (!path) return false;
   std::ifstream f(path);
   std::string line;
@@ -64,20 +66,24 @@ bool cache_lookup(const char *path, const std::string &key, uint32_t *group, uin
     uint32_t g, r;
     double t;
     if (!(is >> h >> gpu >> sig >> g >> r >> t)) continue;
+    uint32_t jg = 0;
+    if (!(is >> jg)) jg = 0;  // a line without a join group: the join follows the group
     if (h + " " + gpu + " " + sig == key) {
       *group = g;
       *rounds = r;
       *ms = t;
+      *jgroup = jg;
       found = true;  // the last line for a key wins
     }
   }
   return found;
 }
 
-void cache_store(const char *path, const std::string &key, uint32_t group, uint32_t rounds, double ms) {
+void cache_store(const char *path, const std::string &key, uint32_t group, uint32_t rounds, double ms,
+                 uint32_t jgroup) {
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << " " << group << " " << rounds << " " << ms << "\n";
+  f << key << " " << group << " " << rounds << " " << ms << " " << jgroup << "\n";
 }
 
 }  // namespace
@@ -92,15 +98,17 @@ extern "C" gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const 
   snprintf(sk, sizeof sk, "%016llx", (unsigned long long)load_signature(qs, n, opts));
   const std::string key = std::string(hk) + " " + gpu_name(g->device) + " " + sk;
   memset(out, 0, sizeof(*out));
-  uint32_t group = 0, rounds = 0;
+  uint32_t group = 0, rounds = 0, jgroup = 0;
   double best = 0;
-  if (cache_lookup(cache_path, key, &group, &rounds, &best)) {
+  if (cache_lookup(cache_path, key, &group, &rounds, &best, &jgroup)) {
     out->group = group;
     out->refine_rounds = rounds;
     out->ms = best;
     out->from_cache = 1;
+    out->join_group = jgroup ? jgroup : group;
     g->tuned_group = group;
     g->tuned_rounds = rounds;
+    g->tuned_jgroup = jgroup;
     return GS_OK;
   }
   gs_batch *b = nullptr;
@@ -113,23 +121,28 @@ extern "C" gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const 
   const uint32_t round_opts[] = {GS_ROUNDS_NONE, 1, 2, 4};
   best = 1e30;
   uint32_t tried = 0;
+  // the fastest of a few timed runs (the first run captures the graphs)
+  auto time_runs = [&](double &tmin) {
+    tmin = 1e30;
+    for (int rep = 0; rep < 4 && st == GS_OK; ++rep) {
+      cudaEventRecord(e0, b->stream);
+      st = run_waves(b);
+      cudaEventRecord(e1, b->stream);
+      if (st != GS_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(GS_ERR_CUDA, "tuning run failed"); break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tmin = std::min(tmin, (double)ms);
+    }
+    if (st == GS_OK) tried++;
+  };
   for (uint32_t gi : groups) {
     for (uint32_t r : round_opts) {
       st = gs_batch_set(b, 1, (int)gi, r);
       if (st != GS_OK) break;
-      double tmin = 1e30;
-      for (int rep = 0; rep < 4 && st == GS_OK; ++rep) {  // first run captures the graphs
-        cudaEventRecord(e0, b->stream);
-        st = run_waves(b);
-        cudaEventRecord(e1, b->stream);
-        if (st != GS_OK) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(GS_ERR_CUDA, "tuning run failed"); break; }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0) tmin = std::min(tmin, (double)ms);
-      }
+      double tmin;
+      time_runs(tmin);
       if (st != GS_OK) break;
-      tried++;
       if (tmin < best) {
         best = tmin;
         group = gi;
@@ -137,6 +150,23 @@ extern "C" gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const 
       }
     }
     if (st != GS_OK) break;
+  }
+  // then the join's own lanes (it often wants fewer than exploration and
+  // the edge tables), with the best refinement rounds
+  for (uint32_t gi : groups) {
+    for (uint32_t jg : {4u, 8u}) {
+      if (st != GS_OK || jg == gi) continue;
+      st = gs_batch_set(b, 1, (int)gi, rounds);
+      if (st != GS_OK) break;
+      b->jgroup = (int)jg;
+      double tmin;
+      time_runs(tmin);
+      if (st == GS_OK && tmin < best) {
+        best = tmin;
+        group = gi;
+        jgroup = jg;
+      }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -146,9 +176,11 @@ extern "C" gs_status gs_tune(gs_graph *g, const gs_query *qs, uint32_t n, const 
   out->refine_rounds = rounds;
   out->ms = best;
   out->configs_tried = tried;
+  out->join_group = jgroup ? jgroup : group;
   g->tuned_group = group;
   g->tuned_rounds = rounds;
-  cache_store(cache_path, key, group, rounds, best);
+  g->tuned_jgroup = jgroup;
+  cache_store(cache_path, key, group, rounds, best, jgroup);
   return GS_OK;
 }
 
@@ -160,5 +192,6 @@ extern "C" gs_status gs_tune_set(gs_graph *g, uint32_t group, uint32_t refine_ro
     return fail(GS_ERR_INVALID, "too many refinement rounds");
   g->tuned_group = group;
   g->tuned_rounds = refine_rounds;
+  g->tuned_jgroup = 0;
   return GS_OK;
 }

@@ -313,9 +313,10 @@ def test_autotuner_choice_is_cached_and_results_unchanged(small, tmp_path):
     cache = str(tmp_path / "tune.txt")
     t1 = gs.tune(dg, sub, cap=1 << 20, cache_path=cache)
     assert t1["group"] in (4, 8, 16, 32) and t1["refine_rounds"] in (gs.GS_ROUNDS_NONE, 1, 2, 4) and not t1["from_cache"]
-    assert t1["configs_tried"] == 16
+    assert t1["configs_tried"] == 22 and t1["join_group"] in (4, 8, 16, 32)
     t2 = gs.tune(dg, sub, cap=1 << 20, cache_path=cache)
-    assert t2["from_cache"] and (t2["group"], t2["refine_rounds"]) == (t1["group"], t1["refine_rounds"])
+    assert t2["from_cache"] and (t2["group"], t2["refine_rounds"], t2["join_group"]) == (
+        t1["group"], t1["refine_rounds"], t1["join_group"])
     b = gs.Batch(dg, sub, cap=1 << 20)  # built with the tuned settings
     b.run()
     b.finish()
