@@ -222,6 +222,7 @@ __device__ __forceinline__ uint64_t row_hash(const DQuery &Q, const uint32_t *ro
 // form the visit order; each newly covered vertex hangs below the vertex that
 // covered it (the spanning tree T).
 __global__ void k_plan(Wave W, const uint32_t *type_count) {
+  gdc_wait();
   const WaveDesc D = W.waves[W.ctrl->wave];
   for (uint64_t qi = gtid(); qi <= W.nq; qi += gthreads()) {
     DQuery &Q = W.dq[qi];
@@ -386,6 +387,7 @@ __device__ __forceinline__ void word_or(const Wave &W, uint32_t *slot, uint32_t 
 }
 
 __global__ void __launch_bounds__(kThreads) k_filter(Wave W) {
+  gdc_wait();
   const DevGraph &G = W.G;
   auto warp = cg::tiled_partition<32>(cg::this_thread_block());
   const uint32_t lane = threadIdx.x & 31;
@@ -582,6 +584,7 @@ __device__ __forceinline__ uint32_t l1_word(const DevGraph &G, const uint32_t *s
 // per level-2 word appends its set bits with one atomic; the order of the
 // list does not matter (positions come from the scan of the counts).
 __global__ void __launch_bounds__(kThreads) k_chunk_list(Wave W, int mode, uint32_t step) {
+  gdc_wait();
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
@@ -610,6 +613,7 @@ __global__ void __launch_bounds__(kThreads) k_chunk_list(Wave W, int mode, uint3
 // owns level-1 word j and counts its level-0 words; the level-1 words of kCU
 // chunks are loaded together.
 __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W) {
+  gdc_wait();
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
@@ -647,6 +651,7 @@ __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W) {
 // the lanes before it.
 __global__ void __launch_bounds__(kThreads) k_compact_write(Wave W, int mode, const uint64_t *scan, uint32_t *dst,
                                                              uint32_t *owner, uint64_t dst_cap, int hw_slot) {
+  gdc_wait();
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
@@ -804,6 +809,7 @@ __device__ __forceinline__ void explore_item(const cg::thread_block_tile<G> &til
 // grid waits for them.
 template <int G>
 __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) {
+  gdc_wait();
   const auto warp = cg::tiled_partition<32>(cg::this_thread_block());
   const auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const DevGraph &Gr = W.G;
@@ -844,6 +850,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
 // refine_low incident edges) neither refined nor used to refine.
 template <int G>
 __global__ void __launch_bounds__(kThreads, 6) k_refine(Wave W, uint32_t round, uint32_t sub) {
+  gdc_wait();
   if (round > 0 && W.ctrl->changed[round - 1] == 0) return;
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const DevGraph &Gr = W.G;
@@ -898,6 +905,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_refine(Wave W, uint32_t round, 
 // Final candidate lists: offsets and lengths per query vertex; a query with
 // an empty set has no embedding.
 __global__ void k_list_table(Wave W) {
+  gdc_wait();
   const uint32_t ipg = W.G.nchunks;
   for (uint64_t g = gtid(); g < W.nqv; g += gthreads()) {
     uint64_t b = W.cscan[g * ipg], e = W.cscan[(g + 1) * ipg];
@@ -915,6 +923,7 @@ __global__ void k_list_table(Wave W) {
 // query edge is oriented from its earlier-joined endpoint, whose candidates
 // key its candidate-edge table.
 __global__ void k_join_plan(Wave W) {
+  gdc_wait();
   for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
     DQuery &Q = W.dq[qi];
     const bool ok = Q.status == QS_OK;
@@ -960,6 +969,7 @@ __global__ void k_join_plan(Wave W) {
 // candidates of the other endpoint y, ascending.
 template <int G, bool WRITE>
 __global__ void __launch_bounds__(kThreads) k_ec(Wave W) {
+  gdc_wait();
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const DevGraph &Gr = W.G;
   const uint32_t r = tile.thread_rank();
@@ -1016,6 +1026,7 @@ __global__ void __launch_bounds__(kThreads) k_ec(Wave W) {
 // and words flagged at level 1 are visited), so the slots are clean for the
 // next run.
 __global__ void __launch_bounds__(kThreads) k_clear(Wave W) {
+  gdc_wait();
   const DevGraph &G = W.G;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
@@ -1046,6 +1057,7 @@ __global__ void __launch_bounds__(kThreads) k_clear(Wave W) {
 // Queries whose edge-table keys would pass the capacity are sent to the
 // fallback path; the item count is clamped so no kernel reads past it.
 __global__ void k_ec_limit(Wave W) {
+  gdc_wait();
   const uint64_t total = W.ec_key_base[W.nqe];
   for (uint64_t ge = gtid(); ge < W.nqe; ge += gthreads())
     if (W.ec_key_base[ge + 1] > W.ec_items_cap && W.ec_key_base[ge + 1] > W.ec_key_base[ge])
@@ -1061,6 +1073,7 @@ __global__ void k_ec_limit(Wave W) {
 // block.  The wave index advances in the epilogue, so replaying the same
 // captured graph runs the waves in order.
 __global__ void k_prologue(Wave W) {
+  gdc_wait();
   const WaveDesc D = W.waves[W.ctrl->wave];
   const uint64_t words = sizeof(DQuery) / 4;
   const uint32_t *src = reinterpret_cast<const uint32_t *>(W.all_dq + D.q0);
@@ -1085,6 +1098,7 @@ __global__ void k_prologue(Wave W) {
 // Owner tables of the wave's query vertices and edges (after the plan has
 // rebased each slot's vertex and edge ranges).
 __global__ void k_owners(Wave W) {
+  gdc_wait();
   for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
     const DQuery &Q = W.dq[qi];
     W.fcnt[qi] = filter_items(W.G, Q);
@@ -1097,6 +1111,7 @@ __global__ void k_owners(Wave W) {
 // ============================================================ join
 // Level 0: the candidates of join[0] are the first partial embeddings.
 __global__ void k_join0_rows(Wave W) {
+  gdc_wait();
   for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
     const DQuery &Q = W.dq[qi];
     QState &S = W.qs[qi];
@@ -1142,6 +1157,7 @@ __device__ __forceinline__ void level_sizes(const Wave &W, uint32_t qi, uint32_t
 // pass also the rows produced per query (from the scan of the per-row
 // counts), and the current level kept aside as the source of the write pass.
 __global__ void k_level_sizes(Wave W, uint32_t lvl) {
+  gdc_wait();
   for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
     if (lvl > 0) {
       QState &S = W.qs[qi];
@@ -1163,6 +1179,7 @@ __global__ void k_level_sizes(Wave W, uint32_t lvl) {
 // (QS_OVERFLOW) each query that would pass a pool's end, the second assigns
 // the places of the others.
 __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
+  gdc_wait();
   __shared__ uint64_t sm[4][32];
   __shared__ uint64_t carry[4];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1250,6 +1267,7 @@ __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
 
 // Level-0 rows (final rows when k == 1), one block per query.
 __global__ void k_join0_write(Wave W) {
+  gdc_wait();
   for (uint64_t qi = blockIdx.x; qi < W.nq; qi += gridDim.x) {
     const DQuery &Q = W.dq[qi];
     QState &S = W.qs[qi];
@@ -1332,6 +1350,7 @@ __device__ __forceinline__ uint32_t seg_of_src(const SrcRows *src, uint32_t nq, 
 // embeddings and their hashes to its count and fingerprint here.
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_join_count(Wave W, uint32_t s) {
+  gdc_wait();
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const uint32_t r = tile.thread_rank();
   const uint64_t ntile = gthreads() / G;
@@ -1396,6 +1415,7 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Wave W, uint32_t s) {
 // Write pass of level s -> s+1 into the layout made by k_level_alloc.
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_join_write(Wave W, uint32_t s) {
+  gdc_wait();
   auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const uint32_t r = tile.thread_rank();
   const uint64_t ntile = gthreads() / G;
@@ -1452,6 +1472,7 @@ __global__ void __launch_bounds__(kThreads) k_join_write(Wave W, uint32_t s) {
 __device__ __forceinline__ bool small_output(const DQuery &, const QState &S) { return S.out_rows <= kSmallRows; }
 
 __global__ void __launch_bounds__(1024) k_final_bases(Wave W) {
+  gdc_wait();
   __shared__ uint64_t sm[4][32];
   __shared__ uint64_t carry[4];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1651,6 +1672,7 @@ __device__ __forceinline__ uint32_t block_scan_excl(uint32_t *v, uint32_t n) {
 // the first row of each run of equal projected tuples (its rank among the
 // runs from a block scan) and writes the first `cap` of them.
 __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
+  gdc_wait();
   __shared__ uint64_t key[kSmallRows];
   __shared__ uint64_t key2[kSmallRows];  // the columns from the first one key does not hold whole
   __shared__ uint32_t idx[kSmallRows];
@@ -1739,6 +1761,7 @@ __global__ void __launch_bounds__(256) k_small_sort(Wave W) {
 // shared memory with coalesced loads (rows are contiguous there), then each
 // lane builds its row's key from shared memory.
 __global__ void __launch_bounds__(256) k_sort_keys(Wave W, uint32_t *perm, SortKey *keys) {
+  gdc_wait();
   __shared__ uint32_t stage[256 / 32][32 * kMaxK];
   const uint64_t n = W.ctrl->len[6];
   const uint32_t b = W.G.idbits, lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1816,6 +1839,7 @@ __device__ __forceinline__ void sel_finish(SelState &s) {
 }
 
 __global__ void k_sel_start(Wave W) {
+  gdc_wait();
   for (uint64_t qi = gtid(); qi < W.nq; qi += gthreads()) {
     SelState &s = W.sel[qi];
     if (s.state != 1) continue;
@@ -1841,6 +1865,7 @@ __device__ __forceinline__ bool sel_in_play(const SelState &s, uint64_t key) {
 // one query's, so counts gather in shared memory for the block's first
 // query and go to global memory directly for any other.
 __global__ void __launch_bounds__(256) k_sel_hist(Wave W, const SortKey *keys) {
+  gdc_wait();
   __shared__ uint32_t h[256];
   const uint64_t n = W.ctrl->len[6];
   const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
@@ -1868,6 +1893,7 @@ __global__ void __launch_bounds__(256) k_sel_hist(Wave W, const SortKey *keys) {
 
 // Choose the bucket holding the need-th key; one warp per query.
 __global__ void k_sel_pick(Wave W, int last) {
+  gdc_wait();
   const uint32_t lane = threadIdx.x & 31;
   for (uint64_t qi = gtid() / 32; qi < W.nq; qi += gthreads() / 32) {
     SelState &s = W.sel[qi];
@@ -1929,6 +1955,7 @@ __global__ void k_sel_pick(Wave W, int last) {
 // (order does not matter: the sort follows); other rows are copied as they
 // are.  One atomic per warp and query.
 __global__ void k_sel_compact(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout) {
+  gdc_wait();
   const uint64_t n = W.ctrl->len[6];
   const uint32_t lane = threadIdx.x & 31;
   uint64_t acc = 0;
@@ -1964,6 +1991,7 @@ __global__ void k_sel_compact(Wave W, const uint32_t *pin, const SortKey *kin, u
 
 // Rows entering the sort and the tile layout after the cut.
 __global__ void __launch_bounds__(1024) k_sort_bases(Wave W) {
+  gdc_wait();
   __shared__ uint64_t sm[32];
   __shared__ uint64_t carry;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -2006,6 +2034,7 @@ __global__ void __launch_bounds__(1024) k_sort_bases(Wave W) {
 // order equal keys.
 __global__ void __launch_bounds__(256) k_tile_sort(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout,
                                                    SortKey *kout) {
+  gdc_wait();
   __shared__ SortKey key[kTileRows];
   __shared__ uint32_t row[kTileRows];
   __shared__ uint32_t idx[kTileRows];
@@ -2102,6 +2131,7 @@ __device__ __forceinline__ uint64_t merge_split_at(const Wave &W, const DQuery &
 
 // Split of every active output tile at its first output.  One thread per tile.
 __global__ void k_merge_split(Wave W, const uint32_t *perm, const SortKey *key, uint64_t run) {
+  gdc_wait();
   if (!W.ctrl->bkt_fail) return;
   const uint64_t ntiles = W.ctrl->len[7];
   for (uint64_t t = gtid(); t < ntiles; t += gthreads()) {
@@ -2124,6 +2154,7 @@ __global__ void k_merge_split(Wave W, const uint32_t *perm, const SortKey *key, 
 // the slices.
 __global__ void __launch_bounds__(256) k_merge_tiles(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout,
                                                      SortKey *kout, uint64_t run) {
+  gdc_wait();
   __shared__ SortKey sk[kTileRows];
   __shared__ uint32_t si[kTileRows];
   __shared__ uint64_t s_end;
@@ -2364,6 +2395,7 @@ __device__ __forceinline__ uint64_t bkt_base(const QState &S) { return kBktPerTi
 // (b = 1 .. nb - 1) with their second keys.  Also clears every query's
 // overflow flag and sets the number of bucket slots (kBktPerTile per tile).
 __global__ void __launch_bounds__(1024) k_bkt_split(Wave W, const uint32_t *pin, const SortKey *kin) {
+  gdc_wait();
   extern __shared__ __align__(16) uint8_t bkt_smem[];
   const SmemEnts e = carve_ents(bkt_smem, kBktSampleMax);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -2419,6 +2451,7 @@ __global__ void __launch_bounds__(1024) k_bkt_split(Wave W, const uint32_t *pin,
 // second key is built only when its first key equals a splitter's.
 __global__ void __launch_bounds__(256) k_bkt_place(Wave W, const uint32_t *pin, const SortKey *kin, uint32_t *pout,
                                                    SortKey *kout, int scatter) {
+  gdc_wait();
   __shared__ uint64_t ssh[kBktSmemSpl];
   if (W.merge_only) return;
   const uint64_t nt = W.ctrl->len[7];
@@ -2490,6 +2523,7 @@ __global__ void __launch_bounds__(256) k_bkt_place(Wave W, const uint32_t *pin, 
 // cursor for the scatter pass; a bucket above kBktCap entries sends its
 // query to the merge path.
 __global__ void k_bkt_bases(Wave W) {
+  gdc_wait();
   const uint64_t nt = W.ctrl->nbkt;
   for (uint64_t t = gtid(); t < nt; t += gthreads()) {
     const uint32_t qi = seg_of_large(W.qs, W.nq, t / kBktPerTile, true);
@@ -2510,6 +2544,7 @@ __global__ void k_bkt_bases(Wave W) {
 template <uint32_t LO, uint32_t CAP>
 __global__ void k_bkt_sort(Wave W, const uint32_t *px, const SortKey *kx, uint32_t *p0, SortKey *k0, uint32_t *p1,
                            SortKey *k1) {
+  gdc_wait();
   extern __shared__ __align__(16) uint8_t bkt_smem[];
   const SmemEnts e = carve_ents(bkt_smem, CAP);
   const uint64_t nt = W.ctrl->nbkt;
@@ -2545,6 +2580,7 @@ __global__ void k_bkt_sort(Wave W, const uint32_t *px, const SortKey *kx, uint32
 // Sorted large rows in query-vertex column order, laid out query by query:
 // the first cap rows of each query, from the buffer its last pass wrote.
 __global__ void k_gather(Wave W, const uint32_t *perm0, const uint32_t *perm1) {
+  gdc_wait();
   const uint64_t n = W.ctrl->len[6];
   uint64_t acc = 0;
   for (uint64_t i = gtid(); i < n; i += gthreads()) {
@@ -2575,6 +2611,7 @@ __device__ __forceinline__ bool proj_start(const Wave &W, const DQuery &Q, const
 
 __global__ void __launch_bounds__(256) k_proj_count(Wave W, const uint32_t *perm0, const uint32_t *perm1,
                                                     const SortKey *key0, const SortKey *key1) {
+  gdc_wait();
   __shared__ uint32_t wsum[8];
   const uint64_t ntiles = W.ctrl->len[7];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -2603,6 +2640,7 @@ __global__ void __launch_bounds__(256) k_proj_count(Wave W, const uint32_t *perm
 
 __global__ void __launch_bounds__(256) k_proj_write(Wave W, const uint32_t *perm0, const uint32_t *perm1,
                                                     const SortKey *key0, const SortKey *key1) {
+  gdc_wait();
   __shared__ uint32_t rk[kTileRows];
   const uint64_t ntiles = W.ctrl->len[7];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -2638,6 +2676,7 @@ __global__ void __launch_bounds__(256) k_proj_write(Wave W, const uint32_t *perm
 
 // Epilogue: per-query results and rows of this wave into the batch store.
 __global__ void k_epilogue_copy(Wave W) {
+  gdc_wait();
   const WaveDesc D = W.waves[W.ctrl->wave];
   const uint64_t top = W.ctrl->store_top, words = W.ctrl->fin_words;
   const bool fits = top + words <= W.bo.store_cap;
@@ -2660,6 +2699,7 @@ __global__ void k_epilogue_copy(Wave W) {
 }
 
 __global__ void k_epilogue_advance(Wave W) {
+  gdc_wait();
   const uint64_t top = W.ctrl->store_top, words = W.ctrl->fin_words;
   if (top + words > W.ctrl->hw[HW_STORE]) W.ctrl->hw[HW_STORE] = top + words;
   if (top + words <= W.bo.store_cap) W.ctrl->store_top = top + words;
@@ -2708,102 +2748,102 @@ inline unsigned blocks_for(uint64_t n, unsigned per) {
 
 // ------------------------------------------------------------ launchers
 void launch_prologue(const Wave &W, cudaStream_t s, int sms) {
-  k_prologue<<<grid_for(sms, 2), kThreads, 0, s>>>(W);
+  pdl(k_prologue, grid_for(sms, 2), kThreads, 0, s, W);
 }
 void launch_plan(const Wave &W, const uint32_t *type_count, cudaStream_t s, int sms) {
-  k_plan<<<blocks_for(W.nq + 1, 128), 128, 0, s>>>(W, type_count);
-  k_owners<<<blocks_for(W.nq, 128), 128, 0, s>>>(W);
+  pdl(k_plan, blocks_for(W.nq + 1, 128), 128, 0, s, W, type_count);
+  pdl(k_owners, blocks_for(W.nq, 128), 128, 0, s, W);
 }
 void launch_filter(const Wave &W, cudaStream_t s, int sms) {
-  k_filter<<<grid_items(k_filter, (uint64_t)W.nq * W.G.W1, sms), kThreads, 0, s>>>(W);
+  pdl(k_filter, grid_items(k_filter, (uint64_t)W.nq * W.G.W1, sms), kThreads, 0, s, W);
 }
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms) {
   const uint64_t sets = mode == 0 ? W.nq : W.nqv;
   cudaMemsetAsync(&W.ctrl->len[9], 0, sizeof(uint64_t), s);
-  k_chunk_list<<<grid_items(k_chunk_list, sets * W.G.ipg, sms), kThreads, 0, s>>>(W, mode, step);
-  k_compact_count<<<persistent_grid(k_compact_count, sms), kThreads, 0, s>>>(W);
+  pdl(k_chunk_list, grid_items(k_chunk_list, sets * W.G.ipg, sms), kThreads, 0, s, W, mode, step);
+  pdl(k_compact_count, persistent_grid(k_compact_count, sms), kThreads, 0, s, W);
 }
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint32_t *owner,
                           uint64_t cap, int hw_slot, cudaStream_t s, int sms) {
-  k_compact_write<<<persistent_grid(k_compact_write, sms), kThreads, 0, s>>>(W, mode, scan, dst, owner, cap, hw_slot);
+  pdl(k_compact_write, persistent_grid(k_compact_write, sms), kThreads, 0, s, W, mode, scan, dst, owner, cap, hw_slot);
 }
 void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms) {
   switch (group) {
-    case 4: k_explore<4><<<persistent_grid(k_explore<4>, sms), kThreads, 0, s>>>(W, step); break;
-    case 8: k_explore<8><<<persistent_grid(k_explore<8>, sms), kThreads, 0, s>>>(W, step); break;
-    case 16: k_explore<16><<<persistent_grid(k_explore<16>, sms), kThreads, 0, s>>>(W, step); break;
-    default: k_explore<32><<<persistent_grid(k_explore<32>, sms), kThreads, 0, s>>>(W, step); break;
+    case 4: pdl(k_explore<4>, persistent_grid(k_explore<4>, sms), kThreads, 0, s, W, step); break;
+    case 8: pdl(k_explore<8>, persistent_grid(k_explore<8>, sms), kThreads, 0, s, W, step); break;
+    case 16: pdl(k_explore<16>, persistent_grid(k_explore<16>, sms), kThreads, 0, s, W, step); break;
+    default: pdl(k_explore<32>, persistent_grid(k_explore<32>, sms), kThreads, 0, s, W, step); break;
   }
 }
 void launch_refine(const Wave &W, uint32_t round, uint32_t sub, int group, cudaStream_t s, int sms) {
   switch (group) {
-    case 4: k_refine<4><<<persistent_grid(k_refine<4>, sms), kThreads, 0, s>>>(W, round, sub); break;
-    case 8: k_refine<8><<<persistent_grid(k_refine<8>, sms), kThreads, 0, s>>>(W, round, sub); break;
-    case 16: k_refine<16><<<persistent_grid(k_refine<16>, sms), kThreads, 0, s>>>(W, round, sub); break;
-    default: k_refine<32><<<persistent_grid(k_refine<32>, sms), kThreads, 0, s>>>(W, round, sub); break;
+    case 4: pdl(k_refine<4>, persistent_grid(k_refine<4>, sms), kThreads, 0, s, W, round, sub); break;
+    case 8: pdl(k_refine<8>, persistent_grid(k_refine<8>, sms), kThreads, 0, s, W, round, sub); break;
+    case 16: pdl(k_refine<16>, persistent_grid(k_refine<16>, sms), kThreads, 0, s, W, round, sub); break;
+    default: pdl(k_refine<32>, persistent_grid(k_refine<32>, sms), kThreads, 0, s, W, round, sub); break;
   }
 }
 void launch_list_table(const Wave &W, cudaStream_t s, int sms) {
-  k_list_table<<<blocks_for(W.nqv, kThreads), kThreads, 0, s>>>(W);
+  pdl(k_list_table, blocks_for(W.nqv, kThreads), kThreads, 0, s, W);
 }
-void launch_join_plan(const Wave &W, cudaStream_t s, int sms) { k_join_plan<<<blocks_for(W.nq, 64), 64, 0, s>>>(W); }
+void launch_join_plan(const Wave &W, cudaStream_t s, int sms) { pdl(k_join_plan, blocks_for(W.nq, 64), 64, 0, s, W); }
 void launch_ec_limit(const Wave &W, cudaStream_t s, int sms) {
-  k_ec_limit<<<blocks_for(W.nqe, kThreads), kThreads, 0, s>>>(W);
+  pdl(k_ec_limit, blocks_for(W.nqe, kThreads), kThreads, 0, s, W);
 }
 void launch_ec(const Wave &W, bool write, int group, cudaStream_t s, int sms) {
   switch (group) {
-    case 4: if (write) k_ec<4, true><<<persistent_grid(k_ec<4, true>, sms), kThreads, 0, s>>>(W); else k_ec<4, false><<<persistent_grid(k_ec<4, false>, sms), kThreads, 0, s>>>(W); break;
-    case 8: if (write) k_ec<8, true><<<persistent_grid(k_ec<8, true>, sms), kThreads, 0, s>>>(W); else k_ec<8, false><<<persistent_grid(k_ec<8, false>, sms), kThreads, 0, s>>>(W); break;
-    case 16: if (write) k_ec<16, true><<<persistent_grid(k_ec<16, true>, sms), kThreads, 0, s>>>(W); else k_ec<16, false><<<persistent_grid(k_ec<16, false>, sms), kThreads, 0, s>>>(W); break;
-    default: if (write) k_ec<32, true><<<persistent_grid(k_ec<32, true>, sms), kThreads, 0, s>>>(W); else k_ec<32, false><<<persistent_grid(k_ec<32, false>, sms), kThreads, 0, s>>>(W); break;
+    case 4: if (write) pdl(k_ec<4, true>, persistent_grid(k_ec<4, true>, sms), kThreads, 0, s, W); else pdl(k_ec<4, false>, persistent_grid(k_ec<4, false>, sms), kThreads, 0, s, W); break;
+    case 8: if (write) pdl(k_ec<8, true>, persistent_grid(k_ec<8, true>, sms), kThreads, 0, s, W); else pdl(k_ec<8, false>, persistent_grid(k_ec<8, false>, sms), kThreads, 0, s, W); break;
+    case 16: if (write) pdl(k_ec<16, true>, persistent_grid(k_ec<16, true>, sms), kThreads, 0, s, W); else pdl(k_ec<16, false>, persistent_grid(k_ec<16, false>, sms), kThreads, 0, s, W); break;
+    default: if (write) pdl(k_ec<32, true>, persistent_grid(k_ec<32, true>, sms), kThreads, 0, s, W); else pdl(k_ec<32, false>, persistent_grid(k_ec<32, false>, sms), kThreads, 0, s, W); break;
   }
 }
 void launch_clear(const Wave &W, cudaStream_t s, int sms) {
-  k_clear<<<grid_items(k_clear, (uint64_t)W.nqv * W.G.ipg, sms), kThreads, 0, s>>>(W);
+  pdl(k_clear, grid_items(k_clear, (uint64_t)W.nqv * W.G.ipg, sms), kThreads, 0, s, W);
 }
 void launch_join0(const Wave &W, cudaStream_t s, int sms) {
-  k_join0_rows<<<blocks_for(W.nq, 256), 256, 0, s>>>(W);
-  k_level_sizes<<<blocks_for(W.nq, kThreads), kThreads, 0, s>>>(W, 0);
-  k_level_alloc<<<1, 1024, 0, s>>>(W, 0);
-  k_join0_write<<<persistent_grid(k_join0_write, sms), kThreads, 0, s>>>(W);
+  pdl(k_join0_rows, blocks_for(W.nq, 256), 256, 0, s, W);
+  pdl(k_level_sizes, blocks_for(W.nq, kThreads), kThreads, 0, s, W, 0);
+  pdl(k_level_alloc, 1, 1024, 0, s, W, 0);
+  pdl(k_join0_write, persistent_grid(k_join0_write, sms), kThreads, 0, s, W);
 }
 void launch_join_count(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms) {
   switch (group) {
-    case 4: k_join_count<4><<<persistent_grid(k_join_count<4>, sms), kThreads, 0, s>>>(W, lvl); break;
-    case 8: k_join_count<8><<<persistent_grid(k_join_count<8>, sms), kThreads, 0, s>>>(W, lvl); break;
-    case 16: k_join_count<16><<<persistent_grid(k_join_count<16>, sms), kThreads, 0, s>>>(W, lvl); break;
-    default: k_join_count<32><<<persistent_grid(k_join_count<32>, sms), kThreads, 0, s>>>(W, lvl); break;
+    case 4: pdl(k_join_count<4>, persistent_grid(k_join_count<4>, sms), kThreads, 0, s, W, lvl); break;
+    case 8: pdl(k_join_count<8>, persistent_grid(k_join_count<8>, sms), kThreads, 0, s, W, lvl); break;
+    case 16: pdl(k_join_count<16>, persistent_grid(k_join_count<16>, sms), kThreads, 0, s, W, lvl); break;
+    default: pdl(k_join_count<32>, persistent_grid(k_join_count<32>, sms), kThreads, 0, s, W, lvl); break;
   }
 }
 void launch_level_alloc(const Wave &W, uint32_t lvl, cudaStream_t s) {
-  k_level_sizes<<<blocks_for(W.nq, kThreads), kThreads, 0, s>>>(W, lvl);
-  k_level_alloc<<<1, 1024, 0, s>>>(W, lvl);
+  pdl(k_level_sizes, blocks_for(W.nq, kThreads), kThreads, 0, s, W, lvl);
+  pdl(k_level_alloc, 1, 1024, 0, s, W, lvl);
 }
 void launch_join_write(const Wave &W, uint32_t lvl, int group, cudaStream_t s, int sms) {
   switch (group) {
-    case 4: k_join_write<4><<<persistent_grid(k_join_write<4>, sms), kThreads, 0, s>>>(W, lvl); break;
-    case 8: k_join_write<8><<<persistent_grid(k_join_write<8>, sms), kThreads, 0, s>>>(W, lvl); break;
-    case 16: k_join_write<16><<<persistent_grid(k_join_write<16>, sms), kThreads, 0, s>>>(W, lvl); break;
-    default: k_join_write<32><<<persistent_grid(k_join_write<32>, sms), kThreads, 0, s>>>(W, lvl); break;
+    case 4: pdl(k_join_write<4>, persistent_grid(k_join_write<4>, sms), kThreads, 0, s, W, lvl); break;
+    case 8: pdl(k_join_write<8>, persistent_grid(k_join_write<8>, sms), kThreads, 0, s, W, lvl); break;
+    case 16: pdl(k_join_write<16>, persistent_grid(k_join_write<16>, sms), kThreads, 0, s, W, lvl); break;
+    default: pdl(k_join_write<32>, persistent_grid(k_join_write<32>, sms), kThreads, 0, s, W, lvl); break;
   }
 }
-void launch_final_bases(const Wave &W, cudaStream_t s) { k_final_bases<<<1, 1024, 0, s>>>(W); }
+void launch_final_bases(const Wave &W, cudaStream_t s) { pdl(k_final_bases, 1, 1024, 0, s, W); }
 void launch_small_sort(const Wave &W, cudaStream_t s, int sms) {
   const unsigned cap = persistent_grid(k_small_sort, sms, 256);
-  k_small_sort<<<W.nq < cap ? (W.nq ? W.nq : 1) : cap, 256, 0, s>>>(W);
+  pdl(k_small_sort, W.nq < cap ? (W.nq ? W.nq : 1) : cap, 256, 0, s, W);
 }
 void launch_sort_keys(const Wave &W, uint32_t *perm, SortKey *keys, cudaStream_t s, int sms) {
-  k_sort_keys<<<persistent_grid(k_sort_keys, sms), kThreads, 0, s>>>(W, perm, keys);
+  pdl(k_sort_keys, persistent_grid(k_sort_keys, sms), kThreads, 0, s, W, perm, keys);
 }
 void launch_select(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                    cudaStream_t s, int sms) {
-  k_sel_start<<<blocks_for(W.nq, 256), 256, 0, s>>>(W);
+  pdl(k_sel_start, blocks_for(W.nq, 256), 256, 0, s, W);
   for (int r = 0; r < kSelRounds; ++r) {
-    k_sel_hist<<<persistent_grid(k_sel_hist, sms, 256), 256, 0, s>>>(W, kin);
-    k_sel_pick<<<blocks_for((uint64_t)W.nq * 32, 256), 256, 0, s>>>(W, r == kSelRounds - 1);
+    pdl(k_sel_hist, persistent_grid(k_sel_hist, sms, 256), 256, 0, s, W, kin);
+    pdl(k_sel_pick, blocks_for((uint64_t)W.nq * 32, 256), 256, 0, s, W, r == kSelRounds - 1);
   }
-  k_sel_compact<<<persistent_grid(k_sel_compact, sms), kThreads, 0, s>>>(W, pin, kin, pout, kout);
-  k_sort_bases<<<1, 1024, 0, s>>>(W);
+  pdl(k_sel_compact, persistent_grid(k_sel_compact, sms), kThreads, 0, s, W, pin, kin, pout, kout);
+  pdl(k_sort_bases, 1, 1024, 0, s, W);
 }
 void launch_bucket_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *px, SortKey *kx,
                         uint32_t *p0, SortKey *k0, uint32_t *p1, SortKey *k1, uint64_t *scan_tmp, cudaStream_t s,
@@ -2820,42 +2860,40 @@ void launch_bucket_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, 
   (void)attrs;
   const uint64_t slots = kBktPerTile * (W.out_rows_cap / kTileRows + W.nq + 1);
   cudaMemsetAsync(W.ptcount, 0, 4 * slots, s);
-  k_bkt_split<<<std::max(1u, std::min<unsigned>(W.nq, (unsigned)sms * 2)), 1024, split_smem, s>>>(W, pin, kin);
+  pdl(k_bkt_split, std::max(1u, std::min<unsigned>(W.nq, (unsigned)sms * 2)), 1024, split_smem, s, W, pin, kin);
   const unsigned place = persistent_grid(k_bkt_place, sms);
-  k_bkt_place<<<place, kThreads, 0, s>>>(W, pin, kin, px, kx, 0);
+  pdl(k_bkt_place, place, kThreads, 0, s, W, pin, kin, px, kx, 0);
   scan_u32(W.ptcount, W.ptscan, &W.ctrl->nbkt, slots, scan_tmp, s, sms);
-  k_bkt_bases<<<persistent_grid(k_bkt_bases, sms), kThreads, 0, s>>>(W);
-  k_bkt_place<<<place, kThreads, 0, s>>>(W, pin, kin, px, kx, 1);
-  k_bkt_sort<0, kBktSmall><<<persistent_grid(k_bkt_sort<0, kBktSmall>, sms, 256, small_smem), 256, small_smem, s>>>(
+  pdl(k_bkt_bases, persistent_grid(k_bkt_bases, sms), kThreads, 0, s, W);
+  pdl(k_bkt_place, place, kThreads, 0, s, W, pin, kin, px, kx, 1);
+  pdl(k_bkt_sort<0, kBktSmall>, persistent_grid(k_bkt_sort<0, kBktSmall>, sms, 256, small_smem), 256, small_smem, s, 
       W, px, kx, p0, k0, p1, k1);
-  k_bkt_sort<kBktSmall, kBktMid><<<persistent_grid(k_bkt_sort<kBktSmall, kBktMid>, sms, 256, mid_smem), 256, mid_smem,
-                                   s>>>(W, px, kx, p0, k0, p1, k1);
-  k_bkt_sort<kBktMid, kBktCap><<<persistent_grid(k_bkt_sort<kBktMid, kBktCap>, sms, 1024, big_smem), 1024,
-                                 big_smem, s>>>(W, px, kx, p0, k0, p1, k1);
+  pdl(k_bkt_sort<kBktSmall, kBktMid>, persistent_grid(k_bkt_sort<kBktSmall, kBktMid>, sms, 256, mid_smem), 256, mid_smem, s, W, px, kx, p0, k0, p1, k1);
+  pdl(k_bkt_sort<kBktMid, kBktCap>, persistent_grid(k_bkt_sort<kBktMid, kBktCap>, sms, 1024, big_smem), 1024, big_smem, s, W, px, kx, p0, k0, p1, k1);
 }
 void launch_tile_sort(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                       cudaStream_t s, int sms) {
-  k_tile_sort<<<persistent_grid(k_tile_sort, sms, 256), 256, 0, s>>>(W, pin, kin, pout, kout);
+  pdl(k_tile_sort, persistent_grid(k_tile_sort, sms, 256), 256, 0, s, W, pin, kin, pout, kout);
 }
 void launch_merge_pass(const Wave &W, const uint32_t *pin, const SortKey *kin, uint32_t *pout, SortKey *kout,
                        uint64_t run, cudaStream_t s, int sms) {
-  k_merge_split<<<persistent_grid(k_merge_split, sms), kThreads, 0, s>>>(W, pin, kin, run);
-  k_merge_tiles<<<persistent_grid(k_merge_tiles, sms, 256), 256, 0, s>>>(W, pin, kin, pout, kout, run);
+  pdl(k_merge_split, persistent_grid(k_merge_split, sms), kThreads, 0, s, W, pin, kin, run);
+  pdl(k_merge_tiles, persistent_grid(k_merge_tiles, sms, 256), 256, 0, s, W, pin, kin, pout, kout, run);
 }
 void launch_gather(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, cudaStream_t s, int sms) {
-  k_gather<<<persistent_grid(k_gather, sms), kThreads, 0, s>>>(W, perm0, perm1);
+  pdl(k_gather, persistent_grid(k_gather, sms), kThreads, 0, s, W, perm0, perm1);
 }
 
 void launch_project(const Wave &W, const uint32_t *perm0, const uint32_t *perm1, const SortKey *key0,
                     const SortKey *key1, uint64_t max_tiles, uint64_t *scan_tmp, cudaStream_t s, int sms) {
   const unsigned grid = (unsigned)std::min<uint64_t>(std::max<uint64_t>(max_tiles, 1), (uint64_t)sms * 8);
-  k_proj_count<<<grid, 256, 0, s>>>(W, perm0, perm1, key0, key1);
+  pdl(k_proj_count, grid, 256, 0, s, W, perm0, perm1, key0, key1);
   scan_u32(W.ptcount, W.ptscan, &W.ctrl->len[7], max_tiles, scan_tmp, s, sms);
-  k_proj_write<<<grid, 256, 0, s>>>(W, perm0, perm1, key0, key1);
+  pdl(k_proj_write, grid, 256, 0, s, W, perm0, perm1, key0, key1);
 }
 void launch_epilogue(const Wave &W, cudaStream_t s, int sms) {
-  k_epilogue_copy<<<persistent_grid(k_epilogue_copy, sms), kThreads, 0, s>>>(W);
-  k_epilogue_advance<<<1, 1, 0, s>>>(W);
+  pdl(k_epilogue_copy, persistent_grid(k_epilogue_copy, sms), kThreads, 0, s, W);
+  pdl(k_epilogue_advance, 1, 1, 0, s, W);
 }
 
 }  // namespace gs

@@ -86,6 +86,7 @@ __device__ __forceinline__ uint64_t block_scan_excl(uint64_t v, uint64_t *total,
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan(const T *in, const uint64_t *d_n, uint64_t *out, ScanState *st,
                                                         ScanDesc *desc) {
+  gdc_wait();
   __shared__ uint64_t vals[kScanTile];
   __shared__ uint64_t red[kScanThreads / 32];
   __shared__ uint32_t s_tile;
@@ -225,7 +226,7 @@ void scan_impl(const T *in, uint64_t *out, const uint64_t *d_n, uint64_t max_n, 
   const unsigned grid = (unsigned)std::min(tiles, cap);
   ScanState *st = reinterpret_cast<ScanState *>(tmp);
   ScanDesc *desc = reinterpret_cast<ScanDesc *>(tmp + 4);  // 32 bytes in
-  k_scan<T><<<grid, kScanThreads, 0, s>>>(in, d_n, out, st, desc);
+  pdl(k_scan<T>, grid, kScanThreads, 0, s, in, d_n, out, st, desc);
 }
 
 // ------------------------------------------------------------ radix sort
