@@ -414,9 +414,7 @@ void enqueue_front(Pipe &P, int K) {
   const int steps = K >= 2 ? K - 1 : 0;
   for (int step = 0; step < steps; ++step) {
     P.begin(KK_COMPACT);
-    launch_compact_count(W, 0, step, P.cur, sms);
-    scan_u32(W.ccount, W.cscan, &W.ctrl->len[0], (uint64_t)W.nq * cps, b->scan_tmp, P.cur, sms);
-    launch_compact_write(W, 0, step, W.cscan, W.tlist, W.tlist_q, W.tlist_cap, HW_TLIST, P.cur, sms);
+    launch_compact_claim(W, step, P.cur, sms);
     P.end();
     P.begin(KK_EXPLORE);
     launch_explore(W, step, grp, P.cur, sms);

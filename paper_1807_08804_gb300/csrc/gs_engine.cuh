@@ -201,6 +201,7 @@ struct Ctrl {
   uint32_t bkt_fail;                // some query's sample-sort bucket overflowed (merge path runs)
   uint32_t pad_;
   uint64_t nbkt;                    // bucket slots of the sample sort (kBktPerTile per tile)
+  uint64_t tlist_top;               // exploration work list: entries claimed this step
 };
 
 // Everything a kernel needs, passed by value.  Capacities are fixed when the
@@ -272,6 +273,7 @@ void launch_prologue(const Wave &W, cudaStream_t s, int sms);
 void launch_plan(const Wave &W, const uint32_t *type_count, cudaStream_t s, int sms);
 void launch_filter(const Wave &W, cudaStream_t s, int sms);
 void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s, int sms);
+void launch_compact_claim(const Wave &W, uint32_t step, cudaStream_t s, int sms);
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint32_t *owner,
                           uint64_t cap, int hw_slot, cudaStream_t s, int sms);
 void launch_explore(const Wave &W, uint32_t step, int group, cudaStream_t s, int sms);

@@ -589,6 +589,7 @@ __global__ void __launch_bounds__(kThreads) k_chunk_list(Wave W, int mode, uint3
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = gthreads() / 32;
   const uint64_t items = group_items(W, mode);
+  if (gtid() == 0) W.ctrl->tlist_top = 0;  // the claim kernel after this one counts from zero
   for (uint64_t it = gtid() / 32; it < items; it += warps) {
     uint32_t s, gqv = 0;
     const uint32_t *slot;
@@ -640,6 +641,66 @@ __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W) {
 #pragma unroll
       for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
       if (lane == 0) W.ccount[ci] = cnt;
+    }
+  }
+}
+
+// The exploration work list of one step in one pass: per listed chunk of a
+// query's set, the warp counts the chunk's candidates, claims that many
+// places with one atomic, and writes the ids in ascending order with the
+// query beside each.  Chunks land in any order (exploration takes each entry
+// on its own); a query whose chunk would pass the list's end is marked
+// overflowed, the places of that chunk below the end name it, and the size
+// the run asked for is recorded for the pool.
+__global__ void __launch_bounds__(kThreads) k_compact_claim(Wave W) {
+  gdc_wait();
+  const DevGraph &G = W.G;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = gthreads() / 32;
+  const uint64_t items = W.ctrl->len[9];
+  for (uint64_t it = gtid() / 32; it < items; it += warps) {
+    const uint64_t e = W.clist[it];
+    const uint32_t ci = (uint32_t)e, s = ci / G.nchunks, c = ci % G.nchunks;
+    const uint32_t *slot = slot_of(W, (uint32_t)(e >> 32));
+    const uint32_t sw = l1_word(G, slot, c, lane);
+    uint32_t x[32];
+    uint32_t n = 0;
+    if (sw) {
+      load_l0(slot, c, lane, sw, x);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) n += __popc(x[i]);
+    }
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) continue;
+    unsigned long long base = 0;
+    if (lane == 0) {
+      base = atomicAdd((unsigned long long *)&W.ctrl->tlist_top, (unsigned long long)total);
+      atomicMax((unsigned long long *)&W.ctrl->hw[HW_TLIST], base + total);
+    }
+    base = __shfl_sync(kFull, base, 0);
+    if (base + total > W.tlist_cap) {
+      if (lane == 0) mark(W.dq[s], QS_OVERFLOW);
+      for (uint64_t p = base + lane; p < W.tlist_cap; p += 32) W.tlist_q[p] = s;
+      continue;
+    }
+    if (!sw) continue;
+    uint64_t p = base + incl - n;
+    const uint32_t id0 = (c * 32 + lane) * 1024;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      uint32_t w = x[i];
+      while (w) {
+        const int bpos = __ffs(w) - 1;
+        w &= w - 1;
+        W.tlist_q[p] = s;
+        W.tlist[p++] = id0 + i * 32 + bpos;
+      }
     }
   }
 }
@@ -813,7 +874,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_explore(Wave W, uint32_t step) 
   const auto warp = cg::tiled_partition<32>(cg::this_thread_block());
   const auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const DevGraph &Gr = W.G;
-  const uint64_t n = W.cscan[(uint64_t)W.nq * Gr.nchunks];
+  const uint64_t n = W.ctrl->tlist_top;
   const uint64_t items = n < W.tlist_cap ? n : W.tlist_cap;  // entries past the list belong to overflowed queries
   constexpr uint32_t T = 32 / G;
   const uint32_t ti = (threadIdx.x & 31) / G;
@@ -2762,6 +2823,11 @@ void launch_compact_count(const Wave &W, int mode, uint32_t step, cudaStream_t s
   cudaMemsetAsync(&W.ctrl->len[9], 0, sizeof(uint64_t), s);
   pdl(k_chunk_list, grid_items(k_chunk_list, sets * W.G.ipg, sms), kThreads, 0, s, W, mode, step);
   pdl(k_compact_count, persistent_grid(k_compact_count, sms), kThreads, 0, s, W);
+}
+void launch_compact_claim(const Wave &W, uint32_t step, cudaStream_t s, int sms) {
+  cudaMemsetAsync(&W.ctrl->len[9], 0, sizeof(uint64_t), s);
+  pdl(k_chunk_list, grid_items(k_chunk_list, (uint64_t)W.nq * W.G.ipg, sms), kThreads, 0, s, W, 0, step);
+  pdl(k_compact_claim, persistent_grid(k_compact_claim, sms), kThreads, 0, s, W);
 }
 void launch_compact_write(const Wave &W, int mode, uint32_t step, const uint64_t *scan, uint32_t *dst, uint32_t *owner,
                           uint64_t cap, int hw_slot, cudaStream_t s, int sms) {
