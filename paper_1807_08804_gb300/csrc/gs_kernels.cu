@@ -646,29 +646,38 @@ __global__ void __launch_bounds__(kThreads) k_compact_count(Wave W) {
 }
 
 // The exploration work list of one step in one pass: per listed chunk of a
-// query's set, the warp counts the chunk's candidates, claims that many
-// places with one atomic, and writes the ids in ascending order with the
-// query beside each.  Chunks land in any order (exploration takes each entry
-// on its own); a query whose chunk would pass the list's end is marked
-// overflowed, the places of that chunk below the end name it, and the size
-// the run asked for is recorded for the pool.
+// query's set, a warp counts the chunk's candidates; the block's warps take
+// consecutive chunks of the list and claim places for all of them with one
+// atomic, so the list stays grouped by query (the chunk list is in query
+// order) and each warp writes its chunk's ids in ascending order with the
+// query beside each.  A query whose chunk would pass the list's end is
+// marked overflowed, the places of that chunk below the end name it, and
+// the size the run asked for is recorded for the pool.
 __global__ void __launch_bounds__(kThreads) k_compact_claim(Wave W) {
   gdc_wait();
+  __shared__ uint32_t wtot[kThreads / 32];
+  __shared__ unsigned long long bbase;
   const DevGraph &G = W.G;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t warps = gthreads() / 32;
+  const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  constexpr uint32_t kWarps = kThreads / 32;
   const uint64_t items = W.ctrl->len[9];
-  for (uint64_t it = gtid() / 32; it < items; it += warps) {
-    const uint64_t e = W.clist[it];
-    const uint32_t ci = (uint32_t)e, s = ci / G.nchunks, c = ci % G.nchunks;
-    const uint32_t *slot = slot_of(W, (uint32_t)(e >> 32));
-    const uint32_t sw = l1_word(G, slot, c, lane);
+  for (uint64_t it0 = (uint64_t)blockIdx.x * kWarps; it0 < items; it0 += (uint64_t)gridDim.x * kWarps) {  // block-uniform
+    const uint64_t it = it0 + wib;
+    uint32_t s = 0, c = 0, sw = 0, n = 0;
+    const uint32_t *slot = nullptr;
     uint32_t x[32];
-    uint32_t n = 0;
-    if (sw) {
-      load_l0(slot, c, lane, sw, x);
+    if (it < items) {
+      const uint64_t e = W.clist[it];
+      const uint32_t ci = (uint32_t)e;
+      s = ci / G.nchunks;
+      c = ci % G.nchunks;
+      slot = slot_of(W, (uint32_t)(e >> 32));
+      sw = l1_word(G, slot, c, lane);
+      if (sw) {
+        load_l0(slot, c, lane, sw, x);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) n += __popc(x[i]);
+        for (int i = 0; i < 32; ++i) n += __popc(x[i]);
+      }
     }
     uint32_t incl = n;
 #pragma unroll
@@ -676,14 +685,20 @@ __global__ void __launch_bounds__(kThreads) k_compact_claim(Wave W) {
       const uint32_t y = __shfl_up_sync(kFull, incl, o);
       if (lane >= o) incl += y;
     }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) continue;
-    unsigned long long base = 0;
-    if (lane == 0) {
-      base = atomicAdd((unsigned long long *)&W.ctrl->tlist_top, (unsigned long long)total);
-      atomicMax((unsigned long long *)&W.ctrl->hw[HW_TLIST], base + total);
+    const uint32_t total = __shfl_sync(kFull, incl, 31);  // this warp's chunk
+    if (lane == 0) wtot[wib] = total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long sum = 0;
+      for (uint32_t w = 0; w < kWarps; ++w) sum += wtot[w];
+      bbase = sum ? atomicAdd((unsigned long long *)&W.ctrl->tlist_top, sum) : 0;
+      if (sum) atomicMax((unsigned long long *)&W.ctrl->hw[HW_TLIST], bbase + sum);
     }
-    base = __shfl_sync(kFull, base, 0);
+    __syncthreads();
+    uint64_t base = bbase;
+    for (uint32_t w = 0; w < wib; ++w) base += wtot[w];
+    __syncthreads();  // wtot and bbase are read before the next round writes them
+    if (total == 0) continue;
     if (base + total > W.tlist_cap) {
       if (lane == 0) mark(W.dq[s], QS_OVERFLOW);
       for (uint64_t p = base + lane; p < W.tlist_cap; p += 32) W.tlist_q[p] = s;
