@@ -1251,15 +1251,20 @@ __global__ void k_level_sizes(Wave W, uint32_t lvl) {
 }
 
 // The row allocator of a join level (one block): an exclusive scan of the
-// sizes over the queries places every query's rows; a first pass sends away
-// (QS_OVERFLOW) each query that would pass a pool's end, the second assigns
-// the places of the others.
+// sizes over the queries places every query's rows.  A first pass sends away
+// (QS_OVERFLOW) each query that would pass a pool's end and assigns the
+// places as if none did; only when some query was sent away does a second
+// pass assign the places of the others again.
 __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
   gdc_wait();
   __shared__ uint64_t sm[4][32];
   __shared__ uint64_t carry[4];
+  __shared__ int any_over;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) any_over = 0;
   for (int pass = 0; pass < 2; ++pass) {
+    __syncthreads();
+    if (pass == 1 && !any_over) break;  // block-uniform: the first pass's places stand
     if (threadIdx.x == 0) {
       carry[0] = 0; carry[1] = 0;
       carry[2] = W.ctrl->out_rows_total; carry[3] = W.ctrl->out_top;
@@ -1304,6 +1309,16 @@ __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
           if (over) {
             mark(W.dq[qi], QS_OVERFLOW);
             W.lsz[qi].flags = flags | 4u;
+            any_over = 1;
+          }
+          QState &S = W.qs[qi];  // the places if no query is sent away
+          S.cur_row_base = pos[0];
+          S.cur_word_base = pos[1];
+          S.cur_rows = over ? 0 : v[0];
+          if (to_out && !over) {
+            S.out_row_base = pos[2];
+            S.out_word_base = pos[3];
+            S.out_rows = v[2];
           }
         } else {
           QState &S = W.qs[qi];
@@ -1334,6 +1349,14 @@ __global__ void __launch_bounds__(1024) k_level_alloc(Wave W, uint32_t lvl) {
     }
     __syncthreads();
   }
+  if (!any_over)  // block-uniform; the second pass counted them otherwise
+    for (uint32_t qi = threadIdx.x; qi < W.nq; qi += blockDim.x) {
+      const LevelSize &z = W.lsz[qi];
+      if (!(z.flags & 2u)) continue;
+      QState &S = W.qs[qi];
+      S.inter_words += z.v[1];
+      S.peak_words = max(S.peak_words, z.v[1]);
+    }
   if (threadIdx.x == 0) {
     W.ctrl->len[3] = carry[0];
     W.ctrl->out_rows_total = carry[2];
