@@ -299,15 +299,16 @@ def cpu_baseline(workload, g, qs, sample_n=None, min_seconds=10.0, max_repeats=3
             "embeddings_per_s": emb / dt}
 
 
-def serve_measure(gs, dg, qs, rate_qps, duration_s, cap, seed=1, warmup_s=1.0):
+def serve_measure(gs, dg, qs, rate_qps, duration_s, cap, seed=1, warmup_s=1.0, warmup_min=4096):
     """Poisson arrivals at rate_qps for duration_s into the serving loop,
-    after warmup_s of arrivals at the same rate whose results are dropped
-    (the slots capture their pipelines and size their pools then); latency
-    is submit-to-completion as the server observes it."""
+    after warmup_s of arrivals at the same rate (at least warmup_min of
+    them) whose results are dropped: the slots capture their pipelines for
+    each query size and size their pools then.  Latency is
+    submit-to-completion as the server observes it."""
     from paper_1807_08804_gb300 import inputs as I
     pack = gs._QueryPack(qs)
     srv = gs.Server(dg, slots=4, max_batch=256)
-    nw = int(rate_qps * warmup_s)
+    nw = max(int(rate_qps * warmup_s), warmup_min) if warmup_s > 0 else 0
     if nw:
         warr = I.make_arrivals(nw, rate_qps, seed=seed + 1000)
         wt, t0 = [], time.perf_counter()
@@ -349,7 +350,7 @@ def serve_measure(gs, dg, qs, rate_qps, duration_s, cap, seed=1, warmup_s=1.0):
     last = max(done_at) if done_at else float("inf")
     return {"offered_qps": rate_qps, "requests": n, "completed": len(lat), "p50_ms": q(0.50), "p99_ms": q(0.99),
             "p999_ms": q(0.999), "sustained_qps": len(lat) / max(last, submit_end), "submit_s": submit_end,
-            "warmup_s": warmup_s}
+            "warmup_requests": nw}
 
 
 def run_reference(args, world, rank):
